@@ -1,0 +1,321 @@
+"""Benchmark: Newton-operator matvecs per second of the well-conditioned IPM inner solve.
+
+One step = one Newton solve (Section 3: split, preconditioner setup, indefinite PCG on
+eq. augsys, recovery) of the matrix-sensing SDP with n = 200, m = 2000 dense constraints
+A_i = (G_i + G_i^T)/2, G_i iid N(0, 1/n), b = A(U U^T) with U 200 x 3, C = I, rank
+parameter r_hat = 3, at a synthetic NT scaling point with the two-cluster spectrum of
+(A0) (top 3 eigenvalues ~ 1/sqrt(mu) along range(U), the rest ~ sqrt(mu)), mu = 1e-6.
+A "Newton-op matvec" is one PCG iteration: one product with the augmented matrix plus one
+preconditioner application.  value = PCG iterations of all steps / device time of all
+steps (setup and recovery included).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: independent replicas (the solve does not shard), one process per GPU under
+torchrun; value = iterations of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Newton-op matvecs/s (PCG iterations per second of whole Newton solves)"
+UNIT = "matvecs/s"
+N, M, RANK, MU = 200, 2000, 3, 1e-6
+N_INPUTS = 4
+
+
+def workload_config():
+    return {"workload": "matrix-sensing SDP n=200 m=2000 dense A_i, r_hat=3, one Newton solve per step",
+            "n": N, "m": M, "r_hat": RANK, "mu": MU, "scaling_point": "synthetic two-cluster spectrum (A0)",
+            "stop": "||r_k|| <= 1e-12 ||[svec C~; b~]||", "precision": "fp64",
+            "l2": "dense A (321.6 MB fp64) is larger than L2; L2 also flushed before every step"}
+
+
+def make_inputs():
+    import workloads as W
+    prob = W.workload("sensing200")
+    U = prob.meta["U"]
+    ins = []
+    for k in range(N_INPUTS):
+        sp = W.scaling_point(N, RANK, MU, 77 + k, V_top=U)
+        Ct, bt = W.newton_rhs(N, M, 177 + k)
+        ins.append((sp.V, sp.lam, Ct, bt))
+    return prob, ins
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def read_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if any."""
+    p = os.path.join(ROOT, "profiles", "rows_gemvT_sensing200.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        if line.startswith("dram_bytes_per_launch:"):
+            try:
+                return float(line.split(":", 1)[1].split()[0])
+            except ValueError:
+                return None
+    return None
+
+
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "clocks_event_reasons.active", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(prob, ins, budget_s: float = 15.0, max_solves: int = 8):
+    """The oracle's step-by-step reformulation (numpy FP64), timed on the host cores."""
+    import numpy as np
+    from oracle import operators, reform
+    sA = operators.row_norm_scale(prob)
+    iters, t0, solves = 0, time.perf_counter(), 0
+    while solves < max_solves:
+        V, lam, Ct, bt = ins[solves % len(ins)]
+        _, _, _, info = reform.newton_reform(prob, V, lam, Ct, bt, r_hat=RANK, s_A=sA, rtol=1e-12, maxit=2000)
+        iters += info.pcg.iters
+        solves += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": iters / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{solves} whole Newton solves (oracle/reform.py, numpy/scipy FP64 with the default "
+                      f"BLAS threads) of the same workload, {iters} PCG iterations in {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    prob, ins = make_inputs()
+    for _ in range(max(0, min(args.warmup, 1))):
+        cpu_baseline(prob, ins, budget_s=0.0, max_solves=1)
+    t0 = time.perf_counter()
+    iters = 0
+    from oracle import operators, reform
+    sA = operators.row_norm_scale(prob)
+    for k in range(args.steps):
+        V, lam, Ct, bt = ins[k % len(ins)]
+        _, _, _, info = reform.newton_reform(prob, V, lam, Ct, bt, r_hat=RANK, s_A=sA, rtol=1e-12, maxit=2000)
+        iters += info.pcg.iters
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    val = iters / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} whole Newton solves of the workload on the host cores"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    # the oracle baseline runs before any GPU work (no process pool after CUDA init)
+    prob, ins = make_inputs()
+    base = cpu_baseline(prob, ins) if (rank == 0 and world == 1 and not args.no_cpu) else None
+
+    from paper_2407_14013_gb300 import NewtonSolver
+    solver = NewtonSolver(prob, r_hat=RANK, device=str(dev))
+    solver.set_profiling(True)
+    f64 = torch.float64
+    dins = [(torch.from_numpy(V).to(dev), torch.from_numpy(lam).to(dev), torch.from_numpy(Ct).to(dev),
+             torch.from_numpy(bt).to(dev)) for (V, lam, Ct, bt) in ins]
+    out = (torch.empty((N, N), dtype=f64, device=dev), torch.empty(M, dtype=f64, device=dev),
+           torch.empty((N, N), dtype=f64, device=dev))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = solver.stream
+
+    for k in range(args.warmup):
+        solver.solve(*dins[k % N_INPUTS], out=out)
+    torch.cuda.synchronize(dev)
+
+    iters, launches, step_ms = 0, 0, []
+    prof = {"At_ms": 0.0, "At_n": 0, "A_ms": 0.0, "A_n": 0, "setup": 0.0, "pcg": 0.0, "rec": 0.0}
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, _, info = solver.solve(*dins[k % N_INPUTS], out=out)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            iters += info.pcg_iters
+            launches += info.launches
+            prof["At_ms"] += info.prof_At_ms
+            prof["At_n"] += info.prof_At_launches
+            prof["A_ms"] += info.prof_A_ms
+            prof["A_n"] += info.prof_A_launches
+            prof["setup"] += info.setup_ms
+            prof["pcg"] += info.pcg_ms
+            prof["rec"] += info.recover_ms
+            assert info.converged, "Newton solve did not converge"
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    dev_s = sum(step_ms) / 1e3
+    t_tot = torch.tensor([dev_s, float(iters), wall], dtype=f64, device=dev)
+    if world > 1:
+        tmax = t_tot.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t_tot.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        dev_s_max, iters_all = float(tmax[0]), float(tsum[1])
+    else:
+        dev_s_max, iters_all = dev_s, float(iters)
+    value = iters_all / dev_s_max
+
+    # end to end through the C ABI with pinned host buffers (H2D and D2H inside the call)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    hins = [(pin(V.T).t(), pin(lam), pin(Ct), pin(bt)) for (V, lam, Ct, bt) in ins]
+    hout = (torch.empty((N, N), dtype=f64).pin_memory(), torch.empty(M, dtype=f64).pin_memory(),
+            torch.empty((N, N), dtype=f64).pin_memory())
+    solver.set_profiling(False)
+    e2e_steps = 0 if args.no_e2e else max(3, min(args.steps, 10))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e2e_iters = 0
+    for k in range(e2e_steps):
+        _, _, _, info = solver.solve_host(*hins[k % N_INPUTS], out=hout)
+        e2e_iters += info.pcg_iters
+    e2e_s = time.perf_counter() - t0
+    h2d = 8 * (N * N + N + N * N + M)
+    d2h = 8 * (N * N + M + N * N)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = read_peaks()
+    L = N * (N + 1) // 2
+    bytes_per_pass = 8.0 * M * L                     # the dense svec rows, read once per pass
+    avg_At = prof["At_ms"] / max(prof["At_n"], 1)
+    avg_A = prof["A_ms"] / max(prof["A_n"], 1)
+    dom_ms, dom_name = (avg_At, "rows_gemvT (A^T(y) pass)") if prof["At_ms"] >= prof["A_ms"] else \
+        (avg_A, "rows_gemv (A(X) pass)")
+    achieved = bytes_per_pass / (dom_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dev_s_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(workload_config(), parallelism=f"replicas{world}"),
+        "pcg_iters_per_step": iters / args.steps,
+        "phase_ms_per_step": {"setup": prof["setup"] / args.steps, "pcg": prof["pcg"] / args.steps,
+                              "recover": prof["rec"] / args.steps},
+        "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": read_traffic(),
+                     "bytes_per_launch": bytes_per_pass, "avg_launch_ms": dom_ms,
+                     "other_pass": {"A^T_avg_ms": avg_At, "A_avg_ms": avg_A,
+                                    "A^T_GBps": bytes_per_pass / (avg_At * 1e-3) / 1e9,
+                                    "A_GBps": bytes_per_pass / (avg_A * 1e-3) / 1e9,
+                                    "share_of_device_time": (prof["At_ms"] + prof["A_ms"]) / (1e3 * dev_s)}},
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_iters / e2e_s if e2e_steps else None, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
+        "wall_s_timed": wall,
+    }
+    if base is not None:
+        line["cpu_baseline"] = base
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg (profiling runs)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * wcipm.h -- C ABI of the GB300 library for the inner Newton solve of a
+ * primal-dual interior-point method on low-rank SDPs, following
+ * Chiu & Zhang, "Well-conditioned primal-dual interior-point method for
+ * accurate low-rank semidefinite programming" (arXiv 2407.14013).
+ *
+ * Problem (Section 1, eq. sdp-pd):  min <C,X>  s.t.  A(X) = b,  X PSD,
+ * with A(X) = [<A_i, X>]_{i=1..m}.  Given the eigen-decomposition of the
+ * Nesterov-Todd scaling point W = V diag(lam) V^T and the residuals
+ * (C~, b~), one call of sdp_newton_solve returns the Newton direction of
+ * (Newt-eps) (Section 3):
+ *
+ *   [ -(W (x)s W)^{-1}  A^T ] [svec dX]   [svec C~]
+ *   [        A           0  ] [  dy   ] = [   b~  ],   dS = C~ - A^T(dy),
+ *
+ * computed, as the paper proposes, through the well-conditioned augmented
+ * system (eq. augsys) solved by PCG with the indefinite preconditioner of
+ * Cor. pcg, then recovered with eq. recover.  Every step runs in the
+ * library's own CUDA kernels (sm_103a) on the stream given at setup.
+ *
+ * Conventions shared by every entry point
+ *   - Symmetric n x n matrices are full, column-major, FP64 (row- and
+ *     column-major coincide; both triangles must be filled).
+ *   - Unless a function says otherwise, array arguments are DEVICE pointers
+ *     that the caller allocates and owns; they must stay valid until the
+ *     call returns (all calls return after their work has completed on the
+ *     handle's stream).
+ *   - The handle owns all scratch memory; it is allocated once in
+ *     sdp_setup (sized for the largest rank the options allow).  No other
+ *     entry point allocates device memory.
+ *   - Status codes are returned; sdp_last_error() gives a message.  A CUDA
+ *     error reported by the runtime is returned as SDP_ECUDA and leaves the
+ *     handle unusable except for sdp_destroy.
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef WCIPM_H
+#define WCIPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sdp_handle sdp_handle;
+
+typedef enum {
+  SDP_OK = 0,
+  SDP_EINVAL = 1,        /* bad argument: shape, NULL pointer, r out of range, unsorted COO ... */
+  SDP_ENOMEM = 2,        /* workspace allocation failed in sdp_setup                            */
+  SDP_ECUDA = 3,         /* a CUDA runtime error; see sdp_last_error                            */
+  SDP_ENOTCONV = 4,      /* PCG reached max_pcg without the stopping test; outputs hold the last iterate */
+  SDP_ENUMERIC = 5,      /* non-finite or non-positive PCG scalar, or a non-positive pivot     */
+  SDP_ETIMEOUT = 6,      /* reserved: a bounded device-side wait gave up                         */
+  SDP_EUNSUPPORTED = 7   /* option combination not built                                        */
+} sdp_status;
+
+/* Storage kinds of the constraint operator A (eq. sdp-pd; rows svec(A_i) of (Newt-eps)). */
+typedef enum {
+  SDP_A_DIAG = 0,        /* A_i = e_i e_i^T, m = n: A(X) = diag(X)                               */
+  SDP_A_SPARSE_COO = 1,  /* entries (con, row, col, val), row >= col, sorted by con (ascending):
+                            <A_i, X> = sum over entries of con i of val * X[row,col] * (row==col ? 1 : 2) */
+  SDP_A_DENSE_SVEC = 2   /* a_dense: m x n(n+1)/2 row-major, row i = svec(A_i): lower triangle
+                            column by column, off-diagonal entries times sqrt(2) (Notations)     */
+} sdp_a_kind;
+
+typedef enum {
+  SDP_FP64 = 0           /* every product in FP64 (the plain form)                                */
+} sdp_precision;
+
+typedef struct {
+  int32_t n;             /* matrix order, >= 2                                                  */
+  int32_t m;             /* number of constraints, >= 1                                          */
+  int32_t kind;          /* sdp_a_kind                                                          */
+  int32_t pad_;
+  int64_t nnz;           /* SPARSE_COO: number of entries                                        */
+  const int32_t* a_con;  /* SPARSE_COO: device int32[nnz], constraint index, nondecreasing        */
+  const int32_t* a_row;  /* SPARSE_COO: device int32[nnz]                                        */
+  const int32_t* a_col;  /* SPARSE_COO: device int32[nnz], a_col <= a_row                        */
+  const double* a_val;   /* SPARSE_COO: device double[nnz]                                       */
+  const double* a_dense; /* DENSE_SVEC: device double[m * n(n+1)/2]                              */
+} sdp_problem;
+
+typedef struct {
+  int32_t r_fixed;       /* > 0: use this rank parameter r (1 <= r < n)                          */
+  int32_t r_hat;         /* r_fixed == 0: r = argmax_{i <= r_hat} lam_i/lam_{i+1} (Section 7)     */
+  int32_t precision;     /* sdp_precision                                                       */
+  int32_t precond_space; /* 0 = auto (the smaller of m and d), 1 = d x d complement C (Section 6),
+                            2 = m x m complement K = beta I + B D^{-1} B^T (same preconditioner) */
+  int32_t max_pcg;       /* iteration cap                                                       */
+  int32_t check_every;   /* PCG iterations between host reads of the stop flag (>= 1)            */
+  int32_t beta_rule;     /* 0: beta = median(eig E)^2 * ||A||_F^2/m;  1: median(eig E)^2 (Section 7 as printed) */
+  int32_t pad_;
+  double newton_rtol;    /* stop when ||r_k|| <= newton_rtol * ||[svec C~; b~]||; with the second
+                            block of r_k at rounding level, ||r_k|| is the (Newt-eps) residual of
+                            the recovered direction (Lemma smallres)                             */
+} sdp_options;
+
+typedef struct {
+  int32_t r;             /* rank parameter used                                                 */
+  int32_t d;             /* n r - r(r-1)/2                                                      */
+  int32_t pcg_iters;     /* PCG iterations performed                                            */
+  int32_t space;         /* 1 = d-space, 2 = m-space                                            */
+  int32_t converged;     /* 1 if the stopping test held                                         */
+  int32_t pad_;
+  double tau;            /* lambda_{r+1}(W)/2 (eq. EQSigdef)                                     */
+  double beta;           /* preconditioner scale (Cor. pcg)                                      */
+  double res_norm;       /* ||r_k|| of the PCG recurrence at exit                                 */
+  double rhs_norm;       /* ||[svec C~; b~]|| (right side of (Newt-eps))                          */
+  double res0_norm;      /* ||r_0||                                                             */
+  double s_A;            /* ||A||_F^2 / m                                                       */
+  double setup_ms;       /* device time of the split and the preconditioner setup (a1, a2)       */
+  double pcg_ms;         /* device time from the right-hand side to the PCG stop (a3 - a6)       */
+  double recover_ms;     /* device time of the recovery (a8)                                     */
+  double prof_At_ms;     /* with profiling on: summed time of the A^T(y) passes over the dense A */
+  double prof_A_ms;      /* with profiling on: summed time of the A(X) passes over the dense A   */
+  int32_t prof_At_launches;  /* number of those A^T passes that did work                        */
+  int32_t prof_A_launches;   /* number of those A passes that did work                          */
+} sdp_newton_info;
+
+/* Fill *opt with the defaults: r_fixed 0, r_hat 10, FP64, auto space,
+ * max_pcg 2000, check_every 8, beta_rule 0, newton_rtol 1e-12. */
+void sdp_default_options(sdp_options* opt);
+
+/* Validate the problem, record its (device) pointers -- the caller keeps
+ * them alive for the handle's lifetime -- compute s_A = ||A||_F^2/m and
+ * allocate all workspace for ranks up to r_fixed (or r_hat).
+ * `stream` is a cudaStream_t (NULL = legacy default stream). */
+sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt, void* stream,
+                     sdp_handle** out);
+
+/* One Newton solve (Section 3 (Newt-eps) through eq. augsys + eq. recover).
+ *   V    n x n column-major, orthonormal eigenvectors of W (any order)
+ *   lam  n eigenvalues of W, all > 0, paired with the columns of V
+ *   Ct   n x n symmetric residual C~;   bt  m residual b~
+ *   dX   out n x n;  dy  out m;  dS  out n x n (= C~ - A^T(dy))
+ *   info out (host pointer, may be NULL)
+ * All array arguments are device pointers.  Returns SDP_ENOTCONV if the
+ * stopping test did not hold within max_pcg iterations (outputs are still
+ * written from the last iterate). */
+sdp_status sdp_newton_solve(sdp_handle* h, const double* V, const double* lam,
+                            const double* Ct, const double* bt,
+                            double* dX, double* dy, double* dS, sdp_newton_info* info);
+
+/* Same as sdp_newton_solve with every array argument a HOST pointer
+ * (pinned memory gives asynchronous copies); the copies to and from the
+ * device are part of the call. */
+sdp_status sdp_newton_solve_host(sdp_handle* h, const double* V, const double* lam,
+                                 const double* Ct, const double* bt,
+                                 double* dX, double* dy, double* dS, sdp_newton_info* info);
+
+/* Diagnostics: copy `count` doubles of an internal buffer of the most recent solve into the
+ * device array `dst` (stream-ordered, synchronous).  which: 0 = E (n x n), 1 = D = tau^2 Sigma
+ * (d), 2 = B = A Q (m x d, row-major), 3 = inverse of the preconditioner's Schur complement
+ * (d x d or m x m), 4 = eigenvectors sorted by descending eigenvalue (n x n), 5 = the PCG
+ * iterate [u; v] (m + d), 6 = the right side g of eq. augsys (m + d), 7 = the raw device
+ * control block of the PCG loop (its size in doubles), 8..11 = the PCG vectors r, z, p and
+ * A p (m + d each).  SDP_EINVAL if
+ * `count` exceeds the buffer. */
+sdp_status sdp_debug_copy(sdp_handle* h, int32_t which, double* dst, int64_t count);
+
+/* Turn on (1) or off (0) CUDA-event timing of every pass over the dense constraint matrix
+ * (reported in sdp_newton_info.prof_*).  Creates its events on first use. */
+sdp_status sdp_set_profiling(sdp_handle* h, int32_t on);
+
+/* Bytes of device workspace owned by the handle. */
+size_t sdp_workspace_bytes(const sdp_handle* h);
+
+/* Number of kernel launches issued by the most recent solve call. */
+int64_t sdp_last_launch_count(const sdp_handle* h);
+
+/* Message for the most recent failure on this handle (or of sdp_setup when h is NULL). */
+const char* sdp_last_error(const sdp_handle* h);
+
+void sdp_destroy(sdp_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WCIPM_H */

@@ -25,7 +25,7 @@ Each function follows one passage of the paper, in the paper's notation:
 Readings taken where the paper is garbled or silent: the sqrt(2) placement of Section 5; the beta^{-1}
 factors of the block inverse in Section 6; the PCG beta index of Def. pcg;
 beta scaled by s_A = ||A||_F^2/m (equal to the paper's rule when the rows
-svec(A_i) have unit norm); the PCG stop ||r_k|| <= rtol ||g||.
+svec(A_i) have unit norm); the PCG stop ||r_k|| <= rtol ||[svec C~; b~]||.
 """
 from __future__ import annotations
 
@@ -268,19 +268,23 @@ class PCGResult:
     converged: bool
 
 
-def pcg(Aop, b: np.ndarray, Pinv, x0: np.ndarray, rtol: float, maxit: int,
+def pcg(Aop, b: np.ndarray, Pinv, x0: np.ndarray, tol: float, maxit: int,
         keep_iterates: bool = False, stop_norm=None) -> PCGResult:
-    """PCG_k(A, b, P, x0) of Def. pcg with beta_j = <r_{j+1}, z_{j+1}>/<r_j, z_j>."""
+    """PCG_k(A, b, P, x0) of Def. pcg with beta_j = <r_{j+1}, z_{j+1}>/<r_j, z_j>.
+
+    Runs until ||r_k|| <= tol (an absolute threshold chosen by the caller) or maxit.
+    No sign test on <p, A p>: with an indefinite P the iteration is Def. pcg as written,
+    and at the rounding floor that product may change sign without harm.
+    """
     x = x0.copy()
     r = b - Aop(x)
     z = Pinv(r)
     p = z.copy()
     rz = float(r @ z)
-    nb = float(np.linalg.norm(b))
     norm = stop_norm if stop_norm is not None else (lambda v: float(np.linalg.norm(v)))
     hist, xs = [norm(r)], ([x.copy()] if keep_iterates else [])
     k = 0
-    conv = hist[-1] <= rtol * nb
+    conv = hist[-1] <= tol
     while not conv and k < maxit:
         Ap = Aop(p)
         alpha = rz / float(p @ Ap)
@@ -295,7 +299,7 @@ def pcg(Aop, b: np.ndarray, Pinv, x0: np.ndarray, rtol: float, maxit: int,
         hist.append(norm(r))
         if keep_iterates:
             xs.append(x.copy())
-        conv = hist[-1] <= rtol * nb
+        conv = hist[-1] <= tol
     return PCGResult(x=x, iters=k, res_hist=hist, x_hist=xs, converged=conv)
 
 
@@ -332,7 +336,11 @@ def newton_reform(prob, V: np.ndarray, lam: np.ndarray, Ct: np.ndarray, bt: np.n
         return np.concatenate([a, b_])
 
     x0 = np.concatenate([np.zeros(m), v0])
-    res = pcg(Aop, g, Pinv, x0, rtol, maxit, keep_iterates=keep_iterates)
+    # Stop on ||r_k|| <= rtol ||[svec C~; b~]||: with the second-block residual at rounding
+    # level, ||r_k|| is the (Newt-eps) residual of the recovered direction (Lemma smallres),
+    # measured against the right side of (Newt-eps).
+    tol = rtol * math.sqrt(float(np.sum(Ct * Ct)) + float(bt @ bt))
+    res = pcg(Aop, g, Pinv, x0, tol, maxit, keep_iterates=keep_iterates)
     dX, dy, dS = recover(prob, sp, Ct, res.x[:m], res.x[m:])
     return dX, dy, dS, ReformInfo(split=sp, precond=P, pcg=res, g=g)
 

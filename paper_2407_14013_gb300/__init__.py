@@ -1,0 +1,169 @@
+"""GB300 (sm_103a) inner Newton solve of a well-conditioned primal-dual IPM for low-rank SDP.
+
+Chiu & Zhang, arXiv 2407.14013: the Newton system (Newt-eps) is solved through
+the augmented system eq. augsys with the indefinite preconditioned PCG of
+Cor. pcg and recovered with eq. recover.  All arithmetic runs in the CUDA
+library (``libwcipm.so``, C ABI in ``include/wcipm.h``); this module only
+moves torch device tensors across that boundary.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Optional
+
+from . import _native as native
+from ._native import (SDP_A_DENSE_SVEC, SDP_A_DIAG, SDP_A_SPARSE_COO, SDP_ENOTCONV, SDP_FP64, SDP_OK,
+                      SdpError, sdp_default_options)
+
+__all__ = ["NewtonSolver", "SdpError", "native", "SDP_A_DIAG", "SDP_A_SPARSE_COO", "SDP_A_DENSE_SVEC"]
+
+KINDS = {"diag": SDP_A_DIAG, "sparse": SDP_A_SPARSE_COO, "dense": SDP_A_DENSE_SVEC}
+
+
+@dataclass
+class NewtonInfo:
+    r: int
+    d: int
+    pcg_iters: int
+    space: int
+    converged: bool
+    tau: float
+    beta: float
+    res_norm: float
+    rhs_norm: float
+    res0_norm: float
+    s_A: float
+    status: int
+    launches: int
+    setup_ms: float = 0.0
+    pcg_ms: float = 0.0
+    recover_ms: float = 0.0
+    prof_At_ms: float = 0.0
+    prof_A_ms: float = 0.0
+    prof_At_launches: int = 0
+    prof_A_launches: int = 0
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _colmajor(V):
+    """Storage of the matrix V in column-major order (the C ABI's layout), without a copy
+    when V already is a transposed view of a contiguous tensor."""
+    if V.t().is_contiguous():
+        return V
+    return V.t().contiguous().t()
+
+
+class NewtonSolver:
+    """Owns one library handle: problem data on the GPU plus the solve workspace.
+
+    ``prob`` is any object with ``kind`` ("diag" | "sparse" | "dense"), ``n``, ``m``
+    and the matching arrays (``a_dense`` m x n(n+1)/2; ``a_con``, ``a_row``,
+    ``a_col``, ``a_val``), as numpy arrays or torch tensors.
+    """
+
+    def __init__(self, prob, r_fixed: int = 0, r_hat: int = 10, precond_space: int = 0,
+                 max_pcg: int = 2000, check_every: int = 8, beta_rule: int = 0,
+                 newton_rtol: float = 1e-12, device: str = "cuda", stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        f64 = torch.float64
+
+        def dev(a, dtype):
+            if a is None:
+                return None
+            t = a if isinstance(a, torch.Tensor) else torch.from_numpy(a)
+            return t.to(device=self.device, dtype=dtype).contiguous()
+
+        self.kind = KINDS[prob.kind] if isinstance(prob.kind, str) else int(prob.kind)
+        self.n, self.m = int(prob.n), int(prob.m)
+        self._keep = {
+            "a_dense": dev(getattr(prob, "a_dense", None), f64),
+            "a_con": dev(getattr(prob, "a_con", None), torch.int32),
+            "a_row": dev(getattr(prob, "a_row", None), torch.int32),
+            "a_col": dev(getattr(prob, "a_col", None), torch.int32),
+            "a_val": dev(getattr(prob, "a_val", None), f64),
+        }
+        k = self._keep
+        p = native.sdp_problem()
+        p.n, p.m, p.kind = self.n, self.m, self.kind
+        p.nnz = 0 if k["a_val"] is None else int(k["a_val"].numel())
+        p.a_con, p.a_row, p.a_col, p.a_val = _ptr(k["a_con"]), _ptr(k["a_row"]), _ptr(k["a_col"]), _ptr(k["a_val"])
+        p.a_dense = _ptr(k["a_dense"])
+        o = sdp_default_options()
+        o.r_fixed, o.r_hat, o.precond_space = r_fixed, r_hat, precond_space
+        o.max_pcg, o.check_every, o.beta_rule = max_pcg, check_every, beta_rule
+        o.newton_rtol = newton_rtol
+        o.precision = SDP_FP64
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        torch.cuda.synchronize(self.device)
+        self.handle = native.sdp_setup(p, o, int(self.stream.cuda_stream))
+        self.last_info: Optional[NewtonInfo] = None
+
+    def debug_buffer(self, which: int, count: int):
+        """Copy of an internal buffer of the last solve (see sdp_debug_copy)."""
+        t = self.torch.empty(count, dtype=self.torch.float64, device=self.device)
+        native.sdp_debug_copy(self.handle, which, _ptr(t), count)
+        return t
+
+    def set_profiling(self, on: bool = True) -> None:
+        """CUDA-event timing of every pass over the dense constraint matrix."""
+        native.sdp_set_profiling(self.handle, on)
+
+    def workspace_bytes(self) -> int:
+        return native.sdp_workspace_bytes(self.handle)
+
+    def _info(self, ci, st) -> NewtonInfo:
+        return NewtonInfo(r=ci.r, d=ci.d, pcg_iters=ci.pcg_iters, space=ci.space, converged=bool(ci.converged),
+                          tau=ci.tau, beta=ci.beta, res_norm=ci.res_norm, rhs_norm=ci.rhs_norm, res0_norm=ci.res0_norm, s_A=ci.s_A,
+                          status=st, launches=native.sdp_last_launch_count(self.handle),
+                          setup_ms=ci.setup_ms, pcg_ms=ci.pcg_ms, recover_ms=ci.recover_ms,
+                          prof_At_ms=ci.prof_At_ms, prof_A_ms=ci.prof_A_ms,
+                          prof_At_launches=ci.prof_At_launches, prof_A_launches=ci.prof_A_launches)
+
+    def solve(self, V, lam, Ct, bt, out=None, allow_notconv: bool = False):
+        """Newton direction (dX, dy, dS) of (Newt-eps) for W = V diag(lam) V^T; device tensors.
+
+        V may have any strides (it is passed column-major, copied only if needed); Ct is
+        symmetric, so its layout does not matter."""
+        torch = self.torch
+        n, m = self.n, self.m
+        f64 = torch.float64
+        lam, Ct, bt = (t.to(device=self.device, dtype=f64).contiguous() for t in (lam, Ct, bt))
+        V = _colmajor(V.to(device=self.device, dtype=f64))
+        if out is None:
+            out = (torch.empty((n, n), dtype=f64, device=self.device), torch.empty(m, dtype=f64, device=self.device),
+                   torch.empty((n, n), dtype=f64, device=self.device))
+        dX, dy, dS = out
+        ci = native.sdp_newton_info()
+        st = native.sdp_newton_solve(self.handle, _ptr(V), _ptr(lam), _ptr(Ct), _ptr(bt), _ptr(dX), _ptr(dy),
+                                     _ptr(dS), ci, allow_notconv=allow_notconv)
+        self.last_info = self._info(ci, st)
+        return dX, dy, dS, self.last_info
+
+    def solve_host(self, V, lam, Ct, bt, out, allow_notconv: bool = False):
+        """Same solve with host (CPU, ideally pinned) tensors; copies are inside the call.
+        V must already be stored column-major (e.g. ``V.t().contiguous().t()``), so that
+        no host-side copy is hidden in the call."""
+        if not V.t().is_contiguous():
+            raise ValueError("solve_host needs V stored column-major")
+        dX, dy, dS = out
+        ci = native.sdp_newton_info()
+        st = native.sdp_newton_solve_host(self.handle, _ptr(V), _ptr(lam), _ptr(Ct), _ptr(bt), _ptr(dX), _ptr(dy),
+                                          _ptr(dS), ci, allow_notconv=allow_notconv)
+        self.last_info = self._info(ci, st)
+        return dX, dy, dS, self.last_info
+
+    def close(self):
+        if getattr(self, "handle", None):
+            native.sdp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,145 @@
+"""ctypes binding of the C ABI in include/wcipm.h (argument marshalling only).
+
+Every function here forwards to the CUDA library ``libwcipm.so`` built next to
+this file; there is no Python or CPU implementation of any step.  Loading fails
+loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, Structure, c_char_p, c_double, c_int32, c_int64, c_size_t, c_void_p
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwcipm.so")
+
+SDP_OK, SDP_EINVAL, SDP_ENOMEM, SDP_ECUDA, SDP_ENOTCONV, SDP_ENUMERIC, SDP_ETIMEOUT, SDP_EUNSUPPORTED = range(8)
+STATUS_NAMES = ["SDP_OK", "SDP_EINVAL", "SDP_ENOMEM", "SDP_ECUDA", "SDP_ENOTCONV", "SDP_ENUMERIC",
+                "SDP_ETIMEOUT", "SDP_EUNSUPPORTED"]
+SDP_A_DIAG, SDP_A_SPARSE_COO, SDP_A_DENSE_SVEC = 0, 1, 2
+SDP_FP64 = 0
+
+
+class sdp_problem(Structure):
+    _fields_ = [("n", c_int32), ("m", c_int32), ("kind", c_int32), ("pad_", c_int32), ("nnz", c_int64),
+                ("a_con", c_void_p), ("a_row", c_void_p), ("a_col", c_void_p), ("a_val", c_void_p),
+                ("a_dense", c_void_p)]
+
+
+class sdp_options(Structure):
+    _fields_ = [("r_fixed", c_int32), ("r_hat", c_int32), ("precision", c_int32), ("precond_space", c_int32),
+                ("max_pcg", c_int32), ("check_every", c_int32), ("beta_rule", c_int32), ("pad_", c_int32),
+                ("newton_rtol", c_double)]
+
+
+class sdp_newton_info(Structure):
+    _fields_ = [("r", c_int32), ("d", c_int32), ("pcg_iters", c_int32), ("space", c_int32),
+                ("converged", c_int32), ("pad_", c_int32), ("tau", c_double), ("beta", c_double),
+                ("res_norm", c_double), ("rhs_norm", c_double), ("res0_norm", c_double), ("s_A", c_double),
+                ("setup_ms", c_double), ("pcg_ms", c_double), ("recover_ms", c_double),
+                ("prof_At_ms", c_double), ("prof_A_ms", c_double),
+                ("prof_At_launches", c_int32), ("prof_A_launches", c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+EXPORTS = {
+    "sdp_default_options": (None, [POINTER(sdp_options)]),
+    "sdp_setup": (c_int32, [POINTER(sdp_problem), POINTER(sdp_options), c_void_p, POINTER(c_void_p)]),
+    "sdp_newton_solve": (c_int32, [c_void_p] + [c_void_p] * 7 + [POINTER(sdp_newton_info)]),
+    "sdp_newton_solve_host": (c_int32, [c_void_p] + [c_void_p] * 7 + [POINTER(sdp_newton_info)]),
+    "sdp_debug_copy": (c_int32, [c_void_p, c_int32, c_void_p, c_int64]),
+    "sdp_set_profiling": (c_int32, [c_void_p, c_int32]),
+    "sdp_workspace_bytes": (c_size_t, [c_void_p]),
+    "sdp_last_launch_count": (c_int64, [c_void_p]),
+    "sdp_last_error": (c_char_p, [c_void_p]),
+    "sdp_destroy": (None, [c_void_p]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libwcipm.so and declare every exported symbol; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class SdpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+def sdp_default_options() -> sdp_options:
+    o = sdp_options()
+    load().sdp_default_options(ctypes.byref(o))
+    return o
+
+
+def sdp_setup(prob: sdp_problem, opt: sdp_options, stream: int) -> int:
+    lib = load()
+    h = c_void_p()
+    st = lib.sdp_setup(ctypes.byref(prob), ctypes.byref(opt), c_void_p(stream), ctypes.byref(h))
+    if st != SDP_OK:
+        raise SdpError(st, lib.sdp_last_error(None).decode())
+    return h.value
+
+
+def _solve(fn_name: str, h: int, ptrs, info: sdp_newton_info, allow_notconv: bool) -> int:
+    lib = load()
+    st = getattr(lib, fn_name)(c_void_p(h), *[c_void_p(p) for p in ptrs], ctypes.byref(info))
+    if st != SDP_OK and not (allow_notconv and st == SDP_ENOTCONV):
+        raise SdpError(st, lib.sdp_last_error(c_void_p(h)).decode())
+    return st
+
+
+def sdp_newton_solve(h: int, V: int, lam: int, Ct: int, bt: int, dX: int, dy: int, dS: int,
+                     info: sdp_newton_info, allow_notconv: bool = False) -> int:
+    return _solve("sdp_newton_solve", h, (V, lam, Ct, bt, dX, dy, dS), info, allow_notconv)
+
+
+def sdp_newton_solve_host(h: int, V: int, lam: int, Ct: int, bt: int, dX: int, dy: int, dS: int,
+                          info: sdp_newton_info, allow_notconv: bool = False) -> int:
+    return _solve("sdp_newton_solve_host", h, (V, lam, Ct, bt, dX, dy, dS), info, allow_notconv)
+
+
+def sdp_debug_copy(h: int, which: int, dst: int, count: int) -> None:
+    lib = load()
+    st = lib.sdp_debug_copy(c_void_p(h), which, c_void_p(dst), count)
+    if st != SDP_OK:
+        raise SdpError(st, lib.sdp_last_error(c_void_p(h)).decode())
+
+
+def sdp_set_profiling(h: int, on: bool) -> None:
+    lib = load()
+    st = lib.sdp_set_profiling(c_void_p(h), 1 if on else 0)
+    if st != SDP_OK:
+        raise SdpError(st, lib.sdp_last_error(c_void_p(h)).decode())
+
+
+def sdp_workspace_bytes(h: int) -> int:
+    return int(load().sdp_workspace_bytes(c_void_p(h)))
+
+
+def sdp_last_launch_count(h: int) -> int:
+    return int(load().sdp_last_launch_count(c_void_p(h)))
+
+
+def sdp_last_error(h: int | None) -> str:
+    return load().sdp_last_error(c_void_p(h) if h else None).decode()
+
+
+def sdp_destroy(h: int) -> None:
+    load().sdp_destroy(c_void_p(h))

@@ -1,0 +1,76 @@
+// Internal launch wrappers shared by the translation units of the library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace wc {
+
+extern int g_num_sms;
+
+// ---- gemm_f64.cu -----------------------------------------------------------------------------
+cudaError_t gemm_f64(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha,
+                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                     double* C, int64_t ldc, double* ws, size_t ws_elems, int64_t* launches,
+                     const int32_t* done = nullptr);
+
+// ---- rows.cu: products with row-major matrices streamed from memory ---------------------------
+// Partial sums of y_i = <row_i(A), x>: part[s * m + i] over column slabs s (returns slab count).
+int rows_gemv_slabs(int64_t L);
+void rows_gemv(cudaStream_t st, const double* A, int m, int64_t L, const double* x, double* part,
+               const int32_t* done, int64_t* launches);
+// Partial sums of y = sum_i p_i row_i(A): part[g * L + k] over row groups g (returns group count).
+int rows_gemvT_groups(int m, int64_t L);
+void rows_gemvT(cudaStream_t st, const double* A, int m, int64_t L, const double* p, double* part,
+                int groups, const int32_t* done, int64_t* launches);
+// sum_i ||row_i||^2
+void rows_sumsq(cudaStream_t st, const double* A, int m, int64_t L, double* out, double* scratch,
+                int64_t* launches);
+
+// ---- sym.cu: symmetric-matrix layouts ----------------------------------------------------------
+// Y (n x n full) = smat(sum_g part[g * N + idx]) ; scale multiplies the result.
+void svec_unpack_sum(cudaStream_t st, int n, const double* part, int groups, double scale, double* Y,
+                     const int32_t* done, int64_t* launches);
+// out(svec, N) = svec(Z + sym(U Q^T)) with U, Q n x r (U may be NULL).
+void svec_pack_plus(cudaStream_t st, int n, int r, const double* Z, const double* U, const double* Q,
+                    double* out, const int32_t* done, int64_t* launches);
+// Stack of full matrices from svec rows i0 .. i0+mb-1: out[b * (mb n) + il * n + a] = A_{i0+il}[a, b].
+void svec_rows_unpack(cudaStream_t st, const double* A, int n, int i0, int mb, double* out,
+                      int64_t* launches);
+
+// ---- split.cu: eq. EQSigdef ------------------------------------------------------------------
+// Sort lam descending (ties by index), permute V's columns, choose r, tau, beta and write them to ctl;
+// e[k] = diagonal of V^T E V (1 for k < r, lam_k / tau after); Ve = Vs diag(e).
+void split_sort(cudaStream_t st, int n, const double* V, const double* lam, double* Vs, double* lam_s,
+                int64_t* launches);
+void split_params(cudaStream_t st, int n, int r_fixed, int r_hat, int beta_rule, const double* lam_s,
+                  double* e, PcgCtl* ctl, int64_t* launches);
+void split_scale_cols(cudaStream_t st, int n, const double* Vs, const double* e, double* Ve,
+                      int64_t* launches);
+// D (d) = tau^2 Sigma in h-coordinates.
+void split_sigma(cudaStream_t st, int n, int r, const double* lam_s, const PcgCtl* ctl, double* Dv,
+                 int64_t* launches);
+
+// ---- hcoord.cu: coordinates h = [svec B; vec N] of range(Q) (Section 5) ---------------------
+// out[h] = c_out * pack(H)[h] + c_in * in[h] - Dv[h] * pv[h] (any of in / Dv may be NULL)
+void h_pack(cudaStream_t st, int n, int r, const double* H, int64_t ldH, double c_out, const double* in,
+            double c_in, const double* Dv, const double* pv, double* out, const int32_t* done,
+            int64_t* launches);
+// Hp (n x r) with Vs Hp = Q B + sqrt2 Qp N for h = [svec B; vec N]
+void h_unpack(cudaStream_t st, int n, int r, const double* h, double* Hp, const int32_t* done,
+              int64_t* launches);
+// B rows of A Q from a batch H = Vs^T [A_i Q] (n x mb r, column j * mb + il): B[(i0+il) * d + h]
+void h_pack_rows(cudaStream_t st, int n, int r, int mb, int i0, const double* H, double* B,
+                 int64_t ldB, int64_t* launches);
+// DIAG kind: B[i, :] = pack(Vs[i, :]^T Q[i, :])
+void h_pack_rows_diag(cudaStream_t st, int n, int r, const double* Vs, double* B, int64_t ldB,
+                      int64_t* launches);
+
+// ---- spd_inverse.cu ----------------------------------------------------------------------------
+// In-place inverse of an SPD matrix (n x n, column-major, ld = n) by blocked Gauss-Jordan.
+cudaError_t spd_inverse(cudaStream_t st, int n, double* A, double* work, size_t work_elems,
+                        double* gemm_ws, size_t gemm_ws_elems, int32_t* status, int64_t* launches);
+
+}  // namespace wc

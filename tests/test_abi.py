@@ -1,0 +1,112 @@
+"""CPU checks of the C ABI boundary: the library builds, loads, and exports every symbol
+that include/wcipm.h declares, with ctypes structures whose layout matches the header."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "wcipm.h")
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(sdp_[a-z_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2407_14013_gb300 import build, _native
+    build.build()
+    return _native.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for need in ("sdp_setup", "sdp_newton_solve", "sdp_newton_solve_host", "sdp_destroy", "sdp_last_error",
+                 "sdp_default_options"):
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2407_14013_gb300 import _native
+    so = _native.LIB_PATH
+    out = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (sdp_[a-z_]+)", out))
+    for name in declared_functions():
+        assert name in exported, f"{name} declared in wcipm.h but not exported"
+        assert name in _native.EXPORTS, f"{name} has no binding"
+
+
+def test_struct_layout_matches_header(lib):
+    """Compile a tiny C program against the header and compare sizeof/offsetof with ctypes."""
+    from paper_2407_14013_gb300 import _native
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "wcipm.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\n", sizeof(sdp_problem), offsetof(sdp_problem, a_dense), sizeof(sdp_options),
+         offsetof(sdp_options, newton_rtol));
+  printf("%zu %zu\n", sizeof(sdp_newton_info), offsetof(sdp_newton_info, s_A));
+  return 0;
+}
+'''
+    tmpd = os.path.join(ROOT, "paper_2407_14013_gb300", "_build")
+    os.makedirs(tmpd, exist_ok=True)
+    c = os.path.join(tmpd, "layout.c")
+    exe = os.path.join(tmpd, "layout")
+    open(c, "w").write(src)
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+    vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
+    assert vals[0] == ctypes.sizeof(_native.sdp_problem)
+    assert vals[1] == _native.sdp_problem.a_dense.offset
+    assert vals[2] == ctypes.sizeof(_native.sdp_options)
+    assert vals[3] == _native.sdp_options.newton_rtol.offset
+    assert vals[4] == ctypes.sizeof(_native.sdp_newton_info)
+    assert vals[5] == _native.sdp_newton_info.s_A.offset
+
+
+def test_default_options_and_setup_errors(lib):
+    """Host-side validation needs no GPU: bad shapes are rejected before any CUDA call."""
+    from paper_2407_14013_gb300 import _native
+    o = _native.sdp_default_options()
+    assert o.r_hat == 10 and o.max_pcg == 2000 and o.newton_rtol == 1e-12
+    p = _native.sdp_problem()
+    p.n, p.m, p.kind = 1, 1, _native.SDP_A_DIAG
+    with pytest.raises(_native.SdpError) as e:
+        _native.sdp_setup(p, o, 0)
+    assert e.value.status == _native.SDP_EINVAL
+    p.n, p.m, p.kind = 4, 3, _native.SDP_A_DIAG
+    with pytest.raises(_native.SdpError) as e:
+        _native.sdp_setup(p, o, 0)
+    assert e.value.status == _native.SDP_EINVAL
+    p.n, p.m, p.kind = 4, 4, _native.SDP_A_DENSE_SVEC
+    with pytest.raises(_native.SdpError) as e:
+        _native.sdp_setup(p, o, 0)                        # a_dense is NULL
+    assert e.value.status == _native.SDP_EINVAL
+    p.kind = _native.SDP_A_DIAG
+    o.r_fixed = 4                                        # r must be < n
+    with pytest.raises(_native.SdpError) as e:
+        _native.sdp_setup(p, o, 0)
+    assert e.value.status == _native.SDP_EINVAL
+
+
+def test_product_path_does_not_touch_the_oracle():
+    """The package never imports the oracle, and fails loudly without its CUDA library."""
+    pkg = os.path.join(ROOT, "paper_2407_14013_gb300")
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            src = open(os.path.join(pkg, f)).read()
+            assert not re.search(r"^\s*(import|from)\s+oracle", src, flags=re.M), f
+    from paper_2407_14013_gb300 import _native
+    saved = _native._lib
+    try:
+        _native._lib = None
+        with pytest.raises(RuntimeError):
+            _native.load(os.path.join(ROOT, "does_not_exist.so"))
+    finally:
+        _native._lib = saved

@@ -1,0 +1,166 @@
+"""GPU parity of the Newton solve (C ABI) against the CPU oracle.
+
+Tolerance: the spec bar for the FP64 form is relative 1e-8.  Both sides solve the
+same well-conditioned augmented system (eq. augsys) to ||r|| <= 1e-12 ||g||; their
+difference is bounded by cond(augsys) * 1e-12 plus rounding, so 1e-8 holds for the
+moderate spectra used here.  Against the plain Schur-complement definition the FP64
+error of that route itself grows like cond(W)^2 eps (Section 1), so those checks use
+mu >= 1e-3 where cond(W)^2 eps < 1e-9.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import linalg, newton as onewton, operators as oops, reform
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-8
+
+
+def _t(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def gpu_solve(prob, sp, Ct, bt, **kw):
+    from paper_2407_14013_gb300 import NewtonSolver
+    s = NewtonSolver(prob, **kw)
+    dX, dy, dS, info = s.solve(_t(sp.V), _t(sp.lam), _t(Ct), _t(bt))
+    out = (dX.cpu().numpy(), dy.cpu().numpy(), dS.cpu().numpy(), info)
+    return s, out
+
+
+def w_of(sp):
+    return (sp.V * sp.lam) @ sp.V.T
+
+
+CASES = [
+    # name, problem factory, r_true, mu, r_hat
+    ("sensing12", lambda: W.sensing(12, 40, 2, 101), 2, 1e-3, 4),
+    ("sensing37_ragged", lambda: W.sensing(37, 150, 3, 102), 3, 1e-3, 5),
+    ("sensing65", lambda: W.sensing(65, 400, 2, 103), 2, 1e-2, 3),
+    ("maxcut64", lambda: W.workload("maxcut64"), 3, 1e-3, 12),
+    ("maxcut130", lambda: W.maxcut(130, 0.05, 104), 4, 1e-2, 6),
+]
+
+
+@pytest.mark.parametrize("name,mk,rt,mu,rh", CASES, ids=[c[0] for c in CASES])
+def test_newton_matches_direct_definition(name, mk, rt, mu, rh):
+    prob = mk()
+    sp = W.scaling_point(prob.n, rt, mu, 200 + prob.n)
+    Ct, bt = W.newton_rhs(prob.n, prob.m, 300 + prob.n)
+    s, (dX, dy, dS, info) = gpu_solve(prob, sp, Ct, bt, r_hat=rh)
+    assert info.converged and info.status == 0
+    rX, ry, rS = onewton.newton_direct(prob, w_of(sp), Ct, bt)
+    assert rel(dX, rX) < TOL and rel(dy, ry) < TOL and rel(dS, rS) < TOL
+    assert np.allclose(dX, dX.T, rtol=0, atol=1e-14 * np.abs(dX).max())
+
+
+@pytest.mark.parametrize("space", [1, 2])
+@pytest.mark.parametrize("name,mk,rt,mu,rh", CASES[:4], ids=[c[0] for c in CASES[:4]])
+def test_newton_matches_reform_oracle_each_space(name, mk, rt, mu, rh, space):
+    """Same r, beta, space and stopping rule as the oracle's step-by-step reformulation."""
+    prob = mk()
+    sp = W.scaling_point(prob.n, rt, 1e-5, 400 + prob.n)
+    Ct, bt = W.newton_rhs(prob.n, prob.m, 500 + prob.n)
+    s, (dX, dy, dS, info) = gpu_solve(prob, sp, Ct, bt, r_hat=rh, precond_space=space)
+    assert info.converged and info.space == space
+    sA = oops.row_norm_scale(prob)
+    oX, oy, oS, oinfo = reform.newton_reform(prob, sp.V, sp.lam, Ct, bt, r_hat=rh, s_A=sA,
+                                             space="d" if space == 1 else "m", rtol=1e-12, maxit=2000)
+    assert info.r == oinfo.split.r and info.d == oinfo.split.d
+    assert abs(info.tau - oinfo.split.tau) <= 1e-14 * oinfo.split.tau
+    assert abs(info.beta - oinfo.split.beta) <= 1e-12 * oinfo.split.beta
+    assert abs(info.s_A - sA) <= 1e-12 * sA
+    assert rel(dX, oX) < TOL and rel(dy, oy) < TOL and rel(dS, oS) < TOL
+    # setup objects: E, D = tau^2 Sigma, B = A Q (row-major)
+    n, m, d = prob.n, prob.m, info.d
+    E = s.debug_buffer(0, n * n).cpu().numpy().reshape(n, n, order="F")
+    assert rel(E, oinfo.split.E) < 1e-12
+    Dv = s.debug_buffer(1, d).cpu().numpy()
+    assert rel(Dv, oinfo.split.tau ** 2 * reform.sigma_vec(oinfo.split)) < 1e-12
+    B = s.debug_buffer(2, m * d).cpu().numpy().reshape(m, d)
+    assert rel(B, oinfo.precond.B) < 1e-12
+    s.close()
+
+
+def test_newt_eps_residual_full_size_sensing200():
+    """Full-size sensing workload (n=200, m=2000, r=3): the recovered direction satisfies
+    (Newt-eps) to a small residual; the residual is evaluated by the oracle's operators."""
+    prob = W.workload("sensing200")
+    sp = W.scaling_point(prob.n, 3, 1e-6, 4242)
+    Ct, bt = W.newton_rhs(prob.n, prob.m, 4243)
+    s, (dX, dy, dS, info) = gpu_solve(prob, sp, Ct, bt, r_hat=3)
+    assert info.converged and info.r == 3 and info.d == 597 and info.space == 1
+    Wm = w_of(sp)
+    res = onewton.newt_eps_residual(prob, Wm, Ct, bt, dX, dy)
+    N = prob.n * (prob.n + 1) // 2
+    # primal block: A(dX) = b~ ; dual block relative to ||C~|| (amplified by ||W^-1||^2 rounding)
+    assert np.linalg.norm(res[N:]) <= 1e-8 * np.linalg.norm(bt)
+    Wi = np.linalg.inv(Wm)
+    scale = np.linalg.norm(Wi @ dX @ Wi) + np.linalg.norm(Ct)
+    assert np.linalg.norm(res[:N]) <= 1e-8 * scale
+    assert np.allclose(dS, Ct - oops.At_op(prob, dy), rtol=0, atol=1e-10 * np.abs(Ct).max())
+    # sampled entries of A(dX) equal b~ (computed one by one from the svec rows)
+    idx = np.random.default_rng(0).choice(prob.m, 16, replace=False)
+    sv = linalg.svec(dX)
+    for i in idx:
+        assert abs(prob.a_dense[i] @ sv - bt[i]) <= 1e-8 * (1 + abs(bt[i]))
+    s.close()
+
+
+def test_host_entry_matches_device_entry():
+    import torch
+    prob = W.sensing(20, 80, 2, 111)
+    sp = W.scaling_point(20, 2, 1e-4, 112)
+    Ct, bt = W.newton_rhs(20, 80, 113)
+    s, (dX, dy, dS, info) = gpu_solve(prob, sp, Ct, bt, r_hat=3)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    out = (torch.empty((20, 20), dtype=torch.float64).pin_memory(), torch.empty(80, dtype=torch.float64).pin_memory(),
+           torch.empty((20, 20), dtype=torch.float64).pin_memory())
+    Vcm = pin(sp.V.T).t()            # pinned, column-major storage of V
+    hX, hy, hS, hinfo = s.solve_host(Vcm, pin(sp.lam), pin(Ct), pin(bt), out)
+    assert np.array_equal(hX.numpy(), dX) and np.array_equal(hy.numpy(), dy) and np.array_equal(hS.numpy(), dS)
+    s.close()
+
+
+def test_edge_cases_rank_and_sizes():
+    # r = n - 1 (largest rank), r = 1, n = 2, m = 1
+    for n, m, rfix in [(6, 10, 5), (6, 10, 1), (2, 2, 1), (5, 1, 1)]:
+        prob = W.sensing(n, m, 1, 600 + n + m)
+        sp = W.scaling_point(n, 1, 1e-2, 601 + n)
+        Ct, bt = W.newton_rhs(n, m, 602 + n)
+        s, (dX, dy, dS, info) = gpu_solve(prob, sp, Ct, bt, r_fixed=rfix)
+        assert info.r == rfix and info.converged
+        rX, ry, rS = onewton.newton_direct(prob, w_of(sp), Ct, bt)
+        assert rel(dX, rX) < TOL and rel(dy, ry) < TOL, (n, m, rfix)
+        s.close()
+
+
+def test_errors_are_reported():
+    from paper_2407_14013_gb300 import SdpError, native
+    prob = W.sensing(8, 20, 2, 700)
+    sp = W.scaling_point(8, 2, 1e-3, 701)
+    Ct, bt = W.newton_rhs(8, 20, 702)
+    lam_bad = sp.lam.copy()
+    lam_bad[3] = -1.0
+    from paper_2407_14013_gb300 import NewtonSolver
+    s = NewtonSolver(prob, r_hat=3)
+    with pytest.raises(SdpError) as e:
+        s.solve(_t(sp.V), _t(lam_bad), _t(Ct), _t(bt))
+    assert e.value.status == native.SDP_EINVAL
+    s.close()
+    s = NewtonSolver(prob, r_hat=3, max_pcg=1, newton_rtol=1e-15)
+    dX, dy, dS, info = s.solve(_t(sp.V), _t(sp.lam), _t(Ct), _t(bt), allow_notconv=True)
+    assert info.status == native.SDP_ENOTCONV and info.pcg_iters == 1 and not info.converged
+    # a later good solve on the same handle still works
+    s2 = NewtonSolver(prob, r_hat=3)
+    _, _, _, i2 = s2.solve(_t(sp.V), _t(sp.lam), _t(Ct), _t(bt))
+    assert i2.converged
+    s.close()
+    s2.close()

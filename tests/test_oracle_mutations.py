@@ -83,7 +83,7 @@ def test_mutation_literal_pcg_beta_breaks_equivalence():
     A = G @ G.T + n * np.eye(n)
     Pm = np.diag(np.diag(A))
     b = g.standard_normal(n)
-    good = reform.pcg(lambda x: A @ x, b, lambda r: np.linalg.solve(Pm, r), np.zeros(n), rtol=0, maxit=n)
+    good = reform.pcg(lambda x: A @ x, b, lambda r: np.linalg.solve(Pm, r), np.zeros(n), tol=0.0, maxit=n)
     assert np.linalg.norm(A @ good.x - b) < 1e-9 * np.linalg.norm(b)
 
     def pcg_literal(maxit):

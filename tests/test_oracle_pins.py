@@ -318,7 +318,7 @@ def test_indefinite_pcg_equals_schur_pcg():
     c = linalg.svec(Ct)
     gH = bt + s.tau ** 2 * Am @ (Eb + s.tau ** -2 * Qb @ Sgi @ Qb.T) @ c
     ref = reform.pcg(lambda x: H @ x, gH, lambda r_: np.linalg.solve(Ht, r_), np.zeros(prob.m),
-                     rtol=0.0, maxit=12, keep_iterates=True)
+                     tol=0.0, maxit=12, keep_iterates=True)
     m = prob.m
     for k in range(1, 10):
         uk = info.pcg.x_hist[k][:m]
@@ -365,7 +365,7 @@ def test_claim_condition_bound_and_cor_pcg_iterations():
 
     gg = np.concatenate([gu, gv])
     eps = 1e-8 * np.linalg.norm(gg)
-    res = reform.pcg(Aop, gg, Pinv, np.concatenate([np.zeros(m), v0]), rtol=1e-8, maxit=500)
+    res = reform.pcg(Aop, gg, Pinv, np.concatenate([np.zeros(m), v0]), tol=eps, maxit=500)
     kE = math.sqrt(np.linalg.eigvalsh(Eb)[-1] / np.linalg.eigvalsh(Eb)[0])
     eA = np.linalg.eigvalsh(Am @ Am.T)
     kA = math.sqrt(eA[-1] / eA[0])
