@@ -164,6 +164,24 @@ sdp_status sdp_debug_copy(sdp_handle* h, int32_t which, double* dst, int64_t cou
  * (reported in sdp_newton_info.prof_*).  Creates its events on first use. */
 sdp_status sdp_set_profiling(sdp_handle* h, int32_t on);
 
+/* Y = A^T(y) = sum_i y_i A_i (n x n, full, column-major) for the dense svec storage of A
+ * (m x n(n+1)/2 row-major, as SDP_A_DENSE_SVEC), without allocating any device memory.
+ * The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (code inside an allocator or memory-pool callback, a process whose device
+ * memory another framework has reserved in full, a path that must not fail with an
+ * out-of-memory error once started).  The caller passes the device arrays a_dense, y (m)
+ * and Y (n x n); the only scratch, the row-group partial sums of A^T(y), lives in a fixed
+ * 4 MiB array in the library's device data, held by every GPU that loads the library
+ * until the process exits.  Limit: n(n+1)/2 <= 524288 (n <= 1023), else SDP_EINVAL.
+ * Other errors: SDP_EINVAL for NULL arrays or n, m < 1; SDP_ECUDA if a CUDA call fails.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  All calls
+ * share the array, so calls that overlap on the GPU race; every value read is written
+ * earlier in the same call, so nothing needs clearing between calls.  `stream` is a
+ * cudaStream_t; the call returns after its work on that stream has completed. */
+sdp_status sdp_adjoint_dense_noalloc(const double* a_dense, int32_t n, int32_t m, const double* y,
+                                     double* Y, void* stream);
+
 /* Bytes of device workspace owned by the handle. */
 size_t sdp_workspace_bytes(const sdp_handle* h);
 

@@ -51,6 +51,7 @@ EXPORTS = {
     "sdp_newton_solve_host": (c_int32, [c_void_p] + [c_void_p] * 7 + [POINTER(sdp_newton_info)]),
     "sdp_debug_copy": (c_int32, [c_void_p, c_int32, c_void_p, c_int64]),
     "sdp_set_profiling": (c_int32, [c_void_p, c_int32]),
+    "sdp_adjoint_dense_noalloc": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
     "sdp_workspace_bytes": (c_size_t, [c_void_p]),
     "sdp_last_launch_count": (c_int64, [c_void_p]),
     "sdp_last_error": (c_char_p, [c_void_p]),
@@ -127,6 +128,12 @@ def sdp_set_profiling(h: int, on: bool) -> None:
     st = lib.sdp_set_profiling(c_void_p(h), 1 if on else 0)
     if st != SDP_OK:
         raise SdpError(st, lib.sdp_last_error(c_void_p(h)).decode())
+
+
+def sdp_adjoint_dense_noalloc(a_dense: int, n: int, m: int, y: int, Y: int, stream: int) -> int:
+    """Y = A^T(y) with no device allocation (fixed scratch in the library); returns the status."""
+    return int(load().sdp_adjoint_dense_noalloc(c_void_p(a_dense), n, m, c_void_p(y), c_void_p(Y),
+                                                c_void_p(stream)))
 
 
 def sdp_workspace_bytes(h: int) -> int:
