@@ -189,51 +189,57 @@ def run_ours(args):
     base = cpu_baseline(prob, ins) if (rank == 0 and world == 1 and not args.no_cpu) else None
 
     from paper_2407_14013_gb300 import NewtonSolver
-    solver = NewtonSolver(prob, r_hat=RANK, device=str(dev))
-    solver.set_profiling(True)
     f64 = torch.float64
     dins = [(torch.from_numpy(V).to(dev), torch.from_numpy(lam).to(dev), torch.from_numpy(Ct).to(dev),
              torch.from_numpy(bt).to(dev)) for (V, lam, Ct, bt) in ins]
     out = (torch.empty((N, N), dtype=f64, device=dev), torch.empty(M, dtype=f64, device=dev),
            torch.empty((N, N), dtype=f64, device=dev))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
-    stream = solver.stream
 
-    for k in range(args.warmup):
-        solver.solve(*dins[k % N_INPUTS], out=out)
-    torch.cuda.synchronize(dev)
-
-    iters, launches, step_ms = 0, 0, []
-    prof = {"At_ms": 0.0, "At_n": 0, "A_ms": 0.0, "A_n": 0, "setup": 0.0, "pcg": 0.0, "rec": 0.0}
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    with ClockSampler(local) as clk:
+    def timed(solver, steps, warmup):
+        """Warm up, then time `steps` whole solves with CUDA events on the solver's stream
+        (L2 flushed before each step, outside the events)."""
+        for k in range(warmup):
+            solver.solve(*dins[k % N_INPUTS], out=out)
+        torch.cuda.synchronize(dev)
+        acc = {"iters": 0, "launches": 0, "refine": 0, "ms": [], "At_ms": 0.0, "At_n": 0, "A_ms": 0.0, "A_n": 0,
+               "At32_ms": 0.0, "At32_n": 0, "A32_ms": 0.0, "A32_n": 0, "setup": 0.0, "pcg": 0.0, "rec": 0.0}
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
         wall0 = time.perf_counter()
-        for k in range(args.steps):
+        for k in range(steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+            e0.record(solver.stream)
             _, _, _, info = solver.solve(*dins[k % N_INPUTS], out=out)
-            e1.record(stream)
+            e1.record(solver.stream)
             e1.synchronize()
-            step_ms.append(e0.elapsed_time(e1))
-            iters += info.pcg_iters
-            launches += info.launches
-            prof["At_ms"] += info.prof_At_ms
-            prof["At_n"] += info.prof_At_launches
-            prof["A_ms"] += info.prof_A_ms
-            prof["A_n"] += info.prof_A_launches
-            prof["setup"] += info.setup_ms
-            prof["pcg"] += info.pcg_ms
-            prof["rec"] += info.recover_ms
+            acc["ms"].append(e0.elapsed_time(e1))
             assert info.converged, "Newton solve did not converge"
+            acc["iters"] += info.pcg_iters
+            acc["launches"] += info.launches
+            acc["refine"] += info.refine_steps
+            for key, val in (("At_ms", info.prof_At_ms), ("At_n", info.prof_At_launches), ("A_ms", info.prof_A_ms),
+                             ("A_n", info.prof_A_launches), ("At32_ms", info.prof_At32_ms),
+                             ("At32_n", info.prof_At32_launches), ("A32_ms", info.prof_A32_ms),
+                             ("A32_n", info.prof_A32_launches), ("setup", info.setup_ms), ("pcg", info.pcg_ms),
+                             ("rec", info.recover_ms)):
+                acc[key] += val
         torch.cuda.synchronize(dev)
-        wall = time.perf_counter() - wall0
-    if world > 1:
-        dist.barrier()
-    dev_s = sum(step_ms) / 1e3
+        acc["wall"] = time.perf_counter() - wall0
+        if world > 1:
+            dist.barrier()
+        return acc
+
+    solver = NewtonSolver(prob, r_hat=RANK, device=str(dev))
+    solver.set_profiling(True)
+    with ClockSampler(local) as clk:
+        res = timed(solver, args.steps, args.warmup)
+    iters, launches, wall = res["iters"], res["launches"], res["wall"]
+    dev_s = sum(res["ms"]) / 1e3
+    prof = res
     t_tot = torch.tensor([dev_s, float(iters), wall], dtype=f64, device=dev)
     if world > 1:
         tmax = t_tot.clone()
@@ -244,6 +250,31 @@ def run_ours(args):
     else:
         dev_s_max, iters_all = dev_s, float(iters)
     value = iters_all / dev_s_max
+
+    # the mixed-precision form (FP32 A E A^T block in the correction solves, FP64 refinement)
+    # on the same inputs
+    mixed = None
+    if not args.no_mixed:
+        msolver = NewtonSolver(prob, r_hat=RANK, device=str(dev), precision="mixed_fp32")
+        msolver.set_profiling(True)
+        mres = timed(msolver, args.steps, args.warmup)
+        mdev_s = sum(mres["ms"]) / 1e3
+        L_ = N * (N + 1) // 2
+        b32 = 4.0 * M * L_
+        mavg = max(mres["At32_ms"] / max(mres["At32_n"], 1), mres["A32_ms"] / max(mres["A32_n"], 1))
+        mixed = {"ms_per_step": 1e3 * mdev_s / args.steps, "newton_solves_per_s": args.steps / mdev_s,
+                 "correction_pcg_iters_per_step": mres["iters"] / args.steps,
+                 "refine_steps_per_step": mres["refine"] / args.steps,
+                 "matvecs_per_s": mres["iters"] / mdev_s,
+                 "fp64_residual_passes_per_step": mres["A_n"] / args.steps,
+                 "speedup_vs_fp64_per_solve": (dev_s / args.steps) / (mdev_s / args.steps),
+                 "phase_ms_per_step": {"setup": mres["setup"] / args.steps, "pcg_and_refinement": mres["pcg"] / args.steps,
+                                       "recover": mres["rec"] / args.steps},
+                 "fp32_pass": {"A^T_avg_ms": mres["At32_ms"] / max(mres["At32_n"], 1),
+                               "A_avg_ms": mres["A32_ms"] / max(mres["A32_n"], 1),
+                               "bytes_per_launch": b32, "GBps_slower_pass": b32 / (mavg * 1e-3) / 1e9},
+                 "gpu_launches": mres["launches"]}
+        msolver.close()
 
     # end to end through the C ABI with pinned host buffers (H2D and D2H inside the call)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -280,6 +311,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": dict(workload_config(), parallelism=f"replicas{world}"),
         "pcg_iters_per_step": iters / args.steps,
+        "newton_solves_per_s": args.steps / dev_s,
         "phase_ms_per_step": {"setup": prof["setup"] / args.steps, "pcg": prof["pcg"] / args.steps,
                               "recover": prof["rec"] / args.steps},
         "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -294,6 +326,7 @@ def run_ours(args):
         "e2e": {"value": e2e_iters / e2e_s if e2e_steps else None, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
         "wall_s_timed": wall,
+        "mixed_fp32": mixed,
     }
     if base is not None:
         line["cpu_baseline"] = base
@@ -310,6 +343,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg (profiling runs)")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -66,7 +66,13 @@ typedef enum {
 } sdp_a_kind;
 
 typedef enum {
-  SDP_FP64 = 0           /* every product in FP64 (the plain form)                                */
+  SDP_FP64 = 0,          /* every product in FP64 (the plain form)                                */
+  SDP_MIXED_FP32 = 1     /* FP64 iterative refinement of the augmented-system solution from x = 0:
+                            the FP64 residual rho = g - M x, then the same PCG on M~ delta = rho
+                            from delta0 = P^{-1}[0; rho_v], x += delta, until the FP64 residual
+                            passes the stop test.  M~ forms the block A E A^T from an FP32 copy
+                            of A (DENSE) or of E o E (DIAG) with FP32 products; its rows with
+                            B = A Q, the vectors, scalars and the preconditioner stay FP64     */
 } sdp_precision;
 
 typedef struct {
@@ -91,24 +97,30 @@ typedef struct {
   int32_t max_pcg;       /* iteration cap                                                       */
   int32_t check_every;   /* PCG iterations between host reads of the stop flag (>= 1)            */
   int32_t beta_rule;     /* 0: beta = median(eig E)^2 * ||A||_F^2/m;  1: median(eig E)^2 (Section 7 as printed) */
-  int32_t pad_;
+  int32_t use_graph;     /* 1: run the PCG iterations as replays of a captured CUDA graph of
+                            check_every iterations (captured on a private stream, launched on
+                            the handle's stream); 0: plain launches                            */
   double newton_rtol;    /* stop when ||r_k|| <= newton_rtol * ||[svec C~; b~]||; with the second
                             block of r_k at rounding level, ||r_k|| is the (Newt-eps) residual of
-                            the recovered direction (Lemma smallres)                             */
+                            the recovered direction (Lemma smallres).  The mixed form applies the
+                            same test to the FP64 residual g - M x                               */
+  int32_t max_refine;    /* mixed form: refinement steps at most                                 */
+  int32_t max_inner;     /* mixed form: PCG iterations per correction solve at most               */
+  double inner_rtol;     /* mixed form: each correction solve stops at ||r|| <= inner_rtol ||r_0|| */
 } sdp_options;
 
 typedef struct {
   int32_t r;             /* rank parameter used                                                 */
   int32_t d;             /* n r - r(r-1)/2                                                      */
-  int32_t pcg_iters;     /* PCG iterations performed                                            */
+  int32_t pcg_iters;     /* PCG iterations performed (mixed form: of all correction solves)      */
   int32_t space;         /* 1 = d-space, 2 = m-space                                            */
   int32_t converged;     /* 1 if the stopping test held                                         */
-  int32_t pad_;
+  int32_t refine_steps;  /* mixed form: correction solves performed (0 in the plain form)        */
   double tau;            /* lambda_{r+1}(W)/2 (eq. EQSigdef)                                     */
   double beta;           /* preconditioner scale (Cor. pcg)                                      */
-  double res_norm;       /* ||r_k|| of the PCG recurrence at exit                                 */
+  double res_norm;       /* ||r_k|| at exit (plain: the PCG recurrence; mixed: the FP64 residual) */
   double rhs_norm;       /* ||[svec C~; b~]|| (right side of (Newt-eps))                          */
-  double res0_norm;      /* ||r_0||                                                             */
+  double res0_norm;      /* ||r_0|| (mixed form: ||g||, the residual at x = 0)                   */
   double s_A;            /* ||A||_F^2 / m                                                       */
   double setup_ms;       /* device time of the split and the preconditioner setup (a1, a2)       */
   double pcg_ms;         /* device time from the right-hand side to the PCG stop (a3 - a6)       */
@@ -117,10 +129,15 @@ typedef struct {
   double prof_A_ms;      /* with profiling on: summed time of the A(X) passes over the dense A   */
   int32_t prof_At_launches;  /* number of those A^T passes that did work                        */
   int32_t prof_A_launches;   /* number of those A passes that did work                          */
+  double prof_At32_ms;   /* the same for the FP32 passes of the mixed form                       */
+  double prof_A32_ms;
+  int32_t prof_At32_launches;
+  int32_t prof_A32_launches;
 } sdp_newton_info;
 
 /* Fill *opt with the defaults: r_fixed 0, r_hat 10, FP64, auto space,
- * max_pcg 2000, check_every 8, beta_rule 0, newton_rtol 1e-12. */
+ * max_pcg 2000, check_every 8, beta_rule 0, use_graph 1, newton_rtol 1e-12, max_refine 10,
+ * max_inner 500, inner_rtol 1e-6. */
 void sdp_default_options(sdp_options* opt);
 
 /* Validate the problem, record its (device) pointers -- the caller keeps
@@ -156,7 +173,7 @@ sdp_status sdp_newton_solve_host(sdp_handle* h, const double* V, const double* l
  * (d x d or m x m), 4 = eigenvectors sorted by descending eigenvalue (n x n), 5 = the PCG
  * iterate [u; v] (m + d), 6 = the right side g of eq. augsys (m + d), 7 = the raw device
  * control block of the PCG loop (its size in doubles), 8..11 = the PCG vectors r, z, p and
- * A p (m + d each).  SDP_EINVAL if
+ * A p (m + d each), 12 = the control block of the correction solve of the mixed form.  SDP_EINVAL if
  * `count` exceeds the buffer. */
 sdp_status sdp_debug_copy(sdp_handle* h, int32_t which, double* dst, int64_t count);
 

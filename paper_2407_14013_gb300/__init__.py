@@ -12,8 +12,8 @@ from dataclasses import dataclass
 from typing import Optional
 
 from . import _native as native
-from ._native import (SDP_A_DENSE_SVEC, SDP_A_DIAG, SDP_A_SPARSE_COO, SDP_ENOTCONV, SDP_FP64, SDP_OK,
-                      SdpError, sdp_default_options)
+from ._native import (SDP_A_DENSE_SVEC, SDP_A_DIAG, SDP_A_SPARSE_COO, SDP_ENOTCONV, SDP_FP64, SDP_MIXED_FP32,
+                      SDP_OK, SdpError, sdp_default_options)
 
 __all__ = ["NewtonSolver", "SdpError", "native", "SDP_A_DIAG", "SDP_A_SPARSE_COO", "SDP_A_DENSE_SVEC"]
 
@@ -42,6 +42,11 @@ class NewtonInfo:
     prof_A_ms: float = 0.0
     prof_At_launches: int = 0
     prof_A_launches: int = 0
+    refine_steps: int = 0
+    prof_At32_ms: float = 0.0
+    prof_A32_ms: float = 0.0
+    prof_At32_launches: int = 0
+    prof_A32_launches: int = 0
 
 
 def _ptr(t) -> int:
@@ -66,7 +71,8 @@ class NewtonSolver:
 
     def __init__(self, prob, r_fixed: int = 0, r_hat: int = 10, precond_space: int = 0,
                  max_pcg: int = 2000, check_every: int = 8, beta_rule: int = 0,
-                 newton_rtol: float = 1e-12, device: str = "cuda", stream=None):
+                 newton_rtol: float = 1e-12, device: str = "cuda", stream=None, use_graph: bool = True,
+                 precision: str = "fp64", max_refine: int = 10, max_inner: int = 500, inner_rtol: float = 1e-6):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -97,7 +103,9 @@ class NewtonSolver:
         o.r_fixed, o.r_hat, o.precond_space = r_fixed, r_hat, precond_space
         o.max_pcg, o.check_every, o.beta_rule = max_pcg, check_every, beta_rule
         o.newton_rtol = newton_rtol
-        o.precision = SDP_FP64
+        o.use_graph = 1 if use_graph else 0
+        o.precision = {"fp64": SDP_FP64, "mixed_fp32": SDP_MIXED_FP32}[precision]
+        o.max_refine, o.max_inner, o.inner_rtol = max_refine, max_inner, inner_rtol
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         torch.cuda.synchronize(self.device)
         self.handle = native.sdp_setup(p, o, int(self.stream.cuda_stream))
@@ -122,7 +130,9 @@ class NewtonSolver:
                           status=st, launches=native.sdp_last_launch_count(self.handle),
                           setup_ms=ci.setup_ms, pcg_ms=ci.pcg_ms, recover_ms=ci.recover_ms,
                           prof_At_ms=ci.prof_At_ms, prof_A_ms=ci.prof_A_ms,
-                          prof_At_launches=ci.prof_At_launches, prof_A_launches=ci.prof_A_launches)
+                          prof_At_launches=ci.prof_At_launches, prof_A_launches=ci.prof_A_launches,
+                          refine_steps=ci.refine_steps, prof_At32_ms=ci.prof_At32_ms, prof_A32_ms=ci.prof_A32_ms,
+                          prof_At32_launches=ci.prof_At32_launches, prof_A32_launches=ci.prof_A32_launches)
 
     def solve(self, V, lam, Ct, bt, out=None, allow_notconv: bool = False):
         """Newton direction (dX, dy, dS) of (Newt-eps) for W = V diag(lam) V^T; device tensors.

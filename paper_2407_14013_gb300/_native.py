@@ -17,7 +17,7 @@ SDP_OK, SDP_EINVAL, SDP_ENOMEM, SDP_ECUDA, SDP_ENOTCONV, SDP_ENUMERIC, SDP_ETIME
 STATUS_NAMES = ["SDP_OK", "SDP_EINVAL", "SDP_ENOMEM", "SDP_ECUDA", "SDP_ENOTCONV", "SDP_ENUMERIC",
                 "SDP_ETIMEOUT", "SDP_EUNSUPPORTED"]
 SDP_A_DIAG, SDP_A_SPARSE_COO, SDP_A_DENSE_SVEC = 0, 1, 2
-SDP_FP64 = 0
+SDP_FP64, SDP_MIXED_FP32 = 0, 1
 
 
 class sdp_problem(Structure):
@@ -28,17 +28,20 @@ class sdp_problem(Structure):
 
 class sdp_options(Structure):
     _fields_ = [("r_fixed", c_int32), ("r_hat", c_int32), ("precision", c_int32), ("precond_space", c_int32),
-                ("max_pcg", c_int32), ("check_every", c_int32), ("beta_rule", c_int32), ("pad_", c_int32),
-                ("newton_rtol", c_double)]
+                ("max_pcg", c_int32), ("check_every", c_int32), ("beta_rule", c_int32), ("use_graph", c_int32),
+                ("newton_rtol", c_double), ("max_refine", c_int32), ("max_inner", c_int32),
+                ("inner_rtol", c_double)]
 
 
 class sdp_newton_info(Structure):
     _fields_ = [("r", c_int32), ("d", c_int32), ("pcg_iters", c_int32), ("space", c_int32),
-                ("converged", c_int32), ("pad_", c_int32), ("tau", c_double), ("beta", c_double),
+                ("converged", c_int32), ("refine_steps", c_int32), ("tau", c_double), ("beta", c_double),
                 ("res_norm", c_double), ("rhs_norm", c_double), ("res0_norm", c_double), ("s_A", c_double),
                 ("setup_ms", c_double), ("pcg_ms", c_double), ("recover_ms", c_double),
                 ("prof_At_ms", c_double), ("prof_A_ms", c_double),
-                ("prof_At_launches", c_int32), ("prof_A_launches", c_int32)]
+                ("prof_At_launches", c_int32), ("prof_A_launches", c_int32),
+                ("prof_At32_ms", c_double), ("prof_A32_ms", c_double),
+                ("prof_At32_launches", c_int32), ("prof_A32_launches", c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}

@@ -63,19 +63,33 @@ __device__ __forceinline__ double ld_stream_d(const double* p, uint64_t pol) {
   return v;
 }
 
+// 16-byte streaming load of four floats (evict-first L2 policy, no L1 allocation).
+__device__ __forceinline__ float4 ld_stream_f4(const float4* p, uint64_t pol) {
+  float4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float ld_stream_f(const float* p, uint64_t pol) {
+  float v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
 // pack(H)[h] for H n x r with leading dimension ldH.
-__device__ __forceinline__ double pack_at(const double* __restrict__ H, int64_t ldH, int n, int r, int h) {
+template <typename T>
+__device__ __forceinline__ double pack_at(const T* __restrict__ H, int64_t ldH, int n, int r, int h) {
   const int nb = r * (r + 1) / 2;
   if (h < nb) {
     int j = 0, base = 0;
     while (h >= base + (r - j)) { base += r - j; ++j; }
     int i = j + (h - base);
-    if (i == j) return H[i + (int64_t)j * ldH];
-    return WC_SQRT2 * 0.5 * (H[i + (int64_t)j * ldH] + H[j + (int64_t)i * ldH]);
+    if (i == j) return (double)H[i + (int64_t)j * ldH];
+    return WC_SQRT2 * 0.5 * ((double)H[i + (int64_t)j * ldH] + (double)H[j + (int64_t)i * ldH]);
   }
   int q = h - nb;
   int k = q % (n - r), j = q / (n - r);
-  return WC_SQRT2 * H[r + k + (int64_t)j * ldH];
+  return WC_SQRT2 * (double)H[r + k + (int64_t)j * ldH];
 }
 
 // Device-resident PCG control block (one per handle).

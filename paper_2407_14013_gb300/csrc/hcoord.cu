@@ -25,7 +25,8 @@ __global__ void h_pack_kernel(int n, int r, const double* __restrict__ H, int64_
   out[h] = v;
 }
 
-__global__ void h_unpack_kernel(int n, int r, const double* __restrict__ h, double* __restrict__ Hp,
+template <typename T>
+__global__ void h_unpack_kernel(int n, int r, const T* __restrict__ h, T* __restrict__ Hp,
                                 const int32_t* __restrict__ done) {
   if (done && *done) return;
   int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -34,27 +35,29 @@ __global__ void h_unpack_kernel(int n, int r, const double* __restrict__ h, doub
   double v;
   if (a < r) {
     int i = a > j ? a : j, jj = a > j ? j : a;
-    double hv = h[svec_index(r, i, jj)];
+    double hv = (double)h[svec_index(r, i, jj)];
     v = (i == jj) ? hv : hv * WC_RSQRT2;
   } else {
-    v = WC_SQRT2 * h[r * (r + 1) / 2 + (a - r) + j * (n - r)];
+    v = WC_SQRT2 * (double)h[r * (r + 1) / 2 + (a - r) + j * (n - r)];
   }
-  Hp[q] = v;
+  Hp[q] = (T)v;
 }
 
 __global__ void h_pack_rows_kernel(int n, int r, int mb, int i0, const double* __restrict__ H,
-                                   double* __restrict__ B, int64_t ldB) {
+                                   double* __restrict__ B, int64_t ldB, double* __restrict__ Bt, int64_t ldBt) {
   const int d = n * r - r * (r - 1) / 2;
   int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (int64_t)mb * d) return;
   const int il = (int)(q / d), h = (int)(q % d);
   // column j of H_il is column j * mb + il of H: H_il = H + il * n with leading dimension mb * n
-  B[(int64_t)(i0 + il) * ldB + h] = pack_at(H + (int64_t)il * n, (int64_t)mb * n, n, r, h);
+  const double v = pack_at(H + (int64_t)il * n, (int64_t)mb * n, n, r, h);
+  B[(int64_t)(i0 + il) * ldB + h] = v;
+  if (Bt) Bt[(int64_t)h * ldBt + i0 + il] = v;
 }
 
 // DIAG: A_i = e_i e_i^T, so Vs^T A_i Q = Vs[i, :]^T Q[i, :].
 __global__ void h_pack_rows_diag_kernel(int n, int r, const double* __restrict__ Vs, double* __restrict__ B,
-                                        int64_t ldB) {
+                                        int64_t ldB, double* __restrict__ Bt, int64_t ldBt) {
   const int d = n * r - r * (r - 1) / 2;
   const int nb = r * (r + 1) / 2;
   int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -73,6 +76,7 @@ __global__ void h_pack_rows_diag_kernel(int n, int r, const double* __restrict__
     v = WC_SQRT2 * Vs[i + (int64_t)(r + k) * n] * Vs[i + (int64_t)j * n];
   }
   B[(int64_t)i * ldB + h] = v;
+  if (Bt) Bt[(int64_t)h * ldBt + i] = v;
 }
 
 inline unsigned nblk(int64_t total, int t) { return (unsigned)((total + t - 1) / t); }
@@ -87,23 +91,25 @@ void h_pack(cudaStream_t st, int n, int r, const double* H, int64_t ldH, double 
   if (launches) ++*launches;
 }
 
-void h_unpack(cudaStream_t st, int n, int r, const double* h, double* Hp, const int32_t* done,
-              int64_t* launches) {
-  h_unpack_kernel<<<nblk((int64_t)n * r, 256), 256, 0, st>>>(n, r, h, Hp, done);
+template <typename T>
+void h_unpack(cudaStream_t st, int n, int r, const T* h, T* Hp, const int32_t* done, int64_t* launches) {
+  h_unpack_kernel<T><<<nblk((int64_t)n * r, 256), 256, 0, st>>>(n, r, h, Hp, done);
   if (launches) ++*launches;
 }
 
+template void h_unpack<double>(cudaStream_t, int, int, const double*, double*, const int32_t*, int64_t*);
+
 void h_pack_rows(cudaStream_t st, int n, int r, int mb, int i0, const double* H, double* B,
-                 int64_t ldB, int64_t* launches) {
+                 int64_t ldB, double* Bt, int64_t ldBt, int64_t* launches) {
   int d = n * r - r * (r - 1) / 2;
-  h_pack_rows_kernel<<<nblk((int64_t)mb * d, 256), 256, 0, st>>>(n, r, mb, i0, H, B, ldB);
+  h_pack_rows_kernel<<<nblk((int64_t)mb * d, 256), 256, 0, st>>>(n, r, mb, i0, H, B, ldB, Bt, ldBt);
   if (launches) ++*launches;
 }
 
 void h_pack_rows_diag(cudaStream_t st, int n, int r, const double* Vs, double* B, int64_t ldB,
-                      int64_t* launches) {
+                      double* Bt, int64_t ldBt, int64_t* launches) {
   int d = n * r - r * (r - 1) / 2;
-  h_pack_rows_diag_kernel<<<nblk((int64_t)n * d, 256), 256, 0, st>>>(n, r, Vs, B, ldB);
+  h_pack_rows_diag_kernel<<<nblk((int64_t)n * d, 256), 256, 0, st>>>(n, r, Vs, B, ldB, Bt, ldBt);
   if (launches) ++*launches;
 }
 

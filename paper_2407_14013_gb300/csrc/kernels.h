@@ -19,23 +19,27 @@ cudaError_t gemm_f64(cudaStream_t st, bool tA, bool tB, int M, int N, int K, dou
 // ---- rows.cu: products with row-major matrices streamed from memory ---------------------------
 // Partial sums of y_i = <row_i(A), x>: part[s * m + i] over column slabs s (returns slab count).
 int rows_gemv_slabs(int64_t L);
-void rows_gemv(cudaStream_t st, const double* A, int m, int64_t L, const double* x, double* part,
-               const int32_t* done, int64_t* launches);
+template <typename T>
+void rows_gemv(cudaStream_t st, const T* A, int m, int64_t L, const T* x, T* part, const int32_t* done,
+               int64_t* launches);
 // Partial sums of y = sum_i p_i row_i(A): part[g * L + k] over row groups g (returns group count).
 int rows_gemvT_groups(int m, int64_t L);
-void rows_gemvT(cudaStream_t st, const double* A, int m, int64_t L, const double* p, double* part,
-                int groups, const int32_t* done, int64_t* launches);
+template <typename T>
+void rows_gemvT(cudaStream_t st, const T* A, int m, int64_t L, const T* p, T* part, int groups,
+                const int32_t* done, int64_t* launches);
 // sum_i ||row_i||^2
 void rows_sumsq(cudaStream_t st, const double* A, int m, int64_t L, double* out, double* scratch,
                 int64_t* launches);
 
 // ---- sym.cu: symmetric-matrix layouts ----------------------------------------------------------
 // Y (n x n full) = smat(sum_g part[g * N + idx]) ; scale multiplies the result.
-void svec_unpack_sum(cudaStream_t st, int n, const double* part, int groups, double scale, double* Y,
+template <typename T>
+void svec_unpack_sum(cudaStream_t st, int n, const T* part, int groups, double scale, T* Y,
                      const int32_t* done, int64_t* launches);
 // out(svec, N) = svec(Z + sym(U Q^T)) with U, Q n x r (U may be NULL).
-void svec_pack_plus(cudaStream_t st, int n, int r, const double* Z, const double* U, const double* Q,
-                    double* out, const int32_t* done, int64_t* launches);
+template <typename T>
+void svec_pack_plus(cudaStream_t st, int n, int r, const T* Z, const T* U, const T* Q, T* out,
+                    const int32_t* done, int64_t* launches);
 // Stack of full matrices from svec rows i0 .. i0+mb-1: out[b * (mb n) + il * n + a] = A_{i0+il}[a, b].
 void svec_rows_unpack(cudaStream_t st, const double* A, int n, int i0, int mb, double* out,
                       int64_t* launches);
@@ -59,17 +63,33 @@ void h_pack(cudaStream_t st, int n, int r, const double* H, int64_t ldH, double 
             double c_in, const double* Dv, const double* pv, double* out, const int32_t* done,
             int64_t* launches);
 // Hp (n x r) with Vs Hp = Q B + sqrt2 Qp N for h = [svec B; vec N]
-void h_unpack(cudaStream_t st, int n, int r, const double* h, double* Hp, const int32_t* done,
-              int64_t* launches);
+template <typename T>
+void h_unpack(cudaStream_t st, int n, int r, const T* h, T* Hp, const int32_t* done, int64_t* launches);
 // B rows of A Q from a batch H = Vs^T [A_i Q] (n x mb r, column j * mb + il): B[(i0+il) * d + h]
 void h_pack_rows(cudaStream_t st, int n, int r, int mb, int i0, const double* H, double* B,
-                 int64_t ldB, int64_t* launches);
+                 int64_t ldB, double* Bt, int64_t ldBt, int64_t* launches);
 // DIAG kind: B[i, :] = pack(Vs[i, :]^T Q[i, :])
 void h_pack_rows_diag(cudaStream_t st, int n, int r, const double* Vs, double* B, int64_t ldB,
-                      int64_t* launches);
+                      double* Bt, int64_t ldBt, int64_t* launches);
+// DENSE kind: G (n x mb r, column j * mb + il) = A_{i0+il} Q for a batch of constraints, straight
+// from the svec rows (one CTA per constraint, per-warp accumulators in shared memory).  Returns
+// false when n r is too large for the shared-memory accumulators.
+bool dense_AiQ(cudaStream_t st, const double* A, int n, int i0, int mb, int r, const double* Q, double* G,
+               int64_t* launches);
+
+// ---- gemm_f32.cu: FP32 GEMM (FFMA tiles, FP32 accumulation), same conventions as gemm_f64 ----
+cudaError_t gemm_f32(cudaStream_t st, bool tA, bool tB, int M, int N, int K, float alpha,
+                     const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
+                     float* C, int64_t ldc, float* ws, size_t ws_elems, int64_t* launches,
+                     const int32_t* done = nullptr);
+// element-wise conversion dst = (To) src
+template <typename To, typename From>
+void convert(cudaStream_t st, int64_t count, const From* src, To* dst, int64_t* launches);
 
 // ---- spd_inverse.cu ----------------------------------------------------------------------------
-// In-place inverse of an SPD matrix (n x n, column-major, ld = n) by blocked Gauss-Jordan.
+// In-place inverse of an SPD matrix (n x n, column-major, ld = n) through its Cholesky factor;
+// work must hold spd_inverse_work(n) doubles.
+size_t spd_inverse_work(int n);
 cudaError_t spd_inverse(cudaStream_t st, int n, double* A, double* work, size_t work_elems,
                         double* gemm_ws, size_t gemm_ws_elems, int32_t* status, int64_t* launches);
 

@@ -10,6 +10,10 @@
 //   a4  operator (matrix-free, Section 5): [A(E A^T(p_u) E + sym(U_p Q^T)); Q^T A^T(p_u) - D p_v]
 //   a5  preconditioner (block-triangular inverse, Section 6)
 //   a6  PCG scalars / updates (Def. pcg)
+//   a7  (mixed form) FP64 refinement: rho = g - M x in FP64, then M~ delta = rho by the same
+//       PCG, where M~ forms the A E A^T block from an FP32 copy of A (the two A passes and the
+//       n^3 products in FP32) and keeps the rows with B = A Q, the vectors, the scalars and the
+//       preconditioner in FP64; x += delta, until the FP64 residual passes the stop test
 //   a8  recovery (eq. recover): dy = u / tau^2, dX = E(A^T u - tau^2 C~)E + sym(U_v Q^T),
 //       dS = C~ - A^T(dy)
 #include <cuda_runtime.h>
@@ -29,6 +33,46 @@
 
 using namespace wc;
 
+namespace {
+
+// The FP64 buffers of one PCG solve.  The inner solve of the mixed form shares everything
+// with the outer one except its vectors and its control block.
+struct Space {
+  double *Vs = nullptr, *E = nullptr, *EE = nullptr, *Dv = nullptr, *B = nullptr, *Bt = nullptr, *Pinv = nullptr;
+  double *Y = nullptr, *F = nullptr, *Z = nullptr, *Tm = nullptr, *H = nullptr, *Hp = nullptr, *Up = nullptr;
+  double *zsvec = nullptr, *partY = nullptr, *partA = nullptr, *sd = nullptr, *wm = nullptr;
+  double *partB = nullptr, *partBt = nullptr, *partC = nullptr;
+  double *x = nullptr, *rv = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr;
+  double* ws = nullptr;                        // split-K GEMM scratch
+  size_t ws_elems = 0;
+  PcgCtl* ctl = nullptr;
+};
+
+// FP32 data of the mixed form's A E A^T block, plus its FP64 partial sums of B p_v, B^T p_u.
+struct Mixed32 {
+  float* A = nullptr;                          // FP32 copy of the svec rows (DENSE kind)
+  float *E = nullptr, *EE = nullptr, *Y = nullptr, *F = nullptr, *Z = nullptr;
+  float *zsvec = nullptr, *partY = nullptr, *partA = nullptr, *pu = nullptr;
+  float* ws = nullptr;
+  size_t ws_elems = 0;
+  double *partBv = nullptr, *partBu = nullptr;
+};
+
+struct ProfEntry {
+  int kind;   // 0: A^T pass FP64, 1: A pass FP64, 2: A^T pass FP32, 3: A pass FP32
+  int iter;   // chunk-local PCG iteration, or -1 outside the loop
+};
+
+struct Graph {
+  cudaGraphExec_t exec = nullptr;
+  int key[4] = {-1, -1, -1, -1};
+  int64_t launches = 0;
+  size_t prof_first = 0, prof_last = 0;
+  std::vector<ProfEntry> entries;
+};
+
+}  // namespace
+
 struct sdp_handle {
   // problem (device pointers owned by the caller)
   int n = 0, m = 0, kind = 0;
@@ -36,44 +80,47 @@ struct sdp_handle {
   const int32_t *a_con = nullptr, *a_row = nullptr, *a_col = nullptr;
   const double *a_val = nullptr, *a_dense = nullptr;
   sdp_options opt{};
+  bool mixed = false;
   cudaStream_t st = nullptr;
-  int r_max = 0, d_max = 0, mb = 0;
+  int r_max = 0, d_max = 0, mb = 0, mb2 = 0;
   double s_A = 1.0;
   // workspace
   char* pool = nullptr;
   size_t pool_bytes = 0;
-  PcgCtl* ctl = nullptr;
-  PcgCtl* ctl_host = nullptr;      // pinned mirror
+  PcgCtl* ctl = nullptr;            // FP64 solve / outer refinement
+  PcgCtl* ctl_in = nullptr;         // inner solve of the mixed form
+  PcgCtl* ctl_host = nullptr;       // pinned mirror
   unsigned int* counter = nullptr;
-  double *Vs = nullptr, *lam_s = nullptr, *e = nullptr, *Ve = nullptr, *E = nullptr, *EE = nullptr;
-  double *Dv = nullptr, *B = nullptr, *Bs = nullptr, *Pinv = nullptr;
-  double *Y = nullptr, *F = nullptr, *Z = nullptr, *Cw = nullptr;
-  double *T = nullptr, *H = nullptr, *Hp = nullptr, *Up = nullptr;
-  double *zsvec = nullptr, *partY = nullptr, *partA = nullptr;
-  double *x = nullptr, *rv = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr, *g = nullptr;
-  double *sd = nullptr, *wm = nullptr, *partB = nullptr, *partBt = nullptr, *partC = nullptr;
+  double *lam_s = nullptr, *e = nullptr, *Ve = nullptr, *Bs = nullptr, *Cw = nullptr, *g = nullptr;
   double *dotbuf = nullptr, *scratch = nullptr;
-  double *gemm_ws = nullptr;
-  size_t gemm_ws_elems = 0;
-  double *gj_work = nullptr;
+  double* gj_work = nullptr;
   size_t gj_work_elems = 0;
   double *ubatch = nullptr, *Gb = nullptr, *Hb = nullptr;
+  int pinv_dim = 0;                 // order of the largest preconditioner core the options allow
+  Space s64;                        // FP64 solve, outer refinement of the mixed form
+  Space sin;                        // inner solve of the mixed form (own vectors and control block)
+  Mixed32 m32;
   // device staging for the host-pointer entry point
   double *hV = nullptr, *hlam = nullptr, *hCt = nullptr, *hbt = nullptr, *hdX = nullptr, *hdy = nullptr, *hdS = nullptr;
   int GY = 1, SA = 1;   // row groups of A^T products, column slabs of A products
   int64_t launches = 0;
   int space = 1, r = 0, d = 0;
+  int refine_steps = 0, inner_iters = 0;
   std::string err;
   // optional CUDA-event timing of the constraint-operator passes (sdp_set_profiling)
-  struct ProfEntry { int kind; int iter; };
   bool prof = false;
+  bool capturing = false;           // inside stream capture: event records become graph nodes
   int cur_iter = -1;
   std::vector<cudaEvent_t> ev;
   std::vector<ProfEntry> prof_entries;
+  size_t prof_base = 0;             // first entry not yet collected
   cudaEvent_t ev_phase[4] = {nullptr, nullptr, nullptr, nullptr};
-  double prof_ms[2] = {0.0, 0.0};
-  int64_t prof_n[2] = {0, 0};
+  double prof_ms[4] = {0, 0, 0, 0};
+  int64_t prof_n[4] = {0, 0, 0, 0};
   double phase_ms[3] = {0.0, 0.0, 0.0};
+  // CUDA graphs of `check_every` PCG iterations (FP64 operator, mixed operator), captured once per shape
+  cudaStream_t cap_stream = nullptr;
+  Graph graph[2];
 };
 
 static std::string g_setup_err;
@@ -100,7 +147,11 @@ extern "C" void sdp_default_options(sdp_options* o) {
   o->max_pcg = 2000;
   o->check_every = 8;
   o->beta_rule = 0;
+  o->use_graph = 1;
   o->newton_rtol = 1e-12;
+  o->max_refine = 10;
+  o->max_inner = 500;
+  o->inner_rtol = 1e-6;
 }
 
 namespace {
@@ -120,61 +171,102 @@ struct Carver {
 
 inline int dof(int n, int r) { return n * r - r * (r - 1) / 2; }
 
+void carve_space(sdp_handle* h, Carver& c, Space& S) {
+  const size_t n = h->n, m = h->m, nn = n * n, rm = h->r_max, dm = h->d_max;
+  const size_t vt = m + dm;
+  const size_t pdim = std::max(dm, m);
+  const size_t pc = h->pinv_dim;
+  S.Vs = c.take<double>(nn);
+  S.E = c.take<double>(nn);
+  S.EE = (h->kind == SDP_A_DIAG) ? c.take<double>(nn) : nullptr;
+  S.Dv = c.take<double>(dm);
+  S.B = c.take<double>(m * dm);
+  S.Bt = c.take<double>(m * dm);
+  S.Pinv = c.take<double>(pc * pc);
+  S.Y = c.take<double>(nn);
+  S.F = c.take<double>(nn);
+  S.Z = c.take<double>(nn);
+  S.Tm = c.take<double>(n * rm);
+  S.H = c.take<double>(n * rm);
+  S.Hp = c.take<double>(n * rm);
+  S.Up = c.take<double>(n * rm);
+  if (h->kind == SDP_A_DENSE_SVEC) {
+    S.zsvec = c.take<double>(h->N);
+    S.partY = c.take<double>((size_t)h->GY * h->N);
+  }
+  const size_t sa = std::max<size_t>(h->SA, (size_t)rows_gemv_slabs(std::max<int64_t>(n, pdim)));
+  S.partA = c.take<double>(sa * std::max(m, pdim));
+  S.x = c.take<double>(vt);
+  S.rv = c.take<double>(vt);
+  S.z = c.take<double>(vt);
+  S.p = c.take<double>(vt);
+  S.Ap = c.take<double>(vt);
+  S.sd = c.take<double>(dm);
+  S.wm = c.take<double>(m);
+  const size_t gb = (size_t)rows_gemv_slabs(std::max<int64_t>(m, 1)) + 1;
+  S.partB = c.take<double>(gb * dm);
+  S.partBt = c.take<double>(gb * dm);
+  S.partC = c.take<double>((size_t)rows_gemv_slabs(std::max<size_t>(pc, 1)) * pc);
+  S.ws_elems = 4 * std::max({nn, pc * pc, (size_t)h->mb2 * n * rm * 2});
+  S.ws = c.take<double>(S.ws_elems);
+}
+
+void carve_mixed(sdp_handle* h, Carver& c, Mixed32& M) {
+  const size_t n = h->n, m = h->m, nn = n * n, dm = h->d_max;
+  if (h->kind == SDP_A_DENSE_SVEC) {
+    M.A = c.take<float>((size_t)m * h->N);
+    M.E = c.take<float>(nn);
+    M.Y = c.take<float>(nn);
+    M.F = c.take<float>(nn);
+    M.Z = c.take<float>(nn);
+    M.zsvec = c.take<float>(h->N);
+    M.partY = c.take<float>((size_t)h->GY * h->N);
+    M.partA = c.take<float>((size_t)h->SA * m);
+  } else {
+    M.EE = c.take<float>(nn);
+    M.partA = c.take<float>((size_t)rows_gemv_slabs(n) * m);
+  }
+  M.pu = c.take<float>(m);
+  M.ws_elems = 4 * nn;
+  M.ws = c.take<float>(M.ws_elems);
+  M.partBv = c.take<double>((size_t)rows_gemv_slabs(std::max<size_t>(dm, 1)) * m);
+  M.partBu = c.take<double>((size_t)rows_gemv_slabs(m) * dm);
+}
+
 // Lay out every buffer; with base == nullptr only the size is computed.
 size_t carve(sdp_handle* h, char* base) {
   Carver c(base);
   const size_t n = h->n, m = h->m, nn = n * n, rm = h->r_max, dm = h->d_max;
   const size_t vt = m + dm;
-  const size_t pdim = std::max(dm, m);
   h->ctl = c.take<PcgCtl>(1);
+  h->ctl_in = c.take<PcgCtl>(1);
   h->counter = c.take<unsigned int>(4);
-  h->Vs = c.take<double>(nn);
   h->lam_s = c.take<double>(n);
   h->e = c.take<double>(n);
   h->Ve = c.take<double>(nn);
-  h->E = c.take<double>(nn);
-  h->EE = (h->kind == SDP_A_DIAG) ? c.take<double>(nn) : nullptr;
-  h->Dv = c.take<double>(dm);
-  h->B = c.take<double>(m * dm);
   h->Bs = c.take<double>(m * dm);
-  h->Pinv = c.take<double>(pdim * pdim);
-  h->Y = c.take<double>(nn);
-  h->F = c.take<double>(nn);
-  h->Z = c.take<double>(nn);
   h->Cw = c.take<double>(nn);
-  h->T = c.take<double>(n * rm);
-  h->H = c.take<double>(n * rm);
-  h->Hp = c.take<double>(n * rm);
-  h->Up = c.take<double>(n * rm);
-  if (h->kind == SDP_A_DENSE_SVEC) {
-    h->zsvec = c.take<double>(h->N);
-    h->partY = c.take<double>((size_t)h->GY * h->N);
-  }
-  const size_t sa = std::max<size_t>(h->SA, (size_t)rows_gemv_slabs(std::max<int64_t>(n, pdim)));
-  h->partA = c.take<double>(sa * std::max(m, pdim));
-  h->x = c.take<double>(vt);
-  h->rv = c.take<double>(vt);
-  h->z = c.take<double>(vt);
-  h->p = c.take<double>(vt);
-  h->Ap = c.take<double>(vt);
   h->g = c.take<double>(vt);
-  h->sd = c.take<double>(dm);
-  h->wm = c.take<double>(m);
-  // upper bound of rows_gemvT_groups(m, d) over every d <= d_max
-  const size_t gb = std::min<size_t>((m + 31) / 32, 4 * (size_t)g_num_sms) + 1;
-  h->partB = c.take<double>(gb * dm);
-  h->partBt = c.take<double>(gb * dm);
-  h->partC = c.take<double>((size_t)rows_gemv_slabs(pdim) * pdim);
   h->dotbuf = c.take<double>(1024);
   h->scratch = c.take<double>(8192);
-  h->gemm_ws_elems = 4 * std::max({nn, dm * dm, pdim * pdim, (size_t)h->mb * n * rm * 2});
-  h->gemm_ws = c.take<double>(h->gemm_ws_elems);
-  h->gj_work_elems = 64 * 64 + 2 * pdim * 64;
+  h->gj_work_elems = spd_inverse_work(h->pinv_dim);
   h->gj_work = c.take<double>(h->gj_work_elems);
   if (h->kind == SDP_A_DENSE_SVEC) {
     h->ubatch = c.take<double>((size_t)h->mb * nn);
-    h->Gb = c.take<double>((size_t)h->mb * n * rm);
-    h->Hb = c.take<double>((size_t)h->mb * n * rm);
+    h->Gb = c.take<double>((size_t)h->mb2 * n * rm);
+    h->Hb = c.take<double>((size_t)h->mb2 * n * rm);
+  }
+  carve_space(h, c, h->s64);
+  h->s64.ctl = h->ctl;
+  if (h->mixed) {
+    h->sin = h->s64;
+    h->sin.x = c.take<double>(vt);
+    h->sin.rv = c.take<double>(vt);
+    h->sin.z = c.take<double>(vt);
+    h->sin.p = c.take<double>(vt);
+    h->sin.Ap = c.take<double>(vt);
+    h->sin.ctl = h->ctl_in;
+    carve_mixed(h, c, h->m32);
   }
   h->hV = c.take<double>(nn);
   h->hlam = c.take<double>(n);
@@ -201,9 +293,12 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
     return fail(nullptr, SDP_EUNSUPPORTED, "constraint kind not built");
   if (prob->kind == SDP_A_DIAG && m != n) return fail(nullptr, SDP_EINVAL, "DIAG kind needs m == n");
   if (prob->kind == SDP_A_DENSE_SVEC && !prob->a_dense) return fail(nullptr, SDP_EINVAL, "a_dense is NULL");
-  if (opt.precision != SDP_FP64) return fail(nullptr, SDP_EUNSUPPORTED, "precision not built");
+  if (opt.precision != SDP_FP64 && opt.precision != SDP_MIXED_FP32)
+    return fail(nullptr, SDP_EUNSUPPORTED, "precision not built");
   if (opt.max_pcg < 1 || opt.check_every < 1 || !(opt.newton_rtol >= 0.0))
     return fail(nullptr, SDP_EINVAL, "bad PCG options");
+  if (opt.precision == SDP_MIXED_FP32 && (opt.max_refine < 1 || opt.max_inner < 1 || !(opt.inner_rtol > 0.0)))
+    return fail(nullptr, SDP_EINVAL, "bad refinement options");
   const int r_max = opt.r_fixed > 0 ? opt.r_fixed : std::min(opt.r_hat, n - 1);
   if (r_max < 1 || r_max >= n) return fail(nullptr, SDP_EINVAL, "rank parameter out of range [1, n)");
   if (opt.precond_space < 0 || opt.precond_space > 2) return fail(nullptr, SDP_EINVAL, "bad precond_space");
@@ -214,10 +309,13 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   h->a_con = prob->a_con; h->a_row = prob->a_row; h->a_col = prob->a_col; h->a_val = prob->a_val;
   h->a_dense = prob->a_dense;
   h->opt = opt;
+  h->mixed = (opt.precision == SDP_MIXED_FP32);
   h->st = static_cast<cudaStream_t>(stream);
   h->N = (int64_t)n * (n + 1) / 2;
   h->r_max = r_max;
   h->d_max = dof(n, r_max);
+  // d-space core (d x d) when d <= m, m-space core (m x m) otherwise, unless forced
+  h->pinv_dim = opt.precond_space == 1 ? h->d_max : opt.precond_space == 2 ? m : std::min(h->d_max, m);
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -227,6 +325,8 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
     // batch of constraints unpacked to full matrices while forming B (at most ~64 MB)
     int64_t per = (int64_t)n * n * 8;
     h->mb = (int)std::max<int64_t>(1, std::min<int64_t>(m, ((int64_t)64 << 20) / per));
+    // batch of constraints whose A_i Q factors are formed at once (at most ~32 MB per factor)
+    h->mb2 = (int)std::max<int64_t>(h->mb, std::min<int64_t>(m, ((int64_t)32 << 20) / ((int64_t)n * r_max * 8)));
   }
   h->pool_bytes = carve(h, nullptr);
   cudaError_t e = cudaMalloc(&h->pool, h->pool_bytes);
@@ -243,7 +343,7 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   }
   std::memset(h->ctl_host, 0, sizeof(PcgCtl));
   CU(cudaMemsetAsync(h->counter, 0, 4 * sizeof(unsigned int), h->st));
-  // s_A = ||A||_F^2 / m (beta rule 0)
+  // s_A = ||A||_F^2 / m (beta rule 0); FP32 copy of A for the mixed form
   if (h->kind == SDP_A_DENSE_SVEC) {
     rows_sumsq(h->st, h->a_dense, m, h->N, h->dotbuf, h->scratch, &h->launches);
     double tot = 0.0;
@@ -254,9 +354,11 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
       sdp_destroy(h);
       return fail(nullptr, SDP_EINVAL, "A has a zero or non-finite Frobenius norm");
     }
+    if (h->mixed) convert<float, double>(h->st, (int64_t)m * h->N, h->a_dense, h->m32.A, &h->launches);
   } else {
     h->s_A = 1.0;
   }
+  CU(cudaStreamSynchronize(h->st));
   *out = h;
   return SDP_OK;
 }
@@ -265,90 +367,246 @@ namespace {
 
 constexpr size_t kProfCap = 8192;
 
-// Bracket one launch with events when profiling (kind 0: A^T pass, 1: A pass).
+// Bracket one launch with events when profiling.
 void prof_begin(sdp_handle* h, int kind) {
   if (!h->prof || h->prof_entries.size() >= kProfCap) return;
   size_t k = h->prof_entries.size();
-  cudaEventRecord(h->ev[2 * k], h->st);
+  if (h->capturing) cudaEventRecordWithFlags(h->ev[2 * k], h->st, cudaEventRecordExternal);
+  else cudaEventRecord(h->ev[2 * k], h->st);
   h->prof_entries.push_back({kind, h->cur_iter});
 }
+
 void prof_end(sdp_handle* h) {
   if (!h->prof || h->prof_entries.empty()) return;
   size_t k = h->prof_entries.size() - 1;
-  cudaEventRecord(h->ev[2 * k + 1], h->st);
+  if (h->capturing) cudaEventRecordWithFlags(h->ev[2 * k + 1], h->st, cudaEventRecordExternal);
+  else cudaEventRecord(h->ev[2 * k + 1], h->st);
 }
 
-// Y = A^T(u) as a full n x n matrix.
-void adjoint_full(sdp_handle* h, const double* u, double* Y, const int32_t* done) {
-  if (h->kind == SDP_A_DENSE_SVEC) {
-    prof_begin(h, 0);
-    rows_gemvT(h->st, h->a_dense, h->m, h->N, u, h->partY, h->GY, done, &h->launches);
-    prof_end(h);
-    svec_unpack_sum(h->st, h->n, h->partY, h->GY, 1.0, Y, done, &h->launches);
-  } else {
-    launch_diag_matrix(h->st, h->n, u, Y, &h->launches);
-  }
-}
-
-// out = M pin (mode 1 also computes alpha) or out = g - M pin (mode 0, g != NULL).
-sdp_status apply_operator(sdp_handle* h, const double* pin, double* out, const double* gsub, int mode) {
-  const int n = h->n, m = h->m, r = h->r, d = h->d;
-  const int32_t* done = &h->ctl->done;
-  cudaStream_t st = h->st;
-  int64_t* L = &h->launches;
-  const double* Q = h->Vs;   // first r columns
-  const size_t ws = h->gemm_ws_elems;
-  const double* pu = pin;
-  const double* pv = pin + m;
-  // Up = Vs Hp with Hp = [B_p; sqrt2 N_p]: Q p_v as an n x r factor (Section 5)
-  h_unpack(st, n, r, pv, h->Hp, done, L);
-  CU(gemm_f64(st, false, false, n, r, n, 1.0, h->Vs, n, h->Hp, n, 0.0, h->Up, n, h->gemm_ws, ws, L, done));
-  if (h->kind == SDP_A_DENSE_SVEC) {
-    adjoint_full(h, pu, h->Y, done);                                   // Y = A^T(p_u)
-    CU(gemm_f64(st, false, false, n, r, n, 1.0, h->Y, n, Q, n, 0.0, h->T, n, h->gemm_ws, ws, L, done));
-    CU(gemm_f64(st, true, false, n, r, n, 1.0, h->Vs, n, h->T, n, 0.0, h->H, n, h->gemm_ws, ws, L, done));
-    CU(gemm_f64(st, false, false, n, n, n, 1.0, h->E, n, h->Y, n, 0.0, h->F, n, h->gemm_ws, ws, L, done));
-    CU(gemm_f64(st, false, false, n, n, n, 1.0, h->F, n, h->E, n, 0.0, h->Z, n, h->gemm_ws, ws, L, done));
-    svec_pack_plus(st, n, r, h->Z, h->Up, Q, h->zsvec, done, L);      // svec(E Y E + sym(Up Q^T))
-    prof_begin(h, 1);
-    rows_gemv(st, h->a_dense, m, h->N, h->zsvec, h->partA, done, L);
-    prof_end(h);
-    launch_ap_finish(st, m, d, n, r, h->partA, h->SA, nullptr, h->Vs, h->H, h->Dv, pin, gsub, out, mode,
-                     h->ctl, h->dotbuf, h->counter, L);
-  } else {
-    launch_diag_scale_rows(st, n, r, pu, h->Vs, h->T, done, L);       // A^T(p_u) Q = diag(p_u) Q
-    CU(gemm_f64(st, true, false, n, r, n, 1.0, h->Vs, n, h->T, n, 0.0, h->H, n, h->gemm_ws, ws, L, done));
-    rows_gemv(st, h->EE, n, n, pu, h->partA, done, L);                 // diag(E diag(p_u) E) = (E o E) p_u
-    launch_ap_finish(st, m, d, n, r, h->partA, rows_gemv_slabs(n), h->Up, h->Vs, h->H, h->Dv, pin, gsub, out,
-                     mode, h->ctl, h->dotbuf, h->counter, L);
+// Time of the profiled launches whose iteration (relative to `base`) ran, given `iters` done.
+// Events first..last-1 belong to entries meta[0..]; meta defaults to prof_entries[first..].
+sdp_status prof_collect(sdp_handle* h, size_t first, size_t last, int base, int iters,
+                        const std::vector<ProfEntry>* meta = nullptr) {
+  for (size_t k = first; k < last; ++k) {
+    const auto& pe = meta ? (*meta)[k - first] : h->prof_entries[k];
+    if (pe.iter >= 0 && base + pe.iter >= iters) continue;   // launches after the stop returned at once
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev[2 * k], h->ev[2 * k + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      return SDP_ECUDA;
+    }
+    h->prof_ms[pe.kind] += ms;
+    h->prof_n[pe.kind] += 1;
   }
   return SDP_OK;
 }
 
-// z = P^{-1} rin (Section 6), then <r, z>; mode 0 sets rz, mode 1 computes the PCG beta.
-void apply_precond(sdp_handle* h, const double* rin, double* zout, int mode) {
-  const int m = h->m, d = h->d;
-  const int32_t* done = &h->ctl->done;
+// Y = A^T(u) as a full n x n matrix (DENSE kind).
+void adjoint_dense(sdp_handle* h, Space& S, const double* u, double* Y, const int32_t* done) {
+  prof_begin(h, 0);
+  rows_gemvT<double>(h->st, h->a_dense, h->m, h->N, u, S.partY, h->GY, done, &h->launches);
+  prof_end(h);
+  svec_unpack_sum<double>(h->st, h->n, S.partY, h->GY, 1.0, Y, done, &h->launches);
+}
+
+// out = M pin (mode 1 also computes alpha) or out = g - M pin (mode 0, g != NULL), in FP64.
+sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* out, const double* gsub, int mode) {
+  const int n = h->n, m = h->m, r = h->r, d = h->d;
+  const int32_t* done = &S.ctl->done;
   cudaStream_t st = h->st;
   int64_t* L = &h->launches;
-  const int Gb = rows_gemvT_groups(m, d);
-  if (h->space == 1) {
-    rows_gemvT(st, h->B, m, d, rin, h->partB, Gb, done, L);           // B^T r_u
-    launch_pc_d_s(st, m, d, Gb, h->partB, rin, h->sd, h->ctl, L);      // s = r_v - beta^{-1} B^T r_u
-    rows_gemv(st, h->Pinv, d, d, h->sd, h->partC, done, L);            // C^{-1} s
-    launch_pc_d_zv(st, m, d, rows_gemv_slabs(d), h->partC, zout, h->ctl, L);
-    rows_gemv(st, h->B, m, d, zout + m, h->partA, done, L);            // B z_v
-    launch_pc_zu_dot(st, m, d, rows_gemv_slabs(d), h->partA, 1, rin, zout, mode, h->ctl, h->dotbuf, h->counter, L);
+  const double* Q = S.Vs;   // first r columns
+  const double* pu = pin;
+  const double* pv = pin + m;
+  // Up = Vs Hp with Hp = [B_p; sqrt2 N_p]: Q p_v as an n x r factor (Section 5)
+  h_unpack<double>(st, n, r, pv, S.Hp, done, L);
+  CU(gemm_f64(st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, S.ws_elems, L, done));
+  if (h->kind == SDP_A_DENSE_SVEC) {
+    adjoint_dense(h, S, pu, S.Y, done);                                // Y = A^T(p_u)
+    CU(gemm_f64(st, false, false, n, r, n, 1.0, S.Y, n, Q, n, 0.0, S.Tm, n, S.ws, S.ws_elems, L, done));
+    CU(gemm_f64(st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, done));
+    CU(gemm_f64(st, false, false, n, n, n, 1.0, S.E, n, S.Y, n, 0.0, S.F, n, S.ws, S.ws_elems, L, done));
+    CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, S.ws_elems, L, done));
+    svec_pack_plus<double>(st, n, r, S.Z, S.Up, Q, S.zsvec, done, L);    // svec(E Y E + sym(Up Q^T))
+    prof_begin(h, 1);
+    rows_gemv<double>(st, h->a_dense, m, h->N, S.zsvec, S.partA, done, L);
+    prof_end(h);
+    launch_ap_finish<double>(st, m, d, n, r, S.partA, h->SA, nullptr, S.Vs, S.H, S.Dv, pin, gsub, out, mode, S.ctl,
+                             h->dotbuf, h->counter, L);
   } else {
-    launch_pc_m_tv(st, m, d, rin, h->Dv, h->sd, h->ctl, L);            // t = D^{-1} r_v
-    rows_gemv(st, h->B, m, d, h->sd, h->partA, done, L);               // B t
-    launch_pc_m_w(st, m, rows_gemv_slabs(d), h->partA, rin, h->wm, h->ctl, L);   // w = r_u + B D^{-1} r_v
-    rows_gemv(st, h->Pinv, m, m, h->wm, h->partC, done, L);            // K^{-1} w
-    launch_pc_m_w(st, m, rows_gemv_slabs(m), h->partC, nullptr, zout, h->ctl, L);  // z_u
-    rows_gemvT(st, h->B, m, d, zout, h->partBt, Gb, done, L);          // B^T z_u
-    launch_pc_m_zv(st, m, d, Gb, h->partBt, rin, h->Dv, zout, h->ctl, L);          // z_v = D^{-1}(B^T z_u - r_v)
-    launch_pc_zu_dot(st, m, d, 0, nullptr, 2, rin, zout, mode, h->ctl, h->dotbuf, h->counter, L);
+    launch_diag_scale_rows<double>(st, n, r, pu, S.Vs, S.Tm, done, L);  // A^T(p_u) Q = diag(p_u) Q
+    CU(gemm_f64(st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, done));
+    rows_gemv<double>(st, S.EE, n, n, pu, S.partA, done, L);              // diag(E diag(p_u) E) = (E o E) p_u
+    launch_ap_finish<double>(st, m, d, n, r, S.partA, rows_gemv_slabs(n), S.Up, S.Vs, S.H, S.Dv, pin, gsub, out,
+                             mode, S.ctl, h->dotbuf, h->counter, L);
   }
+  return SDP_OK;
+}
+
+// The mixed form's operator M~: [A E A^T p_u + B p_v; B^T p_u - D p_v] with A E A^T p_u from the
+// FP32 copies (FP32 products, FP32 accumulation inside each slab, FP64 sum of the slabs) and the
+// B rows in FP64 from the explicit B, so that M~ and the preconditioner share their second block
+// row exactly and the Prop. indefpcg invariant r_v = 0 survives (in the rounding of FP64).
+sdp_status apply_operator_mixed(sdp_handle* h, Space& S, const double* pin, double* out, const double* gsub,
+                                int mode) {
+  const int n = h->n, m = h->m, d = h->d;
+  const int32_t* done = &S.ctl->done;
+  cudaStream_t st = h->st;
+  int64_t* L = &h->launches;
+  Mixed32& M = h->m32;
+  const double* pu = pin;
+  const double* pv = pin + m;
+  launch_to_float(st, m, pu, M.pu, done, L);
+  int SA;
+  if (h->kind == SDP_A_DENSE_SVEC) {
+    prof_begin(h, 2);
+    rows_gemvT<float>(st, M.A, m, h->N, M.pu, M.partY, h->GY, done, L);   // A^T(p_u)
+    prof_end(h);
+    svec_unpack_sum<float>(st, n, M.partY, h->GY, 1.0, M.Y, done, L);
+    CU(gemm_f32(st, false, false, n, n, n, 1.f, M.E, n, M.Y, n, 0.f, M.F, n, M.ws, M.ws_elems, L, done));
+    CU(gemm_f32(st, false, false, n, n, n, 1.f, M.F, n, M.E, n, 0.f, M.Z, n, M.ws, M.ws_elems, L, done));
+    svec_pack_plus<float>(st, n, 0, M.Z, nullptr, nullptr, M.zsvec, done, L);
+    prof_begin(h, 3);
+    rows_gemv<float>(st, M.A, m, h->N, M.zsvec, M.partA, done, L);          // A(E Y E)
+    prof_end(h);
+    SA = h->SA;
+  } else {
+    rows_gemv<float>(st, M.EE, n, n, M.pu, M.partA, done, L);               // (E o E) p_u
+    SA = rows_gemv_slabs(n);
+  }
+  rows_gemv<double>(st, S.B, m, d, pv, M.partBv, done, L);                  // B p_v
+  rows_gemv<double>(st, S.Bt, d, m, pu, M.partBu, done, L);                 // B^T p_u
+  launch_mixed_finish(st, m, d, M.partA, SA, M.partBv, rows_gemv_slabs(d), M.partBu, rows_gemv_slabs(m), S.Dv, pin,
+                      gsub, out, mode, S.ctl, h->dotbuf, h->counter, L);
+  return SDP_OK;
+}
+
+sdp_status apply_op(sdp_handle* h, Space& S, bool mixed, const double* pin, double* out, const double* gsub,
+                    int mode) {
+  return mixed ? apply_operator_mixed(h, S, pin, out, gsub, mode) : apply_operator(h, S, pin, out, gsub, mode);
+}
+
+// z = P^{-1} rin (Section 6), then <r, z>; mode 0 sets rz, mode 1 computes the PCG beta.
+void apply_precond(sdp_handle* h, Space& S, const double* rin, double* zout, int mode) {
+  const int m = h->m, d = h->d;
+  const int32_t* done = &S.ctl->done;
+  cudaStream_t st = h->st;
+  int64_t* L = &h->launches;
+  const int Sm = rows_gemv_slabs(m);
+  if (h->space == 1) {
+    rows_gemv<double>(st, S.Bt, d, m, rin, S.partB, done, L);              // B^T r_u (rows of B^T)
+    launch_pc_d_s<double>(st, m, d, Sm, S.partB, rin, S.sd, S.ctl, L);     // s = r_v - beta^{-1} B^T r_u
+    rows_gemv<double>(st, S.Pinv, d, d, S.sd, S.partC, done, L);           // C^{-1} s
+    launch_pc_d_zv<double>(st, m, d, rows_gemv_slabs(d), S.partC, zout, S.ctl, L);
+    rows_gemv<double>(st, S.B, m, d, zout + m, S.partA, done, L);          // B z_v
+    launch_pc_zu_dot<double>(st, m, d, rows_gemv_slabs(d), S.partA, 1, rin, zout, mode, S.ctl, h->dotbuf,
+                             h->counter, L);
+  } else {
+    launch_pc_m_tv<double>(st, m, d, rin, S.Dv, S.sd, S.ctl, L);           // t = D^{-1} r_v
+    rows_gemv<double>(st, S.B, m, d, S.sd, S.partA, done, L);              // B t
+    launch_pc_m_w<double>(st, m, rows_gemv_slabs(d), S.partA, rin, S.wm, S.ctl, L);   // w = r_u + B D^{-1} r_v
+    rows_gemv<double>(st, S.Pinv, m, m, S.wm, S.partC, done, L);           // K^{-1} w
+    launch_pc_m_w<double>(st, m, rows_gemv_slabs(m), S.partC, nullptr, zout, S.ctl, L);  // z_u
+    rows_gemv<double>(st, S.Bt, d, m, zout, S.partBt, done, L);            // B^T z_u (rows of B^T)
+    launch_pc_m_zv<double>(st, m, d, Sm, S.partBt, rin, S.Dv, zout, S.ctl, L);  // z_v = D^{-1}(B^T z_u - r_v)
+    launch_pc_zu_dot<double>(st, m, d, 0, nullptr, 2, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L);
+  }
+}
+
+// r0 = g - M x (given), stop test, z0 = P^{-1} r0, p0 = z0.  rel_rtol2 > 0 sets a relative threshold.
+sdp_status pcg_start(sdp_handle* h, Space& S, bool mixed, const double* gsub, double rel_rtol2) {
+  sdp_status s = apply_op(h, S, mixed, S.x, S.rv, gsub, 0);
+  if (s != SDP_OK) return s;
+  launch_norm_check<double>(h->st, h->m + h->d, S.rv, rel_rtol2, S.ctl, h->dotbuf, h->counter, &h->launches);
+  apply_precond(h, S, S.rv, S.z, 0);
+  launch_p_update<double>(h->st, h->m + h->d, S.z, S.p, 1, S.ctl, &h->launches);
+  return SDP_OK;
+}
+
+// PCG iterations until the device stop flag is set.  `check_every` iterations run as one
+// replay of a captured CUDA graph (every kernel returns at once after the stop), with one
+// host read of the control block between replays.
+sdp_status pcg_loop(sdp_handle* h, Space& S, bool mixed) {
+  const int every = h->opt.check_every;
+  const int nt = h->m + h->d;
+  Graph& G = h->graph[mixed ? 1 : 0];
+  int64_t* L = &h->launches;
+  cudaStream_t st = h->st;
+  CU(cudaMemcpyAsync(h->ctl_host, S.ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (h->prof) {   // launches recorded so far (outside any graph) are complete: collect them
+    sdp_status ps = prof_collect(h, h->prof_base, h->prof_entries.size(), 0, 1);
+    if (ps != SDP_OK) return fail(h, ps, "event timing failed");
+  }
+  h->prof_entries.clear();
+  h->prof_base = 0;
+  auto chunk = [&](cudaStream_t s_) -> sdp_status {
+    cudaStream_t saved = h->st;
+    h->st = s_;
+    for (int k = 0; k < every; ++k) {
+      h->cur_iter = k;
+      sdp_status s = apply_op(h, S, mixed, S.p, S.Ap, nullptr, 1);
+      if (s != SDP_OK) { h->st = saved; return s; }
+      launch_update<double>(s_, nt, S.x, S.rv, S.p, S.Ap, S.ctl, h->dotbuf, h->counter, L);
+      apply_precond(h, S, S.rv, S.z, 1);
+      launch_p_update<double>(s_, nt, S.z, S.p, 0, S.ctl, L);
+    }
+    h->st = saved;
+    h->cur_iter = -1;
+    return SDP_OK;
+  };
+  const int key[4] = {h->r, h->d, h->space, every * 2 + (h->prof ? 1 : 0)};
+  if (!h->ctl_host->done && h->opt.use_graph) {
+    if (!G.exec || std::memcmp(key, G.key, sizeof(key)) != 0) {
+      if (G.exec) { cudaGraphExecDestroy(G.exec); G.exec = nullptr; }
+      if (!h->cap_stream) CU(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+      const int64_t before = h->launches;
+      CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+      h->capturing = true;
+      sdp_status s = chunk(h->cap_stream);
+      h->capturing = false;
+      cudaGraph_t graph = nullptr;
+      cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
+      if (s != SDP_OK) { if (graph) cudaGraphDestroy(graph); return s; }
+      if (ce != cudaSuccess) return fail(h, SDP_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+      ce = cudaGraphInstantiate(&G.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) return fail(h, SDP_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+      std::memcpy(G.key, key, sizeof(key));
+      G.launches = h->launches - before;
+      h->launches = before;
+      G.prof_first = 0;
+      G.prof_last = h->prof_entries.size();
+      G.entries = h->prof_entries;
+    }
+  }
+  int base = 0;
+  while (!h->ctl_host->done) {
+    size_t first = 0, last = 0;
+    if (h->opt.use_graph) {
+      CU(cudaGraphLaunch(G.exec, st));
+      h->launches += G.launches;
+      first = G.prof_first;
+      last = G.prof_last;
+    } else {
+      h->prof_entries.clear();
+      sdp_status s = chunk(st);
+      if (s != SDP_OK) return s;
+      last = h->prof_entries.size();
+    }
+    CU(cudaMemcpyAsync(h->ctl_host, S.ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (h->prof) {
+      sdp_status ps = h->opt.use_graph ? prof_collect(h, first, last, base, h->ctl_host->iters, &G.entries)
+                                       : prof_collect(h, first, last, base, h->ctl_host->iters);
+      if (ps != SDP_OK) return fail(h, ps, "event timing failed");
+    }
+    base += every;
+  }
+  // later profiled launches take events after the ones the graph records into
+  h->prof_entries.assign(h->opt.use_graph ? G.prof_last : 0, ProfEntry{0, 0});
+  h->prof_base = h->prof_entries.size();
+  return SDP_OK;
 }
 
 }  // namespace
@@ -362,9 +620,14 @@ extern "C" sdp_status sdp_newton_solve(sdp_handle* h, const double* V, const dou
   const int n = h->n, m = h->m;
   cudaStream_t st = h->st;
   int64_t* L = &h->launches;
-  const size_t ws = h->gemm_ws_elems;
+  Space& S = h->s64;
+  const size_t ws = S.ws_elems;
   h->prof_entries.clear();
+  h->prof_base = 0;
   h->cur_iter = -1;
+  for (int k = 0; k < 4; ++k) { h->prof_ms[k] = 0.0; h->prof_n[k] = 0; }
+  h->refine_steps = 0;
+  h->inner_iters = 0;
   if (!h->ev_phase[0])
     for (auto& e : h->ev_phase) CU(cudaEventCreate(&e));
   CU(cudaEventRecord(h->ev_phase[0], st));
@@ -375,7 +638,7 @@ extern "C" sdp_status sdp_newton_solve(sdp_handle* h, const double* V, const dou
   init.max_iters = h->opt.max_pcg;
   init.done = 0;
   CU(cudaMemcpyAsync(h->ctl, &init, sizeof(PcgCtl), cudaMemcpyHostToDevice, st));
-  split_sort(st, n, V, lam, h->Vs, h->lam_s, L);
+  split_sort(st, n, V, lam, S.Vs, h->lam_s, L);
   split_params(st, n, h->opt.r_fixed, h->opt.r_hat, h->opt.beta_rule, h->lam_s, h->e, h->ctl, L);
   CU(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
@@ -386,83 +649,114 @@ extern "C" sdp_status sdp_newton_solve(sdp_handle* h, const double* V, const dou
   h->d = d;
   h->space = h->opt.precond_space == 0 ? (d <= m ? 1 : 2) : h->opt.precond_space;
   const int nt = m + d;
-  split_scale_cols(st, n, h->Vs, h->e, h->Ve, L);
-  CU(gemm_f64(st, false, true, n, n, n, 1.0, h->Ve, n, h->Vs, n, 0.0, h->E, n, h->gemm_ws, ws, L));
-  split_sigma(st, n, r, h->lam_s, h->ctl, h->Dv, L);
+  split_scale_cols(st, n, S.Vs, h->e, h->Ve, L);
+  CU(gemm_f64(st, false, true, n, n, n, 1.0, h->Ve, n, S.Vs, n, 0.0, S.E, n, S.ws, ws, L));
+  split_sigma(st, n, r, h->lam_s, h->ctl, S.Dv, L);
 
   // ---- a2: B = A Q and the preconditioner core ----
   if (h->kind == SDP_A_DENSE_SVEC) {
-    for (int i0 = 0; i0 < m; i0 += h->mb) {
-      const int mb = std::min(h->mb, m - i0);
-      svec_rows_unpack(st, h->a_dense, n, i0, mb, h->ubatch, L);
-      // Gb (mb n x r) = [A_i] Q ; Hb (n x mb r) = Vs^T Gb viewed n x (mb r)
-      CU(gemm_f64(st, false, false, mb * n, r, n, 1.0, h->ubatch, (int64_t)mb * n, h->Vs, n, 0.0, h->Gb,
-                  (int64_t)mb * n, h->gemm_ws, ws, L));
-      CU(gemm_f64(st, true, false, n, mb * r, n, 1.0, h->Vs, n, h->Gb, n, 0.0, h->Hb, n, h->gemm_ws, ws, L));
-      h_pack_rows(st, n, r, mb, i0, h->Hb, h->B, d, L);
+    // row i of B is Q^T svec(A_i) = pack(Vs^T A_i Q): G = [A_i Q] straight from the svec rows,
+    // then one GEMM H = Vs^T G for a whole batch of constraints
+    bool direct = true;
+    for (int i0 = 0; i0 < m && direct; i0 += h->mb2) {
+      const int mb = std::min(h->mb2, m - i0);
+      direct = dense_AiQ(st, h->a_dense, n, i0, mb, r, S.Vs, h->Gb, L);
+      if (!direct) break;
+      CU(gemm_f64(st, true, false, n, mb * r, n, 1.0, S.Vs, n, h->Gb, n, 0.0, h->Hb, n, S.ws, ws, L));
+      h_pack_rows(st, n, r, mb, i0, h->Hb, S.B, d, S.Bt, m, L);
+    }
+    if (!direct) {   // n r too large for the shared-memory accumulators: unpack, then GEMM
+      for (int i0 = 0; i0 < m; i0 += h->mb) {
+        const int mb = std::min(h->mb, m - i0);
+        svec_rows_unpack(st, h->a_dense, n, i0, mb, h->ubatch, L);
+        // Gb (mb n x r) = [A_i] Q ; Hb (n x mb r) = Vs^T Gb viewed n x (mb r)
+        CU(gemm_f64(st, false, false, mb * n, r, n, 1.0, h->ubatch, (int64_t)mb * n, S.Vs, n, 0.0, h->Gb,
+                    (int64_t)mb * n, S.ws, ws, L));
+        CU(gemm_f64(st, true, false, n, mb * r, n, 1.0, S.Vs, n, h->Gb, n, 0.0, h->Hb, n, S.ws, ws, L));
+        h_pack_rows(st, n, r, mb, i0, h->Hb, S.B, d, S.Bt, m, L);
+      }
     }
   } else {
-    launch_hadamard_sq(st, (int64_t)n * n, h->E, h->EE, L);
-    h_pack_rows_diag(st, n, r, h->Vs, h->B, d, L);
+    launch_hadamard_sq(st, (int64_t)n * n, S.E, S.EE, L);
+    h_pack_rows_diag(st, n, r, S.Vs, S.B, d, S.Bt, m, L);
   }
   int32_t* pstatus = &h->ctl->status;
+  const int pd = (h->space == 1) ? d : m;
+  if (pd > h->pinv_dim) return fail(h, SDP_EINVAL, "preconditioner core larger than the setup allows");
   if (h->space == 1) {
     // C = beta^{-1} B^T B + tau^2 Sigma  (B row-major m x d == column-major d x m)
     const double beta = h->ctl_host->beta_pc;
-    CU(gemm_f64(st, false, true, d, d, m, 1.0 / beta, h->B, d, h->B, d, 0.0, h->Pinv, d, h->gemm_ws, ws, L));
-    launch_add_diag(st, d, h->Pinv, h->Dv, 0.0, L);
-    CU(spd_inverse(st, d, h->Pinv, h->gj_work, h->gj_work_elems, h->gemm_ws, ws, pstatus, L));
+    CU(gemm_f64(st, false, true, d, d, m, 1.0 / beta, S.B, d, S.B, d, 0.0, S.Pinv, d, S.ws, ws, L));
+    launch_add_diag(st, d, S.Pinv, S.Dv, 0.0, L);
+    CU(spd_inverse(st, d, S.Pinv, h->gj_work, h->gj_work_elems, S.ws, ws, pstatus, L));
   } else {
     // K = beta I + B D^{-1} B^T = Bs^T Bs + beta I with Bs = D^{-1/2} B^T (d x m)
-    launch_scale_B(st, m, d, h->B, h->Dv, h->Bs, L);
-    CU(gemm_f64(st, true, false, m, m, d, 1.0, h->Bs, d, h->Bs, d, 0.0, h->Pinv, m, h->gemm_ws, ws, L));
-    launch_add_diag(st, m, h->Pinv, nullptr, h->ctl_host->beta_pc, L);
-    CU(spd_inverse(st, m, h->Pinv, h->gj_work, h->gj_work_elems, h->gemm_ws, ws, pstatus, L));
+    launch_scale_B(st, m, d, S.B, S.Dv, h->Bs, L);
+    CU(gemm_f64(st, true, false, m, m, d, 1.0, h->Bs, d, h->Bs, d, 0.0, S.Pinv, m, S.ws, ws, L));
+    launch_add_diag(st, m, S.Pinv, nullptr, h->ctl_host->beta_pc, L);
+    CU(spd_inverse(st, m, S.Pinv, h->gj_work, h->gj_work_elems, S.ws, ws, pstatus, L));
   }
-
+  if (h->mixed) {   // FP32 copies for the A E A^T block of the mixed operator
+    if (S.EE) convert<float, double>(st, (int64_t)n * n, S.EE, h->m32.EE, L);
+    else convert<float, double>(st, (int64_t)n * n, S.E, h->m32.E, L);
+  }
   CU(cudaEventRecord(h->ev_phase[1], st));
 
   // ---- a3: right-hand side and start ----
-  const double* Q = h->Vs;
-  CU(gemm_f64(st, false, false, n, n, n, 1.0, h->E, n, Ct, n, 0.0, h->F, n, h->gemm_ws, ws, L));
-  CU(gemm_f64(st, false, false, n, r, n, 1.0, Ct, n, Q, n, 0.0, h->T, n, h->gemm_ws, ws, L));
-  CU(gemm_f64(st, true, false, n, r, n, 1.0, h->Vs, n, h->T, n, 0.0, h->H, n, h->gemm_ws, ws, L));
+  const double* Q = S.Vs;
+  CU(gemm_f64(st, false, false, n, n, n, 1.0, S.E, n, Ct, n, 0.0, S.F, n, S.ws, ws, L));
+  CU(gemm_f64(st, false, false, n, r, n, 1.0, Ct, n, Q, n, 0.0, S.Tm, n, S.ws, ws, L));
+  CU(gemm_f64(st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, ws, L));
   if (h->kind == SDP_A_DENSE_SVEC) {
-    CU(gemm_f64(st, false, false, n, n, n, 1.0, h->F, n, h->E, n, 0.0, h->Z, n, h->gemm_ws, ws, L));
-    svec_pack_plus(st, n, r, h->Z, nullptr, nullptr, h->zsvec, nullptr, L);
+    CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, ws, L));
+    svec_pack_plus<double>(st, n, r, S.Z, nullptr, nullptr, S.zsvec, nullptr, L);
     prof_begin(h, 1);
-    rows_gemv(st, h->a_dense, m, h->N, h->zsvec, h->partA, nullptr, L);
+    rows_gemv<double>(st, h->a_dense, m, h->N, S.zsvec, S.partA, nullptr, L);
     prof_end(h);
-    launch_rhs_finish(st, m, d, n, r, h->partA, h->SA, nullptr, nullptr, bt, Ct, h->H, h->Dv, h->g, h->x,
+    launch_rhs_finish(st, m, d, n, r, S.partA, h->SA, nullptr, nullptr, bt, Ct, S.H, S.Dv, h->g, S.x,
                       h->opt.newton_rtol, h->ctl, h->dotbuf, h->counter, L);
   } else {
-    launch_rhs_finish(st, m, d, n, r, nullptr, 0, h->F, h->E, bt, Ct, h->H, h->Dv, h->g, h->x,
-                      h->opt.newton_rtol, h->ctl, h->dotbuf, h->counter, L);
+    launch_rhs_finish(st, m, d, n, r, nullptr, 0, S.F, S.E, bt, Ct, S.H, S.Dv, h->g, S.x, h->opt.newton_rtol,
+                      h->ctl, h->dotbuf, h->counter, L);
   }
-  // the inverse above may have flagged a non-positive pivot: keep it
-  // r0 = g - M x0 ; stop test ; z0 = P^{-1} r0 ; p0 = z0
-  {
-    sdp_status s = apply_operator(h, h->x, h->rv, h->g, 0);
-    if (s != SDP_OK) return s;
-  }
-  launch_norm_check(st, nt, h->rv, h->ctl, h->dotbuf, h->counter, L);
-  apply_precond(h, h->rv, h->z, 0);
-  launch_p_update(st, nt, h->z, h->p, 1, h->ctl, L);
 
-  // ---- a4-a6: PCG loop ----
-  const int every = h->opt.check_every;
-  int host_iter = 0;
-  for (;;) {
-    CU(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    if (h->ctl_host->done) break;
-    for (int k = 0; k < every; ++k, ++host_iter) {
-      h->cur_iter = host_iter;
-      sdp_status s = apply_operator(h, h->p, h->Ap, nullptr, 1);
+  if (!h->mixed) {
+    // ---- a4-a6: FP64 PCG from x0 ----
+    sdp_status s = pcg_start(h, S, false, h->g, 0.0);
+    if (s != SDP_OK) return s;
+    s = pcg_loop(h, S, false);
+    if (s != SDP_OK) return s;
+  } else {
+    // ---- a7: FP64 refinement around solves with the mixed operator ----
+    // x starts at 0, so that rho_0 = g and the first correction starts at P^{-1}[0; g_v]: the
+    // second block of the residual vanishes as Cor. pcg asks, without the large first block
+    // that x0 = [0; -Sigma^{-1} Q^T c] leaves (it sets the floor of the true residual).
+    Space& Si = h->sin;
+    CU(cudaMemsetAsync(S.x, 0, nt * sizeof(double), st));
+    for (;;) {
+      // rho = g - M x in FP64, and the stop test on ||rho|| (the true residual)
+      if (h->refine_steps == 0) {
+        CU(cudaMemcpyAsync(S.rv, h->g, nt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      } else {
+        sdp_status s = apply_operator(h, S, S.x, S.rv, h->g, 0);
+        if (s != SDP_OK) return s;
+      }
+      launch_norm_check<double>(st, nt, S.rv, 0.0, h->ctl, h->dotbuf, h->counter, L);
+      CU(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
+      CU(cudaStreamSynchronize(st));
+      if (h->ctl_host->done || h->refine_steps >= h->opt.max_refine) break;
+      // M~ delta = rho by PCG from delta0 = P^{-1}[0; rho_v], to inner_rtol relative reduction
+      launch_ctl_reset(st, h->ctl_in, h->ctl, h->opt.max_inner, L);
+      launch_correction_rhs(st, m, d, S.rv, Si.z, L);
+      apply_precond(h, Si, Si.z, Si.x, 0);
+      sdp_status s = pcg_start(h, Si, true, S.rv, h->opt.inner_rtol * h->opt.inner_rtol);
       if (s != SDP_OK) return s;
-      launch_update(st, nt, h->x, h->rv, h->p, h->Ap, h->ctl, h->dotbuf, h->counter, L);
-      apply_precond(h, h->rv, h->z, 1);
-      launch_p_update(st, nt, h->z, h->p, 0, h->ctl, L);
+      s = pcg_loop(h, Si, true);
+      if (s != SDP_OK) return s;
+      h->inner_iters += h->ctl_host->iters;
+      if (h->ctl_host->status == 5) return fail(h, SDP_ENUMERIC, "breakdown in the inner solve of the mixed form");
+      launch_add_correction(st, nt, Si.x, S.x, L);
+      h->refine_steps += 1;
     }
   }
 
@@ -470,15 +764,16 @@ extern "C" sdp_status sdp_newton_solve(sdp_handle* h, const double* V, const dou
   CU(cudaEventRecord(h->ev_phase[2], st));
 
   // ---- a8: recovery ----
-  const double* u = h->x;
-  const double* v = h->x + m;
-  adjoint_full(h, u, h->Y, nullptr);
-  launch_recover_pre(st, n, m, h->Y, Ct, u, h->Cw, dy, dS, h->ctl, L);
-  CU(gemm_f64(st, false, false, n, n, n, 1.0, h->E, n, h->Cw, n, 0.0, h->F, n, h->gemm_ws, ws, L));
-  CU(gemm_f64(st, false, false, n, n, n, 1.0, h->F, n, h->E, n, 0.0, h->Z, n, h->gemm_ws, ws, L));
-  h_unpack(st, n, r, v, h->Hp, nullptr, L);
-  CU(gemm_f64(st, false, false, n, r, n, 1.0, h->Vs, n, h->Hp, n, 0.0, h->Up, n, h->gemm_ws, ws, L));
-  launch_sym_plus_full(st, n, r, h->Z, h->Up, Q, dX, L);
+  const double* u = S.x;
+  const double* v = S.x + m;
+  if (h->kind == SDP_A_DENSE_SVEC) adjoint_dense(h, S, u, S.Y, nullptr);
+  else launch_diag_matrix(st, n, u, S.Y, L);
+  launch_recover_pre(st, n, m, S.Y, Ct, u, h->Cw, dy, dS, h->ctl, L);
+  CU(gemm_f64(st, false, false, n, n, n, 1.0, S.E, n, h->Cw, n, 0.0, S.F, n, S.ws, ws, L));
+  CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, ws, L));
+  h_unpack<double>(st, n, r, v, S.Hp, nullptr, L);
+  CU(gemm_f64(st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, ws, L));
+  launch_sym_plus_full(st, n, r, S.Z, S.Up, Q, dX, L);
   CU(cudaEventRecord(h->ev_phase[3], st));
   CU(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
@@ -490,35 +785,34 @@ extern "C" sdp_status sdp_newton_solve(sdp_handle* h, const double* V, const dou
     CU(cudaEventElapsedTime(&ms, h->ev_phase[q], h->ev_phase[q + 1]));
     h->phase_ms[q] = ms;
   }
-  h->prof_ms[0] = h->prof_ms[1] = 0.0;
-  h->prof_n[0] = h->prof_n[1] = 0;
-  for (size_t k = 0; k < h->prof_entries.size(); ++k) {
-    const auto& pe = h->prof_entries[k];
-    if (pe.iter >= c.iters) continue;          // launches after the stop returned at once
-    float ms = 0.f;
-    CU(cudaEventElapsedTime(&ms, h->ev[2 * k], h->ev[2 * k + 1]));
-    h->prof_ms[pe.kind] += ms;
-    h->prof_n[pe.kind] += 1;
+  if (h->prof) {
+    sdp_status ps = prof_collect(h, h->prof_base, h->prof_entries.size(), 0, 1);
+    if (ps != SDP_OK) return fail(h, ps, "event timing failed");
   }
   if (info) {
     info->r = r;
     info->d = d;
-    info->pcg_iters = c.iters;
+    info->pcg_iters = h->mixed ? h->inner_iters : c.iters;
     info->space = h->space;
     info->converged = (c.status == 0 && c.rr <= c.tol2) ? 1 : 0;
+    info->refine_steps = h->refine_steps;
     info->tau = c.tau;
     info->beta = c.beta_pc;
     info->res_norm = std::sqrt(c.rr);
     info->rhs_norm = std::sqrt(c.newt_rhs2);
     info->res0_norm = std::sqrt(c.rr0);
+    info->s_A = h->s_A;
     info->setup_ms = h->phase_ms[0];
     info->pcg_ms = h->phase_ms[1];
     info->recover_ms = h->phase_ms[2];
     info->prof_At_ms = h->prof_ms[0];
-    info->prof_At_launches = (int32_t)h->prof_n[0];
     info->prof_A_ms = h->prof_ms[1];
+    info->prof_At_launches = (int32_t)h->prof_n[0];
     info->prof_A_launches = (int32_t)h->prof_n[1];
-    info->s_A = h->s_A;
+    info->prof_At32_ms = h->prof_ms[2];
+    info->prof_A32_ms = h->prof_ms[3];
+    info->prof_At32_launches = (int32_t)h->prof_n[2];
+    info->prof_A32_launches = (int32_t)h->prof_n[3];
   }
   if (c.status == 5) return fail(h, SDP_ENUMERIC, "PCG breakdown or non-positive pivot");
   if (c.status == 4 || !(c.rr <= c.tol2)) return fail(h, SDP_ENOTCONV, "PCG did not reach the stopping test");
@@ -549,21 +843,23 @@ extern "C" sdp_status sdp_debug_copy(sdp_handle* h, int32_t which, double* dst, 
   if (!h || !dst || count < 0) return fail(h, SDP_EINVAL, "bad debug copy argument");
   const int64_t n = h->n, m = h->m, d = h->d;
   const int64_t pd = h->space == 1 ? d : m;
+  const Space& S = h->s64;
   const double* src = nullptr;
   int64_t avail = 0;
   switch (which) {
-    case 0: src = h->E; avail = n * n; break;
-    case 1: src = h->Dv; avail = d; break;
-    case 2: src = h->B; avail = m * d; break;
-    case 3: src = h->Pinv; avail = pd * pd; break;
-    case 4: src = h->Vs; avail = n * n; break;
-    case 5: src = h->x; avail = m + d; break;
+    case 0: src = S.E; avail = n * n; break;
+    case 1: src = S.Dv; avail = d; break;
+    case 2: src = S.B; avail = m * d; break;
+    case 3: src = S.Pinv; avail = pd * pd; break;
+    case 4: src = S.Vs; avail = n * n; break;
+    case 5: src = S.x; avail = m + d; break;
     case 6: src = h->g; avail = m + d; break;
     case 7: src = reinterpret_cast<const double*>(h->ctl); avail = sizeof(PcgCtl) / sizeof(double); break;
-    case 8: src = h->rv; avail = m + d; break;
-    case 9: src = h->z; avail = m + d; break;
-    case 10: src = h->p; avail = m + d; break;
-    case 11: src = h->Ap; avail = m + d; break;
+    case 8: src = S.rv; avail = m + d; break;
+    case 9: src = S.z; avail = m + d; break;
+    case 10: src = S.p; avail = m + d; break;
+    case 11: src = S.Ap; avail = m + d; break;
+    case 12: src = reinterpret_cast<const double*>(h->ctl_in); avail = sizeof(PcgCtl) / sizeof(double); break;
     default: return fail(h, SDP_EINVAL, "unknown buffer");
   }
   if (count > avail) return fail(h, SDP_EINVAL, "count exceeds the buffer");
@@ -594,9 +890,12 @@ extern "C" void sdp_destroy(sdp_handle* h) {
   if (!h) return;
   if (h->st) cudaStreamSynchronize(h->st);
   if (h->pool) cudaFree(h->pool);
+  if (h->ctl_host) cudaFreeHost(h->ctl_host);
   for (auto& e : h->ev) cudaEventDestroy(e);
   for (auto& e : h->ev_phase)
     if (e) cudaEventDestroy(e);
-  if (h->ctl_host) cudaFreeHost(h->ctl_host);
+  for (auto& G : h->graph)
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }

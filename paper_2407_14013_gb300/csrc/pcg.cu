@@ -3,10 +3,11 @@
 // and the finishing steps of the operator, preconditioner, right-hand side and recovery.
 //
 // Vectors have length m + d: the u-block (m) followed by the v-block (d, h-coordinates).
-// Scalars (alpha, beta, <r,z>, ||r||^2, tau, ...) live in the device control block, so a
-// PCG iteration needs no host round trip; every kernel returns at once when ctl->done is set.
-// Dot products are reduced deterministically: per-block partial sums, then the last block
-// to finish (atomic ticket) adds them in block order.
+// Vectors and scalars (alpha, beta, <r,z>, ||r||^2, tau, ...) are FP64; the scalars live in a
+// device control block, so an iteration needs no host round trip; every kernel returns
+// at once when ctl->done is set.  Dot products are accumulated in FP64 and reduced
+// deterministically: per-block partial sums, then the last block to finish (atomic ticket)
+// adds them in block order.
 #include "common.cuh"
 #include "pcg.h"
 
@@ -35,13 +36,12 @@ __device__ __forceinline__ double sum_partials(const double* part, int nb, doubl
 }
 
 // out = [u_src; pack(H) - D p_v] (optionally g - that), and in mode 1 the dot <p, out> -> alpha.
+template <typename T>
 __global__ void __launch_bounds__(VT)
-ap_finish_kernel(int m, int d, int n, int r, const double* __restrict__ partA, int S,
-                 const double* __restrict__ Up, const double* __restrict__ Vs,
-                 const double* __restrict__ H, const double* __restrict__ Dv,
-                 const double* __restrict__ p, const double* __restrict__ g, double* __restrict__ out,
-                 int mode, PcgCtl* __restrict__ ctl, double* __restrict__ dotbuf,
-                 unsigned int* __restrict__ counter) {
+ap_finish_kernel(int m, int d, int n, int r, const T* __restrict__ partA, int S, const T* __restrict__ Up,
+                 const T* __restrict__ Vs, const T* __restrict__ H, const T* __restrict__ Dv,
+                 const T* __restrict__ p, const T* __restrict__ g, T* __restrict__ out, int mode,
+                 PcgCtl* __restrict__ ctl, double* __restrict__ dotbuf, unsigned int* __restrict__ counter) {
   if (ctl->done) return;
   __shared__ double sh[32];
   const int nt = m + d;
@@ -50,17 +50,17 @@ ap_finish_kernel(int m, int d, int n, int r, const double* __restrict__ partA, i
     double v;
     if (q < m) {
       v = 0.0;
-      for (int s = 0; s < S; ++s) v += partA[(int64_t)s * m + q];
+      for (int s = 0; s < S; ++s) v += (double)partA[(int64_t)s * m + q];
       if (Up) {   // DIAG: A(sym(U Q^T)) = diag(U Q^T)
-        for (int k = 0; k < r; ++k) v += Up[q + (int64_t)k * n] * Vs[q + (int64_t)k * n];
+        for (int k = 0; k < r; ++k) v += (double)Up[q + (int64_t)k * n] * (double)Vs[q + (int64_t)k * n];
       }
     } else {
       const int h = q - m;
-      v = pack_at(H, n, n, r, h) - Dv[h] * p[q];
+      v = pack_at(H, n, n, r, h) - (double)Dv[h] * (double)p[q];
     }
-    if (g) v = g[q] - v;
-    out[q] = v;
-    if (mode == 1) acc = fma(p[q], v, acc);
+    if (g) v = (double)g[q] - v;
+    out[q] = (T)v;
+    if (mode == 1) acc = fma((double)p[q], v, acc);
   }
   if (mode != 1) return;
   acc = block_sum(acc, sh);
@@ -83,19 +83,19 @@ ap_finish_kernel(int m, int d, int n, int r, const double* __restrict__ partA, i
 }
 
 // x += alpha p; r -= alpha Ap; ||r||^2 -> stop test.
+template <typename T>
 __global__ void __launch_bounds__(VT)
-update_kernel(int nt, double* __restrict__ x, double* __restrict__ rv, const double* __restrict__ p,
-              const double* __restrict__ Ap, PcgCtl* __restrict__ ctl, double* __restrict__ dotbuf,
-              unsigned int* __restrict__ counter) {
+update_kernel(int nt, T* __restrict__ x, T* __restrict__ rv, const T* __restrict__ p, const T* __restrict__ Ap,
+              PcgCtl* __restrict__ ctl, double* __restrict__ dotbuf, unsigned int* __restrict__ counter) {
   if (ctl->done) return;
   __shared__ double sh[32];
   const double alpha = ctl->alpha;
   double acc = 0.0;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nt; q += gridDim.x * blockDim.x) {
-    x[q] = fma(alpha, p[q], x[q]);
-    double rr = fma(-alpha, Ap[q], rv[q]);
+    x[q] = (T)fma(alpha, (double)p[q], (double)x[q]);
+    const T rr = (T)fma(-alpha, (double)Ap[q], (double)rv[q]);
     rv[q] = rr;
-    acc = fma(rr, rr, acc);
+    acc = fma((double)rr, (double)rr, acc);
   }
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) dotbuf[blockIdx.x] = acc;
@@ -113,33 +113,36 @@ update_kernel(int nt, double* __restrict__ x, double* __restrict__ rv, const dou
 }
 
 // d-space: s = r_v - beta^{-1} (B^T r_u)
-__global__ void pc_d_s_kernel(int m, int d, int G, const double* __restrict__ partB, const double* __restrict__ rv,
-                              double* __restrict__ s, const PcgCtl* __restrict__ ctl) {
+template <typename T>
+__global__ void pc_d_s_kernel(int m, int d, int G, const T* __restrict__ partB, const T* __restrict__ rv,
+                              T* __restrict__ s, const PcgCtl* __restrict__ ctl) {
   if (ctl->done) return;
   int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= d) return;
   double t = 0.0;
-  for (int gg = 0; gg < G; ++gg) t += partB[(int64_t)gg * d + h];
-  s[h] = rv[m + h] - t / ctl->beta_pc;
+  for (int gg = 0; gg < G; ++gg) t += (double)partB[(int64_t)gg * d + h];
+  s[h] = (T)((double)rv[m + h] - t / ctl->beta_pc);
 }
 
 // d-space: z_v = -(C^{-1} s)
-__global__ void pc_d_zv_kernel(int m, int d, int S, const double* __restrict__ partC, double* __restrict__ z,
+template <typename T>
+__global__ void pc_d_zv_kernel(int m, int d, int S, const T* __restrict__ partC, T* __restrict__ z,
                                const PcgCtl* __restrict__ ctl) {
   if (ctl->done) return;
   int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= d) return;
   double t = 0.0;
-  for (int s = 0; s < S; ++s) t += partC[(int64_t)s * d + h];
-  z[m + h] = -t;
+  for (int s = 0; s < S; ++s) t += (double)partC[(int64_t)s * d + h];
+  z[m + h] = (T)(-t);
 }
 
-// z_u (d-space: beta^{-1}(r_u - B z_v); m-space: K^{-1} w) then <r, z> -> beta_pcg.
+// z_u (d-space: beta^{-1}(r_u - B z_v); m-space: already formed) then <r, z> -> beta_pcg.
 // mode 0 (start): rz = <r0, z0>;  mode 1 (iteration): beta = <r_{k+1}, z_{k+1}> / <r_k, z_k>.
+template <typename T>
 __global__ void __launch_bounds__(VT)
-pc_zu_dot_kernel(int m, int d, int S, const double* __restrict__ partU, int space,
-                 const double* __restrict__ rv, double* __restrict__ z, int mode, PcgCtl* __restrict__ ctl,
-                 double* __restrict__ dotbuf, unsigned int* __restrict__ counter) {
+pc_zu_dot_kernel(int m, int d, int S, const T* __restrict__ partU, int space, const T* __restrict__ rv,
+                 T* __restrict__ z, int mode, PcgCtl* __restrict__ ctl, double* __restrict__ dotbuf,
+                 unsigned int* __restrict__ counter) {
   if (ctl->done) return;
   __shared__ double sh[32];
   const int nt = m + d;
@@ -149,13 +152,13 @@ pc_zu_dot_kernel(int m, int d, int S, const double* __restrict__ partU, int spac
     double zq;
     if (q < m && partU) {
       double t = 0.0;
-      for (int s = 0; s < S; ++s) t += partU[(int64_t)s * m + q];
-      zq = (space == 1) ? (rv[q] - t) * ib : t;
-      z[q] = zq;
+      for (int s = 0; s < S; ++s) t += (double)partU[(int64_t)s * m + q];
+      zq = (space == 1) ? ((double)rv[q] - t) * ib : t;
+      z[q] = (T)zq;
     } else {
-      zq = z[q];
+      zq = (double)z[q];
     }
-    acc = fma(rv[q], zq, acc);
+    acc = fma((double)rv[q], zq, acc);
   }
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) dotbuf[blockIdx.x] = acc;
@@ -171,41 +174,45 @@ pc_zu_dot_kernel(int m, int d, int S, const double* __restrict__ partU, int spac
 }
 
 // m-space helpers: t_v = r_v / D;  w = r_u + B t_v;  z_v = (B^T z_u - r_v) / D
-__global__ void pc_m_tv_kernel(int m, int d, const double* __restrict__ rv, const double* __restrict__ Dv,
-                               double* __restrict__ t, const PcgCtl* __restrict__ ctl) {
+template <typename T>
+__global__ void pc_m_tv_kernel(int m, int d, const T* __restrict__ rv, const T* __restrict__ Dv, T* __restrict__ t,
+                               const PcgCtl* __restrict__ ctl) {
   if (ctl->done) return;
   int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= d) return;
-  t[h] = rv[m + h] / Dv[h];
+  t[h] = (T)((double)rv[m + h] / (double)Dv[h]);
 }
 
-__global__ void pc_m_w_kernel(int m, int S, const double* __restrict__ partB, const double* __restrict__ rv,
-                              double* __restrict__ w, const PcgCtl* __restrict__ ctl) {
+template <typename T>
+__global__ void pc_m_w_kernel(int m, int S, const T* __restrict__ partB, const T* __restrict__ rv, T* __restrict__ w,
+                              const PcgCtl* __restrict__ ctl) {
   if (ctl->done) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   double t = 0.0;
-  for (int s = 0; s < S; ++s) t += partB[(int64_t)s * m + i];
-  w[i] = (rv ? rv[i] : 0.0) + t;
+  for (int s = 0; s < S; ++s) t += (double)partB[(int64_t)s * m + i];
+  w[i] = (T)((rv ? (double)rv[i] : 0.0) + t);
 }
 
-__global__ void pc_m_zv_kernel(int m, int d, int G, const double* __restrict__ partBt, const double* __restrict__ rv,
-                               const double* __restrict__ Dv, double* __restrict__ z, const PcgCtl* __restrict__ ctl) {
+template <typename T>
+__global__ void pc_m_zv_kernel(int m, int d, int G, const T* __restrict__ partBt, const T* __restrict__ rv,
+                               const T* __restrict__ Dv, T* __restrict__ z, const PcgCtl* __restrict__ ctl) {
   if (ctl->done) return;
   int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= d) return;
   double t = 0.0;
-  for (int gg = 0; gg < G; ++gg) t += partBt[(int64_t)gg * d + h];
-  z[m + h] = (t - rv[m + h]) / Dv[h];
+  for (int gg = 0; gg < G; ++gg) t += (double)partBt[(int64_t)gg * d + h];
+  z[m + h] = (T)((t - (double)rv[m + h]) / (double)Dv[h]);
 }
 
 // p = z + beta p  (start: p = z)
-__global__ void p_update_kernel(int nt, const double* __restrict__ z, double* __restrict__ p, int start,
+template <typename T>
+__global__ void p_update_kernel(int nt, const T* __restrict__ z, T* __restrict__ p, int start,
                                 const PcgCtl* __restrict__ ctl) {
   if (ctl->done && !start) return;
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nt) return;
-  p[q] = start ? z[q] : fma(ctl->beta, p[q], z[q]);
+  p[q] = start ? z[q] : (T)fma(ctl->beta, (double)p[q], (double)z[q]);
 }
 
 // Right side of eq. augsys: g = [b~ + tau^2 A(E C~ E); tau^2 pack(H)], x0 = [0; -g_v / D]
@@ -267,13 +274,15 @@ rhs_finish_kernel(int m, int d, int n, int r, const double* __restrict__ partA, 
   }
 }
 
-// ||r0||^2 and the stop test before the first iteration.
+// ||r||^2 and the stop test (rel_rtol2 > 0: the threshold becomes rel_rtol2 ||r||^2).
+template <typename T>
 __global__ void __launch_bounds__(VT)
-norm_check_kernel(int nt, const double* __restrict__ rv, PcgCtl* __restrict__ ctl, double* __restrict__ dotbuf,
-                  unsigned int* __restrict__ counter) {
+norm_check_kernel(int nt, const T* __restrict__ rv, double rel_rtol2, PcgCtl* __restrict__ ctl,
+                  double* __restrict__ dotbuf, unsigned int* __restrict__ counter) {
   __shared__ double sh[32];
   double acc = 0.0;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nt; q += gridDim.x * blockDim.x) acc = fma(rv[q], rv[q], acc);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nt; q += gridDim.x * blockDim.x)
+    acc = fma((double)rv[q], (double)rv[q], acc);
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) dotbuf[blockIdx.x] = acc;
   if (last_block(counter)) {
@@ -281,7 +290,8 @@ norm_check_kernel(int nt, const double* __restrict__ rv, PcgCtl* __restrict__ ct
     if (threadIdx.x == 0) {
       *counter = 0;
       ctl->rr = rr;
-      ctl->rr0 = rr;
+      if (ctl->iters == 0) ctl->rr0 = rr;
+      if (rel_rtol2 > 0.0) ctl->tol2 = rel_rtol2 * rr;
       if (!isfinite(rr)) { ctl->status = 5; ctl->done = 1; }
       else if (rr <= ctl->tol2) ctl->done = 1;
     }
@@ -289,12 +299,13 @@ norm_check_kernel(int nt, const double* __restrict__ rv, PcgCtl* __restrict__ ct
 }
 
 // T = diag(p_u) Q  (DIAG kind: A^T(p_u) Q)
-__global__ void diag_scale_rows_kernel(int n, int r, const double* __restrict__ pu, const double* __restrict__ Vs,
-                                       double* __restrict__ T, const int32_t* __restrict__ done) {
+template <typename T>
+__global__ void diag_scale_rows_kernel(int n, int r, const T* __restrict__ pu, const T* __restrict__ Vs,
+                                       T* __restrict__ Tm, const int32_t* __restrict__ done) {
   if (done && *done) return;
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n * r) return;
-  T[q] = pu[q % n] * Vs[q];
+  Tm[q] = pu[q % n] * Vs[q];
 }
 
 // Y = diag(u) (DIAG kind: A^T(u))
@@ -355,6 +366,86 @@ __global__ void scale_B_kernel(int m, int d, const double* __restrict__ B, const
   Bs[q] = B[q] / sqrt(Dv[h]);
 }
 
+// Mixed form: [0; rho_v], whose image under the preconditioner starts the correction solve
+// (P delta0 = [0; rho_v] leaves the second block of rho - M delta0 at zero, as Cor. pcg asks,
+// while delta0 stays of the size of rho_v, with no division by the small entries of D).
+__global__ void correction_rhs_kernel(int m, int d, const double* __restrict__ rho, double* __restrict__ out) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= m + d) return;
+  out[q] = (q < m) ? 0.0 : rho[q];
+}
+
+// x += delta
+__global__ void add_correction_kernel(int nt, const double* __restrict__ delta, double* __restrict__ x) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nt) return;
+  x[q] += delta[q];
+}
+
+// Mixed-form operator: the well-conditioned block A E A^T p_u from FP32 partial sums, the
+// blocks with B = A Q (which meet D^{-1} through the iterates) in FP64:
+//   out = [sum_s partA32 + sum_s partBv; sum_g partBu - D p_v]  (optionally g - that);
+// mode 1 also forms <p, out> and alpha.
+__global__ void __launch_bounds__(VT)
+mixed_finish_kernel(int m, int d, const float* __restrict__ partA32, int SA, const double* __restrict__ partBv,
+                    int SB, const double* __restrict__ partBu, int SBu, const double* __restrict__ Dv,
+                    const double* __restrict__ p, const double* __restrict__ g, double* __restrict__ out, int mode,
+                    PcgCtl* __restrict__ ctl, double* __restrict__ dotbuf, unsigned int* __restrict__ counter) {
+  if (ctl->done) return;
+  __shared__ double sh[32];
+  const int nt = m + d;
+  double acc = 0.0;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nt; q += gridDim.x * blockDim.x) {
+    double v = 0.0;
+    if (q < m) {
+      for (int s = 0; s < SA; ++s) v += (double)partA32[(int64_t)s * m + q];
+      for (int s = 0; s < SB; ++s) v += partBv[(int64_t)s * m + q];
+    } else {
+      const int h = q - m;
+      for (int s = 0; s < SBu; ++s) v += partBu[(int64_t)s * d + h];
+      v -= Dv[h] * p[q];
+    }
+    if (g) v = g[q] - v;
+    out[q] = v;
+    if (mode == 1) acc = fma(p[q], v, acc);
+  }
+  if (mode != 1) return;
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) dotbuf[blockIdx.x] = acc;
+  if (last_block(counter)) {
+    double pAp = sum_partials(dotbuf, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      *counter = 0;
+      ctl->pAp = pAp;
+      if (pAp == 0.0 || !isfinite(pAp) || !isfinite(ctl->rz)) {
+        ctl->status = 5;
+        ctl->done = 1;
+      } else {
+        ctl->alpha = ctl->rz / pAp;
+      }
+    }
+  }
+}
+
+// p_u32 = (float) p_u
+__global__ void to_float_kernel(int cnt, const double* __restrict__ src, float* __restrict__ dst,
+                                const int32_t* __restrict__ done) {
+  if (done && *done) return;
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < cnt) dst[q] = (float)src[q];
+}
+
+// inner control block: the split scalars of src, counters reset
+__global__ void ctl_reset_kernel(PcgCtl* __restrict__ dst, const PcgCtl* __restrict__ src, int max_iters) {
+  if (threadIdx.x != 0) return;
+  *dst = *src;
+  dst->done = 0;
+  dst->iters = 0;
+  dst->status = 0;
+  dst->max_iters = max_iters;
+  dst->tol2 = 0.0;
+}
+
 inline unsigned nblk(int64_t total, int t) { return (unsigned)((total + t - 1) / t); }
 inline int vec_blocks(int nt) {
   int b = (nt + VT - 1) / VT;
@@ -363,61 +454,104 @@ inline int vec_blocks(int nt) {
 
 }  // namespace
 
-void launch_ap_finish(cudaStream_t st, int m, int d, int n, int r, const double* partA, int S, const double* Up,
-                      const double* Vs, const double* H, const double* Dv, const double* p, const double* g,
-                      double* out, int mode, PcgCtl* ctl, double* dotbuf, unsigned int* counter, int64_t* launches) {
-  ap_finish_kernel<<<vec_blocks(m + d), VT, 0, st>>>(m, d, n, r, partA, S, Up, Vs, H, Dv, p, g, out, mode, ctl,
-                                                    dotbuf, counter);
+template <typename T>
+void launch_ap_finish(cudaStream_t st, int m, int d, int n, int r, const T* partA, int S, const T* Up, const T* Vs,
+                      const T* H, const T* Dv, const T* p, const T* g, T* out, int mode, PcgCtl* ctl,
+                      double* dotbuf, unsigned int* counter, int64_t* launches) {
+  ap_finish_kernel<T><<<vec_blocks(m + d), VT, 0, st>>>(m, d, n, r, partA, S, Up, Vs, H, Dv, p, g, out, mode, ctl,
+                                                       dotbuf, counter);
   ++*launches;
 }
 
-void launch_update(cudaStream_t st, int nt, double* x, double* rv, const double* p, const double* Ap, PcgCtl* ctl,
-                   double* dotbuf, unsigned int* counter, int64_t* launches) {
-  update_kernel<<<vec_blocks(nt), VT, 0, st>>>(nt, x, rv, p, Ap, ctl, dotbuf, counter);
+template <typename T>
+void launch_update(cudaStream_t st, int nt, T* x, T* rv, const T* p, const T* Ap, PcgCtl* ctl, double* dotbuf,
+                   unsigned int* counter, int64_t* launches) {
+  update_kernel<T><<<vec_blocks(nt), VT, 0, st>>>(nt, x, rv, p, Ap, ctl, dotbuf, counter);
   ++*launches;
 }
 
-void launch_pc_d_s(cudaStream_t st, int m, int d, int G, const double* partB, const double* rv, double* s,
-                   const PcgCtl* ctl, int64_t* launches) {
-  pc_d_s_kernel<<<nblk(d, VT), VT, 0, st>>>(m, d, G, partB, rv, s, ctl);
+template <typename T>
+void launch_pc_d_s(cudaStream_t st, int m, int d, int G, const T* partB, const T* rv, T* s, const PcgCtl* ctl,
+                   int64_t* launches) {
+  pc_d_s_kernel<T><<<nblk(d, VT), VT, 0, st>>>(m, d, G, partB, rv, s, ctl);
   ++*launches;
 }
 
-void launch_pc_d_zv(cudaStream_t st, int m, int d, int S, const double* partC, double* z, const PcgCtl* ctl,
+template <typename T>
+void launch_pc_d_zv(cudaStream_t st, int m, int d, int S, const T* partC, T* z, const PcgCtl* ctl,
                     int64_t* launches) {
-  pc_d_zv_kernel<<<nblk(d, VT), VT, 0, st>>>(m, d, S, partC, z, ctl);
+  pc_d_zv_kernel<T><<<nblk(d, VT), VT, 0, st>>>(m, d, S, partC, z, ctl);
   ++*launches;
 }
 
-void launch_pc_zu_dot(cudaStream_t st, int m, int d, int S, const double* partU, int space, const double* rv,
-                      double* z, int mode, PcgCtl* ctl, double* dotbuf, unsigned int* counter, int64_t* launches) {
-  pc_zu_dot_kernel<<<vec_blocks(m + d), VT, 0, st>>>(m, d, S, partU, space, rv, z, mode, ctl, dotbuf, counter);
+template <typename T>
+void launch_pc_zu_dot(cudaStream_t st, int m, int d, int S, const T* partU, int space, const T* rv, T* z, int mode,
+                      PcgCtl* ctl, double* dotbuf, unsigned int* counter, int64_t* launches) {
+  pc_zu_dot_kernel<T><<<vec_blocks(m + d), VT, 0, st>>>(m, d, S, partU, space, rv, z, mode, ctl, dotbuf, counter);
   ++*launches;
 }
 
-void launch_pc_m_tv(cudaStream_t st, int m, int d, const double* rv, const double* Dv, double* t, const PcgCtl* ctl,
+template <typename T>
+void launch_pc_m_tv(cudaStream_t st, int m, int d, const T* rv, const T* Dv, T* t, const PcgCtl* ctl,
                     int64_t* launches) {
-  pc_m_tv_kernel<<<nblk(d, VT), VT, 0, st>>>(m, d, rv, Dv, t, ctl);
+  pc_m_tv_kernel<T><<<nblk(d, VT), VT, 0, st>>>(m, d, rv, Dv, t, ctl);
   ++*launches;
 }
 
-void launch_pc_m_w(cudaStream_t st, int m, int S, const double* partB, const double* rv, double* w,
-                   const PcgCtl* ctl, int64_t* launches) {
-  pc_m_w_kernel<<<nblk(m, VT), VT, 0, st>>>(m, S, partB, rv, w, ctl);
+template <typename T>
+void launch_pc_m_w(cudaStream_t st, int m, int S, const T* partB, const T* rv, T* w, const PcgCtl* ctl,
+                   int64_t* launches) {
+  pc_m_w_kernel<T><<<nblk(m, VT), VT, 0, st>>>(m, S, partB, rv, w, ctl);
   ++*launches;
 }
 
-void launch_pc_m_zv(cudaStream_t st, int m, int d, int G, const double* partBt, const double* rv, const double* Dv,
-                    double* z, const PcgCtl* ctl, int64_t* launches) {
-  pc_m_zv_kernel<<<nblk(d, VT), VT, 0, st>>>(m, d, G, partBt, rv, Dv, z, ctl);
+template <typename T>
+void launch_pc_m_zv(cudaStream_t st, int m, int d, int G, const T* partBt, const T* rv, const T* Dv, T* z,
+                    const PcgCtl* ctl, int64_t* launches) {
+  pc_m_zv_kernel<T><<<nblk(d, VT), VT, 0, st>>>(m, d, G, partBt, rv, Dv, z, ctl);
   ++*launches;
 }
 
-void launch_p_update(cudaStream_t st, int nt, const double* z, double* p, int start, const PcgCtl* ctl,
-                     int64_t* launches) {
-  p_update_kernel<<<nblk(nt, VT), VT, 0, st>>>(nt, z, p, start, ctl);
+template <typename T>
+void launch_p_update(cudaStream_t st, int nt, const T* z, T* p, int start, const PcgCtl* ctl, int64_t* launches) {
+  p_update_kernel<T><<<nblk(nt, VT), VT, 0, st>>>(nt, z, p, start, ctl);
   ++*launches;
 }
+
+template <typename T>
+void launch_norm_check(cudaStream_t st, int nt, const T* rv, double rel_rtol2, PcgCtl* ctl, double* dotbuf,
+                       unsigned int* counter, int64_t* launches) {
+  norm_check_kernel<T><<<vec_blocks(nt), VT, 0, st>>>(nt, rv, rel_rtol2, ctl, dotbuf, counter);
+  ++*launches;
+}
+
+template <typename T>
+void launch_diag_scale_rows(cudaStream_t st, int n, int r, const T* pu, const T* Vs, T* Tm, const int32_t* done,
+                            int64_t* launches) {
+  diag_scale_rows_kernel<T><<<nblk((int64_t)n * r, VT), VT, 0, st>>>(n, r, pu, Vs, Tm, done);
+  ++*launches;
+}
+
+#define WC_INSTANTIATE(T)                                                                                          \
+  template void launch_ap_finish<T>(cudaStream_t, int, int, int, int, const T*, int, const T*, const T*, const T*,  \
+                                    const T*, const T*, const T*, T*, int, PcgCtl*, double*, unsigned int*,          \
+                                    int64_t*);                                                                      \
+  template void launch_update<T>(cudaStream_t, int, T*, T*, const T*, const T*, PcgCtl*, double*, unsigned int*,   \
+                                 int64_t*);                                                                         \
+  template void launch_pc_d_s<T>(cudaStream_t, int, int, int, const T*, const T*, T*, const PcgCtl*, int64_t*);      \
+  template void launch_pc_d_zv<T>(cudaStream_t, int, int, int, const T*, T*, const PcgCtl*, int64_t*);              \
+  template void launch_pc_zu_dot<T>(cudaStream_t, int, int, int, const T*, int, const T*, T*, int, PcgCtl*, double*, \
+                                    unsigned int*, int64_t*);                                                       \
+  template void launch_pc_m_tv<T>(cudaStream_t, int, int, const T*, const T*, T*, const PcgCtl*, int64_t*);         \
+  template void launch_pc_m_w<T>(cudaStream_t, int, int, const T*, const T*, T*, const PcgCtl*, int64_t*);          \
+  template void launch_pc_m_zv<T>(cudaStream_t, int, int, int, const T*, const T*, const T*, T*, const PcgCtl*,     \
+                                  int64_t*);                                                                        \
+  template void launch_p_update<T>(cudaStream_t, int, const T*, T*, int, const PcgCtl*, int64_t*);                  \
+  template void launch_norm_check<T>(cudaStream_t, int, const T*, double, PcgCtl*, double*, unsigned int*,          \
+                                     int64_t*);                                                                     \
+  template void launch_diag_scale_rows<T>(cudaStream_t, int, int, const T*, const T*, T*, const int32_t*, int64_t*);
+WC_INSTANTIATE(double)
+#undef WC_INSTANTIATE
 
 void launch_rhs_finish(cudaStream_t st, int m, int d, int n, int r, const double* partA, int S, const double* F,
                        const double* E, const double* bt, const double* Ct, const double* H, const double* Dv,
@@ -425,18 +559,6 @@ void launch_rhs_finish(cudaStream_t st, int m, int d, int n, int r, const double
                        int64_t* launches) {
   rhs_finish_kernel<<<vec_blocks(m + d), VT, 0, st>>>(m, d, n, r, partA, S, F, E, bt, Ct, H, Dv, g, x, rtol, ctl,
                                                      dotbuf, counter);
-  ++*launches;
-}
-
-void launch_norm_check(cudaStream_t st, int nt, const double* rv, PcgCtl* ctl, double* dotbuf,
-                       unsigned int* counter, int64_t* launches) {
-  norm_check_kernel<<<vec_blocks(nt), VT, 0, st>>>(nt, rv, ctl, dotbuf, counter);
-  ++*launches;
-}
-
-void launch_diag_scale_rows(cudaStream_t st, int n, int r, const double* pu, const double* Vs, double* T,
-                            const int32_t* done, int64_t* launches) {
-  diag_scale_rows_kernel<<<nblk((int64_t)n * r, VT), VT, 0, st>>>(n, r, pu, Vs, T, done);
   ++*launches;
 }
 
@@ -470,6 +592,35 @@ void launch_add_diag(cudaStream_t st, int n, double* C, const double* Dv, double
 
 void launch_scale_B(cudaStream_t st, int m, int d, const double* B, const double* Dv, double* Bs, int64_t* launches) {
   scale_B_kernel<<<nblk((int64_t)m * d, VT), VT, 0, st>>>(m, d, B, Dv, Bs);
+  ++*launches;
+}
+
+void launch_correction_rhs(cudaStream_t st, int m, int d, const double* rho, double* out, int64_t* launches) {
+  correction_rhs_kernel<<<nblk(m + d, VT), VT, 0, st>>>(m, d, rho, out);
+  ++*launches;
+}
+
+void launch_mixed_finish(cudaStream_t st, int m, int d, const float* partA32, int SA, const double* partBv, int SB,
+                         const double* partBu, int SBu, const double* Dv, const double* p, const double* g,
+                         double* out, int mode, PcgCtl* ctl, double* dotbuf, unsigned int* counter,
+                         int64_t* launches) {
+  mixed_finish_kernel<<<vec_blocks(m + d), VT, 0, st>>>(m, d, partA32, SA, partBv, SB, partBu, SBu, Dv, p, g, out,
+                                                       mode, ctl, dotbuf, counter);
+  ++*launches;
+}
+
+void launch_to_float(cudaStream_t st, int cnt, const double* src, float* dst, const int32_t* done, int64_t* launches) {
+  to_float_kernel<<<nblk(cnt, VT), VT, 0, st>>>(cnt, src, dst, done);
+  ++*launches;
+}
+
+void launch_add_correction(cudaStream_t st, int nt, const double* delta, double* x, int64_t* launches) {
+  add_correction_kernel<<<nblk(nt, VT), VT, 0, st>>>(nt, delta, x);
+  ++*launches;
+}
+
+void launch_ctl_reset(cudaStream_t st, PcgCtl* dst, const PcgCtl* src, int max_iters, int64_t* launches) {
+  ctl_reset_kernel<<<1, 32, 0, st>>>(dst, src, max_iters);
   ++*launches;
 }
 

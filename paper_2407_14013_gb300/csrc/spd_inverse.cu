@@ -1,15 +1,16 @@
-// In-place inverse of a symmetric positive definite matrix by blocked Gauss-Jordan elimination.
+// Inverse of a symmetric positive definite matrix through its Cholesky factor:
+//   A = L L^T,  X = L^{-1},  A^{-1} = X^T X.
 //
 // The preconditioner of Section 6 needs one solve with its Schur complement per PCG
 // iteration.  A triangular solve is a chain of dependent steps that occupies a few SMs;
 // multiplying by an explicit inverse is one bandwidth-bound matrix-vector product over the
 // whole GPU, so the complement (C = tau^2 Sigma + beta^{-1} B^T B, or the m-space
-// K = beta I + B D^{-1} B^T) is inverted once per Newton solve.
+// K = beta I + B D^{-1} B^T) is inverted once per Newton solve.  The Cholesky route keeps the
+// error of the inverse near cond(A) eps (Gauss-Jordan sweeps lose about cond(A)^2 eps, which
+// the m-space complement, ill-conditioned at small mu, cannot afford).
 //
-// Pivoting on the diagonal block K of [[A_KK, A_KR], [A_RK, A_RR]] maps it to
-//   [[P, P A_KR], [-A_RK P, A_RR - A_RK P A_KR]],  P = A_KK^{-1};
-// after pivoting on every block the array holds A^{-1}.  For an SPD matrix every pivot
-// block is a Schur complement of an SPD matrix, hence SPD, and no pivoting is needed.
+// Blocked with NB x NB diagonal blocks: each diagonal block is factored and its triangular
+// factor inverted inside one CTA; everything else is FP64 GEMM (DMMA).
 #include "common.cuh"
 #include "kernels.h"
 
@@ -17,14 +18,15 @@ namespace wc {
 
 namespace {
 
-constexpr int NB = 64;
+constexpr int NB = 32;
 
-// P = inverse of the w x w block A[k0:k0+w, k0:k0+w] by scalar Gauss-Jordan in shared memory.
+// Factor the w x w diagonal block at k0 (already updated by earlier blocks): L_KK into the
+// lower triangle of A (upper part of the block zeroed), its inverse into Li (w x w, ld w).
 __global__ void __launch_bounds__(256)
-block_inverse_kernel(int n, int k0, int w, const double* __restrict__ A, double* __restrict__ P,
-                     int32_t* __restrict__ status) {
+chol_block_kernel(int n, int k0, int w, double* __restrict__ A, double* __restrict__ Li,
+                  int32_t* __restrict__ status) {
   __shared__ double S[NB][NB + 1];
-  __shared__ double rowp[NB], colp[NB];
+  __shared__ double X[NB][NB + 1];
   __shared__ int bad;
   for (int q = threadIdx.x; q < w * w; q += blockDim.x) {
     int i = q % w, j = q / w;
@@ -32,59 +34,55 @@ block_inverse_kernel(int n, int k0, int w, const double* __restrict__ A, double*
   }
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
+  // right-looking unblocked Cholesky on the lower triangle
   for (int p = 0; p < w; ++p) {
-    const double piv = S[p][p];
-    if (!(piv > 0.0) || !isfinite(piv)) {
-      if (threadIdx.x == 0) bad = 1;
+    if (threadIdx.x == 0) {
+      double piv = S[p][p];
+      if (!(piv > 0.0) || !isfinite(piv)) { bad = 1; piv = 1.0; }
+      S[p][p] = sqrt(piv);
     }
-    const double ip = 1.0 / piv;
-    for (int q = threadIdx.x; q < w; q += blockDim.x) {
-      rowp[q] = S[p][q];
-      colp[q] = S[q][p];
-    }
+    __syncthreads();
+    const double lpp = S[p][p];
+    for (int i = p + 1 + threadIdx.x; i < w; i += blockDim.x) S[i][p] /= lpp;
     __syncthreads();
     for (int q = threadIdx.x; q < w * w; q += blockDim.x) {
       int i = q % w, j = q / w;
-      double v;
-      if (i == p && j == p) v = ip;
-      else if (i == p) v = ip * rowp[j];
-      else if (j == p) v = -colp[i] * ip;
-      else v = S[i][j] - colp[i] * ip * rowp[j];
-      S[i][j] = v;
+      if (j > p && i >= j) S[i][j] -= S[i][p] * S[j][p];
     }
     __syncthreads();
   }
+  // X = L^{-1} by forward substitution, one column per thread
+  for (int j = threadIdx.x; j < w; j += blockDim.x) {
+    for (int i = 0; i < w; ++i) {
+      double s = (i == j) ? 1.0 : 0.0;
+      for (int k = j; k < i; ++k) s -= S[i][k] * X[k][j];
+      X[i][j] = (i >= j) ? s / S[i][i] : 0.0;
+    }
+  }
+  __syncthreads();
   for (int q = threadIdx.x; q < w * w; q += blockDim.x) {
     int i = q % w, j = q / w;
-    P[i + (int64_t)j * w] = S[i][j];
+    A[(k0 + i) + (int64_t)(k0 + j) * n] = (i >= j) ? S[i][j] : 0.0;
+    Li[i + (int64_t)j * w] = X[i][j];
   }
   if (threadIdx.x == 0 && bad) *status = 5;
 }
 
-// T (n x w) = A[:, K] with the rows of K set to zero.
-__global__ void copy_panel_kernel(int n, int k0, int w, const double* __restrict__ A, double* __restrict__ T) {
+// dst (rows x cols, ld ldd) = src (ld lds)
+__global__ void copy_block_kernel(int rows, int cols, const double* __restrict__ src, int64_t lds,
+                                  double* __restrict__ dst, int64_t ldd) {
   int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= (int64_t)n * w) return;
+  if (q >= (int64_t)rows * cols) return;
+  int i = (int)(q % rows), j = (int)(q / rows);
+  dst[i + (int64_t)j * ldd] = src[i + (int64_t)j * lds];
+}
+
+// zero the strictly upper triangle of an n x n matrix
+__global__ void zero_upper_kernel(int n, double* __restrict__ A) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)n * n) return;
   int i = (int)(q % n), j = (int)(q / n);
-  T[q] = (i >= k0 && i < k0 + w) ? 0.0 : A[i + (int64_t)(k0 + j) * n];
-}
-
-// Zero the columns K of R (w x n).
-__global__ void zero_cols_kernel(int n, int k0, int w, double* __restrict__ R) {
-  int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= w * w) return;
-  int i = q % w, j = q / w;
-  R[i + (int64_t)(k0 + j) * w] = 0.0;
-}
-
-// Rows K of A: A[K, j] = R[:, j] for j outside K, A[K, K] = P.
-__global__ void finish_rows_kernel(int n, int k0, int w, const double* __restrict__ R,
-                                   const double* __restrict__ P, double* __restrict__ A) {
-  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= (int64_t)w * n) return;
-  int i = (int)(q % w), j = (int)(q / w);
-  double v = (j >= k0 && j < k0 + w) ? P[i + (int64_t)(j - k0) * w] : R[i + (int64_t)j * w];
-  A[(k0 + i) + (int64_t)j * n] = v;
+  if (j > i) A[q] = 0.0;
 }
 
 __global__ void symmetrize_kernel(int n, double* __restrict__ A) {
@@ -101,34 +99,56 @@ inline unsigned nblk(int64_t total, int t) { return (unsigned)((total + t - 1) /
 
 }  // namespace
 
-// work must hold NB * NB + 2 * n * NB doubles.
+size_t spd_inverse_work(int n) { return (size_t)n * n + 2 * (size_t)n * NB + (size_t)((n + NB - 1) / NB) * NB * NB; }
+
+// A (n x n, ld n) is overwritten with its inverse.  work must hold spd_inverse_work(n) doubles.
 cudaError_t spd_inverse(cudaStream_t st, int n, double* A, double* work, size_t work_elems,
                         double* gemm_ws, size_t gemm_ws_elems, int32_t* status, int64_t* launches) {
-  if ((size_t)NB * NB + 2 * (size_t)n * NB > work_elems) return cudaErrorInvalidValue;
-  double* P = work;
-  double* T = work + NB * NB;
-  double* R = T + (size_t)n * NB;
-  for (int k0 = 0; k0 < n; k0 += NB) {
+  if (spd_inverse_work(n) > work_elems) return cudaErrorInvalidValue;
+  double* X = work;                                   // n x n, becomes L^{-1}
+  double* T = X + (size_t)n * n;                      // n x NB panel
+  double* U = T + (size_t)n * NB;                     // NB x n temporary
+  double* Li = U + (size_t)n * NB;                    // inverses of the diagonal blocks
+  cudaError_t e;
+  // ---- blocked right-looking Cholesky, L in the lower triangle of A
+  for (int k0 = 0, b = 0; k0 < n; k0 += NB, ++b) {
     const int w = (n - k0) < NB ? (n - k0) : NB;
-    block_inverse_kernel<<<1, 256, 0, st>>>(n, k0, w, A, P, status);
-    copy_panel_kernel<<<nblk((int64_t)n * w, 256), 256, 0, st>>>(n, k0, w, A, T);
-    if (launches) *launches += 2;
-    // R = P A[K, :]   (w x n)
-    cudaError_t e = gemm_f64(st, false, false, w, n, w, 1.0, P, w, A + k0, n, 0.0, R, w, gemm_ws,
-                             gemm_ws_elems, launches);
-    if (e != cudaSuccess) return e;
-    zero_cols_kernel<<<nblk((int64_t)w * w, 256), 256, 0, st>>>(n, k0, w, R);
+    const int k1 = k0 + w, rest = n - k1;
+    double* Lib = Li + (size_t)b * NB * NB;
+    chol_block_kernel<<<1, 256, 0, st>>>(n, k0, w, A, Lib, status);
     if (launches) ++*launches;
-    // A_RR -= A_RK P A_KR (rows and columns of K untouched: T rows K and R columns K are zero)
-    e = gemm_f64(st, false, false, n, n, w, -1.0, T, n, R, w, 1.0, A, n, gemm_ws, gemm_ws_elems, launches);
-    if (e != cudaSuccess) return e;
-    // A[:, K] = -A_RK P
-    e = gemm_f64(st, false, false, n, w, w, -1.0, T, n, P, w, 0.0, A + (int64_t)k0 * n, n, gemm_ws,
+    if (rest == 0) break;
+    // L_RK = A_RK L_KK^{-T}
+    e = gemm_f64(st, false, true, rest, w, w, 1.0, A + k1 + (int64_t)k0 * n, n, Lib, w, 0.0, T, rest, gemm_ws,
                  gemm_ws_elems, launches);
     if (e != cudaSuccess) return e;
-    finish_rows_kernel<<<nblk((int64_t)w * n, 256), 256, 0, st>>>(n, k0, w, R, P, A);
+    copy_block_kernel<<<nblk((int64_t)rest * w, 256), 256, 0, st>>>(rest, w, T, rest, A + k1 + (int64_t)k0 * n, n);
+    if (launches) ++*launches;
+    // A_RR -= L_RK L_RK^T
+    e = gemm_f64(st, false, true, rest, rest, w, -1.0, T, rest, T, rest, 1.0, A + k1 + (int64_t)k1 * n, n, gemm_ws,
+                 gemm_ws_elems, launches);
+    if (e != cudaSuccess) return e;
+  }
+  zero_upper_kernel<<<nblk((int64_t)n * n, 256), 256, 0, st>>>(n, A);
+  if (launches) ++*launches;
+  // ---- X = L^{-1} by block rows: X[I, :I] = -Li_II (L[I, :I] X[:I, :I]), X[I, I] = Li_II
+  e = cudaMemsetAsync(X, 0, (size_t)n * n * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  for (int i0 = 0, b = 0; i0 < n; i0 += NB, ++b) {
+    const int w = (n - i0) < NB ? (n - i0) : NB;
+    const double* Lib = Li + (size_t)b * NB * NB;
+    if (i0 > 0) {
+      e = gemm_f64(st, false, false, w, i0, i0, 1.0, A + i0, n, X, n, 0.0, U, w, gemm_ws, gemm_ws_elems, launches);
+      if (e != cudaSuccess) return e;
+      e = gemm_f64(st, false, false, w, i0, w, -1.0, Lib, w, U, w, 0.0, X + i0, n, gemm_ws, gemm_ws_elems, launches);
+      if (e != cudaSuccess) return e;
+    }
+    copy_block_kernel<<<nblk((int64_t)w * w, 256), 256, 0, st>>>(w, w, Lib, w, X + i0 + (int64_t)i0 * n, n);
     if (launches) ++*launches;
   }
+  // ---- A^{-1} = X^T X
+  e = gemm_f64(st, true, false, n, n, n, 1.0, X, n, X, n, 0.0, A, n, gemm_ws, gemm_ws_elems, launches);
+  if (e != cudaSuccess) return e;
   symmetrize_kernel<<<nblk((int64_t)n * n, 256), 256, 0, st>>>(n, A);
   if (launches) ++*launches;
   return cudaGetLastError();

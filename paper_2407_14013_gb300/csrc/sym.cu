@@ -8,8 +8,9 @@ namespace wc {
 
 namespace {
 
-__global__ void svec_unpack_sum_kernel(int n, const double* __restrict__ part, int groups, int64_t N,
-                                       double scale, double* __restrict__ Y,
+template <typename T>
+__global__ void svec_unpack_sum_kernel(int n, const T* __restrict__ part, int groups, int64_t N,
+                                       double scale, T* __restrict__ Y,
                                        const int32_t* __restrict__ done) {
   if (done && *done) return;
   int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -18,26 +19,28 @@ __global__ void svec_unpack_sum_kernel(int n, const double* __restrict__ part, i
   int i = a > b ? a : b, j = a > b ? b : a;
   int64_t idx = svec_index(n, i, j);
   double s = 0.0;
-  for (int g = 0; g < groups; ++g) s += part[(int64_t)g * N + idx];
-  Y[q] = (a == b ? s : s * WC_RSQRT2) * scale;
+  for (int g = 0; g < groups; ++g) s += (double)part[(int64_t)g * N + idx];
+  Y[q] = (T)((a == b ? s : s * WC_RSQRT2) * scale);
 }
 
-__global__ void svec_pack_plus_kernel(int n, int r, const double* __restrict__ Z, const double* __restrict__ U,
-                                      const double* __restrict__ Q, double* __restrict__ out,
+template <typename T>
+__global__ void svec_pack_plus_kernel(int n, int r, const T* __restrict__ Z, const T* __restrict__ U,
+                                      const T* __restrict__ Q, T* __restrict__ out,
                                       const int32_t* __restrict__ done) {
   if (done && *done) return;
   int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (int64_t)n * n) return;
   int a = (int)(q % n), b = (int)(q / n);
   if (a < b) return;
-  double v = 0.5 * (Z[a + (int64_t)b * n] + Z[b + (int64_t)a * n]);
+  double v = 0.5 * ((double)Z[a + (int64_t)b * n] + (double)Z[b + (int64_t)a * n]);
   if (U) {
     double t = 0.0;
     for (int k = 0; k < r; ++k)
-      t += U[a + (int64_t)k * n] * Q[b + (int64_t)k * n] + Q[a + (int64_t)k * n] * U[b + (int64_t)k * n];
+      t += (double)U[a + (int64_t)k * n] * (double)Q[b + (int64_t)k * n] +
+           (double)Q[a + (int64_t)k * n] * (double)U[b + (int64_t)k * n];
     v += 0.5 * t;
   }
-  out[svec_index(n, a, b)] = (a == b) ? v : v * WC_SQRT2;
+  out[svec_index(n, a, b)] = (T)((a == b) ? v : v * WC_SQRT2);
 }
 
 __global__ void svec_rows_unpack_kernel(const double* __restrict__ A, int n, int64_t N, int i0, int mb,
@@ -58,24 +61,143 @@ inline unsigned nblk(int64_t total, int t) { return (unsigned)((total + t - 1) /
 
 }  // namespace
 
-void svec_unpack_sum(cudaStream_t st, int n, const double* part, int groups, double scale, double* Y,
+template <typename T>
+void svec_unpack_sum(cudaStream_t st, int n, const T* part, int groups, double scale, T* Y,
                      const int32_t* done, int64_t* launches) {
   int64_t N = (int64_t)n * (n + 1) / 2;
-  svec_unpack_sum_kernel<<<nblk((int64_t)n * n, 256), 256, 0, st>>>(n, part, groups, N, scale, Y, done);
+  svec_unpack_sum_kernel<T><<<nblk((int64_t)n * n, 256), 256, 0, st>>>(n, part, groups, N, scale, Y, done);
   if (launches) ++*launches;
 }
 
-void svec_pack_plus(cudaStream_t st, int n, int r, const double* Z, const double* U, const double* Q,
-                    double* out, const int32_t* done, int64_t* launches) {
-  svec_pack_plus_kernel<<<nblk((int64_t)n * n, 256), 256, 0, st>>>(n, r, Z, U, Q, out, done);
+template <typename T>
+void svec_pack_plus(cudaStream_t st, int n, int r, const T* Z, const T* U, const T* Q, T* out,
+                    const int32_t* done, int64_t* launches) {
+  svec_pack_plus_kernel<T><<<nblk((int64_t)n * n, 256), 256, 0, st>>>(n, r, Z, U, Q, out, done);
   if (launches) ++*launches;
 }
+
+template void svec_unpack_sum<double>(cudaStream_t, int, const double*, int, double, double*, const int32_t*,
+                                      int64_t*);
+template void svec_unpack_sum<float>(cudaStream_t, int, const float*, int, double, float*, const int32_t*, int64_t*);
+template void svec_pack_plus<double>(cudaStream_t, int, int, const double*, const double*, const double*, double*,
+                                     const int32_t*, int64_t*);
+template void svec_pack_plus<float>(cudaStream_t, int, int, const float*, const float*, const float*, float*,
+                                    const int32_t*, int64_t*);
+
+namespace {
+template <typename To, typename From>
+__global__ void convert_kernel(int64_t count, const From* __restrict__ src, To* __restrict__ dst) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += (int64_t)gridDim.x * blockDim.x)
+    dst[q] = (To)src[q];
+}
+}  // namespace
+
+template <typename To, typename From>
+void convert(cudaStream_t st, int64_t count, const From* src, To* dst, int64_t* launches) {
+  if (count <= 0) return;
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 8 * g_num_sms) blocks = 8 * g_num_sms;
+  convert_kernel<To, From><<<(unsigned)blocks, 256, 0, st>>>(count, src, dst);
+  if (launches) ++*launches;
+}
+
+template void convert<float, double>(cudaStream_t, int64_t, const double*, float*, int64_t*);
+template void convert<double, float>(cudaStream_t, int64_t, const float*, double*, int64_t*);
 
 void svec_rows_unpack(cudaStream_t st, const double* A, int n, int i0, int mb, double* out,
                       int64_t* launches) {
   int64_t N = (int64_t)n * (n + 1) / 2;
   svec_rows_unpack_kernel<<<nblk((int64_t)n * n * mb, 256), 256, 0, st>>>(A, n, N, i0, mb, out);
   if (launches) ++*launches;
+}
+
+}  // namespace wc
+
+namespace wc {
+
+namespace {
+
+constexpr int AQ_WARPS = 8;
+
+// One CTA per constraint i: G_i = A_i Q with A_i read once from its svec row.  Column b of
+// the lower triangle (entries a = b..n-1, contiguous) goes to warp b mod 8; an off-diagonal
+// entry s = sqrt2 A_i[a,b] adds (s/sqrt2) Q[b,:] to row a and (s/sqrt2) Q[a,:] to row b.
+// Each warp accumulates into its own n x r copy, so no two threads update the same word.
+template <int r>
+__global__ void __launch_bounds__(AQ_WARPS * 32)
+dense_AiQ_kernel(const double* __restrict__ A, int n, int64_t N, int i0, int mb, const double* __restrict__ Q,
+                 double* __restrict__ G) {
+  extern __shared__ double sm[];
+  double* Qs = sm;                                 // n x r, row-major
+  double* acc = sm + (int64_t)n * r;               // AQ_WARPS x n x r
+  const int il = blockIdx.x, i = i0 + il;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nr = n * r;
+  for (int q = threadIdx.x; q < nr; q += blockDim.x) {
+    const int a = q / r, j = q % r;
+    Qs[q] = Q[a + (int64_t)j * n];
+  }
+  for (int q = threadIdx.x; q < AQ_WARPS * nr; q += blockDim.x) acc[q] = 0.0;
+  __syncthreads();
+  const double* row = A + (int64_t)i * N;
+  double* my = acc + (int64_t)warp * nr;
+  for (int b = warp; b < n; b += AQ_WARPS) {
+    const double* col = row + svec_index(n, b, b);
+    double colsum[r];
+#pragma unroll
+    for (int j = 0; j < r; ++j) colsum[j] = 0.0;
+    for (int a = b + lane; a < n; a += 32) {
+      const double s = __ldg(col + (a - b));
+      if (a == b) {
+#pragma unroll
+        for (int j = 0; j < r; ++j) colsum[j] = fma(s, Qs[b * r + j], colsum[j]);
+      } else {
+        const double v = s * WC_RSQRT2;
+#pragma unroll
+        for (int j = 0; j < r; ++j) {
+          my[a * r + j] = fma(v, Qs[b * r + j], my[a * r + j]);
+          colsum[j] = fma(v, Qs[a * r + j], colsum[j]);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < r; ++j) {
+      double t = warp_sum(colsum[j]);
+      if (lane == 0) my[b * r + j] += t;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nr; q += blockDim.x) {
+    const int a = q / r, j = q % r;
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < AQ_WARPS; ++w) s += acc[(int64_t)w * nr + q];
+    G[a + ((int64_t)j * mb + il) * n] = s;
+  }
+}
+
+}  // namespace
+
+bool dense_AiQ(cudaStream_t st, const double* A, int n, int i0, int mb, int r, const double* Q, double* G,
+               int64_t* launches) {
+  const size_t smem = (size_t)(AQ_WARPS + 1) * n * r * sizeof(double);
+  if (r < 1 || r > 16 || smem > 200 * 1024) return false;
+  const int64_t N = (int64_t)n * (n + 1) / 2;
+  switch (r) {
+#define WC_AIQ_CASE(R)                                                                              \
+    case R:                                                                                         \
+      cudaFuncSetAttribute(dense_AiQ_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
+      dense_AiQ_kernel<R><<<mb, AQ_WARPS * 32, smem, st>>>(A, n, N, i0, mb, Q, G);                   \
+      break;
+    WC_AIQ_CASE(1) WC_AIQ_CASE(2) WC_AIQ_CASE(3) WC_AIQ_CASE(4) WC_AIQ_CASE(5) WC_AIQ_CASE(6)
+    WC_AIQ_CASE(7) WC_AIQ_CASE(8) WC_AIQ_CASE(9) WC_AIQ_CASE(10) WC_AIQ_CASE(11) WC_AIQ_CASE(12)
+    WC_AIQ_CASE(13) WC_AIQ_CASE(14) WC_AIQ_CASE(15) WC_AIQ_CASE(16)
+#undef WC_AIQ_CASE
+    default: return false;
+  }
+  if (launches) ++*launches;
+  return true;
 }
 
 }  // namespace wc

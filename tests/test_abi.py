@@ -51,7 +51,9 @@ def test_struct_layout_matches_header(lib):
 int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(sdp_problem), offsetof(sdp_problem, a_dense), sizeof(sdp_options),
          offsetof(sdp_options, newton_rtol));
-  printf("%zu %zu\n", sizeof(sdp_newton_info), offsetof(sdp_newton_info, s_A));
+  printf("%zu %zu %zu\n", sizeof(sdp_newton_info), offsetof(sdp_newton_info, s_A),
+         offsetof(sdp_newton_info, prof_A32_launches));
+  printf("%zu\n", offsetof(sdp_options, inner_rtol));
   return 0;
 }
 '''
@@ -68,6 +70,8 @@ int main(void) {
     assert vals[3] == _native.sdp_options.newton_rtol.offset
     assert vals[4] == ctypes.sizeof(_native.sdp_newton_info)
     assert vals[5] == _native.sdp_newton_info.s_A.offset
+    assert vals[6] == _native.sdp_newton_info.prof_A32_launches.offset
+    assert vals[7] == _native.sdp_options.inner_rtol.offset
 
 
 def test_default_options_and_setup_errors(lib):

@@ -28,6 +28,7 @@ def rel(a, b):
 
 
 def gpu_solve(prob, sp, Ct, bt, **kw):
+    """Set up a solver for `prob` (keyword options of NewtonSolver) and solve once."""
     from paper_2407_14013_gb300 import NewtonSolver
     s = NewtonSolver(prob, **kw)
     dX, dy, dS, info = s.solve(_t(sp.V), _t(sp.lam), _t(Ct), _t(bt))
@@ -164,3 +165,66 @@ def test_errors_are_reported():
     assert i2.converged
     s.close()
     s2.close()
+
+
+def test_graph_replay_matches_plain_launches():
+    """The PCG iterations replayed from a captured CUDA graph give the same bits as plain launches."""
+    prob = W.sensing(40, 200, 2, 801)
+    sp = W.scaling_point(40, 2, 1e-5, 802)
+    Ct, bt = W.newton_rhs(40, 200, 803)
+    s1, (X1, y1, S1, i1) = gpu_solve(prob, sp, Ct, bt, r_hat=3, use_graph=True)
+    s2, (X2, y2, S2, i2) = gpu_solve(prob, sp, Ct, bt, r_hat=3, use_graph=False)
+    assert i1.pcg_iters == i2.pcg_iters and i1.converged and i2.converged
+    assert np.array_equal(X1, X2) and np.array_equal(y1, y2) and np.array_equal(S1, S2)
+    # a second solve on the same handle reuses the captured graph
+    _, _, _, i3 = s1.solve(_t(sp.V), _t(sp.lam), _t(Ct), _t(bt))
+    assert i3.pcg_iters == i1.pcg_iters
+    # event timing of the dense passes works in both modes
+    for s in (s1, s2):
+        s.set_profiling(True)
+        _, _, _, info = s.solve(_t(sp.V), _t(sp.lam), _t(Ct), _t(bt))
+        assert info.prof_A_launches == info.pcg_iters + 2       # right side, r0, one per iteration
+        assert info.prof_At_launches == info.pcg_iters + 2      # r0, one per iteration, recovery
+        assert info.prof_A_ms > 0 and info.prof_At_ms > 0
+        s.close()
+
+
+MIXED_CASES = [
+    ("sensing40", lambda: W.sensing(40, 200, 2, 901), 2, 1e-5, 3, 1),
+    ("sensing37_m", lambda: W.sensing(37, 150, 3, 902), 3, 1e-3, 5, 2),
+    ("maxcut64", lambda: W.workload("maxcut64"), 3, 1e-4, 12, 0),
+]
+
+
+@pytest.mark.parametrize("name,mk,rt,mu,rh,space", MIXED_CASES, ids=[c[0] for c in MIXED_CASES])
+def test_mixed_precision_matches_fp64(name, mk, rt, mu, rh, space):
+    """Correction solves with the FP32 A E A^T block under FP64 refinement reach the same
+    (Newt-eps) stop test as the FP64 form, on the true FP64 residual, so the two directions
+    agree to the FP64 tolerance."""
+    prob = mk()
+    sp = W.scaling_point(prob.n, rt, mu, 1000 + prob.n)
+    Ct, bt = W.newton_rhs(prob.n, prob.m, 1100 + prob.n)
+    s64, (X64, y64, S64, i64) = gpu_solve(prob, sp, Ct, bt, r_hat=rh, precond_space=space)
+    s32, (X32, y32, S32, i32) = gpu_solve(prob, sp, Ct, bt, r_hat=rh, precond_space=space, precision="mixed_fp32")
+    assert i64.converged and i32.converged and i32.refine_steps >= 1
+    assert i32.res_norm <= 1e-12 * i32.rhs_norm                      # the FP64 residual itself
+    assert rel(X32, X64) < TOL and rel(y32, y64) < TOL and rel(S32, S64) < TOL
+    s64.close()
+    s32.close()
+
+
+def test_mixed_full_size_sensing200():
+    prob = W.workload("sensing200")
+    sp = W.scaling_point(prob.n, 3, 1e-6, 4242, V_top=prob.meta["U"])
+    Ct, bt = W.newton_rhs(prob.n, prob.m, 4243)
+    s, (dX, dy, dS, info) = gpu_solve(prob, sp, Ct, bt, r_hat=3, precision="mixed_fp32")
+    assert info.converged and info.refine_steps >= 1
+    Wm = w_of(sp)
+    res = onewton.newt_eps_residual(prob, Wm, Ct, bt, dX, dy)
+    N = prob.n * (prob.n + 1) // 2
+    assert np.linalg.norm(res[N:]) <= 1e-8 * np.linalg.norm(bt)
+    s.set_profiling(True)
+    _, _, _, i2 = s.solve(_t(sp.V), _t(sp.lam), _t(Ct), _t(bt))
+    assert i2.prof_A32_launches == i2.pcg_iters + i2.refine_steps       # r0 of each solve + one per iteration
+    assert i2.prof_A_launches == i2.refine_steps + 1                    # right side + one residual per correction
+    s.close()
