@@ -8,15 +8,18 @@ namespace wc {
 
 namespace {
 
-constexpr int BK = 16;
 constexpr int THREADS = 256;
 
-template <int BM, int BN, int TM, int TN>
+// Each thread owns a TM x TN block of C; K advances in steps of BK with the next step's
+// tiles prefetched into registers while the current one is multiplied (the small products
+// of the mixed form are latency-bound, so few, long K steps matter more than tile reuse).
+template <int BM, int BN, int TM, int TN, int BK>
 __global__ void __launch_bounds__(THREADS)
 gemm_f32_kernel(int M, int N, int K, int kchunk, float alpha, const float* __restrict__ A, int64_t lda, int tA,
                 const float* __restrict__ B, int64_t ldb, int tB, float beta, float* __restrict__ C, int64_t ldc,
                 float* __restrict__ part, const int32_t* __restrict__ done) {
   static_assert((BM / TM) * (BN / TN) == THREADS, "thread layout");
+  constexpr int A_PER = (BM * BK + THREADS - 1) / THREADS, B_PER = (BN * BK + THREADS - 1) / THREADS;
   if (done && *done) return;
   __shared__ float As[BK][BM + 4];
   __shared__ float Bs[BK][BN + 4];
@@ -30,37 +33,69 @@ gemm_f32_kernel(int M, int N, int K, int kchunk, float alpha, const float* __res
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
-  for (int k0 = kbeg; k0 < kend; k0 += BK) {
-    for (int e = tid; e < BM * BK; e += THREADS) {
+  float ra[A_PER], rb[B_PER];
+  auto load_tiles = [&](int k0) {
+#pragma unroll
+    for (int e = 0; e < A_PER; ++e) {
+      const int idx = tid + e * THREADS;
       int mi, ki;
-      if (!tA) { mi = e % BM; ki = e / BM; } else { ki = e % BK; mi = e / BK; }
-      int gm = m0 + mi, gk = k0 + ki;
+      if (!tA) { mi = idx % BM; ki = idx / BM; } else { ki = idx % BK; mi = idx / BK; }
+      const int gm = m0 + mi, gk = k0 + ki;
       float v = 0.f;
-      if (gm < M && gk < kend) v = tA ? A[(int64_t)gk + (int64_t)gm * lda] : A[(int64_t)gm + (int64_t)gk * lda];
-      As[ki][mi] = v;
+      if (idx < BM * BK && gm < M && gk < kend)
+        v = tA ? A[(int64_t)gk + (int64_t)gm * lda] : A[(int64_t)gm + (int64_t)gk * lda];
+      ra[e] = v;
     }
-    for (int e = tid; e < BN * BK; e += THREADS) {
+#pragma unroll
+    for (int e = 0; e < B_PER; ++e) {
+      const int idx = tid + e * THREADS;
       int ni, kj;
-      if (!tB) { kj = e % BK; ni = e / BK; } else { ni = e % BN; kj = e / BN; }
-      int gn = n0 + ni, gk = k0 + kj;
+      if (!tB) { kj = idx % BK; ni = idx / BK; } else { ni = idx % BN; kj = idx / BN; }
+      const int gn = n0 + ni, gk = k0 + kj;
       float w = 0.f;
-      if (gn < N && gk < kend) w = tB ? B[(int64_t)gn + (int64_t)gk * ldb] : B[(int64_t)gk + (int64_t)gn * ldb];
-      Bs[kj][ni] = w;
+      if (idx < BN * BK && gn < N && gk < kend)
+        w = tB ? B[(int64_t)gn + (int64_t)gk * ldb] : B[(int64_t)gk + (int64_t)gn * ldb];
+      rb[e] = w;
     }
-    __syncthreads();
+  };
+  auto store_tiles = [&]() {
 #pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      float a[TM], b[TN];
-#pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
-#pragma unroll
-      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
-#pragma unroll
-      for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    for (int e = 0; e < A_PER; ++e) {
+      const int idx = tid + e * THREADS;
+      if (idx >= BM * BK) break;
+      int mi, ki;
+      if (!tA) { mi = idx % BM; ki = idx / BM; } else { ki = idx % BK; mi = idx / BK; }
+      As[ki][mi] = ra[e];
     }
-    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < B_PER; ++e) {
+      const int idx = tid + e * THREADS;
+      if (idx >= BN * BK) break;
+      int ni, kj;
+      if (!tB) { kj = idx % BK; ni = idx / BK; } else { ni = idx % BN; kj = idx / BN; }
+      Bs[kj][ni] = rb[e];
+    }
+  };
+  if (kbeg < kend) {
+    load_tiles(kbeg);
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+      store_tiles();
+      __syncthreads();
+      if (k0 + BK < kend) load_tiles(k0 + BK);
+#pragma unroll 8
+      for (int kk = 0; kk < BK; ++kk) {
+        float a[TM], b[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
   }
   const bool split = gridDim.z > 1;
   float* P = split ? part + (int64_t)blockIdx.z * M * N : nullptr;
@@ -93,7 +128,7 @@ __global__ void splitk_reduce_f32_kernel(int M, int N, int S, const float* __res
   *cp = (beta == 0.f) ? s : s + beta * *cp;
 }
 
-template <int BM, int BN, int TM, int TN>
+template <int BM, int BN, int TM, int TN, int BK>
 cudaError_t launch(cudaStream_t st, bool tA, bool tB, int M, int N, int K, float alpha, const float* A, int64_t lda,
                    const float* B, int64_t ldb, float beta, float* C, int64_t ldc, float* ws, size_t ws_elems,
                    int64_t* launches, const int32_t* done) {
@@ -102,7 +137,7 @@ cudaError_t launch(cudaStream_t st, bool tA, bool tB, int M, int N, int K, float
   int S = 1;
   if (K > 0 && ws != nullptr) {
     int want = (2 * g_num_sms + tiles - 1) / tiles;
-    int maxS = (K + 63) / 64;
+    int maxS = K / 256;                           // split only long products
     S = want < maxS ? want : maxS;
     if (S < 1) S = 1;
     if (S > 64) S = 64;
@@ -112,7 +147,7 @@ cudaError_t launch(cudaStream_t st, bool tA, bool tB, int M, int N, int K, float
   if (K > 0) S = (K + kchunk - 1) / kchunk;
   if (K <= 0) { S = 1; kchunk = 0; }
   dim3 grid(gm, gn, S);
-  gemm_f32_kernel<BM, BN, TM, TN><<<grid, THREADS, 0, st>>>(M, N, K, kchunk, alpha, A, lda, tA ? 1 : 0, B, ldb,
+  gemm_f32_kernel<BM, BN, TM, TN, BK><<<grid, THREADS, 0, st>>>(M, N, K, kchunk, alpha, A, lda, tA ? 1 : 0, B, ldb,
                                                            tB ? 1 : 0, beta, C, ldc, ws, done);
   if (launches) ++*launches;
   if (S > 1) {
@@ -130,10 +165,13 @@ cudaError_t gemm_f32(cudaStream_t st, bool tA, bool tB, int M, int N, int K, flo
                      size_t ws_elems, int64_t* launches, const int32_t* done) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (N <= 8)
-    return launch<256, 8, 2, 4>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, launches, done);
+    return launch<256, 8, 2, 4, 32>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, launches,
+                                   done);
   if ((int64_t)M * N <= 512 * 512)
-    return launch<32, 32, 2, 2>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, launches, done);
-  return launch<64, 64, 4, 4>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, launches, done);
+    return launch<32, 32, 2, 2, 64>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, launches,
+                                    done);
+  return launch<64, 64, 4, 4, 16>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, launches,
+                                  done);
 }
 
 }  // namespace wc

@@ -3,12 +3,13 @@
 //   C (M x N) = alpha * op(A) * op(B) + beta * C
 //
 // op(A) is M x K (A col-major M x K, or its transpose stored K x M); op(B) is K x N.
-// GB300 runs FP64 FMA at about 1 TFLOP/s and this MMA at about 4 TFLOP/s, and the
+// GB300 runs FP64 FMA at about 1.26 TFLOP/s and this MMA at about 4 TFLOP/s, and the
 // dense products of the Newton solve are small (n of a few hundred to a few thousand),
-// so three tile shapes are compiled (64 x 64 for large products, 32 x 32 for n ~ 200,
-// 64 x 8 for the n x r factors) and the grid is filled by splitting K across CTAs when
-// the M x N tile count is below the SM count; the K-slices write partial tiles to scratch
-// and a second kernel reduces them in a fixed order (results are bitwise reproducible).
+// so four tile shapes are compiled (64 x 64 for large products, 32 x 32 and 16 x 16 with
+// long K steps for n ~ 200-500, 64 x 8 for the n x r factors) and the grid is filled by
+// splitting a long K across CTAs when the M x N tile count is below the SM count; the
+// K-slices write partial tiles to scratch and a second kernel reduces them in a fixed
+// order (results are bitwise reproducible).
 #include "common.cuh"
 #include "kernels.h"
 
@@ -16,19 +17,21 @@ namespace wc {
 
 namespace {
 
-constexpr int BK = 16;
 constexpr int THREADS = 128;        // 4 warps
+constexpr int kGemmTickets = 4096;  // split-K tickets (tiles) at most
+constexpr size_t kGemmTicketDoubles = kGemmTickets / 2;
 constexpr int PAD = 4;              // row stride BM+4 doubles: conflict-free fragment reads
 
 // Warp layout WARPS_M x WARPS_N (= 4); each warp owns a (BM/WARPS_M) x (BN/WARPS_N) block of
 // 8 x 8 MMA tiles.
-template <int BM, int BN, int WARPS_M>
+template <int BM, int BN, int WARPS_M, int BK>
 __global__ void __launch_bounds__(THREADS)
 gemm_f64_kernel(int M, int N, int K, int kchunk, double alpha,
                 const double* __restrict__ A, int64_t lda, int tA,
                 const double* __restrict__ B, int64_t ldb, int tB,
                 double beta, double* __restrict__ C, int64_t ldc,
-                double* __restrict__ part, const int32_t* __restrict__ done) {
+                double* __restrict__ part, unsigned int* __restrict__ counters, int flags,
+                const int32_t* __restrict__ done) {
   constexpr int WARPS_N = 4 / WARPS_M;
   constexpr int WM = BM / WARPS_M, WN = BN / WARPS_N;
   constexpr int TM = WM / 8, TN = WN / 8;
@@ -39,8 +42,11 @@ gemm_f64_kernel(int M, int N, int K, int kchunk, double alpha,
   __shared__ double Bs[BK][BN + PAD];
 
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const int kbeg = blockIdx.z * kchunk;
+  if ((flags & GEMM_LOWER) && m0 + BM <= n0) return;      // tile entirely above the diagonal
+  int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
+  if (flags & GEMM_KSTART_ROW) kbeg = max(kbeg, m0);       // op(A)[i, k] = 0 for k < i
+  if (flags & GEMM_KSTART_COL) kbeg = max(kbeg, n0);       // op(B)[k, j] = 0 for k < j
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = (warp % WARPS_M) * WM, wn = (warp / WARPS_M) * WN;
   const int g = lane >> 2, t = lane & 3;
@@ -117,7 +123,10 @@ gemm_f64_kernel(int M, int N, int K, int kchunk, double alpha,
     }
   }
 
-  // Epilogue: c0 = C[g][2t], c1 = C[g][2t+1] within each 8 x 8 tile.
+  // Epilogue: c0 = C[g][2t], c1 = C[g][2t+1] within each 8 x 8 tile.  With K split over
+  // gridDim.z slices, every slice writes its partial tile; the last slice to finish (atomic
+  // ticket per tile) adds the partials in slice order, so the result does not depend on
+  // which slice finished last, and resets the ticket for the next product.
   const bool split = (gridDim.z > 1);
   double* P = split ? part + (int64_t)blockIdx.z * M * N : nullptr;
 #pragma unroll
@@ -138,49 +147,54 @@ gemm_f64_kernel(int M, int N, int K, int kchunk, double alpha,
           }
         }
       }
+  if (!split) return;
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  unsigned int* ticket = counters + (blockIdx.x + (int64_t)blockIdx.y * gridDim.x);
+  if (tid == 0) last = (atomicAdd(ticket, 1u) == gridDim.z - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int64_t MN = (int64_t)M * N;
+  for (int e = tid; e < BM * BN; e += THREADS) {
+    const int gm = m0 + e % BM, gn = n0 + e / BM;
+    if (gm >= M || gn >= N) continue;
+    const int64_t idx = (int64_t)gm + (int64_t)gn * M;
+    double sum = 0.0;
+    for (int z = 0; z < (int)gridDim.z; ++z) sum += __ldcg(part + z * MN + idx);
+    double* cp = C + (int64_t)gm + (int64_t)gn * ldc;
+    *cp = (beta == 0.0) ? sum : sum + beta * *cp;
+  }
+  if (tid == 0) *ticket = 0u;
 }
 
-__global__ void splitk_reduce_kernel(int M, int N, int S, const double* __restrict__ part,
-                                     double beta, double* __restrict__ C, int64_t ldc,
-                                     const int32_t* __restrict__ done) {
-  if (done && *done) return;
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t MN = (int64_t)M * N;
-  if (idx >= MN) return;
-  double s = 0.0;
-  for (int z = 0; z < S; ++z) s += part[(int64_t)z * MN + idx];
-  int64_t gm = idx % M, gn = idx / M;
-  double* cp = C + gm + gn * ldc;
-  *cp = (beta == 0.0) ? s : s + beta * *cp;
-}
-
-template <int BM, int BN, int WARPS_M>
+template <int BM, int BN, int WARPS_M, int BK>
 cudaError_t launch(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
                    int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, double* ws,
-                   size_t ws_elems, int64_t* launches, const int32_t* done) {
+                   size_t ws_elems, int64_t* launches, int flags, const int32_t* done) {
   int gm = (M + BM - 1) / BM, gn = (N + BN - 1) / BN;
   int tiles = gm * gn;
+  if (flags & GEMM_LOWER) tiles = (tiles + gm) / 2;                // about half the tiles do work
   int S = 1;
-  if (K > 0 && ws != nullptr) {
+  // the last kGemmTickets doubles of ws hold the per-tile tickets of the split-K reduction
+  const size_t part_elems = ws_elems > kGemmTicketDoubles ? ws_elems - kGemmTicketDoubles : 0;
+  if (K > 0 && ws != nullptr && gm * gn <= kGemmTickets) {
     int want = (2 * g_num_sms + tiles - 1) / tiles;               // about two CTAs per SM
-    int maxS = (K + 31) / 32;                                      // keep >= 32 of K per slice
+    int maxS = K / (2 * BK);                                       // at least two K steps per slice
     S = want < maxS ? want : maxS;
     if (S < 1) S = 1;
     if (S > 64) S = 64;
-    while (S > 1 && (size_t)S * M * N > ws_elems) --S;
+    while (S > 1 && (size_t)S * M * N > part_elems) --S;
   }
   int kchunk = K > 0 ? ((K + S - 1) / S + BK - 1) / BK * BK : 0;
   if (K > 0) S = (K + kchunk - 1) / kchunk;
   if (K <= 0) { S = 1; kchunk = 0; }
+  unsigned int* tickets = ws ? reinterpret_cast<unsigned int*>(ws + part_elems) : nullptr;
   dim3 grid(gm, gn, S);
-  gemm_f64_kernel<BM, BN, WARPS_M><<<grid, THREADS, 0, st>>>(M, N, K, kchunk, alpha, A, lda, tA ? 1 : 0, B, ldb,
-                                                            tB ? 1 : 0, beta, C, ldc, ws, done);
+  gemm_f64_kernel<BM, BN, WARPS_M, BK><<<grid, THREADS, 0, st>>>(M, N, K, kchunk, alpha, A, lda, tA ? 1 : 0, B, ldb,
+                                                                tB ? 1 : 0, beta, C, ldc, ws, tickets, flags, done);
   if (launches) ++*launches;
-  if (S > 1) {
-    int64_t MN = (int64_t)M * N;
-    splitk_reduce_kernel<<<(unsigned)((MN + 255) / 256), 256, 0, st>>>(M, N, S, ws, beta, C, ldc, done);
-    if (launches) ++*launches;
-  }
   return cudaGetLastError();
 }
 
@@ -191,13 +205,19 @@ int g_num_sms = 152;
 cudaError_t gemm_f64(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha,
                      const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                      double* C, int64_t ldc, double* ws, size_t ws_elems, int64_t* launches,
-                     const int32_t* done) {
+                     const int32_t* done, int flags) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  if (N <= 8)
-    return launch<64, 8, 4>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, launches, done);
+  if (N <= 8)   // the n x r factors: short tiles, K split over many CTAs
+    return launch<32, 8, 4, 16>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, launches,
+                                flags, done);
+  if ((int64_t)M * N <= 320 * 320)   // one 8 x 8 MMA tile per warp, long K steps: few, latency-bound steps
+    return launch<16, 16, 2, 64>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, launches,
+                                 flags, done);
   if ((int64_t)M * N <= 512 * 512)
-    return launch<32, 32, 2>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, launches, done);
-  return launch<64, 64, 2>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, launches, done);
+    return launch<32, 32, 2, 32>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, launches,
+                                 flags, done);
+  return launch<64, 64, 2, 16>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, launches,
+                               flags, done);
 }
 
 }  // namespace wc

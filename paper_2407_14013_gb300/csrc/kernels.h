@@ -11,19 +11,31 @@ namespace wc {
 extern int g_num_sms;
 
 // ---- gemm_f64.cu -----------------------------------------------------------------------------
+// C = alpha op(A) op(B) + beta C (column-major).  ws: split-K partial tiles, its last 16 KB the
+// per-tile tickets of the in-kernel reduction; it must be zero when first used (the tickets
+// return to zero after every product).  flags:
+enum : int {
+  GEMM_LOWER = 1,        // only output tiles that meet the lower triangle (i >= j) are written
+  GEMM_KSTART_ROW = 2,   // op(A)[i, k] = 0 for k < i (skip those K steps)
+  GEMM_KSTART_COL = 4    // op(B)[k, j] = 0 for k < j
+};
 cudaError_t gemm_f64(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha,
                      const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                      double* C, int64_t ldc, double* ws, size_t ws_elems, int64_t* launches,
-                     const int32_t* done = nullptr);
+                     const int32_t* done = nullptr, int flags = 0);
 
 // ---- rows.cu: products with row-major matrices streamed from memory ---------------------------
-// Partial sums of y_i = <row_i(A), x>: part[s * m + i] over column slabs s (returns slab count).
-int rows_gemv_slabs(int64_t L);
+// Partial sums of y_i = <row_i(A), x>: part[s * m + i] over column slabs s.  The slab count
+// depends on the shape and the element size (8: double, 4: float); a partial-sum buffer of
+// rows_gemv_part_elems(rows_max, L) elements serves every m <= rows_max.
+int rows_gemv_slabs(int m, int64_t L, int esize = 8);
+size_t rows_gemv_part_elems(int64_t rows_max, int64_t L);
 template <typename T>
 void rows_gemv(cudaStream_t st, const T* A, int m, int64_t L, const T* x, T* part, const int32_t* done,
                int64_t* launches);
-// Partial sums of y = sum_i p_i row_i(A): part[g * L + k] over row groups g (returns group count).
-int rows_gemvT_groups(int m, int64_t L);
+// Partial sums of y = sum_i p_i row_i(A): part[g * L + k] over row groups g; the group count
+// for an m x L matrix of `esize`-byte elements spreads the CTAs evenly over the SMs.
+int rows_gemvT_groups(int m, int64_t L, int esize = 8);
 template <typename T>
 void rows_gemvT(cudaStream_t st, const T* A, int m, int64_t L, const T* p, T* part, int groups,
                 const int32_t* done, int64_t* launches);
@@ -36,7 +48,8 @@ void rows_sumsq(cudaStream_t st, const double* A, int m, int64_t L, double* out,
 template <typename T>
 void svec_unpack_sum(cudaStream_t st, int n, const T* part, int groups, double scale, T* Y,
                      const int32_t* done, int64_t* launches);
-// out(svec, N) = svec(Z + sym(U Q^T)) with U, Q n x r (U may be NULL).
+// out(svec, N) = svec(Z + sym(U Q^T)) with U, Q n x r (U may be NULL); Z is symmetric and only
+// its lower triangle is read.
 template <typename T>
 void svec_pack_plus(cudaStream_t st, int n, int r, const T* Z, const T* U, const T* Q, T* out,
                     const int32_t* done, int64_t* launches);

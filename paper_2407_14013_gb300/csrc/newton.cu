@@ -102,7 +102,8 @@ struct sdp_handle {
   Mixed32 m32;
   // device staging for the host-pointer entry point
   double *hV = nullptr, *hlam = nullptr, *hCt = nullptr, *hbt = nullptr, *hdX = nullptr, *hdy = nullptr, *hdS = nullptr;
-  int GY = 1, SA = 1;   // row groups of A^T products, column slabs of A products
+  int GY = 1, SA = 1;       // row groups of the FP64 A^T products, column slabs of the FP64 A products
+  int GY32 = 1, SA32 = 1;   // the same for the FP32 copy of A (mixed form)
   int64_t launches = 0;
   int space = 1, r = 0, d = 0;
   int refine_steps = 0, inner_iters = 0;
@@ -174,7 +175,6 @@ inline int dof(int n, int r) { return n * r - r * (r - 1) / 2; }
 void carve_space(sdp_handle* h, Carver& c, Space& S) {
   const size_t n = h->n, m = h->m, nn = n * n, rm = h->r_max, dm = h->d_max;
   const size_t vt = m + dm;
-  const size_t pdim = std::max(dm, m);
   const size_t pc = h->pinv_dim;
   S.Vs = c.take<double>(nn);
   S.E = c.take<double>(nn);
@@ -194,8 +194,10 @@ void carve_space(sdp_handle* h, Carver& c, Space& S) {
     S.zsvec = c.take<double>(h->N);
     S.partY = c.take<double>((size_t)h->GY * h->N);
   }
-  const size_t sa = std::max<size_t>(h->SA, (size_t)rows_gemv_slabs(std::max<int64_t>(n, pdim)));
-  S.partA = c.take<double>(sa * std::max(m, pdim));
+  size_t pa = std::max(rows_gemv_part_elems(m, dm), rows_gemv_part_elems(pc, pc));
+  if (h->kind == SDP_A_DENSE_SVEC) pa = std::max(pa, rows_gemv_part_elems(m, h->N));
+  else pa = std::max(pa, rows_gemv_part_elems(n, n));
+  S.partA = c.take<double>(pa);
   S.x = c.take<double>(vt);
   S.rv = c.take<double>(vt);
   S.z = c.take<double>(vt);
@@ -203,10 +205,9 @@ void carve_space(sdp_handle* h, Carver& c, Space& S) {
   S.Ap = c.take<double>(vt);
   S.sd = c.take<double>(dm);
   S.wm = c.take<double>(m);
-  const size_t gb = (size_t)rows_gemv_slabs(std::max<int64_t>(m, 1)) + 1;
-  S.partB = c.take<double>(gb * dm);
-  S.partBt = c.take<double>(gb * dm);
-  S.partC = c.take<double>((size_t)rows_gemv_slabs(std::max<size_t>(pc, 1)) * pc);
+  S.partB = c.take<double>(rows_gemv_part_elems(dm, m));
+  S.partBt = c.take<double>(rows_gemv_part_elems(dm, m));
+  S.partC = c.take<double>(rows_gemv_part_elems(pc, pc));
   S.ws_elems = 4 * std::max({nn, pc * pc, (size_t)h->mb2 * n * rm * 2});
   S.ws = c.take<double>(S.ws_elems);
 }
@@ -220,17 +221,17 @@ void carve_mixed(sdp_handle* h, Carver& c, Mixed32& M) {
     M.F = c.take<float>(nn);
     M.Z = c.take<float>(nn);
     M.zsvec = c.take<float>(h->N);
-    M.partY = c.take<float>((size_t)h->GY * h->N);
-    M.partA = c.take<float>((size_t)h->SA * m);
+    M.partY = c.take<float>((size_t)h->GY32 * h->N);
+    M.partA = c.take<float>(rows_gemv_part_elems(m, h->N));
   } else {
     M.EE = c.take<float>(nn);
-    M.partA = c.take<float>((size_t)rows_gemv_slabs(n) * m);
+    M.partA = c.take<float>(rows_gemv_part_elems(n, n));
   }
   M.pu = c.take<float>(m);
   M.ws_elems = 4 * nn;
   M.ws = c.take<float>(M.ws_elems);
-  M.partBv = c.take<double>((size_t)rows_gemv_slabs(std::max<size_t>(dm, 1)) * m);
-  M.partBu = c.take<double>((size_t)rows_gemv_slabs(m) * dm);
+  M.partBv = c.take<double>(rows_gemv_part_elems(m, dm));
+  M.partBu = c.take<double>(rows_gemv_part_elems(dm, m));
 }
 
 // Lay out every buffer; with base == nullptr only the size is computed.
@@ -320,8 +321,10 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (h->kind == SDP_A_DENSE_SVEC) {
-    h->GY = rows_gemvT_groups(m, h->N);
-    h->SA = rows_gemv_slabs(h->N);
+    h->GY = rows_gemvT_groups(m, h->N, 8);
+    h->SA = rows_gemv_slabs(m, h->N, 8);
+    h->GY32 = rows_gemvT_groups(m, h->N, 4);
+    h->SA32 = rows_gemv_slabs(m, h->N, 4);
     // batch of constraints unpacked to full matrices while forming B (at most ~64 MB)
     int64_t per = (int64_t)n * n * 8;
     h->mb = (int)std::max<int64_t>(1, std::min<int64_t>(m, ((int64_t)64 << 20) / per));
@@ -335,6 +338,13 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
     return fail(nullptr, SDP_ENOMEM, std::string("cudaMalloc of workspace failed: ") + cudaGetErrorString(e));
   }
   carve(h, h->pool);
+  // zero workspace: the split-K tickets of the GEMMs must start at zero
+  e = cudaMemsetAsync(h->pool, 0, h->pool_bytes, h->st);
+  if (e != cudaSuccess) {
+    cudaFree(h->pool);
+    delete h;
+    return fail(nullptr, SDP_ECUDA, std::string("workspace clear failed: ") + cudaGetErrorString(e));
+  }
   e = cudaMallocHost(&h->ctl_host, sizeof(PcgCtl));
   if (e != cudaSuccess) {
     cudaFree(h->pool);
@@ -426,7 +436,8 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
     CU(gemm_f64(st, false, false, n, r, n, 1.0, S.Y, n, Q, n, 0.0, S.Tm, n, S.ws, S.ws_elems, L, done));
     CU(gemm_f64(st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, done));
     CU(gemm_f64(st, false, false, n, n, n, 1.0, S.E, n, S.Y, n, 0.0, S.F, n, S.ws, S.ws_elems, L, done));
-    CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, S.ws_elems, L, done));
+    CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, S.ws_elems, L, done,
+                GEMM_LOWER));                                          // E Y E is symmetric: lower triangle
     svec_pack_plus<double>(st, n, r, S.Z, S.Up, Q, S.zsvec, done, L);    // svec(E Y E + sym(Up Q^T))
     prof_begin(h, 1);
     rows_gemv<double>(st, h->a_dense, m, h->N, S.zsvec, S.partA, done, L);
@@ -437,7 +448,7 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
     launch_diag_scale_rows<double>(st, n, r, pu, S.Vs, S.Tm, done, L);  // A^T(p_u) Q = diag(p_u) Q
     CU(gemm_f64(st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, done));
     rows_gemv<double>(st, S.EE, n, n, pu, S.partA, done, L);              // diag(E diag(p_u) E) = (E o E) p_u
-    launch_ap_finish<double>(st, m, d, n, r, S.partA, rows_gemv_slabs(n), S.Up, S.Vs, S.H, S.Dv, pin, gsub, out,
+    launch_ap_finish<double>(st, m, d, n, r, S.partA, rows_gemv_slabs(n, n), S.Up, S.Vs, S.H, S.Dv, pin, gsub, out,
                              mode, S.ctl, h->dotbuf, h->counter, L);
   }
   return SDP_OK;
@@ -460,23 +471,23 @@ sdp_status apply_operator_mixed(sdp_handle* h, Space& S, const double* pin, doub
   int SA;
   if (h->kind == SDP_A_DENSE_SVEC) {
     prof_begin(h, 2);
-    rows_gemvT<float>(st, M.A, m, h->N, M.pu, M.partY, h->GY, done, L);   // A^T(p_u)
+    rows_gemvT<float>(st, M.A, m, h->N, M.pu, M.partY, h->GY32, done, L);   // A^T(p_u)
     prof_end(h);
-    svec_unpack_sum<float>(st, n, M.partY, h->GY, 1.0, M.Y, done, L);
+    svec_unpack_sum<float>(st, n, M.partY, h->GY32, 1.0, M.Y, done, L);
     CU(gemm_f32(st, false, false, n, n, n, 1.f, M.E, n, M.Y, n, 0.f, M.F, n, M.ws, M.ws_elems, L, done));
     CU(gemm_f32(st, false, false, n, n, n, 1.f, M.F, n, M.E, n, 0.f, M.Z, n, M.ws, M.ws_elems, L, done));
     svec_pack_plus<float>(st, n, 0, M.Z, nullptr, nullptr, M.zsvec, done, L);
     prof_begin(h, 3);
     rows_gemv<float>(st, M.A, m, h->N, M.zsvec, M.partA, done, L);          // A(E Y E)
     prof_end(h);
-    SA = h->SA;
+    SA = h->SA32;
   } else {
     rows_gemv<float>(st, M.EE, n, n, M.pu, M.partA, done, L);               // (E o E) p_u
-    SA = rows_gemv_slabs(n);
+    SA = rows_gemv_slabs(n, n, 4);
   }
   rows_gemv<double>(st, S.B, m, d, pv, M.partBv, done, L);                  // B p_v
   rows_gemv<double>(st, S.Bt, d, m, pu, M.partBu, done, L);                 // B^T p_u
-  launch_mixed_finish(st, m, d, M.partA, SA, M.partBv, rows_gemv_slabs(d), M.partBu, rows_gemv_slabs(m), S.Dv, pin,
+  launch_mixed_finish(st, m, d, M.partA, SA, M.partBv, rows_gemv_slabs(m, d), M.partBu, rows_gemv_slabs(d, m), S.Dv, pin,
                       gsub, out, mode, S.ctl, h->dotbuf, h->counter, L);
   return SDP_OK;
 }
@@ -492,21 +503,21 @@ void apply_precond(sdp_handle* h, Space& S, const double* rin, double* zout, int
   const int32_t* done = &S.ctl->done;
   cudaStream_t st = h->st;
   int64_t* L = &h->launches;
-  const int Sm = rows_gemv_slabs(m);
+  const int Sm = rows_gemv_slabs(d, m);   // slabs of the products with the rows of B^T
   if (h->space == 1) {
     rows_gemv<double>(st, S.Bt, d, m, rin, S.partB, done, L);              // B^T r_u (rows of B^T)
     launch_pc_d_s<double>(st, m, d, Sm, S.partB, rin, S.sd, S.ctl, L);     // s = r_v - beta^{-1} B^T r_u
     rows_gemv<double>(st, S.Pinv, d, d, S.sd, S.partC, done, L);           // C^{-1} s
-    launch_pc_d_zv<double>(st, m, d, rows_gemv_slabs(d), S.partC, zout, S.ctl, L);
+    launch_pc_d_zv<double>(st, m, d, rows_gemv_slabs(d, d), S.partC, zout, S.ctl, L);
     rows_gemv<double>(st, S.B, m, d, zout + m, S.partA, done, L);          // B z_v
-    launch_pc_zu_dot<double>(st, m, d, rows_gemv_slabs(d), S.partA, 1, rin, zout, mode, S.ctl, h->dotbuf,
+    launch_pc_zu_dot<double>(st, m, d, rows_gemv_slabs(m, d), S.partA, 1, rin, zout, mode, S.ctl, h->dotbuf,
                              h->counter, L);
   } else {
     launch_pc_m_tv<double>(st, m, d, rin, S.Dv, S.sd, S.ctl, L);           // t = D^{-1} r_v
     rows_gemv<double>(st, S.B, m, d, S.sd, S.partA, done, L);              // B t
-    launch_pc_m_w<double>(st, m, rows_gemv_slabs(d), S.partA, rin, S.wm, S.ctl, L);   // w = r_u + B D^{-1} r_v
+    launch_pc_m_w<double>(st, m, rows_gemv_slabs(m, d), S.partA, rin, S.wm, S.ctl, L);   // w = r_u + B D^{-1} r_v
     rows_gemv<double>(st, S.Pinv, m, m, S.wm, S.partC, done, L);           // K^{-1} w
-    launch_pc_m_w<double>(st, m, rows_gemv_slabs(m), S.partC, nullptr, zout, S.ctl, L);  // z_u
+    launch_pc_m_w<double>(st, m, rows_gemv_slabs(m, m), S.partC, nullptr, zout, S.ctl, L);  // z_u
     rows_gemv<double>(st, S.Bt, d, m, zout, S.partBt, done, L);            // B^T z_u (rows of B^T)
     launch_pc_m_zv<double>(st, m, d, Sm, S.partBt, rin, S.Dv, zout, S.ctl, L);  // z_v = D^{-1}(B^T z_u - r_v)
     launch_pc_zu_dot<double>(st, m, d, 0, nullptr, 2, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L);
@@ -686,13 +697,14 @@ extern "C" sdp_status sdp_newton_solve(sdp_handle* h, const double* V, const dou
   if (h->space == 1) {
     // C = beta^{-1} B^T B + tau^2 Sigma  (B row-major m x d == column-major d x m)
     const double beta = h->ctl_host->beta_pc;
-    CU(gemm_f64(st, false, true, d, d, m, 1.0 / beta, S.B, d, S.B, d, 0.0, S.Pinv, d, S.ws, ws, L));
+    CU(gemm_f64(st, false, true, d, d, m, 1.0 / beta, S.B, d, S.B, d, 0.0, S.Pinv, d, S.ws, ws, L, nullptr,
+                GEMM_LOWER));   // the Cholesky reads the lower triangle only
     launch_add_diag(st, d, S.Pinv, S.Dv, 0.0, L);
     CU(spd_inverse(st, d, S.Pinv, h->gj_work, h->gj_work_elems, S.ws, ws, pstatus, L));
   } else {
     // K = beta I + B D^{-1} B^T = Bs^T Bs + beta I with Bs = D^{-1/2} B^T (d x m)
     launch_scale_B(st, m, d, S.B, S.Dv, h->Bs, L);
-    CU(gemm_f64(st, true, false, m, m, d, 1.0, h->Bs, d, h->Bs, d, 0.0, S.Pinv, m, S.ws, ws, L));
+    CU(gemm_f64(st, true, false, m, m, d, 1.0, h->Bs, d, h->Bs, d, 0.0, S.Pinv, m, S.ws, ws, L, nullptr, GEMM_LOWER));
     launch_add_diag(st, m, S.Pinv, nullptr, h->ctl_host->beta_pc, L);
     CU(spd_inverse(st, m, S.Pinv, h->gj_work, h->gj_work_elems, S.ws, ws, pstatus, L));
   }
@@ -708,7 +720,7 @@ extern "C" sdp_status sdp_newton_solve(sdp_handle* h, const double* V, const dou
   CU(gemm_f64(st, false, false, n, r, n, 1.0, Ct, n, Q, n, 0.0, S.Tm, n, S.ws, ws, L));
   CU(gemm_f64(st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, ws, L));
   if (h->kind == SDP_A_DENSE_SVEC) {
-    CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, ws, L));
+    CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, ws, L, nullptr, GEMM_LOWER));
     svec_pack_plus<double>(st, n, r, S.Z, nullptr, nullptr, S.zsvec, nullptr, L);
     prof_begin(h, 1);
     rows_gemv<double>(st, h->a_dense, m, h->N, S.zsvec, S.partA, nullptr, L);

@@ -8,8 +8,8 @@
 // that the consumer kernel reduces in a fixed order.  A matrix larger than L2 is loaded with
 // an evict-first L2 policy so that the L2-resident operands (B, the inverse, the n x n work
 // matrices) survive the stream.  In FP64 these kernels are limited by the FP64 FMA rate of
-// GB300 (about 1 TFLOP/s: one FMA per 8-byte element caps them near 4 TB/s); in FP32 they
-// are limited by HBM.
+// GB300 (1.26 TFLOP/s: one FMA per 8-byte element caps them near 5 TB/s); in FP32 they are
+// limited by HBM.  Launch shapes are chosen so that the CTAs spread evenly over the SMs.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -17,7 +17,7 @@ namespace wc {
 
 namespace {
 
-constexpr int GV_SLAB = 2048;           // elements of x per CTA
+constexpr int GV_SWMAX = 4096;          // largest slab of x per CTA (elements)
 constexpr int GV_WARPS = 8;
 
 template <typename T> struct V16;
@@ -45,66 +45,125 @@ __device__ __forceinline__ float ld1<float>(const float* p, uint64_t pol, bool s
   return stream ? ld_stream_f(p, pol) : __ldg(p);
 }
 
-// STREAM (a matrix larger than L2): 4 rows per warp, evict-first loads.  Otherwise one row per
-// warp, so that the small L2-resident matrices still spread over the whole GPU.
+// One CTA: R rows (warp w takes rows w, w + 8, ...; two at a time for memory-level
+// parallelism) times one slab of SW columns, whose x segment it stages in shared memory.
+// STREAM (a matrix larger than L2) loads A with the evict-first policy.
 template <typename T, bool VEC, bool STREAM>
 __global__ void __launch_bounds__(GV_WARPS * 32)
-rows_gemv_kernel(const T* __restrict__ A, int m, int64_t L, const T* __restrict__ x,
-                 T* __restrict__ part, const int32_t* __restrict__ done) {
+rows_gemv_kernel(const T* __restrict__ A, int m, int64_t L, const T* __restrict__ x, T* __restrict__ part,
+                 int SW, int R, const int32_t* __restrict__ done) {
   if (done && *done) return;
   const uint64_t pol = STREAM ? evict_first_policy() : 0;
   using VT = V16<T>;
+  using V = typename VT::type;
   constexpr int W = VT::W;
-  __shared__ __align__(16) T xs[GV_SLAB];
+  __shared__ __align__(16) T xs[GV_SWMAX];
   const int s = blockIdx.x;
-  const int64_t k0 = (int64_t)s * GV_SLAB;
-  const int len = (int)((L - k0) < (int64_t)GV_SLAB ? (L - k0) : (int64_t)GV_SLAB);
+  const int64_t k0 = (int64_t)s * SW;
+  const int len = (int)((L - k0) < (int64_t)SW ? (L - k0) : (int64_t)SW);
   for (int q = threadIdx.x; q < len; q += blockDim.x) xs[q] = x[k0 + q];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int RPW = STREAM ? 4 : 1;
-  for (int rr = 0; rr < RPW; ++rr) {
-    const int i = blockIdx.y * (RPW * GV_WARPS) + rr * GV_WARPS + warp;
-    if (i >= m) break;
-    const T* row = A + (int64_t)i * L + k0;
-    T acc = 0;
-    if (VEC) {
-      // row start is 16-byte aligned (L a multiple of W, base aligned); tail handled below
-      const typename VT::type* rv = reinterpret_cast<const typename VT::type*>(row);
-      const typename VT::type* xv = reinterpret_cast<const typename VT::type*>(xs);
-      const int np = len / W;
-      int q = lane;
-      for (; q + 96 < np; q += 128) {
-        typename VT::type v0 = VT::ld(rv + q, pol, STREAM), v1 = VT::ld(rv + q + 32, pol, STREAM);
-        typename VT::type v2 = VT::ld(rv + q + 64, pol, STREAM), v3 = VT::ld(rv + q + 96, pol, STREAM);
-        typename VT::type w0 = xv[q], w1 = xv[q + 32], w2 = xv[q + 64], w3 = xv[q + 96];
+  const int rbase = blockIdx.y * R;
+  for (int t = warp; t < R; t += 2 * GV_WARPS) {
+    const int ia = rbase + t;
+    if (ia >= m) break;
+    const int ib = rbase + t + GV_WARPS;
+    const bool hb = (t + GV_WARPS < R) && (ib < m);
+    const T* ra = A + (int64_t)ia * L + k0;
+    const T* rb = A + (int64_t)(hb ? ib : ia) * L + k0;
+    T acc_a = 0, acc_b = 0;
+    if (hb) {   // two rows in flight (warp-uniform branch)
+      if (VEC) {
+        // row starts are 16-byte aligned (L and SW multiples of W, base aligned); tail below
+        const V* va = reinterpret_cast<const V*>(ra);
+        const V* vb = reinterpret_cast<const V*>(rb);
+        const V* xv = reinterpret_cast<const V*>(xs);
+        const int np = len / W;
+        int q = lane;
+        for (; q + 32 < np; q += 64) {
+          V a0 = VT::ld(va + q, pol, STREAM), a1 = VT::ld(va + q + 32, pol, STREAM);
+          V b0 = VT::ld(vb + q, pol, STREAM), b1 = VT::ld(vb + q + 32, pol, STREAM);
+          V w0 = xv[q], w1 = xv[q + 32];
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-          acc = fma(VT::get(v0, k), VT::get(w0, k), acc);
-          acc = fma(VT::get(v1, k), VT::get(w1, k), acc);
-          acc = fma(VT::get(v2, k), VT::get(w2, k), acc);
-          acc = fma(VT::get(v3, k), VT::get(w3, k), acc);
+          for (int k = 0; k < W; ++k) {
+            acc_a = fma(VT::get(a0, k), VT::get(w0, k), acc_a);
+            acc_b = fma(VT::get(b0, k), VT::get(w0, k), acc_b);
+            acc_a = fma(VT::get(a1, k), VT::get(w1, k), acc_a);
+            acc_b = fma(VT::get(b1, k), VT::get(w1, k), acc_b);
+          }
+        }
+        for (; q < np; q += 32) {
+          V a0 = VT::ld(va + q, pol, STREAM), b0 = VT::ld(vb + q, pol, STREAM), w0 = xv[q];
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            acc_a = fma(VT::get(a0, k), VT::get(w0, k), acc_a);
+            acc_b = fma(VT::get(b0, k), VT::get(w0, k), acc_b);
+          }
+        }
+        for (int c = np * W + lane; c < len; c += 32) {
+          acc_a = fma(ra[c], xs[c], acc_a);
+          acc_b = fma(rb[c], xs[c], acc_b);
+        }
+      } else {
+        int q = lane;
+        for (; q + 32 < len; q += 64) {
+          T a0 = ld1<T>(ra + q, pol, STREAM), a1 = ld1<T>(ra + q + 32, pol, STREAM);
+          T b0 = ld1<T>(rb + q, pol, STREAM), b1 = ld1<T>(rb + q + 32, pol, STREAM);
+          acc_a = fma(a0, xs[q], acc_a); acc_b = fma(b0, xs[q], acc_b);
+          acc_a = fma(a1, xs[q + 32], acc_a); acc_b = fma(b1, xs[q + 32], acc_b);
+        }
+        for (; q < len; q += 32) {
+          acc_a = fma(ld1<T>(ra + q, pol, STREAM), xs[q], acc_a);
+          acc_b = fma(ld1<T>(rb + q, pol, STREAM), xs[q], acc_b);
         }
       }
-      for (; q < np; q += 32) {
-        typename VT::type v = VT::ld(rv + q, pol, STREAM), w = xv[q];
+    } else {    // a single row: four loads in flight
+      if (VEC) {
+        const V* va = reinterpret_cast<const V*>(ra);
+        const V* xv = reinterpret_cast<const V*>(xs);
+        const int np = len / W;
+        int q = lane;
+        for (; q + 96 < np; q += 128) {
+          V a0 = VT::ld(va + q, pol, STREAM), a1 = VT::ld(va + q + 32, pol, STREAM);
+          V a2 = VT::ld(va + q + 64, pol, STREAM), a3 = VT::ld(va + q + 96, pol, STREAM);
+          V w0 = xv[q], w1 = xv[q + 32], w2 = xv[q + 64], w3 = xv[q + 96];
 #pragma unroll
-        for (int k = 0; k < W; ++k) acc = fma(VT::get(v, k), VT::get(w, k), acc);
+          for (int k = 0; k < W; ++k) {
+            acc_a = fma(VT::get(a0, k), VT::get(w0, k), acc_a);
+            acc_b = fma(VT::get(a1, k), VT::get(w1, k), acc_b);
+            acc_a = fma(VT::get(a2, k), VT::get(w2, k), acc_a);
+            acc_b = fma(VT::get(a3, k), VT::get(w3, k), acc_b);
+          }
+        }
+        for (; q < np; q += 32) {
+          V a0 = VT::ld(va + q, pol, STREAM), w0 = xv[q];
+#pragma unroll
+          for (int k = 0; k < W; ++k) acc_a = fma(VT::get(a0, k), VT::get(w0, k), acc_a);
+        }
+        for (int c = np * W + lane; c < len; c += 32) acc_a = fma(ra[c], xs[c], acc_a);
+      } else {
+        int q = lane;
+        for (; q + 96 < len; q += 128) {
+          T a0 = ld1<T>(ra + q, pol, STREAM), a1 = ld1<T>(ra + q + 32, pol, STREAM);
+          T a2 = ld1<T>(ra + q + 64, pol, STREAM), a3 = ld1<T>(ra + q + 96, pol, STREAM);
+          acc_a = fma(a0, xs[q], acc_a); acc_b = fma(a1, xs[q + 32], acc_b);
+          acc_a = fma(a2, xs[q + 64], acc_a); acc_b = fma(a3, xs[q + 96], acc_b);
+        }
+        for (; q < len; q += 32) acc_a = fma(ld1<T>(ra + q, pol, STREAM), xs[q], acc_a);
       }
-      for (int t = np * W + lane; t < len; t += 32) acc = fma(row[t], xs[t], acc);
-    } else {
-      int q = lane;
-      for (; q + 96 < len; q += 128) {
-        T v0 = ld1<T>(row + q, pol, STREAM), v1 = ld1<T>(row + q + 32, pol, STREAM);
-        T v2 = ld1<T>(row + q + 64, pol, STREAM), v3 = ld1<T>(row + q + 96, pol, STREAM);
-        acc = fma(v0, xs[q], acc); acc = fma(v1, xs[q + 32], acc);
-        acc = fma(v2, xs[q + 64], acc); acc = fma(v3, xs[q + 96], acc);
-      }
-      for (; q < len; q += 32) acc = fma(ld1<T>(row + q, pol, STREAM), xs[q], acc);
+      acc_a += acc_b;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) part[(int64_t)s * m + i] = acc;
+    for (int o = 16; o > 0; o >>= 1) acc_a += __shfl_xor_sync(0xffffffffu, acc_a, o);
+    if (hb) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc_b += __shfl_xor_sync(0xffffffffu, acc_b, o);
+    }
+    if (lane == 0) {
+      part[(int64_t)s * m + ia] = acc_a;
+      if (hb) part[(int64_t)s * m + ib] = acc_b;
+    }
   }
 }
 
@@ -129,17 +188,16 @@ rows_gemvT_kernel(const T* __restrict__ A, int m, int64_t L, const T* __restrict
     for (int k = 0; k < W; ++k) a[k] = 0;
     const int64_t stv = L / W;   // rows apart, in vector units (L a multiple of W)
     int i = i0;
-    for (; i + 3 < i1; i += 4) {
+    for (; i + 7 < i1; i += 8) {
       const typename VT::type* b = reinterpret_cast<const typename VT::type*>(A + (int64_t)i * L + c);
-      typename VT::type v0 = VT::ld(b, pol, STREAM), v1 = VT::ld(b + stv, pol, STREAM);
-      typename VT::type v2 = VT::ld(b + 2 * stv, pol, STREAM), v3 = VT::ld(b + 3 * stv, pol, STREAM);
-      const T p0 = __ldg(p + i), p1 = __ldg(p + i + 1), p2 = __ldg(p + i + 2), p3 = __ldg(p + i + 3);
+      typename VT::type v[8];
 #pragma unroll
-      for (int k = 0; k < W; ++k) {
-        a[k] = fma(p0, VT::get(v0, k), a[k]);
-        a[k] = fma(p1, VT::get(v1, k), a[k]);
-        a[k] = fma(p2, VT::get(v2, k), a[k]);
-        a[k] = fma(p3, VT::get(v3, k), a[k]);
+      for (int u = 0; u < 8; ++u) v[u] = VT::ld(b + u * stv, pol, STREAM);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const T pu = __ldg(p + i + u);
+#pragma unroll
+        for (int k = 0; k < W; ++k) a[k] = fma(pu, VT::get(v[u], k), a[k]);
       }
     }
     for (; i < i1; ++i) {
@@ -195,33 +253,94 @@ bool is_vec_ok(const T* A, int64_t L) {
   return (L % V16<T>::W == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
 }
 
+struct GvPlan {
+  int slabs, SW, R;
+  bool stream;
+};
+
+// Fraction of the busiest SM's share that the average SM does, for `units` equal CTAs.
+double balance(int64_t units) {
+  const int64_t S = g_num_sms;
+  const int64_t per = (units + S - 1) / S;
+  return (double)units / (double)(per * S);
+}
+
+// Launch shape of y = A x (A m x L of `esize`-byte elements): the slab width and rows per CTA.
+// A streamed matrix gets wide slabs and the rows per CTA whose CTA count spreads evenly over
+// the SMs; a small one gets one row per warp and enough slabs to cover the GPU.
+GvPlan gv_plan(int m, int64_t L, int esize) {
+  GvPlan P;
+  P.stream = (int64_t)m * L * esize > ((int64_t)64 << 20);
+  const int64_t S = g_num_sms;
+  if (P.stream) {
+    double best = -1.0;
+    P.SW = 0; P.R = 0; P.slabs = 0;
+    for (int sw : {GV_SWMAX, GV_SWMAX / 2}) {
+      const int64_t slabs = (L + sw - 1) / sw;
+      for (int R = 16; R <= 64; ++R) {
+        const int64_t units = slabs * ((m + R - 1) / R);
+        if (units < 4 * S) continue;
+        double b = balance(units);
+        if (b > best + 1e-9) { best = b; P.SW = sw; P.R = R; P.slabs = (int)slabs; }
+      }
+    }
+    if (P.SW == 0) { P.SW = GV_SWMAX / 2; P.R = 16; P.slabs = (int)((L + P.SW - 1) / P.SW); }
+    return P;
+  }
+  P.R = GV_WARPS;
+  const int64_t rb = (m + P.R - 1) / P.R;
+  int64_t slabs = (L + 2047) / 2048;
+  const int64_t want = 4 * S;
+  if (slabs * rb < want) {
+    int64_t need = (want + rb - 1) / rb;
+    int64_t cap = (L + 127) / 128;
+    slabs = need < cap ? need : cap;
+    if (slabs < 1) slabs = 1;
+  }
+  int64_t sw = (L + slabs - 1) / slabs;
+  sw = (sw + 3) / 4 * 4;
+  P.SW = (int)sw;
+  P.slabs = (int)((L + sw - 1) / sw);
+  return P;
+}
+
 }  // namespace
 
-int rows_gemv_slabs(int64_t L) { return (int)((L + GV_SLAB - 1) / GV_SLAB); }
+int rows_gemv_slabs(int m, int64_t L, int esize) { return gv_plan(m, L, esize).slabs; }
+
+size_t rows_gemv_part_elems(int64_t rows_max, int64_t L) {
+  return (size_t)(rows_max < 1 ? 1 : rows_max) * (size_t)((L + 127) / 128 + 1);
+}
 
 template <typename T>
 void rows_gemv(cudaStream_t st, const T* A, int m, int64_t L, const T* x, T* part, const int32_t* done,
                int64_t* launches) {
-  const bool stream = (int64_t)m * L * (int64_t)sizeof(T) > (int64_t)64 << 20;   // stream what cannot stay in L2
-  const int rows = (stream ? 4 : 1) * GV_WARPS;
-  dim3 grid(rows_gemv_slabs(L), (m + rows - 1) / rows);
-  if (is_vec_ok(A, L)) {
-    if (stream) rows_gemv_kernel<T, true, true><<<grid, GV_WARPS * 32, 0, st>>>(A, m, L, x, part, done);
-    else rows_gemv_kernel<T, true, false><<<grid, GV_WARPS * 32, 0, st>>>(A, m, L, x, part, done);
+  const GvPlan P = gv_plan(m, L, (int)sizeof(T));
+  dim3 grid(P.slabs, (m + P.R - 1) / P.R);
+  const bool vec = is_vec_ok(A, L);
+  if (vec) {
+    if (P.stream) rows_gemv_kernel<T, true, true><<<grid, GV_WARPS * 32, 0, st>>>(A, m, L, x, part, P.SW, P.R, done);
+    else rows_gemv_kernel<T, true, false><<<grid, GV_WARPS * 32, 0, st>>>(A, m, L, x, part, P.SW, P.R, done);
   } else {
-    if (stream) rows_gemv_kernel<T, false, true><<<grid, GV_WARPS * 32, 0, st>>>(A, m, L, x, part, done);
-    else rows_gemv_kernel<T, false, false><<<grid, GV_WARPS * 32, 0, st>>>(A, m, L, x, part, done);
+    if (P.stream) rows_gemv_kernel<T, false, true><<<grid, GV_WARPS * 32, 0, st>>>(A, m, L, x, part, P.SW, P.R, done);
+    else rows_gemv_kernel<T, false, false><<<grid, GV_WARPS * 32, 0, st>>>(A, m, L, x, part, P.SW, P.R, done);
   }
   if (launches) ++*launches;
 }
 
-int rows_gemvT_groups(int m, int64_t L) {
-  int64_t cols_per_cta = GT_THREADS * 2;
-  int64_t ctas = (L + cols_per_cta - 1) / cols_per_cta;
-  int64_t want = (4 * (int64_t)g_num_sms + ctas - 1) / ctas;
-  int64_t maxg = (m + 31) / 32;
-  int64_t g = want < maxg ? want : maxg;
-  return (int)(g < 1 ? 1 : g);
+int rows_gemvT_groups(int m, int64_t L, int esize) {
+  const int64_t W = 16 / esize;
+  const int64_t cb = (L + W * GT_THREADS - 1) / (W * GT_THREADS);
+  const int64_t maxg = (m + 31) / 32;
+  int64_t bestg = 1;
+  double best = -1.0;
+  for (int64_t g = 1; g <= maxg; ++g) {
+    const int64_t units = cb * g;
+    double b = balance(units);
+    if (units < 2 * g_num_sms) b -= 1.0;   // too few CTAs to cover the GPU
+    if (b > best + 1e-9) { best = b; bestg = g; }
+  }
+  return (int)bestg;
 }
 
 template <typename T>

@@ -22,48 +22,79 @@ constexpr int NB = 32;
 
 // Factor the w x w diagonal block at k0 (already updated by earlier blocks): L_KK into the
 // lower triangle of A (upper part of the block zeroed), its inverse into Li (w x w, ld w).
+//
+// GB300 issues FP64 arithmetic at 2 lane-operations per SM per clock and a warp instruction
+// costs its full width even with lanes masked off, so this kernel, which runs on one SM,
+// enumerates exactly the active entries of each step (a table of the lower pairs, last
+// column first) and takes one division per pivot.  Step p (one barrier each) does
+//   the LDL^T update  S_ij -= S_ip S_jp / S_pp             (p < j <= i),
+//   the inverse sweep X~_ij -= (S_ip / S_pp) X~_pj          (i > p >= j),
+// so that X~ = L~^{-1} for the unit lower factor L~ = [S_ip / S_pp]; then L = L~ D^{1/2} and
+// L^{-1} = D^{-1/2} X~ with D = diag(S_pp).
 __global__ void __launch_bounds__(256)
 chol_block_kernel(int n, int k0, int w, double* __restrict__ A, double* __restrict__ Li,
                   int32_t* __restrict__ status) {
   __shared__ double S[NB][NB + 1];
   __shared__ double X[NB][NB + 1];
+  __shared__ double inv[NB], dsq[NB], rdsq[NB];
+  __shared__ unsigned char ti[NB * (NB + 1) / 2], tj[NB * (NB + 1) / 2];
   __shared__ int bad;
-  for (int q = threadIdx.x; q < w * w; q += blockDim.x) {
-    int i = q % w, j = q / w;
+  const int ww = w * w;
+  for (int q = threadIdx.x; q < ww; q += blockDim.x) {
+    const int i = q % w, j = q / w;
     S[i][j] = A[(k0 + i) + (int64_t)(k0 + j) * n];
+    X[i][j] = (i == j) ? 1.0 : 0.0;
+    if (i >= j) {                          // column j's pairs start at T(w-1-j), T(k) = k(k+1)/2
+      const int c = w - 1 - j;
+      const int pos = c * (c + 1) / 2 + (i - j);
+      ti[pos] = (unsigned char)i;
+      tj[pos] = (unsigned char)j;
+    }
   }
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
-  // right-looking unblocked Cholesky on the lower triangle
-  for (int p = 0; p < w; ++p) {
-    if (threadIdx.x == 0) {
-      double piv = S[p][p];
-      if (!(piv > 0.0) || !isfinite(piv)) { bad = 1; piv = 1.0; }
-      S[p][p] = sqrt(piv);
-    }
-    __syncthreads();
-    const double lpp = S[p][p];
-    for (int i = p + 1 + threadIdx.x; i < w; i += blockDim.x) S[i][p] /= lpp;
-    __syncthreads();
-    for (int q = threadIdx.x; q < w * w; q += blockDim.x) {
-      int i = q % w, j = q / w;
-      if (j > p && i >= j) S[i][j] -= S[i][p] * S[j][p];
-    }
-    __syncthreads();
-  }
-  // X = L^{-1} by forward substitution, one column per thread
-  for (int j = threadIdx.x; j < w; j += blockDim.x) {
-    for (int i = 0; i < w; ++i) {
-      double s = (i == j) ? 1.0 : 0.0;
-      for (int k = j; k < i; ++k) s -= S[i][k] * X[k][j];
-      X[i][j] = (i >= j) ? s / S[i][i] : 0.0;
-    }
+  if (threadIdx.x == 0) {
+    const double piv = S[0][0];
+    if (!(piv > 0.0) || !isfinite(piv)) bad = 1;
+    inv[0] = (piv > 0.0 && isfinite(piv)) ? 1.0 / piv : 1.0;
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < w * w; q += blockDim.x) {
-    int i = q % w, j = q / w;
-    A[(k0 + i) + (int64_t)(k0 + j) * n] = (i >= j) ? S[i][j] : 0.0;
-    Li[i + (int64_t)j * w] = X[i][j];
+  for (int p = 0; p < w; ++p) {
+    const double ip = inv[p];
+    const int k = w - 1 - p;
+    const int cnt_a = k * (k + 1) / 2;     // pairs with j > p: the first T(k) table entries
+    const int cnt = cnt_a + k * (p + 1);   // plus the k x (p + 1) block of the sweep
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      if (t < cnt_a) {
+        const int i = ti[t], j = tj[t];
+        const double v = S[i][j] - S[i][p] * S[j][p] * ip;
+        S[i][j] = v;
+        if (i == j && j == p + 1) {        // the next pivot is final now
+          if (!(v > 0.0) || !isfinite(v)) bad = 1;
+          inv[j] = (v > 0.0 && isfinite(v)) ? 1.0 / v : 1.0;
+        }
+      } else {
+        const int u = t - cnt_a;
+        const int i = p + 1 + u % k, j = u / k;
+        X[i][j] -= (S[i][p] * ip) * X[p][j];
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < w) {                   // D^{1/2} and D^{-1/2}, once per pivot
+    const int j = threadIdx.x;
+    const double dj = sqrt(S[j][j] > 0.0 ? S[j][j] : 1.0);
+    dsq[j] = dj;
+    rdsq[j] = 1.0 / dj;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < ww; q += blockDim.x) {
+    const int i = q % w, j = q / w;
+    double l = 0.0, x = 0.0;
+    if (i > j) { l = S[i][j] * rdsq[j]; x = X[i][j] * rdsq[i]; }
+    else if (i == j) { l = dsq[j]; x = rdsq[i]; }
+    A[(k0 + i) + (int64_t)(k0 + j) * n] = l;
+    Li[i + (int64_t)j * w] = x;
   }
   if (threadIdx.x == 0 && bad) *status = 5;
 }
@@ -85,14 +116,13 @@ __global__ void zero_upper_kernel(int n, double* __restrict__ A) {
   if (j > i) A[q] = 0.0;
 }
 
-__global__ void symmetrize_kernel(int n, double* __restrict__ A) {
+// upper triangle := lower triangle
+__global__ void lower_to_full_kernel(int n, double* __restrict__ A) {
   int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (int64_t)n * n) return;
   int i = (int)(q % n), j = (int)(q / n);
   if (i <= j) return;
-  double v = 0.5 * (A[q] + A[j + (int64_t)i * n]);
-  A[q] = v;
-  A[j + (int64_t)i * n] = v;
+  A[j + (int64_t)i * n] = A[q];
 }
 
 inline unsigned nblk(int64_t total, int t) { return (unsigned)((total + t - 1) / t); }
@@ -126,7 +156,7 @@ cudaError_t spd_inverse(cudaStream_t st, int n, double* A, double* work, size_t 
     if (launches) ++*launches;
     // A_RR -= L_RK L_RK^T
     e = gemm_f64(st, false, true, rest, rest, w, -1.0, T, rest, T, rest, 1.0, A + k1 + (int64_t)k1 * n, n, gemm_ws,
-                 gemm_ws_elems, launches);
+                 gemm_ws_elems, launches, nullptr, GEMM_LOWER);
     if (e != cudaSuccess) return e;
   }
   zero_upper_kernel<<<nblk((int64_t)n * n, 256), 256, 0, st>>>(n, A);
@@ -138,7 +168,8 @@ cudaError_t spd_inverse(cudaStream_t st, int n, double* A, double* work, size_t 
     const int w = (n - i0) < NB ? (n - i0) : NB;
     const double* Lib = Li + (size_t)b * NB * NB;
     if (i0 > 0) {
-      e = gemm_f64(st, false, false, w, i0, i0, 1.0, A + i0, n, X, n, 0.0, U, w, gemm_ws, gemm_ws_elems, launches);
+      e = gemm_f64(st, false, false, w, i0, i0, 1.0, A + i0, n, X, n, 0.0, U, w, gemm_ws, gemm_ws_elems, launches,
+                   nullptr, GEMM_KSTART_COL);   // X lower triangular
       if (e != cudaSuccess) return e;
       e = gemm_f64(st, false, false, w, i0, w, -1.0, Lib, w, U, w, 0.0, X + i0, n, gemm_ws, gemm_ws_elems, launches);
       if (e != cudaSuccess) return e;
@@ -147,9 +178,11 @@ cudaError_t spd_inverse(cudaStream_t st, int n, double* A, double* work, size_t 
     if (launches) ++*launches;
   }
   // ---- A^{-1} = X^T X
-  e = gemm_f64(st, true, false, n, n, n, 1.0, X, n, X, n, 0.0, A, n, gemm_ws, gemm_ws_elems, launches);
+  // lower triangle of X^T X, skipping the zero upper part of X
+  e = gemm_f64(st, true, false, n, n, n, 1.0, X, n, X, n, 0.0, A, n, gemm_ws, gemm_ws_elems, launches, nullptr,
+               GEMM_LOWER | GEMM_KSTART_ROW | GEMM_KSTART_COL);
   if (e != cudaSuccess) return e;
-  symmetrize_kernel<<<nblk((int64_t)n * n, 256), 256, 0, st>>>(n, A);
+  lower_to_full_kernel<<<nblk((int64_t)n * n, 256), 256, 0, st>>>(n, A);
   if (launches) ++*launches;
   return cudaGetLastError();
 }

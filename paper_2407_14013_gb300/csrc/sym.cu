@@ -32,7 +32,7 @@ __global__ void svec_pack_plus_kernel(int n, int r, const T* __restrict__ Z, con
   if (q >= (int64_t)n * n) return;
   int a = (int)(q % n), b = (int)(q / n);
   if (a < b) return;
-  double v = 0.5 * ((double)Z[a + (int64_t)b * n] + (double)Z[b + (int64_t)a * n]);
+  double v = (double)Z[a + (int64_t)b * n];   // lower triangle (a >= b) of the symmetric Z
   if (U) {
     double t = 0.0;
     for (int k = 0; k < r; ++k)
@@ -117,78 +117,77 @@ namespace wc {
 
 namespace {
 
-constexpr int AQ_WARPS = 8;
+constexpr int AQ_THREADS = 256;
 
-// One CTA per constraint i: G_i = A_i Q with A_i read once from its svec row.  Column b of
-// the lower triangle (entries a = b..n-1, contiguous) goes to warp b mod 8; an off-diagonal
-// entry s = sqrt2 A_i[a,b] adds (s/sqrt2) Q[b,:] to row a and (s/sqrt2) Q[a,:] to row b.
-// Each warp accumulates into its own n x r copy, so no two threads update the same word.
+// One CTA per constraint i: G_i = A_i Q.  The svec row of A_i is staged in shared memory,
+// then thread a forms row a of G_i in registers,
+//   G_i[a, :] = sum_b A_i[a, b] Q[b, :],
+// reading A_i[a, b] below the diagonal from column b of the svec row (entry a - b: lanes with
+// consecutive a read consecutive words) and above it from column a (entry b - a).  Every
+// thread does n multiply-add rows of width r, so the work is balanced, and no partial sums
+// are shared: FP64 work is the n^2 r multiply-adds of the product and nothing else.
 template <int r>
-__global__ void __launch_bounds__(AQ_WARPS * 32)
+__global__ void __launch_bounds__(AQ_THREADS)
 dense_AiQ_kernel(const double* __restrict__ A, int n, int64_t N, int i0, int mb, const double* __restrict__ Q,
                  double* __restrict__ G) {
-  extern __shared__ double sm[];
-  double* Qs = sm;                                 // n x r, row-major
-  double* acc = sm + (int64_t)n * r;               // AQ_WARPS x n x r
+  extern __shared__ __align__(16) double sm[];
+  double* As = sm;                                  // svec row, N entries (+ pad to 2)
+  double* Qs = sm + ((N + 1) & ~int64_t(1));        // n x r, row-major
   const int il = blockIdx.x, i = i0 + il;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nr = n * r;
-  for (int q = threadIdx.x; q < nr; q += blockDim.x) {
-    const int a = q / r, j = q % r;
-    Qs[q] = Q[a + (int64_t)j * n];
-  }
-  for (int q = threadIdx.x; q < AQ_WARPS * nr; q += blockDim.x) acc[q] = 0.0;
-  __syncthreads();
   const double* row = A + (int64_t)i * N;
-  double* my = acc + (int64_t)warp * nr;
-  for (int b = warp; b < n; b += AQ_WARPS) {
-    const double* col = row + svec_index(n, b, b);
-    double colsum[r];
-#pragma unroll
-    for (int j = 0; j < r; ++j) colsum[j] = 0.0;
-    for (int a = b + lane; a < n; a += 32) {
-      const double s = __ldg(col + (a - b));
-      if (a == b) {
-#pragma unroll
-        for (int j = 0; j < r; ++j) colsum[j] = fma(s, Qs[b * r + j], colsum[j]);
-      } else {
-        const double v = s * WC_RSQRT2;
-#pragma unroll
-        for (int j = 0; j < r; ++j) {
-          my[a * r + j] = fma(v, Qs[b * r + j], my[a * r + j]);
-          colsum[j] = fma(v, Qs[a * r + j], colsum[j]);
-        }
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < r; ++j) {
-      double t = warp_sum(colsum[j]);
-      if (lane == 0) my[b * r + j] += t;
-    }
-    __syncwarp();
+  if ((N & 1) == 0) {                               // 16-byte rows: vector loads
+    const double2* src = reinterpret_cast<const double2*>(row);
+    double2* dst = reinterpret_cast<double2*>(As);
+    for (int64_t q = threadIdx.x; q < N / 2; q += blockDim.x) dst[q] = __ldg(src + q);
+  } else {
+    for (int64_t q = threadIdx.x; q < N; q += blockDim.x) As[q] = __ldg(row + q);
+  }
+  for (int q = threadIdx.x; q < n * r; q += blockDim.x) {
+    const int b = q / r, j = q % r;
+    Qs[q] = Q[b + (int64_t)j * n];
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < nr; q += blockDim.x) {
-    const int a = q / r, j = q % r;
-    double s = 0.0;
+  for (int a = threadIdx.x; a < n; a += blockDim.x) {
+    double off[r], dg[r];
 #pragma unroll
-    for (int w = 0; w < AQ_WARPS; ++w) s += acc[(int64_t)w * nr + q];
-    G[a + ((int64_t)j * mb + il) * n] = s;
+    for (int j = 0; j < r; ++j) off[j] = 0.0;
+    int64_t idx = a;                                // (a, b = 0) in column 0
+    for (int b = 0; b < a; ++b) {
+      const double s = As[idx];
+#pragma unroll
+      for (int j = 0; j < r; ++j) off[j] = fma(s, Qs[b * r + j], off[j]);
+      idx += n - b - 1;                             // (a, b + 1) in column b + 1
+    }
+    const double sd = As[idx];                      // diagonal (a, a)
+#pragma unroll
+    for (int j = 0; j < r; ++j) dg[j] = sd * Qs[a * r + j];
+    for (int b = a + 1; b < n; ++b) {               // (b, a) in column a
+      const double s = As[idx + (b - a)];
+#pragma unroll
+      for (int j = 0; j < r; ++j) off[j] = fma(s, Qs[b * r + j], off[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < r; ++j) G[a + ((int64_t)j * mb + il) * n] = fma(off[j], WC_RSQRT2, dg[j]);
   }
 }
 
 }  // namespace
 
+static size_t dense_AiQ_smem(int n, int r) {
+  const int64_t N = (int64_t)n * (n + 1) / 2;
+  return (size_t)(((N + 1) & ~int64_t(1)) + (int64_t)n * r) * sizeof(double);
+}
+
 bool dense_AiQ(cudaStream_t st, const double* A, int n, int i0, int mb, int r, const double* Q, double* G,
                int64_t* launches) {
-  const size_t smem = (size_t)(AQ_WARPS + 1) * n * r * sizeof(double);
-  if (r < 1 || r > 16 || smem > 200 * 1024) return false;
+  const size_t smem = dense_AiQ_smem(n, r);
+  if (r < 1 || r > 16 || smem > 220 * 1024) return false;
   const int64_t N = (int64_t)n * (n + 1) / 2;
   switch (r) {
 #define WC_AIQ_CASE(R)                                                                              \
     case R:                                                                                         \
-      cudaFuncSetAttribute(dense_AiQ_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
-      dense_AiQ_kernel<R><<<mb, AQ_WARPS * 32, smem, st>>>(A, n, N, i0, mb, Q, G);                   \
+      cudaFuncSetAttribute(dense_AiQ_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+      dense_AiQ_kernel<R><<<mb, AQ_THREADS, smem, st>>>(A, n, N, i0, mb, Q, G);                      \
       break;
     WC_AIQ_CASE(1) WC_AIQ_CASE(2) WC_AIQ_CASE(3) WC_AIQ_CASE(4) WC_AIQ_CASE(5) WC_AIQ_CASE(6)
     WC_AIQ_CASE(7) WC_AIQ_CASE(8) WC_AIQ_CASE(9) WC_AIQ_CASE(10) WC_AIQ_CASE(11) WC_AIQ_CASE(12)
