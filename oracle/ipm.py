@@ -156,3 +156,39 @@ def ipm_solve(prob, tol: float = 1e-8, max_iter: int = 100, step_frac: float = 0
         st = IPMState(X=0.5 * (Xn + Xn.T), y=y + ad * dy, S=0.5 * (Sn + Sn.T))
         log.append(IPMLog(it=it, mu=mu, rel_gap=gap, pinf=pinf, dinf=dinf, alpha_p=ap, alpha_d=ad, sigma=sigma))
     return IPMResult(X=st.X, y=st.y, S=st.S, iters=it, converged=converged, log=log, history=hist)
+
+
+def center(prob, st: IPMState, mu: float, max_iter: int = 50, tol: float = 1e-12) -> IPMState:
+    """Newton steps towards the central-path point of parameter mu: A(X) = b, A^T y + S = C,
+    X S = mu I (NT direction with R_c = mu S^{-1} - X, i.e. sigma mu = mu and no second-order
+    term), with step lengths that keep X, S positive definite.  Stops when the residuals and
+    ||G^{-1} X S G - mu I|| / mu (the scaled centrality) fall below tol."""
+    n = prob.n
+    X, y, S = st.X, st.y, st.S
+    for _ in range(max_iter):
+        r_p = prob.b - A_op(prob, X)
+        R_d = prob.C - At_op(prob, y) - S
+        W = nt_scaling(X, S)
+        G = sqrtm_psd(W)
+        Lam = G @ S @ G
+        Lam = 0.5 * (Lam + Lam.T)
+        cen = float(np.linalg.norm(Lam @ Lam - mu * np.eye(n))) / mu
+        res = max(float(np.linalg.norm(r_p)) / (1 + np.linalg.norm(prob.b)),
+                  float(np.linalg.norm(R_d)) / (1 + np.linalg.norm(prob.C)))
+        if cen <= tol and res <= tol:
+            break
+        Wi = np.linalg.inv(W)
+        Rc = mu * np.linalg.inv(S) - X
+        Rc = 0.5 * (Rc + Rc.T)
+        Ct = R_d - Wi @ Rc @ Wi
+        dX, dy, _ = newton_direct(prob, W, 0.5 * (Ct + Ct.T), r_p, WCW=W @ R_d @ W - Rc)
+        dS = R_d - At_op(prob, dy)
+        dS = 0.5 * (dS + dS.T)
+        ap = min(1.0, 0.95 * max_step(X, dX))
+        ad = min(1.0, 0.95 * max_step(S, dS))
+        a = min(ap, ad)
+        X = X + a * dX
+        y = y + a * dy
+        S = S + a * dS
+        X, S = 0.5 * (X + X.T), 0.5 * (S + S.T)
+    return IPMState(X=X, y=y, S=S)
