@@ -167,6 +167,22 @@ sdp_status sdp_newton_solve_host(sdp_handle* h, const double* V, const double* l
                                  const double* Ct, const double* bt,
                                  double* dX, double* dy, double* dS, sdp_newton_info* info);
 
+/* Vector-Jacobian product of the SDP optimum with respect to the data (C, b), by implicit
+ * differentiation at the final iterate.  The linearised optimality conditions of Section 3,
+ *   A(dX) = db,  A^T(dy) + dS = dC,  dX + W dS W = 0,
+ * have the symmetric KKT matrix K of (Newt-eps), so the cotangents of the data are
+ * [gC; gb] = K^{-1} [sym gX; gy]: one Newton solve on the reformulated operator and its
+ * preconditioner with (C~, b~) = (sym gX, gy), gC = dX, gb = dy.  This is the derivative of
+ * the central-path point at the scaling point W = V diag(lam) V^T; for W the NT scaling of a
+ * well-centred iterate near the optimum it differs from the derivative of the optimum by
+ * O(mu).  The paper states no such product; it reuses its Newton system.
+ *   V, lam  eigen-decomposition of W (as for sdp_newton_solve)
+ *   gX      n x n cotangent of X (its symmetric part is used);  gy  m cotangent of y
+ *   gC      out n x n (symmetric);  gb  out m;  info as for sdp_newton_solve
+ * All arrays are device pointers.  Same status codes as sdp_newton_solve. */
+sdp_status sdp_grad(sdp_handle* h, const double* V, const double* lam, const double* gX, const double* gy,
+                    double* gC, double* gb, sdp_newton_info* info);
+
 /* Diagnostics: copy `count` doubles of an internal buffer of the most recent solve into the
  * device array `dst` (stream-ordered, synchronous).  which: 0 = E (n x n), 1 = D = tau^2 Sigma
  * (d), 2 = B = A Q (m x d, row-major), 3 = inverse of the preconditioner's Schur complement

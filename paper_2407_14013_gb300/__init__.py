@@ -15,7 +15,8 @@ from . import _native as native
 from ._native import (SDP_A_DENSE_SVEC, SDP_A_DIAG, SDP_A_SPARSE_COO, SDP_ENOTCONV, SDP_FP64, SDP_MIXED_FP32,
                       SDP_OK, SdpError, sdp_default_options)
 
-__all__ = ["NewtonSolver", "SdpError", "native", "SDP_A_DIAG", "SDP_A_SPARSE_COO", "SDP_A_DENSE_SVEC"]
+__all__ = ["NewtonSolver", "SdpError", "native", "sdp_optimum", "SDP_A_DIAG", "SDP_A_SPARSE_COO",
+           "SDP_A_DENSE_SVEC"]
 
 KINDS = {"diag": SDP_A_DIAG, "sparse": SDP_A_SPARSE_COO, "dense": SDP_A_DENSE_SVEC}
 
@@ -167,6 +168,22 @@ class NewtonSolver:
         self.last_info = self._info(ci, st)
         return dX, dy, dS, self.last_info
 
+    def grad(self, V, lam, gX, gy, allow_notconv: bool = False):
+        """Cotangents (gC, gb) of the data for cotangents (gX, gy) of the optimum (X, y), by
+        implicit differentiation at the scaling point W = V diag(lam) V^T (sdp_grad)."""
+        torch = self.torch
+        n, m = self.n, self.m
+        f64 = torch.float64
+        lam, gX, gy = (t.to(device=self.device, dtype=f64).contiguous() for t in (lam, gX, gy))
+        V = _colmajor(V.to(device=self.device, dtype=f64))
+        gC = torch.empty((n, n), dtype=f64, device=self.device)
+        gb = torch.empty(m, dtype=f64, device=self.device)
+        ci = native.sdp_newton_info()
+        st = native.sdp_grad(self.handle, _ptr(V), _ptr(lam), _ptr(gX), _ptr(gy), _ptr(gC), _ptr(gb), ci,
+                             allow_notconv=allow_notconv)
+        self.last_info = self._info(ci, st)
+        return gC, gb
+
     def close(self):
         if getattr(self, "handle", None):
             native.sdp_destroy(self.handle)
@@ -177,3 +194,31 @@ class NewtonSolver:
             self.close()
         except Exception:
             pass
+
+
+def sdp_optimum(C, b, X, y, V, lam, solver: NewtonSolver):
+    """Differentiable view of an SDP optimum: returns (X, y) as a function of (C, b).
+
+    (X, y) is the final iterate of an interior-point solve of min <C,X> s.t. A(X) = b, X PSD;
+    (V, lam) is the eigen-decomposition of the NT scaling point of that (well-centred) iterate.
+    Only these are kept for the backward pass, which is one ``solver.grad`` call: the Newton
+    system of the reformulation at the final iterate, reused as the adjoint."""
+    import torch
+
+    class _SdpOptimum(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, C_, b_, X_, y_, V_, lam_):
+            ctx.save_for_backward(V_, lam_)
+            return X_.clone(), y_.clone()
+
+        @staticmethod
+        def backward(ctx, gX, gy):
+            V_, lam_ = ctx.saved_tensors
+            if gX is None:
+                gX = torch.zeros((solver.n, solver.n), dtype=torch.float64, device=solver.device)
+            if gy is None:
+                gy = torch.zeros(solver.m, dtype=torch.float64, device=solver.device)
+            gC, gb = solver.grad(V_, lam_, gX, gy)
+            return gC.to(C.dtype), gb.to(b.dtype), None, None, None, None
+
+    return _SdpOptimum.apply(C, b, X.detach(), y.detach(), V.detach(), lam.detach())

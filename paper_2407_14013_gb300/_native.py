@@ -52,6 +52,7 @@ EXPORTS = {
     "sdp_setup": (c_int32, [POINTER(sdp_problem), POINTER(sdp_options), c_void_p, POINTER(c_void_p)]),
     "sdp_newton_solve": (c_int32, [c_void_p] + [c_void_p] * 7 + [POINTER(sdp_newton_info)]),
     "sdp_newton_solve_host": (c_int32, [c_void_p] + [c_void_p] * 7 + [POINTER(sdp_newton_info)]),
+    "sdp_grad": (c_int32, [c_void_p] + [c_void_p] * 6 + [POINTER(sdp_newton_info)]),
     "sdp_debug_copy": (c_int32, [c_void_p, c_int32, c_void_p, c_int64]),
     "sdp_set_profiling": (c_int32, [c_void_p, c_int32]),
     "sdp_adjoint_dense_noalloc": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
@@ -117,6 +118,11 @@ def sdp_newton_solve(h: int, V: int, lam: int, Ct: int, bt: int, dX: int, dy: in
 def sdp_newton_solve_host(h: int, V: int, lam: int, Ct: int, bt: int, dX: int, dy: int, dS: int,
                           info: sdp_newton_info, allow_notconv: bool = False) -> int:
     return _solve("sdp_newton_solve_host", h, (V, lam, Ct, bt, dX, dy, dS), info, allow_notconv)
+
+
+def sdp_grad(h: int, V: int, lam: int, gX: int, gy: int, gC: int, gb: int, info: sdp_newton_info,
+             allow_notconv: bool = False) -> int:
+    return _solve("sdp_grad", h, (V, lam, gX, gy, gC, gb), info, allow_notconv)
 
 
 def sdp_debug_copy(h: int, which: int, dst: int, count: int) -> None:

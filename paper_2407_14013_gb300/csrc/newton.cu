@@ -851,6 +851,16 @@ extern "C" sdp_status sdp_newton_solve_host(sdp_handle* h, const double* V, cons
   return s;
 }
 
+extern "C" sdp_status sdp_grad(sdp_handle* h, const double* V, const double* lam, const double* gX,
+                               const double* gy, double* gC, double* gb, sdp_newton_info* info) {
+  if (!h) return fail(nullptr, SDP_EINVAL, "NULL handle");
+  if (!V || !lam || !gX || !gy || !gC || !gb) return fail(h, SDP_EINVAL, "NULL array argument");
+  // (C~, b~) = (sym gX, gy); the handle's host-staging buffers hold sym gX and the unused dS
+  launch_sym_copy(h->st, h->n, gX, h->hCt, &h->launches);
+  CU(cudaGetLastError());
+  return sdp_newton_solve(h, V, lam, h->hCt, gy, gC, gb, h->hdS, info);
+}
+
 extern "C" sdp_status sdp_debug_copy(sdp_handle* h, int32_t which, double* dst, int64_t count) {
   if (!h || !dst || count < 0) return fail(h, SDP_EINVAL, "bad debug copy argument");
   const int64_t n = h->n, m = h->m, d = h->d;

@@ -375,6 +375,14 @@ __global__ void correction_rhs_kernel(int m, int d, const double* __restrict__ r
   out[q] = (q < m) ? 0.0 : rho[q];
 }
 
+// out = (g + g^T) / 2 (n x n)
+__global__ void sym_copy_kernel(int n, const double* __restrict__ g, double* __restrict__ out) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)n * n) return;
+  int a = (int)(q % n), b = (int)(q / n);
+  out[q] = 0.5 * (g[q] + g[b + (int64_t)a * n]);
+}
+
 // x += delta
 __global__ void add_correction_kernel(int nt, const double* __restrict__ delta, double* __restrict__ x) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -611,6 +619,11 @@ void launch_mixed_finish(cudaStream_t st, int m, int d, const float* partA32, in
 
 void launch_to_float(cudaStream_t st, int cnt, const double* src, float* dst, const int32_t* done, int64_t* launches) {
   to_float_kernel<<<nblk(cnt, VT), VT, 0, st>>>(cnt, src, dst, done);
+  ++*launches;
+}
+
+void launch_sym_copy(cudaStream_t st, int n, const double* g, double* out, int64_t* launches) {
+  sym_copy_kernel<<<nblk((int64_t)n * n, VT), VT, 0, st>>>(n, g, out);
   ++*launches;
 }
 

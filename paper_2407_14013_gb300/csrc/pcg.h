@@ -61,6 +61,7 @@ void launch_mixed_finish(cudaStream_t st, int m, int d, const float* partA32, in
                          double* out, int mode, PcgCtl* ctl, double* dotbuf, unsigned int* counter,
                          int64_t* launches);
 void launch_to_float(cudaStream_t st, int cnt, const double* src, float* dst, const int32_t* done, int64_t* launches);
+void launch_sym_copy(cudaStream_t st, int n, const double* g, double* out, int64_t* launches);
 void launch_ctl_reset(cudaStream_t st, PcgCtl* dst, const PcgCtl* src, int max_iters, int64_t* launches);
 
 }  // namespace wc
