@@ -107,6 +107,12 @@ typedef struct {
   int32_t max_refine;    /* mixed form: refinement steps at most                                 */
   int32_t max_inner;     /* mixed form: PCG iterations per correction solve at most               */
   double inner_rtol;     /* mixed form: each correction solve stops at ||r|| <= inner_rtol ||r_0|| */
+  int32_t pcg_start;     /* start of the FP64 PCG (both satisfy Cor. pcg: the second block of the
+                            residual is zero):  0 = x0 = P^{-1}[0; g_v] (the preconditioner applied
+                            to the second block of g), which keeps ||r_0|| of the size of ||g||;
+                            1 = x0 = [0; -Sigma^{-1} Q^T c] as printed in Cor. pcg, whose first
+                            block of r_0 grows like 1/mu^2 and sets a floor for the attainable
+                            residual near the end of the interior-point path                     */
 } sdp_options;
 
 typedef struct {
@@ -135,9 +141,65 @@ typedef struct {
   int32_t prof_A32_launches;
 } sdp_newton_info;
 
+/* One outer interior-point iteration (ipm_step) or a whole solve (sdp_solve). */
+typedef struct {
+  int32_t iters;         /* outer iterations performed (sdp_solve) / 1 (ipm_step)                */
+  int32_t converged;     /* 1 if rel_gap, pinf and dinf are all <= gap_tol at exit               */
+  int32_t pcg_iters;     /* PCG iterations of all Newton solves                                  */
+  int32_t eig_sweeps;    /* Jacobi sweeps of all eigen-decompositions                            */
+  int32_t newton_inexact;/* Newton solves that stopped at max_pcg before the stopping test (their
+                            directions are used as they are)                                    */
+  int32_t pad_;
+  double pobj;           /* <C, X>                                                              */
+  double dobj;           /* b^T y                                                               */
+  double rel_gap;        /* |pobj - dobj| / (1 + |pobj| + |dobj|)                               */
+  double pinf;           /* ||b - A(X)|| / (1 + ||b||)                                          */
+  double dinf;           /* ||C - A^T(y) - S||_F / (1 + ||C||_F)                                */
+  double mu;             /* <X, S> / n                                                          */
+  double alpha_p;        /* last primal step length                                             */
+  double alpha_d;        /* last dual step length                                               */
+  double sigma;          /* last centring parameter                                             */
+  double newton_ms;      /* device time in Newton solves                                        */
+  double total_ms;       /* wall time of the call                                               */
+} sdp_ipm_info;
+
+/* Symmetric eigen-decomposition on the device by the parallel cyclic Jacobi method (FP64),
+ * used by the outer loop: A = V diag(lam) V^T.  A (n x n, symmetric, column-major) is
+ * destroyed; V (n x n), lam (n, in no particular order) are outputs.  Stops when the
+ * off-diagonal Frobenius norm is <= tol times the Frobenius norm, or after max_sweeps sweeps
+ * (then SDP_ENOTCONV).  work: device scratch of sdp_eigh_work_elems(n) doubles.  All on
+ * `stream`, synchronous (one host read per sweep).  *sweeps (host, may be NULL) receives the
+ * sweep count.  Not in the paper: its outer loop is an existing solver's (Section 7). */
+int64_t sdp_eigh_work_elems(int32_t n);
+sdp_status sdp_eigh(void* stream, int32_t n, double* A, double* V, double* lam, double tol, int32_t max_sweeps,
+                    double* work, int64_t work_elems, int32_t* sweeps);
+
+/* One iteration of the outer primal-dual interior-point method on the problem of the handle
+ * with data (b, C): (X, y, S) -> (X + a_p dX, y + a_d dy, S + a_d dS) in place.  The method
+ * (Section 7 keeps an existing solver's outer loop and does not describe it) is the textbook
+ * infeasible NT path-following Mehrotra predictor-corrector also written in the oracle:
+ *   W = L (L^T S L)^{-1/2} L^T with X = L L^T (eq. newt), G = L U Gamma^{-1/4} from
+ *   L^T S L = U Gamma U^T (so W = G G^T and G^{-1} X G^{-T} = Gamma^{1/2} is diagonal);
+ *   predictor: (Newt-eps) with b~ = b - A(X), C~ = R_d + S (R_c = -X), R_d = C - A^T(y) - S;
+ *   sigma = (mu_aff / mu)^3; corrector: R_c = G R G^T with Lam R + R Lam =
+ *   2 sigma mu I - 2 Lam^2 - (Dx Ds + Ds Dx), C~ = R_d - G^{-T} R G^{-1};
+ *   steps: a = min(1, 0.98 * max{a : X + a dX PSD}) by the smallest eigenvalue of the scaled
+ *   step, dS = R_d - A^T(dy).
+ * Every Newton direction is one sdp_newton_solve on the reformulation (eig(W) by sdp_eigh).
+ * b (m), C (n x n symmetric), X, S (n x n, positive definite), y (m): device pointers.
+ * The first call allocates the loop's workspace (about 24 n^2 doubles). */
+sdp_status ipm_step(sdp_handle* h, const double* b, const double* C, double* X, double* y, double* S,
+                    sdp_ipm_info* info);
+
+/* Whole solve from X = S = xi I, y = 0 (xi = max(10, sqrt n, max_i (1+|b_i|)/(1+||A_i||_F),
+ * (1+||C||_F)/sqrt n)) until rel_gap, pinf and dinf are <= gap_tol (SDP_OK) or max_iter
+ * iterations (SDP_ENOTCONV).  X, y, S: device outputs. */
+sdp_status sdp_solve(sdp_handle* h, const double* b, const double* C, double* X, double* y, double* S,
+                     double gap_tol, int32_t max_iter, sdp_ipm_info* info);
+
 /* Fill *opt with the defaults: r_fixed 0, r_hat 10, FP64, auto space,
  * max_pcg 2000, check_every 8, beta_rule 0, use_graph 1, newton_rtol 1e-12, max_refine 10,
- * max_inner 500, inner_rtol 1e-6. */
+ * max_inner 500, inner_rtol 1e-6, pcg_start 0. */
 void sdp_default_options(sdp_options* opt);
 
 /* Validate the problem, record its (device) pointers -- the caller keeps

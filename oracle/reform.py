@@ -318,8 +318,14 @@ class ReformInfo:
 def newton_reform(prob, V: np.ndarray, lam: np.ndarray, Ct: np.ndarray, bt: np.ndarray,
                   r: int | None = None, r_hat: int | None = None, s_A: float = 1.0,
                   rtol: float = 1e-12, maxit: int = 2000, space: str = "d",
-                  keep_iterates: bool = False):
-    """Solve (Newt-eps) through eq. augsys with the indefinite PCG of Cor. pcg."""
+                  keep_iterates: bool = False, start: str = "paper"):
+    """Solve (Newt-eps) through eq. augsys with the indefinite PCG of Cor. pcg.
+
+    start = "paper": x0 = [0; -Sigma^{-1} Q^T c] as Cor. pcg prints it.
+    start = "precond": x0 = P^{-1}[0; g_v], the preconditioner applied to the second block
+    of the right side.  Both make the second block of r0 zero, which is what Cor. pcg and
+    Prop. indefpcg need (P x0 = [0; g_v] and the operator shares P's second block row).
+    """
     sp = split(V, lam, r=r, r_hat=r_hat, s_A=s_A)
     P = precond_setup(prob, sp, space=space)
     m = prob.m
@@ -335,7 +341,12 @@ def newton_reform(prob, V: np.ndarray, lam: np.ndarray, Ct: np.ndarray, bt: np.n
         a, b_ = precond_apply(P, rr[:m], rr[m:])
         return np.concatenate([a, b_])
 
-    x0 = np.concatenate([np.zeros(m), v0])
+    if start == "paper":
+        x0 = np.concatenate([np.zeros(m), v0])
+    elif start == "precond":
+        x0 = Pinv(np.concatenate([np.zeros(m), gv]))
+    else:
+        raise ValueError(start)
     # Stop on ||r_k|| <= rtol ||[svec C~; b~]||: with the second-block residual at rounding
     # level, ||r_k|| is the (Newt-eps) residual of the recovered direction (Lemma smallres),
     # measured against the right side of (Newt-eps).

@@ -15,7 +15,7 @@ from . import _native as native
 from ._native import (SDP_A_DENSE_SVEC, SDP_A_DIAG, SDP_A_SPARSE_COO, SDP_ENOTCONV, SDP_FP64, SDP_MIXED_FP32,
                       SDP_OK, SdpError, sdp_default_options)
 
-__all__ = ["NewtonSolver", "SdpError", "native", "sdp_optimum", "SDP_A_DIAG", "SDP_A_SPARSE_COO",
+__all__ = ["NewtonSolver", "SdpError", "native", "sdp_optimum", "eigh", "SDP_A_DIAG", "SDP_A_SPARSE_COO",
            "SDP_A_DENSE_SVEC"]
 
 KINDS = {"diag": SDP_A_DIAG, "sparse": SDP_A_SPARSE_COO, "dense": SDP_A_DENSE_SVEC}
@@ -73,10 +73,13 @@ class NewtonSolver:
     def __init__(self, prob, r_fixed: int = 0, r_hat: int = 10, precond_space: int = 0,
                  max_pcg: int = 2000, check_every: int = 8, beta_rule: int = 0,
                  newton_rtol: float = 1e-12, device: str = "cuda", stream=None, use_graph: bool = True,
-                 precision: str = "fp64", max_refine: int = 10, max_inner: int = 500, inner_rtol: float = 1e-6):
+                 precision: str = "fp64", max_refine: int = 10, max_inner: int = 500, inner_rtol: float = 1e-6,
+                 pcg_start: int = 0):
         import torch
         self.torch = torch
         self.device = torch.device(device)
+        if self.device.type == "cuda" and self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         f64 = torch.float64
 
         def dev(a, dtype):
@@ -107,6 +110,7 @@ class NewtonSolver:
         o.use_graph = 1 if use_graph else 0
         o.precision = {"fp64": SDP_FP64, "mixed_fp32": SDP_MIXED_FP32}[precision]
         o.max_refine, o.max_inner, o.inner_rtol = max_refine, max_inner, inner_rtol
+        o.pcg_start = pcg_start
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         torch.cuda.synchronize(self.device)
         self.handle = native.sdp_setup(p, o, int(self.stream.cuda_stream))
@@ -184,6 +188,35 @@ class NewtonSolver:
         self.last_info = self._info(ci, st)
         return gC, gb
 
+    def ipm_step(self, b, C, X, y, S):
+        """One outer interior-point iteration in place on the device tensors X, y, S (ipm_step)."""
+        torch = self.torch
+        f64 = torch.float64
+        b, C = (t.to(device=self.device, dtype=f64).contiguous() for t in (b, C))
+        for t in (X, y, S):
+            if t.dtype != f64 or t.device != self.device or not t.is_contiguous():
+                raise ValueError("X, y, S must be contiguous float64 tensors on the solver's device")
+        ci = native.sdp_ipm_info()
+        native.ipm_step(self.handle, _ptr(b), _ptr(C), _ptr(X), _ptr(y), _ptr(S), ci)
+        return ci.as_dict()
+
+    def solve_sdp(self, b, C, gap_tol: float = 1e-8, max_iter: int = 100, allow_notconv: bool = False):
+        """Whole interior-point solve of min <C,X> s.t. A(X) = b, X PSD (sdp_solve); returns
+        (X, y, S, info)."""
+        torch = self.torch
+        f64 = torch.float64
+        n, m = self.n, self.m
+        b, C = (t.to(device=self.device, dtype=f64).contiguous() for t in (b, C))
+        X = torch.empty((n, n), dtype=f64, device=self.device)
+        S = torch.empty((n, n), dtype=f64, device=self.device)
+        y = torch.empty(m, dtype=f64, device=self.device)
+        ci = native.sdp_ipm_info()
+        st = native.sdp_solve(self.handle, _ptr(b), _ptr(C), _ptr(X), _ptr(y), _ptr(S), gap_tol, max_iter, ci,
+                              allow_notconv=allow_notconv)
+        info = ci.as_dict()
+        info["status"] = st
+        return X, y, S, info
+
     def close(self):
         if getattr(self, "handle", None):
             native.sdp_destroy(self.handle)
@@ -222,3 +255,20 @@ def sdp_optimum(C, b, X, y, V, lam, solver: NewtonSolver):
             return gC.to(C.dtype), gb.to(b.dtype), None, None, None, None
 
     return _SdpOptimum.apply(C, b, X.detach(), y.detach(), V.detach(), lam.detach())
+
+
+def eigh(A, tol: float = 1e-14, max_sweeps: int = 40):
+    """Symmetric eigen-decomposition of the device matrix A by the library's Jacobi solver
+    (sdp_eigh); returns (lam, V, sweeps) with A = V diag(lam) V^T, lam unsorted."""
+    import torch
+    n = A.shape[0]
+    A = A.to(dtype=torch.float64).t().contiguous().t().clone()
+    V = torch.empty_like(A)
+    lam = torch.empty(n, dtype=torch.float64, device=A.device)
+    work = torch.empty(native.sdp_eigh_work_elems(n), dtype=torch.float64, device=A.device)
+    stream = torch.cuda.current_stream(A.device)
+    st, sweeps = native.sdp_eigh(int(stream.cuda_stream), n, _ptr(A), _ptr(V), _ptr(lam), tol, max_sweeps,
+                                 _ptr(work), work.numel())
+    if st != SDP_OK:
+        raise SdpError(st, "Jacobi eigensolver did not converge")
+    return lam, V, sweeps

@@ -30,7 +30,7 @@ class sdp_options(Structure):
     _fields_ = [("r_fixed", c_int32), ("r_hat", c_int32), ("precision", c_int32), ("precond_space", c_int32),
                 ("max_pcg", c_int32), ("check_every", c_int32), ("beta_rule", c_int32), ("use_graph", c_int32),
                 ("newton_rtol", c_double), ("max_refine", c_int32), ("max_inner", c_int32),
-                ("inner_rtol", c_double)]
+                ("inner_rtol", c_double), ("pcg_start", c_int32)]
 
 
 class sdp_newton_info(Structure):
@@ -47,12 +47,27 @@ class sdp_newton_info(Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
 
 
+class sdp_ipm_info(ctypes.Structure):
+    _fields_ = [("iters", c_int32), ("converged", c_int32), ("pcg_iters", c_int32), ("eig_sweeps", c_int32),
+                ("newton_inexact", c_int32), ("pad_", c_int32), ("pobj", c_double), ("dobj", c_double), ("rel_gap", c_double), ("pinf", c_double),
+                ("dinf", c_double), ("mu", c_double), ("alpha_p", c_double), ("alpha_d", c_double),
+                ("sigma", c_double), ("newton_ms", c_double), ("total_ms", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
 EXPORTS = {
     "sdp_default_options": (None, [POINTER(sdp_options)]),
     "sdp_setup": (c_int32, [POINTER(sdp_problem), POINTER(sdp_options), c_void_p, POINTER(c_void_p)]),
     "sdp_newton_solve": (c_int32, [c_void_p] + [c_void_p] * 7 + [POINTER(sdp_newton_info)]),
     "sdp_newton_solve_host": (c_int32, [c_void_p] + [c_void_p] * 7 + [POINTER(sdp_newton_info)]),
     "sdp_grad": (c_int32, [c_void_p] + [c_void_p] * 6 + [POINTER(sdp_newton_info)]),
+    "sdp_eigh_work_elems": (c_int64, [c_int32]),
+    "sdp_eigh": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_double, c_int32, c_void_p, c_int64,
+                           POINTER(c_int32)]),
+    "ipm_step": (c_int32, [c_void_p] + [c_void_p] * 5 + [POINTER(sdp_ipm_info)]),
+    "sdp_solve": (c_int32, [c_void_p] + [c_void_p] * 5 + [c_double, c_int32, POINTER(sdp_ipm_info)]),
     "sdp_debug_copy": (c_int32, [c_void_p, c_int32, c_void_p, c_int64]),
     "sdp_set_profiling": (c_int32, [c_void_p, c_int32]),
     "sdp_adjoint_dense_noalloc": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
@@ -123,6 +138,41 @@ def sdp_newton_solve_host(h: int, V: int, lam: int, Ct: int, bt: int, dX: int, d
 def sdp_grad(h: int, V: int, lam: int, gX: int, gy: int, gC: int, gb: int, info: sdp_newton_info,
              allow_notconv: bool = False) -> int:
     return _solve("sdp_grad", h, (V, lam, gX, gy, gC, gb), info, allow_notconv)
+
+
+def sdp_eigh(stream: int, n: int, A: int, V: int, lam: int, tol: float, max_sweeps: int, work: int,
+             work_elems: int) -> tuple[int, int]:
+    """Jacobi eigen-decomposition on the device; returns (status, sweeps)."""
+    lib = load()
+    sw = c_int32(0)
+    st = lib.sdp_eigh(c_void_p(stream), n, c_void_p(A), c_void_p(V), c_void_p(lam), tol, max_sweeps,
+                      c_void_p(work), work_elems, ctypes.byref(sw))
+    if st not in (SDP_OK, SDP_ENOTCONV):
+        raise SdpError(st, lib.sdp_last_error(None).decode())
+    return st, sw.value
+
+
+def sdp_eigh_work_elems(n: int) -> int:
+    return int(load().sdp_eigh_work_elems(n))
+
+
+def ipm_step(h: int, b: int, C: int, X: int, y: int, S: int, info: sdp_ipm_info) -> int:
+    lib = load()
+    st = lib.ipm_step(c_void_p(h), c_void_p(b), c_void_p(C), c_void_p(X), c_void_p(y), c_void_p(S),
+                      ctypes.byref(info))
+    if st != SDP_OK:
+        raise SdpError(st, lib.sdp_last_error(c_void_p(h)).decode())
+    return st
+
+
+def sdp_solve(h: int, b: int, C: int, X: int, y: int, S: int, gap_tol: float, max_iter: int,
+              info: sdp_ipm_info, allow_notconv: bool = False) -> int:
+    lib = load()
+    st = lib.sdp_solve(c_void_p(h), c_void_p(b), c_void_p(C), c_void_p(X), c_void_p(y), c_void_p(S), gap_tol,
+                       max_iter, ctypes.byref(info))
+    if st != SDP_OK and not (allow_notconv and st == SDP_ENOTCONV):
+        raise SdpError(st, lib.sdp_last_error(c_void_p(h)).decode())
+    return st
 
 
 def sdp_debug_copy(h: int, which: int, dst: int, count: int) -> None:

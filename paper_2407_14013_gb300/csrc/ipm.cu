@@ -1,0 +1,569 @@
+// The outer primal-dual interior-point loop on the device: NT scaling, the Mehrotra
+// predictor-corrector around two Newton solves on the well-conditioned reformulation, step
+// lengths, and the stopping test.  The paper keeps an existing solver's outer loop unchanged
+// (Section 7) and specifies it only through the log-barrier path and eq. newt; this file is
+// the textbook method that the oracle also writes down (same definitions, same order):
+//
+//   measures   pobj = <C,X>, dobj = b^T y, rel_gap, pinf = ||b - A(X)||/(1+||b||),
+//              dinf = ||C - A^T y - S||_F/(1+||C||_F), mu = <X,S>/n
+//   NT scaling X = L L^T, L^T S L = U Gamma U^T, G = L U Gamma^{-1/4}, W = G G^T
+//              (= L (L^T S L)^{-1/2} L^T of eq. newt); Lam = G^{-1} X G^{-T} = Gamma^{1/2}
+//   predictor  (Newt-eps) with b~ = r_p, C~ = R_d + S  (R_c = -X);  dS = R_d - A^T(dy)
+//   sigma      = min(1, (mu_aff / mu)^3), mu_aff from full predictor steps
+//   corrector  Lam R + R Lam = 2 sigma mu I - 2 Lam^2 - (Dx Ds + Ds Dx), Dx = G^{-1} dX_a G^{-T},
+//              Ds = G^T dS_a G;  C~ = R_d - G^{-T} R G^{-1}  (= R_d - W^{-1} R_c W^{-1})
+//   steps      a = min(1, f * sup{a : Lam + a D PSD}) from the smallest eigenvalue of
+//              Lam^{-1/2} D Lam^{-1/2}  (f = 1 for the predictor, 0.98 for the step)
+//
+// Every Newton direction is one sdp_newton_solve (the hot path); eig(W) for its split, eig of
+// L^T S L and the smallest eigenvalues come from the Jacobi eigensolver (eigh.cu).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "handle.h"
+#include "kernels.h"
+#include "pcg.h"
+
+using namespace wc;
+
+namespace wc {
+
+struct IpmWork {
+  int n = 0, m = 0;
+  char* pool = nullptr;
+  double *L = nullptr, *Linv = nullptr, *T = nullptr, *U = nullptr, *G = nullptr, *Ginv = nullptr, *Wm = nullptr;
+  double *V = nullptr, *Rd = nullptr, *Ct = nullptr, *Y = nullptr, *dX = nullptr, *dS = nullptr, *dSs = nullptr;
+  double *dXa = nullptr, *dSa = nullptr, *Dx = nullptr, *Ds = nullptr, *R = nullptr, *M1 = nullptr, *M2 = nullptr;
+  double *Eg = nullptr, *EV = nullptr;
+  double *lam = nullptr, *gam = nullptr, *g = nullptr, *q = nullptr, *qi = nullptr, *elam = nullptr;
+  double *rp = nullptr, *dy = nullptr, *dya = nullptr, *Ax = nullptr, *rownrm = nullptr;
+  double *zsvec = nullptr, *partY = nullptr, *partA = nullptr;
+  double *eigw = nullptr, *chw = nullptr, *dots = nullptr, *dpart = nullptr;
+  size_t eigw_elems = 0, chw_elems = 0;
+  int32_t* status = nullptr;
+  double xi = 0.0;
+};
+
+}  // namespace wc
+
+namespace {
+
+constexpr int IT = 256;
+constexpr int kDotBlocks = 128;
+constexpr int kDots = 16;
+
+inline unsigned nb(int64_t total) { return (unsigned)((total + IT - 1) / IT); }
+
+#define CUI(call)                                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return wc_fail(h, SDP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+__global__ void scaled_identity_kernel(int n, double xi, double* __restrict__ X) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < (int64_t)n * n) X[q] = ((q % n) == (q / n)) ? xi : 0.0;
+}
+
+// out = a * A + b * B (+ c * Cm), elementwise over `count`
+__global__ void lincomb_kernel(int64_t count, double a, const double* __restrict__ A, double b,
+                               const double* __restrict__ B, double c, const double* __restrict__ Cm,
+                               double* __restrict__ out) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  double v = a * A[q] + b * B[q];
+  if (Cm) v += c * Cm[q];
+  out[q] = v;
+}
+
+// X += alpha sym(D) (n x n), keeping X exactly symmetric
+__global__ void sym_axpy_kernel(int n, double alpha, const double* __restrict__ D, double* __restrict__ X) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)n * n) return;
+  const int i = (int)(q % n), j = (int)(q / n);
+  if (i < j) return;
+  const double d = 0.5 * (D[q] + D[j + (int64_t)i * n]);
+  const double v = 0.5 * (X[q] + X[j + (int64_t)i * n]) + alpha * d;
+  X[q] = v;
+  X[j + (int64_t)i * n] = v;
+}
+
+__global__ void axpy_kernel(int count, double alpha, const double* __restrict__ x, double* __restrict__ y) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < count) y[q] += alpha * x[q];
+}
+
+// rp = b - sum_s part[s * m + i]  (A(X) from the slab partials), or b - X_ii (DIAG: part = X, nslab < 0)
+__global__ void rp_kernel(int m, int n, const double* __restrict__ b, const double* __restrict__ part, int nslab,
+                          double* __restrict__ Ax, double* __restrict__ rp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double v = 0.0;
+  if (nslab < 0) v = part[i + (int64_t)i * n];
+  else
+    for (int s = 0; s < nslab; ++s) v += part[(int64_t)s * m + i];
+  Ax[i] = v;
+  rp[i] = b[i] - v;
+}
+
+// gamma -> g = gamma^{1/2}, q = gamma^{-1/4}, qi = gamma^{1/4}
+__global__ void gamma_kernel(int n, const double* __restrict__ gam, double* __restrict__ g, double* __restrict__ q,
+                             double* __restrict__ qi, int32_t* __restrict__ status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = gam[i];
+  if (!(v > 0.0) || !isfinite(v)) {
+    *status = 5;
+    v = 1.0;
+  }
+  const double s = sqrt(v);
+  g[i] = s;
+  qi[i] = sqrt(s);
+  q[i] = 1.0 / sqrt(s);
+}
+
+// out[i, j] = dl[i] * M[i, j] * dr[j]  (dl, dr may be NULL)
+__global__ void scale_kernel(int n, const double* __restrict__ M, const double* __restrict__ dl,
+                             const double* __restrict__ dr, double* __restrict__ out) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)n * n) return;
+  const int i = (int)(q % n), j = (int)(q / n);
+  double v = M[q];
+  if (dl) v *= dl[i];
+  if (dr) v *= dr[j];
+  out[q] = v;
+}
+
+// R_ij = rhs_ij / (g_i + g_j), rhs = 2 sigma mu I - 2 diag(g)^2 - (P + P^T)
+__global__ void lyap_kernel(int n, double smu2, const double* __restrict__ g, const double* __restrict__ P,
+                            double* __restrict__ R) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)n * n) return;
+  const int i = (int)(q % n), j = (int)(q / n);
+  double rhs = -(P[q] + P[j + (int64_t)i * n]);
+  if (i == j) rhs += smu2 - 2.0 * g[i] * g[i];
+  R[q] = rhs / (g[i] + g[j]);
+}
+
+// sum of a[k] * b[k] (b NULL: sum of a[k]^2) into per-block partials
+__global__ void dot_partial_kernel(int64_t count, const double* __restrict__ a, const double* __restrict__ b,
+                                   double* __restrict__ part) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += (int64_t)gridDim.x * blockDim.x)
+    acc = fma(a[q], b ? b[q] : a[q], acc);
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void dot_final_kernel(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int q = threadIdx.x; q < nparts; q += blockDim.x) acc += part[q];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) *out = acc;
+}
+
+// squared norms of the svec rows (||A_i||_F^2), one warp per row
+__global__ void row_sumsq_kernel(const double* __restrict__ A, int m, int64_t N, double* __restrict__ out) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= m) return;
+  const double* row = A + (int64_t)w * N;
+  double acc = 0.0;
+  for (int64_t k = lane; k < N; k += 32) acc = fma(row[k], row[k], acc);
+  acc = warp_sum(acc);
+  if (lane == 0) out[w] = acc;
+}
+
+struct Ctx {
+  sdp_handle* h;
+  IpmWork* w;
+  int n, m;
+  cudaStream_t st;
+  int64_t* L;
+};
+
+cudaError_t gemm(Ctx& c, bool tA, bool tB, const double* A, const double* B, double* C, double alpha = 1.0,
+                 double beta = 0.0) {
+  const int n = c.n;
+  return gemm_f64(c.st, tA, tB, n, n, n, alpha, A, n, B, n, beta, C, n, c.h->s64.ws, c.h->s64.ws_elems, c.L);
+}
+
+void dot(Ctx& c, int64_t count, const double* a, const double* b, int slot) {
+  dot_partial_kernel<<<kDotBlocks, IT, 0, c.st>>>(count, a, b, c.w->dpart + slot * kDotBlocks);
+  dot_final_kernel<<<1, IT, 0, c.st>>>(c.w->dpart + slot * kDotBlocks, kDotBlocks, c.w->dots + slot);
+  *c.L += 2;
+}
+
+// Y = A^T(y) as a full matrix
+void adjoint(Ctx& c, const double* y, double* Y) {
+  sdp_handle* h = c.h;
+  if (h->kind == SDP_A_DENSE_SVEC) {
+    rows_gemvT<double>(c.st, h->a_dense, c.m, h->N, y, c.w->partY, h->GY, nullptr, c.L);
+    svec_unpack_sum<double>(c.st, c.n, c.w->partY, h->GY, 1.0, Y, nullptr, c.L);
+  } else {
+    launch_diag_matrix(c.st, c.n, y, Y, c.L);
+  }
+}
+
+// Ax = A(X) (X symmetric, lower triangle read) and rp = b - Ax
+void residual_p(Ctx& c, const double* b, const double* X) {
+  sdp_handle* h = c.h;
+  if (h->kind == SDP_A_DENSE_SVEC) {
+    svec_pack_plus<double>(c.st, c.n, 0, X, nullptr, nullptr, c.w->zsvec, nullptr, c.L);
+    rows_gemv<double>(c.st, h->a_dense, c.m, h->N, c.w->zsvec, c.w->partA, nullptr, c.L);
+    rp_kernel<<<nb(c.m), IT, 0, c.st>>>(c.m, c.n, b, c.w->partA, rows_gemv_slabs(c.m, h->N), c.w->Ax, c.w->rp);
+  } else {
+    rp_kernel<<<nb(c.m), IT, 0, c.st>>>(c.m, c.n, b, X, -1, c.w->Ax, c.w->rp);
+  }
+  ++*c.L;
+}
+
+// smallest eigenvalue of the symmetric M (copied; M is kept)
+sdp_status lam_min(Ctx& c, const double* M, double* out, int* sweeps) {
+  sdp_handle* h = c.h;
+  IpmWork* w = c.w;
+  const size_t nn = (size_t)c.n * c.n;
+  CUI(cudaMemcpyAsync(w->Eg, M, nn * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+  int sw = 0;
+  double off = 0.0;
+  CUI(eigh_jacobi(c.st, c.n, w->Eg, w->EV, w->elam, 1e-13, 40, w->eigw, w->eigw_elems, &sw, &off, c.L));
+  *sweeps += sw;
+  std::vector<double> lh(c.n);
+  CUI(cudaMemcpyAsync(lh.data(), w->elam, c.n * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+  CUI(cudaStreamSynchronize(c.st));
+  *out = *std::min_element(lh.begin(), lh.end());
+  return SDP_OK;
+}
+
+// sup{a : Lam + a D PSD} for D = Dx or Ds, through Lam^{-1/2} D Lam^{-1/2} (Lam^{-1/2} = diag(q))
+sdp_status max_step(Ctx& c, const double* D, double* a, int* sweeps) {
+  scale_kernel<<<nb((int64_t)c.n * c.n), IT, 0, c.st>>>(c.n, D, c.w->q, c.w->q, c.w->M2);
+  ++*c.L;
+  double lmin = 0.0;
+  sdp_status s = lam_min(c, c.w->M2, &lmin, sweeps);
+  if (s != SDP_OK) return s;
+  *a = (lmin >= 0.0) ? INFINITY : -1.0 / lmin;
+  return SDP_OK;
+}
+
+sdp_status newton(Ctx& c, const double* Ct, const double* bt, double* dX, double* dy, double* dSs, sdp_ipm_info* info) {
+  sdp_newton_info ni;
+  std::memset(&ni, 0, sizeof(ni));
+  sdp_status s = sdp_newton_solve(c.h, c.w->V, c.w->lam, Ct, bt, dX, dy, dSs, &ni);
+  info->pcg_iters += ni.pcg_iters;
+  info->newton_ms += ni.setup_ms + ni.pcg_ms + ni.recover_ms;
+  if (s == SDP_ENOTCONV) {   // an inexact direction: the outer loop proceeds with it
+    info->newton_inexact += 1;
+    return SDP_OK;
+  }
+  return s;
+}
+
+sdp_status ensure_workspace(sdp_handle* h) {
+  if (h->ipm) return SDP_OK;
+  IpmWork* w = new (std::nothrow) IpmWork();
+  if (!w) return wc_fail(h, SDP_ENOMEM, "host allocation failed");
+  const int n = h->n, m = h->m;
+  const size_t nn = (size_t)n * n;
+  w->n = n;
+  w->m = m;
+  w->eigw_elems = eigh_work_elems(n);
+  w->chw_elems = spd_inverse_work(n);
+  size_t off = 0;
+  auto take = [&](size_t count) {
+    off = (off + 31) & ~size_t(31);
+    size_t at = off;
+    off += count;
+    return at;
+  };
+  std::vector<std::pair<double**, size_t>> plan = {
+      {&w->L, nn}, {&w->Linv, nn}, {&w->T, nn}, {&w->U, nn}, {&w->G, nn}, {&w->Ginv, nn}, {&w->Wm, nn},
+      {&w->V, nn}, {&w->Rd, nn}, {&w->Ct, nn}, {&w->Y, nn}, {&w->dX, nn}, {&w->dS, nn}, {&w->dSs, nn},
+      {&w->dXa, nn}, {&w->dSa, nn}, {&w->Dx, nn}, {&w->Ds, nn}, {&w->R, nn}, {&w->M1, nn}, {&w->M2, nn},
+      {&w->Eg, nn}, {&w->EV, nn}, {&w->lam, (size_t)n}, {&w->gam, (size_t)n}, {&w->g, (size_t)n},
+      {&w->q, (size_t)n}, {&w->qi, (size_t)n}, {&w->elam, (size_t)n}, {&w->rp, (size_t)m}, {&w->dy, (size_t)m},
+      {&w->dya, (size_t)m}, {&w->Ax, (size_t)m}, {&w->rownrm, (size_t)m}, {&w->eigw, w->eigw_elems},
+      {&w->chw, w->chw_elems}, {&w->dots, (size_t)kDots}, {&w->dpart, (size_t)kDots * kDotBlocks}};
+  if (h->kind == SDP_A_DENSE_SVEC) {
+    plan.push_back({&w->zsvec, (size_t)h->N});
+    plan.push_back({&w->partY, (size_t)h->GY * h->N});
+    plan.push_back({&w->partA, rows_gemv_part_elems(m, h->N)});
+  }
+  std::vector<size_t> at;
+  for (auto& p : plan) at.push_back(take(p.second));
+  const size_t status_at = take(1);
+  const size_t total = off * sizeof(double) + 256;
+  cudaError_t e = cudaMalloc(&w->pool, total);
+  if (e != cudaSuccess) {
+    delete w;
+    return wc_fail(h, SDP_ENOMEM, std::string("cudaMalloc of the interior-point workspace failed: ") +
+                                      cudaGetErrorString(e));
+  }
+  double* base = reinterpret_cast<double*>(w->pool);
+  for (size_t k = 0; k < plan.size(); ++k) *plan[k].first = base + at[k];
+  w->status = reinterpret_cast<int32_t*>(base + status_at);
+  h->ipm = w;
+  return SDP_OK;
+}
+
+struct Measures {
+  double pobj, dobj, gap, pinf, dinf, mu, nb, nc;
+};
+
+// R_d = C - A^T(y) - S, r_p = b - A(X), and the measures (one host read)
+sdp_status residuals(Ctx& c, const double* b, const double* C, const double* X, const double* y, const double* S,
+                     Measures* M) {
+  sdp_handle* h = c.h;
+  IpmWork* w = c.w;
+  const int64_t nn = (int64_t)c.n * c.n;
+  adjoint(c, y, w->Y);
+  lincomb_kernel<<<nb(nn), IT, 0, c.st>>>(nn, 1.0, C, -1.0, w->Y, -1.0, S, w->Rd);
+  ++*c.L;
+  residual_p(c, b, X);
+  dot(c, nn, C, X, 0);
+  dot(c, c.m, b, y, 1);
+  dot(c, c.m, w->rp, nullptr, 2);
+  dot(c, nn, w->Rd, nullptr, 3);
+  dot(c, nn, X, S, 4);
+  dot(c, c.m, b, nullptr, 5);
+  dot(c, nn, C, nullptr, 6);
+  double d[7];
+  CUI(cudaMemcpyAsync(d, w->dots, 7 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+  CUI(cudaStreamSynchronize(c.st));
+  M->pobj = d[0];
+  M->dobj = d[1];
+  M->gap = std::fabs(d[0] - d[1]) / (1.0 + std::fabs(d[0]) + std::fabs(d[1]));
+  M->nb = std::sqrt(d[5]);
+  M->nc = std::sqrt(d[6]);
+  M->pinf = std::sqrt(d[2]) / (1.0 + M->nb);
+  M->dinf = std::sqrt(d[3]) / (1.0 + M->nc);
+  M->mu = d[4] / c.n;
+  return SDP_OK;
+}
+
+void fill_info(sdp_ipm_info* info, const Measures& M) {
+  info->pobj = M.pobj;
+  info->dobj = M.dobj;
+  info->rel_gap = M.gap;
+  info->pinf = M.pinf;
+  info->dinf = M.dinf;
+  info->mu = M.mu;
+}
+
+// one predictor-corrector step from (X, y, S) whose residuals w->Rd, w->rp and measures M
+// are current
+sdp_status step(Ctx& c, double* X, double* y, double* S, const Measures& Mz, sdp_ipm_info* info) {
+  sdp_handle* h = c.h;
+  IpmWork* w = c.w;
+  const int n = c.n;
+  const int64_t nn = (int64_t)n * n;
+  const size_t bytes = (size_t)nn * sizeof(double);
+  const double mu = Mz.mu;
+  int sweeps = 0;
+  double off = 0.0;
+  // ---- NT scaling: X = L L^T, L^T S L = U Gamma U^T, G = L U Gamma^{-1/4}, W = G G^T
+  CUI(cudaMemsetAsync(w->status, 0, sizeof(int32_t), c.st));
+  CUI(cudaMemcpyAsync(w->L, X, bytes, cudaMemcpyDeviceToDevice, c.st));
+  CUI(spd_cholesky(c.st, n, w->L, w->Linv, w->chw, w->chw_elems, h->s64.ws, h->s64.ws_elems, w->status, c.L));
+  CUI(gemm(c, false, false, S, w->L, w->M1));
+  CUI(gemm(c, true, false, w->L, w->M1, w->T));
+  int sw = 0;
+  CUI(eigh_jacobi(c.st, n, w->T, w->U, w->gam, 1e-14, 40, w->eigw, w->eigw_elems, &sw, &off, c.L));
+  sweeps += sw;
+  gamma_kernel<<<nb(n), IT, 0, c.st>>>(n, w->gam, w->g, w->q, w->qi, w->status);
+  ++*c.L;
+  CUI(gemm(c, false, false, w->L, w->U, w->M1));
+  scale_kernel<<<nb(nn), IT, 0, c.st>>>(n, w->M1, nullptr, w->q, w->G);          // G = L U Gamma^{-1/4}
+  CUI(gemm(c, true, false, w->U, w->Linv, w->M1));
+  scale_kernel<<<nb(nn), IT, 0, c.st>>>(n, w->M1, w->qi, nullptr, w->Ginv);      // G^{-1} = Gamma^{1/4} U^T L^{-1}
+  *c.L += 2;
+  CUI(gemm(c, false, true, w->G, w->G, w->Wm));                                  // W = G G^T
+  CUI(cudaMemcpyAsync(w->Eg, w->Wm, bytes, cudaMemcpyDeviceToDevice, c.st));
+  CUI(eigh_jacobi(c.st, n, w->Eg, w->V, w->lam, 1e-14, 40, w->eigw, w->eigw_elems, &sw, &off, c.L));
+  sweeps += sw;
+  int32_t st_h = 0;
+  CUI(cudaMemcpyAsync(&st_h, w->status, sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
+  CUI(cudaStreamSynchronize(c.st));
+  if (st_h != 0) return wc_fail(h, SDP_ENUMERIC, "X is not positive definite or L^T S L is singular");
+
+  // ---- predictor: C~ = R_d + S, b~ = r_p
+  lincomb_kernel<<<nb(nn), IT, 0, c.st>>>(nn, 1.0, w->Rd, 1.0, S, 0.0, nullptr, w->Ct);
+  ++*c.L;
+  sdp_status s = newton(c, w->Ct, w->rp, w->dXa, w->dya, w->dSs, info);
+  if (s != SDP_OK) return s;
+  lincomb_kernel<<<nb(nn), IT, 0, c.st>>>(nn, 1.0, w->dSs, -1.0, S, 0.0, nullptr, w->dSa);   // R_d - A^T dy
+  ++*c.L;
+  CUI(gemm(c, false, false, w->Ginv, w->dXa, w->M1));
+  CUI(gemm(c, false, true, w->M1, w->Ginv, w->Dx));                              // Dx = G^{-1} dX G^{-T}
+  CUI(gemm(c, true, false, w->G, w->dSa, w->M1));
+  CUI(gemm(c, false, false, w->M1, w->G, w->Ds));                                // Ds = G^T dS G
+  double ap = 0.0, ad = 0.0;
+  s = max_step(c, w->Dx, &ap, &sweeps);
+  if (s != SDP_OK) return s;
+  s = max_step(c, w->Ds, &ad, &sweeps);
+  if (s != SDP_OK) return s;
+  ap = std::min(1.0, ap);
+  ad = std::min(1.0, ad);
+  // mu_aff = <X + ap dX, S + ad dS> / n
+  dot(c, nn, X, w->dSa, 7);
+  dot(c, nn, w->dXa, S, 8);
+  dot(c, nn, w->dXa, w->dSa, 9);
+  double d3[3];
+  CUI(cudaMemcpyAsync(d3, w->dots + 7, 3 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+  CUI(cudaStreamSynchronize(c.st));
+  const double mu_aff = (mu * n + ad * d3[0] + ap * d3[1] + ap * ad * d3[2]) / n;
+  const double sigma = std::min(1.0, std::pow(mu_aff / mu, 3.0));
+
+  // ---- corrector: Lam R + R Lam = 2 sigma mu I - 2 Lam^2 - (Dx Ds + Ds Dx)
+  CUI(gemm(c, false, false, w->Dx, w->Ds, w->M1));
+  lyap_kernel<<<nb(nn), IT, 0, c.st>>>(n, 2.0 * sigma * mu, w->g, w->M1, w->R);
+  ++*c.L;
+  CUI(gemm(c, false, false, w->R, w->Ginv, w->M1));
+  CUI(gemm(c, true, false, w->Ginv, w->M1, w->M2));                             // G^{-T} R G^{-1}
+  lincomb_kernel<<<nb(nn), IT, 0, c.st>>>(nn, 1.0, w->Rd, -1.0, w->M2, 0.0, nullptr, w->Ct);
+  ++*c.L;
+  CUI(cudaMemcpyAsync(w->T, w->M2, bytes, cudaMemcpyDeviceToDevice, c.st));    // keep G^{-T} R G^{-1}
+  s = newton(c, w->Ct, w->rp, w->dX, w->dy, w->dSs, info);
+  if (s != SDP_OK) return s;
+  lincomb_kernel<<<nb(nn), IT, 0, c.st>>>(nn, 1.0, w->dSs, 1.0, w->T, 0.0, nullptr, w->dS);  // R_d - A^T dy
+  ++*c.L;
+  CUI(gemm(c, false, false, w->Ginv, w->dX, w->M1));
+  CUI(gemm(c, false, true, w->M1, w->Ginv, w->Dx));
+  CUI(gemm(c, true, false, w->G, w->dS, w->M1));
+  CUI(gemm(c, false, false, w->M1, w->G, w->Ds));
+  s = max_step(c, w->Dx, &ap, &sweeps);
+  if (s != SDP_OK) return s;
+  s = max_step(c, w->Ds, &ad, &sweeps);
+  if (s != SDP_OK) return s;
+  ap = std::min(1.0, 0.98 * ap);
+  ad = std::min(1.0, 0.98 * ad);
+  sym_axpy_kernel<<<nb(nn), IT, 0, c.st>>>(n, ap, w->dX, X);
+  sym_axpy_kernel<<<nb(nn), IT, 0, c.st>>>(n, ad, w->dS, S);
+  axpy_kernel<<<nb(c.m), IT, 0, c.st>>>(c.m, ad, w->dy, y);
+  *c.L += 3;
+  CUI(cudaGetLastError());
+  info->alpha_p = ap;
+  info->alpha_d = ad;
+  info->sigma = sigma;
+  info->eig_sweeps += sweeps;
+  return SDP_OK;
+}
+
+sdp_status check_args(sdp_handle* h, const double* b, const double* C, double* X, double* y, double* S) {
+  if (!h) return wc_fail(nullptr, SDP_EINVAL, "NULL handle");
+  if (!b || !C || !X || !y || !S) return wc_fail(h, SDP_EINVAL, "NULL array argument");
+  if (h->kind != SDP_A_DENSE_SVEC && h->kind != SDP_A_DIAG)
+    return wc_fail(h, SDP_EUNSUPPORTED, "constraint kind not built");
+  return ensure_workspace(h);
+}
+
+}  // namespace
+
+void wc_ipm_free(sdp_handle* h) {
+  if (!h || !h->ipm) return;
+  if (h->ipm->pool) cudaFree(h->ipm->pool);
+  delete h->ipm;
+  h->ipm = nullptr;
+}
+
+extern "C" int64_t sdp_eigh_work_elems(int32_t n) { return n < 1 ? 0 : (int64_t)eigh_work_elems(n); }
+
+extern "C" sdp_status sdp_eigh(void* stream, int32_t n, double* A, double* V, double* lam, double tol,
+                               int32_t max_sweeps, double* work, int64_t work_elems, int32_t* sweeps) {
+  sdp_handle* h = nullptr;
+  if (n < 1 || !A || !V || !lam || !work) return wc_fail(nullptr, SDP_EINVAL, "bad eigh argument");
+  if (work_elems < (int64_t)eigh_work_elems(n)) return wc_fail(nullptr, SDP_EINVAL, "eigh workspace too small");
+  if (!(tol > 0.0) || max_sweeps < 1) return wc_fail(nullptr, SDP_EINVAL, "bad eigh tolerance or sweep cap");
+  int sw = 0;
+  double off = 0.0;
+  cudaError_t e = eigh_jacobi(static_cast<cudaStream_t>(stream), n, A, V, lam, tol, max_sweeps, work,
+                              (size_t)work_elems, &sw, &off, nullptr);
+  if (e != cudaSuccess) return wc_fail(h, SDP_ECUDA, std::string("eigh: ") + cudaGetErrorString(e));
+  if (sweeps) *sweeps = sw;
+  return (off <= tol) ? SDP_OK : SDP_ENOTCONV;
+}
+
+extern "C" sdp_status ipm_step(sdp_handle* h, const double* b, const double* C, double* X, double* y, double* S,
+                               sdp_ipm_info* info) {
+  sdp_status s = check_args(h, b, C, X, y, S);
+  if (s != SDP_OK) return s;
+  const auto t0 = std::chrono::steady_clock::now();
+  int64_t L = 0;
+  Ctx c{h, h->ipm, h->n, h->m, h->st, &L};
+  sdp_ipm_info loc;
+  std::memset(&loc, 0, sizeof(loc));
+  Measures M;
+  s = residuals(c, b, C, X, y, S, &M);
+  if (s != SDP_OK) return s;
+  fill_info(&loc, M);
+  s = step(c, X, y, S, M, &loc);
+  loc.iters = 1;
+  loc.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = loc;
+  return s;
+}
+
+extern "C" sdp_status sdp_solve(sdp_handle* h, const double* b, const double* C, double* X, double* y, double* S,
+                                double gap_tol, int32_t max_iter, sdp_ipm_info* info) {
+  sdp_status s = check_args(h, b, C, X, y, S);
+  if (s != SDP_OK) return s;
+  if (!(gap_tol > 0.0) || max_iter < 0) return wc_fail(h, SDP_EINVAL, "bad gap_tol or max_iter");
+  const auto t0 = std::chrono::steady_clock::now();
+  int64_t L = 0;
+  IpmWork* w = h->ipm;
+  Ctx c{h, w, h->n, h->m, h->st, &L};
+  const int n = h->n, m = h->m;
+  // ---- start X = S = xi I, y = 0
+  std::vector<double> bh(m), rn(m, 1.0);
+  CUI(cudaMemcpyAsync(bh.data(), b, m * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  if (h->kind == SDP_A_DENSE_SVEC) {
+    row_sumsq_kernel<<<(unsigned)((m * 32 + IT - 1) / IT), IT, 0, h->st>>>(h->a_dense, m, h->N, w->rownrm);
+    CUI(cudaMemcpyAsync(rn.data(), w->rownrm, m * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  }
+  dot(c, (int64_t)n * n, C, nullptr, 6);
+  double cc = 0.0;
+  CUI(cudaMemcpyAsync(&cc, w->dots + 6, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CUI(cudaStreamSynchronize(h->st));
+  double xi = std::max(10.0, std::sqrt((double)n));
+  for (int i = 0; i < m; ++i) {
+    const double an = (h->kind == SDP_A_DENSE_SVEC) ? std::sqrt(rn[i]) : 1.0;
+    xi = std::max(xi, (1.0 + std::fabs(bh[i])) / (1.0 + an));
+  }
+  xi = std::max(xi, (1.0 + std::sqrt(cc)) / std::sqrt((double)n));
+  w->xi = xi;
+  scaled_identity_kernel<<<nb((int64_t)n * n), IT, 0, h->st>>>(n, xi, X);
+  scaled_identity_kernel<<<nb((int64_t)n * n), IT, 0, h->st>>>(n, xi, S);
+  CUI(cudaMemsetAsync(y, 0, m * sizeof(double), h->st));
+  sdp_ipm_info loc;
+  std::memset(&loc, 0, sizeof(loc));
+  Measures M;
+  int it = 0;
+  for (;; ++it) {
+    s = residuals(c, b, C, X, y, S, &M);
+    if (s != SDP_OK) return s;
+    fill_info(&loc, M);
+    if (M.gap <= gap_tol && M.pinf <= gap_tol && M.dinf <= gap_tol) {
+      loc.converged = 1;
+      break;
+    }
+    if (it >= max_iter) break;
+    s = step(c, X, y, S, M, &loc);
+    if (s != SDP_OK) {
+      loc.iters = it;
+      if (info) *info = loc;
+      return s;
+    }
+  }
+  loc.iters = it;
+  loc.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = loc;
+  return loc.converged ? SDP_OK : SDP_ENOTCONV;
+}

@@ -105,5 +105,15 @@ void convert(cudaStream_t st, int64_t count, const From* src, To* dst, int64_t* 
 size_t spd_inverse_work(int n);
 cudaError_t spd_inverse(cudaStream_t st, int n, double* A, double* work, size_t work_elems,
                         double* gemm_ws, size_t gemm_ws_elems, int32_t* status, int64_t* launches);
+// Cholesky A = L L^T (L into A, upper zeroed) and Linv = L^{-1}; same workspace.
+cudaError_t spd_cholesky(cudaStream_t st, int n, double* A, double* Linv, double* work, size_t work_elems,
+                         double* gemm_ws, size_t gemm_ws_elems, int32_t* status, int64_t* launches);
+
+// ---- eigh.cu: symmetric eigen-decomposition (parallel cyclic Jacobi, FP64) ------------------
+// A (n x n, symmetric, destroyed) = V diag(lam) V^T; stops when ||offdiag A||_F <= tol ||A||_F
+// or after max_sweeps sweeps (sweeps and the final relative off-diagonal norm are returned).
+size_t eigh_work_elems(int n);
+cudaError_t eigh_jacobi(cudaStream_t st, int n, double* A, double* V, double* lam, double tol, int max_sweeps,
+                        double* work, size_t work_elems, int* sweeps_out, double* off_out, int64_t* launches);
 
 }  // namespace wc

@@ -33,96 +33,7 @@
 
 using namespace wc;
 
-namespace {
-
-// The FP64 buffers of one PCG solve.  The inner solve of the mixed form shares everything
-// with the outer one except its vectors and its control block.
-struct Space {
-  double *Vs = nullptr, *E = nullptr, *EE = nullptr, *Dv = nullptr, *B = nullptr, *Bt = nullptr, *Pinv = nullptr;
-  double *Y = nullptr, *F = nullptr, *Z = nullptr, *Tm = nullptr, *H = nullptr, *Hp = nullptr, *Up = nullptr;
-  double *zsvec = nullptr, *partY = nullptr, *partA = nullptr, *sd = nullptr, *wm = nullptr;
-  double *partB = nullptr, *partBt = nullptr, *partC = nullptr;
-  double *x = nullptr, *rv = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr;
-  double* ws = nullptr;                        // split-K GEMM scratch
-  size_t ws_elems = 0;
-  PcgCtl* ctl = nullptr;
-};
-
-// FP32 data of the mixed form's A E A^T block, plus its FP64 partial sums of B p_v, B^T p_u.
-struct Mixed32 {
-  float* A = nullptr;                          // FP32 copy of the svec rows (DENSE kind)
-  float *E = nullptr, *EE = nullptr, *Y = nullptr, *F = nullptr, *Z = nullptr;
-  float *zsvec = nullptr, *partY = nullptr, *partA = nullptr, *pu = nullptr;
-  float* ws = nullptr;
-  size_t ws_elems = 0;
-  double *partBv = nullptr, *partBu = nullptr;
-};
-
-struct ProfEntry {
-  int kind;   // 0: A^T pass FP64, 1: A pass FP64, 2: A^T pass FP32, 3: A pass FP32
-  int iter;   // chunk-local PCG iteration, or -1 outside the loop
-};
-
-struct Graph {
-  cudaGraphExec_t exec = nullptr;
-  int key[4] = {-1, -1, -1, -1};
-  int64_t launches = 0;
-  size_t prof_first = 0, prof_last = 0;
-  std::vector<ProfEntry> entries;
-};
-
-}  // namespace
-
-struct sdp_handle {
-  // problem (device pointers owned by the caller)
-  int n = 0, m = 0, kind = 0;
-  int64_t nnz = 0, N = 0;
-  const int32_t *a_con = nullptr, *a_row = nullptr, *a_col = nullptr;
-  const double *a_val = nullptr, *a_dense = nullptr;
-  sdp_options opt{};
-  bool mixed = false;
-  cudaStream_t st = nullptr;
-  int r_max = 0, d_max = 0, mb = 0, mb2 = 0;
-  double s_A = 1.0;
-  // workspace
-  char* pool = nullptr;
-  size_t pool_bytes = 0;
-  PcgCtl* ctl = nullptr;            // FP64 solve / outer refinement
-  PcgCtl* ctl_in = nullptr;         // inner solve of the mixed form
-  PcgCtl* ctl_host = nullptr;       // pinned mirror
-  unsigned int* counter = nullptr;
-  double *lam_s = nullptr, *e = nullptr, *Ve = nullptr, *Bs = nullptr, *Cw = nullptr, *g = nullptr;
-  double *dotbuf = nullptr, *scratch = nullptr;
-  double* gj_work = nullptr;
-  size_t gj_work_elems = 0;
-  double *ubatch = nullptr, *Gb = nullptr, *Hb = nullptr;
-  int pinv_dim = 0;                 // order of the largest preconditioner core the options allow
-  Space s64;                        // FP64 solve, outer refinement of the mixed form
-  Space sin;                        // inner solve of the mixed form (own vectors and control block)
-  Mixed32 m32;
-  // device staging for the host-pointer entry point
-  double *hV = nullptr, *hlam = nullptr, *hCt = nullptr, *hbt = nullptr, *hdX = nullptr, *hdy = nullptr, *hdS = nullptr;
-  int GY = 1, SA = 1;       // row groups of the FP64 A^T products, column slabs of the FP64 A products
-  int GY32 = 1, SA32 = 1;   // the same for the FP32 copy of A (mixed form)
-  int64_t launches = 0;
-  int space = 1, r = 0, d = 0;
-  int refine_steps = 0, inner_iters = 0;
-  std::string err;
-  // optional CUDA-event timing of the constraint-operator passes (sdp_set_profiling)
-  bool prof = false;
-  bool capturing = false;           // inside stream capture: event records become graph nodes
-  int cur_iter = -1;
-  std::vector<cudaEvent_t> ev;
-  std::vector<ProfEntry> prof_entries;
-  size_t prof_base = 0;             // first entry not yet collected
-  cudaEvent_t ev_phase[4] = {nullptr, nullptr, nullptr, nullptr};
-  double prof_ms[4] = {0, 0, 0, 0};
-  int64_t prof_n[4] = {0, 0, 0, 0};
-  double phase_ms[3] = {0.0, 0.0, 0.0};
-  // CUDA graphs of `check_every` PCG iterations (FP64 operator, mixed operator), captured once per shape
-  cudaStream_t cap_stream = nullptr;
-  Graph graph[2];
-};
+#include "handle.h"
 
 static std::string g_setup_err;
 
@@ -130,6 +41,8 @@ static sdp_status fail(sdp_handle* h, sdp_status s, const std::string& msg) {
   if (h) h->err = msg; else g_setup_err = msg;
   return s;
 }
+
+sdp_status wc_fail(sdp_handle* h, sdp_status s, const std::string& msg) { return fail(h, s, msg); }
 
 #define CU(call)                                                                           \
   do {                                                                                     \
@@ -153,6 +66,7 @@ extern "C" void sdp_default_options(sdp_options* o) {
   o->max_refine = 10;
   o->max_inner = 500;
   o->inner_rtol = 1e-6;
+  o->pcg_start = 0;
 }
 
 namespace {
@@ -303,6 +217,7 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   const int r_max = opt.r_fixed > 0 ? opt.r_fixed : std::min(opt.r_hat, n - 1);
   if (r_max < 1 || r_max >= n) return fail(nullptr, SDP_EINVAL, "rank parameter out of range [1, n)");
   if (opt.precond_space < 0 || opt.precond_space > 2) return fail(nullptr, SDP_EINVAL, "bad precond_space");
+  if (opt.pcg_start < 0 || opt.pcg_start > 1) return fail(nullptr, SDP_EINVAL, "bad pcg_start");
 
   h = new (std::nothrow) sdp_handle();
   if (!h) return fail(nullptr, SDP_ENOMEM, "host allocation failed");
@@ -734,6 +649,10 @@ extern "C" sdp_status sdp_newton_solve(sdp_handle* h, const double* V, const dou
 
   if (!h->mixed) {
     // ---- a4-a6: FP64 PCG from x0 ----
+    if (h->opt.pcg_start == 0) {   // x0 = P^{-1}[0; g_v]: P x0 = [0; g_v], so r0_v = 0 with r0_u ~ g
+      launch_correction_rhs(st, m, d, h->g, S.z, L);
+      apply_precond(h, S, S.z, S.x, 0);
+    }
     sdp_status s = pcg_start(h, S, false, h->g, 0.0);
     if (s != SDP_OK) return s;
     s = pcg_loop(h, S, false);
@@ -919,5 +838,6 @@ extern "C" void sdp_destroy(sdp_handle* h) {
   for (auto& G : h->graph)
     if (G.exec) cudaGraphExecDestroy(G.exec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  wc_ipm_free(h);
   delete h;
 }

@@ -131,14 +131,12 @@ inline unsigned nblk(int64_t total, int t) { return (unsigned)((total + t - 1) /
 
 size_t spd_inverse_work(int n) { return (size_t)n * n + 2 * (size_t)n * NB + (size_t)((n + NB - 1) / NB) * NB * NB; }
 
-// A (n x n, ld n) is overwritten with its inverse.  work must hold spd_inverse_work(n) doubles.
-cudaError_t spd_inverse(cudaStream_t st, int n, double* A, double* work, size_t work_elems,
-                        double* gemm_ws, size_t gemm_ws_elems, int32_t* status, int64_t* launches) {
-  if (spd_inverse_work(n) > work_elems) return cudaErrorInvalidValue;
-  double* X = work;                                   // n x n, becomes L^{-1}
-  double* T = X + (size_t)n * n;                      // n x NB panel
-  double* U = T + (size_t)n * NB;                     // NB x n temporary
-  double* Li = U + (size_t)n * NB;                    // inverses of the diagonal blocks
+namespace {
+
+// Blocked Cholesky A = L L^T (L into the lower triangle of A, upper zeroed) and X = L^{-1}
+// (lower triangular, n x n, ld n).
+cudaError_t cholesky_and_inverse(cudaStream_t st, int n, double* A, double* X, double* T, double* U, double* Li,
+                                 double* gemm_ws, size_t gemm_ws_elems, int32_t* status, int64_t* launches) {
   cudaError_t e;
   // ---- blocked right-looking Cholesky, L in the lower triangle of A
   for (int k0 = 0, b = 0; k0 < n; k0 += NB, ++b) {
@@ -177,6 +175,21 @@ cudaError_t spd_inverse(cudaStream_t st, int n, double* A, double* work, size_t 
     copy_block_kernel<<<nblk((int64_t)w * w, 256), 256, 0, st>>>(w, w, Lib, w, X + i0 + (int64_t)i0 * n, n);
     if (launches) ++*launches;
   }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// A (n x n, ld n) is overwritten with its inverse.  work must hold spd_inverse_work(n) doubles.
+cudaError_t spd_inverse(cudaStream_t st, int n, double* A, double* work, size_t work_elems,
+                        double* gemm_ws, size_t gemm_ws_elems, int32_t* status, int64_t* launches) {
+  if (spd_inverse_work(n) > work_elems) return cudaErrorInvalidValue;
+  double* X = work;                                   // n x n, becomes L^{-1}
+  double* T = X + (size_t)n * n;                      // n x NB panel
+  double* U = T + (size_t)n * NB;                     // NB x n temporary
+  double* Li = U + (size_t)n * NB;                    // inverses of the diagonal blocks
+  cudaError_t e = cholesky_and_inverse(st, n, A, X, T, U, Li, gemm_ws, gemm_ws_elems, status, launches);
+  if (e != cudaSuccess) return e;
   // ---- A^{-1} = X^T X
   // lower triangle of X^T X, skipping the zero upper part of X
   e = gemm_f64(st, true, false, n, n, n, 1.0, X, n, X, n, 0.0, A, n, gemm_ws, gemm_ws_elems, launches, nullptr,
@@ -185,6 +198,16 @@ cudaError_t spd_inverse(cudaStream_t st, int n, double* A, double* work, size_t 
   lower_to_full_kernel<<<nblk((int64_t)n * n, 256), 256, 0, st>>>(n, A);
   if (launches) ++*launches;
   return cudaGetLastError();
+}
+
+// A = L L^T: L into A (lower, upper zeroed), L^{-1} into Linv (n x n).  work as for spd_inverse.
+cudaError_t spd_cholesky(cudaStream_t st, int n, double* A, double* Linv, double* work, size_t work_elems,
+                         double* gemm_ws, size_t gemm_ws_elems, int32_t* status, int64_t* launches) {
+  if (spd_inverse_work(n) > work_elems) return cudaErrorInvalidValue;
+  double* T = work + (size_t)n * n;
+  double* U = T + (size_t)n * NB;
+  double* Li = U + (size_t)n * NB;
+  return cholesky_and_inverse(st, n, A, Linv, T, U, Li, gemm_ws, gemm_ws_elems, status, launches);
 }
 
 }  // namespace wc

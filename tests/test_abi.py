@@ -54,6 +54,7 @@ int main(void) {
   printf("%zu %zu %zu\n", sizeof(sdp_newton_info), offsetof(sdp_newton_info, s_A),
          offsetof(sdp_newton_info, prof_A32_launches));
   printf("%zu\n", offsetof(sdp_options, inner_rtol));
+  printf("%zu %zu %zu\n", offsetof(sdp_options, pcg_start), sizeof(sdp_ipm_info), offsetof(sdp_ipm_info, total_ms));
   return 0;
 }
 '''
@@ -72,6 +73,9 @@ int main(void) {
     assert vals[5] == _native.sdp_newton_info.s_A.offset
     assert vals[6] == _native.sdp_newton_info.prof_A32_launches.offset
     assert vals[7] == _native.sdp_options.inner_rtol.offset
+    assert vals[8] == _native.sdp_options.pcg_start.offset
+    assert vals[9] == ctypes.sizeof(_native.sdp_ipm_info)
+    assert vals[10] == _native.sdp_ipm_info.total_ms.offset
 
 
 def test_default_options_and_setup_errors(lib):

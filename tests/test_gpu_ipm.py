@@ -1,0 +1,105 @@
+"""GPU outer loop: the Jacobi eigensolver (sdp_eigh), one interior-point step (ipm_step) in
+lockstep with the oracle's step, and whole solves (sdp_solve) against the oracle's optimum.
+
+Lockstep (one step from the oracle's own iterate) is compared at the early iterates, where
+the oracle's Schur-complement directions are accurate to ~cond(W)^2 eps; whole solves are
+compared on the objective (relative 1e-8 with both at gap <= 1e-8) and on X (relative 1e-6:
+X is determined to O(mu) near the end of the path).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import ipm as oipm, operators as oops
+
+pytestmark = pytest.mark.gpu
+
+
+def _t(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("n,kind", [(1, "rand"), (2, "rand"), (7, "rand"), (64, "rand"), (201, "rand"),
+                                    (60, "graded"), (40, "clustered")])
+def test_eigh_matches_lapack(n, kind):
+    from paper_2407_14013_gb300 import eigh
+    rng = np.random.default_rng(n)
+    if kind == "rand":
+        M = rng.standard_normal((n, n))
+        A = M + M.T
+    else:
+        Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        if kind == "graded":
+            w = np.logspace(-10, 3, n)
+        else:
+            w = np.concatenate([np.full(n // 2, 1.0), np.full(n - n // 2, 1.0 + 1e-9)])
+        A = (Q * w) @ Q.T
+        A = 0.5 * (A + A.T)
+    lam, V, sweeps = eigh(_t(A))
+    lam, V = lam.cpu().numpy(), V.cpu().numpy()
+    ref = np.linalg.eigvalsh(A)
+    nrm = np.linalg.norm(A, 2)
+    assert np.max(np.abs(np.sort(lam) - ref)) <= 1e-13 * nrm * max(1, n) ** 0.5
+    assert np.max(np.abs(V.T @ V - np.eye(n))) <= 1e-13 * n
+    assert np.linalg.norm((V * lam) @ V.T - A) <= 1e-13 * nrm * n
+    assert sweeps <= 20
+
+
+LOCK = [
+    ("maxcut20", lambda: W.maxcut(20, 0.3, 4101), 6),
+    ("sensing12", lambda: W.sensing(12, 40, 2, 4102), 4),
+]
+
+
+@pytest.mark.parametrize("name,mk,rh", LOCK, ids=[c[0] for c in LOCK])
+def test_ipm_step_lockstep_with_oracle(name, mk, rh):
+    from paper_2407_14013_gb300 import NewtonSolver
+    prob = mk()
+    res = oipm.ipm_solve(prob, max_iter=6, keep_history=True)
+    s = NewtonSolver(prob, r_hat=rh)
+    for k in (1, 3):
+        h0, h1 = res.history[k], res.history[k + 1]
+        X, y, S = _t(h0["X"]), _t(h0["y"]), _t(h0["S"])
+        info = s.ipm_step(_t(prob.b), _t(prob.C), X, y, S)
+        assert rel(X.cpu().numpy(), h1["X"]) < 1e-8, (k, info)
+        assert rel(y.cpu().numpy(), h1["y"]) < 1e-8
+        assert rel(S.cpu().numpy(), h1["S"]) < 1e-8
+        assert abs(info["mu"] - h0["mu"]) <= 1e-12 * h0["mu"]
+    s.close()
+
+
+SOLVE = [
+    ("maxcut64", lambda: W.workload("maxcut64"), 12),
+    ("sensing20", lambda: W.sensing(20, 120, 2, 77), 4),
+    ("maxcut_bipartite", lambda: W.maxcut(7, 0.0, 5, edges=[(i, 3 + j) for i in range(3) for j in range(4)]), 4),
+]
+
+
+@pytest.mark.parametrize("name,mk,rh", SOLVE, ids=[c[0] for c in SOLVE])
+def test_sdp_solve_matches_oracle(name, mk, rh):
+    from paper_2407_14013_gb300 import NewtonSolver
+    prob = mk()
+    ref = oipm.ipm_solve(prob, tol=1e-8, max_iter=100)
+    assert ref.converged
+    s = NewtonSolver(prob, r_hat=rh)
+    X, y, S, info = s.solve_sdp(_t(prob.b), _t(prob.C), gap_tol=1e-8, max_iter=100)
+    assert info["converged"] == 1, info
+    X, y, S = X.cpu().numpy(), y.cpu().numpy(), S.cpu().numpy()
+    pobj, pobj_ref = float(np.sum(prob.C * X)), float(np.sum(prob.C * ref.X))
+    # each side is at rel_gap <= 1e-8 with infeasibilities <= 1e-8, so each objective is within
+    # about 1e-8 (1 + 2|p*|) of the optimal value
+    assert abs(pobj - pobj_ref) <= 2e-8 * (1 + 2 * abs(pobj_ref))
+    assert rel(X, ref.X) < 1e-6
+    # invariants at the GPU optimum
+    assert np.linalg.norm(oops.A_op(prob, X) - prob.b) <= 1e-8 * (1 + np.linalg.norm(prob.b))
+    assert np.linalg.norm(prob.C - oops.At_op(prob, y) - S) <= 1e-8 * (1 + np.linalg.norm(prob.C))
+    assert np.linalg.eigvalsh(X)[0] > -1e-9 and np.linalg.eigvalsh(S)[0] > -1e-9
+    if name == "maxcut_bipartite":
+        m_edges = len(prob.meta["edges"])
+        assert abs(pobj + m_edges) <= 1e-7 * m_edges        # value -|E| (connected bipartite, unit weights)
+    s.close()
