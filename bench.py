@@ -281,6 +281,31 @@ def run_ours(args):
                  "gpu_launches": mres["launches"]}
         msolver.close()
 
+    # time to a 1e-8 relative gap: whole interior-point solves on the device (sdp_solve), the
+    # plain FP64 form against the mixed form, on the same instance (not part of the timed steps)
+    ttg = None
+    if not args.no_ttg:
+        ttg = {}
+        b_d = torch.from_numpy(prob.b).to(dev)
+        C_d = torch.from_numpy(prob.C).to(dev)
+        U = prob.meta["U"]
+        Xs = U @ U.T
+        for prec in ("fp64", "mixed_fp32"):
+            ts = NewtonSolver(prob, r_hat=RANK, device=str(dev), precision=prec)
+            ts.solve_sdp(b_d, C_d, gap_tol=1e-2, max_iter=2, allow_notconv=True)       # warm-up
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            Xo, yo, So, inf = ts.solve_sdp(b_d, C_d, gap_tol=1e-8, max_iter=100, allow_notconv=True)
+            torch.cuda.synchronize(dev)
+            t1 = time.perf_counter()
+            ttg[prec] = {"seconds": t1 - t0, "outer_iters": inf["iters"], "converged": bool(inf["converged"]),
+                         "rel_gap": inf["rel_gap"], "pinf": inf["pinf"], "dinf": inf["dinf"],
+                         "pcg_iters": inf["pcg_iters"], "newton_s": inf["newton_ms"] / 1e3,
+                         "eig_sweeps": inf["eig_sweeps"],
+                         "recovery_err": float(np.linalg.norm(Xo.cpu().numpy() - Xs) / np.linalg.norm(Xs))}
+            ts.close()
+        ttg["mixed_speedup"] = ttg["fp64"]["seconds"] / ttg["mixed_fp32"]["seconds"]
+
     # end to end through the C ABI with pinned host buffers (H2D and D2H inside the call)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     hins = [(pin(V.T).t(), pin(lam), pin(Ct), pin(bt)) for (V, lam, Ct, bt) in ins]
@@ -337,6 +362,7 @@ def run_ours(args):
                 "steps": e2e_steps},
         "wall_s_timed": wall,
         "mixed_fp32": mixed,
+        "time_to_gap_1e-8": ttg,
     }
     if base is not None:
         line["cpu_baseline"] = base
@@ -354,6 +380,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg (profiling runs)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
+    ap.add_argument("--no-ttg", action="store_true", help="skip the time-to-gap solves")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -61,13 +61,11 @@ __global__ void jacobi_params_kernel(int n, int npad, int k, const double* __res
 __global__ void jacobi_apply_kernel(int n, int np, const int2* __restrict__ pq, const double2* __restrict__ cs,
                                     double* __restrict__ A, double* __restrict__ V) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nblk = (int64_t)np * (np + 1) / 2;
+  const int64_t nblk = (int64_t)np * np;
   if (t < nblk) {
-    // t -> (I, J), I <= J: row I of the upper triangle holds np - I blocks
-    int I = 0;
-    int64_t rem = t;
-    while (rem >= np - I) { rem -= np - I; ++I; }
-    const int J = I + (int)rem;
+    // t -> (I, J) on the full np x np grid; the blocks with I > J are written by (J, I)
+    const int I = (int)(t % np), J = (int)(t / np);
+    if (I > J) return;
     const int2 a = pq[I], b = pq[J];
     const double2 ra = cs[I], rb = cs[J];
     const int ri[2] = {a.x, a.y}, cj[2] = {b.x, b.y};
@@ -174,8 +172,18 @@ size_t eigh_work_elems(int n) {
   return (size_t)np * 3 + 2 * kNormBlocks + 2 + 2 + 16;
 }
 
+void eigh_graph_release(EighGraph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->cap) cudaStreamDestroy(g->cap);
+  g->exec = nullptr;
+  g->cap = nullptr;
+  g->n = 0;
+}
+
 cudaError_t eigh_jacobi(cudaStream_t st, int n, double* A, double* V, double* lam, double tol, int max_sweeps,
-                        double* work, size_t work_elems, int* sweeps_out, double* off_out, int64_t* launches) {
+                        double* work, size_t work_elems, int* sweeps_out, double* off_out, int64_t* launches,
+                        EighGraph* graph) {
   if (n < 1 || work_elems < eigh_work_elems(n)) return cudaErrorInvalidValue;
   const int npad = n + (n & 1);
   const int np = npad / 2;
@@ -190,7 +198,37 @@ cudaError_t eigh_jacobi(cudaStream_t st, int n, double* A, double* V, double* la
   if (launches) ++*launches;
   double h[2] = {0.0, 0.0};
   int sweep = 0;
-  const int64_t apply_threads = (int64_t)np * (np + 1) / 2 + (int64_t)n * np;
+  const int64_t apply_threads = (int64_t)np * np + (int64_t)n * np;
+  auto sweep_kernels = [&](cudaStream_t s_) {
+    for (int k = 0; k < npad - 1; ++k) {
+      jacobi_params_kernel<<<nb(np), ET, 0, s_>>>(n, npad, k, A, pq, cs);
+      jacobi_apply_kernel<<<nb(apply_threads), ET, 0, s_>>>(n, np, pq, cs, A, V);
+    }
+  };
+  // one sweep (2 (npad - 1) kernels) as a CUDA graph, captured once per (n, A, V, work)
+  if (graph && !(graph->exec && graph->n == n && graph->A == A && graph->V == V && graph->work == work)) {
+    if (graph->exec) {
+      cudaGraphExecDestroy(graph->exec);
+      graph->exec = nullptr;
+    }
+    if (!graph->cap) {
+      e = cudaStreamCreateWithFlags(&graph->cap, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return e;
+    }
+    e = cudaStreamBeginCapture(graph->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    sweep_kernels(graph->cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(graph->cap, &g);
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(&graph->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return e;
+    graph->n = n;
+    graph->A = A;
+    graph->V = V;
+    graph->work = work;
+  }
   for (;; ++sweep) {
     jacobi_norms_kernel<<<kNormBlocks, ET, 0, st>>>(n, A, part, counter, res);
     if (launches) ++*launches;
@@ -199,11 +237,13 @@ cudaError_t eigh_jacobi(cudaStream_t st, int n, double* A, double* V, double* la
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
     if (!(h[0] > tol * tol * h[1]) || sweep >= max_sweeps) break;
-    for (int k = 0; k < npad - 1; ++k) {
-      jacobi_params_kernel<<<nb(np), ET, 0, st>>>(n, npad, k, A, pq, cs);
-      jacobi_apply_kernel<<<nb(apply_threads), ET, 0, st>>>(n, np, pq, cs, A, V);
-      if (launches) *launches += 2;
+    if (graph) {
+      e = cudaGraphLaunch(graph->exec, st);
+      if (e != cudaSuccess) return e;
+    } else {
+      sweep_kernels(st);
     }
+    if (launches) *launches += 2 * (npad - 1);
   }
   diag_kernel<<<nb(n), ET, 0, st>>>(n, A, lam);
   if (launches) ++*launches;

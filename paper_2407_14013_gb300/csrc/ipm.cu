@@ -40,7 +40,8 @@ struct IpmWork {
   double *L = nullptr, *Linv = nullptr, *T = nullptr, *U = nullptr, *G = nullptr, *Ginv = nullptr, *Wm = nullptr;
   double *V = nullptr, *Rd = nullptr, *Ct = nullptr, *Y = nullptr, *dX = nullptr, *dS = nullptr, *dSs = nullptr;
   double *dXa = nullptr, *dSa = nullptr, *Dx = nullptr, *Ds = nullptr, *R = nullptr, *M1 = nullptr, *M2 = nullptr;
-  double *Eg = nullptr, *EV = nullptr;
+  double *Eg = nullptr, *EV = nullptr, *Vprev = nullptr;
+  bool have_prev = false;   // Vprev holds the eigenvectors of the previous iteration's W
   double *lam = nullptr, *gam = nullptr, *g = nullptr, *q = nullptr, *qi = nullptr, *elam = nullptr;
   double *rp = nullptr, *dy = nullptr, *dya = nullptr, *Ax = nullptr, *rownrm = nullptr;
   double *zsvec = nullptr, *partY = nullptr, *partA = nullptr;
@@ -48,6 +49,7 @@ struct IpmWork {
   size_t eigw_elems = 0, chw_elems = 0;
   int32_t* status = nullptr;
   double xi = 0.0;
+  EighGraph eg[2];   // Jacobi sweeps for L^T S L, and for W and the step-length matrices
 };
 
 }  // namespace wc
@@ -139,6 +141,13 @@ __global__ void scale_kernel(int n, const double* __restrict__ M, const double* 
   if (dl) v *= dl[i];
   if (dr) v *= dr[j];
   out[q] = v;
+}
+
+// out = I + s M
+__global__ void shift_identity_kernel(int n, double s, const double* __restrict__ M, double* __restrict__ out) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)n * n) return;
+  out[q] = s * M[q] + (((q % n) == (q / n)) ? 1.0 : 0.0);
 }
 
 // R_ij = rhs_ij / (g_i + g_j), rhs = 2 sigma mu I - 2 diag(g)^2 - (P + P^T)
@@ -234,7 +243,7 @@ sdp_status lam_min(Ctx& c, const double* M, double* out, int* sweeps) {
   CUI(cudaMemcpyAsync(w->Eg, M, nn * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
   int sw = 0;
   double off = 0.0;
-  CUI(eigh_jacobi(c.st, c.n, w->Eg, w->EV, w->elam, 1e-13, 40, w->eigw, w->eigw_elems, &sw, &off, c.L));
+  CUI(eigh_jacobi(c.st, c.n, w->Eg, w->EV, w->elam, 1e-12, 40, w->eigw, w->eigw_elems, &sw, &off, c.L, &w->eg[1]));
   *sweeps += sw;
   std::vector<double> lh(c.n);
   CUI(cudaMemcpyAsync(lh.data(), w->elam, c.n * sizeof(double), cudaMemcpyDeviceToHost, c.st));
@@ -243,10 +252,25 @@ sdp_status lam_min(Ctx& c, const double* M, double* out, int* sweeps) {
   return SDP_OK;
 }
 
-// sup{a : Lam + a D PSD} for D = Dx or Ds, through Lam^{-1/2} D Lam^{-1/2} (Lam^{-1/2} = diag(q))
-sdp_status max_step(Ctx& c, const double* D, double* a, int* sweeps) {
-  scale_kernel<<<nb((int64_t)c.n * c.n), IT, 0, c.st>>>(c.n, D, c.w->q, c.w->q, c.w->M2);
-  ++*c.L;
+// sup{a : Lam + a D PSD} for D = Dx or Ds, through Lam^{-1/2} D Lam^{-1/2} (Lam^{-1/2} = diag(q)).
+// The caller uses min(1, f sup); when I + M / f is positive definite (a Cholesky factorisation
+// succeeds) that is 1 and the eigenvalue is not needed, so +inf is returned.
+sdp_status max_step(Ctx& c, const double* D, double f, double* a, int* sweeps) {
+  sdp_handle* h = c.h;
+  IpmWork* w = c.w;
+  const int64_t nn = (int64_t)c.n * c.n;
+  scale_kernel<<<nb(nn), IT, 0, c.st>>>(c.n, D, w->q, w->q, w->M2);
+  shift_identity_kernel<<<nb(nn), IT, 0, c.st>>>(c.n, 1.0 / f, w->M2, w->Eg);   // Eg = I + M / f
+  *c.L += 2;
+  CUI(cudaMemsetAsync(w->status, 0, sizeof(int32_t), c.st));
+  CUI(spd_cholesky(c.st, c.n, w->Eg, nullptr, w->chw, w->chw_elems, h->s64.ws, h->s64.ws_elems, w->status, c.L));
+  int32_t st_h = 0;
+  CUI(cudaMemcpyAsync(&st_h, w->status, sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
+  CUI(cudaStreamSynchronize(c.st));
+  if (st_h == 0) {
+    *a = INFINITY;
+    return SDP_OK;
+  }
   double lmin = 0.0;
   sdp_status s = lam_min(c, c.w->M2, &lmin, sweeps);
   if (s != SDP_OK) return s;
@@ -288,7 +312,7 @@ sdp_status ensure_workspace(sdp_handle* h) {
       {&w->L, nn}, {&w->Linv, nn}, {&w->T, nn}, {&w->U, nn}, {&w->G, nn}, {&w->Ginv, nn}, {&w->Wm, nn},
       {&w->V, nn}, {&w->Rd, nn}, {&w->Ct, nn}, {&w->Y, nn}, {&w->dX, nn}, {&w->dS, nn}, {&w->dSs, nn},
       {&w->dXa, nn}, {&w->dSa, nn}, {&w->Dx, nn}, {&w->Ds, nn}, {&w->R, nn}, {&w->M1, nn}, {&w->M2, nn},
-      {&w->Eg, nn}, {&w->EV, nn}, {&w->lam, (size_t)n}, {&w->gam, (size_t)n}, {&w->g, (size_t)n},
+      {&w->Eg, nn}, {&w->EV, nn}, {&w->Vprev, nn}, {&w->lam, (size_t)n}, {&w->gam, (size_t)n}, {&w->g, (size_t)n},
       {&w->q, (size_t)n}, {&w->qi, (size_t)n}, {&w->elam, (size_t)n}, {&w->rp, (size_t)m}, {&w->dy, (size_t)m},
       {&w->dya, (size_t)m}, {&w->Ax, (size_t)m}, {&w->rownrm, (size_t)m}, {&w->eigw, w->eigw_elems},
       {&w->chw, w->chw_elems}, {&w->dots, (size_t)kDots}, {&w->dpart, (size_t)kDots * kDotBlocks}};
@@ -376,7 +400,7 @@ sdp_status step(Ctx& c, double* X, double* y, double* S, const Measures& Mz, sdp
   CUI(gemm(c, false, false, S, w->L, w->M1));
   CUI(gemm(c, true, false, w->L, w->M1, w->T));
   int sw = 0;
-  CUI(eigh_jacobi(c.st, n, w->T, w->U, w->gam, 1e-14, 40, w->eigw, w->eigw_elems, &sw, &off, c.L));
+  CUI(eigh_jacobi(c.st, n, w->T, w->U, w->gam, 1e-14, 40, w->eigw, w->eigw_elems, &sw, &off, c.L, &w->eg[0]));
   sweeps += sw;
   gamma_kernel<<<nb(n), IT, 0, c.st>>>(n, w->gam, w->g, w->q, w->qi, w->status);
   ++*c.L;
@@ -386,9 +410,20 @@ sdp_status step(Ctx& c, double* X, double* y, double* S, const Measures& Mz, sdp
   scale_kernel<<<nb(nn), IT, 0, c.st>>>(n, w->M1, w->qi, nullptr, w->Ginv);      // G^{-1} = Gamma^{1/4} U^T L^{-1}
   *c.L += 2;
   CUI(gemm(c, false, true, w->G, w->G, w->Wm));                                  // W = G G^T
-  CUI(cudaMemcpyAsync(w->Eg, w->Wm, bytes, cudaMemcpyDeviceToDevice, c.st));
-  CUI(eigh_jacobi(c.st, n, w->Eg, w->V, w->lam, 1e-14, 40, w->eigw, w->eigw_elems, &sw, &off, c.L));
+  // eig(W), started from the previous iteration's eigenvectors when there are any: Jacobi on
+  // Vprev^T W Vprev (nearly diagonal along the path), then V = Vprev V'
+  if (w->have_prev) {
+    CUI(gemm(c, false, false, w->Wm, w->Vprev, w->M1));
+    CUI(gemm(c, true, false, w->Vprev, w->M1, w->Eg));
+  } else {
+    CUI(cudaMemcpyAsync(w->Eg, w->Wm, bytes, cudaMemcpyDeviceToDevice, c.st));
+  }
+  CUI(eigh_jacobi(c.st, n, w->Eg, w->EV, w->lam, 1e-14, 40, w->eigw, w->eigw_elems, &sw, &off, c.L, &w->eg[1]));
   sweeps += sw;
+  if (w->have_prev) CUI(gemm(c, false, false, w->Vprev, w->EV, w->V));
+  else CUI(cudaMemcpyAsync(w->V, w->EV, bytes, cudaMemcpyDeviceToDevice, c.st));
+  CUI(cudaMemcpyAsync(w->Vprev, w->V, bytes, cudaMemcpyDeviceToDevice, c.st));
+  w->have_prev = true;
   int32_t st_h = 0;
   CUI(cudaMemcpyAsync(&st_h, w->status, sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
   CUI(cudaStreamSynchronize(c.st));
@@ -406,9 +441,9 @@ sdp_status step(Ctx& c, double* X, double* y, double* S, const Measures& Mz, sdp
   CUI(gemm(c, true, false, w->G, w->dSa, w->M1));
   CUI(gemm(c, false, false, w->M1, w->G, w->Ds));                                // Ds = G^T dS G
   double ap = 0.0, ad = 0.0;
-  s = max_step(c, w->Dx, &ap, &sweeps);
+  s = max_step(c, w->Dx, 1.0, &ap, &sweeps);
   if (s != SDP_OK) return s;
-  s = max_step(c, w->Ds, &ad, &sweeps);
+  s = max_step(c, w->Ds, 1.0, &ad, &sweeps);
   if (s != SDP_OK) return s;
   ap = std::min(1.0, ap);
   ad = std::min(1.0, ad);
@@ -439,9 +474,9 @@ sdp_status step(Ctx& c, double* X, double* y, double* S, const Measures& Mz, sdp
   CUI(gemm(c, false, true, w->M1, w->Ginv, w->Dx));
   CUI(gemm(c, true, false, w->G, w->dS, w->M1));
   CUI(gemm(c, false, false, w->M1, w->G, w->Ds));
-  s = max_step(c, w->Dx, &ap, &sweeps);
+  s = max_step(c, w->Dx, 0.98, &ap, &sweeps);
   if (s != SDP_OK) return s;
-  s = max_step(c, w->Ds, &ad, &sweeps);
+  s = max_step(c, w->Ds, 0.98, &ad, &sweeps);
   if (s != SDP_OK) return s;
   ap = std::min(1.0, 0.98 * ap);
   ad = std::min(1.0, 0.98 * ad);
@@ -469,6 +504,7 @@ sdp_status check_args(sdp_handle* h, const double* b, const double* C, double* X
 
 void wc_ipm_free(sdp_handle* h) {
   if (!h || !h->ipm) return;
+  for (auto& g : h->ipm->eg) eigh_graph_release(&g);
   if (h->ipm->pool) cudaFree(h->ipm->pool);
   delete h->ipm;
   h->ipm = nullptr;
@@ -539,6 +575,7 @@ extern "C" sdp_status sdp_solve(sdp_handle* h, const double* b, const double* C,
   }
   xi = std::max(xi, (1.0 + std::sqrt(cc)) / std::sqrt((double)n));
   w->xi = xi;
+  w->have_prev = false;
   scaled_identity_kernel<<<nb((int64_t)n * n), IT, 0, h->st>>>(n, xi, X);
   scaled_identity_kernel<<<nb((int64_t)n * n), IT, 0, h->st>>>(n, xi, S);
   CUI(cudaMemsetAsync(y, 0, m * sizeof(double), h->st));

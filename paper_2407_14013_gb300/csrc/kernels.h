@@ -112,8 +112,18 @@ cudaError_t spd_cholesky(cudaStream_t st, int n, double* A, double* Linv, double
 // ---- eigh.cu: symmetric eigen-decomposition (parallel cyclic Jacobi, FP64) ------------------
 // A (n x n, symmetric, destroyed) = V diag(lam) V^T; stops when ||offdiag A||_F <= tol ||A||_F
 // or after max_sweeps sweeps (sweeps and the final relative off-diagonal norm are returned).
+// With `graph` non-NULL a sweep runs as one replay of a CUDA graph captured (on the graph's own
+// stream) for these pointers; the graph is recaptured when n or a pointer changes.
+struct EighGraph {
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+  int n = 0;
+  const void *A = nullptr, *V = nullptr, *work = nullptr;
+};
+void eigh_graph_release(EighGraph* g);
 size_t eigh_work_elems(int n);
 cudaError_t eigh_jacobi(cudaStream_t st, int n, double* A, double* V, double* lam, double tol, int max_sweeps,
-                        double* work, size_t work_elems, int* sweeps_out, double* off_out, int64_t* launches);
+                        double* work, size_t work_elems, int* sweeps_out, double* off_out, int64_t* launches,
+                        EighGraph* graph = nullptr);
 
 }  // namespace wc

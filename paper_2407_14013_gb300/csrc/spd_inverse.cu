@@ -159,6 +159,7 @@ cudaError_t cholesky_and_inverse(cudaStream_t st, int n, double* A, double* X, d
   }
   zero_upper_kernel<<<nblk((int64_t)n * n, 256), 256, 0, st>>>(n, A);
   if (launches) ++*launches;
+  if (!X) return cudaGetLastError();   // factor only
   // ---- X = L^{-1} by block rows: X[I, :I] = -Li_II (L[I, :I] X[:I, :I]), X[I, I] = Li_II
   e = cudaMemsetAsync(X, 0, (size_t)n * n * sizeof(double), st);
   if (e != cudaSuccess) return e;
@@ -200,7 +201,8 @@ cudaError_t spd_inverse(cudaStream_t st, int n, double* A, double* work, size_t 
   return cudaGetLastError();
 }
 
-// A = L L^T: L into A (lower, upper zeroed), L^{-1} into Linv (n x n).  work as for spd_inverse.
+// A = L L^T: L into A (lower, upper zeroed), L^{-1} into Linv (n x n; NULL: factor only).
+// work as for spd_inverse.
 cudaError_t spd_cholesky(cudaStream_t st, int n, double* A, double* Linv, double* work, size_t work_elems,
                          double* gemm_ws, size_t gemm_ws_elems, int32_t* status, int64_t* launches) {
   if (spd_inverse_work(n) > work_elems) return cudaErrorInvalidValue;
