@@ -16,8 +16,16 @@
 // block [[a_pp, a_pq], [a_pq, a_qq]] diagonal: tau = (a_qq - a_pp) / (2 a_pq),
 // t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c, and the update
 // is A <- R^T A R, V <- V R with R = [[c, s], [-s, c]] on the rows / columns (p, q).
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "common.cuh"
 #include "kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace wc {
 
@@ -163,13 +171,178 @@ __global__ void diag_kernel(int n, const double* __restrict__ A, double* __restr
 inline unsigned nb(int64_t total) { return (unsigned)((total + ET - 1) / ET); }
 
 constexpr int kNormBlocks = 64;
+constexpr int TI = 16;   // pairs per A tile side
+constexpr int TR = 32;   // rows per V tile
+constexpr int TV = 8;    // pairs per V tile
+
+__device__ __forceinline__ double2 rotation(int n, int p, int q, const double* __restrict__ A) {
+  double c = 1.0, s = 0.0;
+  if (q < n) {
+    const double apq = A[p + (int64_t)q * n];
+    if (apq != 0.0) {
+      const double tau = (A[q + (int64_t)q * n] - A[p + (int64_t)p * n]) / (2.0 * apq);
+      double t;
+      if (fabs(tau) > 1e100) t = 0.5 / tau;
+      else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+      c = 1.0 / sqrt(1.0 + t * t);
+      s = t * c;
+    }
+  }
+  return make_double2(c, s);
+}
+
+// The whole Jacobi iteration in one cooperative launch: every step reads A from one buffer and
+// writes the rotated matrix to the other (so each block can compute the rotations it needs
+// from the old matrix without waiting for anyone), then one grid-wide barrier; the stopping
+// test after each sweep is evaluated identically by every block.  Replaces 2 (n - 1) launches
+// per sweep and the host read per sweep of the graph path.
+__global__ void __launch_bounds__(ET)
+jacobi_coop_kernel(int n, int npad, double* __restrict__ A0, double* __restrict__ A1, double* __restrict__ V,
+                   double* __restrict__ lam, double tol2, int max_sweeps, double* __restrict__ red,
+                   int* __restrict__ sweeps_out, double* __restrict__ off_out) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double2 cs_s[2 * TI];
+  __shared__ int2 pq_s[2 * TI];
+  __shared__ double sh[32];
+  const int np = npad / 2;
+  const int nT = (np + TI - 1) / TI;
+  const int nA = nT * (nT + 1) / 2;                          // A tiles (ti <= tj)
+  const int nRT = (n + TR - 1) / TR, nV = nRT * ((np + TV - 1) / TV);
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t q = gtid; q < nn; q += gsz) V[q] = ((q % n) == (q / n)) ? 1.0 : 0.0;
+  double* Ain = A0;
+  double* Aout = A1;
+  int sweep = 0;
+  double so = 0.0, sa = 0.0;
+  for (;; ++sweep) {
+    double o = 0.0, a = 0.0;
+    for (int64_t q = gtid; q < nn; q += gsz) {
+      const double v = Ain[q];
+      a = fma(v, v, a);
+      if ((q % n) != (q / n)) o = fma(v, v, o);
+    }
+    o = block_sum(o, sh);
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) {
+      red[2 * blockIdx.x] = o;
+      red[2 * blockIdx.x + 1] = a;
+    }
+    grid.sync();
+    so = 0.0;
+    sa = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+      so += red[2 * b];
+      sa += red[2 * b + 1];
+    }
+    so = block_sum(so, sh);
+    sa = block_sum(sa, sh);
+    grid.sync();                               // every block has read red before it is reused
+    if (!(so > tol2 * sa) || sweep >= max_sweeps) break;
+    for (int k = 0; k < npad - 1; ++k) {
+      // tiles: A blocks (TI pairs x TJ pairs, tile row <= tile column), then V (TR rows x TV pairs);
+      // a block computes only the rotations its tile needs (FP64 arithmetic is the scarce unit)
+      for (int tile = blockIdx.x; tile < nA + nV; tile += gridDim.x) {
+        int I0 = 0, J0 = 0, R0 = 0, nI = 0, nJ = 0;
+        if (tile < nA) {
+          // tile = tj (tj + 1) / 2 + ti with ti <= tj
+          int tj = 0;
+          while ((tj + 1) * (tj + 2) / 2 <= tile) ++tj;
+          const int ti = tile - tj * (tj + 1) / 2;
+          I0 = ti * TI;
+          J0 = tj * TI;
+          nI = min(TI, np - I0);
+          nJ = min(TI, np - J0);
+        } else {
+          const int tv = tile - nA;
+          R0 = (tv % nRT) * TR;
+          J0 = (tv / nRT) * TV;
+          nJ = min(TV, np - J0);
+        }
+        // rotations of pairs I0 .. I0+nI-1 into slots [0, nI), of J0 .. into [TI, TI + nJ)
+        for (int u = threadIdx.x; u < nI + nJ; u += blockDim.x) {
+          const int P = (u < nI) ? I0 + u : J0 + (u - nI);
+          const int slot = (u < nI) ? u : TI + (u - nI);   // J rotations at slots TI ..
+          int p, q;
+          pair_of(k, P, npad, p, q);
+          pq_s[slot] = make_int2(p, q);
+          cs_s[slot] = rotation(n, p, q, Ain);
+        }
+        __syncthreads();
+        if (tile < nA) {
+          for (int e = threadIdx.x; e < nI * nJ; e += blockDim.x) {
+            const int iu = e % nI, ju = e / nI;
+            const int I = I0 + iu, J = J0 + ju;
+            if (I > J) continue;
+            const int2 pa = pq_s[iu], pb = pq_s[TI + ju];
+            const double2 ra = cs_s[iu], rb = cs_s[TI + ju];
+            const int ri[2] = {pa.x, pa.y}, cj[2] = {pb.x, pb.y};
+            double X[2][2], T[2][2], Y[2][2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+              for (int v = 0; v < 2; ++v)
+                X[u][v] = (ri[u] < n && cj[v] < n) ? Ain[ri[u] + (int64_t)cj[v] * n] : 0.0;
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+              T[0][v] = ra.x * X[0][v] - ra.y * X[1][v];
+              T[1][v] = ra.y * X[0][v] + ra.x * X[1][v];
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              Y[u][0] = rb.x * T[u][0] - rb.y * T[u][1];
+              Y[u][1] = rb.y * T[u][0] + rb.x * T[u][1];
+            }
+            if (I == J) {
+              Y[0][1] = 0.0;
+              Y[1][0] = 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+              for (int v = 0; v < 2; ++v) {
+                if (ri[u] >= n || cj[v] >= n) continue;
+                Aout[ri[u] + (int64_t)cj[v] * n] = Y[u][v];
+                Aout[cj[v] + (int64_t)ri[u] * n] = Y[u][v];
+              }
+          }
+        } else {
+          const int nR = min(TR, n - R0);
+          for (int e = threadIdx.x; e < nR * nJ; e += blockDim.x) {
+            const int i = R0 + e % nR, ju = e / nR;
+            const int2 pb = pq_s[TI + ju];
+            if (pb.y >= n) continue;
+            const double2 r = cs_s[TI + ju];
+            const double vp = V[i + (int64_t)pb.x * n], vq = V[i + (int64_t)pb.y * n];
+            V[i + (int64_t)pb.x * n] = r.x * vp - r.y * vq;
+            V[i + (int64_t)pb.y * n] = r.y * vp + r.x * vq;
+          }
+        }
+        __syncthreads();
+      }
+      grid.sync();
+      double* tmp = Ain;
+      Ain = Aout;
+      Aout = tmp;
+    }
+  }
+  for (int64_t i = gtid; i < n; i += gsz) lam[i] = Ain[i + i * n];
+  if (gtid == 0) {
+    *sweeps_out = sweep;
+    *off_out = (sa > 0.0) ? sqrt(so / sa) : 0.0;
+  }
+}
 
 }  // namespace
 
+constexpr int kCoopMaxBlocks = 1024;
+
 size_t eigh_work_elems(int n) {
   const int np = (n + 1) / 2;
-  // pq (int2 = 1 double each), cs (2 doubles each), norm partials, result, counter
-  return (size_t)np * 3 + 2 * kNormBlocks + 2 + 2 + 16;
+  // pq (int2 = 1 double each), cs (2 doubles each), norm partials, result, counter; the second
+  // copy of A and the block partials of the cooperative path
+  return (size_t)np * 3 + 2 * kNormBlocks + 2 + 2 + 16 + (size_t)n * n + 2 * kCoopMaxBlocks + 64;
 }
 
 void eigh_graph_release(EighGraph* g) {
@@ -187,6 +360,42 @@ cudaError_t eigh_jacobi(cudaStream_t st, int n, double* A, double* V, double* la
   if (n < 1 || work_elems < eigh_work_elems(n)) return cudaErrorInvalidValue;
   const int npad = n + (n & 1);
   const int np = npad / 2;
+  {
+    // cooperative path: one launch for the whole iteration
+    double* A1 = work + ((size_t)np * 3 + 2 * kNormBlocks + 2 + 2 + 16 + 7) / 8 * 8;
+    double* red = A1 + (size_t)n * n;
+    int* out_i = reinterpret_cast<int*>(red + 2 * kCoopMaxBlocks);
+    double* out_d = red + 2 * kCoopMaxBlocks + 2;
+    int dev = 0, coop = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    const size_t smem = 0;
+    if (coop &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel, ET, smem) == cudaSuccess &&
+        per_sm > 0) {
+      const int64_t nT = (np + TI - 1) / TI;
+      const int64_t want = nT * (nT + 1) / 2 + ((n + TR - 1) / TR) * (int64_t)((np + TV - 1) / TV);
+      int blocks = (int)std::min<int64_t>({want, (int64_t)per_sm * g_num_sms, (int64_t)kCoopMaxBlocks});
+      if (blocks < 1) blocks = 1;
+      double tol2 = tol * tol;
+      void* args[] = {&n, (void*)&npad, &A, &A1, &V, &lam, &tol2, &max_sweeps, &red, &out_i, &out_d};
+      cudaError_t e = cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel, dim3(blocks), dim3(ET), args,
+                                                  smem, st);
+      if (e == cudaSuccess) {
+        if (launches) ++*launches;
+        int sw = 0;
+        double off = 0.0;
+        e = cudaMemcpyAsync(&sw, out_i, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&off, out_d, sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        if (sweeps_out) *sweeps_out = sw;
+        if (off_out) *off_out = off;
+        return cudaSuccess;
+      }
+      cudaGetLastError();   // not launchable cooperatively here: take the graph path
+    }
+  }
   int2* pq = reinterpret_cast<int2*>(work);
   double2* cs = reinterpret_cast<double2*>(work + ((np + 1) & ~1));          // 16-byte aligned
   double* part = work + ((np + 1) & ~1) + 2 * (size_t)np;
@@ -250,6 +459,189 @@ cudaError_t eigh_jacobi(cudaStream_t st, int n, double* A, double* V, double* la
   if (sweeps_out) *sweeps_out = sweep;
   if (off_out) *off_out = (h[1] > 0.0) ? sqrt(h[0] / h[1]) : 0.0;
   return cudaGetLastError();
+}
+
+}  // namespace wc
+
+// ---- smallest eigenvalue by Lanczos -----------------------------------------------------------
+//
+// lambda_min(M) for a symmetric M (n x n): Lanczos on the Krylov space of a fixed start vector,
+// with full re-orthogonalisation (classical Gram-Schmidt applied twice), run in chunks of
+// iterations by one cooperative launch each; after each chunk the host finds the smallest
+// eigenvalue of the tridiagonal T_k (bisection on Sturm counts).  It stops when that value has
+// not moved for two chunks (relative 1e-14), when the basis spans R^n (k = n, then T_n is
+// similar to M), or on breakdown (beta_k = 0: an invariant subspace).  Ritz values of a
+// symmetric matrix decrease monotonically to lambda_min as k grows.
+
+namespace wc {
+
+namespace {
+
+__global__ void __launch_bounds__(ET)
+lanczos_coop_kernel(int n, const double* __restrict__ M, double* __restrict__ Vb, double* __restrict__ alpha,
+                    double* __restrict__ beta, double* __restrict__ w, double* __restrict__ hbuf,
+                    double* __restrict__ red, int k0, int k1) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gwarp = gtid >> 5, nwarps = gsz >> 5;
+  auto grid_sum = [&](double v) -> double {   // identical result in every block
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) red[blockIdx.x] = v;
+    grid.sync();
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += red[b];
+    s = block_sum(s, sh);
+    grid.sync();
+    return s;
+  };
+  if (k0 == 0) {   // v_0 = fixed start vector, normalised
+    double loc = 0.0;
+    for (int64_t i = gtid; i < n; i += gsz) {
+      const double v = 1.0 + 0.5 * sin(0.7 * (double)i + 0.3);
+      Vb[i] = v;
+      loc = fma(v, v, loc);
+    }
+    const double nrm = sqrt(grid_sum(loc));
+    for (int64_t i = gtid; i < n; i += gsz) Vb[i] /= nrm;
+    grid.sync();
+  }
+  for (int k = k0; k < k1; ++k) {
+    const double* vk = Vb + (int64_t)k * n;
+    // w = M v_k (M symmetric: row i = column i, contiguous), one warp per row
+    for (int64_t i = gwarp; i < n; i += nwarps) {
+      const double* col = M + i * n;
+      double acc = 0.0;
+      for (int j = lane; j < n; j += 32) acc = fma(col[j], vk[j], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) w[i] = acc;
+    }
+    grid.sync();
+    double loc = 0.0;
+    for (int64_t i = gtid; i < n; i += gsz) loc = fma(vk[i], w[i], loc);
+    const double a = grid_sum(loc);
+    const double bprev = (k > 0) ? beta[k - 1] : 0.0;
+    for (int64_t i = gtid; i < n; i += gsz) {
+      double v = w[i] - a * vk[i];
+      if (k > 0) v -= bprev * Vb[(int64_t)(k - 1) * n + i];
+      w[i] = v;
+    }
+    if (gtid == 0) alpha[k] = a;
+    grid.sync();
+    // full re-orthogonalisation against v_0 .. v_k, twice
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int64_t j = gwarp; j <= k; j += nwarps) {
+        const double* vj = Vb + j * n;
+        double acc = 0.0;
+        for (int i = lane; i < n; i += 32) acc = fma(vj[i], w[i], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) hbuf[j] = acc;
+      }
+      grid.sync();
+      for (int64_t i = gtid; i < n; i += gsz) {
+        double v = w[i];
+        for (int j = 0; j <= k; ++j) v = fma(-hbuf[j], Vb[(int64_t)j * n + i], v);
+        w[i] = v;
+      }
+      grid.sync();
+    }
+    loc = 0.0;
+    for (int64_t i = gtid; i < n; i += gsz) loc = fma(w[i], w[i], loc);
+    const double b = sqrt(grid_sum(loc));
+    if (gtid == 0) beta[k] = b;
+    double* vn = Vb + (int64_t)(k + 1) * n;
+    for (int64_t i = gtid; i < n; i += gsz) vn[i] = (b > 0.0) ? w[i] / b : 0.0;
+    grid.sync();
+  }
+}
+
+// number of eigenvalues of the tridiagonal (a, b) below x (Sturm sequence)
+int sturm_count(const std::vector<double>& a, const std::vector<double>& b, int k, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  for (int i = 0; i < k; ++i) {
+    const double bb = (i > 0) ? b[i - 1] * b[i - 1] : 0.0;
+    d = (a[i] - x) - (i > 0 ? bb / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+double tridiag_min(const std::vector<double>& a, const std::vector<double>& b, int k) {
+  double lo = INFINITY, hi = -INFINITY;
+  for (int i = 0; i < k; ++i) {
+    const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < k ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  for (int it = 0; it < 200 && hi - lo > 1e-16 * std::max(std::fabs(lo), std::fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_count(a, b, k, mid) >= 1) hi = mid;
+    else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+}  // namespace
+
+size_t lanczos_work_elems(int n) {
+  const size_t K = (size_t)n + 1;
+  return (size_t)n * (K + 1) + 3 * K + (size_t)n + 2 * kCoopMaxBlocks + 64;
+}
+
+cudaError_t lanczos_min(cudaStream_t st, int n, const double* M, double* work, size_t work_elems, double* lmin,
+                        int* iters, int64_t* launches) {
+  if (n < 1 || work_elems < lanczos_work_elems(n)) return cudaErrorInvalidValue;
+  const int K = n;   // at most n vectors span R^n
+  double* Vb = work;
+  double* alpha = Vb + (size_t)n * (K + 2);
+  double* beta = alpha + K + 1;
+  double* hbuf = beta + K + 1;
+  double* w = hbuf + K + 1;
+  double* red = w + n;
+  int dev = 0, coop = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop) return cudaErrorNotSupported;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_coop_kernel, ET, 0);
+  if (e != cudaSuccess || per_sm < 1) return cudaErrorNotSupported;
+  const int want = (int)std::max<int64_t>(1, ((int64_t)n * 32 + ET - 1) / ET);   // one warp per row
+  const int blocks = std::min({want, per_sm * g_num_sms, kCoopMaxBlocks});
+  std::vector<double> ah(K + 1), bh(K + 1);
+  double prev = INFINITY, prev2 = INFINITY, theta = 0.0;
+  int k = 0;
+  const int chunk = 32;
+  while (k < K) {
+    int k0 = k, k1 = std::min(K, k + chunk);
+    void* args[] = {&n, (void*)&M, &Vb, &alpha, &beta, &w, &hbuf, &red, &k0, &k1};
+    e = cudaLaunchCooperativeKernel((const void*)lanczos_coop_kernel, dim3(blocks), dim3(ET), args, 0, st);
+    if (e != cudaSuccess) return e;
+    if (launches) ++*launches;
+    e = cudaMemcpyAsync(ah.data(), alpha, k1 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bh.data(), beta, k1 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    // breakdown: the Krylov space is invariant; T_j holds its eigenvalues
+    int kk = k1;
+    for (int j = k0; j < k1; ++j)
+      if (!(bh[j] > 1e-300)) {
+        kk = j + 1;
+        break;
+      }
+    theta = tridiag_min(ah, bh, kk);
+    k = k1;
+    if (kk < k1) break;
+    const double scale = std::max(std::fabs(theta), 1e-300);
+    if (std::fabs(theta - prev) <= 1e-14 * scale && std::fabs(prev - prev2) <= 1e-14 * scale) break;
+    prev2 = prev;
+    prev = theta;
+  }
+  *lmin = theta;
+  if (iters) *iters = k;
+  return cudaSuccess;
 }
 
 }  // namespace wc

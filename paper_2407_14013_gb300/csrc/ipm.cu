@@ -45,8 +45,8 @@ struct IpmWork {
   double *lam = nullptr, *gam = nullptr, *g = nullptr, *q = nullptr, *qi = nullptr, *elam = nullptr;
   double *rp = nullptr, *dy = nullptr, *dya = nullptr, *Ax = nullptr, *rownrm = nullptr;
   double *zsvec = nullptr, *partY = nullptr, *partA = nullptr;
-  double *eigw = nullptr, *chw = nullptr, *dots = nullptr, *dpart = nullptr;
-  size_t eigw_elems = 0, chw_elems = 0;
+  double *eigw = nullptr, *chw = nullptr, *dots = nullptr, *dpart = nullptr, *lzw = nullptr;
+  size_t eigw_elems = 0, chw_elems = 0, lzw_elems = 0;
   int32_t* status = nullptr;
   double xi = 0.0;
   EighGraph eg[2];   // Jacobi sweeps for L^T S L, and for W and the step-length matrices
@@ -236,7 +236,8 @@ void residual_p(Ctx& c, const double* b, const double* X) {
 }
 
 // smallest eigenvalue of the symmetric M (copied; M is kept)
-sdp_status lam_min(Ctx& c, const double* M, double* out, int* sweeps) {
+// smallest eigenvalue of the symmetric M by the Jacobi eigensolver (all eigenvalues)
+sdp_status lam_min_jacobi(Ctx& c, const double* M, double* out, int* sweeps) {
   sdp_handle* h = c.h;
   IpmWork* w = c.w;
   const size_t nn = (size_t)c.n * c.n;
@@ -249,6 +250,20 @@ sdp_status lam_min(Ctx& c, const double* M, double* out, int* sweeps) {
   CUI(cudaMemcpyAsync(lh.data(), w->elam, c.n * sizeof(double), cudaMemcpyDeviceToHost, c.st));
   CUI(cudaStreamSynchronize(c.st));
   *out = *std::min_element(lh.begin(), lh.end());
+  return SDP_OK;
+}
+
+// smallest eigenvalue of M: Lanczos, or Jacobi where cooperative launches are unavailable
+sdp_status lam_min(Ctx& c, const double* M, double* out, int* sweeps) {
+  sdp_handle* h = c.h;
+  IpmWork* w = c.w;
+  int it = 0;
+  cudaError_t e = lanczos_min(c.st, c.n, M, w->lzw, w->lzw_elems, out, &it, c.L);
+  if (e == cudaErrorNotSupported) {
+    cudaGetLastError();
+    return lam_min_jacobi(c, M, out, sweeps);
+  }
+  CUI(e);
   return SDP_OK;
 }
 
@@ -272,9 +287,25 @@ sdp_status max_step(Ctx& c, const double* D, double f, double* a, int* sweeps) {
     return SDP_OK;
   }
   double lmin = 0.0;
-  sdp_status s = lam_min(c, c.w->M2, &lmin, sweeps);
+  sdp_status s = lam_min(c, w->M2, &lmin, sweeps);
   if (s != SDP_OK) return s;
   *a = (lmin >= 0.0) ? INFINITY : -1.0 / lmin;
+  if (f < 1.0 && std::isfinite(*a) && f * *a < 1.0) {
+    // the step taken is f a: check that I + f a M is positive definite, else recompute lambda_min
+    // with the Jacobi eigensolver
+    shift_identity_kernel<<<nb(nn), IT, 0, c.st>>>(c.n, f * *a, w->M2, w->Eg);
+    ++*c.L;
+    CUI(cudaMemsetAsync(w->status, 0, sizeof(int32_t), c.st));
+    CUI(spd_cholesky(c.st, c.n, w->Eg, nullptr, w->chw, w->chw_elems, h->s64.ws, h->s64.ws_elems, w->status, c.L));
+    int32_t ok = 0;
+    CUI(cudaMemcpyAsync(&ok, w->status, sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
+    CUI(cudaStreamSynchronize(c.st));
+    if (ok != 0) {
+      s = lam_min_jacobi(c, w->M2, &lmin, sweeps);
+      if (s != SDP_OK) return s;
+      *a = (lmin >= 0.0) ? INFINITY : -1.0 / lmin;
+    }
+  }
   return SDP_OK;
 }
 
@@ -301,6 +332,7 @@ sdp_status ensure_workspace(sdp_handle* h) {
   w->m = m;
   w->eigw_elems = eigh_work_elems(n);
   w->chw_elems = spd_inverse_work(n);
+  w->lzw_elems = lanczos_work_elems(n);
   size_t off = 0;
   auto take = [&](size_t count) {
     off = (off + 31) & ~size_t(31);
@@ -315,7 +347,7 @@ sdp_status ensure_workspace(sdp_handle* h) {
       {&w->Eg, nn}, {&w->EV, nn}, {&w->Vprev, nn}, {&w->lam, (size_t)n}, {&w->gam, (size_t)n}, {&w->g, (size_t)n},
       {&w->q, (size_t)n}, {&w->qi, (size_t)n}, {&w->elam, (size_t)n}, {&w->rp, (size_t)m}, {&w->dy, (size_t)m},
       {&w->dya, (size_t)m}, {&w->Ax, (size_t)m}, {&w->rownrm, (size_t)m}, {&w->eigw, w->eigw_elems},
-      {&w->chw, w->chw_elems}, {&w->dots, (size_t)kDots}, {&w->dpart, (size_t)kDots * kDotBlocks}};
+      {&w->chw, w->chw_elems}, {&w->lzw, w->lzw_elems}, {&w->dots, (size_t)kDots}, {&w->dpart, (size_t)kDots * kDotBlocks}};
   if (h->kind == SDP_A_DENSE_SVEC) {
     plan.push_back({&w->zsvec, (size_t)h->N});
     plan.push_back({&w->partY, (size_t)h->GY * h->N});
