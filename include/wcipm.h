@@ -222,6 +222,14 @@ sdp_status sdp_newton_solve(sdp_handle* h, const double* V, const double* lam,
                             const double* Ct, const double* bt,
                             double* dX, double* dy, double* dS, sdp_newton_info* info);
 
+/* Another right side (C~, b~) at the scaling point of the most recent sdp_newton_solve on this
+ * handle: the split and the preconditioner core (a1, a2: E, Sigma, B = A Q and the inverse of
+ * the Schur complement) are reused, so only the right side, the PCG and the recovery run.
+ * The interior-point corrector uses it (two right sides per scaling point).  SDP_EINVAL when
+ * the handle has no usable previous solve (none yet, or its factorisation failed). */
+sdp_status sdp_newton_resolve(sdp_handle* h, const double* Ct, const double* bt, double* dX, double* dy, double* dS,
+                              sdp_newton_info* info);
+
 /* Same as sdp_newton_solve with every array argument a HOST pointer
  * (pinned memory gives asynchronous copies); the copies to and from the
  * device are part of the call. */

@@ -159,6 +159,22 @@ class NewtonSolver:
         self.last_info = self._info(ci, st)
         return dX, dy, dS, self.last_info
 
+    def resolve(self, Ct, bt, out=None, allow_notconv: bool = False):
+        """Another right side at the scaling point of the last solve (sdp_newton_resolve)."""
+        torch = self.torch
+        n, m = self.n, self.m
+        f64 = torch.float64
+        Ct, bt = (t.to(device=self.device, dtype=f64).contiguous() for t in (Ct, bt))
+        if out is None:
+            out = (torch.empty((n, n), dtype=f64, device=self.device), torch.empty(m, dtype=f64, device=self.device),
+                   torch.empty((n, n), dtype=f64, device=self.device))
+        dX, dy, dS = out
+        ci = native.sdp_newton_info()
+        st = native.sdp_newton_resolve(self.handle, _ptr(Ct), _ptr(bt), _ptr(dX), _ptr(dy), _ptr(dS), ci,
+                                       allow_notconv=allow_notconv)
+        self.last_info = self._info(ci, st)
+        return dX, dy, dS, self.last_info
+
     def solve_host(self, V, lam, Ct, bt, out, allow_notconv: bool = False):
         """Same solve with host (CPU, ideally pinned) tensors; copies are inside the call.
         V must already be stored column-major (e.g. ``V.t().contiguous().t()``), so that

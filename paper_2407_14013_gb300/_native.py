@@ -63,6 +63,7 @@ EXPORTS = {
     "sdp_newton_solve": (c_int32, [c_void_p] + [c_void_p] * 7 + [POINTER(sdp_newton_info)]),
     "sdp_newton_solve_host": (c_int32, [c_void_p] + [c_void_p] * 7 + [POINTER(sdp_newton_info)]),
     "sdp_grad": (c_int32, [c_void_p] + [c_void_p] * 6 + [POINTER(sdp_newton_info)]),
+    "sdp_newton_resolve": (c_int32, [c_void_p] + [c_void_p] * 5 + [POINTER(sdp_newton_info)]),
     "sdp_eigh_work_elems": (c_int64, [c_int32]),
     "sdp_eigh": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_double, c_int32, c_void_p, c_int64,
                            POINTER(c_int32)]),
@@ -133,6 +134,11 @@ def sdp_newton_solve(h: int, V: int, lam: int, Ct: int, bt: int, dX: int, dy: in
 def sdp_newton_solve_host(h: int, V: int, lam: int, Ct: int, bt: int, dX: int, dy: int, dS: int,
                           info: sdp_newton_info, allow_notconv: bool = False) -> int:
     return _solve("sdp_newton_solve_host", h, (V, lam, Ct, bt, dX, dy, dS), info, allow_notconv)
+
+
+def sdp_newton_resolve(h: int, Ct: int, bt: int, dX: int, dy: int, dS: int, info: sdp_newton_info,
+                       allow_notconv: bool = False) -> int:
+    return _solve("sdp_newton_resolve", h, (Ct, bt, dX, dy, dS), info, allow_notconv)
 
 
 def sdp_grad(h: int, V: int, lam: int, gX: int, gy: int, gC: int, gb: int, info: sdp_newton_info,

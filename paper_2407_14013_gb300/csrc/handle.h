@@ -103,6 +103,9 @@ struct sdp_handle {
   // CUDA graphs of `check_every` PCG iterations (FP64 operator, mixed operator), captured once per shape
   cudaStream_t cap_stream = nullptr;
   wc::Graph graph[2];
+  // the split and preconditioner core of the last solve can serve another right side
+  bool setup_valid = false;
+  wc::PcgCtl setup_ctl{};           // the control block as a2 left it (r, d, tau, beta, s_A)
   // outer interior-point loop (ipm.cu): workspace allocated on first use
   wc::IpmWork* ipm = nullptr;
 };

@@ -309,10 +309,14 @@ sdp_status max_step(Ctx& c, const double* D, double f, double* a, int* sweeps) {
   return SDP_OK;
 }
 
-sdp_status newton(Ctx& c, const double* Ct, const double* bt, double* dX, double* dy, double* dSs, sdp_ipm_info* info) {
+// Newton direction at the current scaling point; `again` reuses the split and preconditioner of
+// the previous call (the corrector has the predictor's scaling point)
+sdp_status newton(Ctx& c, const double* Ct, const double* bt, double* dX, double* dy, double* dSs, sdp_ipm_info* info,
+                  bool again = false) {
   sdp_newton_info ni;
   std::memset(&ni, 0, sizeof(ni));
-  sdp_status s = sdp_newton_solve(c.h, c.w->V, c.w->lam, Ct, bt, dX, dy, dSs, &ni);
+  sdp_status s = again ? sdp_newton_resolve(c.h, Ct, bt, dX, dy, dSs, &ni)
+                       : sdp_newton_solve(c.h, c.w->V, c.w->lam, Ct, bt, dX, dy, dSs, &ni);
   info->pcg_iters += ni.pcg_iters;
   info->newton_ms += ni.setup_ms + ni.pcg_ms + ni.recover_ms;
   if (s == SDP_ENOTCONV) {   // an inexact direction: the outer loop proceeds with it
@@ -498,7 +502,7 @@ sdp_status step(Ctx& c, double* X, double* y, double* S, const Measures& Mz, sdp
   lincomb_kernel<<<nb(nn), IT, 0, c.st>>>(nn, 1.0, w->Rd, -1.0, w->M2, 0.0, nullptr, w->Ct);
   ++*c.L;
   CUI(cudaMemcpyAsync(w->T, w->M2, bytes, cudaMemcpyDeviceToDevice, c.st));    // keep G^{-T} R G^{-1}
-  s = newton(c, w->Ct, w->rp, w->dX, w->dy, w->dSs, info);
+  s = newton(c, w->Ct, w->rp, w->dX, w->dy, w->dSs, info, true);
   if (s != SDP_OK) return s;
   lincomb_kernel<<<nb(nn), IT, 0, c.st>>>(nn, 1.0, w->dSs, 1.0, w->T, 0.0, nullptr, w->dS);  // R_d - A^T dy
   ++*c.L;

@@ -537,11 +537,12 @@ sdp_status pcg_loop(sdp_handle* h, Space& S, bool mixed) {
 
 }  // namespace
 
-extern "C" sdp_status sdp_newton_solve(sdp_handle* h, const double* V, const double* lam, const double* Ct,
-                                       const double* bt, double* dX, double* dy, double* dS,
-                                       sdp_newton_info* info) {
-  if (!h) return fail(nullptr, SDP_EINVAL, "NULL handle");
-  if (!V || !lam || !Ct || !bt || !dX || !dy || !dS) return fail(h, SDP_EINVAL, "NULL array argument");
+namespace {
+
+// One Newton solve; with `reuse` the split and the preconditioner core (a1, a2) of the previous
+// solve on this handle are kept (a second right side at the same scaling point).
+sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, const double* Ct, const double* bt,
+                             double* dX, double* dy, double* dS, sdp_newton_info* info, bool reuse) {
   h->launches = 0;
   const int n = h->n, m = h->m;
   cudaStream_t st = h->st;
@@ -558,6 +559,19 @@ extern "C" sdp_status sdp_newton_solve(sdp_handle* h, const double* V, const dou
     for (auto& e : h->ev_phase) CU(cudaEventCreate(&e));
   CU(cudaEventRecord(h->ev_phase[0], st));
 
+  if (reuse) {
+    // the control block keeps r, d, tau, beta and s_A of the last setup; its counters restart
+    PcgCtl c = h->setup_ctl;
+    c.done = 0;
+    c.iters = 0;
+    c.status = 0;
+    c.max_iters = h->opt.max_pcg;
+    CU(cudaMemcpyAsync(h->ctl, &c, sizeof(PcgCtl), cudaMemcpyHostToDevice, st));
+    CU(cudaEventRecord(h->ev_phase[1], st));
+  }
+  int r = h->r, d = h->d;
+  if (!reuse) {
+  h->setup_valid = false;
   // ---- a1: split ----
   PcgCtl init{};
   init.s_A = h->s_A;
@@ -569,12 +583,12 @@ extern "C" sdp_status sdp_newton_solve(sdp_handle* h, const double* V, const dou
   CU(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
   if (h->ctl_host->status != 0) return fail(h, SDP_EINVAL, "eigenvalues must be positive and finite, 1 <= r < n");
-  const int r = h->ctl_host->r, d = h->ctl_host->d;
+  r = h->ctl_host->r;
+  d = h->ctl_host->d;
   if (r > h->r_max) return fail(h, SDP_EINVAL, "rank above the setup maximum");
   h->r = r;
   h->d = d;
   h->space = h->opt.precond_space == 0 ? (d <= m ? 1 : 2) : h->opt.precond_space;
-  const int nt = m + d;
   split_scale_cols(st, n, S.Vs, h->e, h->Ve, L);
   CU(gemm_f64(st, false, true, n, n, n, 1.0, h->Ve, n, S.Vs, n, 0.0, S.E, n, S.ws, ws, L));
   split_sigma(st, n, r, h->lam_s, h->ctl, S.Dv, L);
@@ -628,6 +642,9 @@ extern "C" sdp_status sdp_newton_solve(sdp_handle* h, const double* V, const dou
     else convert<float, double>(st, (int64_t)n * n, S.E, h->m32.E, L);
   }
   CU(cudaEventRecord(h->ev_phase[1], st));
+  CU(cudaMemcpyAsync(&h->setup_ctl, h->ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
+  }   // !reuse
+  const int nt = m + d;
 
   // ---- a3: right-hand side and start ----
   const double* Q = S.Vs;
@@ -745,9 +762,30 @@ extern "C" sdp_status sdp_newton_solve(sdp_handle* h, const double* V, const dou
     info->prof_At32_launches = (int32_t)h->prof_n[2];
     info->prof_A32_launches = (int32_t)h->prof_n[3];
   }
+  // the split and the preconditioner core stay usable for another right side (sdp_newton_resolve)
+  // unless the factorisation failed
+  h->setup_valid = (c.status != 5);
   if (c.status == 5) return fail(h, SDP_ENUMERIC, "PCG breakdown or non-positive pivot");
   if (c.status == 4 || !(c.rr <= c.tol2)) return fail(h, SDP_ENOTCONV, "PCG did not reach the stopping test");
   return SDP_OK;
+}
+
+}  // namespace
+
+extern "C" sdp_status sdp_newton_solve(sdp_handle* h, const double* V, const double* lam, const double* Ct,
+                                       const double* bt, double* dX, double* dy, double* dS,
+                                       sdp_newton_info* info) {
+  if (!h) return fail(nullptr, SDP_EINVAL, "NULL handle");
+  if (!V || !lam || !Ct || !bt || !dX || !dy || !dS) return fail(h, SDP_EINVAL, "NULL array argument");
+  return newton_solve_impl(h, V, lam, Ct, bt, dX, dy, dS, info, false);
+}
+
+extern "C" sdp_status sdp_newton_resolve(sdp_handle* h, const double* Ct, const double* bt, double* dX, double* dy,
+                                         double* dS, sdp_newton_info* info) {
+  if (!h) return fail(nullptr, SDP_EINVAL, "NULL handle");
+  if (!Ct || !bt || !dX || !dy || !dS) return fail(h, SDP_EINVAL, "NULL array argument");
+  if (!h->setup_valid) return fail(h, SDP_EINVAL, "no previous Newton solve to reuse on this handle");
+  return newton_solve_impl(h, nullptr, nullptr, Ct, bt, dX, dy, dS, info, true);
 }
 
 extern "C" sdp_status sdp_newton_solve_host(sdp_handle* h, const double* V, const double* lam, const double* Ct,

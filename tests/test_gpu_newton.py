@@ -228,3 +228,23 @@ def test_mixed_full_size_sensing200():
     assert i2.prof_A32_launches == i2.pcg_iters + i2.refine_steps       # r0 of each solve + one per iteration
     assert i2.prof_A_launches == i2.refine_steps + 1                    # right side + one residual per correction
     s.close()
+
+
+def test_resolve_reuses_setup():
+    """sdp_newton_resolve (second right side at the same scaling point, a1/a2 reused) gives the
+    direction a fresh solve gives, and refuses to run on a handle without a previous solve."""
+    from paper_2407_14013_gb300 import NewtonSolver, SdpError
+    prob = W.sensing(30, 120, 2, 1701)
+    sp = W.scaling_point(prob.n, 2, 1e-4, 1702)
+    Ct1, bt1 = W.newton_rhs(prob.n, prob.m, 1703)
+    Ct2, bt2 = W.newton_rhs(prob.n, prob.m, 1704)
+    s = NewtonSolver(prob, r_hat=4)
+    with pytest.raises(SdpError):
+        s.resolve(_t(Ct2), _t(bt2))
+    s.solve(_t(sp.V), _t(sp.lam), _t(Ct1), _t(bt1))
+    dX, dy, dS, info = s.resolve(_t(Ct2), _t(bt2))
+    assert info.converged
+    fX, fy, fS, _ = s.solve(_t(sp.V), _t(sp.lam), _t(Ct2), _t(bt2))
+    for a, b in ((dX, fX), (dy, fy), (dS, fS)):
+        assert rel(a.cpu().numpy(), b.cpu().numpy()) < 1e-10
+    s.close()
