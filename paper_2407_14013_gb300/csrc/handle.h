@@ -102,6 +102,11 @@ struct sdp_handle {
   double phase_ms[3] = {0.0, 0.0, 0.0};
   // CUDA graphs of `check_every` PCG iterations (FP64 operator, mixed operator), captured once per shape
   cudaStream_t cap_stream = nullptr;
+  // side streams and events for the independent branches of the operator (also inside capture)
+  cudaStream_t aux[2] = {nullptr, nullptr};
+  cudaEvent_t br_ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double *ws_b[2] = {nullptr, nullptr};   // split-K scratch of the GEMMs on the side streams
+  size_t ws_b_elems = 0;
   wc::Graph graph[2];
   // the split and preconditioner core of the last solve can serve another right side
   bool setup_valid = false;

@@ -173,6 +173,9 @@ size_t carve(sdp_handle* h, char* base) {
   }
   carve_space(h, c, h->s64);
   h->s64.ctl = h->ctl;
+  h->ws_b_elems = 64 * n * rm + 4096;
+  h->ws_b[0] = c.take<double>(h->ws_b_elems);
+  h->ws_b[1] = c.take<double>(h->ws_b_elems);
   if (h->mixed) {
     h->sin = h->s64;
     h->sin.x = c.take<double>(vt);
@@ -267,6 +270,8 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
     return fail(nullptr, SDP_ENOMEM, "pinned allocation failed");
   }
   std::memset(h->ctl_host, 0, sizeof(PcgCtl));
+  for (auto& a : h->aux) CU(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+  for (auto& ev : h->br_ev) CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   CU(cudaMemsetAsync(h->counter, 0, 4 * sizeof(unsigned int), h->st));
   // s_A = ||A||_F^2 / m (beta rule 0); FP32 copy of A for the mixed form
   if (h->kind == SDP_A_DENSE_SVEC) {
@@ -326,6 +331,19 @@ sdp_status prof_collect(sdp_handle* h, size_t first, size_t last, int base, int 
   return SDP_OK;
 }
 
+// Side branch: a stream that starts after everything issued so far on h->st (event fork; inside
+// stream capture the side stream joins the capture), and the join back into h->st.
+cudaStream_t fork(sdp_handle* h, int which, int ev) {
+  cudaEventRecord(h->br_ev[ev], h->st);
+  cudaStreamWaitEvent(h->aux[which], h->br_ev[ev], 0);
+  return h->aux[which];
+}
+
+void join(sdp_handle* h, int which, int ev) {
+  cudaEventRecord(h->br_ev[ev], h->aux[which]);
+  cudaStreamWaitEvent(h->st, h->br_ev[ev], 0);
+}
+
 // Y = A^T(u) as a full n x n matrix (DENSE kind).
 void adjoint_dense(sdp_handle* h, Space& S, const double* u, double* Y, const int32_t* done) {
   prof_begin(h, 0);
@@ -343,16 +361,22 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
   const double* Q = S.Vs;   // first r columns
   const double* pu = pin;
   const double* pv = pin + m;
-  // Up = Vs Hp with Hp = [B_p; sqrt2 N_p]: Q p_v as an n x r factor (Section 5)
-  h_unpack<double>(st, n, r, pv, S.Hp, done, L);
-  CU(gemm_f64(st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, S.ws_elems, L, done));
+  // side branch 0: Up = Vs Hp with Hp = [B_p; sqrt2 N_p], Q p_v as an n x r factor (Section 5),
+  // independent of A^T(p_u)
+  cudaStream_t s0 = fork(h, 0, 0);
+  h_unpack<double>(s0, n, r, pv, S.Hp, done, L);
+  CU(gemm_f64(s0, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, h->ws_b[0], h->ws_b_elems, L, done));
   if (h->kind == SDP_A_DENSE_SVEC) {
     adjoint_dense(h, S, pu, S.Y, done);                                // Y = A^T(p_u)
-    CU(gemm_f64(st, false, false, n, r, n, 1.0, S.Y, n, Q, n, 0.0, S.Tm, n, S.ws, S.ws_elems, L, done));
-    CU(gemm_f64(st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, done));
+    // side branch 1: H = Vs^T (Y Q), beside E Y E on the main stream
+    cudaStream_t s1 = fork(h, 1, 1);
+    CU(gemm_f64(s1, false, false, n, r, n, 1.0, S.Y, n, Q, n, 0.0, S.Tm, n, h->ws_b[1], h->ws_b_elems, L, done));
+    CU(gemm_f64(s1, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, h->ws_b[1], h->ws_b_elems, L, done));
     CU(gemm_f64(st, false, false, n, n, n, 1.0, S.E, n, S.Y, n, 0.0, S.F, n, S.ws, S.ws_elems, L, done));
     CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, S.ws_elems, L, done,
                 GEMM_LOWER));                                          // E Y E is symmetric: lower triangle
+    join(h, 0, 2);
+    join(h, 1, 3);
     svec_pack_plus<double>(st, n, r, S.Z, S.Up, Q, S.zsvec, done, L);    // svec(E Y E + sym(Up Q^T))
     prof_begin(h, 1);
     rows_gemv<double>(st, h->a_dense, m, h->N, S.zsvec, S.partA, done, L);
@@ -363,6 +387,7 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
     launch_diag_scale_rows<double>(st, n, r, pu, S.Vs, S.Tm, done, L);  // A^T(p_u) Q = diag(p_u) Q
     CU(gemm_f64(st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, done));
     rows_gemv<double>(st, S.EE, n, n, pu, S.partA, done, L);              // diag(E diag(p_u) E) = (E o E) p_u
+    join(h, 0, 2);
     launch_ap_finish<double>(st, m, d, n, r, S.partA, rows_gemv_slabs(n, n), S.Up, S.Vs, S.H, S.Dv, pin, gsub, out,
                              mode, S.ctl, h->dotbuf, h->counter, L);
   }
@@ -382,6 +407,10 @@ sdp_status apply_operator_mixed(sdp_handle* h, Space& S, const double* pin, doub
   Mixed32& M = h->m32;
   const double* pu = pin;
   const double* pv = pin + m;
+  // side branch: the FP64 rows with B, beside the FP32 A E A^T chain on the main stream
+  cudaStream_t s0 = fork(h, 0, 0);
+  rows_gemv<double>(s0, S.B, m, d, pv, M.partBv, done, L);                  // B p_v
+  rows_gemv<double>(s0, S.Bt, d, m, pu, M.partBu, done, L);                 // B^T p_u
   launch_to_float(st, m, pu, M.pu, done, L);
   int SA;
   if (h->kind == SDP_A_DENSE_SVEC) {
@@ -400,8 +429,7 @@ sdp_status apply_operator_mixed(sdp_handle* h, Space& S, const double* pin, doub
     rows_gemv<float>(st, M.EE, n, n, M.pu, M.partA, done, L);               // (E o E) p_u
     SA = rows_gemv_slabs(n, n, 4);
   }
-  rows_gemv<double>(st, S.B, m, d, pv, M.partBv, done, L);                  // B p_v
-  rows_gemv<double>(st, S.Bt, d, m, pu, M.partBu, done, L);                 // B^T p_u
+  join(h, 0, 2);
   launch_mixed_finish(st, m, d, M.partA, SA, M.partBv, rows_gemv_slabs(m, d), M.partBu, rows_gemv_slabs(d, m), S.Dv, pin,
                       gsub, out, mode, S.ctl, h->dotbuf, h->counter, L);
   return SDP_OK;
@@ -876,6 +904,10 @@ extern "C" void sdp_destroy(sdp_handle* h) {
   for (auto& G : h->graph)
     if (G.exec) cudaGraphExecDestroy(G.exec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (auto& a : h->aux)
+    if (a) cudaStreamDestroy(a);
+  for (auto& ev : h->br_ev)
+    if (ev) cudaEventDestroy(ev);
   wc_ipm_free(h);
   delete h;
 }
