@@ -72,6 +72,7 @@ struct sdp_handle {
   wc::PcgCtl* ctl_in = nullptr;         // inner solve of the mixed form
   wc::PcgCtl* ctl_host = nullptr;       // pinned mirror
   unsigned int* counter = nullptr;
+  unsigned int* gt_tickets = nullptr;   // per column block of the fused A^T(y) pass
   double *lam_s = nullptr, *e = nullptr, *Ve = nullptr, *Bs = nullptr, *Cw = nullptr, *g = nullptr;
   double *dotbuf = nullptr, *scratch = nullptr;
   double* gj_work = nullptr;

@@ -33,12 +33,25 @@ size_t rows_gemv_part_elems(int64_t rows_max, int64_t L);
 template <typename T>
 void rows_gemv(cudaStream_t st, const T* A, int m, int64_t L, const T* x, T* part, const int32_t* done,
                int64_t* launches);
+// rows_gemv with the vector formed while it is staged: x = base + c * sum_{g < G} xpart[g L + k]
+// with c = c0 / *cdiv (cdiv device pointer, may be NULL: c = c0); x is also stored to xout
+// (may be NULL).  Fuses an elementwise step that would otherwise be its own launch.
+void rows_gemv_formed(cudaStream_t st, const double* A, int m, int64_t L, const double* base, const double* xpart,
+                      int G, double c0, const double* cdiv, double* xout, double* part, const int32_t* done,
+                      int64_t* launches);
 // Partial sums of y = sum_i p_i row_i(A): part[g * L + k] over row groups g; the group count
 // for an m x L matrix of `esize`-byte elements spreads the CTAs evenly over the SMs.
 int rows_gemvT_groups(int m, int64_t L, int esize = 8);
 template <typename T>
 void rows_gemvT(cudaStream_t st, const T* A, int m, int64_t L, const T* p, T* part, int groups,
                 const int32_t* done, int64_t* launches);
+// The same with the partial sums reduced in-kernel (last CTA per column block) and written as
+// the full symmetric n x n matrix Y = scale * smat(sum_g part_g) (L = n(n+1)/2).  tickets: at
+// least rows_gemvT_blocks(L, sizeof(T)) zeroed words (left zero after the call).
+template <typename T>
+void rows_gemvT_unpack(cudaStream_t st, const T* A, int m, int64_t L, const T* p, T* part, int groups, int n,
+                       double scale, T* Y, unsigned int* tickets, const int32_t* done, int64_t* launches);
+int rows_gemvT_blocks(int64_t L, int esize);
 // sum_i ||row_i||^2
 void rows_sumsq(cudaStream_t st, const double* A, int m, int64_t L, double* out, double* scratch,
                 int64_t* launches);

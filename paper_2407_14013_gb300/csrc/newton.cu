@@ -156,6 +156,8 @@ size_t carve(sdp_handle* h, char* base) {
   h->ctl = c.take<PcgCtl>(1);
   h->ctl_in = c.take<PcgCtl>(1);
   h->counter = c.take<unsigned int>(4);
+  // one ticket per column block of the A^T pass (at most one block per 256 columns)
+  h->gt_tickets = c.take<unsigned int>(h->kind == SDP_A_DENSE_SVEC ? (size_t)(h->N + 255) / 256 + 1 : 1);
   h->lam_s = c.take<double>(n);
   h->e = c.take<double>(n);
   h->Ve = c.take<double>(nn);
@@ -347,9 +349,9 @@ void join(sdp_handle* h, int which, int ev) {
 // Y = A^T(u) as a full n x n matrix (DENSE kind).
 void adjoint_dense(sdp_handle* h, Space& S, const double* u, double* Y, const int32_t* done) {
   prof_begin(h, 0);
-  rows_gemvT<double>(h->st, h->a_dense, h->m, h->N, u, S.partY, h->GY, done, &h->launches);
+  rows_gemvT_unpack<double>(h->st, h->a_dense, h->m, h->N, u, S.partY, h->GY, h->n, 1.0, Y, h->gt_tickets, done,
+                            &h->launches);
   prof_end(h);
-  svec_unpack_sum<double>(h->st, h->n, S.partY, h->GY, 1.0, Y, done, &h->launches);
 }
 
 // out = M pin (mode 1 also computes alpha) or out = g - M pin (mode 0, g != NULL), in FP64.
@@ -415,7 +417,9 @@ sdp_status apply_operator_mixed(sdp_handle* h, Space& S, const double* pin, doub
   int SA;
   if (h->kind == SDP_A_DENSE_SVEC) {
     prof_begin(h, 2);
-    rows_gemvT<float>(st, M.A, m, h->N, M.pu, M.partY, h->GY32, done, L);   // A^T(p_u)
+    // A^T(p_u); the FP32 pass has twice the row groups of the FP64 one, and a separate unpack
+    // (all SMs) reduces them faster than the last CTA of each column block would
+    rows_gemvT<float>(st, M.A, m, h->N, M.pu, M.partY, h->GY32, done, L);
     prof_end(h);
     svec_unpack_sum<float>(st, n, M.partY, h->GY32, 1.0, M.Y, done, L);
     CU(gemm_f32(st, false, false, n, n, n, 1.f, M.E, n, M.Y, n, 0.f, M.F, n, M.ws, M.ws_elems, L, done));
@@ -449,10 +453,11 @@ void apply_precond(sdp_handle* h, Space& S, const double* rin, double* zout, int
   const int Sm = rows_gemv_slabs(d, m);   // slabs of the products with the rows of B^T
   if (h->space == 1) {
     rows_gemv<double>(st, S.Bt, d, m, rin, S.partB, done, L);              // B^T r_u (rows of B^T)
-    launch_pc_d_s<double>(st, m, d, Sm, S.partB, rin, S.sd, S.ctl, L);     // s = r_v - beta^{-1} B^T r_u
-    rows_gemv<double>(st, S.Pinv, d, d, S.sd, S.partC, done, L);           // C^{-1} s
-    launch_pc_d_zv<double>(st, m, d, rows_gemv_slabs(d, d), S.partC, zout, S.ctl, L);
-    rows_gemv<double>(st, S.B, m, d, zout + m, S.partA, done, L);          // B z_v
+    // C^{-1} s with s = r_v - beta^{-1} B^T r_u formed while staged
+    rows_gemv_formed(st, S.Pinv, d, d, rin + m, S.partB, Sm, -1.0, &S.ctl->beta_pc, nullptr, S.partC, done, L);
+    // B z_v with z_v = -(C^{-1} s) formed while staged and stored
+    rows_gemv_formed(st, S.B, m, d, nullptr, S.partC, rows_gemv_slabs(d, d), -1.0, nullptr, zout + m, S.partA, done,
+                     L);
     launch_pc_zu_dot<double>(st, m, d, rows_gemv_slabs(m, d), S.partA, 1, rin, zout, mode, S.ctl, h->dotbuf,
                              h->counter, L);
   } else {

@@ -48,10 +48,23 @@ __device__ __forceinline__ float ld1<float>(const float* p, uint64_t pol, bool s
 // One CTA: R rows (warp w takes rows w, w + 8, ...; two at a time for memory-level
 // parallelism) times one slab of SW columns, whose x segment it stages in shared memory.
 // STREAM (a matrix larger than L2) loads A with the evict-first policy.
+// Optional prologue of the GEMV: the vector is formed while it is staged,
+//   x_k = base_k + c * sum_{g < G} xpart[g * L + k],  c = c0 / *cdiv (or c0 when cdiv is NULL),
+// and the CTAs of the first row block also store it to xout (may be NULL).
+template <typename T>
+struct XForm {
+  const T* base;
+  const T* xpart;
+  int G;
+  double c0;
+  const double* cdiv;
+  T* xout;
+};
+
 template <typename T, bool VEC, bool STREAM>
 __global__ void __launch_bounds__(GV_WARPS * 32)
 rows_gemv_kernel(const T* __restrict__ A, int m, int64_t L, const T* __restrict__ x, T* __restrict__ part,
-                 int SW, int R, const int32_t* __restrict__ done) {
+                 int SW, int R, const int32_t* __restrict__ done, XForm<T> xf) {
   if (done && *done) return;
   const uint64_t pol = STREAM ? evict_first_policy() : 0;
   using VT = V16<T>;
@@ -61,7 +74,18 @@ rows_gemv_kernel(const T* __restrict__ A, int m, int64_t L, const T* __restrict_
   const int s = blockIdx.x;
   const int64_t k0 = (int64_t)s * SW;
   const int len = (int)((L - k0) < (int64_t)SW ? (L - k0) : (int64_t)SW);
-  for (int q = threadIdx.x; q < len; q += blockDim.x) xs[q] = x[k0 + q];
+  if (xf.xpart) {
+    const double cc = xf.cdiv ? xf.c0 / *xf.cdiv : xf.c0;
+    for (int q = threadIdx.x; q < len; q += blockDim.x) {
+      double t = 0.0;
+      for (int gg = 0; gg < xf.G; ++gg) t += (double)xf.xpart[(int64_t)gg * L + k0 + q];
+      const T v = (T)((xf.base ? (double)xf.base[k0 + q] : 0.0) + cc * t);
+      xs[q] = v;
+      if (xf.xout && blockIdx.y == 0) xf.xout[k0 + q] = v;
+    }
+  } else {
+    for (int q = threadIdx.x; q < len; q += blockDim.x) xs[q] = x[k0 + q];
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int rbase = blockIdx.y * R;
@@ -169,10 +193,27 @@ rows_gemv_kernel(const T* __restrict__ A, int m, int64_t L, const T* __restrict_
 
 constexpr int GT_THREADS = 256;
 
+// svec position c -> (a, b), a >= b, of the column-major lower triangle of an n x n matrix
+__device__ __forceinline__ void svec_pos(int n, int64_t c, int& a, int& b) {
+  const double t = 2.0 * n + 1.0;
+  int bb = (int)((t - sqrtf((float)(t * t - 8.0 * (double)c))) * 0.5f);
+  if (bb < 0) bb = 0;
+  if (bb > n - 1) bb = n - 1;
+  while (bb > 0 && (int64_t)bb * n - (int64_t)bb * (bb - 1) / 2 > c) --bb;
+  while (bb + 1 < n && (int64_t)(bb + 1) * n - (int64_t)(bb + 1) * bb / 2 <= c) ++bb;
+  b = bb;
+  a = bb + (int)(c - ((int64_t)bb * n - (int64_t)bb * (bb - 1) / 2));
+}
+
+// A^T p over row groups (partial sums part[g * L + c]).  With Y != NULL (UNPACK), the last CTA
+// of each column block to finish (atomic ticket) adds the groups' partials in group order and
+// writes them as the symmetric n x n matrix smat(.) scaled by `scale` (both triangles), so no
+// separate unpack pass is needed.
 template <typename T, bool VEC, bool STREAM>
 __global__ void __launch_bounds__(GT_THREADS)
 rows_gemvT_kernel(const T* __restrict__ A, int m, int64_t L, const T* __restrict__ p,
-                  T* __restrict__ part, int rows_per_group, const int32_t* __restrict__ done) {
+                  T* __restrict__ part, int rows_per_group, const int32_t* __restrict__ done,
+                  int n, double scale, T* __restrict__ Y, unsigned int* __restrict__ tickets) {
   if (done && *done) return;
   const uint64_t pol = STREAM ? evict_first_policy() : 0;
   using VT = V16<T>;
@@ -182,7 +223,7 @@ rows_gemvT_kernel(const T* __restrict__ A, int m, int64_t L, const T* __restrict
   const int i1 = min(m, i0 + rows_per_group);
   if (VEC) {
     const int64_t c = ((int64_t)blockIdx.x * GT_THREADS + threadIdx.x) * W;
-    if (c >= L) return;
+    if (c < L) {
     T a[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) a[k] = 0;
@@ -209,9 +250,10 @@ rows_gemvT_kernel(const T* __restrict__ A, int m, int64_t L, const T* __restrict
     }
 #pragma unroll
     for (int k = 0; k < W; ++k) part[(int64_t)g * L + c + k] = a[k];
+    }
   } else {
     const int64_t c = (int64_t)blockIdx.x * GT_THREADS + threadIdx.x;
-    if (c >= L) return;
+    if (c < L) {
     T a0 = 0;
     int i = i0;
     for (; i + 3 < i1; i += 4) {
@@ -225,7 +267,30 @@ rows_gemvT_kernel(const T* __restrict__ A, int m, int64_t L, const T* __restrict
     }
     for (; i < i1; ++i) a0 = fma(__ldg(p + i), ld1<T>(A + (int64_t)i * L + c, pol, STREAM), a0);
     part[(int64_t)g * L + c] = a0;
+    }
   }
+  if (!Y) return;
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(tickets + blockIdx.x, 1u) == gridDim.y - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int per = VEC ? V16<T>::W : 1;
+  const int64_t c0 = (int64_t)blockIdx.x * GT_THREADS * per;
+  for (int u = threadIdx.x; u < GT_THREADS * per; u += GT_THREADS) {
+    const int64_t c = c0 + u;
+    if (c >= L) break;
+    double sum = 0.0;
+    for (int gg = 0; gg < (int)gridDim.y; ++gg) sum += (double)__ldcg(part + (int64_t)gg * L + c);
+    int a, b;
+    svec_pos(n, c, a, b);
+    const T v = (T)((a == b ? sum : sum * WC_RSQRT2) * scale);
+    Y[a + (int64_t)b * n] = v;
+    Y[b + (int64_t)a * n] = v;
+  }
+  if (threadIdx.x == 0) tickets[blockIdx.x] = 0u;
 }
 
 __global__ void sumsq_kernel(const double* __restrict__ A, int64_t total, double* __restrict__ scratch) {
@@ -313,19 +378,35 @@ size_t rows_gemv_part_elems(int64_t rows_max, int64_t L) {
 }
 
 template <typename T>
-void rows_gemv(cudaStream_t st, const T* A, int m, int64_t L, const T* x, T* part, const int32_t* done,
-               int64_t* launches) {
+void rows_gemv_impl(cudaStream_t st, const T* A, int m, int64_t L, const T* x, T* part, const int32_t* done,
+                    int64_t* launches, XForm<T> xf) {
   const GvPlan P = gv_plan(m, L, (int)sizeof(T));
   dim3 grid(P.slabs, (m + P.R - 1) / P.R);
   const bool vec = is_vec_ok(A, L);
   if (vec) {
-    if (P.stream) rows_gemv_kernel<T, true, true><<<grid, GV_WARPS * 32, 0, st>>>(A, m, L, x, part, P.SW, P.R, done);
-    else rows_gemv_kernel<T, true, false><<<grid, GV_WARPS * 32, 0, st>>>(A, m, L, x, part, P.SW, P.R, done);
+    if (P.stream)
+      rows_gemv_kernel<T, true, true><<<grid, GV_WARPS * 32, 0, st>>>(A, m, L, x, part, P.SW, P.R, done, xf);
+    else
+      rows_gemv_kernel<T, true, false><<<grid, GV_WARPS * 32, 0, st>>>(A, m, L, x, part, P.SW, P.R, done, xf);
   } else {
-    if (P.stream) rows_gemv_kernel<T, false, true><<<grid, GV_WARPS * 32, 0, st>>>(A, m, L, x, part, P.SW, P.R, done);
-    else rows_gemv_kernel<T, false, false><<<grid, GV_WARPS * 32, 0, st>>>(A, m, L, x, part, P.SW, P.R, done);
+    if (P.stream)
+      rows_gemv_kernel<T, false, true><<<grid, GV_WARPS * 32, 0, st>>>(A, m, L, x, part, P.SW, P.R, done, xf);
+    else
+      rows_gemv_kernel<T, false, false><<<grid, GV_WARPS * 32, 0, st>>>(A, m, L, x, part, P.SW, P.R, done, xf);
   }
   if (launches) ++*launches;
+}
+
+template <typename T>
+void rows_gemv(cudaStream_t st, const T* A, int m, int64_t L, const T* x, T* part, const int32_t* done,
+               int64_t* launches) {
+  rows_gemv_impl<T>(st, A, m, L, x, part, done, launches, XForm<T>{nullptr, nullptr, 0, 0.0, nullptr, nullptr});
+}
+
+void rows_gemv_formed(cudaStream_t st, const double* A, int m, int64_t L, const double* base, const double* xpart,
+                      int G, double c0, const double* cdiv, double* xout, double* part, const int32_t* done,
+                      int64_t* launches) {
+  rows_gemv_impl<double>(st, A, m, L, nullptr, part, done, launches, XForm<double>{base, xpart, G, c0, cdiv, xout});
 }
 
 int rows_gemvT_groups(int m, int64_t L, int esize) {
@@ -344,21 +425,43 @@ int rows_gemvT_groups(int m, int64_t L, int esize) {
 }
 
 template <typename T>
-void rows_gemvT(cudaStream_t st, const T* A, int m, int64_t L, const T* p, T* part, int groups,
-                const int32_t* done, int64_t* launches) {
+void rows_gemvT_impl(cudaStream_t st, const T* A, int m, int64_t L, const T* p, T* part, int groups,
+                     const int32_t* done, int64_t* launches, int n, double scale, T* Y, unsigned int* tickets) {
   const int rpg = (m + groups - 1) / groups;
   const bool stream = (int64_t)m * L * (int64_t)sizeof(T) > (int64_t)64 << 20;
   if (is_vec_ok(A, L)) {
     constexpr int W = V16<T>::W;
     dim3 grid((unsigned)((L + W * GT_THREADS - 1) / (W * GT_THREADS)), groups);
-    if (stream) rows_gemvT_kernel<T, true, true><<<grid, GT_THREADS, 0, st>>>(A, m, L, p, part, rpg, done);
-    else rows_gemvT_kernel<T, true, false><<<grid, GT_THREADS, 0, st>>>(A, m, L, p, part, rpg, done);
+    if (stream)
+      rows_gemvT_kernel<T, true, true><<<grid, GT_THREADS, 0, st>>>(A, m, L, p, part, rpg, done, n, scale, Y, tickets);
+    else
+      rows_gemvT_kernel<T, true, false><<<grid, GT_THREADS, 0, st>>>(A, m, L, p, part, rpg, done, n, scale, Y, tickets);
   } else {
     dim3 grid((unsigned)((L + GT_THREADS - 1) / GT_THREADS), groups);
-    if (stream) rows_gemvT_kernel<T, false, true><<<grid, GT_THREADS, 0, st>>>(A, m, L, p, part, rpg, done);
-    else rows_gemvT_kernel<T, false, false><<<grid, GT_THREADS, 0, st>>>(A, m, L, p, part, rpg, done);
+    if (stream)
+      rows_gemvT_kernel<T, false, true><<<grid, GT_THREADS, 0, st>>>(A, m, L, p, part, rpg, done, n, scale, Y, tickets);
+    else
+      rows_gemvT_kernel<T, false, false><<<grid, GT_THREADS, 0, st>>>(A, m, L, p, part, rpg, done, n, scale, Y,
+                                                                     tickets);
   }
   if (launches) ++*launches;
+}
+
+template <typename T>
+void rows_gemvT(cudaStream_t st, const T* A, int m, int64_t L, const T* p, T* part, int groups,
+                const int32_t* done, int64_t* launches) {
+  rows_gemvT_impl<T>(st, A, m, L, p, part, groups, done, launches, 0, 1.0, nullptr, nullptr);
+}
+
+template <typename T>
+void rows_gemvT_unpack(cudaStream_t st, const T* A, int m, int64_t L, const T* p, T* part, int groups, int n,
+                       double scale, T* Y, unsigned int* tickets, const int32_t* done, int64_t* launches) {
+  rows_gemvT_impl<T>(st, A, m, L, p, part, groups, done, launches, n, scale, Y, tickets);
+}
+
+int rows_gemvT_blocks(int64_t L, int esize) {
+  const int64_t W = 16 / esize;
+  return (int)((L + W * GT_THREADS - 1) / (W * GT_THREADS));
 }
 
 template void rows_gemv<double>(cudaStream_t, const double*, int, int64_t, const double*, double*, const int32_t*,
@@ -369,6 +472,10 @@ template void rows_gemvT<double>(cudaStream_t, const double*, int, int64_t, cons
                                  const int32_t*, int64_t*);
 template void rows_gemvT<float>(cudaStream_t, const float*, int, int64_t, const float*, float*, int, const int32_t*,
                                 int64_t*);
+template void rows_gemvT_unpack<double>(cudaStream_t, const double*, int, int64_t, const double*, double*, int, int,
+                                        double, double*, unsigned int*, const int32_t*, int64_t*);
+template void rows_gemvT_unpack<float>(cudaStream_t, const float*, int, int64_t, const float*, float*, int, int,
+                                       double, float*, unsigned int*, const int32_t*, int64_t*);
 
 void rows_sumsq(cudaStream_t st, const double* A, int m, int64_t L, double* out, double* scratch,
                 int64_t* launches) {
