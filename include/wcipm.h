@@ -60,7 +60,14 @@ typedef enum {
 typedef enum {
   SDP_A_DIAG = 0,        /* A_i = e_i e_i^T, m = n: A(X) = diag(X)                               */
   SDP_A_SPARSE_COO = 1,  /* entries (con, row, col, val), row >= col, sorted by con (ascending):
-                            <A_i, X> = sum over entries of con i of val * X[row,col] * (row==col ? 1 : 2) */
+                            <A_i, X> = sum over entries of con i of val * X[row,col] * (row==col ? 1 : 2).
+                            Repeated positions within a constraint add up.  sdp_setup copies the
+                            entries to the host once, validates them (EINVAL: an unsorted or
+                            out-of-range con, col > row, row >= n, a non-finite val, a constraint
+                            with no entry, nnz < 1 or nnz > 2^31 - 1) and uploads two index tables
+                            into the workspace (entries by constraint, entries by position); the
+                            handle keeps reading the caller's four arrays.  SDP_MIXED_FP32 is not
+                            built for this kind (EUNSUPPORTED).                                    */
   SDP_A_DENSE_SVEC = 2   /* a_dense: m x n(n+1)/2 row-major, row i = svec(A_i): lower triangle
                             column by column, off-diagonal entries times sqrt(2) (Notations)     */
 } sdp_a_kind;

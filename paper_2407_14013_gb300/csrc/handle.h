@@ -9,6 +9,7 @@
 
 #include "../../include/wcipm.h"
 #include "common.cuh"
+#include "kernels.h"
 
 namespace wc {
 
@@ -60,6 +61,8 @@ struct sdp_handle {
   int64_t nnz = 0, N = 0;
   const int32_t *a_con = nullptr, *a_row = nullptr, *a_col = nullptr;
   const double *a_val = nullptr, *a_dense = nullptr;
+  wc::SparseA sp;                   // SPARSE_COO: the entries and the index tables built at setup
+  std::vector<double> sp_rownorm2;  // SPARSE_COO: ||A_i||_F^2 (start point of the outer loop)
   sdp_options opt{};
   bool mixed = false;
   cudaStream_t st = nullptr;

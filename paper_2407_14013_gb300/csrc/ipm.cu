@@ -217,6 +217,8 @@ void adjoint(Ctx& c, const double* y, double* Y) {
   if (h->kind == SDP_A_DENSE_SVEC) {
     rows_gemvT<double>(c.st, h->a_dense, c.m, h->N, y, c.w->partY, h->GY, nullptr, c.L);
     svec_unpack_sum<double>(c.st, c.n, c.w->partY, h->GY, 1.0, Y, nullptr, c.L);
+  } else if (h->kind == SDP_A_SPARSE_COO) {
+    sparse_adjoint(c.st, h->sp, c.n, y, 1.0, Y, nullptr, c.L);   // Y is zero off the pattern
   } else {
     launch_diag_matrix(c.st, c.n, y, Y, c.L);
   }
@@ -229,6 +231,9 @@ void residual_p(Ctx& c, const double* b, const double* X) {
     svec_pack_plus<double>(c.st, c.n, 0, X, nullptr, nullptr, c.w->zsvec, nullptr, c.L);
     rows_gemv<double>(c.st, h->a_dense, c.m, h->N, c.w->zsvec, c.w->partA, nullptr, c.L);
     rp_kernel<<<nb(c.m), IT, 0, c.st>>>(c.m, c.n, b, c.w->partA, rows_gemv_slabs(c.m, h->N), c.w->Ax, c.w->rp);
+  } else if (h->kind == SDP_A_SPARSE_COO) {
+    sparse_apply(c.st, h->sp, c.n, c.m, 0, X, nullptr, nullptr, c.w->partA, nullptr, c.L);
+    rp_kernel<<<nb(c.m), IT, 0, c.st>>>(c.m, c.n, b, c.w->partA, 1, c.w->Ax, c.w->rp);
   } else {
     rp_kernel<<<nb(c.m), IT, 0, c.st>>>(c.m, c.n, b, X, -1, c.w->Ax, c.w->rp);
   }
@@ -356,6 +361,8 @@ sdp_status ensure_workspace(sdp_handle* h) {
     plan.push_back({&w->zsvec, (size_t)h->N});
     plan.push_back({&w->partY, (size_t)h->GY * h->N});
     plan.push_back({&w->partA, rows_gemv_part_elems(m, h->N)});
+  } else if (h->kind == SDP_A_SPARSE_COO) {
+    plan.push_back({&w->partA, (size_t)m});
   }
   std::vector<size_t> at;
   for (auto& p : plan) at.push_back(take(p.second));
@@ -370,6 +377,14 @@ sdp_status ensure_workspace(sdp_handle* h) {
   double* base = reinterpret_cast<double*>(w->pool);
   for (size_t k = 0; k < plan.size(); ++k) *plan[k].first = base + at[k];
   w->status = reinterpret_cast<int32_t*>(base + status_at);
+  // A^T(y) of the SPARSE_COO kind writes only the pattern: the rest of Y stays zero
+  e = cudaMemsetAsync(w->Y, 0, nn * sizeof(double), h->st);
+  if (e != cudaSuccess) {
+    cudaFree(w->pool);
+    delete w;
+    return wc_fail(h, SDP_ECUDA, std::string("clearing the interior-point workspace failed: ") +
+                                     cudaGetErrorString(e));
+  }
   h->ipm = w;
   return SDP_OK;
 }
@@ -531,7 +546,7 @@ sdp_status step(Ctx& c, double* X, double* y, double* S, const Measures& Mz, sdp
 sdp_status check_args(sdp_handle* h, const double* b, const double* C, double* X, double* y, double* S) {
   if (!h) return wc_fail(nullptr, SDP_EINVAL, "NULL handle");
   if (!b || !C || !X || !y || !S) return wc_fail(h, SDP_EINVAL, "NULL array argument");
-  if (h->kind != SDP_A_DENSE_SVEC && h->kind != SDP_A_DIAG)
+  if (h->kind != SDP_A_DENSE_SVEC && h->kind != SDP_A_DIAG && h->kind != SDP_A_SPARSE_COO)
     return wc_fail(h, SDP_EUNSUPPORTED, "constraint kind not built");
   return ensure_workspace(h);
 }
@@ -606,7 +621,8 @@ extern "C" sdp_status sdp_solve(sdp_handle* h, const double* b, const double* C,
   CUI(cudaStreamSynchronize(h->st));
   double xi = std::max(10.0, std::sqrt((double)n));
   for (int i = 0; i < m; ++i) {
-    const double an = (h->kind == SDP_A_DENSE_SVEC) ? std::sqrt(rn[i]) : 1.0;
+    const double an = (h->kind == SDP_A_DENSE_SVEC) ? std::sqrt(rn[i])
+                      : (h->kind == SDP_A_SPARSE_COO) ? std::sqrt(h->sp_rownorm2[i]) : 1.0;
     xi = std::max(xi, (1.0 + std::fabs(bh[i])) / (1.0 + an));
   }
   xi = std::max(xi, (1.0 + std::sqrt(cc)) / std::sqrt((double)n));

@@ -112,6 +112,29 @@ cudaError_t gemm_f32(cudaStream_t st, bool tA, bool tB, int M, int N, int K, flo
 template <typename To, typename From>
 void convert(cudaStream_t st, int64_t count, const From* src, To* dst, int64_t* launches);
 
+// ---- sparse.cu: SDP_A_SPARSE_COO operators ------------------------------------------------------
+// The caller's entries (con, row, col, val; sorted by con, row >= col) plus the index tables
+// sdp_setup builds: con_ptr (m + 1) and the entries grouped by position (pos_r, pos_c,
+// pos_ptr (npos + 1), perm (nnz): entry indices in position order).
+struct SparseA {
+  int64_t nnz = 0;
+  int npos = 0;
+  const int32_t *con = nullptr, *row = nullptr, *col = nullptr;
+  const double* val = nullptr;
+  int32_t *con_ptr = nullptr, *pos_r = nullptr, *pos_c = nullptr, *pos_ptr = nullptr, *perm = nullptr;
+};
+// Y = scale * A^T(y) on the pattern positions (both triangles); Y is zero elsewhere already.
+void sparse_adjoint(cudaStream_t st, const SparseA& S, int n, const double* y, double scale, double* Y,
+                    const int32_t* done, int64_t* launches);
+// out[i] = <A_i, Z + sym(U Q^T)>, Z symmetric with its lower triangle read, U may be NULL.
+void sparse_apply(cudaStream_t st, const SparseA& S, int n, int m, int r, const double* Z, const double* U,
+                  const double* Q, double* out, const int32_t* done, int64_t* launches);
+// B = A Q (m x d row-major, ld ldB) and B^T (d x m, ld ldBt) in h-coordinates.
+void sparse_B(cudaStream_t st, const SparseA& S, int n, int m, int r, const double* Vs, double* B, int64_t ldB,
+              double* Bt, int64_t ldBt, int64_t* launches);
+// *out = sum_i ||A_i||_F^2; scratch holds 2 * g_num_sms doubles.
+void sparse_sumsq(cudaStream_t st, const SparseA& S, double* out, double* scratch, int64_t* launches);
+
 // ---- spd_inverse.cu ----------------------------------------------------------------------------
 // In-place inverse of an SPD matrix (n x n, column-major, ld = n) through its Cholesky factor;
 // work must hold spd_inverse_work(n) doubles.

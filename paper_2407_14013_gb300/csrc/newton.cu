@@ -167,6 +167,13 @@ size_t carve(sdp_handle* h, char* base) {
   h->dotbuf = c.take<double>(1024);
   h->scratch = c.take<double>(8192);
   h->gj_work_elems = spd_inverse_work(h->pinv_dim);
+  if (h->kind == SDP_A_SPARSE_COO) {
+    h->sp.con_ptr = c.take<int32_t>(m + 1);
+    h->sp.pos_r = c.take<int32_t>(h->sp.npos);
+    h->sp.pos_c = c.take<int32_t>(h->sp.npos);
+    h->sp.pos_ptr = c.take<int32_t>(h->sp.npos + 1);
+    h->sp.perm = c.take<int32_t>(h->sp.nnz);
+  }
   h->gj_work = c.take<double>(h->gj_work_elems);
   if (h->kind == SDP_A_DENSE_SVEC) {
     h->ubatch = c.take<double>((size_t)h->mb * nn);
@@ -209,8 +216,14 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   if (opt_in) opt = *opt_in; else sdp_default_options(&opt);
   const int n = prob->n, m = prob->m;
   if (n < 2 || m < 1) return fail(nullptr, SDP_EINVAL, "need n >= 2 and m >= 1");
-  if (prob->kind != SDP_A_DIAG && prob->kind != SDP_A_DENSE_SVEC)
-    return fail(nullptr, SDP_EUNSUPPORTED, "constraint kind not built");
+  if (prob->kind != SDP_A_DIAG && prob->kind != SDP_A_DENSE_SVEC && prob->kind != SDP_A_SPARSE_COO)
+    return fail(nullptr, SDP_EINVAL, "unknown constraint kind");
+  if (prob->kind == SDP_A_SPARSE_COO) {
+    if (prob->nnz < 1 || prob->nnz > INT32_MAX || !prob->a_con || !prob->a_row || !prob->a_col || !prob->a_val)
+      return fail(nullptr, SDP_EINVAL, "SPARSE_COO needs 1 <= nnz < 2^31 and all four entry arrays");
+    if (opt_in && opt_in->precision == SDP_MIXED_FP32)
+      return fail(nullptr, SDP_EUNSUPPORTED, "the mixed form is built for the DIAG and DENSE_SVEC kinds");
+  }
   if (prob->kind == SDP_A_DIAG && m != n) return fail(nullptr, SDP_EINVAL, "DIAG kind needs m == n");
   if (prob->kind == SDP_A_DENSE_SVEC && !prob->a_dense) return fail(nullptr, SDP_EINVAL, "a_dense is NULL");
   if (opt.precision != SDP_FP64 && opt.precision != SDP_MIXED_FP32)
@@ -224,8 +237,58 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   if (opt.precond_space < 0 || opt.precond_space > 2) return fail(nullptr, SDP_EINVAL, "bad precond_space");
   if (opt.pcg_start < 0 || opt.pcg_start > 1) return fail(nullptr, SDP_EINVAL, "bad pcg_start");
 
+  // SPARSE_COO: validate the entries and build the index tables on the host (once per problem)
+  std::vector<int32_t> sp_con_ptr, sp_pos_r, sp_pos_c, sp_pos_ptr, sp_perm;
+  std::vector<double> sp_rownorm2;
+  if (prob->kind == SDP_A_SPARSE_COO) {
+    const int64_t nnz = prob->nnz;
+    std::vector<int32_t> con(nnz), row(nnz), col(nnz);
+    std::vector<double> val(nnz);
+    if (cudaMemcpy(con.data(), prob->a_con, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(row.data(), prob->a_row, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(col.data(), prob->a_col, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(val.data(), prob->a_val, nnz * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(nullptr, SDP_ECUDA, "reading the sparse entries failed");
+    sp_con_ptr.assign(m + 1, 0);
+    sp_rownorm2.assign(m, 0.0);
+    for (int64_t e = 0; e < nnz; ++e) {
+      if (con[e] < 0 || con[e] >= m || (e > 0 && con[e] < con[e - 1]))
+        return fail(nullptr, SDP_EINVAL, "a_con must be nondecreasing and in [0, m)");
+      if (col[e] < 0 || row[e] < col[e] || row[e] >= n)
+        return fail(nullptr, SDP_EINVAL, "entries need 0 <= a_col <= a_row < n");
+      if (!std::isfinite(val[e])) return fail(nullptr, SDP_EINVAL, "non-finite a_val");
+      sp_con_ptr[con[e] + 1] += 1;
+      sp_rownorm2[con[e]] += val[e] * val[e] * (row[e] == col[e] ? 1.0 : 2.0);
+    }
+    for (int i = 0; i < m; ++i) {
+      if (sp_con_ptr[i + 1] == 0) return fail(nullptr, SDP_EINVAL, "every constraint needs at least one entry");
+      sp_con_ptr[i + 1] += sp_con_ptr[i];
+    }
+    sp_perm.resize(nnz);
+    for (int64_t e = 0; e < nnz; ++e) sp_perm[e] = (int32_t)e;
+    auto key = [&](int32_t e) { return (int64_t)col[e] * n + row[e]; };
+    std::stable_sort(sp_perm.begin(), sp_perm.end(), [&](int32_t a, int32_t b) { return key(a) < key(b); });
+    for (int64_t k = 0; k < nnz; ++k) {
+      if (k == 0 || key(sp_perm[k]) != key(sp_perm[k - 1])) {
+        sp_pos_r.push_back(row[sp_perm[k]]);
+        sp_pos_c.push_back(col[sp_perm[k]]);
+        sp_pos_ptr.push_back((int32_t)k);
+      }
+    }
+    sp_pos_ptr.push_back((int32_t)nnz);
+  }
+
   h = new (std::nothrow) sdp_handle();
   if (!h) return fail(nullptr, SDP_ENOMEM, "host allocation failed");
+  if (prob->kind == SDP_A_SPARSE_COO) {
+    h->sp.nnz = prob->nnz;
+    h->sp.npos = (int)sp_pos_r.size();
+    h->sp.con = prob->a_con;
+    h->sp.row = prob->a_row;
+    h->sp.col = prob->a_col;
+    h->sp.val = prob->a_val;
+    h->sp_rownorm2 = sp_rownorm2;
+  }
   h->n = n; h->m = m; h->kind = prob->kind; h->nnz = prob->nnz;
   h->a_con = prob->a_con; h->a_row = prob->a_row; h->a_col = prob->a_col; h->a_val = prob->a_val;
   h->a_dense = prob->a_dense;
@@ -258,12 +321,21 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
     return fail(nullptr, SDP_ENOMEM, std::string("cudaMalloc of workspace failed: ") + cudaGetErrorString(e));
   }
   carve(h, h->pool);
-  // zero workspace: the split-K tickets of the GEMMs must start at zero
+  // zero workspace: the split-K tickets of the GEMMs must start at zero (and, for SPARSE_COO,
+  // the n x n matrices that A^T(y) fills only on the pattern)
   e = cudaMemsetAsync(h->pool, 0, h->pool_bytes, h->st);
   if (e != cudaSuccess) {
     cudaFree(h->pool);
     delete h;
     return fail(nullptr, SDP_ECUDA, std::string("workspace clear failed: ") + cudaGetErrorString(e));
+  }
+  if (h->kind == SDP_A_SPARSE_COO) {
+    const size_t b32 = sizeof(int32_t);
+    CU(cudaMemcpyAsync(h->sp.con_ptr, sp_con_ptr.data(), sp_con_ptr.size() * b32, cudaMemcpyHostToDevice, h->st));
+    CU(cudaMemcpyAsync(h->sp.pos_r, sp_pos_r.data(), sp_pos_r.size() * b32, cudaMemcpyHostToDevice, h->st));
+    CU(cudaMemcpyAsync(h->sp.pos_c, sp_pos_c.data(), sp_pos_c.size() * b32, cudaMemcpyHostToDevice, h->st));
+    CU(cudaMemcpyAsync(h->sp.pos_ptr, sp_pos_ptr.data(), sp_pos_ptr.size() * b32, cudaMemcpyHostToDevice, h->st));
+    CU(cudaMemcpyAsync(h->sp.perm, sp_perm.data(), sp_perm.size() * b32, cudaMemcpyHostToDevice, h->st));
   }
   e = cudaMallocHost(&h->ctl_host, sizeof(PcgCtl));
   if (e != cudaSuccess) {
@@ -287,6 +359,12 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
       return fail(nullptr, SDP_EINVAL, "A has a zero or non-finite Frobenius norm");
     }
     if (h->mixed) convert<float, double>(h->st, (int64_t)m * h->N, h->a_dense, h->m32.A, &h->launches);
+  } else if (h->kind == SDP_A_SPARSE_COO) {
+    sparse_sumsq(h->st, h->sp, h->dotbuf, h->scratch, &h->launches);
+    double tot = 0.0;
+    CU(cudaMemcpyAsync(&tot, h->dotbuf, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CU(cudaStreamSynchronize(h->st));
+    h->s_A = tot / m;
   } else {
     h->s_A = 1.0;
   }
@@ -384,6 +462,19 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
     rows_gemv<double>(st, h->a_dense, m, h->N, S.zsvec, S.partA, done, L);
     prof_end(h);
     launch_ap_finish<double>(st, m, d, n, r, S.partA, h->SA, nullptr, S.Vs, S.H, S.Dv, pin, gsub, out, mode, S.ctl,
+                             h->dotbuf, h->counter, L);
+  } else if (h->kind == SDP_A_SPARSE_COO) {
+    sparse_adjoint(st, h->sp, n, pu, 1.0, S.Y, done, L);               // Y = A^T(p_u) on the pattern
+    cudaStream_t s1 = fork(h, 1, 1);
+    CU(gemm_f64(s1, false, false, n, r, n, 1.0, S.Y, n, Q, n, 0.0, S.Tm, n, h->ws_b[1], h->ws_b_elems, L, done));
+    CU(gemm_f64(s1, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, h->ws_b[1], h->ws_b_elems, L, done));
+    CU(gemm_f64(st, false, false, n, n, n, 1.0, S.E, n, S.Y, n, 0.0, S.F, n, S.ws, S.ws_elems, L, done));
+    CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, S.ws_elems, L, done,
+                GEMM_LOWER));
+    join(h, 0, 2);
+    join(h, 1, 3);
+    sparse_apply(st, h->sp, n, m, r, S.Z, S.Up, Q, S.partA, done, L);     // A(E Y E + sym(Up Q^T))
+    launch_ap_finish<double>(st, m, d, n, r, S.partA, 1, nullptr, S.Vs, S.H, S.Dv, pin, gsub, out, mode, S.ctl,
                              h->dotbuf, h->counter, L);
   } else {
     launch_diag_scale_rows<double>(st, n, r, pu, S.Vs, S.Tm, done, L);  // A^T(p_u) Q = diag(p_u) Q
@@ -649,6 +740,8 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
         h_pack_rows(st, n, r, mb, i0, h->Hb, S.B, d, S.Bt, m, L);
       }
     }
+  } else if (h->kind == SDP_A_SPARSE_COO) {
+    sparse_B(st, h->sp, n, m, r, S.Vs, S.B, d, S.Bt, m, L);
   } else {
     launch_hadamard_sq(st, (int64_t)n * n, S.E, S.EE, L);
     h_pack_rows_diag(st, n, r, S.Vs, S.B, d, S.Bt, m, L);
@@ -691,6 +784,11 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     rows_gemv<double>(st, h->a_dense, m, h->N, S.zsvec, S.partA, nullptr, L);
     prof_end(h);
     launch_rhs_finish(st, m, d, n, r, S.partA, h->SA, nullptr, nullptr, bt, Ct, S.H, S.Dv, h->g, S.x,
+                      h->opt.newton_rtol, h->ctl, h->dotbuf, h->counter, L);
+  } else if (h->kind == SDP_A_SPARSE_COO) {
+    CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, ws, L, nullptr, GEMM_LOWER));
+    sparse_apply(st, h->sp, n, m, r, S.Z, nullptr, nullptr, S.partA, nullptr, L);   // A(E C~ E)
+    launch_rhs_finish(st, m, d, n, r, S.partA, 1, nullptr, nullptr, bt, Ct, S.H, S.Dv, h->g, S.x,
                       h->opt.newton_rtol, h->ctl, h->dotbuf, h->counter, L);
   } else {
     launch_rhs_finish(st, m, d, n, r, nullptr, 0, S.F, S.E, bt, Ct, S.H, S.Dv, h->g, S.x, h->opt.newton_rtol,
@@ -748,6 +846,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   const double* u = S.x;
   const double* v = S.x + m;
   if (h->kind == SDP_A_DENSE_SVEC) adjoint_dense(h, S, u, S.Y, nullptr);
+  else if (h->kind == SDP_A_SPARSE_COO) sparse_adjoint(st, h->sp, n, u, 1.0, S.Y, nullptr, L);
   else launch_diag_matrix(st, n, u, S.Y, L);
   launch_recover_pre(st, n, m, S.Y, Ct, u, h->Cw, dy, dS, h->ctl, L);
   CU(gemm_f64(st, false, false, n, n, n, 1.0, S.E, n, h->Cw, n, 0.0, S.F, n, S.ws, ws, L));

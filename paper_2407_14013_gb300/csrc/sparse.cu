@@ -1,0 +1,162 @@
+// Sparse constraint operators (SDP_A_SPARSE_COO): A_i = sum over its entries e of
+// val_e (e_r e_c^T + e_c e_r^T) for r > c, val_e e_r e_r^T for r = c, so that
+// <A_i, X> = sum_e val_e X[r, c] (2 if r != c) (eq. sdp-pd with A given by its entries; matrix
+// completion samples one off-diagonal entry per constraint).
+//
+// The entries arrive sorted by constraint; sdp_setup adds two index tables (built once per
+// problem): con_ptr (the entries of constraint i are con_ptr[i] .. con_ptr[i+1]-1) and the
+// entries grouped by matrix position (pos_r, pos_c, pos_ptr, perm), so that
+//   A(Z):     one thread per constraint sums its entries          (a gather, no atomics)
+//   A^T(y):   one thread per distinct position sums its entries   (fixed order, no atomics)
+// both deterministic.  A^T(y) writes only the positions of the pattern; every other entry of
+// the output matrix must already be zero (the callers zero it once).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace wc {
+
+namespace {
+
+constexpr int ST = 256;
+
+inline unsigned nb(int64_t total) { return (unsigned)((total + ST - 1) / ST); }
+
+// Y[r, c] = Y[c, r] = sum over the entries e at position (r, c) of y[con_e] val_e (times scale)
+__global__ void sparse_adjoint_kernel(int n, int npos, const int32_t* __restrict__ pos_r,
+                                      const int32_t* __restrict__ pos_c, const int32_t* __restrict__ pos_ptr,
+                                      const int32_t* __restrict__ perm, const int32_t* __restrict__ con,
+                                      const double* __restrict__ val, const double* __restrict__ y, double scale,
+                                      double* __restrict__ Y, const int32_t* __restrict__ done) {
+  if (done && *done) return;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npos) return;
+  double s = 0.0;
+  for (int k = pos_ptr[p]; k < pos_ptr[p + 1]; ++k) {
+    const int e = perm[k];
+    s = fma(y[con[e]], val[e], s);
+  }
+  s *= scale;
+  const int r = pos_r[p], c = pos_c[p];
+  Y[r + (int64_t)c * n] = s;
+  Y[c + (int64_t)r * n] = s;
+}
+
+// out[i] = <A_i, Z + sym(U Q^T)> for the symmetric Z (lower triangle read) and U, Q n x r
+// (U may be NULL)
+__global__ void sparse_apply_kernel(int n, int m, int r, const int32_t* __restrict__ con_ptr,
+                                    const int32_t* __restrict__ row, const int32_t* __restrict__ col,
+                                    const double* __restrict__ val, const double* __restrict__ Z,
+                                    const double* __restrict__ U, const double* __restrict__ Q,
+                                    double* __restrict__ out, const int32_t* __restrict__ done) {
+  if (done && *done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double s = 0.0;
+  for (int e = con_ptr[i]; e < con_ptr[i + 1]; ++e) {
+    const int a = row[e], b = col[e];   // a >= b
+    double z = Z[a + (int64_t)b * n];
+    if (U) {
+      double t = 0.0;
+      for (int k = 0; k < r; ++k)
+        t += U[a + (int64_t)k * n] * Q[b + (int64_t)k * n] + Q[a + (int64_t)k * n] * U[b + (int64_t)k * n];
+      z += 0.5 * t;
+    }
+    s = fma(val[e] * (a == b ? 1.0 : 2.0), z, s);
+  }
+  out[i] = s;
+}
+
+// Row i of B = A Q in h-coordinates: B[i, h] = pack(Vs^T A_i Q)[h] with
+// (Vs^T A_i Q)[k, j] = sum_e val_e (Vs[r,k] Q[c,j] + Vs[c,k] Q[r,j])  (one term when r = c)
+__device__ __forceinline__ double sparse_H(int n, int k, int j, int e0, int e1, const int32_t* __restrict__ row,
+                                           const int32_t* __restrict__ col, const double* __restrict__ val,
+                                           const double* __restrict__ Vs) {
+  double s = 0.0;
+  for (int e = e0; e < e1; ++e) {
+    const int a = row[e], b = col[e];
+    double t = Vs[a + (int64_t)k * n] * Vs[b + (int64_t)j * n];
+    if (a != b) t += Vs[b + (int64_t)k * n] * Vs[a + (int64_t)j * n];
+    s = fma(val[e], t, s);
+  }
+  return s;
+}
+
+__global__ void sparse_B_kernel(int n, int m, int r, const int32_t* __restrict__ con_ptr,
+                                const int32_t* __restrict__ row, const int32_t* __restrict__ col,
+                                const double* __restrict__ val, const double* __restrict__ Vs, double* __restrict__ B,
+                                int64_t ldB, double* __restrict__ Bt, int64_t ldBt) {
+  const int d = n * r - r * (r - 1) / 2;
+  const int nb_ = r * (r + 1) / 2;
+  const int64_t total = (int64_t)m * d;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(q / d), h = (int)(q % d);
+    const int e0 = con_ptr[i], e1 = con_ptr[i + 1];
+    double v;
+    if (h < nb_) {
+      int j = 0, base = 0;
+      while (h >= base + (r - j)) { base += r - j; ++j; }
+      const int a = j + (h - base);
+      if (a == j) v = sparse_H(n, a, a, e0, e1, row, col, val, Vs);
+      else v = WC_SQRT2 * 0.5 * (sparse_H(n, a, j, e0, e1, row, col, val, Vs) + sparse_H(n, j, a, e0, e1, row, col, val, Vs));
+    } else {
+      const int qq = h - nb_;
+      const int k = qq % (n - r), j = qq / (n - r);
+      v = WC_SQRT2 * sparse_H(n, r + k, j, e0, e1, row, col, val, Vs);
+    }
+    B[(int64_t)i * ldB + h] = v;
+    if (Bt) Bt[(int64_t)h * ldBt + i] = v;
+  }
+}
+
+// sum_i ||A_i||_F^2 = sum_e val_e^2 (2 if off-diagonal), per-block partials then one block
+__global__ void sparse_sumsq_kernel(int64_t nnz, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
+                                    const double* __restrict__ val, double* __restrict__ part) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+    acc = fma(val[e] * val[e], row[e] == col[e] ? 1.0 : 2.0, acc);
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void sum_parts_kernel(const double* __restrict__ part, int np, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int q = threadIdx.x; q < np; q += blockDim.x) acc += part[q];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) *out = acc;
+}
+
+}  // namespace
+
+void sparse_adjoint(cudaStream_t st, const SparseA& S, int n, const double* y, double scale, double* Y,
+                    const int32_t* done, int64_t* launches) {
+  if (S.npos > 0)
+    sparse_adjoint_kernel<<<nb(S.npos), ST, 0, st>>>(n, S.npos, S.pos_r, S.pos_c, S.pos_ptr, S.perm, S.con, S.val, y,
+                                                     scale, Y, done);
+  if (launches) ++*launches;
+}
+
+void sparse_apply(cudaStream_t st, const SparseA& S, int n, int m, int r, const double* Z, const double* U,
+                  const double* Q, double* out, const int32_t* done, int64_t* launches) {
+  sparse_apply_kernel<<<nb(m), ST, 0, st>>>(n, m, r, S.con_ptr, S.row, S.col, S.val, Z, U, Q, out, done);
+  if (launches) ++*launches;
+}
+
+void sparse_B(cudaStream_t st, const SparseA& S, int n, int m, int r, const double* Vs, double* B, int64_t ldB,
+              double* Bt, int64_t ldBt, int64_t* launches) {
+  const int d = n * r - r * (r - 1) / 2;
+  int64_t blocks = ((int64_t)m * d + ST - 1) / ST;
+  if (blocks > 16 * (int64_t)g_num_sms) blocks = 16 * (int64_t)g_num_sms;
+  sparse_B_kernel<<<(unsigned)blocks, ST, 0, st>>>(n, m, r, S.con_ptr, S.row, S.col, S.val, Vs, B, ldB, Bt, ldBt);
+  if (launches) ++*launches;
+}
+
+void sparse_sumsq(cudaStream_t st, const SparseA& S, double* out, double* scratch, int64_t* launches) {
+  const int np = 2 * g_num_sms;
+  sparse_sumsq_kernel<<<np, ST, 0, st>>>(S.nnz, S.row, S.col, S.val, scratch);
+  sum_parts_kernel<<<1, ST, 0, st>>>(scratch, np, out);
+  if (launches) *launches += 2;
+}
+
+}  // namespace wc

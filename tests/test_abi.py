@@ -96,6 +96,18 @@ def test_default_options_and_setup_errors(lib):
     with pytest.raises(_native.SdpError) as e:
         _native.sdp_setup(p, o, 0)                        # a_dense is NULL
     assert e.value.status == _native.SDP_EINVAL
+    p.kind = _native.SDP_A_SPARSE_COO                     # no entries
+    with pytest.raises(_native.SdpError) as e:
+        _native.sdp_setup(p, o, 0)
+    assert e.value.status == _native.SDP_EINVAL
+    p.nnz = 1
+    p.a_con = p.a_row = p.a_col = p.a_val = 8            # never read: the mixed form is refused first
+    o.precision = _native.SDP_MIXED_FP32
+    with pytest.raises(_native.SdpError) as e:
+        _native.sdp_setup(p, o, 0)
+    assert e.value.status == _native.SDP_EUNSUPPORTED
+    o.precision = _native.SDP_FP64
+    p.nnz, p.a_con, p.a_row, p.a_col, p.a_val = 0, 0, 0, 0, 0
     p.kind = _native.SDP_A_DIAG
     o.r_fixed = 4                                        # r must be < n
     with pytest.raises(_native.SdpError) as e:
