@@ -82,6 +82,8 @@ struct sdp_handle {
   size_t gj_work_elems = 0;
   double *ubatch = nullptr, *Gb = nullptr, *Hb = nullptr;
   int pinv_dim = 0;                 // order of the largest preconditioner core the options allow
+  int64_t b_elems = 0;              // capacity of the explicit B = A Q (m x d) and of B^T
+  int64_t bs_elems = 0;             // capacity of D^{-1/2} B^T (m-space core by a product)
   wc::Space s64;                        // FP64 solve, outer refinement of the mixed form
   wc::Space sin;                        // inner solve of the mixed form (own vectors and control block)
   wc::Mixed32 m32;

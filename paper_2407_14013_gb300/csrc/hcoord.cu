@@ -26,7 +26,7 @@ __global__ void h_pack_kernel(int n, int r, const double* __restrict__ H, int64_
 }
 
 template <typename T>
-__global__ void h_unpack_kernel(int n, int r, const T* __restrict__ h, T* __restrict__ Hp,
+__global__ void h_unpack_kernel(int n, int r, const T* __restrict__ h, const T* __restrict__ Dv, T* __restrict__ Hp,
                                 const int32_t* __restrict__ done) {
   if (done && *done) return;
   int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -35,10 +35,12 @@ __global__ void h_unpack_kernel(int n, int r, const T* __restrict__ h, T* __rest
   double v;
   if (a < r) {
     int i = a > j ? a : j, jj = a > j ? j : a;
-    double hv = (double)h[svec_index(r, i, jj)];
+    const int k = svec_index(r, i, jj);
+    double hv = Dv ? (double)h[k] / (double)Dv[k] : (double)h[k];
     v = (i == jj) ? hv : hv * WC_RSQRT2;
   } else {
-    v = WC_SQRT2 * (double)h[r * (r + 1) / 2 + (a - r) + j * (n - r)];
+    const int k = r * (r + 1) / 2 + (a - r) + j * (n - r);
+    v = WC_SQRT2 * (Dv ? (double)h[k] / (double)Dv[k] : (double)h[k]);
   }
   Hp[q] = (T)v;
 }
@@ -92,12 +94,14 @@ void h_pack(cudaStream_t st, int n, int r, const double* H, int64_t ldH, double 
 }
 
 template <typename T>
-void h_unpack(cudaStream_t st, int n, int r, const T* h, T* Hp, const int32_t* done, int64_t* launches) {
-  h_unpack_kernel<T><<<nblk((int64_t)n * r, 256), 256, 0, st>>>(n, r, h, Hp, done);
+void h_unpack(cudaStream_t st, int n, int r, const T* h, T* Hp, const int32_t* done, int64_t* launches,
+              const T* Dv) {
+  h_unpack_kernel<T><<<nblk((int64_t)n * r, 256), 256, 0, st>>>(n, r, h, Dv, Hp, done);
   if (launches) ++*launches;
 }
 
-template void h_unpack<double>(cudaStream_t, int, int, const double*, double*, const int32_t*, int64_t*);
+template void h_unpack<double>(cudaStream_t, int, int, const double*, double*, const int32_t*, int64_t*,
+                               const double*);
 
 void h_pack_rows(cudaStream_t st, int n, int r, int mb, int i0, const double* H, double* B,
                  int64_t ldB, double* Bt, int64_t ldBt, int64_t* launches) {

@@ -88,9 +88,10 @@ void split_sigma(cudaStream_t st, int n, int r, const double* lam_s, const PcgCt
 void h_pack(cudaStream_t st, int n, int r, const double* H, int64_t ldH, double c_out, const double* in,
             double c_in, const double* Dv, const double* pv, double* out, const int32_t* done,
             int64_t* launches);
-// Hp (n x r) with Vs Hp = Q B + sqrt2 Qp N for h = [svec B; vec N]
+// Hp (n x r) with Vs Hp = Q B + sqrt2 Qp N for h = [svec B; vec N] (of h / Dv when Dv is given)
 template <typename T>
-void h_unpack(cudaStream_t st, int n, int r, const T* h, T* Hp, const int32_t* done, int64_t* launches);
+void h_unpack(cudaStream_t st, int n, int r, const T* h, T* Hp, const int32_t* done, int64_t* launches,
+              const T* Dv = nullptr);
 // B rows of A Q from a batch H = Vs^T [A_i Q] (n x mb r, column j * mb + il): B[(i0+il) * d + h]
 void h_pack_rows(cudaStream_t st, int n, int r, int mb, int i0, const double* H, double* B,
                  int64_t ldB, double* Bt, int64_t ldBt, int64_t* launches);
@@ -119,9 +120,13 @@ void convert(cudaStream_t st, int64_t count, const From* src, To* dst, int64_t* 
 struct SparseA {
   int64_t nnz = 0;
   int npos = 0;
+  int64_t nnzY = 0;      // nonzeros of the symmetric pattern of A^T(y) (off-diagonal positions twice)
   const int32_t *con = nullptr, *row = nullptr, *col = nullptr;
   const double* val = nullptr;
   int32_t *con_ptr = nullptr, *pos_r = nullptr, *pos_c = nullptr, *pos_ptr = nullptr, *perm = nullptr;
+  int32_t* epos = nullptr;                                  // position index of each entry (nnz)
+  int32_t *yptr = nullptr, *ycol = nullptr, *ypidx = nullptr;   // CSR of the pattern: row i holds
+                                                            // (column, position index) pairs
 };
 // Y = scale * A^T(y) on the pattern positions (both triangles); Y is zero elsewhere already.
 void sparse_adjoint(cudaStream_t st, const SparseA& S, int n, const double* y, double scale, double* Y,
@@ -132,6 +137,20 @@ void sparse_apply(cudaStream_t st, const SparseA& S, int n, int m, int r, const 
 // B = A Q (m x d row-major, ld ldB) and B^T (d x m, ld ldBt) in h-coordinates.
 void sparse_B(cudaStream_t st, const SparseA& S, int n, int m, int r, const double* Vs, double* B, int64_t ldB,
               double* Bt, int64_t ldBt, int64_t* launches);
+// Position values of Y = A^T(y): ypos[p] = sum over the entries e at position p of y[con_e] val_e.
+void sparse_posval(cudaStream_t st, const SparseA& S, const double* y, double* ypos, const int32_t* done,
+                   int64_t* launches);
+// Out (n x ncols, ld ldo) = Y Bm (Bm n x ncols, ld ldb) with Y = A^T(y) given by its position values.
+void sparse_sym_spmm(cudaStream_t st, const SparseA& S, int n, int ncols, const double* ypos, const double* Bm,
+                     int64_t ldb, double* Out, int64_t ldo, const int32_t* done, int64_t* launches);
+// zpos[p] = (E G)[a_p, b_p] = <E[:, a_p], G[:, b_p]> for symmetric E (n x n): the entries of E Y E at
+// the pattern positions with G = Y E.
+void sparse_pos_dots(cudaStream_t st, const SparseA& S, int n, const double* E, const double* G, double* zpos,
+                     const int32_t* done, int64_t* launches);
+// out[i] = <A_i, Z + sym(U Q^T)> with Z given by its values at the pattern positions (zpos, may be
+// NULL: Z = 0) and U, Q n x r (U may be NULL).
+void sparse_apply_pos(cudaStream_t st, const SparseA& S, int n, int m, int r, const double* zpos, const double* U,
+                      const double* Q, double* out, const int32_t* done, int64_t* launches);
 // *out = sum_i ||A_i||_F^2; scratch holds 2 * g_num_sms doubles.
 void sparse_sumsq(cudaStream_t st, const SparseA& S, double* out, double* scratch, int64_t* launches);
 

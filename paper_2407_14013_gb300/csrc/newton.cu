@@ -94,8 +94,8 @@ void carve_space(sdp_handle* h, Carver& c, Space& S) {
   S.E = c.take<double>(nn);
   S.EE = (h->kind == SDP_A_DIAG) ? c.take<double>(nn) : nullptr;
   S.Dv = c.take<double>(dm);
-  S.B = c.take<double>(m * dm);
-  S.Bt = c.take<double>(m * dm);
+  S.B = c.take<double>(h->b_elems);
+  S.Bt = c.take<double>(h->b_elems);
   S.Pinv = c.take<double>(pc * pc);
   S.Y = c.take<double>(nn);
   S.F = c.take<double>(nn);
@@ -161,7 +161,7 @@ size_t carve(sdp_handle* h, char* base) {
   h->lam_s = c.take<double>(n);
   h->e = c.take<double>(n);
   h->Ve = c.take<double>(nn);
-  h->Bs = c.take<double>(m * dm);
+  h->Bs = c.take<double>(h->bs_elems);
   h->Cw = c.take<double>(nn);
   h->g = c.take<double>(vt);
   h->dotbuf = c.take<double>(1024);
@@ -300,6 +300,15 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   h->d_max = dof(n, r_max);
   // d-space core (d x d) when d <= m, m-space core (m x m) otherwise, unless forced
   h->pinv_dim = opt.precond_space == 1 ? h->d_max : opt.precond_space == 2 ? m : std::min(h->d_max, m);
+  // explicit B = A Q: DIAG forms its m-space core in closed form and its products with B from
+  // Vs, so it needs B only for the d-space core (auto selects that only at r = 1, d = n)
+  if (h->kind == SDP_A_DIAG) {
+    h->b_elems = opt.precond_space == 2 ? 0 : (int64_t)m * (opt.precond_space == 1 ? h->d_max : dof(n, 1));
+    h->bs_elems = 0;
+  } else {
+    h->b_elems = (int64_t)m * h->d_max;
+    h->bs_elems = opt.precond_space == 1 ? 0 : (int64_t)m * h->d_max;
+  }
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -500,6 +509,21 @@ sdp_status apply_operator_mixed(sdp_handle* h, Space& S, const double* pin, doub
   Mixed32& M = h->m32;
   const double* pu = pin;
   const double* pv = pin + m;
+  if (h->kind == SDP_A_DIAG) {
+    // the FP64 products with B from Vs, as in the FP64 operator, beside the FP32 (E o E) p_u
+    const int n = h->n, r = h->r;
+    cudaStream_t s0 = fork(h, 0, 0);
+    h_unpack<double>(s0, n, r, pv, S.Hp, done, L);
+    CU(gemm_f64(s0, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, h->ws_b[0], h->ws_b_elems, L, done));
+    launch_to_float(st, m, pu, M.pu, done, L);
+    rows_gemv<float>(st, M.EE, n, n, M.pu, M.partA, done, L);               // (E o E) p_u
+    launch_diag_scale_rows<double>(st, n, r, pu, S.Vs, S.Tm, done, L);
+    CU(gemm_f64(st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, done));
+    join(h, 0, 2);
+    launch_ap_finish<double>(st, m, d, n, r, nullptr, 0, S.Up, S.Vs, S.H, S.Dv, pin, gsub, out, mode, S.ctl,
+                             h->dotbuf, h->counter, L, M.partA, rows_gemv_slabs(n, n, 4));
+    return SDP_OK;
+  }
   // side branch: the FP64 rows with B, beside the FP32 A E A^T chain on the main stream
   cudaStream_t s0 = fork(h, 0, 0);
   rows_gemv<double>(s0, S.B, m, d, pv, M.partBv, done, L);                  // B p_v
@@ -536,7 +560,7 @@ sdp_status apply_op(sdp_handle* h, Space& S, bool mixed, const double* pin, doub
 }
 
 // z = P^{-1} rin (Section 6), then <r, z>; mode 0 sets rz, mode 1 computes the PCG beta.
-void apply_precond(sdp_handle* h, Space& S, const double* rin, double* zout, int mode) {
+sdp_status apply_precond(sdp_handle* h, Space& S, const double* rin, double* zout, int mode) {
   const int m = h->m, d = h->d;
   const int32_t* done = &S.ctl->done;
   cudaStream_t st = h->st;
@@ -551,6 +575,19 @@ void apply_precond(sdp_handle* h, Space& S, const double* rin, double* zout, int
                      L);
     launch_pc_zu_dot<double>(st, m, d, rows_gemv_slabs(m, d), S.partA, 1, rin, zout, mode, S.ctl, h->dotbuf,
                              h->counter, L);
+  } else if (h->kind == SDP_A_DIAG) {
+    // the products with B from Vs: B t = rowdot(Vs unpack(t), Q), B^T u = pack(Vs^T diag(u) Q)
+    const int n = h->n, r = h->r;
+    const double* Q = S.Vs;
+    h_unpack<double>(st, n, r, rin + m, S.Hp, done, L, S.Dv);              // unpack(D^{-1} r_v)
+    CU(gemm_f64(st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, S.ws_elems, L, done));
+    launch_diag_w(st, n, r, S.Up, Q, rin, S.wm, S.ctl, L);                 // w = r_u + B D^{-1} r_v
+    rows_gemv<double>(st, S.Pinv, m, m, S.wm, S.partC, done, L);           // K^{-1} w
+    launch_pc_m_w<double>(st, m, rows_gemv_slabs(m, m), S.partC, nullptr, zout, S.ctl, L);  // z_u
+    launch_diag_scale_rows<double>(st, n, r, zout, S.Vs, S.Tm, done, L);  // diag(z_u) Q
+    CU(gemm_f64(st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, done));
+    launch_diag_zv(st, m, d, n, r, S.H, rin, S.Dv, zout, S.ctl, L);        // z_v = D^{-1}(B^T z_u - r_v)
+    launch_pc_zu_dot<double>(st, m, d, 0, nullptr, 2, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L);
   } else {
     launch_pc_m_tv<double>(st, m, d, rin, S.Dv, S.sd, S.ctl, L);           // t = D^{-1} r_v
     rows_gemv<double>(st, S.B, m, d, S.sd, S.partA, done, L);              // B t
@@ -561,6 +598,7 @@ void apply_precond(sdp_handle* h, Space& S, const double* rin, double* zout, int
     launch_pc_m_zv<double>(st, m, d, Sm, S.partBt, rin, S.Dv, zout, S.ctl, L);  // z_v = D^{-1}(B^T z_u - r_v)
     launch_pc_zu_dot<double>(st, m, d, 0, nullptr, 2, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L);
   }
+  return SDP_OK;
 }
 
 // r0 = g - M x (given), stop test, z0 = P^{-1} r0, p0 = z0.  rel_rtol2 > 0 sets a relative threshold.
@@ -568,7 +606,8 @@ sdp_status pcg_start(sdp_handle* h, Space& S, bool mixed, const double* gsub, do
   sdp_status s = apply_op(h, S, mixed, S.x, S.rv, gsub, 0);
   if (s != SDP_OK) return s;
   launch_norm_check<double>(h->st, h->m + h->d, S.rv, rel_rtol2, S.ctl, h->dotbuf, h->counter, &h->launches);
-  apply_precond(h, S, S.rv, S.z, 0);
+  s = apply_precond(h, S, S.rv, S.z, 0);
+  if (s != SDP_OK) return s;
   launch_p_update<double>(h->st, h->m + h->d, S.z, S.p, 1, S.ctl, &h->launches);
   return SDP_OK;
 }
@@ -598,7 +637,8 @@ sdp_status pcg_loop(sdp_handle* h, Space& S, bool mixed) {
       sdp_status s = apply_op(h, S, mixed, S.p, S.Ap, nullptr, 1);
       if (s != SDP_OK) { h->st = saved; return s; }
       launch_update<double>(s_, nt, S.x, S.rv, S.p, S.Ap, S.ctl, h->dotbuf, h->counter, L);
-      apply_precond(h, S, S.rv, S.z, 1);
+      s = apply_precond(h, S, S.rv, S.z, 1);
+      if (s != SDP_OK) { h->st = saved; return s; }
       launch_p_update<double>(s_, nt, S.z, S.p, 0, S.ctl, L);
     }
     h->st = saved;
@@ -744,12 +784,21 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     sparse_B(st, h->sp, n, m, r, S.Vs, S.B, d, S.Bt, m, L);
   } else {
     launch_hadamard_sq(st, (int64_t)n * n, S.E, S.EE, L);
-    h_pack_rows_diag(st, n, r, S.Vs, S.B, d, S.Bt, m, L);
+    if (h->space == 1) {
+      if ((int64_t)m * d > h->b_elems) return fail(h, SDP_EINVAL, "d-space core larger than the setup allows");
+      h_pack_rows_diag(st, n, r, S.Vs, S.B, d, S.Bt, m, L);
+    }
   }
   int32_t* pstatus = &h->ctl->status;
   const int pd = (h->space == 1) ? d : m;
   if (pd > h->pinv_dim) return fail(h, SDP_EINVAL, "preconditioner core larger than the setup allows");
-  if (h->space == 1) {
+  if (h->kind == SDP_A_DIAG && h->space == 2) {
+    // K = beta I + tau^-2 G o (G + 2 tau E) with G = Q (Lam - tau I) Q^T (lower triangle)
+    launch_shift_cols(st, n, r, S.Vs, h->lam_s, h->ctl, S.Tm, L);
+    CU(gemm_f64(st, false, true, n, n, r, 1.0, S.Tm, n, S.Vs, n, 0.0, S.F, n, S.ws, ws, L, nullptr, GEMM_LOWER));
+    launch_diag_K(st, n, S.F, S.E, h->ctl, S.Pinv, L);
+    CU(spd_inverse(st, m, S.Pinv, h->gj_work, h->gj_work_elems, S.ws, ws, pstatus, L));
+  } else if (h->space == 1) {
     // C = beta^{-1} B^T B + tau^2 Sigma  (B row-major m x d == column-major d x m)
     const double beta = h->ctl_host->beta_pc;
     CU(gemm_f64(st, false, true, d, d, m, 1.0 / beta, S.B, d, S.B, d, 0.0, S.Pinv, d, S.ws, ws, L, nullptr,
@@ -758,6 +807,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     CU(spd_inverse(st, d, S.Pinv, h->gj_work, h->gj_work_elems, S.ws, ws, pstatus, L));
   } else {
     // K = beta I + B D^{-1} B^T = Bs^T Bs + beta I with Bs = D^{-1/2} B^T (d x m)
+    if ((int64_t)m * d > h->bs_elems) return fail(h, SDP_EINVAL, "m-space core larger than the setup allows");
     launch_scale_B(st, m, d, S.B, S.Dv, h->Bs, L);
     CU(gemm_f64(st, true, false, m, m, d, 1.0, h->Bs, d, h->Bs, d, 0.0, S.Pinv, m, S.ws, ws, L, nullptr, GEMM_LOWER));
     launch_add_diag(st, m, S.Pinv, nullptr, h->ctl_host->beta_pc, L);
@@ -799,7 +849,8 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     // ---- a4-a6: FP64 PCG from x0 ----
     if (h->opt.pcg_start == 0) {   // x0 = P^{-1}[0; g_v]: P x0 = [0; g_v], so r0_v = 0 with r0_u ~ g
       launch_correction_rhs(st, m, d, h->g, S.z, L);
-      apply_precond(h, S, S.z, S.x, 0);
+      sdp_status s0 = apply_precond(h, S, S.z, S.x, 0);
+      if (s0 != SDP_OK) return s0;
     }
     sdp_status s = pcg_start(h, S, false, h->g, 0.0);
     if (s != SDP_OK) return s;
@@ -827,8 +878,9 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
       // M~ delta = rho by PCG from delta0 = P^{-1}[0; rho_v], to inner_rtol relative reduction
       launch_ctl_reset(st, h->ctl_in, h->ctl, h->opt.max_inner, L);
       launch_correction_rhs(st, m, d, S.rv, Si.z, L);
-      apply_precond(h, Si, Si.z, Si.x, 0);
-      sdp_status s = pcg_start(h, Si, true, S.rv, h->opt.inner_rtol * h->opt.inner_rtol);
+      sdp_status s = apply_precond(h, Si, Si.z, Si.x, 0);
+      if (s != SDP_OK) return s;
+      s = pcg_start(h, Si, true, S.rv, h->opt.inner_rtol * h->opt.inner_rtol);
       if (s != SDP_OK) return s;
       s = pcg_loop(h, Si, true);
       if (s != SDP_OK) return s;
@@ -960,7 +1012,9 @@ extern "C" sdp_status sdp_debug_copy(sdp_handle* h, int32_t which, double* dst, 
   switch (which) {
     case 0: src = S.E; avail = n * n; break;
     case 1: src = S.Dv; avail = d; break;
-    case 2: src = S.B; avail = m * d; break;
+    case 2:
+      if (h->kind == SDP_A_DIAG && h->space == 2) return fail(h, SDP_EINVAL, "B is not formed for this kind and space");
+      src = S.B; avail = m * d; break;
     case 3: src = S.Pinv; avail = pd * pd; break;
     case 4: src = S.Vs; avail = n * n; break;
     case 5: src = S.x; avail = m + d; break;

@@ -41,7 +41,8 @@ __global__ void __launch_bounds__(VT)
 ap_finish_kernel(int m, int d, int n, int r, const T* __restrict__ partA, int S, const T* __restrict__ Up,
                  const T* __restrict__ Vs, const T* __restrict__ H, const T* __restrict__ Dv,
                  const T* __restrict__ p, const T* __restrict__ g, T* __restrict__ out, int mode,
-                 PcgCtl* __restrict__ ctl, double* __restrict__ dotbuf, unsigned int* __restrict__ counter) {
+                 PcgCtl* __restrict__ ctl, double* __restrict__ dotbuf, unsigned int* __restrict__ counter,
+                 const float* __restrict__ partA32, int S32) {
   if (ctl->done) return;
   __shared__ double sh[32];
   const int nt = m + d;
@@ -51,6 +52,7 @@ ap_finish_kernel(int m, int d, int n, int r, const T* __restrict__ partA, int S,
     if (q < m) {
       v = 0.0;
       for (int s = 0; s < S; ++s) v += (double)partA[(int64_t)s * m + q];
+      for (int s = 0; s < S32; ++s) v += (double)partA32[(int64_t)s * m + q];
       if (Up) {   // DIAG: A(sym(U Q^T)) = diag(U Q^T)
         for (int k = 0; k < r; ++k) v += (double)Up[q + (int64_t)k * n] * (double)Vs[q + (int64_t)k * n];
       }
@@ -203,6 +205,58 @@ __global__ void pc_m_zv_kernel(int m, int d, int G, const T* __restrict__ partBt
   double t = 0.0;
   for (int gg = 0; gg < G; ++gg) t += (double)partBt[(int64_t)gg * d + h];
   z[m + h] = (T)((t - (double)rv[m + h]) / (double)Dv[h]);
+}
+
+// DIAG kind, m-space core with the products with B formed from Vs (no explicit B):
+//   B t   = A(Q t) = diag(sym(U Q^T)) = rowdot(U, Q) with U = Vs unpack(t)
+//   B^T u = Q^T svec(Diag(u)) = pack(Vs^T diag(u) Q)
+// w = r_u + rowdot(U, Q)
+__global__ void diag_w_kernel(int n, int r, const double* __restrict__ U, const double* __restrict__ Vs,
+                              const double* __restrict__ rv, double* __restrict__ w, const PcgCtl* __restrict__ ctl) {
+  if (ctl->done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double t = rv[i];
+  for (int k = 0; k < r; ++k) t = fma(U[i + (int64_t)k * n], Vs[i + (int64_t)k * n], t);
+  w[i] = t;
+}
+
+// z_v = (pack(H) - r_v) / D with H = Vs^T diag(z_u) Q
+__global__ void diag_zv_kernel(int m, int d, int n, int r, const double* __restrict__ H,
+                               const double* __restrict__ rv, const double* __restrict__ Dv, double* __restrict__ z,
+                               const PcgCtl* __restrict__ ctl) {
+  if (ctl->done) return;
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= d) return;
+  z[m + h] = (pack_at(H, n, n, r, h) - rv[m + h]) / Dv[h];
+}
+
+// Tm = Q (Lam - tau I): the first r columns of Vs scaled by lam_j - tau
+__global__ void shift_cols_kernel(int n, int r, const double* __restrict__ Vs, const double* __restrict__ lam_s,
+                                  const PcgCtl* __restrict__ ctl, double* __restrict__ Tm) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)n * r) return;
+  Tm[q] = Vs[q] * (lam_s[q / n] - ctl->tau);
+}
+
+// DIAG kind, m-space core in closed form (lower triangle and diagonal):
+//   K = beta I + B D^{-1} B^T = beta I + tau^-2 G o (G + 2 tau E),  G = Q (Lam - tau I) Q^T.
+// Row i of B is [svec(q_i q_i^T); sqrt2 vec(p_i q_i^T)] (q_i, p_i: row i of Q, Qp), and
+// D^{-1} = diag(Lam (x)s Lam - tau^2 I, (Lam - tau I) (x) Lamp) / tau^2 (eq. EQSigdef), so
+//   (B D^{-1} B^T)_il = tau^-2 [ (Q Lam Q^T)_il^2 - tau^2 (Q Q^T)_il^2
+//                                + 2 (Q (Lam - tau I) Q^T)_il (Qp Lamp Qp^T)_il ];
+// with Qp Lamp Qp^T = tau (E - Q Q^T) the bracket factors as G_il (G_il + 2 tau E_il).
+__global__ void diag_K_kernel(int n, const double* __restrict__ G, const double* __restrict__ E,
+                              const PcgCtl* __restrict__ ctl, double* __restrict__ K) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)n * n) return;
+  const int i = (int)(q % n), l = (int)(q / n);
+  if (i < l) return;
+  const double tau = ctl->tau;
+  const double g = G[q];
+  double v = g * fma(2.0 * tau, E[q], g) / (tau * tau);
+  if (i == l) v += ctl->beta_pc;
+  K[q] = v;
 }
 
 // p = z + beta p  (start: p = z)
@@ -465,9 +519,9 @@ inline int vec_blocks(int nt) {
 template <typename T>
 void launch_ap_finish(cudaStream_t st, int m, int d, int n, int r, const T* partA, int S, const T* Up, const T* Vs,
                       const T* H, const T* Dv, const T* p, const T* g, T* out, int mode, PcgCtl* ctl,
-                      double* dotbuf, unsigned int* counter, int64_t* launches) {
+                      double* dotbuf, unsigned int* counter, int64_t* launches, const float* partA32, int S32) {
   ap_finish_kernel<T><<<vec_blocks(m + d), VT, 0, st>>>(m, d, n, r, partA, S, Up, Vs, H, Dv, p, g, out, mode, ctl,
-                                                       dotbuf, counter);
+                                                       dotbuf, counter, partA32, S32);
   ++*launches;
 }
 
@@ -543,7 +597,7 @@ void launch_diag_scale_rows(cudaStream_t st, int n, int r, const T* pu, const T*
 #define WC_INSTANTIATE(T)                                                                                          \
   template void launch_ap_finish<T>(cudaStream_t, int, int, int, int, const T*, int, const T*, const T*, const T*,  \
                                     const T*, const T*, const T*, T*, int, PcgCtl*, double*, unsigned int*,          \
-                                    int64_t*);                                                                      \
+                                    int64_t*, const float*, int);                                                   \
   template void launch_update<T>(cudaStream_t, int, T*, T*, const T*, const T*, PcgCtl*, double*, unsigned int*,   \
                                  int64_t*);                                                                         \
   template void launch_pc_d_s<T>(cudaStream_t, int, int, int, const T*, const T*, T*, const PcgCtl*, int64_t*);      \
@@ -629,6 +683,30 @@ void launch_sym_copy(cudaStream_t st, int n, const double* g, double* out, int64
 
 void launch_add_correction(cudaStream_t st, int nt, const double* delta, double* x, int64_t* launches) {
   add_correction_kernel<<<nblk(nt, VT), VT, 0, st>>>(nt, delta, x);
+  ++*launches;
+}
+
+void launch_diag_w(cudaStream_t st, int n, int r, const double* U, const double* Vs, const double* rv, double* w,
+                   const PcgCtl* ctl, int64_t* launches) {
+  diag_w_kernel<<<nblk(n, VT), VT, 0, st>>>(n, r, U, Vs, rv, w, ctl);
+  ++*launches;
+}
+
+void launch_diag_zv(cudaStream_t st, int m, int d, int n, int r, const double* H, const double* rv, const double* Dv,
+                    double* z, const PcgCtl* ctl, int64_t* launches) {
+  diag_zv_kernel<<<nblk(d, VT), VT, 0, st>>>(m, d, n, r, H, rv, Dv, z, ctl);
+  ++*launches;
+}
+
+void launch_shift_cols(cudaStream_t st, int n, int r, const double* Vs, const double* lam_s, const PcgCtl* ctl,
+                       double* Tm, int64_t* launches) {
+  shift_cols_kernel<<<nblk((int64_t)n * r, VT), VT, 0, st>>>(n, r, Vs, lam_s, ctl, Tm);
+  ++*launches;
+}
+
+void launch_diag_K(cudaStream_t st, int n, const double* G, const double* E, const PcgCtl* ctl, double* K,
+                   int64_t* launches) {
+  diag_K_kernel<<<nblk((int64_t)n * n, VT), VT, 0, st>>>(n, G, E, ctl, K);
   ++*launches;
 }
 

@@ -12,7 +12,8 @@ namespace wc {
 template <typename T>
 void launch_ap_finish(cudaStream_t st, int m, int d, int n, int r, const T* partA, int S, const T* Up, const T* Vs,
                       const T* H, const T* Dv, const T* p, const T* g, T* out, int mode, PcgCtl* ctl,
-                      double* dotbuf, unsigned int* counter, int64_t* launches);
+                      double* dotbuf, unsigned int* counter, int64_t* launches, const float* partA32 = nullptr,
+                      int S32 = 0);
 template <typename T>
 void launch_update(cudaStream_t st, int nt, T* x, T* rv, const T* p, const T* Ap, PcgCtl* ctl, double* dotbuf,
                    unsigned int* counter, int64_t* launches);
@@ -63,5 +64,15 @@ void launch_mixed_finish(cudaStream_t st, int m, int d, const float* partA32, in
 void launch_to_float(cudaStream_t st, int cnt, const double* src, float* dst, const int32_t* done, int64_t* launches);
 void launch_sym_copy(cudaStream_t st, int n, const double* g, double* out, int64_t* launches);
 void launch_ctl_reset(cudaStream_t st, PcgCtl* dst, const PcgCtl* src, int max_iters, int64_t* launches);
+// DIAG kind, m-space core without an explicit B: w = r_u + rowdot(U, Q); z_v = (pack(H) - r_v) / D;
+// Tm = Q (Lam - tau I); K = beta I + tau^-2 G o (G + 2 tau E) (lower triangle)
+void launch_diag_w(cudaStream_t st, int n, int r, const double* U, const double* Vs, const double* rv, double* w,
+                   const PcgCtl* ctl, int64_t* launches);
+void launch_diag_zv(cudaStream_t st, int m, int d, int n, int r, const double* H, const double* rv, const double* Dv,
+                    double* z, const PcgCtl* ctl, int64_t* launches);
+void launch_shift_cols(cudaStream_t st, int n, int r, const double* Vs, const double* lam_s, const PcgCtl* ctl,
+                       double* Tm, int64_t* launches);
+void launch_diag_K(cudaStream_t st, int n, const double* G, const double* E, const PcgCtl* ctl, double* K,
+                   int64_t* launches);
 
 }  // namespace wc

@@ -10,6 +10,13 @@
 //   A^T(y):   one thread per distinct position sums its entries   (fixed order, no atomics)
 // both deterministic.  A^T(y) writes only the positions of the pattern; every other entry of
 // the output matrix must already be zero (the callers zero it once).
+//
+// Inside the PCG loop Y = A^T(y) is never formed as a matrix: it is kept as its values at the
+// pattern positions, with a CSR table of the symmetric pattern (row i: the columns c with
+// Y[i, c] a pattern entry, and their position index), so that
+//   Y Bm        one thread per (row, column of Bm) sums its row's pattern entries (SpMM)
+//   (E Y E)_ab  only at the pattern positions: <E[:, a], (Y E)[:, b]>, one warp each
+// which replaces the two dense n^3 products E Y and (E Y) E by O(nnz(Y) n + npos n) work.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -108,6 +115,76 @@ __global__ void sparse_B_kernel(int n, int m, int r, const int32_t* __restrict__
   }
 }
 
+__global__ void sparse_posval_kernel(int npos, const int32_t* __restrict__ pos_ptr, const int32_t* __restrict__ perm,
+                                     const int32_t* __restrict__ con, const double* __restrict__ val,
+                                     const double* __restrict__ y, double* __restrict__ ypos,
+                                     const int32_t* __restrict__ done) {
+  if (done && *done) return;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npos) return;
+  double s = 0.0;
+  for (int k = pos_ptr[p]; k < pos_ptr[p + 1]; ++k) {
+    const int e = perm[k];
+    s = fma(y[con[e]], val[e], s);
+  }
+  ypos[p] = s;
+}
+
+// Out[i, j] = sum over the pattern entries (i, c) of row i of Y[i, c] Bm[c, j]; grid (row blocks, ncols)
+__global__ void sym_spmm_kernel(int n, const int32_t* __restrict__ yptr, const int32_t* __restrict__ ycol,
+                                const int32_t* __restrict__ ypidx, const double* __restrict__ ypos,
+                                const double* __restrict__ Bm, int64_t ldb, double* __restrict__ Out, int64_t ldo,
+                                const int32_t* __restrict__ done) {
+  if (done && *done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int j = blockIdx.y;
+  const double* b = Bm + (int64_t)j * ldb;
+  double s = 0.0;
+  for (int k = yptr[i]; k < yptr[i + 1]; ++k) s = fma(ypos[ypidx[k]], b[ycol[k]], s);
+  Out[i + (int64_t)j * ldo] = s;
+}
+
+// one warp per position: <E[:, a], G[:, b]>
+__global__ void pos_dots_kernel(int npos, const int32_t* __restrict__ pos_r, const int32_t* __restrict__ pos_c,
+                                int n, const double* __restrict__ E, const double* __restrict__ G,
+                                double* __restrict__ zpos, const int32_t* __restrict__ done) {
+  if (done && *done) return;
+  const int lane = threadIdx.x & 31;
+  const int p = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (p >= npos) return;
+  const double* ea = E + (int64_t)pos_r[p] * n;
+  const double* gb = G + (int64_t)pos_c[p] * n;
+  double s = 0.0;
+  for (int c = lane; c < n; c += 32) s = fma(ea[c], gb[c], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) zpos[p] = s;
+}
+
+__global__ void sparse_apply_pos_kernel(int n, int m, int r, const int32_t* __restrict__ con_ptr,
+                                        const int32_t* __restrict__ row, const int32_t* __restrict__ col,
+                                        const double* __restrict__ val, const int32_t* __restrict__ epos,
+                                        const double* __restrict__ zpos, const double* __restrict__ U,
+                                        const double* __restrict__ Q, double* __restrict__ out,
+                                        const int32_t* __restrict__ done) {
+  if (done && *done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double s = 0.0;
+  for (int e = con_ptr[i]; e < con_ptr[i + 1]; ++e) {
+    const int a = row[e], b = col[e];
+    double z = zpos ? zpos[epos[e]] : 0.0;
+    if (U) {
+      double t = 0.0;
+      for (int k = 0; k < r; ++k)
+        t += U[a + (int64_t)k * n] * Q[b + (int64_t)k * n] + Q[a + (int64_t)k * n] * U[b + (int64_t)k * n];
+      z += 0.5 * t;
+    }
+    s = fma(val[e] * (a == b ? 1.0 : 2.0), z, s);
+  }
+  out[i] = s;
+}
+
 // sum_i ||A_i||_F^2 = sum_e val_e^2 (2 if off-diagonal), per-block partials then one block
 __global__ void sparse_sumsq_kernel(int64_t nnz, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
                                     const double* __restrict__ val, double* __restrict__ part) {
@@ -149,6 +226,34 @@ void sparse_B(cudaStream_t st, const SparseA& S, int n, int m, int r, const doub
   int64_t blocks = ((int64_t)m * d + ST - 1) / ST;
   if (blocks > 16 * (int64_t)g_num_sms) blocks = 16 * (int64_t)g_num_sms;
   sparse_B_kernel<<<(unsigned)blocks, ST, 0, st>>>(n, m, r, S.con_ptr, S.row, S.col, S.val, Vs, B, ldB, Bt, ldBt);
+  if (launches) ++*launches;
+}
+
+void sparse_posval(cudaStream_t st, const SparseA& S, const double* y, double* ypos, const int32_t* done,
+                   int64_t* launches) {
+  if (S.npos > 0)
+    sparse_posval_kernel<<<nb(S.npos), ST, 0, st>>>(S.npos, S.pos_ptr, S.perm, S.con, S.val, y, ypos, done);
+  if (launches) ++*launches;
+}
+
+void sparse_sym_spmm(cudaStream_t st, const SparseA& S, int n, int ncols, const double* ypos, const double* Bm,
+                     int64_t ldb, double* Out, int64_t ldo, const int32_t* done, int64_t* launches) {
+  dim3 grid(nb(n), (unsigned)ncols);
+  sym_spmm_kernel<<<grid, ST, 0, st>>>(n, S.yptr, S.ycol, S.ypidx, ypos, Bm, ldb, Out, ldo, done);
+  if (launches) ++*launches;
+}
+
+void sparse_pos_dots(cudaStream_t st, const SparseA& S, int n, const double* E, const double* G, double* zpos,
+                     const int32_t* done, int64_t* launches) {
+  if (S.npos > 0)
+    pos_dots_kernel<<<nb((int64_t)S.npos * 32), ST, 0, st>>>(S.npos, S.pos_r, S.pos_c, n, E, G, zpos, done);
+  if (launches) ++*launches;
+}
+
+void sparse_apply_pos(cudaStream_t st, const SparseA& S, int n, int m, int r, const double* zpos, const double* U,
+                      const double* Q, double* out, const int32_t* done, int64_t* launches) {
+  sparse_apply_pos_kernel<<<nb(m), ST, 0, st>>>(n, m, r, S.con_ptr, S.row, S.col, S.val, S.epos, zpos, U, Q, out,
+                                                done);
   if (launches) ++*launches;
 }
 
