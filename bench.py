@@ -127,6 +127,94 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def other_configs(dev, reps: int = 2):
+    """The other workloads, measured beside the headline one (not part of its timed steps).
+
+    - MaxCut n=64 (m=64, DIAG, r_hat=12, FP64): time to a 1e-8 relative gap of the whole
+      interior-point solve on the device, and the device time per PCG iteration (latency-bound).
+    - MaxCut n=5000 (average degree 8, N(0,1) weights, DIAG, r=100, d=495050): Newton solves at a
+      synthetic scaling point (mu=1e-4), FP64 and mixed; m-space core in closed form.
+    - Matrix completion n=2000 (1000+1000, 5% of a rank-5 1000x1000 target, m=50000, r=5,
+      d=9990, d-space core C of 798 MB): Newton solves at a synthetic scaling point (mu=1e-4).
+    Each Newton row: one untimed solve, then `reps` solves timed with CUDA events; the matvec
+    rates are PCG iterations / whole solve time and PCG iterations / PCG phase time."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2407_14013_gb300 import NewtonSolver
+
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    def newton_rows(prob, sp, Ct, bt, r_hat, precs):
+        rows = {}
+        args = (t(sp.V), t(sp.lam), t(Ct), t(bt))
+        for prec in precs:
+            s = NewtonSolver(prob, r_hat=r_hat, device=str(dev), precision=prec)
+            s.solve(*args)
+            ms, it, ph = [], 0, [0.0, 0.0, 0.0]
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s.stream)
+                _, _, _, info = s.solve(*args)
+                e1.record(s.stream)
+                e1.synchronize()
+                assert info.converged
+                ms.append(e0.elapsed_time(e1))
+                it += info.pcg_iters
+                ph[0] += info.setup_ms
+                ph[1] += info.pcg_ms
+                ph[2] += info.recover_ms
+            rows[prec] = {"r": info.r, "d": info.d, "space": "d" if info.space == 1 else "m",
+                          "ms_per_solve": sum(ms) / reps, "pcg_iters_per_solve": it / reps,
+                          "refine_steps": info.refine_steps,
+                          "matvecs_per_s": it / (sum(ms) / 1e3),
+                          "pcg_phase_matvecs_per_s": it / (ph[1] / 1e3),
+                          "phase_ms_per_solve": {"setup": ph[0] / reps, "rhs_and_pcg": ph[1] / reps,
+                                                 "recover": ph[2] / reps},
+                          "gpu_launches_per_solve": info.launches, "workspace_GB": s.workspace_bytes() / 1e9,
+                          "rel_residual": info.res_norm / info.rhs_norm}
+            s.close()
+        return rows
+
+    out = {}
+    # MaxCut n=64: time to gap (whole IPM on the device)
+    prob = W.workload("maxcut64")
+    s = NewtonSolver(prob, r_hat=12, device=str(dev))
+    b_d, C_d = t(prob.b), t(prob.C)
+    s.solve_sdp(b_d, C_d, gap_tol=1e-2, max_iter=2, allow_notconv=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    X, y, S_, inf = s.solve_sdp(b_d, C_d, gap_tol=1e-8, max_iter=100)
+    torch.cuda.synchronize(dev)
+    secs = time.perf_counter() - t0
+    pobj = float((C_d * X).sum())
+    sp = W.scaling_point(64, 3, 1e-4, 5101)
+    Ct, bt = W.newton_rhs(64, 64, 5102)
+    nr = newton_rows(prob, sp, Ct, bt, 12, ["fp64"])["fp64"]
+    out["maxcut64_fp64"] = {"workload": "MaxCut n=64 G(64,0.1) unit weights, DIAG, r_hat=12",
+                            "time_to_gap_1e-8_s": secs, "outer_iters": inf["iters"],
+                            "converged": bool(inf["converged"]), "rel_gap": inf["rel_gap"], "objective": pobj,
+                            "pcg_iters_total": inf["pcg_iters"],
+                            "us_per_pcg_iter": 1e3 * nr["phase_ms_per_solve"]["rhs_and_pcg"] / max(nr["pcg_iters_per_solve"], 1),
+                            "newton": nr}
+    s.close()
+    # MaxCut n=5000, r=100
+    prob = W.workload("maxcut5000")
+    sp = W.scaling_point(5000, 100, 1e-4, 3100)
+    Ct, bt = W.newton_rhs(5000, 5000, 3200)
+    out["maxcut5000_r100"] = {"workload": "MaxCut n=5000 avg degree 8, N(0,1) weights, DIAG, r=100, synthetic "
+                                          "scaling point mu=1e-4",
+                              "newton": newton_rows(prob, sp, Ct, bt, 100, ["fp64", "mixed_fp32"])}
+    # matrix completion n=2000, m=50000, r=5
+    prob = W.workload("completion2000")
+    sp = W.scaling_point(prob.n, 5, 1e-4, 4100)
+    Ct, bt = W.newton_rhs(prob.n, prob.m, 4200)
+    out["completion2000_r5"] = {"workload": "matrix completion n=1000+1000, m=50000 (5%), rank 5, SPARSE_COO, "
+                                            "r=5, synthetic scaling point mu=1e-4",
+                                "newton": newton_rows(prob, sp, Ct, bt, 5, ["fp64"])}
+    return out
+
+
 def cpu_baseline(prob, ins, budget_s: float = 15.0, max_solves: int = 8):
     """The oracle's step-by-step reformulation (numpy FP64), timed on the host cores."""
     import numpy as np
@@ -306,6 +394,8 @@ def run_ours(args):
             ts.close()
         ttg["mixed_speedup"] = ttg["fp64"]["seconds"] / ttg["mixed_fp32"]["seconds"]
 
+    others = other_configs(dev) if (rank == 0 and not args.no_configs) else None
+
     # end to end through the C ABI with pinned host buffers (H2D and D2H inside the call)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     hins = [(pin(V.T).t(), pin(lam), pin(Ct), pin(bt)) for (V, lam, Ct, bt) in ins]
@@ -363,6 +453,7 @@ def run_ours(args):
         "wall_s_timed": wall,
         "mixed_fp32": mixed,
         "time_to_gap_1e-8": ttg,
+        "other_configs": others,
     }
     if base is not None:
         line["cpu_baseline"] = base
@@ -381,6 +472,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg (profiling runs)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
     ap.add_argument("--no-ttg", action="store_true", help="skip the time-to-gap solves")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other workloads (MaxCut 64 / 5000, completion)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -1,15 +1,15 @@
-// FP64 GEMM on the FP64 tensor-core path (mma.sync m8n8k4 f64), column-major operands.
+// FP64 GEMM on the FP64 MMA path (mma.sync m8n8k4 f64), column-major operands.
 //
 //   C (M x N) = alpha * op(A) * op(B) + beta * C
 //
 // op(A) is M x K (A col-major M x K, or its transpose stored K x M); op(B) is K x N.
-// GB300 runs FP64 FMA at about 1.26 TFLOP/s and this MMA at about 4 TFLOP/s, and the
-// dense products of the Newton solve are small (n of a few hundred to a few thousand),
-// so four tile shapes are compiled (64 x 64 for large products, 32 x 32 and 16 x 16 with
-// long K steps for n ~ 200-500, 64 x 8 for the n x r factors) and the grid is filled by
-// splitting a long K across CTAs when the M x N tile count is below the SM count; the
-// K-slices write partial tiles to scratch and a second kernel reduces them in a fixed
-// order (results are bitwise reproducible).
+// On GB300 this MMA issues to the same FP64 pipe as FMA (about 1.1-1.2 TFLOP/s either way);
+// it is used for its operand reuse (fewer shared-memory reads per flop).  The dense products
+// of the Newton solve range from n ~ 200 to n ~ 5000, so four tile shapes are compiled
+// (64 x 64 for large products, 32 x 32 and 16 x 16 with long K steps for n ~ 200-500,
+// 32 x 8 for the n x r factors) and the grid is filled by splitting a long K across CTAs
+// when the M x N tile count is small; the K-slices write partial tiles to scratch and the
+// last slice of each tile adds them in a fixed order (results are bitwise reproducible).
 #include "common.cuh"
 #include "kernels.h"
 
@@ -169,7 +169,8 @@ gemm_f64_kernel(int M, int N, int K, int kchunk, double alpha,
   if (tid == 0) *ticket = 0u;
 }
 
-template <int BM, int BN, int WARPS_M, int BK>
+// CPS: CTAs per SM the K split aims for (more for the large tile, whose CTAs are few and long)
+template <int BM, int BN, int WARPS_M, int BK, int CPS = 2>
 cudaError_t launch(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
                    int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, double* ws,
                    size_t ws_elems, int64_t* launches, int flags, const int32_t* done) {
@@ -180,7 +181,7 @@ cudaError_t launch(cudaStream_t st, bool tA, bool tB, int M, int N, int K, doubl
   // the last kGemmTickets doubles of ws hold the per-tile tickets of the split-K reduction
   const size_t part_elems = ws_elems > kGemmTicketDoubles ? ws_elems - kGemmTicketDoubles : 0;
   if (K > 0 && ws != nullptr && gm * gn <= kGemmTickets) {
-    int want = (2 * g_num_sms + tiles - 1) / tiles;               // about two CTAs per SM
+    int want = (CPS * g_num_sms + tiles - 1) / tiles;             // about CPS CTAs per SM
     int maxS = K / (2 * BK);                                       // at least two K steps per slice
     S = want < maxS ? want : maxS;
     if (S < 1) S = 1;
@@ -216,7 +217,7 @@ cudaError_t gemm_f64(cudaStream_t st, bool tA, bool tB, int M, int N, int K, dou
   if ((int64_t)M * N <= 512 * 512)
     return launch<32, 32, 2, 32>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, launches,
                                  flags, done);
-  return launch<64, 64, 2, 16>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, launches,
+  return launch<64, 64, 2, 16, 6>(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, launches,
                                flags, done);
 }
 

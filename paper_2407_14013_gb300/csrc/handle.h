@@ -20,6 +20,7 @@ struct Space {
   double *Y = nullptr, *F = nullptr, *Z = nullptr, *Tm = nullptr, *H = nullptr, *Hp = nullptr, *Up = nullptr;
   double *zsvec = nullptr, *partY = nullptr, *partA = nullptr, *sd = nullptr, *wm = nullptr;
   double *partB = nullptr, *partBt = nullptr, *partC = nullptr;
+  double *ypos = nullptr, *zpos = nullptr;     // SPARSE_COO: A^T(y) and E Y E at the pattern positions
   double *x = nullptr, *rv = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr;
   double* ws = nullptr;                        // split-K GEMM scratch
   size_t ws_elems = 0;
@@ -82,7 +83,8 @@ struct sdp_handle {
   size_t gj_work_elems = 0;
   double *ubatch = nullptr, *Gb = nullptr, *Hb = nullptr;
   int pinv_dim = 0;                 // order of the largest preconditioner core the options allow
-  int64_t b_elems = 0;              // capacity of the explicit B = A Q (m x d) and of B^T
+  int64_t b_elems = 0;              // capacity of the explicit B = A Q (m x d)
+  int64_t bt_elems = 0;             // capacity of B^T (d x m)
   int64_t bs_elems = 0;             // capacity of D^{-1/2} B^T (m-space core by a product)
   wc::Space s64;                        // FP64 solve, outer refinement of the mixed form
   wc::Space sin;                        // inner solve of the mixed form (own vectors and control block)

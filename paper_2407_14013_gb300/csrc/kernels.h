@@ -125,6 +125,7 @@ struct SparseA {
   const double* val = nullptr;
   int32_t *con_ptr = nullptr, *pos_r = nullptr, *pos_c = nullptr, *pos_ptr = nullptr, *perm = nullptr;
   int32_t* epos = nullptr;                                  // position index of each entry (nnz)
+  int32_t* cptr = nullptr;                                  // positions of column b: cptr[b] .. cptr[b+1]-1
   int32_t *yptr = nullptr, *ycol = nullptr, *ypidx = nullptr;   // CSR of the pattern: row i holds
                                                             // (column, position index) pairs
 };
@@ -143,10 +144,15 @@ void sparse_posval(cudaStream_t st, const SparseA& S, const double* y, double* y
 // Out (n x ncols, ld ldo) = Y Bm (Bm n x ncols, ld ldb) with Y = A^T(y) given by its position values.
 void sparse_sym_spmm(cudaStream_t st, const SparseA& S, int n, int ncols, const double* ypos, const double* Bm,
                      int64_t ldb, double* Out, int64_t ldo, const int32_t* done, int64_t* launches);
-// zpos[p] = (E G)[a_p, b_p] = <E[:, a_p], G[:, b_p]> for symmetric E (n x n): the entries of E Y E at
-// the pattern positions with G = Y E.
-void sparse_pos_dots(cudaStream_t st, const SparseA& S, int n, const double* E, const double* G, double* zpos,
-                     const int32_t* done, int64_t* launches);
+// F = E Y (n x n) for E (n x n) and Y = A^T(y) given by its position values.
+void sparse_EY(cudaStream_t st, const SparseA& S, int n, const double* ypos, const double* E, double* F,
+               const int32_t* done, int64_t* launches);
+// zpos[p] = (F E)[a_p, b_p] = <F[b_p, :], E[:, a_p]> for symmetric E and F E (E Y E with F = E Y);
+// needs n doubles of shared memory per CTA: sparse_prepare(n) once per process and n (before any
+// capture; cudaErrorInvalidValue when n * 8 bytes exceed 227 KB).
+cudaError_t sparse_prepare(int n);
+cudaError_t sparse_pos_dots_col(cudaStream_t st, const SparseA& S, int n, const double* E, const double* F,
+                                double* zpos, const int32_t* done, int64_t* launches);
 // out[i] = <A_i, Z + sym(U Q^T)> with Z given by its values at the pattern positions (zpos, may be
 // NULL: Z = 0) and U, Q n x r (U may be NULL).
 void sparse_apply_pos(cudaStream_t st, const SparseA& S, int n, int m, int r, const double* zpos, const double* U,
@@ -160,6 +166,8 @@ void sparse_sumsq(cudaStream_t st, const SparseA& S, double* out, double* scratc
 size_t spd_inverse_work(int n);
 cudaError_t spd_inverse(cudaStream_t st, int n, double* A, double* work, size_t work_elems,
                         double* gemm_ws, size_t gemm_ws_elems, int32_t* status, int64_t* launches);
+// A[j, i] = A[i, j] for i > j (n x n, column-major): the upper triangle from the lower.
+void lower_to_full(cudaStream_t st, int n, double* A, int64_t* launches);
 // Cholesky A = L L^T (L into A, upper zeroed) and Linv = L^{-1}; same workspace.
 cudaError_t spd_cholesky(cudaStream_t st, int n, double* A, double* Linv, double* work, size_t work_elems,
                          double* gemm_ws, size_t gemm_ws_elems, int32_t* status, int64_t* launches);

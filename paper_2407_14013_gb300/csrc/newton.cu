@@ -94,8 +94,8 @@ void carve_space(sdp_handle* h, Carver& c, Space& S) {
   S.E = c.take<double>(nn);
   S.EE = (h->kind == SDP_A_DIAG) ? c.take<double>(nn) : nullptr;
   S.Dv = c.take<double>(dm);
-  S.B = c.take<double>(h->b_elems);
-  S.Bt = c.take<double>(h->b_elems);
+  S.B = h->b_elems ? c.take<double>(h->b_elems) : nullptr;
+  S.Bt = h->bt_elems ? c.take<double>(h->bt_elems) : nullptr;
   S.Pinv = c.take<double>(pc * pc);
   S.Y = c.take<double>(nn);
   S.F = c.take<double>(nn);
@@ -107,6 +107,10 @@ void carve_space(sdp_handle* h, Carver& c, Space& S) {
   if (h->kind == SDP_A_DENSE_SVEC) {
     S.zsvec = c.take<double>(h->N);
     S.partY = c.take<double>((size_t)h->GY * h->N);
+  }
+  if (h->kind == SDP_A_SPARSE_COO) {
+    S.ypos = c.take<double>(h->sp.npos);
+    S.zpos = c.take<double>(h->sp.npos);
   }
   size_t pa = std::max(rows_gemv_part_elems(m, dm), rows_gemv_part_elems(pc, pc));
   if (h->kind == SDP_A_DENSE_SVEC) pa = std::max(pa, rows_gemv_part_elems(m, h->N));
@@ -161,7 +165,7 @@ size_t carve(sdp_handle* h, char* base) {
   h->lam_s = c.take<double>(n);
   h->e = c.take<double>(n);
   h->Ve = c.take<double>(nn);
-  h->Bs = c.take<double>(h->bs_elems);
+  h->Bs = h->bs_elems ? c.take<double>(h->bs_elems) : nullptr;
   h->Cw = c.take<double>(nn);
   h->g = c.take<double>(vt);
   h->dotbuf = c.take<double>(1024);
@@ -173,6 +177,11 @@ size_t carve(sdp_handle* h, char* base) {
     h->sp.pos_c = c.take<int32_t>(h->sp.npos);
     h->sp.pos_ptr = c.take<int32_t>(h->sp.npos + 1);
     h->sp.perm = c.take<int32_t>(h->sp.nnz);
+    h->sp.epos = c.take<int32_t>(h->sp.nnz);
+    h->sp.cptr = c.take<int32_t>(n + 1);
+    h->sp.yptr = c.take<int32_t>(n + 1);
+    h->sp.ycol = c.take<int32_t>(h->sp.nnzY);
+    h->sp.ypidx = c.take<int32_t>(h->sp.nnzY);
   }
   h->gj_work = c.take<double>(h->gj_work_elems);
   if (h->kind == SDP_A_DENSE_SVEC) {
@@ -238,7 +247,8 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   if (opt.pcg_start < 0 || opt.pcg_start > 1) return fail(nullptr, SDP_EINVAL, "bad pcg_start");
 
   // SPARSE_COO: validate the entries and build the index tables on the host (once per problem)
-  std::vector<int32_t> sp_con_ptr, sp_pos_r, sp_pos_c, sp_pos_ptr, sp_perm;
+  std::vector<int32_t> sp_con_ptr, sp_pos_r, sp_pos_c, sp_pos_ptr, sp_perm, sp_epos, sp_yptr, sp_ycol, sp_ypidx,
+      sp_cptr;
   std::vector<double> sp_rownorm2;
   if (prob->kind == SDP_A_SPARSE_COO) {
     const int64_t nnz = prob->nnz;
@@ -276,6 +286,34 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
       }
     }
     sp_pos_ptr.push_back((int32_t)nnz);
+    // entry -> position, and the CSR of the symmetric pattern of A^T(y): row i holds (c, p) for
+    // every position p = (i, c) and, off the diagonal, (c, p) for p = (c, i)
+    const int npos = (int)sp_pos_r.size();
+    sp_epos.resize(nnz);
+    for (int p = 0; p < npos; ++p)
+      for (int k = sp_pos_ptr[p]; k < sp_pos_ptr[p + 1]; ++k) sp_epos[sp_perm[k]] = p;
+    // positions are sorted by column: cptr[b] .. cptr[b+1]-1 are those of column b
+    sp_cptr.assign(n + 1, 0);
+    for (int p = 0; p < npos; ++p) sp_cptr[sp_pos_c[p] + 1] += 1;
+    for (int b = 0; b < n; ++b) sp_cptr[b + 1] += sp_cptr[b];
+    sp_yptr.assign(n + 1, 0);
+    for (int p = 0; p < npos; ++p) {
+      sp_yptr[sp_pos_r[p] + 1] += 1;
+      if (sp_pos_r[p] != sp_pos_c[p]) sp_yptr[sp_pos_c[p] + 1] += 1;
+    }
+    for (int i = 0; i < n; ++i) sp_yptr[i + 1] += sp_yptr[i];
+    sp_ycol.resize(sp_yptr[n]);
+    sp_ypidx.resize(sp_yptr[n]);
+    std::vector<int32_t> fill(sp_yptr.begin(), sp_yptr.end() - 1);
+    for (int p = 0; p < npos; ++p) {
+      const int a = sp_pos_r[p], b = sp_pos_c[p];
+      sp_ycol[fill[a]] = b;
+      sp_ypidx[fill[a]++] = p;
+      if (a != b) {
+        sp_ycol[fill[b]] = a;
+        sp_ypidx[fill[b]++] = p;
+      }
+    }
   }
 
   h = new (std::nothrow) sdp_handle();
@@ -283,6 +321,7 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   if (prob->kind == SDP_A_SPARSE_COO) {
     h->sp.nnz = prob->nnz;
     h->sp.npos = (int)sp_pos_r.size();
+    h->sp.nnzY = (int64_t)sp_ycol.size();
     h->sp.con = prob->a_con;
     h->sp.row = prob->a_row;
     h->sp.col = prob->a_col;
@@ -302,12 +341,17 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   h->pinv_dim = opt.precond_space == 1 ? h->d_max : opt.precond_space == 2 ? m : std::min(h->d_max, m);
   // explicit B = A Q: DIAG forms its m-space core in closed form and its products with B from
   // Vs, so it needs B only for the d-space core (auto selects that only at r = 1, d = n)
+  // SPARSE_COO reads B only to form the core (its products with B go through the pattern);
+  // DENSE_SVEC streams B and B^T in every preconditioner application
+  const bool m_space_possible = opt.precond_space == 2 || (opt.precond_space == 0 && h->d_max > m);
   if (h->kind == SDP_A_DIAG) {
     h->b_elems = opt.precond_space == 2 ? 0 : (int64_t)m * (opt.precond_space == 1 ? h->d_max : dof(n, 1));
+    h->bt_elems = h->b_elems;
     h->bs_elems = 0;
   } else {
     h->b_elems = (int64_t)m * h->d_max;
-    h->bs_elems = opt.precond_space == 1 ? 0 : (int64_t)m * h->d_max;
+    h->bt_elems = (h->kind == SDP_A_SPARSE_COO && !h->mixed) ? 0 : h->b_elems;
+    h->bs_elems = m_space_possible ? (int64_t)m * h->d_max : 0;
   }
   int dev = 0;
   cudaGetDevice(&dev);
@@ -339,12 +383,22 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
     return fail(nullptr, SDP_ECUDA, std::string("workspace clear failed: ") + cudaGetErrorString(e));
   }
   if (h->kind == SDP_A_SPARSE_COO) {
+    if (sparse_prepare(n) != cudaSuccess) {
+      cudaGetLastError();
+      sdp_destroy(h);
+      return fail(nullptr, SDP_EUNSUPPORTED, "SPARSE_COO is built for n <= 29000 (one row of E Y in shared memory)");
+    }
     const size_t b32 = sizeof(int32_t);
     CU(cudaMemcpyAsync(h->sp.con_ptr, sp_con_ptr.data(), sp_con_ptr.size() * b32, cudaMemcpyHostToDevice, h->st));
     CU(cudaMemcpyAsync(h->sp.pos_r, sp_pos_r.data(), sp_pos_r.size() * b32, cudaMemcpyHostToDevice, h->st));
     CU(cudaMemcpyAsync(h->sp.pos_c, sp_pos_c.data(), sp_pos_c.size() * b32, cudaMemcpyHostToDevice, h->st));
     CU(cudaMemcpyAsync(h->sp.pos_ptr, sp_pos_ptr.data(), sp_pos_ptr.size() * b32, cudaMemcpyHostToDevice, h->st));
     CU(cudaMemcpyAsync(h->sp.perm, sp_perm.data(), sp_perm.size() * b32, cudaMemcpyHostToDevice, h->st));
+    CU(cudaMemcpyAsync(h->sp.epos, sp_epos.data(), sp_epos.size() * b32, cudaMemcpyHostToDevice, h->st));
+    CU(cudaMemcpyAsync(h->sp.cptr, sp_cptr.data(), sp_cptr.size() * b32, cudaMemcpyHostToDevice, h->st));
+    CU(cudaMemcpyAsync(h->sp.yptr, sp_yptr.data(), sp_yptr.size() * b32, cudaMemcpyHostToDevice, h->st));
+    CU(cudaMemcpyAsync(h->sp.ycol, sp_ycol.data(), sp_ycol.size() * b32, cudaMemcpyHostToDevice, h->st));
+    CU(cudaMemcpyAsync(h->sp.ypidx, sp_ypidx.data(), sp_ypidx.size() * b32, cudaMemcpyHostToDevice, h->st));
   }
   e = cudaMallocHost(&h->ctl_host, sizeof(PcgCtl));
   if (e != cudaSuccess) {
@@ -473,16 +527,16 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
     launch_ap_finish<double>(st, m, d, n, r, S.partA, h->SA, nullptr, S.Vs, S.H, S.Dv, pin, gsub, out, mode, S.ctl,
                              h->dotbuf, h->counter, L);
   } else if (h->kind == SDP_A_SPARSE_COO) {
-    sparse_adjoint(st, h->sp, n, pu, 1.0, S.Y, done, L);               // Y = A^T(p_u) on the pattern
-    cudaStream_t s1 = fork(h, 1, 1);
-    CU(gemm_f64(s1, false, false, n, r, n, 1.0, S.Y, n, Q, n, 0.0, S.Tm, n, h->ws_b[1], h->ws_b_elems, L, done));
+    // Y = A^T(p_u) kept as its pattern values; E Y E only at the pattern positions
+    sparse_posval(st, h->sp, pu, S.ypos, done, L);
+    cudaStream_t s1 = fork(h, 1, 1);                                   // H = Vs^T (Y Q)
+    sparse_sym_spmm(s1, h->sp, n, r, S.ypos, Q, n, S.Tm, n, done, L);
     CU(gemm_f64(s1, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, h->ws_b[1], h->ws_b_elems, L, done));
-    CU(gemm_f64(st, false, false, n, n, n, 1.0, S.E, n, S.Y, n, 0.0, S.F, n, S.ws, S.ws_elems, L, done));
-    CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, S.ws_elems, L, done,
-                GEMM_LOWER));
+    sparse_EY(st, h->sp, n, S.ypos, S.E, S.F, done, L);                   // F = E Y
+    CU(sparse_pos_dots_col(st, h->sp, n, S.E, S.F, S.zpos, done, L));     // (F E)_ab at the positions
     join(h, 0, 2);
     join(h, 1, 3);
-    sparse_apply(st, h->sp, n, m, r, S.Z, S.Up, Q, S.partA, done, L);     // A(E Y E + sym(Up Q^T))
+    sparse_apply_pos(st, h->sp, n, m, r, S.zpos, S.Up, Q, S.partA, done, L);   // A(E Y E + sym(Up Q^T))
     launch_ap_finish<double>(st, m, d, n, r, S.partA, 1, nullptr, S.Vs, S.H, S.Dv, pin, gsub, out, mode, S.ctl,
                              h->dotbuf, h->counter, L);
   } else {
@@ -566,7 +620,36 @@ sdp_status apply_precond(sdp_handle* h, Space& S, const double* rin, double* zou
   cudaStream_t st = h->st;
   int64_t* L = &h->launches;
   const int Sm = rows_gemv_slabs(d, m);   // slabs of the products with the rows of B^T
-  if (h->space == 1) {
+  if (h->kind == SDP_A_SPARSE_COO) {
+    // the products with B through the pattern: B t = A(sym(Vs unpack(t) Q^T)) and
+    // B^T u = pack(Vs^T (A^T(u) Q)), A^T(u) kept as its pattern values
+    const int n = h->n, r = h->r;
+    const double* Q = S.Vs;
+    if (h->space == 1) {
+      sparse_posval(st, h->sp, rin, S.ypos, done, L);
+      sparse_sym_spmm(st, h->sp, n, r, S.ypos, Q, n, S.Tm, n, done, L);
+      CU(gemm_f64(st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, done));
+      launch_pc_d_s_H(st, m, d, n, r, S.H, rin, S.sd, S.ctl, L);           // s = r_v - beta^{-1} B^T r_u
+      rows_gemv<double>(st, S.Pinv, d, d, S.sd, S.partC, done, L);          // C^{-1} s
+      launch_pc_d_zv<double>(st, m, d, rows_gemv_slabs(d, d), S.partC, zout, S.ctl, L);   // z_v = -C^{-1} s
+      h_unpack<double>(st, n, r, zout + m, S.Hp, done, L);
+      CU(gemm_f64(st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, S.ws_elems, L, done));
+      sparse_apply_pos(st, h->sp, n, m, r, nullptr, S.Up, Q, S.partA, done, L);  // B z_v
+      launch_pc_zu_dot<double>(st, m, d, 1, S.partA, 1, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L);
+    } else {
+      h_unpack<double>(st, n, r, rin + m, S.Hp, done, L, S.Dv);            // unpack(D^{-1} r_v)
+      CU(gemm_f64(st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, S.ws_elems, L, done));
+      sparse_apply_pos(st, h->sp, n, m, r, nullptr, S.Up, Q, S.partA, done, L);
+      launch_pc_m_w<double>(st, m, 1, S.partA, rin, S.wm, S.ctl, L);      // w = r_u + B D^{-1} r_v
+      rows_gemv<double>(st, S.Pinv, m, m, S.wm, S.partC, done, L);         // K^{-1} w
+      launch_pc_m_w<double>(st, m, rows_gemv_slabs(m, m), S.partC, nullptr, zout, S.ctl, L);  // z_u
+      sparse_posval(st, h->sp, zout, S.ypos, done, L);
+      sparse_sym_spmm(st, h->sp, n, r, S.ypos, Q, n, S.Tm, n, done, L);
+      CU(gemm_f64(st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, done));
+      launch_diag_zv(st, m, d, n, r, S.H, rin, S.Dv, zout, S.ctl, L);      // z_v = D^{-1}(B^T z_u - r_v)
+      launch_pc_zu_dot<double>(st, m, d, 0, nullptr, 2, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L);
+    }
+  } else if (h->space == 1) {
     rows_gemv<double>(st, S.Bt, d, m, rin, S.partB, done, L);              // B^T r_u (rows of B^T)
     // C^{-1} s with s = r_v - beta^{-1} B^T r_u formed while staged
     rows_gemv_formed(st, S.Pinv, d, d, rin + m, S.partB, Sm, -1.0, &S.ctl->beta_pc, nullptr, S.partC, done, L);
@@ -754,7 +837,9 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   h->d = d;
   h->space = h->opt.precond_space == 0 ? (d <= m ? 1 : 2) : h->opt.precond_space;
   split_scale_cols(st, n, S.Vs, h->e, h->Ve, L);
-  CU(gemm_f64(st, false, true, n, n, n, 1.0, h->Ve, n, S.Vs, n, 0.0, S.E, n, S.ws, ws, L));
+  // E = Ve Vs^T is symmetric: the lower triangle by the product, the upper by a mirror
+  CU(gemm_f64(st, false, true, n, n, n, 1.0, h->Ve, n, S.Vs, n, 0.0, S.E, n, S.ws, ws, L, nullptr, GEMM_LOWER));
+  lower_to_full(st, n, S.E, L);
   split_sigma(st, n, r, h->lam_s, h->ctl, S.Dv, L);
 
   // ---- a2: B = A Q and the preconditioner core ----
@@ -901,11 +986,14 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   else if (h->kind == SDP_A_SPARSE_COO) sparse_adjoint(st, h->sp, n, u, 1.0, S.Y, nullptr, L);
   else launch_diag_matrix(st, n, u, S.Y, L);
   launch_recover_pre(st, n, m, S.Y, Ct, u, h->Cw, dy, dS, h->ctl, L);
+  // dX = E Cw E + sym(Up Q^T) with Up = Vs unpack(v): lower triangles by products, then a mirror
   CU(gemm_f64(st, false, false, n, n, n, 1.0, S.E, n, h->Cw, n, 0.0, S.F, n, S.ws, ws, L));
-  CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, ws, L));
+  CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, dX, n, S.ws, ws, L, nullptr, GEMM_LOWER));
   h_unpack<double>(st, n, r, v, S.Hp, nullptr, L);
   CU(gemm_f64(st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, ws, L));
-  launch_sym_plus_full(st, n, r, S.Z, S.Up, Q, dX, L);
+  CU(gemm_f64(st, false, true, n, n, r, 0.5, S.Up, n, Q, n, 1.0, dX, n, S.ws, ws, L, nullptr, GEMM_LOWER));
+  CU(gemm_f64(st, false, true, n, n, r, 0.5, Q, n, S.Up, n, 1.0, dX, n, S.ws, ws, L, nullptr, GEMM_LOWER));
+  lower_to_full(st, n, dX, L);
   CU(cudaEventRecord(h->ev_phase[3], st));
   CU(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));

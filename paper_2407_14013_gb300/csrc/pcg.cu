@@ -231,6 +231,16 @@ __global__ void diag_zv_kernel(int m, int d, int n, int r, const double* __restr
   z[m + h] = (pack_at(H, n, n, r, h) - rv[m + h]) / Dv[h];
 }
 
+// d-space with B^T r_u = pack(H): s = r_v - beta^{-1} pack(H)
+__global__ void pc_d_s_H_kernel(int m, int d, int n, int r, const double* __restrict__ H,
+                                const double* __restrict__ rv, double* __restrict__ s,
+                                const PcgCtl* __restrict__ ctl) {
+  if (ctl->done) return;
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= d) return;
+  s[h] = rv[m + h] - pack_at(H, n, n, r, h) / ctl->beta_pc;
+}
+
 // Tm = Q (Lam - tau I): the first r columns of Vs scaled by lam_j - tau
 __global__ void shift_cols_kernel(int n, int r, const double* __restrict__ Vs, const double* __restrict__ lam_s,
                                   const PcgCtl* __restrict__ ctl, double* __restrict__ Tm) {
@@ -389,19 +399,6 @@ __global__ void recover_pre_kernel(int n, int m, const double* __restrict__ Yu, 
     dS[q] = c - y / t2;
   }
   if (q < m) dy[q] = u[q] / t2;
-}
-
-// dX = sym(Z) + sym(U Q^T)
-__global__ void sym_plus_full_kernel(int n, int r, const double* __restrict__ Z, const double* __restrict__ U,
-                                     const double* __restrict__ Q, double* __restrict__ out) {
-  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= (int64_t)n * n) return;
-  int a = (int)(q % n), b = (int)(q / n);
-  double v = 0.5 * (Z[a + (int64_t)b * n] + Z[b + (int64_t)a * n]);
-  double t = 0.0;
-  for (int k = 0; k < r; ++k)
-    t += U[a + (int64_t)k * n] * Q[b + (int64_t)k * n] + Q[a + (int64_t)k * n] * U[b + (int64_t)k * n];
-  out[q] = v + 0.5 * t;
 }
 
 // C += diag(Dv) * c_d + c_i * I  on an n x n matrix
@@ -641,12 +638,6 @@ void launch_recover_pre(cudaStream_t st, int n, int m, const double* Yu, const d
   ++*launches;
 }
 
-void launch_sym_plus_full(cudaStream_t st, int n, int r, const double* Z, const double* U, const double* Q,
-                          double* out, int64_t* launches) {
-  sym_plus_full_kernel<<<nblk((int64_t)n * n, VT), VT, 0, st>>>(n, r, Z, U, Q, out);
-  ++*launches;
-}
-
 void launch_add_diag(cudaStream_t st, int n, double* C, const double* Dv, double c_i, int64_t* launches) {
   add_diag_kernel<<<nblk(n, VT), VT, 0, st>>>(n, C, Dv, c_i);
   ++*launches;
@@ -695,6 +686,12 @@ void launch_diag_w(cudaStream_t st, int n, int r, const double* U, const double*
 void launch_diag_zv(cudaStream_t st, int m, int d, int n, int r, const double* H, const double* rv, const double* Dv,
                     double* z, const PcgCtl* ctl, int64_t* launches) {
   diag_zv_kernel<<<nblk(d, VT), VT, 0, st>>>(m, d, n, r, H, rv, Dv, z, ctl);
+  ++*launches;
+}
+
+void launch_pc_d_s_H(cudaStream_t st, int m, int d, int n, int r, const double* H, const double* rv, double* s,
+                     const PcgCtl* ctl, int64_t* launches) {
+  pc_d_s_H_kernel<<<nblk(d, VT), VT, 0, st>>>(m, d, n, r, H, rv, s, ctl);
   ++*launches;
 }
 

@@ -51,8 +51,6 @@ void launch_diag_matrix(cudaStream_t st, int n, const double* u, double* Y, int6
 void launch_hadamard_sq(cudaStream_t st, int64_t nn, const double* E, double* EE, int64_t* launches);
 void launch_recover_pre(cudaStream_t st, int n, int m, const double* Yu, const double* Ct, const double* u,
                         double* Cw, double* dy, double* dS, const PcgCtl* ctl, int64_t* launches);
-void launch_sym_plus_full(cudaStream_t st, int n, int r, const double* Z, const double* U, const double* Q,
-                          double* out, int64_t* launches);
 void launch_add_diag(cudaStream_t st, int n, double* C, const double* Dv, double c_i, int64_t* launches);
 void launch_scale_B(cudaStream_t st, int m, int d, const double* B, const double* Dv, double* Bs, int64_t* launches);
 void launch_correction_rhs(cudaStream_t st, int m, int d, const double* rho, double* out, int64_t* launches);
@@ -70,6 +68,8 @@ void launch_diag_w(cudaStream_t st, int n, int r, const double* U, const double*
                    const PcgCtl* ctl, int64_t* launches);
 void launch_diag_zv(cudaStream_t st, int m, int d, int n, int r, const double* H, const double* rv, const double* Dv,
                     double* z, const PcgCtl* ctl, int64_t* launches);
+void launch_pc_d_s_H(cudaStream_t st, int m, int d, int n, int r, const double* H, const double* rv, double* s,
+                     const PcgCtl* ctl, int64_t* launches);
 void launch_shift_cols(cudaStream_t st, int n, int r, const double* Vs, const double* lam_s, const PcgCtl* ctl,
                        double* Tm, int64_t* launches);
 void launch_diag_K(cudaStream_t st, int n, const double* G, const double* E, const PcgCtl* ctl, double* K,

@@ -145,20 +145,56 @@ __global__ void sym_spmm_kernel(int n, const int32_t* __restrict__ yptr, const i
   Out[i + (int64_t)j * ldo] = s;
 }
 
-// one warp per position: <E[:, a], G[:, b]>
-__global__ void pos_dots_kernel(int npos, const int32_t* __restrict__ pos_r, const int32_t* __restrict__ pos_c,
-                                int n, const double* __restrict__ E, const double* __restrict__ G,
-                                double* __restrict__ zpos, const int32_t* __restrict__ done) {
+// F = E Y, column c of F = sum over the pattern entries (r, c) of Y[r, c] E[:, r]: one CTA per
+// (column, block of 1024 rows); the entry loop is uniform over the CTA and every load of E is a
+// coalesced column segment.
+constexpr int EY_ROWS = 4;   // rows per thread
+__global__ void sparse_EY_kernel(int n, const int32_t* __restrict__ yptr, const int32_t* __restrict__ ycol,
+                                 const int32_t* __restrict__ ypidx, const double* __restrict__ ypos,
+                                 const double* __restrict__ E, double* __restrict__ F,
+                                 const int32_t* __restrict__ done) {
   if (done && *done) return;
-  const int lane = threadIdx.x & 31;
-  const int p = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  if (p >= npos) return;
-  const double* ea = E + (int64_t)pos_r[p] * n;
-  const double* gb = G + (int64_t)pos_c[p] * n;
-  double s = 0.0;
-  for (int c = lane; c < n; c += 32) s = fma(ea[c], gb[c], s);
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) zpos[p] = s;
+  const int c = blockIdx.x;
+  const int i0 = blockIdx.y * (ST * EY_ROWS) + threadIdx.x;
+  double acc[EY_ROWS];
+#pragma unroll
+  for (int q = 0; q < EY_ROWS; ++q) acc[q] = 0.0;
+  for (int k = yptr[c]; k < yptr[c + 1]; ++k) {
+    const double w = ypos[ypidx[k]];
+    const double* ec = E + (int64_t)ycol[k] * n;
+#pragma unroll
+    for (int q = 0; q < EY_ROWS; ++q) {
+      const int i = i0 + q * ST;
+      if (i < n) acc[q] = fma(w, ec[i], acc[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < EY_ROWS; ++q) {
+    const int i = i0 + q * ST;
+    if (i < n) F[i + (int64_t)c * n] = acc[q];
+  }
+}
+
+// (E Y E)[a, b] = <F[b, :], E[:, a]> with F = E Y, for the positions (a, b) of column b: one CTA
+// per column b stages row b of F in shared memory, one warp per position reads a column of E.
+__global__ void pos_dots_col_kernel(int n, const int32_t* __restrict__ cptr, const int32_t* __restrict__ pos_r,
+                                    const double* __restrict__ E, const double* __restrict__ F,
+                                    double* __restrict__ zpos, const int32_t* __restrict__ done) {
+  if (done && *done) return;
+  extern __shared__ double frow[];
+  const int b = blockIdx.x;
+  const int p0 = cptr[b], p1 = cptr[b + 1];
+  if (p0 == p1) return;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) frow[c] = F[b + (int64_t)c * n];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int p = p0 + warp; p < p1; p += nw) {
+    const double* ea = E + (int64_t)pos_r[p] * n;
+    double s = 0.0;
+    for (int c = lane; c < n; c += 32) s = fma(ea[c], frow[c], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) zpos[p] = s;
+  }
 }
 
 __global__ void sparse_apply_pos_kernel(int n, int m, int r, const int32_t* __restrict__ con_ptr,
@@ -243,11 +279,25 @@ void sparse_sym_spmm(cudaStream_t st, const SparseA& S, int n, int ncols, const 
   if (launches) ++*launches;
 }
 
-void sparse_pos_dots(cudaStream_t st, const SparseA& S, int n, const double* E, const double* G, double* zpos,
-                     const int32_t* done, int64_t* launches) {
-  if (S.npos > 0)
-    pos_dots_kernel<<<nb((int64_t)S.npos * 32), ST, 0, st>>>(S.npos, S.pos_r, S.pos_c, n, E, G, zpos, done);
+void sparse_EY(cudaStream_t st, const SparseA& S, int n, const double* ypos, const double* E, double* F,
+               const int32_t* done, int64_t* launches) {
+  dim3 grid((unsigned)n, (unsigned)((n + ST * EY_ROWS - 1) / (ST * EY_ROWS)));
+  sparse_EY_kernel<<<grid, ST, 0, st>>>(n, S.yptr, S.ycol, S.ypidx, ypos, E, F, done);
   if (launches) ++*launches;
+}
+
+cudaError_t sparse_prepare(int n) {
+  const size_t smem = (size_t)n * sizeof(double);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(pos_dots_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t sparse_pos_dots_col(cudaStream_t st, const SparseA& S, int n, const double* E, const double* F,
+                                double* zpos, const int32_t* done, int64_t* launches) {
+  const size_t smem = (size_t)n * sizeof(double);
+  pos_dots_col_kernel<<<(unsigned)n, ST, smem, st>>>(n, S.cptr, S.pos_r, E, F, zpos, done);
+  if (launches) ++*launches;
+  return cudaGetLastError();
 }
 
 void sparse_apply_pos(cudaStream_t st, const SparseA& S, int n, int m, int r, const double* zpos, const double* U,

@@ -201,6 +201,11 @@ cudaError_t spd_inverse(cudaStream_t st, int n, double* A, double* work, size_t 
   return cudaGetLastError();
 }
 
+void lower_to_full(cudaStream_t st, int n, double* A, int64_t* launches) {
+  lower_to_full_kernel<<<nblk((int64_t)n * n, 256), 256, 0, st>>>(n, A);
+  if (launches) ++*launches;
+}
+
 // A = L L^T: L into A (lower, upper zeroed), L^{-1} into Linv (n x n; NULL: factor only).
 // work as for spd_inverse.
 cudaError_t spd_cholesky(cudaStream_t st, int n, double* A, double* Linv, double* work, size_t work_elems,

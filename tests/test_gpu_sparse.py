@@ -29,6 +29,9 @@ CASES = [
     ("completion8x8", lambda: W.completion(8, 8, 2, 0.4, 11), 2, 3),
     ("completion20x15", lambda: W.completion(20, 15, 2, 0.3, 13), 2, 4),
     ("random_sparse", lambda: W.random_sparse(12, 30, 3, 12), 2, 4),
+    # several tiles of every kernel, ragged n, d < m and d > m
+    ("completion150x130", lambda: W.completion(150, 130, 3, 0.08, 21), 3, 3),
+    ("random_sparse257", lambda: W.random_sparse(257, 700, 4, 22), 3, 4),
 ]
 
 
