@@ -127,7 +127,7 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def other_configs(dev, reps: int = 2):
+def other_configs(dev, reps: int = 2, only=None):
     """The other workloads, measured beside the headline one (not part of its timed steps).
 
     - MaxCut n=64 (m=64, DIAG, r_hat=12, FP64): time to a 1e-8 relative gap of the whole
@@ -177,7 +177,34 @@ def other_configs(dev, reps: int = 2):
         return rows
 
     out = {}
+    want = lambda name: only is None or name == only
     # MaxCut n=64: time to gap (whole IPM on the device)
+    if want("maxcut64"):
+        out.update(_maxcut64(dev, t, newton_rows))
+    # MaxCut n=5000, r=100
+    if want("maxcut5000"):
+        prob = W.workload("maxcut5000")
+        sp = W.scaling_point(5000, 100, 1e-4, 3100)
+        Ct, bt = W.newton_rhs(5000, 5000, 3200)
+        out["maxcut5000_r100"] = {"workload": "MaxCut n=5000 avg degree 8, N(0,1) weights, DIAG, r=100, synthetic "
+                                              "scaling point mu=1e-4",
+                                  "newton": newton_rows(prob, sp, Ct, bt, 100, ["fp64", "mixed_fp32"])}
+    # matrix completion n=2000, m=50000, r=5
+    if want("completion2000"):
+        prob = W.workload("completion2000")
+        sp = W.scaling_point(prob.n, 5, 1e-4, 4100)
+        Ct, bt = W.newton_rhs(prob.n, prob.m, 4200)
+        out["completion2000_r5"] = {"workload": "matrix completion n=1000+1000, m=50000 (5%), rank 5, SPARSE_COO, "
+                                                "r=5, synthetic scaling point mu=1e-4",
+                                    "newton": newton_rows(prob, sp, Ct, bt, 5, ["fp64"])}
+    return out
+
+
+def _maxcut64(dev, t, newton_rows):
+    import torch
+    import workloads as W
+    from paper_2407_14013_gb300 import NewtonSolver
+    out = {}
     prob = W.workload("maxcut64")
     s = NewtonSolver(prob, r_hat=12, device=str(dev))
     b_d, C_d = t(prob.b), t(prob.C)
@@ -198,20 +225,6 @@ def other_configs(dev, reps: int = 2):
                             "us_per_pcg_iter": 1e3 * nr["phase_ms_per_solve"]["rhs_and_pcg"] / max(nr["pcg_iters_per_solve"], 1),
                             "newton": nr}
     s.close()
-    # MaxCut n=5000, r=100
-    prob = W.workload("maxcut5000")
-    sp = W.scaling_point(5000, 100, 1e-4, 3100)
-    Ct, bt = W.newton_rhs(5000, 5000, 3200)
-    out["maxcut5000_r100"] = {"workload": "MaxCut n=5000 avg degree 8, N(0,1) weights, DIAG, r=100, synthetic "
-                                          "scaling point mu=1e-4",
-                              "newton": newton_rows(prob, sp, Ct, bt, 100, ["fp64", "mixed_fp32"])}
-    # matrix completion n=2000, m=50000, r=5
-    prob = W.workload("completion2000")
-    sp = W.scaling_point(prob.n, 5, 1e-4, 4100)
-    Ct, bt = W.newton_rhs(prob.n, prob.m, 4200)
-    out["completion2000_r5"] = {"workload": "matrix completion n=1000+1000, m=50000 (5%), rank 5, SPARSE_COO, "
-                                            "r=5, synthetic scaling point mu=1e-4",
-                                "newton": newton_rows(prob, sp, Ct, bt, 5, ["fp64"])}
     return out
 
 
@@ -394,7 +407,7 @@ def run_ours(args):
             ts.close()
         ttg["mixed_speedup"] = ttg["fp64"]["seconds"] / ttg["mixed_fp32"]["seconds"]
 
-    others = other_configs(dev) if (rank == 0 and not args.no_configs) else None
+    others = other_configs(dev, args.reps) if (rank == 0 and not args.no_configs) else None
 
     # end to end through the C ABI with pinned host buffers (H2D and D2H inside the call)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -473,9 +486,17 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
     ap.add_argument("--no-ttg", action="store_true", help="skip the time-to-gap solves")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads (MaxCut 64 / 5000, completion)")
+    ap.add_argument("--only", choices=["maxcut64", "maxcut5000", "completion2000"],
+                    help="measure only this other workload (one JSON object; no headline line)")
+    ap.add_argument("--reps", type=int, default=2, help="timed Newton solves per row of the other workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.only:
+        import torch
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+        torch.cuda.set_device(dev)
+        print(json.dumps(other_configs(dev, args.reps, only=args.only)))
     else:
         run_ours(args)
 

@@ -532,8 +532,9 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
     cudaStream_t s1 = fork(h, 1, 1);                                   // H = Vs^T (Y Q)
     sparse_sym_spmm(s1, h->sp, n, r, S.ypos, Q, n, S.Tm, n, done, L);
     CU(gemm_f64(s1, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, h->ws_b[1], h->ws_b_elems, L, done));
-    sparse_EY(st, h->sp, n, S.ypos, S.E, S.F, done, L);                   // F = E Y
-    CU(sparse_pos_dots_col(st, h->sp, n, S.E, S.F, S.zpos, done, L));     // (F E)_ab at the positions
+    // (S.F keeps E C~ of the right side for the recovery)
+    sparse_EY(st, h->sp, n, S.ypos, S.E, S.Z, done, L);                   // E Y
+    CU(sparse_pos_dots_col(st, h->sp, n, S.E, S.Z, S.zpos, done, L));     // (E Y E)_ab at the positions
     join(h, 0, 2);
     join(h, 1, 3);
     sparse_apply_pos(st, h->sp, n, m, r, S.zpos, S.Up, Q, S.partA, done, L);   // A(E Y E + sym(Up Q^T))
@@ -921,8 +922,8 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     launch_rhs_finish(st, m, d, n, r, S.partA, h->SA, nullptr, nullptr, bt, Ct, S.H, S.Dv, h->g, S.x,
                       h->opt.newton_rtol, h->ctl, h->dotbuf, h->counter, L);
   } else if (h->kind == SDP_A_SPARSE_COO) {
-    CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, ws, L, nullptr, GEMM_LOWER));
-    sparse_apply(st, h->sp, n, m, r, S.Z, nullptr, nullptr, S.partA, nullptr, L);   // A(E C~ E)
+    CU(sparse_pos_dots_col(st, h->sp, n, S.E, S.F, S.zpos, nullptr, L));  // E C~ E at the positions
+    sparse_apply_pos(st, h->sp, n, m, r, S.zpos, nullptr, nullptr, S.partA, nullptr, L);   // A(E C~ E)
     launch_rhs_finish(st, m, d, n, r, S.partA, 1, nullptr, nullptr, bt, Ct, S.H, S.Dv, h->g, S.x,
                       h->opt.newton_rtol, h->ctl, h->dotbuf, h->counter, L);
   } else {
@@ -982,12 +983,23 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   // ---- a8: recovery ----
   const double* u = S.x;
   const double* v = S.x + m;
-  if (h->kind == SDP_A_DENSE_SVEC) adjoint_dense(h, S, u, S.Y, nullptr);
-  else if (h->kind == SDP_A_SPARSE_COO) sparse_adjoint(st, h->sp, n, u, 1.0, S.Y, nullptr, L);
-  else launch_diag_matrix(st, n, u, S.Y, L);
-  launch_recover_pre(st, n, m, S.Y, Ct, u, h->Cw, dy, dS, h->ctl, L);
-  // dX = E Cw E + sym(Up Q^T) with Up = Vs unpack(v): lower triangles by products, then a mirror
-  CU(gemm_f64(st, false, false, n, n, n, 1.0, S.E, n, h->Cw, n, 0.0, S.F, n, S.ws, ws, L));
+  // dX = E Cw E + sym(Up Q^T) with Cw = A^T(u) - tau^2 C~ and Up = Vs unpack(v): E Cw from
+  // F = E C~ of the right side where A^T(u) is sparse or diagonal (one product instead of two)
+  if (h->kind == SDP_A_DENSE_SVEC) {
+    adjoint_dense(h, S, u, S.Y, nullptr);
+    launch_recover_pre(st, n, m, S.Y, Ct, u, h->Cw, dy, dS, h->ctl, L);
+    CU(gemm_f64(st, false, false, n, n, n, 1.0, S.E, n, h->Cw, n, 0.0, S.F, n, S.ws, ws, L));
+  } else if (h->kind == SDP_A_SPARSE_COO) {
+    sparse_adjoint(st, h->sp, n, u, 1.0, S.Y, nullptr, L);
+    launch_recover_pre(st, n, m, S.Y, Ct, u, nullptr, dy, dS, h->ctl, L);
+    sparse_posval(st, h->sp, u, S.ypos, nullptr, L);
+    sparse_EY(st, h->sp, n, S.ypos, S.E, S.Z, nullptr, L);
+    launch_recover_F(st, n, S.Z, S.E, nullptr, S.F, h->ctl, L);
+  } else {
+    launch_diag_matrix(st, n, u, S.Y, L);
+    launch_recover_pre(st, n, m, S.Y, Ct, u, nullptr, dy, dS, h->ctl, L);
+    launch_recover_F(st, n, nullptr, S.E, u, S.F, h->ctl, L);
+  }
   CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, dX, n, S.ws, ws, L, nullptr, GEMM_LOWER));
   h_unpack<double>(st, n, r, v, S.Hp, nullptr, L);
   CU(gemm_f64(st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, ws, L));

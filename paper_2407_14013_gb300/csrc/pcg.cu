@@ -395,10 +395,22 @@ __global__ void recover_pre_kernel(int n, int m, const double* __restrict__ Yu, 
   int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q < (int64_t)n * n) {
     double y = Yu[q], c = Ct[q];
-    Cw[q] = y - t2 * c;
+    if (Cw) Cw[q] = y - t2 * c;
     dS[q] = c - y / t2;
   }
   if (q < m) dy[q] = u[q] / t2;
+}
+
+// E Cw with Cw = A^T(u) - tau^2 C~, from F = E C~ of the right side (overwritten):
+// F = E A^T(u) - tau^2 F, with E A^T(u) given (EYu) or, for the DIAG kind, E diag(u)
+__global__ void recover_F_kernel(int n, const double* __restrict__ EYu, const double* __restrict__ E,
+                                 const double* __restrict__ u, double* __restrict__ F,
+                                 const PcgCtl* __restrict__ ctl) {
+  const double t2 = ctl->tau * ctl->tau;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)n * n) return;
+  const double ey = EYu ? EYu[q] : E[q] * u[q / n];
+  F[q] = ey - t2 * F[q];
 }
 
 // C += diag(Dv) * c_d + c_i * I  on an n x n matrix
@@ -635,6 +647,12 @@ void launch_recover_pre(cudaStream_t st, int n, int m, const double* Yu, const d
                         double* Cw, double* dy, double* dS, const PcgCtl* ctl, int64_t* launches) {
   int64_t tot = (int64_t)n * n > m ? (int64_t)n * n : m;
   recover_pre_kernel<<<nblk(tot, VT), VT, 0, st>>>(n, m, Yu, Ct, u, Cw, dy, dS, ctl);
+  ++*launches;
+}
+
+void launch_recover_F(cudaStream_t st, int n, const double* EYu, const double* E, const double* u, double* F,
+                      const PcgCtl* ctl, int64_t* launches) {
+  recover_F_kernel<<<nblk((int64_t)n * n, VT), VT, 0, st>>>(n, EYu, E, u, F, ctl);
   ++*launches;
 }
 

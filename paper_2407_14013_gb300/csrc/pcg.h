@@ -51,6 +51,9 @@ void launch_diag_matrix(cudaStream_t st, int n, const double* u, double* Y, int6
 void launch_hadamard_sq(cudaStream_t st, int64_t nn, const double* E, double* EE, int64_t* launches);
 void launch_recover_pre(cudaStream_t st, int n, int m, const double* Yu, const double* Ct, const double* u,
                         double* Cw, double* dy, double* dS, const PcgCtl* ctl, int64_t* launches);
+// F = E A^T(u) - tau^2 F (EYu = E A^T(u), or NULL for the DIAG kind: E diag(u))
+void launch_recover_F(cudaStream_t st, int n, const double* EYu, const double* E, const double* u, double* F,
+                      const PcgCtl* ctl, int64_t* launches);
 void launch_add_diag(cudaStream_t st, int n, double* C, const double* Dv, double c_i, int64_t* launches);
 void launch_scale_B(cudaStream_t st, int m, int d, const double* B, const double* Dv, double* Bs, int64_t* launches);
 void launch_correction_rhs(cudaStream_t st, int m, int d, const double* rho, double* out, int64_t* launches);
