@@ -197,7 +197,69 @@ def other_configs(dev, reps: int = 2, only=None):
         out["completion2000_r5"] = {"workload": "matrix completion n=1000+1000, m=50000 (5%), rank 5, SPARSE_COO, "
                                                 "r=5, synthetic scaling point mu=1e-4",
                                     "newton": newton_rows(prob, sp, Ct, bt, 5, ["fp64"])}
+    # 256 independent SDPs of uneven size solved by sdp_solve_batch (minutes: only on request)
+    if only == "batch256":
+        out["batch256"] = _batch256(dev)
     return out
+
+
+def _batch256(dev, precs=("mixed_fp32", "fp64")):
+    """The batched workload (workloads.batch_specs): 128 MaxCut (n in 32..512) and 128 sensing
+    (n in 32..256, m = 10 n, drawn on the GPU) SDPs, each on its own handle and stream, solved
+    to a 1e-8 gap by sdp_solve_batch with 16 host workers; wall time of the whole batch."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2407_14013_gb300 import NewtonSolver, solve_sdp_batch
+    t0 = time.perf_counter()
+    specs = W.batch_specs()
+    probs = []
+    for fam, n, seed in specs:
+        if fam == "maxcut":
+            probs.append(W.maxcut(n, 0.05, seed))
+        else:
+            probs.append(W.sensing_device(n, 10 * n, 2, seed, dev))
+    torch.cuda.synchronize(dev)
+    gen_s = time.perf_counter() - t0
+    td = lambda a: a if isinstance(a, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    bs = [td(p.b) for p in probs]
+    Cs = [td(p.C) for p in probs]
+    # rank bound: r_hat = 10, raised for MaxCut to ceil(sqrt(2 m)), the bound on the rank of an
+    # extreme optimal solution (the split needs r >= rank(X*))
+    rh = [max(10, math.ceil(math.sqrt(2 * p.m))) if p.kind == "diag" else 10 for p in probs]
+    res = {"workload": "128 MaxCut (n ~ U{32..512}, G(n,0.05), unit weights, r_hat = max(10, ceil(sqrt(2n)))) + "
+                       "128 matrix sensing (n ~ U{32..256}, m = 10 n, rank 2, r_hat = 10), gap 1e-8, one handle "
+                       "and stream per instance, 16 host workers",
+           "generation_s": gen_s}
+    for prec in precs:
+        solvers = [NewtonSolver(p, r_hat=r_, device=str(dev), stream=torch.cuda.Stream(dev), precision=prec)
+                   for p, r_ in zip(probs, rh)]
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        out = solve_sdp_batch(solvers, bs, Cs, gap_tol=1e-8, max_iter=100, workers=16)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t1
+        infos = [o[3] for o in out]
+        ok = sum(1 for i in infos if i["status"] == 0 and i["rel_gap"] <= 1e-8)
+        res[prec] = {"seconds_whole_batch": wall, "sdps_per_s": len(probs) / wall, "converged": ok,
+                     "instances": len(probs), "outer_iters_total": sum(i["iters"] for i in infos),
+                     "pcg_iters_total": sum(i["pcg_iters"] for i in infos),
+                     "max_rel_gap": max(i["rel_gap"] for i in infos),
+                     "max_pinf": max(i["pinf"] for i in infos), "max_dinf": max(i["dinf"] for i in infos),
+                     "sum_instance_s": sum(i["total_ms"] for i in infos) / 1e3,
+                     "sum_newton_s": sum(i["newton_ms"] for i in infos) / 1e3,
+                     "eig_sweeps_total": sum(i["eig_sweeps"] for i in infos),
+                     "not_converged": [{"family": specs[k][0], "n": specs[k][1], "status": infos[k]["status"],
+                                        "iters": infos[k]["iters"], "rel_gap": infos[k]["rel_gap"],
+                                        "pinf": infos[k]["pinf"], "dinf": infos[k]["dinf"]}
+                                       for k in range(len(infos))
+                                       if not (infos[k]["status"] == 0 and infos[k]["rel_gap"] <= 1e-8)],
+                     "workspace_GB": sum(s_.workspace_bytes() for s_ in solvers) / 1e9}
+        for s_ in solvers:
+            s_.close()
+        del solvers
+        torch.cuda.empty_cache()
+    return res
 
 
 def _maxcut64(dev, t, newton_rows):
@@ -486,7 +548,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
     ap.add_argument("--no-ttg", action="store_true", help="skip the time-to-gap solves")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads (MaxCut 64 / 5000, completion)")
-    ap.add_argument("--only", choices=["maxcut64", "maxcut5000", "completion2000"],
+    ap.add_argument("--only", choices=["maxcut64", "maxcut5000", "completion2000", "batch256"],
                     help="measure only this other workload (one JSON object; no headline line)")
     ap.add_argument("--reps", type=int, default=2, help="timed Newton solves per row of the other workloads")
     args = ap.parse_args()

@@ -204,6 +204,24 @@ sdp_status ipm_step(sdp_handle* h, const double* b, const double* C, double* X, 
 sdp_status sdp_solve(sdp_handle* h, const double* b, const double* C, double* X, double* y, double* S,
                      double gap_tol, int32_t max_iter, sdp_ipm_info* info);
 
+/* Many independent solves at once (batched SDPs of uneven size): sdp_solve of instance i on
+ * hs[i] with (b[i], C[i]) into (X[i], y[i], S[i]), for i < count.  `workers` host threads
+ * (<= 0: min(count, 16)) take the instances largest first; each solve runs on its own
+ * handle's stream, so give every handle its own (non-blocking) stream for the solves to
+ * overlap on the GPU: the small instances of a batch do not fill the GPU one at a time.
+ * While batched, the eigensolver and the smallest-eigenvalue search take their
+ * non-cooperative paths (no grid-wide barrier waits on blocks that share the GPU with other
+ * solves); results agree with single solves to the solve tolerance, not bitwise.
+ * Each workspace of the interior-point loop is allocated before the workers start.
+ *   hs       count distinct handles (a handle must not appear twice: its workspace is shared)
+ *   b, C, X, y, S   count device pointers each, as for sdp_solve
+ *   infos    count host structs (may be NULL);  statuses  count host status codes (required)
+ * Returns SDP_OK when every instance returned SDP_OK, else the status of the first failing
+ * instance (by index); SDP_EINVAL for bad arguments (nothing is solved). */
+sdp_status sdp_solve_batch(int32_t count, sdp_handle* const* hs, const double* const* b, const double* const* C,
+                           double* const* X, double* const* y, double* const* S, double gap_tol, int32_t max_iter,
+                           int32_t workers, sdp_ipm_info* infos, int32_t* statuses);
+
 /* Fill *opt with the defaults: r_fixed 0, r_hat 10, FP64, auto space,
  * max_pcg 2000, check_every 8, beta_rule 0, use_graph 1, newton_rtol 1e-12, max_refine 10,
  * max_inner 500, inner_rtol 1e-6, pcg_start 0. */

@@ -15,7 +15,7 @@ from . import _native as native
 from ._native import (SDP_A_DENSE_SVEC, SDP_A_DIAG, SDP_A_SPARSE_COO, SDP_ENOTCONV, SDP_FP64, SDP_MIXED_FP32,
                       SDP_OK, SdpError, sdp_default_options)
 
-__all__ = ["NewtonSolver", "SdpError", "native", "sdp_optimum", "eigh", "SDP_A_DIAG", "SDP_A_SPARSE_COO",
+__all__ = ["NewtonSolver", "SdpError", "native", "sdp_optimum", "eigh", "solve_sdp_batch", "SDP_A_DIAG", "SDP_A_SPARSE_COO",
            "SDP_A_DENSE_SVEC"]
 
 KINDS = {"diag": SDP_A_DIAG, "sparse": SDP_A_SPARSE_COO, "dense": SDP_A_DENSE_SVEC}
@@ -243,6 +243,36 @@ class NewtonSolver:
             self.close()
         except Exception:
             pass
+
+
+def solve_sdp_batch(solvers, bs, Cs, gap_tol: float = 1e-8, max_iter: int = 100, workers: int = 0):
+    """Whole interior-point solves of many independent problems at once (sdp_solve_batch):
+    instance i on solvers[i] with data (bs[i], Cs[i]).  Give each solver its own stream
+    (``NewtonSolver(..., stream=torch.cuda.Stream())``) for the solves to overlap on the GPU.
+    Returns a list of (X, y, S, info) with info["status"] the instance's status code."""
+    import torch
+    f64 = torch.float64
+    outs, keep = [], []
+    for s_, b_, C_ in zip(solvers, bs, Cs):
+        b_ = b_.to(device=s_.device, dtype=f64).contiguous()
+        C_ = C_.to(device=s_.device, dtype=f64).contiguous()
+        X = torch.empty((s_.n, s_.n), dtype=f64, device=s_.device)
+        S = torch.empty((s_.n, s_.n), dtype=f64, device=s_.device)
+        y = torch.empty(s_.m, dtype=f64, device=s_.device)
+        keep.append((b_, C_))
+        outs.append((X, y, S))
+    for s_ in solvers:
+        torch.cuda.synchronize(s_.device)
+    statuses, infos = native.sdp_solve_batch([s_.handle for s_ in solvers], [_ptr(k[0]) for k in keep],
+                                             [_ptr(k[1]) for k in keep], [_ptr(o[0]) for o in outs],
+                                             [_ptr(o[1]) for o in outs], [_ptr(o[2]) for o in outs],
+                                             gap_tol, max_iter, workers)
+    res = []
+    for (X, y, S), st, ci in zip(outs, statuses, infos):
+        info = ci.as_dict()
+        info["status"] = st
+        res.append((X, y, S, info))
+    return res
 
 
 def sdp_optimum(C, b, X, y, V, lam, solver: NewtonSolver):

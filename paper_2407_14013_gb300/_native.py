@@ -69,6 +69,7 @@ EXPORTS = {
                            POINTER(c_int32)]),
     "ipm_step": (c_int32, [c_void_p] + [c_void_p] * 5 + [POINTER(sdp_ipm_info)]),
     "sdp_solve": (c_int32, [c_void_p] + [c_void_p] * 5 + [c_double, c_int32, POINTER(sdp_ipm_info)]),
+    "sdp_solve_batch": (c_int32, [c_int32] + [c_void_p] * 6 + [c_double, c_int32, c_int32, c_void_p, c_void_p]),
     "sdp_debug_copy": (c_int32, [c_void_p, c_int32, c_void_p, c_int64]),
     "sdp_set_profiling": (c_int32, [c_void_p, c_int32]),
     "sdp_adjoint_dense_noalloc": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
@@ -179,6 +180,20 @@ def sdp_solve(h: int, b: int, C: int, X: int, y: int, S: int, gap_tol: float, ma
     if st != SDP_OK and not (allow_notconv and st == SDP_ENOTCONV):
         raise SdpError(st, lib.sdp_last_error(c_void_p(h)).decode())
     return st
+
+
+def sdp_solve_batch(handles, b, C, X, y, S, gap_tol: float, max_iter: int, workers: int = 0):
+    """sdp_solve_batch over lists of handles and device pointers; returns (statuses, infos)."""
+    lib = load()
+    k = len(handles)
+    arr = lambda xs: (c_void_p * max(k, 1))(*[c_void_p(v) for v in xs])
+    infos = (sdp_ipm_info * max(k, 1))()
+    statuses = (c_int32 * max(k, 1))()
+    st = lib.sdp_solve_batch(k, arr(handles), arr(b), arr(C), arr(X), arr(y), arr(S), gap_tol, max_iter, workers,
+                             ctypes.cast(infos, c_void_p), ctypes.cast(statuses, c_void_p))
+    if st == SDP_EINVAL and (k == 0 or all(v == SDP_EINVAL for v in statuses[:k])):
+        raise SdpError(st, lib.sdp_last_error(None).decode())
+    return [int(v) for v in statuses[:k]], [infos[i] for i in range(k)]
 
 
 def sdp_debug_copy(h: int, which: int, dst: int, count: int) -> None:

@@ -356,11 +356,11 @@ void eigh_graph_release(EighGraph* g) {
 
 cudaError_t eigh_jacobi(cudaStream_t st, int n, double* A, double* V, double* lam, double tol, int max_sweeps,
                         double* work, size_t work_elems, int* sweeps_out, double* off_out, int64_t* launches,
-                        EighGraph* graph) {
+                        EighGraph* graph, bool allow_coop) {
   if (n < 1 || work_elems < eigh_work_elems(n)) return cudaErrorInvalidValue;
   const int npad = n + (n & 1);
   const int np = npad / 2;
-  {
+  if (allow_coop) {
     // cooperative path: one launch for the whole iteration
     double* A1 = work + ((size_t)np * 3 + 2 * kNormBlocks + 2 + 2 + 16 + 7) / 8 * 8;
     double* red = A1 + (size_t)n * n;

@@ -83,6 +83,8 @@ struct sdp_handle {
   size_t gj_work_elems = 0;
   double *ubatch = nullptr, *Gb = nullptr, *Hb = nullptr;
   int pinv_dim = 0;                 // order of the largest preconditioner core the options allow
+  int dev = 0;                      // device of the handle (current at setup)
+  bool no_coop = false;             // batched solves: no cooperative (grid-barrier) launches
   int64_t b_elems = 0;              // capacity of the explicit B = A Q (m x d)
   int64_t bt_elems = 0;             // capacity of B^T (d x m)
   int64_t bs_elems = 0;             // capacity of D^{-1/2} B^T (m-space core by a product)

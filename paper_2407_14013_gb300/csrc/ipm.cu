@@ -20,7 +20,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <exception>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -249,7 +252,7 @@ sdp_status lam_min_jacobi(Ctx& c, const double* M, double* out, int* sweeps) {
   CUI(cudaMemcpyAsync(w->Eg, M, nn * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
   int sw = 0;
   double off = 0.0;
-  CUI(eigh_jacobi(c.st, c.n, w->Eg, w->EV, w->elam, 1e-12, 40, w->eigw, w->eigw_elems, &sw, &off, c.L, &w->eg[1]));
+  CUI(eigh_jacobi(c.st, c.n, w->Eg, w->EV, w->elam, 1e-12, 40, w->eigw, w->eigw_elems, &sw, &off, c.L, &w->eg[1], !h->no_coop));
   *sweeps += sw;
   std::vector<double> lh(c.n);
   CUI(cudaMemcpyAsync(lh.data(), w->elam, c.n * sizeof(double), cudaMemcpyDeviceToHost, c.st));
@@ -263,6 +266,7 @@ sdp_status lam_min(Ctx& c, const double* M, double* out, int* sweeps) {
   sdp_handle* h = c.h;
   IpmWork* w = c.w;
   int it = 0;
+  if (h->no_coop) return lam_min_jacobi(c, M, out, sweeps);
   cudaError_t e = lanczos_min(c.st, c.n, M, w->lzw, w->lzw_elems, out, &it, c.L);
   if (e == cudaErrorNotSupported) {
     cudaGetLastError();
@@ -451,7 +455,7 @@ sdp_status step(Ctx& c, double* X, double* y, double* S, const Measures& Mz, sdp
   CUI(gemm(c, false, false, S, w->L, w->M1));
   CUI(gemm(c, true, false, w->L, w->M1, w->T));
   int sw = 0;
-  CUI(eigh_jacobi(c.st, n, w->T, w->U, w->gam, 1e-14, 40, w->eigw, w->eigw_elems, &sw, &off, c.L, &w->eg[0]));
+  CUI(eigh_jacobi(c.st, n, w->T, w->U, w->gam, 1e-14, 40, w->eigw, w->eigw_elems, &sw, &off, c.L, &w->eg[0], !h->no_coop));
   sweeps += sw;
   gamma_kernel<<<nb(n), IT, 0, c.st>>>(n, w->gam, w->g, w->q, w->qi, w->status);
   ++*c.L;
@@ -469,7 +473,7 @@ sdp_status step(Ctx& c, double* X, double* y, double* S, const Measures& Mz, sdp
   } else {
     CUI(cudaMemcpyAsync(w->Eg, w->Wm, bytes, cudaMemcpyDeviceToDevice, c.st));
   }
-  CUI(eigh_jacobi(c.st, n, w->Eg, w->EV, w->lam, 1e-14, 40, w->eigw, w->eigw_elems, &sw, &off, c.L, &w->eg[1]));
+  CUI(eigh_jacobi(c.st, n, w->Eg, w->EV, w->lam, 1e-14, 40, w->eigw, w->eigw_elems, &sw, &off, c.L, &w->eg[1], !h->no_coop));
   sweeps += sw;
   if (w->have_prev) CUI(gemm(c, false, false, w->Vprev, w->EV, w->V));
   else CUI(cudaMemcpyAsync(w->V, w->EV, bytes, cudaMemcpyDeviceToDevice, c.st));
@@ -655,4 +659,73 @@ extern "C" sdp_status sdp_solve(sdp_handle* h, const double* b, const double* C,
   loc.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = loc;
   return loc.converged ? SDP_OK : SDP_ENOTCONV;
+}
+
+extern "C" sdp_status sdp_solve_batch(int32_t count, sdp_handle* const* hs, const double* const* b,
+                                      const double* const* C, double* const* X, double* const* y, double* const* S,
+                                      double gap_tol, int32_t max_iter, int32_t workers, sdp_ipm_info* infos,
+                                      int32_t* statuses) {
+  using namespace wc;
+  if (count < 0) return wc_fail(nullptr, SDP_EINVAL, "count < 0");
+  if (count == 0) return SDP_OK;
+  if (!hs || !b || !C || !X || !y || !S || !statuses) return wc_fail(nullptr, SDP_EINVAL, "NULL array argument");
+  for (int32_t i = 0; i < count; ++i) statuses[i] = SDP_EINVAL;   // until instance i is solved
+  if (!(gap_tol > 0.0) || max_iter < 0) return wc_fail(nullptr, SDP_EINVAL, "bad gap_tol or max_iter");
+  std::vector<sdp_handle*> seen(hs, hs + count);
+  for (auto* h : seen)
+    if (!h) return wc_fail(nullptr, SDP_EINVAL, "NULL handle");
+  std::sort(seen.begin(), seen.end());
+  if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+    return wc_fail(nullptr, SDP_EINVAL, "a handle appears twice in the batch");
+  // the interior-point workspaces first (allocation is not left to the concurrent solves)
+  for (int32_t i = 0; i < count; ++i) {
+    sdp_handle* h = hs[i];
+    if (cudaSetDevice(h->dev) != cudaSuccess) return wc_fail(nullptr, SDP_ECUDA, "cudaSetDevice failed");
+    sdp_status s = ensure_workspace(h);
+    if (s != SDP_OK) {
+      statuses[i] = s;
+      return s;
+    }
+  }
+  // largest first: about n^3 per outer iteration (eigensolver, dense products) plus m N for
+  // the dense passes over A
+  std::vector<int32_t> order(count);
+  std::vector<double> cost(count);
+  for (int32_t i = 0; i < count; ++i) {
+    const sdp_handle* h = hs[i];
+    order[i] = i;
+    cost[i] = (double)h->n * h->n * h->n + (h->kind == SDP_A_DENSE_SVEC ? 64.0 * h->m * (double)h->N : 0.0);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) { return cost[a] > cost[c]; });
+  for (int32_t i = 0; i < count; ++i) hs[i]->no_coop = true;
+  std::atomic<int32_t> next{0};
+  auto work = [&]() {
+    for (;;) {
+      const int32_t k = next.fetch_add(1);
+      if (k >= count) return;
+      const int32_t i = order[k];
+      sdp_handle* h = hs[i];
+      if (cudaSetDevice(h->dev) != cudaSuccess) {
+        statuses[i] = SDP_ECUDA;
+        continue;
+      }
+      statuses[i] = sdp_solve(h, b[i], C[i], X[i], y[i], S[i], gap_tol, max_iter, infos ? &infos[i] : nullptr);
+    }
+  };
+  int32_t nw = workers > 0 ? workers : std::min<int32_t>(count, 16);
+  nw = std::max<int32_t>(1, std::min<int32_t>({nw, count, 64}));
+  std::vector<std::thread> pool;
+  for (int32_t t = 1; t < nw; ++t) {
+    try {
+      pool.emplace_back(work);
+    } catch (const std::exception&) {
+      break;   // fewer threads: the remaining instances go to the ones that started
+    }
+  }
+  work();
+  for (auto& t : pool) t.join();
+  for (int32_t i = 0; i < count; ++i) hs[i]->no_coop = false;
+  for (int32_t i = 0; i < count; ++i)
+    if (statuses[i] != SDP_OK) return (sdp_status)statuses[i];
+  return SDP_OK;
 }

@@ -192,6 +192,6 @@ cudaError_t lanczos_min(cudaStream_t st, int n, const double* M, double* work, s
 size_t eigh_work_elems(int n);
 cudaError_t eigh_jacobi(cudaStream_t st, int n, double* A, double* V, double* lam, double tol, int max_sweeps,
                         double* work, size_t work_elems, int* sweeps_out, double* off_out, int64_t* launches,
-                        EighGraph* graph = nullptr);
+                        EighGraph* graph = nullptr, bool allow_coop = true);
 
 }  // namespace wc

@@ -355,6 +355,7 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   }
   int dev = 0;
   cudaGetDevice(&dev);
+  h->dev = dev;
   cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (h->kind == SDP_A_DENSE_SVEC) {
     h->GY = rows_gemvT_groups(m, h->N, 8);

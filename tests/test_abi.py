@@ -130,3 +130,19 @@ def test_product_path_does_not_touch_the_oracle():
             _native.load(os.path.join(ROOT, "does_not_exist.so"))
     finally:
         _native._lib = saved
+
+
+def test_batch_argument_errors_without_gpu():
+    """sdp_solve_batch validates its arguments before any CUDA call: an empty batch is a no-op,
+    a NULL handle or a repeated handle is SDP_EINVAL with nothing solved."""
+    from paper_2407_14013_gb300 import _native
+    st, infos = _native.sdp_solve_batch([], [], [], [], [], [], 1e-8, 10)
+    assert st == [] and infos == []
+    with pytest.raises(_native.SdpError) as e:
+        _native.sdp_solve_batch([0, 0], [8, 8], [8, 8], [8, 8], [8, 8], [8, 8], 1e-8, 10)
+    assert e.value.status == _native.SDP_EINVAL and "NULL handle" in str(e.value)
+    with pytest.raises(_native.SdpError) as e:
+        _native.sdp_solve_batch([16, 16], [8, 8], [8, 8], [8, 8], [8, 8], [8, 8], 1e-8, 10)   # never dereferenced
+    assert e.value.status == _native.SDP_EINVAL and "twice" in str(e.value)
+    with pytest.raises(_native.SdpError):
+        _native.sdp_solve_batch([16], [8], [8], [8], [8], [8], -1.0, 10)

@@ -217,6 +217,48 @@ def newton_rhs(n: int, m: int, seed: int, scale: float = 1.0):
 # ---------------------------------------------------------------------------
 # Named workloads (shapes and distributions of the five benchmark families)
 
+def batch_specs(count: int = 256, seed: int = 5) -> list:
+    """The batched workload: ``count`` independent SDPs, the first half MaxCut (n ~ U{32..512},
+    G(n, 0.05), unit weights, diag constraints), the second half matrix sensing (n ~ U{32..256},
+    m = 10 n dense constraints, planted rank 2, C = I).  Returns (family, n, instance seed)."""
+    g = rng(1000 * seed)
+    half = count // 2
+    specs = [("maxcut", int(g.integers(32, 513)), 1000 * seed + 1 + i) for i in range(half)]
+    specs += [("sensing", int(g.integers(32, 257)), 1000 * seed + 1 + half + i) for i in range(count - half)]
+    return specs
+
+
+def batch_problem(spec) -> Problem:
+    """One instance of ``batch_specs`` on the host (numpy)."""
+    fam, n, seed = spec
+    if fam == "maxcut":
+        return maxcut(n, 0.05, seed)
+    return sensing(n, 10 * n, 2, seed)
+
+
+def sensing_device(n: int, m: int, rank: int, seed: int, device):
+    """Matrix sensing drawn on the GPU (torch generator seeded with ``seed``) for the large
+    batched workload: svec(A_i) for A_i = (G_i + G_i^T)/2, G_i iid N(0, 1/n) has iid N(0, 1/n)
+    coordinates (diagonal: N(0, 1/n); off-diagonal: sqrt2 N(0, 1/(2n))), so the svec rows are
+    drawn directly; b = A(U U^T).  Same distribution as ``sensing``, a different stream of
+    numbers.  Returns a Problem whose arrays are torch tensors on ``device``."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    N = svec_len(n)
+    a = torch.randn((m, N), generator=gen, device=device, dtype=torch.float64) / math.sqrt(n)
+    U = torch.randn((n, rank), generator=gen, device=device, dtype=torch.float64)
+    il = np.tril_indices(n)
+    order = np.lexsort((il[0], il[1]))
+    rows = torch.from_numpy(il[0][order]).to(device)
+    cols = torch.from_numpy(il[1][order]).to(device)
+    Xs = U @ U.T
+    sv = Xs[rows, cols] * torch.where(rows == cols, 1.0, SQRT2).to(torch.float64)
+    b = a @ sv
+    C = torch.eye(n, dtype=torch.float64, device=device)
+    return Problem(kind="dense", n=n, m=m, b=b, C=C, a_dense=a, meta={"family": "sensing", "U": U})
+
+
 def workload(name: str, instance: int = 0) -> Problem:
     if name == "maxcut64":
         return maxcut(64, 0.1, seed=1000 * 1 + instance)
