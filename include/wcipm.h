@@ -79,7 +79,10 @@ typedef enum {
                             from delta0 = P^{-1}[0; rho_v], x += delta, until the FP64 residual
                             passes the stop test.  M~ forms the block A E A^T from an FP32 copy
                             of A (DENSE) or of E o E (DIAG) with FP32 products; its rows with
-                            B = A Q, the vectors, scalars and the preconditioner stay FP64     */
+                            B = A Q, the vectors, scalars and the preconditioner stay FP64.
+                            If a correction solve breaks down, or max_refine corrections do not
+                            reach the stop test, the FP64 PCG continues from the refined iterate
+                            (its iterations count in pcg_iters).                              */
 } sdp_precision;
 
 typedef struct {

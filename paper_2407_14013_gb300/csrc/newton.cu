@@ -950,6 +950,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     // that x0 = [0; -Sigma^{-1} Q^T c] leaves (it sets the floor of the true residual).
     Space& Si = h->sin;
     CU(cudaMemsetAsync(S.x, 0, nt * sizeof(double), st));
+    bool fallback = false;
     for (;;) {
       // rho = g - M x in FP64, and the stop test on ||rho|| (the true residual)
       if (h->refine_steps == 0) {
@@ -961,7 +962,11 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
       launch_norm_check<double>(st, nt, S.rv, 0.0, h->ctl, h->dotbuf, h->counter, L);
       CU(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
       CU(cudaStreamSynchronize(st));
-      if (h->ctl_host->done || h->refine_steps >= h->opt.max_refine) break;
+      if (h->ctl_host->done) break;
+      if (h->refine_steps >= h->opt.max_refine) {
+        fallback = true;
+        break;
+      }
       // M~ delta = rho by PCG from delta0 = P^{-1}[0; rho_v], to inner_rtol relative reduction
       launch_ctl_reset(st, h->ctl_in, h->ctl, h->opt.max_inner, L);
       launch_correction_rhs(st, m, d, S.rv, Si.z, L);
@@ -972,9 +977,21 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
       s = pcg_loop(h, Si, true);
       if (s != SDP_OK) return s;
       h->inner_iters += h->ctl_host->iters;
-      if (h->ctl_host->status == 5) return fail(h, SDP_ENUMERIC, "breakdown in the inner solve of the mixed form");
+      if (h->ctl_host->status == 5) {   // breakdown of the correction solve: its correction is dropped
+        fallback = true;
+        break;
+      }
       launch_add_correction(st, nt, Si.x, S.x, L);
       h->refine_steps += 1;
+    }
+    if (fallback) {
+      // a correction solve broke down, or max_refine corrections did not reach the stop test:
+      // the FP64 PCG continues from the refined iterate
+      sdp_status s = pcg_start(h, S, false, h->g, 0.0);
+      if (s != SDP_OK) return s;
+      s = pcg_loop(h, S, false);
+      if (s != SDP_OK) return s;
+      h->inner_iters += h->ctl_host->iters;
     }
   }
 

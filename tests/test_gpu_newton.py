@@ -279,3 +279,18 @@ def test_resolve_reuses_setup():
     for a, b in ((dX, fX), (dy, fy), (dS, fS)):
         assert rel(a.cpu().numpy(), b.cpu().numpy()) < 1e-10
     s.close()
+
+
+def test_mixed_continues_in_fp64_after_the_refinement_limit():
+    """With max_refine = 1 one FP32 correction cannot reach the 1e-12 stop test; the FP64 PCG
+    continues from the refined iterate and the direction equals the FP64 form's."""
+    prob = W.sensing(37, 150, 3, 102)
+    sp = W.scaling_point(prob.n, 3, 1e-4, 1237)
+    Ct, bt = W.newton_rhs(prob.n, prob.m, 1238)
+    s64, (X64, y64, S64, i64) = gpu_solve(prob, sp, Ct, bt, r_hat=5)
+    s32, (X32, y32, S32, i32) = gpu_solve(prob, sp, Ct, bt, r_hat=5, precision="mixed_fp32", max_refine=1)
+    assert i32.converged and i32.refine_steps == 1
+    assert i32.res_norm <= 1e-12 * i32.rhs_norm
+    assert rel(X32, X64) < TOL and rel(y32, y64) < TOL and rel(S32, S64) < TOL
+    s64.close()
+    s32.close()
