@@ -123,6 +123,11 @@ typedef struct {
                             1 = x0 = [0; -Sigma^{-1} Q^T c] as printed in Cor. pcg, whose first
                             block of r_0 grows like 1/mu^2 and sets a floor for the attainable
                             residual near the end of the interior-point path                     */
+  int32_t tc_products;   /* 1 (default): the large dense FP64 products of a Newton solve (n >= 512:
+                            E = Vs diag(e) Vs^T, E C~, the recovery, the complements B^T B and
+                            B D^{-1} B^T) run on the BF16 tensor cores by exact slices (see
+                            sdp_gemm_f64_tc; FP64 accuracy); 0: every product on the FP64 MMA
+                            path.  The Cholesky and inverse of the complement stay FP64 MMA.     */
 } sdp_options;
 
 typedef struct {
@@ -227,7 +232,7 @@ sdp_status sdp_solve_batch(int32_t count, sdp_handle* const* hs, const double* c
 
 /* Fill *opt with the defaults: r_fixed 0, r_hat 10, FP64, auto space,
  * max_pcg 2000, check_every 8, beta_rule 0, use_graph 1, newton_rtol 1e-12, max_refine 10,
- * max_inner 500, inner_rtol 1e-6, pcg_start 0. */
+ * max_inner 500, inner_rtol 1e-6, pcg_start 0, tc_products 1. */
 void sdp_default_options(sdp_options* opt);
 
 /* Validate the problem, record its (device) pointers -- the caller keeps
@@ -312,6 +317,26 @@ sdp_status sdp_set_profiling(sdp_handle* h, int32_t on);
  * cudaStream_t; the call returns after its work on that stream has completed. */
 sdp_status sdp_adjoint_dense_noalloc(const double* a_dense, int32_t n, int32_t m, const double* y,
                                      double* Y, void* stream);
+
+/* Double-precision matrix product on the BF16 tensor cores (tcgen05 with TMEM accumulators,
+ * TMA-fed), C = alpha op(A) op(B) + beta C, column-major like BLAS dgemm (op = transpose when
+ * tA / tB is nonzero; op(A) M x K, op(B) K x N).  The paper has no counterpart: its dense
+ * products are FP64 (the n^3 products of Section 3 and the Schur complements of Section 6), and
+ * the GPU's tensor cores have no FP64 kind.  The operands are split into eight exact BF16
+ * integer slices per row of op(A) and column of op(B) (scaled by a power of two), the 36 slice
+ * products that matter are accumulated exactly in FP32 over K-chunks of 4096 and summed in FP64:
+ * the error is about K 2^-55 max_k|op(A)[i,k]| max_k|op(B)[k,j]| per entry, the FP64 bound when
+ * rows and columns carry no large internal dynamic range.
+ *   work   device scratch of sdp_gemm_f64_tc_work_bytes(M, N, K) bytes, 256-byte aligned
+ *          (about 32 (M + N) K bytes: the slices)
+ * All matrices are device pointers; `stream` is a cudaStream_t; the call returns after its work
+ * on that stream has completed.  SDP_EINVAL for bad sizes, leading dimensions or work;
+ * SDP_EUNSUPPORTED on a device that is not a Blackwell (sm_10x) GPU; SDP_ETIMEOUT if a bounded
+ * wait inside the kernel gave up (about 2 s; the output is then not written). */
+size_t sdp_gemm_f64_tc_work_bytes(int32_t M, int32_t N, int32_t K);
+sdp_status sdp_gemm_f64_tc(void* stream, int32_t tA, int32_t tB, int32_t M, int32_t N, int32_t K, double alpha,
+                           const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                           int64_t ldc, void* work, size_t work_bytes);
 
 /* Bytes of device workspace owned by the handle. */
 size_t sdp_workspace_bytes(const sdp_handle* h);

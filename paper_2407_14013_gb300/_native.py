@@ -30,7 +30,7 @@ class sdp_options(Structure):
     _fields_ = [("r_fixed", c_int32), ("r_hat", c_int32), ("precision", c_int32), ("precond_space", c_int32),
                 ("max_pcg", c_int32), ("check_every", c_int32), ("beta_rule", c_int32), ("use_graph", c_int32),
                 ("newton_rtol", c_double), ("max_refine", c_int32), ("max_inner", c_int32),
-                ("inner_rtol", c_double), ("pcg_start", c_int32)]
+                ("inner_rtol", c_double), ("pcg_start", c_int32), ("tc_products", c_int32)]
 
 
 class sdp_newton_info(Structure):
@@ -70,6 +70,9 @@ EXPORTS = {
     "ipm_step": (c_int32, [c_void_p] + [c_void_p] * 5 + [POINTER(sdp_ipm_info)]),
     "sdp_solve": (c_int32, [c_void_p] + [c_void_p] * 5 + [c_double, c_int32, POINTER(sdp_ipm_info)]),
     "sdp_solve_batch": (c_int32, [c_int32] + [c_void_p] * 6 + [c_double, c_int32, c_int32, c_void_p, c_void_p]),
+    "sdp_gemm_f64_tc_work_bytes": (c_size_t, [c_int32, c_int32, c_int32]),
+    "sdp_gemm_f64_tc": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_double, c_void_p, c_int64,
+                                  c_void_p, c_int64, c_double, c_void_p, c_int64, c_void_p, c_size_t]),
     "sdp_debug_copy": (c_int32, [c_void_p, c_int32, c_void_p, c_int64]),
     "sdp_set_profiling": (c_int32, [c_void_p, c_int32]),
     "sdp_adjoint_dense_noalloc": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
@@ -194,6 +197,15 @@ def sdp_solve_batch(handles, b, C, X, y, S, gap_tol: float, max_iter: int, worke
     if st == SDP_EINVAL and (k == 0 or all(v == SDP_EINVAL for v in statuses[:k])):
         raise SdpError(st, lib.sdp_last_error(None).decode())
     return [int(v) for v in statuses[:k]], [infos[i] for i in range(k)]
+
+
+def sdp_gemm_f64_tc(stream: int, tA: bool, tB: bool, M: int, N: int, K: int, alpha: float, A: int, lda: int, B: int,
+                    ldb: int, beta: float, C: int, ldc: int, work: int, work_bytes: int) -> None:
+    lib = load()
+    st = lib.sdp_gemm_f64_tc(c_void_p(stream), int(tA), int(tB), M, N, K, alpha, c_void_p(A), lda, c_void_p(B), ldb,
+                             beta, c_void_p(C), ldc, c_void_p(work), work_bytes)
+    if st != SDP_OK:
+        raise SdpError(st, lib.sdp_last_error(None).decode())
 
 
 def sdp_debug_copy(h: int, which: int, dst: int, count: int) -> None:

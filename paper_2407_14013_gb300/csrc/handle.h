@@ -84,6 +84,9 @@ struct sdp_handle {
   double *ubatch = nullptr, *Gb = nullptr, *Hb = nullptr;
   int pinv_dim = 0;                 // order of the largest preconditioner core the options allow
   int dev = 0;                      // device of the handle (current at setup)
+  char* tcw = nullptr;              // slices of the tensor-core FP64 products (NULL: not used)
+  size_t tcw_bytes = 0;
+  int* tc_err = nullptr;            // set by a tensor-core product whose bounded wait gave up
   bool no_coop = false;             // batched solves: no cooperative (grid-barrier) launches
   int64_t b_elems = 0;              // capacity of the explicit B = A Q (m x d)
   int64_t bt_elems = 0;             // capacity of B^T (d x m)

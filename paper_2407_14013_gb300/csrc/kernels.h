@@ -24,6 +24,15 @@ cudaError_t gemm_f64(cudaStream_t st, bool tA, bool tB, int M, int N, int K, dou
                      double* C, int64_t ldc, double* ws, size_t ws_elems, int64_t* launches,
                      const int32_t* done = nullptr, int flags = 0);
 
+// ---- tc_gemm.cu: FP64 products on the BF16 tensor cores (exact slices) -------------------------
+// Same convention as gemm_f64 (flags: GEMM_LOWER only).  work: tc_gemm_work_bytes(M, N, K)
+// bytes, 256-byte aligned (its first 256 bytes are not used by the product); err: a device
+// word set to 1 when a bounded wait gave up (the caller clears and reads it).
+size_t tc_gemm_work_bytes(int M, int N, int K);
+cudaError_t gemm_f64_tc(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
+                        int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* work,
+                        size_t work_bytes, int* err, int flags, int64_t* launches);
+
 // ---- rows.cu: products with row-major matrices streamed from memory ---------------------------
 // Partial sums of y_i = <row_i(A), x>: part[s * m + i] over column slabs s.  The slab count
 // depends on the shape and the element size (8: double, 4: float); a partial-sum buffer of

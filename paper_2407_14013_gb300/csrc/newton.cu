@@ -37,6 +37,9 @@ using namespace wc;
 
 static std::string g_setup_err;
 
+// products with both output dimensions at least this large go to the tensor cores
+constexpr int kTcMin = 512;
+
 static sdp_status fail(sdp_handle* h, sdp_status s, const std::string& msg) {
   if (h) h->err = msg; else g_setup_err = msg;
   return s;
@@ -67,6 +70,7 @@ extern "C" void sdp_default_options(sdp_options* o) {
   o->max_inner = 500;
   o->inner_rtol = 1e-6;
   o->pcg_start = 0;
+  o->tc_products = 1;
 }
 
 namespace {
@@ -204,6 +208,10 @@ size_t carve(sdp_handle* h, char* base) {
     h->sin.ctl = h->ctl_in;
     carve_mixed(h, c, h->m32);
   }
+  if (h->tcw_bytes) {
+    h->tc_err = c.take<int>(64);
+    h->tcw = c.take<char>(h->tcw_bytes);
+  }
   h->hV = c.take<double>(nn);
   h->hlam = c.take<double>(n);
   h->hCt = c.take<double>(nn);
@@ -245,6 +253,7 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   if (r_max < 1 || r_max >= n) return fail(nullptr, SDP_EINVAL, "rank parameter out of range [1, n)");
   if (opt.precond_space < 0 || opt.precond_space > 2) return fail(nullptr, SDP_EINVAL, "bad precond_space");
   if (opt.pcg_start < 0 || opt.pcg_start > 1) return fail(nullptr, SDP_EINVAL, "bad pcg_start");
+  if (opt.tc_products < 0 || opt.tc_products > 1) return fail(nullptr, SDP_EINVAL, "bad tc_products");
 
   // SPARSE_COO: validate the entries and build the index tables on the host (once per problem)
   std::vector<int32_t> sp_con_ptr, sp_pos_r, sp_pos_c, sp_pos_ptr, sp_perm, sp_epos, sp_yptr, sp_ycol, sp_ypidx,
@@ -368,6 +377,16 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
     // batch of constraints whose A_i Q factors are formed at once (at most ~32 MB per factor)
     h->mb2 = (int)std::max<int64_t>(h->mb, std::min<int64_t>(m, ((int64_t)32 << 20) / ((int64_t)n * r_max * 8)));
   }
+  // slices of the tensor-core products: the n^3 products, and the complement B^T B or
+  // B D^{-1} B^T (processed in K-chunks when the whole K does not fit in 4 GiB)
+  if (opt.tc_products && n >= kTcMin) {
+    size_t need = tc_gemm_work_bytes(n, n, n);
+    if (h->kind != SDP_A_DIAG) {
+      if (h->pinv_dim >= kTcMin && std::min(h->d_max, m) == h->pinv_dim)
+        need = std::max(need, tc_gemm_work_bytes(h->pinv_dim, h->pinv_dim, std::max(h->d_max, m)));
+    }
+    h->tcw_bytes = std::min(need, std::max(tc_gemm_work_bytes(n, n, n), (size_t)4 << 30));
+  }
   h->pool_bytes = carve(h, nullptr);
   cudaError_t e = cudaMalloc(&h->pool, h->pool_bytes);
   if (e != cudaSuccess) {
@@ -486,6 +505,17 @@ cudaStream_t fork(sdp_handle* h, int which, int ev) {
 void join(sdp_handle* h, int which, int ev) {
   cudaEventRecord(h->br_ev[ev], h->aux[which]);
   cudaStreamWaitEvent(h->st, h->br_ev[ev], 0);
+}
+
+// Dense FP64 product: on the tensor cores (exact slices) when the handle holds their workspace
+// and the product is large, else on the FP64 MMA path.
+cudaError_t gemm_big(sdp_handle* h, cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha,
+                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                     double* ws, size_t ws_elems, int64_t* L, int flags = 0) {
+  if (h->tcw && M >= kTcMin && N >= kTcMin && K >= 64 && !(flags & (GEMM_KSTART_ROW | GEMM_KSTART_COL)))
+    return gemm_f64_tc(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, h->tcw, h->tcw_bytes, h->tc_err,
+                       flags, L);
+  return gemm_f64(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, L, nullptr, flags);
 }
 
 // Y = A^T(u) as a full n x n matrix (DENSE kind).
@@ -840,7 +870,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   h->space = h->opt.precond_space == 0 ? (d <= m ? 1 : 2) : h->opt.precond_space;
   split_scale_cols(st, n, S.Vs, h->e, h->Ve, L);
   // E = Ve Vs^T is symmetric: the lower triangle by the product, the upper by a mirror
-  CU(gemm_f64(st, false, true, n, n, n, 1.0, h->Ve, n, S.Vs, n, 0.0, S.E, n, S.ws, ws, L, nullptr, GEMM_LOWER));
+  CU(gemm_big(h, st, false, true, n, n, n, 1.0, h->Ve, n, S.Vs, n, 0.0, S.E, n, S.ws, ws, L, GEMM_LOWER));
   lower_to_full(st, n, S.E, L);
   split_sigma(st, n, r, h->lam_s, h->ctl, S.Dv, L);
 
@@ -882,13 +912,13 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   if (h->kind == SDP_A_DIAG && h->space == 2) {
     // K = beta I + tau^-2 G o (G + 2 tau E) with G = Q (Lam - tau I) Q^T (lower triangle)
     launch_shift_cols(st, n, r, S.Vs, h->lam_s, h->ctl, S.Tm, L);
-    CU(gemm_f64(st, false, true, n, n, r, 1.0, S.Tm, n, S.Vs, n, 0.0, S.F, n, S.ws, ws, L, nullptr, GEMM_LOWER));
+    CU(gemm_big(h, st, false, true, n, n, r, 1.0, S.Tm, n, S.Vs, n, 0.0, S.F, n, S.ws, ws, L, GEMM_LOWER));
     launch_diag_K(st, n, S.F, S.E, h->ctl, S.Pinv, L);
     CU(spd_inverse(st, m, S.Pinv, h->gj_work, h->gj_work_elems, S.ws, ws, pstatus, L));
   } else if (h->space == 1) {
     // C = beta^{-1} B^T B + tau^2 Sigma  (B row-major m x d == column-major d x m)
     const double beta = h->ctl_host->beta_pc;
-    CU(gemm_f64(st, false, true, d, d, m, 1.0 / beta, S.B, d, S.B, d, 0.0, S.Pinv, d, S.ws, ws, L, nullptr,
+    CU(gemm_big(h, st, false, true, d, d, m, 1.0 / beta, S.B, d, S.B, d, 0.0, S.Pinv, d, S.ws, ws, L,
                 GEMM_LOWER));   // the Cholesky reads the lower triangle only
     launch_add_diag(st, d, S.Pinv, S.Dv, 0.0, L);
     CU(spd_inverse(st, d, S.Pinv, h->gj_work, h->gj_work_elems, S.ws, ws, pstatus, L));
@@ -896,7 +926,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     // K = beta I + B D^{-1} B^T = Bs^T Bs + beta I with Bs = D^{-1/2} B^T (d x m)
     if ((int64_t)m * d > h->bs_elems) return fail(h, SDP_EINVAL, "m-space core larger than the setup allows");
     launch_scale_B(st, m, d, S.B, S.Dv, h->Bs, L);
-    CU(gemm_f64(st, true, false, m, m, d, 1.0, h->Bs, d, h->Bs, d, 0.0, S.Pinv, m, S.ws, ws, L, nullptr, GEMM_LOWER));
+    CU(gemm_big(h, st, true, false, m, m, d, 1.0, h->Bs, d, h->Bs, d, 0.0, S.Pinv, m, S.ws, ws, L, GEMM_LOWER));
     launch_add_diag(st, m, S.Pinv, nullptr, h->ctl_host->beta_pc, L);
     CU(spd_inverse(st, m, S.Pinv, h->gj_work, h->gj_work_elems, S.ws, ws, pstatus, L));
   }
@@ -911,11 +941,11 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
 
   // ---- a3: right-hand side and start ----
   const double* Q = S.Vs;
-  CU(gemm_f64(st, false, false, n, n, n, 1.0, S.E, n, Ct, n, 0.0, S.F, n, S.ws, ws, L));
+  CU(gemm_big(h, st, false, false, n, n, n, 1.0, S.E, n, Ct, n, 0.0, S.F, n, S.ws, ws, L));
   CU(gemm_f64(st, false, false, n, r, n, 1.0, Ct, n, Q, n, 0.0, S.Tm, n, S.ws, ws, L));
   CU(gemm_f64(st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, ws, L));
   if (h->kind == SDP_A_DENSE_SVEC) {
-    CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, ws, L, nullptr, GEMM_LOWER));
+    CU(gemm_big(h, st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, ws, L, GEMM_LOWER));
     svec_pack_plus<double>(st, n, r, S.Z, nullptr, nullptr, S.zsvec, nullptr, L);
     prof_begin(h, 1);
     rows_gemv<double>(st, h->a_dense, m, h->N, S.zsvec, S.partA, nullptr, L);
@@ -1006,7 +1036,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   if (h->kind == SDP_A_DENSE_SVEC) {
     adjoint_dense(h, S, u, S.Y, nullptr);
     launch_recover_pre(st, n, m, S.Y, Ct, u, h->Cw, dy, dS, h->ctl, L);
-    CU(gemm_f64(st, false, false, n, n, n, 1.0, S.E, n, h->Cw, n, 0.0, S.F, n, S.ws, ws, L));
+    CU(gemm_big(h, st, false, false, n, n, n, 1.0, S.E, n, h->Cw, n, 0.0, S.F, n, S.ws, ws, L));
   } else if (h->kind == SDP_A_SPARSE_COO) {
     sparse_adjoint(st, h->sp, n, u, 1.0, S.Y, nullptr, L);
     launch_recover_pre(st, n, m, S.Y, Ct, u, nullptr, dy, dS, h->ctl, L);
@@ -1018,17 +1048,20 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     launch_recover_pre(st, n, m, S.Y, Ct, u, nullptr, dy, dS, h->ctl, L);
     launch_recover_F(st, n, nullptr, S.E, u, S.F, h->ctl, L);
   }
-  CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, dX, n, S.ws, ws, L, nullptr, GEMM_LOWER));
+  CU(gemm_big(h, st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, dX, n, S.ws, ws, L, GEMM_LOWER));
   h_unpack<double>(st, n, r, v, S.Hp, nullptr, L);
   CU(gemm_f64(st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, ws, L));
-  CU(gemm_f64(st, false, true, n, n, r, 0.5, S.Up, n, Q, n, 1.0, dX, n, S.ws, ws, L, nullptr, GEMM_LOWER));
-  CU(gemm_f64(st, false, true, n, n, r, 0.5, Q, n, S.Up, n, 1.0, dX, n, S.ws, ws, L, nullptr, GEMM_LOWER));
+  CU(gemm_big(h, st, false, true, n, n, r, 0.5, S.Up, n, Q, n, 1.0, dX, n, S.ws, ws, L, GEMM_LOWER));
+  CU(gemm_big(h, st, false, true, n, n, r, 0.5, Q, n, S.Up, n, 1.0, dX, n, S.ws, ws, L, GEMM_LOWER));
   lower_to_full(st, n, dX, L);
   CU(cudaEventRecord(h->ev_phase[3], st));
   CU(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
+  int tc_err = 0;
+  if (h->tc_err) CU(cudaMemcpyAsync(&tc_err, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
   CU(cudaGetLastError());
 
+  if (tc_err) return fail(h, SDP_ETIMEOUT, "a bounded wait inside a tensor-core product gave up");
   const PcgCtl& c = *h->ctl_host;
   for (int q = 0; q < 3; ++q) {
     float ms = 0.f;

@@ -1,0 +1,534 @@
+// FP64 matrix products on the BF16 tensor cores: tcgen05 MMA with TMEM accumulators, operands
+// staged by TMA, FP64 accuracy from exact integer slices (the Ozaki splitting).
+//
+//   C (M x N) = alpha * op(A) * op(B) + beta * C     (column-major, as gemm_f64)
+//
+// Splitting.  Row i of op(A) is scaled by 2^-e_i with 2^e_i > max_k |op(A)[i, k]|, so that its
+// entries a lie in (-1, 1), and written as a = sum_{s=1..8} a_s 2^-(7s-1) with integers
+// |a_s| <= 64: a_1 = rint(2^6 a), then each residual (|r| <= 1/2) times 2^7 rounded again.
+// Every a_s is exact in BF16 (8 significand bits).  Columns of op(B) likewise (exponents f_j).
+// Then op(A) op(B) = 2^(e_i + f_j) sum_{s,t} 2^-(7(s+t)-2) (A_s B_t), and each integer product
+// A_s B_t over a K-chunk of at most 4096 has |sum| <= 4096 * 64 * 64 = 2^24: exact in the FP32
+// accumulator of the tensor core.  The chunk results are scaled by the power of two and summed
+// in FP64.  Pairs with s + t <= 9 are kept (36 BF16 products): a dropped term is below
+// 2^-68 max_k|op(A)[i,k]| max_k|op(B)[k,j]| per element of K, and the splitting error of one
+// entry is at most 2^-56 of its row maximum, so the product is accurate to about K 2^-55
+// max_k|op(A)[i,k]| max_k|op(B)[k,j]| -- the FP64 bound when the rows and columns have no
+// large internal dynamic range (use gemm_f64 where they do).
+//
+// Kernel.  One CTA per 128 x 128 output tile, 9 warps: warp 8 (one lane) issues the TMA loads
+// of 128 x 64 BF16 slice tiles (128-byte swizzle) into a 4-stage ring and the 128x128x16
+// tcgen05.mma steps into one of two TMEM accumulators (256 columns); warps 0-7 drain a finished
+// accumulator (tcgen05.ld, 32 lanes x 32 columns per load) into FP64 registers while the tensor
+// core fills the other.  Every wait is bounded (about 2 s, %globaltimer): on expiry the kernel
+// sets an error word, stops issuing, waits (bounded) for its own copies and products in flight,
+// frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include <string>
+
+#include "handle.h"
+
+namespace wc {
+
+namespace {
+
+constexpr int S = 8;                  // slices per operand
+constexpr int KC = 4096;              // exact K-chunk of one slice product
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int STAGES = 4;
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = (EPI_WARPS + 1) * 32;
+constexpr int TILE_BYTES = BM * BK * 2;                 // 16 KB per operand tile
+constexpr int STAGE_BYTES = 2 * TILE_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;  // + alignment slack
+constexpr int TMEM_COLS = 256;                           // two 128-column FP32 accumulators
+constexpr int NPAIRS = S * (S + 1) / 2;                  // s + t <= S + 1
+constexpr unsigned long long WAIT_NS = 2000000000ull;
+
+// ---- PTX wrappers --------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of `parity` to complete; false after WAIT_NS (sets *abort, *err)
+// or when another role has set *abort.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, int* err) {
+  const unsigned long long t0 = gtimer();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 255u) == 255u) {
+      if (*abort) return false;
+      if (gtimer() - t0 > WAIT_NS) {
+        *abort = 1;
+        atomicExch(err, 1);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);      // start address
+  d |= (uint64_t)1u << 16;                      // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024u >> 4) << 32;            // stride byte offset
+  d |= (uint64_t)1u << 46;                      // descriptor version
+  d |= (uint64_t)2u << 61;                      // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: kind::f16 with BF16 A and B (K-major), FP32 D, M = 128, N = 128.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+#define WC_TMEM_LD32(taddr, r)                                                                                  \
+  asm volatile(                                                                                                 \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, " \
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"           \
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),          \
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),    \
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),  \
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])   \
+      : "r"(taddr))
+
+// ---- pair table: (s, t) with s + t <= S + 1 (1-based), largest weights first ---------------
+
+__device__ __forceinline__ void pair_of(int q, int& s, int& t) {
+  // q enumerates g = s + t = 2, 3, ..., S + 1 and within g s = 1 .. g - 1
+  int g = 2, base = 0;
+  while (q >= base + (g - 1)) { base += g - 1; ++g; }
+  s = 1 + (q - base);
+  t = g - s;
+}
+
+// ---- splitting ------------------------------------------------------------------------------
+
+// Rows r0 .. r0 + 31 of the R x K matrix X(r, k) = X[r * rs + k * ks]: exponent e_r and the
+// S slices out[s][r][k] (row length Kpad, zero padded).
+__global__ void __launch_bounds__(256) slice_kernel(int R, int K, int Kpad, const double* __restrict__ X,
+                                                    int64_t rs, int64_t ks, __nv_bfloat16* __restrict__ out,
+                                                    int* __restrict__ expo) {
+  __shared__ double tile[32][BK + 1];
+  __shared__ unsigned long long rmax[32];
+  __shared__ double rscale[32];
+  const int r0 = blockIdx.x * 32, tid = threadIdx.x;
+  if (tid < 32) rmax[tid] = 0ull;
+  __syncthreads();
+  const bool rows_contig = (rs == 1);
+  auto load_tile = [&](int k0) {
+    for (int q = tid; q < 32 * BK; q += 256) {
+      int r, k;
+      if (rows_contig) { r = q % 32; k = q / 32; } else { k = q % BK; r = q / BK; }
+      const int gr = r0 + r, gk = k0 + k;
+      tile[r][k] = (gr < R && gk < K) ? X[(int64_t)gr * rs + (int64_t)gk * ks] : 0.0;
+    }
+  };
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    load_tile(k0);
+    __syncthreads();
+    for (int q = tid; q < 32 * BK; q += 256) {
+      const int r = q / BK, k = q % BK;
+      const double v = fabs(tile[r][k]);
+      if (v > 0.0) atomicMax(&rmax[r], (unsigned long long)__double_as_longlong(v));
+    }
+    __syncthreads();
+  }
+  if (tid < 32) {
+    const double m = __longlong_as_double((long long)rmax[tid]);
+    const int e = (m > 0.0) ? ilogb(m) + 1 : 0;
+    rscale[tid] = scalbn(1.0, 6 - e);      // a_1 = rint(2^6 x 2^-e)
+    if (r0 + tid < R) expo[r0 + tid] = e;
+  }
+  __syncthreads();
+  const int64_t plane = (int64_t)R * Kpad;
+  for (int k0 = 0; k0 < Kpad; k0 += BK) {
+    if (k0 < K) load_tile(k0);
+    __syncthreads();
+    for (int q = tid; q < 32 * BK; q += 256) {
+      const int r = q / BK, k = q % BK;
+      const int gr = r0 + r;
+      if (gr >= R) continue;
+      double t = (k0 < K) ? tile[r][k] * rscale[r] : 0.0;
+      __nv_bfloat16* o = out + (int64_t)gr * Kpad + k0 + k;
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const double a = rint(t);
+        o[s * plane] = __double2bfloat16(a);       // |a| <= 64: exact
+        t = (t - a) * 128.0;                       // exact: |t - a| <= 1/2
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---- the product ----------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(THREADS, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
+               int K, const int* __restrict__ ea, const int* __restrict__ eb, double alpha, double beta,
+               double* __restrict__ C, int64_t ldc, int lower, int* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  if (lower && m0 + BM <= n0) return;               // tile entirely above the diagonal
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < STAGES; ++i) {
+      mbar_init(smem_u32(&full_bar[i]), 1);
+      mbar_init(smem_u32(&empty_bar[i]), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&accf_bar[i]), 1);
+      mbar_init(smem_u32(&acce_bar[i]), EPI_WARPS);
+    }
+    abort_flag = 0;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == EPI_WARPS) {                           // TMEM for two accumulators
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  const int nchunks = (K + KC - 1) / KC;
+  const int units = nchunks * NPAIRS;
+
+  if (warp == EPI_WARPS) {
+    if (lane == 0) {
+      // ---- loads and products (one thread) ----
+      int total_steps = 0;
+      for (int c = 0; c < nchunks; ++c) total_steps += (min(K, (c + 1) * KC) - c * KC + BK - 1) / BK * NPAIRS;
+      int g_load = 0, g_mma = 0;
+      int lu = 0, lk = 0;                            // load cursor: unit, step within it
+      auto unit_steps = [&](int u) {
+        const int c = u / NPAIRS;
+        return (min(K, (c + 1) * KC) - c * KC + BK - 1) / BK;
+      };
+      bool ok = true;
+      for (int u = 0; u < units && ok; ++u) {
+        const int buf = u & 1;
+        if (u >= 2 && !mbar_wait(smem_u32(&acce_bar[buf]), ((u >> 1) - 1) & 1, &abort_flag, err)) { ok = false; break; }
+        tc_fence_after();
+        const int nst = unit_steps(u);
+        for (int kk = 0; kk < nst; ++kk) {
+          while (g_load < total_steps && g_load < g_mma + STAGES) {
+            const int st = g_load % STAGES;
+            if (g_load >= STAGES &&
+                !mbar_wait(smem_u32(&empty_bar[st]), ((g_load / STAGES) - 1) & 1, &abort_flag, err)) {
+              ok = false;
+              break;
+            }
+            int s, t;
+            pair_of(lu % NPAIRS, s, t);
+            const int k0 = (lu / NPAIRS) * KC + lk * BK;
+            const uint32_t fb = smem_u32(&full_bar[st]);
+            mbar_expect_tx(fb, STAGE_BYTES);
+            tma_load_3d(base + st * STAGE_BYTES, &mapA, k0, m0, s - 1, fb);
+            tma_load_3d(base + st * STAGE_BYTES + TILE_BYTES, &mapB, k0, n0, t - 1, fb);
+            ++g_load;
+            if (++lk == unit_steps(lu)) { lk = 0; ++lu; }
+          }
+          if (!ok) break;
+          const int st = g_mma % STAGES;
+          if (!mbar_wait(smem_u32(&full_bar[st]), (g_mma / STAGES) & 1, &abort_flag, err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t a0 = base + st * STAGE_BYTES, b0 = a0 + TILE_BYTES;
+#pragma unroll
+          for (int sub = 0; sub < BK / 16; ++sub)    // 16 BF16 = 32 bytes along K per MMA
+            mma_bf16(tmem + buf * BN, smem_desc(a0 + sub * 32), smem_desc(b0 + sub * 32),
+                     (kk > 0 || sub > 0) ? 1u : 0u);
+          mma_commit(smem_u32(&empty_bar[st]));      // the stage is free once these products finish
+          ++g_mma;
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&accf_bar[buf]));        // the accumulator is complete
+      }
+      if (!ok) {
+        abort_flag = 1;
+        // bounded waits for this CTA's own products and copies still in flight
+        volatile int keep_waiting = 0;
+        if (g_mma > 0) {
+          const int st = (g_mma - 1) % STAGES;
+          mbar_wait(smem_u32(&empty_bar[st]), ((g_mma - 1) / STAGES) & 1, &keep_waiting, err);
+        }
+        for (int g = g_mma; g < g_load; ++g)
+          mbar_wait(smem_u32(&full_bar[g % STAGES]), (g / STAGES) & 1, &keep_waiting, err);
+      }
+    }
+  } else {
+    // ---- drain accumulators into FP64 (warps 0-7) ----
+    const int lg = warp & 3;                         // TMEM lanes 32 lg .. 32 lg + 31 = tile rows
+    const int cg = warp >> 2;                        // columns 64 cg .. 64 cg + 63
+    double acc[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) acc[j] = 0.0;
+    for (int u = 0; u < units; ++u) {
+      const int buf = u & 1;
+      if (!mbar_wait(smem_u32(&accf_bar[buf]), (u >> 1) & 1, &abort_flag, err)) break;
+      tc_fence_after();
+      int s, t;
+      pair_of(u % NPAIRS, s, t);
+      const double w = scalbn(1.0, -(7 * (s + t) - 2));
+      const uint32_t taddr = tmem + (uint32_t)(buf * BN + cg * 64) + ((uint32_t)(32 * lg) << 16);
+      uint32_t r[32];
+      WC_TMEM_LD32(taddr, r);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc[j] = fma(w, (double)__uint_as_float(r[j]), acc[j]);
+      WC_TMEM_LD32(taddr + 32, r);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acce_bar[buf]));
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc[32 + j] = fma(w, (double)__uint_as_float(r[j]), acc[32 + j]);
+    }
+    if (!abort_flag) {
+      const int row = m0 + 32 * lg + lane;
+      if (row < M) {
+        const int er = ea[row];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) {
+          const int col = n0 + cg * 64 + j;
+          if (col < N) {
+            const double v = alpha * scalbn(acc[j], er + eb[col]);
+            double* cp = C + (int64_t)row + (int64_t)col * ldc;
+            *cp = (beta == 0.0) ? v : v + beta * *cp;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == EPI_WARPS)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// ---- host side ------------------------------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+cudaError_t g_encode_err = cudaSuccess;
+
+cudaError_t encode_fn() {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+      g_encode_err = (e != cudaSuccess) ? e : cudaErrorNotSupported;
+      return;
+    }
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  return g_encode ? cudaSuccess : g_encode_err;
+}
+
+cudaError_t make_map(CUtensorMap* map, const void* slices, int rows, int Kpad) {
+  const cuuint64_t dims[3] = {(cuuint64_t)Kpad, (cuuint64_t)rows, (cuuint64_t)S};
+  const cuuint64_t strides[2] = {(cuuint64_t)Kpad * 2, (cuuint64_t)rows * Kpad * 2};
+  const cuuint32_t box[3] = {BK, BM, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(slices), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+inline int kpad_of(int K) { return (K + BK - 1) / BK * BK; }
+
+}  // namespace
+
+size_t tc_gemm_work_bytes(int M, int N, int K) {
+  const size_t kp = (size_t)kpad_of(K > 0 ? K : 1);
+  return 256 + align256((size_t)S * M * kp * 2) + align256((size_t)S * N * kp * 2) + align256((size_t)M * 4) +
+         align256((size_t)N * 4);
+}
+
+namespace {
+
+cudaError_t gemm_f64_tc_one(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
+                            int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                            void* work, int* err, int flags, int64_t* launches);
+
+}  // namespace
+
+// K is processed in host chunks small enough for `work` (each chunk's FP64 result is added to C).
+cudaError_t gemm_f64_tc(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
+                        int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* work,
+                        size_t work_bytes, int* err, int flags, int64_t* launches) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (K < 0 || !work || !err) return cudaErrorInvalidValue;
+  if (work_bytes >= tc_gemm_work_bytes(M, N, K))
+    return gemm_f64_tc_one(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, work, err, flags, launches);
+  const size_t per_k = (size_t)S * (M + N) * 2;           // slice bytes per unit of K
+  const size_t fixed = 256 + align256((size_t)M * 4) + align256((size_t)N * 4) + 512;
+  if (work_bytes <= fixed + per_k * BK) return cudaErrorInvalidValue;
+  int64_t kc64 = (int64_t)((work_bytes - fixed) / per_k) / BK * BK;
+  int kc = (int)std::min<int64_t>(kc64, K);
+  if (kc >= KC) kc = kc / KC * KC;                          // whole exact chunks where possible
+  while (kc >= BK && tc_gemm_work_bytes(M, N, kc) > work_bytes) kc -= BK;
+  if (kc < BK) return cudaErrorInvalidValue;
+  for (int k0 = 0; k0 < K; k0 += kc) {
+    const int kk = std::min(kc, K - k0);
+    const double* Ak = A + (tA ? (int64_t)k0 : (int64_t)k0 * lda);
+    const double* Bk = B + (tB ? (int64_t)k0 * ldb : (int64_t)k0);
+    cudaError_t e = gemm_f64_tc_one(st, tA, tB, M, N, kk, alpha, Ak, lda, Bk, ldb, k0 == 0 ? beta : 1.0, C, ldc, work,
+                                    err, flags, launches);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+namespace {
+
+cudaError_t gemm_f64_tc_one(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
+                            int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                            void* work, int* err, int flags, int64_t* launches) {
+  cudaError_t e = encode_fn();
+  if (e != cudaSuccess) return e;
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  const int Kp = kpad_of(K > 0 ? K : 1);
+  char* w = static_cast<char*>(work) + 256;
+  __nv_bfloat16* sa = reinterpret_cast<__nv_bfloat16*>(w);
+  w += align256((size_t)S * M * Kp * 2);
+  __nv_bfloat16* sb = reinterpret_cast<__nv_bfloat16*>(w);
+  w += align256((size_t)S * N * Kp * 2);
+  int* ea = reinterpret_cast<int*>(w);
+  w += align256((size_t)M * 4);
+  int* eb = reinterpret_cast<int*>(w);
+  // row i of op(A): A[i + k lda] (or A[k + i lda] transposed); row j of op(B)^T: B[k + j ldb]
+  // (or B[j + k ldb] transposed)
+  slice_kernel<<<(M + 31) / 32, 256, 0, st>>>(M, K, Kp, A, tA ? lda : 1, tA ? 1 : lda, sa, ea);
+  slice_kernel<<<(N + 31) / 32, 256, 0, st>>>(N, K, Kp, B, tB ? 1 : ldb, tB ? ldb : 1, sb, eb);
+  if (launches) *launches += 2;
+  CUtensorMap mapA, mapB;
+  e = make_map(&mapA, sa, M, Kp);
+  if (e == cudaSuccess) e = make_map(&mapB, sb, N, Kp);
+  if (e != cudaSuccess) return e;
+  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+  tc_gemm_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(mapA, mapB, M, N, K, ea, eb, alpha, beta, C, ldc,
+                                                    (flags & GEMM_LOWER) ? 1 : 0, err);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+}  // namespace wc
+
+extern "C" size_t sdp_gemm_f64_tc_work_bytes(int32_t M, int32_t N, int32_t K) {
+  if (M < 0 || N < 0 || K < 0) return 0;
+  return wc::tc_gemm_work_bytes(M, N, K);
+}
+
+extern "C" sdp_status sdp_gemm_f64_tc(void* stream, int32_t tA, int32_t tB, int32_t M, int32_t N, int32_t K,
+                                      double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                                      double beta, double* C, int64_t ldc, void* work, size_t work_bytes) {
+  using namespace wc;
+  if (M < 0 || N < 0 || K < 0) return wc_fail(nullptr, SDP_EINVAL, "negative size");
+  if (M == 0 || N == 0) return SDP_OK;
+  if (!C || !work || (K > 0 && (!A || !B))) return wc_fail(nullptr, SDP_EINVAL, "NULL array argument");
+  if (ldc < M || lda < (tA ? K : M) || ldb < (tB ? N : K) || lda < 1 || ldb < 1)
+    return wc_fail(nullptr, SDP_EINVAL, "leading dimension too small");
+  if (work_bytes < tc_gemm_work_bytes(M, N, K)) return wc_fail(nullptr, SDP_EINVAL, "work too small");
+  if ((reinterpret_cast<uintptr_t>(work) & 255u) != 0) return wc_fail(nullptr, SDP_EINVAL, "work not 256-byte aligned");
+  int dev = 0, major = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) !=
+                                                  cudaSuccess)
+    return wc_fail(nullptr, SDP_ECUDA, "no CUDA device");
+  if (major != 10) return wc_fail(nullptr, SDP_EUNSUPPORTED, "tcgen05 products need a Blackwell (sm_10x) device");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int* err = static_cast<int*>(work);
+  if (cudaMemsetAsync(work, 0, 256, st) != cudaSuccess) return wc_fail(nullptr, SDP_ECUDA, "clearing the error word");
+  cudaError_t e = gemm_f64_tc(st, tA != 0, tB != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, work, work_bytes,
+                              err, 0, nullptr);
+  if (e != cudaSuccess) return wc_fail(nullptr, SDP_ECUDA, std::string("tensor-core product: ") + cudaGetErrorString(e));
+  int h_err = 0;
+  e = cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return wc_fail(nullptr, SDP_ECUDA, std::string("tensor-core product: ") + cudaGetErrorString(e));
+  if (h_err) return wc_fail(nullptr, SDP_ETIMEOUT, "a bounded wait of the tensor-core product gave up");
+  return SDP_OK;
+}

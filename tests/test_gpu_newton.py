@@ -294,3 +294,28 @@ def test_mixed_continues_in_fp64_after_the_refinement_limit():
     assert rel(X32, X64) < TOL and rel(y32, y64) < TOL and rel(S32, S64) < TOL
     s64.close()
     s32.close()
+
+
+TC_CASES = [
+    # n >= 512: E, E C~, the recovery and the complement run on the tensor cores (exact slices)
+    ("maxcut700_r20", lambda: W.maxcut(700, 0.012, 107, weights="gauss"), 20, 24),
+    ("completion260x260", lambda: W.completion(260, 260, 3, 0.04, 23), 3, 3),
+]
+
+
+@pytest.mark.parametrize("name,mk,rt,rh", TC_CASES, ids=[c[0] for c in TC_CASES])
+def test_tensor_core_products_match_fp64_mma_and_oracle(name, mk, rt, rh):
+    """The Newton direction with the large products on the BF16 tensor cores equals the one with
+    every product on the FP64 MMA path (both stop at the same 1e-12 test) and the oracle's plain
+    definition to the FP64 tolerance."""
+    prob = mk()
+    sp = W.scaling_point(prob.n, rt, 1e-3, 900 + prob.n)
+    Ct, bt = W.newton_rhs(prob.n, prob.m, 901 + prob.n)
+    s1, (X1, y1, S1, i1) = gpu_solve(prob, sp, Ct, bt, r_hat=rh, tc_products=True)
+    s0, (X0, y0, S0, i0) = gpu_solve(prob, sp, Ct, bt, r_hat=rh, tc_products=False)
+    assert i1.converged and i0.converged and i1.r == rt
+    assert rel(X1, X0) < 1e-10 and rel(y1, y0) < 1e-10 and rel(S1, S0) < 1e-10
+    rX, ry, rS = onewton.newton_direct(prob, w_of(sp), Ct, bt)
+    assert rel(X1, rX) < TOL and rel(y1, ry) < TOL and rel(S1, rS) < TOL
+    s1.close()
+    s0.close()
