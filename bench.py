@@ -127,7 +127,7 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def other_configs(dev, reps: int = 2, only=None):
+def other_configs(dev, reps: int = 2, only=None, tc_n: int = 5000):
     """The other workloads, measured beside the headline one (not part of its timed steps).
 
     - MaxCut n=64 (m=64, DIAG, r_hat=12, FP64): time to a 1e-8 relative gap of the whole
@@ -197,10 +197,57 @@ def other_configs(dev, reps: int = 2, only=None):
         out["completion2000_r5"] = {"workload": "matrix completion n=1000+1000, m=50000 (5%), rank 5, SPARSE_COO, "
                                                 "r=5, synthetic scaling point mu=1e-4",
                                     "newton": newton_rows(prob, sp, Ct, bt, 5, ["fp64"])}
+    # the dense FP64 product on the tensor cores (the n^3 products of the n = 5000 workload)
+    if want("tc_gemm"):
+        out[f"tc_gemm_{tc_n}"] = _tc_gemm(dev, tc_n)
     # 256 independent SDPs of uneven size solved by sdp_solve_batch (minutes: only on request)
     if only == "batch256":
         out["batch256"] = _batch256(dev)
     return out
+
+
+def _tc_gemm(dev, n, reps=3):
+    """C = A B (n x n x n, FP64, column-major) by sdp_gemm_f64_tc: 8 BF16 slices per operand,
+    36 slice products on the tensor cores, FP64 sums; CUDA events around the whole call
+    (splitting included).  Reported as FP64-equivalent TFLOP/s (2 n^3 / time) and as the BF16
+    tensor rate executed (36 x 2 n^3 / time) against the measured BF16 peak."""
+    import torch
+    from paper_2407_14013_gb300 import _native
+    lib = _native.load()
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    A = torch.randn((n, n), generator=g, device=dev, dtype=torch.float64)
+    B = torch.randn((n, n), generator=g, device=dev, dtype=torch.float64)
+    C = torch.zeros((n, n), device=dev, dtype=torch.float64)
+    wb = lib.sdp_gemm_f64_tc_work_bytes(n, n, n)
+    work = torch.empty(wb // 8 + 64, dtype=torch.float64, device=dev)
+    wp = (work.data_ptr() + 255) // 256 * 256
+    st = torch.cuda.current_stream(dev)
+    run = lambda: _native.sdp_gemm_f64_tc(st.cuda_stream, False, False, n, n, n, 1.0, A.data_ptr(), n, B.data_ptr(),
+                                          n, 0.0, C.data_ptr(), n, wp, wb)
+    run()
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        run()
+        e1.record(st)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    # accuracy against the FP64 product of a sample of rows on the host: the row-major torch
+    # arrays are the transposes of the column-major matrices, so C (torch) = B (torch) A (torch)
+    import numpy as np
+    rows = np.random.default_rng(0).choice(n, 8, replace=False)
+    Bh, Ah, Ch = B[rows].cpu().numpy(), A.cpu().numpy(), C[rows].cpu().numpy()
+    ref = Bh @ Ah
+    err = float(np.max(np.abs(Ch - ref)) / np.max(np.abs(ref)))
+    t = min(ms) / 1e3
+    pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
+    bf16_rate = 36 * 2.0 * n ** 3 / t / 1e12
+    return {"n": n, "ms": min(ms), "fp64_equiv_tflops": 2.0 * n ** 3 / t / 1e12, "bf16_tflops_executed": bf16_rate,
+            "frac_of_measured_bf16_peak": bf16_rate / pk, "fp64_pipe_peak_tflops": FP64_PEAK_TFLOPS,
+            "max_rel_err_sampled_rows": err, "work_GB": wb / 1e9}
 
 
 def _batch256(dev, precs=("mixed_fp32", "fp64")):
@@ -548,9 +595,10 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
     ap.add_argument("--no-ttg", action="store_true", help="skip the time-to-gap solves")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads (MaxCut 64 / 5000, completion)")
-    ap.add_argument("--only", choices=["maxcut64", "maxcut5000", "completion2000", "batch256"],
+    ap.add_argument("--only", choices=["maxcut64", "maxcut5000", "completion2000", "tc_gemm", "batch256"],
                     help="measure only this other workload (one JSON object; no headline line)")
     ap.add_argument("--reps", type=int, default=2, help="timed Newton solves per row of the other workloads")
+    ap.add_argument("--tc-n", type=int, default=5000, help="order of the tensor-core product row (--only tc_gemm)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -558,7 +606,7 @@ def main():
         import torch
         dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
         torch.cuda.set_device(dev)
-        print(json.dumps(other_configs(dev, args.reps, only=args.only)))
+        print(json.dumps(other_configs(dev, args.reps, only=args.only, tc_n=args.tc_n)))
     else:
         run_ours(args)
 

@@ -86,6 +86,8 @@ struct sdp_handle {
   int dev = 0;                      // device of the handle (current at setup)
   char* tcw = nullptr;              // slices of the tensor-core FP64 products (NULL: not used)
   size_t tcw_bytes = 0;
+  char* tcw_b = nullptr;            // the same for the n x r products on the first side stream
+  size_t tcw_b_bytes = 0;
   int* tc_err = nullptr;            // set by a tensor-core product whose bounded wait gave up
   bool no_coop = false;             // batched solves: no cooperative (grid-barrier) launches
   int64_t b_elems = 0;              // capacity of the explicit B = A Q (m x d)

@@ -28,10 +28,15 @@ cudaError_t gemm_f64(cudaStream_t st, bool tA, bool tB, int M, int N, int K, dou
 // Same convention as gemm_f64 (flags: GEMM_LOWER only).  work: tc_gemm_work_bytes(M, N, K)
 // bytes, 256-byte aligned (its first 256 bytes are not used by the product); err: a device
 // word set to 1 when a bounded wait gave up (the caller clears and reads it).
+// Products with few output tiles split K over the SMs (FP64 partial tiles, reduced in a fixed
+// order).  done: device stop flag (may be NULL): every kernel returns at once when it is set.
+// tc_prepare(): the one-time setup (driver entry point, shared-memory attribute); call it
+// before any stream capture.
 size_t tc_gemm_work_bytes(int M, int N, int K);
+cudaError_t tc_prepare();
 cudaError_t gemm_f64_tc(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
                         int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* work,
-                        size_t work_bytes, int* err, int flags, int64_t* launches);
+                        size_t work_bytes, int* err, int flags, int64_t* launches, const int32_t* done = nullptr);
 
 // ---- rows.cu: products with row-major matrices streamed from memory ---------------------------
 // Partial sums of y_i = <row_i(A), x>: part[s * m + i] over column slabs s.  The slab count

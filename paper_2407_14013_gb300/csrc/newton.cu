@@ -37,8 +37,9 @@ using namespace wc;
 
 static std::string g_setup_err;
 
-// products with both output dimensions at least this large go to the tensor cores
+// products go to the tensor cores for n >= kTcMin and M N K >= kTcMinWork (all three >= 64)
 constexpr int kTcMin = 512;
+constexpr double kTcMinWork = 134217728.0;   // 512^3
 
 static sdp_status fail(sdp_handle* h, sdp_status s, const std::string& msg) {
   if (h) h->err = msg; else g_setup_err = msg;
@@ -211,6 +212,7 @@ size_t carve(sdp_handle* h, char* base) {
   if (h->tcw_bytes) {
     h->tc_err = c.take<int>(64);
     h->tcw = c.take<char>(h->tcw_bytes);
+    if (h->tcw_b_bytes) h->tcw_b = c.take<char>(h->tcw_b_bytes);
   }
   h->hV = c.take<double>(nn);
   h->hlam = c.take<double>(n);
@@ -386,6 +388,11 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
         need = std::max(need, tc_gemm_work_bytes(h->pinv_dim, h->pinv_dim, std::max(h->d_max, m)));
     }
     h->tcw_bytes = std::min(need, std::max(tc_gemm_work_bytes(n, n, n), (size_t)4 << 30));
+    if (r_max >= 64) h->tcw_b_bytes = tc_gemm_work_bytes(n, r_max, n);
+    if (tc_prepare() != cudaSuccess) {   // no tensor-map encoder: every product on the FP64 MMA path
+      cudaGetLastError();
+      h->tcw_bytes = h->tcw_b_bytes = 0;
+    }
   }
   h->pool_bytes = carve(h, nullptr);
   cudaError_t e = cudaMalloc(&h->pool, h->pool_bytes);
@@ -509,13 +516,17 @@ void join(sdp_handle* h, int which, int ev) {
 
 // Dense FP64 product: on the tensor cores (exact slices) when the handle holds their workspace
 // and the product is large, else on the FP64 MMA path.
+// slot 0: products on the handle's stream; slot 1: on the first side stream (its own slices).
 cudaError_t gemm_big(sdp_handle* h, cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha,
                      const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
-                     double* ws, size_t ws_elems, int64_t* L, int flags = 0) {
-  if (h->tcw && M >= kTcMin && N >= kTcMin && K >= 64 && !(flags & (GEMM_KSTART_ROW | GEMM_KSTART_COL)))
-    return gemm_f64_tc(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, h->tcw, h->tcw_bytes, h->tc_err,
-                       flags, L);
-  return gemm_f64(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, L, nullptr, flags);
+                     double* ws, size_t ws_elems, int64_t* L, int flags = 0, const int32_t* done = nullptr,
+                     int slot = 0) {
+  char* w = slot == 0 ? h->tcw : h->tcw_b;
+  const size_t wb = slot == 0 ? h->tcw_bytes : h->tcw_b_bytes;
+  if (w && M >= 64 && N >= 64 && K >= 64 && (double)M * N * K >= kTcMinWork &&
+      !(flags & (GEMM_KSTART_ROW | GEMM_KSTART_COL)) && tc_gemm_work_bytes(M, N, std::min(K, 4096)) <= wb)
+    return gemm_f64_tc(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, w, wb, h->tc_err, flags, L, done);
+  return gemm_f64(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, L, done, flags);
 }
 
 // Y = A^T(u) as a full n x n matrix (DENSE kind).
@@ -539,7 +550,8 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
   // independent of A^T(p_u)
   cudaStream_t s0 = fork(h, 0, 0);
   h_unpack<double>(s0, n, r, pv, S.Hp, done, L);
-  CU(gemm_f64(s0, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, h->ws_b[0], h->ws_b_elems, L, done));
+  CU(gemm_big(h, s0, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, h->ws_b[0], h->ws_b_elems, L, 0, done,
+              1));
   if (h->kind == SDP_A_DENSE_SVEC) {
     adjoint_dense(h, S, pu, S.Y, done);                                // Y = A^T(p_u)
     // side branch 1: H = Vs^T (Y Q), beside E Y E on the main stream
@@ -573,7 +585,7 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
                              h->dotbuf, h->counter, L);
   } else {
     launch_diag_scale_rows<double>(st, n, r, pu, S.Vs, S.Tm, done, L);  // A^T(p_u) Q = diag(p_u) Q
-    CU(gemm_f64(st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, done));
+    CU(gemm_big(h, st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, 0, done));
     rows_gemv<double>(st, S.EE, n, n, pu, S.partA, done, L);              // diag(E diag(p_u) E) = (E o E) p_u
     join(h, 0, 2);
     launch_ap_finish<double>(st, m, d, n, r, S.partA, rows_gemv_slabs(n, n), S.Up, S.Vs, S.H, S.Dv, pin, gsub, out,
@@ -600,11 +612,12 @@ sdp_status apply_operator_mixed(sdp_handle* h, Space& S, const double* pin, doub
     const int n = h->n, r = h->r;
     cudaStream_t s0 = fork(h, 0, 0);
     h_unpack<double>(s0, n, r, pv, S.Hp, done, L);
-    CU(gemm_f64(s0, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, h->ws_b[0], h->ws_b_elems, L, done));
+    CU(gemm_big(h, s0, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, h->ws_b[0], h->ws_b_elems, L, 0,
+                done, 1));
     launch_to_float(st, m, pu, M.pu, done, L);
     rows_gemv<float>(st, M.EE, n, n, M.pu, M.partA, done, L);               // (E o E) p_u
     launch_diag_scale_rows<double>(st, n, r, pu, S.Vs, S.Tm, done, L);
-    CU(gemm_f64(st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, done));
+    CU(gemm_big(h, st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, 0, done));
     join(h, 0, 2);
     launch_ap_finish<double>(st, m, d, n, r, nullptr, 0, S.Up, S.Vs, S.H, S.Dv, pin, gsub, out, mode, S.ctl,
                              h->dotbuf, h->counter, L, M.partA, rows_gemv_slabs(n, n, 4));
@@ -660,24 +673,24 @@ sdp_status apply_precond(sdp_handle* h, Space& S, const double* rin, double* zou
     if (h->space == 1) {
       sparse_posval(st, h->sp, rin, S.ypos, done, L);
       sparse_sym_spmm(st, h->sp, n, r, S.ypos, Q, n, S.Tm, n, done, L);
-      CU(gemm_f64(st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, done));
+      CU(gemm_big(h, st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, 0, done));
       launch_pc_d_s_H(st, m, d, n, r, S.H, rin, S.sd, S.ctl, L);           // s = r_v - beta^{-1} B^T r_u
       rows_gemv<double>(st, S.Pinv, d, d, S.sd, S.partC, done, L);          // C^{-1} s
       launch_pc_d_zv<double>(st, m, d, rows_gemv_slabs(d, d), S.partC, zout, S.ctl, L);   // z_v = -C^{-1} s
       h_unpack<double>(st, n, r, zout + m, S.Hp, done, L);
-      CU(gemm_f64(st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, S.ws_elems, L, done));
+      CU(gemm_big(h, st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, S.ws_elems, L, 0, done));
       sparse_apply_pos(st, h->sp, n, m, r, nullptr, S.Up, Q, S.partA, done, L);  // B z_v
       launch_pc_zu_dot<double>(st, m, d, 1, S.partA, 1, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L);
     } else {
       h_unpack<double>(st, n, r, rin + m, S.Hp, done, L, S.Dv);            // unpack(D^{-1} r_v)
-      CU(gemm_f64(st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, S.ws_elems, L, done));
+      CU(gemm_big(h, st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, S.ws_elems, L, 0, done));
       sparse_apply_pos(st, h->sp, n, m, r, nullptr, S.Up, Q, S.partA, done, L);
       launch_pc_m_w<double>(st, m, 1, S.partA, rin, S.wm, S.ctl, L);      // w = r_u + B D^{-1} r_v
       rows_gemv<double>(st, S.Pinv, m, m, S.wm, S.partC, done, L);         // K^{-1} w
       launch_pc_m_w<double>(st, m, rows_gemv_slabs(m, m), S.partC, nullptr, zout, S.ctl, L);  // z_u
       sparse_posval(st, h->sp, zout, S.ypos, done, L);
       sparse_sym_spmm(st, h->sp, n, r, S.ypos, Q, n, S.Tm, n, done, L);
-      CU(gemm_f64(st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, done));
+      CU(gemm_big(h, st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, 0, done));
       launch_diag_zv(st, m, d, n, r, S.H, rin, S.Dv, zout, S.ctl, L);      // z_v = D^{-1}(B^T z_u - r_v)
       launch_pc_zu_dot<double>(st, m, d, 0, nullptr, 2, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L);
     }
@@ -695,12 +708,12 @@ sdp_status apply_precond(sdp_handle* h, Space& S, const double* rin, double* zou
     const int n = h->n, r = h->r;
     const double* Q = S.Vs;
     h_unpack<double>(st, n, r, rin + m, S.Hp, done, L, S.Dv);              // unpack(D^{-1} r_v)
-    CU(gemm_f64(st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, S.ws_elems, L, done));
+    CU(gemm_big(h, st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, S.ws_elems, L, 0, done));
     launch_diag_w(st, n, r, S.Up, Q, rin, S.wm, S.ctl, L);                 // w = r_u + B D^{-1} r_v
     rows_gemv<double>(st, S.Pinv, m, m, S.wm, S.partC, done, L);           // K^{-1} w
     launch_pc_m_w<double>(st, m, rows_gemv_slabs(m, m), S.partC, nullptr, zout, S.ctl, L);  // z_u
     launch_diag_scale_rows<double>(st, n, r, zout, S.Vs, S.Tm, done, L);  // diag(z_u) Q
-    CU(gemm_f64(st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, done));
+    CU(gemm_big(h, st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, 0, done));
     launch_diag_zv(st, m, d, n, r, S.H, rin, S.Dv, zout, S.ctl, L);        // z_v = D^{-1}(B^T z_u - r_v)
     launch_pc_zu_dot<double>(st, m, d, 0, nullptr, 2, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L);
   } else {
@@ -942,8 +955,8 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   // ---- a3: right-hand side and start ----
   const double* Q = S.Vs;
   CU(gemm_big(h, st, false, false, n, n, n, 1.0, S.E, n, Ct, n, 0.0, S.F, n, S.ws, ws, L));
-  CU(gemm_f64(st, false, false, n, r, n, 1.0, Ct, n, Q, n, 0.0, S.Tm, n, S.ws, ws, L));
-  CU(gemm_f64(st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, ws, L));
+  CU(gemm_big(h, st, false, false, n, r, n, 1.0, Ct, n, Q, n, 0.0, S.Tm, n, S.ws, ws, L));
+  CU(gemm_big(h, st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, ws, L));
   if (h->kind == SDP_A_DENSE_SVEC) {
     CU(gemm_big(h, st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, ws, L, GEMM_LOWER));
     svec_pack_plus<double>(st, n, r, S.Z, nullptr, nullptr, S.zsvec, nullptr, L);
@@ -1050,7 +1063,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   }
   CU(gemm_big(h, st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, dX, n, S.ws, ws, L, GEMM_LOWER));
   h_unpack<double>(st, n, r, v, S.Hp, nullptr, L);
-  CU(gemm_f64(st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, ws, L));
+  CU(gemm_big(h, st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, ws, L));
   CU(gemm_big(h, st, false, true, n, n, r, 0.5, S.Up, n, Q, n, 1.0, dX, n, S.ws, ws, L, GEMM_LOWER));
   CU(gemm_big(h, st, false, true, n, n, r, 0.5, Q, n, S.Up, n, 1.0, dX, n, S.ws, ws, L, GEMM_LOWER));
   lower_to_full(st, n, dX, L);

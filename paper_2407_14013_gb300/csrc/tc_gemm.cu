@@ -170,7 +170,8 @@ __device__ __forceinline__ void pair_of(int q, int& s, int& t) {
 // S slices out[s][r][k] (row length Kpad, zero padded).
 __global__ void __launch_bounds__(256) slice_kernel(int R, int K, int Kpad, const double* __restrict__ X,
                                                     int64_t rs, int64_t ks, __nv_bfloat16* __restrict__ out,
-                                                    int* __restrict__ expo) {
+                                                    int* __restrict__ expo, const int32_t* __restrict__ done) {
+  if (done && *done) return;
   __shared__ double tile[32][BK + 1];
   __shared__ unsigned long long rmax[32];
   __shared__ double rscale[32];
@@ -228,8 +229,9 @@ __global__ void __launch_bounds__(256) slice_kernel(int R, int K, int Kpad, cons
 
 __global__ void __launch_bounds__(THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
-               int K, const int* __restrict__ ea, const int* __restrict__ eb, double alpha, double beta,
-               double* __restrict__ C, int64_t ldc, int lower, int* __restrict__ err) {
+               int K, int ksplit, const int* __restrict__ ea, const int* __restrict__ eb, double alpha, double beta,
+               double* __restrict__ C, int64_t ldc, double* __restrict__ part, int lower, int* __restrict__ err,
+               const int32_t* __restrict__ done) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2];
   __shared__ uint32_t tmem_slot;
@@ -237,6 +239,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   if (lower && m0 + BM <= n0) return;               // tile entirely above the diagonal
+  if (done && *done) return;
+  // K range of this CTA (split K over gridDim.z: FP64 partial tiles, reduced by tc_reduce_kernel)
+  const int kz0 = blockIdx.z * ksplit;
+  const int Kz = min(K, kz0 + ksplit) - kz0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
 
@@ -263,19 +269,19 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  const int nchunks = (K + KC - 1) / KC;
+  const int nchunks = Kz > 0 ? (Kz + KC - 1) / KC : 0;
   const int units = nchunks * NPAIRS;
 
   if (warp == EPI_WARPS) {
     if (lane == 0) {
       // ---- loads and products (one thread) ----
       int total_steps = 0;
-      for (int c = 0; c < nchunks; ++c) total_steps += (min(K, (c + 1) * KC) - c * KC + BK - 1) / BK * NPAIRS;
+      for (int c = 0; c < nchunks; ++c) total_steps += (min(Kz, (c + 1) * KC) - c * KC + BK - 1) / BK * NPAIRS;
       int g_load = 0, g_mma = 0;
       int lu = 0, lk = 0;                            // load cursor: unit, step within it
       auto unit_steps = [&](int u) {
         const int c = u / NPAIRS;
-        return (min(K, (c + 1) * KC) - c * KC + BK - 1) / BK;
+        return (min(Kz, (c + 1) * KC) - c * KC + BK - 1) / BK;
       };
       bool ok = true;
       for (int u = 0; u < units && ok; ++u) {
@@ -293,7 +299,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             }
             int s, t;
             pair_of(lu % NPAIRS, s, t);
-            const int k0 = (lu / NPAIRS) * KC + lk * BK;
+            const int k0 = kz0 + (lu / NPAIRS) * KC + lk * BK;
             const uint32_t fb = smem_u32(&full_bar[st]);
             mbar_expect_tx(fb, STAGE_BYTES);
             tma_load_3d(base + st * STAGE_BYTES, &mapA, k0, m0, s - 1, fb);
@@ -364,9 +370,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         for (int j = 0; j < 64; ++j) {
           const int col = n0 + cg * 64 + j;
           if (col < N) {
-            const double v = alpha * scalbn(acc[j], er + eb[col]);
-            double* cp = C + (int64_t)row + (int64_t)col * ldc;
-            *cp = (beta == 0.0) ? v : v + beta * *cp;
+            if (part) {                              // partial tile of this K range
+              part[(int64_t)blockIdx.z * M * N + row + (int64_t)col * M] = scalbn(acc[j], er + eb[col]);
+            } else {
+              const double v = alpha * scalbn(acc[j], er + eb[col]);
+              double* cp = C + (int64_t)row + (int64_t)col * ldc;
+              *cp = (beta == 0.0) ? v : v + beta * *cp;
+            }
           }
         }
       }
@@ -377,6 +387,21 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   tc_fence_after();
   if (warp == EPI_WARPS)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// C = alpha sum_z part[z] + beta C over the split K ranges, in z order (deterministic); tiles
+// above the diagonal are skipped when `lower` is set, as in the product.
+__global__ void tc_reduce_kernel(int M, int N, int nz, const double* __restrict__ part, double alpha, double beta,
+                                 double* __restrict__ C, int64_t ldc, int lower, const int32_t* __restrict__ done) {
+  if (done && *done) return;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)M * N) return;
+  const int row = (int)(q % M), col = (int)(q / M);
+  if (lower && (row / BM) * BM + BM <= (col / BN) * BN) return;
+  double sum = 0.0;
+  for (int z = 0; z < nz; ++z) sum += part[(int64_t)z * M * N + q];
+  double* cp = C + (int64_t)row + (int64_t)col * ldc;
+  *cp = (beta == 0.0) ? alpha * sum : alpha * sum + beta * *cp;
 }
 
 // ---- host side ------------------------------------------------------------------------------
@@ -415,28 +440,44 @@ inline int kpad_of(int K) { return (K + BK - 1) / BK * BK; }
 
 }  // namespace
 
+// split-K partial tiles: at most this many doubles (the split is used only when the tiles are
+// fewer than the SMs, so nz M N <= about 2 x SMs x BM x BN)
+constexpr size_t kPartElems = (size_t)320 * BM * BN;
+
 size_t tc_gemm_work_bytes(int M, int N, int K) {
   const size_t kp = (size_t)kpad_of(K > 0 ? K : 1);
   return 256 + align256((size_t)S * M * kp * 2) + align256((size_t)S * N * kp * 2) + align256((size_t)M * 4) +
-         align256((size_t)N * 4);
+         align256((size_t)N * 4) + align256(kPartElems * 8);
+}
+
+cudaError_t tc_prepare() {
+  cudaError_t e = encode_fn();
+  if (e != cudaSuccess) return e;
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  });
+  return attr_err;
 }
 
 namespace {
 
 cudaError_t gemm_f64_tc_one(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
                             int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
-                            void* work, int* err, int flags, int64_t* launches);
+                            void* work, int* err, int flags, int64_t* launches, const int32_t* done);
 
 }  // namespace
 
 // K is processed in host chunks small enough for `work` (each chunk's FP64 result is added to C).
 cudaError_t gemm_f64_tc(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
                         int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* work,
-                        size_t work_bytes, int* err, int flags, int64_t* launches) {
+                        size_t work_bytes, int* err, int flags, int64_t* launches, const int32_t* done) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (K < 0 || !work || !err) return cudaErrorInvalidValue;
   if (work_bytes >= tc_gemm_work_bytes(M, N, K))
-    return gemm_f64_tc_one(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, work, err, flags, launches);
+    return gemm_f64_tc_one(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, work, err, flags, launches,
+                           done);
   const size_t per_k = (size_t)S * (M + N) * 2;           // slice bytes per unit of K
   const size_t fixed = 256 + align256((size_t)M * 4) + align256((size_t)N * 4) + 512;
   if (work_bytes <= fixed + per_k * BK) return cudaErrorInvalidValue;
@@ -450,7 +491,7 @@ cudaError_t gemm_f64_tc(cudaStream_t st, bool tA, bool tB, int M, int N, int K, 
     const double* Ak = A + (tA ? (int64_t)k0 : (int64_t)k0 * lda);
     const double* Bk = B + (tB ? (int64_t)k0 * ldb : (int64_t)k0);
     cudaError_t e = gemm_f64_tc_one(st, tA, tB, M, N, kk, alpha, Ak, lda, Bk, ldb, k0 == 0 ? beta : 1.0, C, ldc, work,
-                                    err, flags, launches);
+                                    err, flags, launches, done);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -460,15 +501,9 @@ namespace {
 
 cudaError_t gemm_f64_tc_one(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
                             int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
-                            void* work, int* err, int flags, int64_t* launches) {
-  cudaError_t e = encode_fn();
+                            void* work, int* err, int flags, int64_t* launches, const int32_t* done) {
+  cudaError_t e = tc_prepare();
   if (e != cudaSuccess) return e;
-  static std::once_flag attr_once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(attr_once, [] {
-    attr_err = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  });
-  if (attr_err != cudaSuccess) return attr_err;
   const int Kp = kpad_of(K > 0 ? K : 1);
   char* w = static_cast<char*>(work) + 256;
   __nv_bfloat16* sa = reinterpret_cast<__nv_bfloat16*>(w);
@@ -478,19 +513,39 @@ cudaError_t gemm_f64_tc_one(cudaStream_t st, bool tA, bool tB, int M, int N, int
   int* ea = reinterpret_cast<int*>(w);
   w += align256((size_t)M * 4);
   int* eb = reinterpret_cast<int*>(w);
+  w += align256((size_t)N * 4);
+  double* part = reinterpret_cast<double*>(w);
   // row i of op(A): A[i + k lda] (or A[k + i lda] transposed); row j of op(B)^T: B[k + j ldb]
   // (or B[j + k ldb] transposed)
-  slice_kernel<<<(M + 31) / 32, 256, 0, st>>>(M, K, Kp, A, tA ? lda : 1, tA ? 1 : lda, sa, ea);
-  slice_kernel<<<(N + 31) / 32, 256, 0, st>>>(N, K, Kp, B, tB ? 1 : ldb, tB ? ldb : 1, sb, eb);
+  slice_kernel<<<(M + 31) / 32, 256, 0, st>>>(M, K, Kp, A, tA ? lda : 1, tA ? 1 : lda, sa, ea, done);
+  slice_kernel<<<(N + 31) / 32, 256, 0, st>>>(N, K, Kp, B, tB ? 1 : ldb, tB ? ldb : 1, sb, eb, done);
   if (launches) *launches += 2;
   CUtensorMap mapA, mapB;
   e = make_map(&mapA, sa, M, Kp);
   if (e == cudaSuccess) e = make_map(&mapB, sb, N, Kp);
   if (e != cudaSuccess) return e;
-  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
-  tc_gemm_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(mapA, mapB, M, N, K, ea, eb, alpha, beta, C, ldc,
-                                                    (flags & GEMM_LOWER) ? 1 : 0, err);
+  const int gm = (M + BM - 1) / BM, gn = (N + BN - 1) / BN;
+  int tiles = gm * gn;
+  if (flags & GEMM_LOWER) tiles = (tiles + gm) / 2;
+  // split K when the tiles leave SMs idle: about one CTA per SM, K ranges of >= 512
+  int nz = 1;
+  if (tiles < g_num_sms && K >= 2 * 512) {
+    nz = std::min((g_num_sms + tiles - 1) / tiles, K / 512);
+    while (nz > 1 && (size_t)nz * M * N > kPartElems) --nz;
+  }
+  int ksplit = K > 0 ? ((K + nz - 1) / nz + BK - 1) / BK * BK : 0;
+  if (ksplit > 0) nz = (K + ksplit - 1) / ksplit;
+  else nz = 1;
+  dim3 grid(gm, gn, nz);
+  tc_gemm_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(mapA, mapB, M, N, K, ksplit, ea, eb, alpha, beta, C, ldc,
+                                                    nz > 1 ? part : nullptr, (flags & GEMM_LOWER) ? 1 : 0, err, done);
   if (launches) ++*launches;
+  if (nz > 1) {
+    const int64_t tot = (int64_t)M * N;
+    tc_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, nz, part, alpha, beta, C, ldc,
+                                                                    (flags & GEMM_LOWER) ? 1 : 0, done);
+    if (launches) ++*launches;
+  }
   return cudaGetLastError();
 }
 
@@ -523,7 +578,7 @@ extern "C" sdp_status sdp_gemm_f64_tc(void* stream, int32_t tA, int32_t tB, int3
   int* err = static_cast<int*>(work);
   if (cudaMemsetAsync(work, 0, 256, st) != cudaSuccess) return wc_fail(nullptr, SDP_ECUDA, "clearing the error word");
   cudaError_t e = gemm_f64_tc(st, tA != 0, tB != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, work, work_bytes,
-                              err, 0, nullptr);
+                              err, 0, nullptr, nullptr);
   if (e != cudaSuccess) return wc_fail(nullptr, SDP_ECUDA, std::string("tensor-core product: ") + cudaGetErrorString(e));
   int h_err = 0;
   e = cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st);

@@ -7,6 +7,8 @@ FP64 matrix products.
   the 64-column step, K above one 4096-chunk), both transposes, alpha/beta: elementwise error
   <= 4 K 2^-53 max_k|A[i,k]| max_k|B[k,j]| (the stated bound, with room).
 - Rows scaled over 1e-150 .. 1e150 (the per-row and per-column exponents absorb it).
+- Products with few output tiles split K over the SMs; their partial tiles are reduced in a
+  fixed order, so the same call twice gives the same bits.
 """
 import numpy as np
 import pytest
@@ -44,7 +46,9 @@ def test_integer_products_are_exact():
 
 
 @pytest.mark.parametrize("M,N,K,tA,tB", [(129, 130, 65, False, False), (256, 100, 5000, False, True),
-                                         (333, 257, 700, True, False), (64, 512, 9000, True, True)])
+                                         (333, 257, 700, True, False), (64, 512, 9000, True, True),
+                                         # few output tiles: K split over the SMs, partial tiles reduced
+                                         (600, 100, 5000, True, False), (130, 70, 3000, False, False)])
 def test_gaussian_products_within_the_bound(M, N, K, tA, tB):
     rng = np.random.default_rng(M + N + K)
     A = rng.standard_normal((M, K))
@@ -71,3 +75,10 @@ def test_zero_and_empty():
     A = np.zeros((70, 30))
     B = np.zeros((30, 90))
     assert np.array_equal(_tc(A, B), np.zeros((70, 90)))
+
+
+def test_split_k_is_deterministic():
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((300, 4000))
+    B = rng.standard_normal((4000, 90))
+    assert np.array_equal(_tc(A, B), _tc(A, B))
