@@ -182,6 +182,17 @@ cudaError_t spd_inverse(cudaStream_t st, int n, double* A, double* work, size_t 
                         double* gemm_ws, size_t gemm_ws_elems, int32_t* status, int64_t* launches);
 // A[j, i] = A[i, j] for i > j (n x n, column-major): the upper triangle from the lower.
 void lower_to_full(cudaStream_t st, int n, double* A, int64_t* launches);
+// The same for large n with 512-wide outer panels: the panel solves, trailing updates, the
+// block rows of L^{-1} and L^{-T} L^{-1} go through the tensor-core product when `tc` allows
+// (NULL: FP64 MMA); the 512 x 512 diagonal blocks use the one-CTA 32 x 32 factorisation.
+struct TcCtx {
+  void* work = nullptr;
+  size_t bytes = 0;
+  int* err = nullptr;
+};
+size_t spd_inverse_tc_work(int n);
+cudaError_t spd_inverse_tc(cudaStream_t st, int n, double* A, double* work, size_t work_elems, double* gemm_ws,
+                           size_t gemm_ws_elems, const TcCtx* tc, int32_t* status, int64_t* launches);
 // Cholesky A = L L^T (L into A, upper zeroed) and Linv = L^{-1}; same workspace.
 cudaError_t spd_cholesky(cudaStream_t st, int n, double* A, double* Linv, double* work, size_t work_elems,
                          double* gemm_ws, size_t gemm_ws_elems, int32_t* status, int64_t* launches);

@@ -176,6 +176,7 @@ size_t carve(sdp_handle* h, char* base) {
   h->dotbuf = c.take<double>(1024);
   h->scratch = c.take<double>(8192);
   h->gj_work_elems = spd_inverse_work(h->pinv_dim);
+  if (h->tcw_bytes) h->gj_work_elems = std::max(h->gj_work_elems, spd_inverse_tc_work(h->pinv_dim));
   if (h->kind == SDP_A_SPARSE_COO) {
     h->sp.con_ptr = c.take<int32_t>(m + 1);
     h->sp.pos_r = c.take<int32_t>(h->sp.npos);
@@ -527,6 +528,20 @@ cudaError_t gemm_big(sdp_handle* h, cudaStream_t st, bool tA, bool tB, int M, in
       !(flags & (GEMM_KSTART_ROW | GEMM_KSTART_COL)) && tc_gemm_work_bytes(M, N, std::min(K, 4096)) <= wb)
     return gemm_f64_tc(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, w, wb, h->tc_err, flags, L, done);
   return gemm_f64(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, L, done, flags);
+}
+
+// Inverse of the SPD preconditioner core: two-level with tensor-core products when the handle
+// holds their workspace, else the one-level FP64 form.
+cudaError_t spd_inverse_any(sdp_handle* h, cudaStream_t st, int dim, double* P, double* ws, size_t ws_elems,
+                            int32_t* status, int64_t* L) {
+  if (h->tcw) {
+    TcCtx tc;
+    tc.work = h->tcw;
+    tc.bytes = h->tcw_bytes;
+    tc.err = h->tc_err;
+    return spd_inverse_tc(st, dim, P, h->gj_work, h->gj_work_elems, ws, ws_elems, &tc, status, L);
+  }
+  return spd_inverse(st, dim, P, h->gj_work, h->gj_work_elems, ws, ws_elems, status, L);
 }
 
 // Y = A^T(u) as a full n x n matrix (DENSE kind).
@@ -927,21 +942,21 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     launch_shift_cols(st, n, r, S.Vs, h->lam_s, h->ctl, S.Tm, L);
     CU(gemm_big(h, st, false, true, n, n, r, 1.0, S.Tm, n, S.Vs, n, 0.0, S.F, n, S.ws, ws, L, GEMM_LOWER));
     launch_diag_K(st, n, S.F, S.E, h->ctl, S.Pinv, L);
-    CU(spd_inverse(st, m, S.Pinv, h->gj_work, h->gj_work_elems, S.ws, ws, pstatus, L));
+    CU(spd_inverse_any(h, st, m, S.Pinv, S.ws, ws, pstatus, L));
   } else if (h->space == 1) {
     // C = beta^{-1} B^T B + tau^2 Sigma  (B row-major m x d == column-major d x m)
     const double beta = h->ctl_host->beta_pc;
     CU(gemm_big(h, st, false, true, d, d, m, 1.0 / beta, S.B, d, S.B, d, 0.0, S.Pinv, d, S.ws, ws, L,
                 GEMM_LOWER));   // the Cholesky reads the lower triangle only
     launch_add_diag(st, d, S.Pinv, S.Dv, 0.0, L);
-    CU(spd_inverse(st, d, S.Pinv, h->gj_work, h->gj_work_elems, S.ws, ws, pstatus, L));
+    CU(spd_inverse_any(h, st, d, S.Pinv, S.ws, ws, pstatus, L));
   } else {
     // K = beta I + B D^{-1} B^T = Bs^T Bs + beta I with Bs = D^{-1/2} B^T (d x m)
     if ((int64_t)m * d > h->bs_elems) return fail(h, SDP_EINVAL, "m-space core larger than the setup allows");
     launch_scale_B(st, m, d, S.B, S.Dv, h->Bs, L);
     CU(gemm_big(h, st, true, false, m, m, d, 1.0, h->Bs, d, h->Bs, d, 0.0, S.Pinv, m, S.ws, ws, L, GEMM_LOWER));
     launch_add_diag(st, m, S.Pinv, nullptr, h->ctl_host->beta_pc, L);
-    CU(spd_inverse(st, m, S.Pinv, h->gj_work, h->gj_work_elems, S.ws, ws, pstatus, L));
+    CU(spd_inverse_any(h, st, m, S.Pinv, S.ws, ws, pstatus, L));
   }
   if (h->mixed) {   // FP32 copies for the A E A^T block of the mixed operator
     if (S.EE) convert<float, double>(st, (int64_t)n * n, S.EE, h->m32.EE, L);

@@ -11,6 +11,8 @@
 //
 // Blocked with NB x NB diagonal blocks: each diagonal block is factored and its triangular
 // factor inverted inside one CTA; everything else is FP64 GEMM (DMMA).
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -33,7 +35,7 @@ constexpr int NB = 32;
 // L^{-1} = D^{-1/2} X~ with D = diag(S_pp).
 __global__ void __launch_bounds__(256)
 chol_block_kernel(int n, int k0, int w, double* __restrict__ A, double* __restrict__ Li,
-                  int32_t* __restrict__ status) {
+                  int32_t* __restrict__ status) {   // n: leading dimension of A
   __shared__ double S[NB][NB + 1];
   __shared__ double X[NB][NB + 1];
   __shared__ double inv[NB], dsq[NB], rdsq[NB];
@@ -109,11 +111,11 @@ __global__ void copy_block_kernel(int rows, int cols, const double* __restrict__
 }
 
 // zero the strictly upper triangle of an n x n matrix
-__global__ void zero_upper_kernel(int n, double* __restrict__ A) {
+__global__ void zero_upper_kernel(int n, int64_t ld, double* __restrict__ A) {
   int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (int64_t)n * n) return;
   int i = (int)(q % n), j = (int)(q / n);
-  if (j > i) A[q] = 0.0;
+  if (j > i) A[i + (int64_t)j * ld] = 0.0;
 }
 
 // upper triangle := lower triangle
@@ -135,45 +137,48 @@ namespace {
 
 // Blocked Cholesky A = L L^T (L into the lower triangle of A, upper zeroed) and X = L^{-1}
 // (lower triangular, n x n, ld n).
-cudaError_t cholesky_and_inverse(cudaStream_t st, int n, double* A, double* X, double* T, double* U, double* Li,
-                                 double* gemm_ws, size_t gemm_ws_elems, int32_t* status, int64_t* launches) {
+// A (n x n, leading dimension ld) = L L^T, L into A (upper zeroed); X (ld ldx, NULL: factor
+// only) = L^{-1}; T: n x NB, U: NB x n, Li: ceil(n / NB) NB x NB blocks.
+cudaError_t cholesky_and_inverse(cudaStream_t st, int n, int64_t ld, double* A, double* X, int64_t ldx, double* T,
+                                 double* U, double* Li, double* gemm_ws, size_t gemm_ws_elems, int32_t* status,
+                                 int64_t* launches) {
   cudaError_t e;
   // ---- blocked right-looking Cholesky, L in the lower triangle of A
   for (int k0 = 0, b = 0; k0 < n; k0 += NB, ++b) {
     const int w = (n - k0) < NB ? (n - k0) : NB;
     const int k1 = k0 + w, rest = n - k1;
     double* Lib = Li + (size_t)b * NB * NB;
-    chol_block_kernel<<<1, 256, 0, st>>>(n, k0, w, A, Lib, status);
+    chol_block_kernel<<<1, 256, 0, st>>>((int)ld, k0, w, A, Lib, status);
     if (launches) ++*launches;
     if (rest == 0) break;
     // L_RK = A_RK L_KK^{-T}
-    e = gemm_f64(st, false, true, rest, w, w, 1.0, A + k1 + (int64_t)k0 * n, n, Lib, w, 0.0, T, rest, gemm_ws,
+    e = gemm_f64(st, false, true, rest, w, w, 1.0, A + k1 + (int64_t)k0 * ld, ld, Lib, w, 0.0, T, rest, gemm_ws,
                  gemm_ws_elems, launches);
     if (e != cudaSuccess) return e;
-    copy_block_kernel<<<nblk((int64_t)rest * w, 256), 256, 0, st>>>(rest, w, T, rest, A + k1 + (int64_t)k0 * n, n);
+    copy_block_kernel<<<nblk((int64_t)rest * w, 256), 256, 0, st>>>(rest, w, T, rest, A + k1 + (int64_t)k0 * ld, ld);
     if (launches) ++*launches;
     // A_RR -= L_RK L_RK^T
-    e = gemm_f64(st, false, true, rest, rest, w, -1.0, T, rest, T, rest, 1.0, A + k1 + (int64_t)k1 * n, n, gemm_ws,
+    e = gemm_f64(st, false, true, rest, rest, w, -1.0, T, rest, T, rest, 1.0, A + k1 + (int64_t)k1 * ld, ld, gemm_ws,
                  gemm_ws_elems, launches, nullptr, GEMM_LOWER);
     if (e != cudaSuccess) return e;
   }
-  zero_upper_kernel<<<nblk((int64_t)n * n, 256), 256, 0, st>>>(n, A);
+  zero_upper_kernel<<<nblk((int64_t)n * n, 256), 256, 0, st>>>(n, ld, A);
   if (launches) ++*launches;
   if (!X) return cudaGetLastError();   // factor only
   // ---- X = L^{-1} by block rows: X[I, :I] = -Li_II (L[I, :I] X[:I, :I]), X[I, I] = Li_II
-  e = cudaMemsetAsync(X, 0, (size_t)n * n * sizeof(double), st);
+  e = cudaMemset2DAsync(X, ldx * sizeof(double), 0, n * sizeof(double), n, st);
   if (e != cudaSuccess) return e;
   for (int i0 = 0, b = 0; i0 < n; i0 += NB, ++b) {
     const int w = (n - i0) < NB ? (n - i0) : NB;
     const double* Lib = Li + (size_t)b * NB * NB;
     if (i0 > 0) {
-      e = gemm_f64(st, false, false, w, i0, i0, 1.0, A + i0, n, X, n, 0.0, U, w, gemm_ws, gemm_ws_elems, launches,
+      e = gemm_f64(st, false, false, w, i0, i0, 1.0, A + i0, ld, X, ldx, 0.0, U, w, gemm_ws, gemm_ws_elems, launches,
                    nullptr, GEMM_KSTART_COL);   // X lower triangular
       if (e != cudaSuccess) return e;
-      e = gemm_f64(st, false, false, w, i0, w, -1.0, Lib, w, U, w, 0.0, X + i0, n, gemm_ws, gemm_ws_elems, launches);
+      e = gemm_f64(st, false, false, w, i0, w, -1.0, Lib, w, U, w, 0.0, X + i0, ldx, gemm_ws, gemm_ws_elems, launches);
       if (e != cudaSuccess) return e;
     }
-    copy_block_kernel<<<nblk((int64_t)w * w, 256), 256, 0, st>>>(w, w, Lib, w, X + i0 + (int64_t)i0 * n, n);
+    copy_block_kernel<<<nblk((int64_t)w * w, 256), 256, 0, st>>>(w, w, Lib, w, X + i0 + (int64_t)i0 * ldx, ldx);
     if (launches) ++*launches;
   }
   return cudaGetLastError();
@@ -189,7 +194,7 @@ cudaError_t spd_inverse(cudaStream_t st, int n, double* A, double* work, size_t 
   double* T = X + (size_t)n * n;                      // n x NB panel
   double* U = T + (size_t)n * NB;                     // NB x n temporary
   double* Li = U + (size_t)n * NB;                    // inverses of the diagonal blocks
-  cudaError_t e = cholesky_and_inverse(st, n, A, X, T, U, Li, gemm_ws, gemm_ws_elems, status, launches);
+  cudaError_t e = cholesky_and_inverse(st, n, n, A, X, n, T, U, Li, gemm_ws, gemm_ws_elems, status, launches);
   if (e != cudaSuccess) return e;
   // ---- A^{-1} = X^T X
   // lower triangle of X^T X, skipping the zero upper part of X
@@ -206,6 +211,93 @@ void lower_to_full(cudaStream_t st, int n, double* A, int64_t* launches) {
   if (launches) ++*launches;
 }
 
+// ---- two-level form for large n: 512-wide outer panels whose products run on the tensor cores
+
+namespace {
+
+constexpr int NB2 = 512;
+
+// dense product: tensor cores (exact slices) when the context allows and the product is large
+cudaError_t gemm_any(const TcCtx* tc, cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha,
+                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                     double* gemm_ws, size_t gemm_ws_elems, int64_t* launches, int flags) {
+  if (tc && tc->work && M >= 64 && N >= 64 && K >= 64 && (double)M * N * K >= 134217728.0 &&
+      tc_gemm_work_bytes(M, N, std::min(K, 4096)) <= tc->bytes)
+    return gemm_f64_tc(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tc->work, tc->bytes, tc->err,
+                       flags & GEMM_LOWER, launches);
+  return gemm_f64(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, gemm_ws, gemm_ws_elems, launches, nullptr,
+                  flags);
+}
+
+}  // namespace
+
+size_t spd_inverse_tc_work(int n) {
+  const size_t nb2 = (size_t)(n + NB2 - 1) / NB2;
+  // X (n x n), panel T (n x NB2), U (NB2 x n), the diagonal-block inverses, the inner temporaries
+  return (size_t)n * n + 2 * (size_t)n * NB2 + nb2 * NB2 * NB2 + 2 * (size_t)NB2 * NB + (size_t)(NB2 / NB) * NB * NB;
+}
+
+cudaError_t spd_inverse_tc(cudaStream_t st, int n, double* A, double* work, size_t work_elems, double* gemm_ws,
+                           size_t gemm_ws_elems, const TcCtx* tc, int32_t* status, int64_t* launches) {
+  if (n < 2 * NB2) return spd_inverse(st, n, A, work, work_elems, gemm_ws, gemm_ws_elems, status, launches);
+  if (spd_inverse_tc_work(n) > work_elems) return cudaErrorInvalidValue;
+  double* X = work;                                       // n x n, becomes L^{-1}
+  double* T = X + (size_t)n * n;                          // rest x NB2 panel
+  double* U = T + (size_t)n * NB2;                        // NB2 x i0
+  double* Xd = U + (size_t)n * NB2;                       // inverses of the diagonal blocks (ld NB2)
+  const size_t nb2 = (size_t)(n + NB2 - 1) / NB2;
+  double* Ti = Xd + nb2 * NB2 * NB2;                      // inner temporaries
+  double* Ui = Ti + (size_t)NB2 * NB;
+  double* Li = Ui + (size_t)NB2 * NB;
+  cudaError_t e;
+  // ---- right-looking Cholesky over 512-wide panels
+  for (int k0 = 0, b = 0; k0 < n; k0 += NB2, ++b) {
+    const int w = std::min(NB2, n - k0);
+    const int k1 = k0 + w, rest = n - k1;
+    double* Xb = Xd + (size_t)b * NB2 * NB2;
+    // L_KK and L_KK^{-1} (one-CTA 32 x 32 blocks inside)
+    e = cholesky_and_inverse(st, w, n, A + k0 + (int64_t)k0 * n, Xb, NB2, Ti, Ui, Li, gemm_ws, gemm_ws_elems, status,
+                             launches);
+    if (e != cudaSuccess) return e;
+    if (rest == 0) break;
+    // L_RK = A_RK L_KK^{-T};  A_RR -= L_RK L_RK^T (lower)
+    e = gemm_any(tc, st, false, true, rest, w, w, 1.0, A + k1 + (int64_t)k0 * n, n, Xb, NB2, 0.0, T, rest, gemm_ws,
+                 gemm_ws_elems, launches, 0);
+    if (e != cudaSuccess) return e;
+    copy_block_kernel<<<nblk((int64_t)rest * w, 256), 256, 0, st>>>(rest, w, T, rest, A + k1 + (int64_t)k0 * n, n);
+    if (launches) ++*launches;
+    e = gemm_any(tc, st, false, true, rest, rest, w, -1.0, T, rest, T, rest, 1.0, A + k1 + (int64_t)k1 * n, n, gemm_ws,
+                 gemm_ws_elems, launches, GEMM_LOWER);
+    if (e != cudaSuccess) return e;
+  }
+  zero_upper_kernel<<<nblk((int64_t)n * n, 256), 256, 0, st>>>(n, n, A);
+  if (launches) ++*launches;
+  // ---- X = L^{-1} by panel rows: X[I, :I] = -X_II (L[I, :I] X[:I, :I]), X[I, I] = X_II
+  e = cudaMemsetAsync(X, 0, (size_t)n * n * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  for (int i0 = 0, b = 0; i0 < n; i0 += NB2, ++b) {
+    const int w = std::min(NB2, n - i0);
+    const double* Xb = Xd + (size_t)b * NB2 * NB2;
+    if (i0 > 0) {
+      e = gemm_any(tc, st, false, false, w, i0, i0, 1.0, A + i0, n, X, n, 0.0, U, w, gemm_ws, gemm_ws_elems, launches,
+                   GEMM_KSTART_COL);
+      if (e != cudaSuccess) return e;
+      e = gemm_any(tc, st, false, false, w, i0, w, -1.0, Xb, NB2, U, w, 0.0, X + i0, n, gemm_ws, gemm_ws_elems,
+                   launches, 0);
+      if (e != cudaSuccess) return e;
+    }
+    copy_block_kernel<<<nblk((int64_t)w * w, 256), 256, 0, st>>>(w, w, Xb, NB2, X + i0 + (int64_t)i0 * n, n);
+    if (launches) ++*launches;
+  }
+  // ---- A^{-1} = X^T X (lower triangle, then mirrored)
+  e = gemm_any(tc, st, true, false, n, n, n, 1.0, X, n, X, n, 0.0, A, n, gemm_ws, gemm_ws_elems, launches,
+               GEMM_LOWER | GEMM_KSTART_ROW | GEMM_KSTART_COL);
+  if (e != cudaSuccess) return e;
+  lower_to_full_kernel<<<nblk((int64_t)n * n, 256), 256, 0, st>>>(n, A);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
 // A = L L^T: L into A (lower, upper zeroed), L^{-1} into Linv (n x n; NULL: factor only).
 // work as for spd_inverse.
 cudaError_t spd_cholesky(cudaStream_t st, int n, double* A, double* Linv, double* work, size_t work_elems,
@@ -214,7 +306,7 @@ cudaError_t spd_cholesky(cudaStream_t st, int n, double* A, double* Linv, double
   double* T = work + (size_t)n * n;
   double* U = T + (size_t)n * NB;
   double* Li = U + (size_t)n * NB;
-  return cholesky_and_inverse(st, n, A, Linv, T, U, Li, gemm_ws, gemm_ws_elems, status, launches);
+  return cholesky_and_inverse(st, n, n, A, Linv, n, T, U, Li, gemm_ws, gemm_ws_elems, status, launches);
 }
 
 }  // namespace wc
