@@ -165,63 +165,90 @@ __device__ __forceinline__ void pair_of(int q, int& s, int& t) {
 }
 
 // ---- splitting ------------------------------------------------------------------------------
+// Two passes over X(r, k) = X[r * rs + k * ks] (R x K): the largest magnitude of every row
+// (bit patterns of non-negative doubles order like the doubles), then the slices.  The
+// slices of x in row r with exponent e (2^e > max |row|) are the signed base-128 digits of the
+// integer N = round(x 2^(55 - e)), |N| < 2^55: N = sum_{s=1..8} a_s 128^(8-s) with a_2..a_8 the
+// centred remainders in [-64, 63] and a_1 in [-64, 64]; then x 2^-e = sum_s a_s 2^-(7s-1) up to
+// the rounding of N (at most 2^-56).  Integer arithmetic only (no FP64 pipe); the BF16 bits of
+// -64..64 come from a shared-memory table.
 
-// Rows r0 .. r0 + 31 of the R x K matrix X(r, k) = X[r * rs + k * ks]: exponent e_r and the
-// S slices out[s][r][k] (row length Kpad, zero padded).
-__global__ void __launch_bounds__(256) slice_kernel(int R, int K, int Kpad, const double* __restrict__ X,
-                                                    int64_t rs, int64_t ks, __nv_bfloat16* __restrict__ out,
-                                                    int* __restrict__ expo, const int32_t* __restrict__ done) {
+__global__ void __launch_bounds__(256) rowmax_kernel(int R, int K, const double* __restrict__ X, int64_t rs,
+                                                     int64_t ks, unsigned long long* __restrict__ rmax,
+                                                     const int32_t* __restrict__ done) {
   if (done && *done) return;
-  __shared__ double tile[32][BK + 1];
-  __shared__ unsigned long long rmax[32];
-  __shared__ double rscale[32];
-  const int r0 = blockIdx.x * 32, tid = threadIdx.x;
-  if (tid < 32) rmax[tid] = 0ull;
+  __shared__ unsigned long long sm[32];
+  const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 256, tid = threadIdx.x;
+  if (tid < 32) sm[tid] = 0ull;
   __syncthreads();
   const bool rows_contig = (rs == 1);
-  auto load_tile = [&](int k0) {
-    for (int q = tid; q < 32 * BK; q += 256) {
-      int r, k;
-      if (rows_contig) { r = q % 32; k = q / 32; } else { k = q % BK; r = q / BK; }
-      const int gr = r0 + r, gk = k0 + k;
-      tile[r][k] = (gr < R && gk < K) ? X[(int64_t)gr * rs + (int64_t)gk * ks] : 0.0;
+  for (int q = tid; q < 32 * 256; q += 256) {
+    int r, k;
+    if (rows_contig) { r = q % 32; k = q / 32; } else { k = q % 256; r = q / 256; }
+    const int gr = r0 + r, gk = k0 + k;
+    if (gr < R && gk < K) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(X[(int64_t)gr * rs + (int64_t)gk * ks]) &
+                                   0x7FFFFFFFFFFFFFFFull;
+      if (b) atomicMax(&sm[r], b);
     }
-  };
-  for (int k0 = 0; k0 < K; k0 += BK) {
-    load_tile(k0);
-    __syncthreads();
-    for (int q = tid; q < 32 * BK; q += 256) {
-      const int r = q / BK, k = q % BK;
-      const double v = fabs(tile[r][k]);
-      if (v > 0.0) atomicMax(&rmax[r], (unsigned long long)__double_as_longlong(v));
-    }
-    __syncthreads();
   }
+  __syncthreads();
+  if (tid < 32 && r0 + tid < R && sm[tid]) atomicMax(&rmax[r0 + tid], sm[tid]);
+}
+
+__device__ __forceinline__ int row_exponent(unsigned long long mbits) {
+  if (mbits == 0ull) return 0;
+  return ilogb(__longlong_as_double((long long)mbits)) + 1;
+}
+
+__global__ void __launch_bounds__(256) slice_kernel(int R, int K, int Kpad, const double* __restrict__ X,
+                                                    int64_t rs, int64_t ks,
+                                                    const unsigned long long* __restrict__ rmax,
+                                                    __nv_bfloat16* __restrict__ out, int* __restrict__ expo,
+                                                    const int32_t* __restrict__ done) {
+  if (done && *done) return;
+  __shared__ double tile[32][BK + 1];
+  __shared__ unsigned short bf[129];
+  __shared__ int rexp[32];
+  const int r0 = blockIdx.x * 32, k0 = blockIdx.y * BK, tid = threadIdx.x;
+  if (tid < 129) bf[tid] = __bfloat16_as_ushort(__float2bfloat16((float)(tid - 64)));   // exact
   if (tid < 32) {
-    const double m = __longlong_as_double((long long)rmax[tid]);
-    const int e = (m > 0.0) ? ilogb(m) + 1 : 0;
-    rscale[tid] = scalbn(1.0, 6 - e);      // a_1 = rint(2^6 x 2^-e)
-    if (r0 + tid < R) expo[r0 + tid] = e;
+    const int e = (r0 + tid < R) ? row_exponent(rmax[r0 + tid]) : 0;
+    rexp[tid] = e;
+    if (blockIdx.y == 0 && r0 + tid < R) expo[r0 + tid] = e;
+  }
+  const bool rows_contig = (rs == 1);
+  for (int q = tid; q < 32 * BK; q += 256) {
+    int r, k;
+    if (rows_contig) { r = q % 32; k = q / 32; } else { k = q % BK; r = q / BK; }
+    const int gr = r0 + r, gk = k0 + k;
+    tile[r][k] = (gr < R && gk < K) ? X[(int64_t)gr * rs + (int64_t)gk * ks] : 0.0;
   }
   __syncthreads();
   const int64_t plane = (int64_t)R * Kpad;
-  for (int k0 = 0; k0 < Kpad; k0 += BK) {
-    if (k0 < K) load_tile(k0);
-    __syncthreads();
-    for (int q = tid; q < 32 * BK; q += 256) {
-      const int r = q / BK, k = q % BK;
-      const int gr = r0 + r;
-      if (gr >= R) continue;
-      double t = (k0 < K) ? tile[r][k] * rscale[r] : 0.0;
-      __nv_bfloat16* o = out + (int64_t)gr * Kpad + k0 + k;
+  for (int q = tid; q < 32 * BK; q += 256) {
+    const int r = q / BK, k = q % BK;
+    const int gr = r0 + r;
+    if (gr >= R) continue;
+    // N = round(x 2^(55 - e)) from the IEEE fields: |x| = m 2^(ex - 1075), m < 2^53
+    const unsigned long long b = (unsigned long long)__double_as_longlong(tile[r][k]);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    if (ex) m |= 1ull << 52;
+    const int sh = (ex ? ex : 1) - 1075 + 55 - rexp[r];
+    long long Nv;
+    if (m == 0ull || sh <= -64) Nv = 0;
+    else if (sh >= 0) Nv = (long long)(m << sh);                       // sh <= 2: |N| < 2^55
+    else Nv = (long long)((m + (1ull << (-sh - 1))) >> (-sh));        // rounded
+    if (b >> 63) Nv = -Nv;
+    __nv_bfloat16* o = out + (int64_t)gr * Kpad + k0 + k;
 #pragma unroll
-      for (int s = 0; s < S; ++s) {
-        const double a = rint(t);
-        o[s * plane] = __double2bfloat16(a);       // |a| <= 64: exact
-        t = (t - a) * 128.0;                       // exact: |t - a| <= 1/2
-      }
+    for (int sidx = S - 1; sidx >= 1; --sidx) {                        // a_8 .. a_2
+      const long long a = ((Nv + 64) & 127) - 64;
+      o[sidx * plane] = __ushort_as_bfloat16(bf[a + 64]);
+      Nv = (Nv - a) >> 7;                                              // exact
     }
-    __syncthreads();
+    o[0] = __ushort_as_bfloat16(bf[Nv + 64]);                          // a_1, |a_1| <= 64
   }
 }
 
@@ -447,7 +474,7 @@ constexpr size_t kPartElems = (size_t)320 * BM * BN;
 size_t tc_gemm_work_bytes(int M, int N, int K) {
   const size_t kp = (size_t)kpad_of(K > 0 ? K : 1);
   return 256 + align256((size_t)S * M * kp * 2) + align256((size_t)S * N * kp * 2) + align256((size_t)M * 4) +
-         align256((size_t)N * 4) + align256(kPartElems * 8);
+         align256((size_t)N * 4) + align256((size_t)M * 8) + align256((size_t)N * 8) + align256(kPartElems * 8);
 }
 
 cudaError_t tc_prepare() {
@@ -479,7 +506,8 @@ cudaError_t gemm_f64_tc(cudaStream_t st, bool tA, bool tB, int M, int N, int K, 
     return gemm_f64_tc_one(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, work, err, flags, launches,
                            done);
   const size_t per_k = (size_t)S * (M + N) * 2;           // slice bytes per unit of K
-  const size_t fixed = 256 + align256((size_t)M * 4) + align256((size_t)N * 4) + 512;
+  const size_t fixed = 256 + align256((size_t)M * 4) + align256((size_t)N * 4) + align256((size_t)M * 8) +
+                       align256((size_t)N * 8) + align256(kPartElems * 8) + 512;
   if (work_bytes <= fixed + per_k * BK) return cudaErrorInvalidValue;
   int64_t kc64 = (int64_t)((work_bytes - fixed) / per_k) / BK * BK;
   int kc = (int)std::min<int64_t>(kc64, K);
@@ -514,12 +542,23 @@ cudaError_t gemm_f64_tc_one(cudaStream_t st, bool tA, bool tB, int M, int N, int
   w += align256((size_t)M * 4);
   int* eb = reinterpret_cast<int*>(w);
   w += align256((size_t)N * 4);
+  unsigned long long* rmA = reinterpret_cast<unsigned long long*>(w);
+  w += align256((size_t)M * 8);
+  unsigned long long* rmB = reinterpret_cast<unsigned long long*>(w);
+  w += align256((size_t)N * 8);
   double* part = reinterpret_cast<double*>(w);
   // row i of op(A): A[i + k lda] (or A[k + i lda] transposed); row j of op(B)^T: B[k + j ldb]
   // (or B[j + k ldb] transposed)
-  slice_kernel<<<(M + 31) / 32, 256, 0, st>>>(M, K, Kp, A, tA ? lda : 1, tA ? 1 : lda, sa, ea, done);
-  slice_kernel<<<(N + 31) / 32, 256, 0, st>>>(N, K, Kp, B, tB ? 1 : ldb, tB ? ldb : 1, sb, eb, done);
-  if (launches) *launches += 2;
+  e = cudaMemsetAsync(rmA, 0, (size_t)M * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(rmB, 0, (size_t)N * 8, st);
+  if (e != cudaSuccess) return e;
+  const int64_t ars = tA ? lda : 1, aks = tA ? 1 : lda, brs = tB ? 1 : ldb, bks = tB ? ldb : 1;
+  const unsigned kb = (unsigned)((std::max(K, 1) + 255) / 256), kp64 = (unsigned)(Kp / BK);
+  rowmax_kernel<<<dim3((M + 31) / 32, kb), 256, 0, st>>>(M, K, A, ars, aks, rmA, done);
+  rowmax_kernel<<<dim3((N + 31) / 32, kb), 256, 0, st>>>(N, K, B, brs, bks, rmB, done);
+  slice_kernel<<<dim3((M + 31) / 32, kp64), 256, 0, st>>>(M, K, Kp, A, ars, aks, rmA, sa, ea, done);
+  slice_kernel<<<dim3((N + 31) / 32, kp64), 256, 0, st>>>(N, K, Kp, B, brs, bks, rmB, sb, eb, done);
+  if (launches) *launches += 4;
   CUtensorMap mapA, mapB;
   e = make_map(&mapA, sa, M, Kp);
   if (e == cudaSuccess) e = make_map(&mapB, sb, N, Kp);
