@@ -200,9 +200,54 @@ def other_configs(dev, reps: int = 2, only=None, tc_n: int = 5000):
     # the dense FP64 product on the tensor cores (the n^3 products of the n = 5000 workload)
     if want("tc_gemm"):
         out[f"tc_gemm_{tc_n}"] = _tc_gemm(dev, tc_n)
+    # the completion SDP solved to a 1e-8 gap and differentiated at its optimum (minutes: on request)
+    if only == "completion2000_solve":
+        out["completion2000_solve"] = _completion_solve(dev)
     # 256 independent SDPs of uneven size solved by sdp_solve_batch (minutes: only on request)
     if only == "batch256":
         out["batch256"] = _batch256(dev)
+    return out
+
+
+def _completion_solve(dev):
+    """Matrix completion n = 1000 + 1000, m = 50000, rank 5 (FP64): sdp_solve to a 1e-8 gap, then
+    the adjoint at the final iterate (sdp_scaling_point + sdp_grad) checked by the envelope
+    theorem (dp*/db = y*, dp*/dC = X*), and the recovery of the planted matrix."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2407_14013_gb300 import NewtonSolver
+    prob = W.workload("completion2000")
+    s = NewtonSolver(prob, r_hat=5, device=str(dev))
+    b = torch.from_numpy(prob.b).to(dev)
+    C = torch.from_numpy(prob.C).to(dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    X, y, S, info = s.solve_sdp(b, C, gap_tol=1e-8, max_iter=100, allow_notconv=True)
+    torch.cuda.synchronize(dev)
+    solve_s = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    V, lam = s.scaling_point(X, S)
+    gC1, gb1 = s.grad(V, lam, C, torch.zeros_like(b))
+    gC2, gb2 = s.grad(V, lam, torch.zeros_like(C), b)
+    torch.cuda.synchronize(dev)
+    grad_s = time.perf_counter() - t1
+    rel = lambda a, r: float(torch.linalg.norm(a - r) / torch.linalg.norm(r))
+    Xh = X.cpu().numpy()
+    n1 = prob.meta["n1"]
+    M = prob.meta["F1"] @ prob.meta["F2"].T
+    nuc = float(np.linalg.svd(M, compute_uv=False).sum())
+    out = {"workload": "matrix completion n=1000+1000, m=50000 (5%), rank-5 target, C = I, r_hat = 5, FP64",
+           "time_to_gap_1e-8_s": solve_s, "outer_iters": info["iters"], "converged": bool(info["converged"]),
+           "rel_gap": info["rel_gap"], "pinf": info["pinf"], "dinf": info["dinf"], "pcg_iters": info["pcg_iters"],
+           "newton_s": info["newton_ms"] / 1e3, "eig_sweeps": info["eig_sweeps"],
+           "objective": float(np.trace(Xh)), "twice_nuclear_norm_of_target": 2 * nuc,
+           "recovery_rel_err": float(np.linalg.norm(Xh[:n1, n1:] - M) / np.linalg.norm(M)),
+           "adjoint_s": grad_s,
+           "envelope_gb_vs_y": rel(gb1, y), "envelope_gC_vs_X": rel(gC2, X),
+           "envelope_gC_norm_rel": float(torch.linalg.norm(gC1) / torch.linalg.norm(X)),
+           "envelope_gb_norm_rel": float(torch.linalg.norm(gb2) / torch.linalg.norm(y))}
+    s.close()
     return out
 
 
@@ -595,7 +640,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
     ap.add_argument("--no-ttg", action="store_true", help="skip the time-to-gap solves")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads (MaxCut 64 / 5000, completion)")
-    ap.add_argument("--only", choices=["maxcut64", "maxcut5000", "completion2000", "tc_gemm", "batch256"],
+    ap.add_argument("--only", choices=["maxcut64", "maxcut5000", "completion2000", "tc_gemm", "completion2000_solve",
+                                       "batch256"],
                     help="measure only this other workload (one JSON object; no headline line)")
     ap.add_argument("--reps", type=int, default=2, help="timed Newton solves per row of the other workloads")
     ap.add_argument("--tc-n", type=int, default=5000, help="order of the tensor-core product row (--only tc_gemm)")

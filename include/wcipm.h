@@ -212,6 +212,16 @@ sdp_status ipm_step(sdp_handle* h, const double* b, const double* C, double* X, 
 sdp_status sdp_solve(sdp_handle* h, const double* b, const double* C, double* X, double* y, double* S,
                      double gap_tol, int32_t max_iter, sdp_ipm_info* info);
 
+/* The NT scaling point of an iterate (eq. newt), as the Newton solve and the adjoint take it:
+ * W = L (L^T S L)^{-1/2} L^T with X = L L^T, computed as G G^T with G = L U Gamma^{-1/4}
+ * (L^T S L = U Gamma U^T), and its eigen-decomposition W = V diag(lam) V^T (Jacobi, FP64; both
+ * eigen-decompositions start from the handle's previous ones, e.g. those of the last
+ * interior-point iteration, when there are any).  X, S: n x n positive definite (device);
+ * V: out n x n, lam: out n (device, any order).  The interior-point workspace is allocated on
+ * first use.  SDP_ENUMERIC when X is not positive definite or L^T S L is singular.  With
+ * sdp_grad this gives the derivative of the optimum at the final iterate of sdp_solve. */
+sdp_status sdp_scaling_point(sdp_handle* h, const double* X, const double* S, double* V, double* lam);
+
 /* Many independent solves at once (batched SDPs of uneven size): sdp_solve of instance i on
  * hs[i] with (b[i], C[i]) into (X[i], y[i], S[i]), for i < count.  `workers` host threads
  * (<= 0: min(count, 16)) take the instances largest first; each solve runs on its own

@@ -234,6 +234,17 @@ class NewtonSolver:
         info["status"] = st
         return X, y, S, info
 
+    def scaling_point(self, X, S):
+        """Eigen-decomposition (V, lam) of the NT scaling point of (X, S) (sdp_scaling_point), the
+        input that solve() and grad() take."""
+        torch = self.torch
+        X = X.to(device=self.device, dtype=torch.float64).contiguous()
+        S = S.to(device=self.device, dtype=torch.float64).contiguous()
+        Vbuf = torch.empty((self.n, self.n), dtype=torch.float64, device=self.device)
+        lam = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        native.sdp_scaling_point(self.handle, _ptr(X), _ptr(S), _ptr(Vbuf), _ptr(lam))
+        return Vbuf.t(), lam          # column-major storage: V[i, j] = Vbuf[j, i]
+
     def close(self):
         if getattr(self, "handle", None):
             native.sdp_destroy(self.handle)

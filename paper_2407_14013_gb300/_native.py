@@ -69,6 +69,7 @@ EXPORTS = {
                            POINTER(c_int32)]),
     "ipm_step": (c_int32, [c_void_p] + [c_void_p] * 5 + [POINTER(sdp_ipm_info)]),
     "sdp_solve": (c_int32, [c_void_p] + [c_void_p] * 5 + [c_double, c_int32, POINTER(sdp_ipm_info)]),
+    "sdp_scaling_point": (c_int32, [c_void_p] * 5),
     "sdp_solve_batch": (c_int32, [c_int32] + [c_void_p] * 6 + [c_double, c_int32, c_int32, c_void_p, c_void_p]),
     "sdp_gemm_f64_tc_work_bytes": (c_size_t, [c_int32, c_int32, c_int32]),
     "sdp_gemm_f64_tc": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_double, c_void_p, c_int64,
@@ -183,6 +184,13 @@ def sdp_solve(h: int, b: int, C: int, X: int, y: int, S: int, gap_tol: float, ma
     if st != SDP_OK and not (allow_notconv and st == SDP_ENOTCONV):
         raise SdpError(st, lib.sdp_last_error(c_void_p(h)).decode())
     return st
+
+
+def sdp_scaling_point(h: int, X: int, S: int, V: int, lam: int) -> None:
+    lib = load()
+    st = lib.sdp_scaling_point(c_void_p(h), c_void_p(X), c_void_p(S), c_void_p(V), c_void_p(lam))
+    if st != SDP_OK:
+        raise SdpError(st, lib.sdp_last_error(c_void_p(h)).decode())
 
 
 def sdp_solve_batch(handles, b, C, X, y, S, gap_tol: float, max_iter: int, workers: int = 0):

@@ -43,8 +43,8 @@ struct IpmWork {
   double *L = nullptr, *Linv = nullptr, *T = nullptr, *U = nullptr, *G = nullptr, *Ginv = nullptr, *Wm = nullptr;
   double *V = nullptr, *Rd = nullptr, *Ct = nullptr, *Y = nullptr, *dX = nullptr, *dS = nullptr, *dSs = nullptr;
   double *dXa = nullptr, *dSa = nullptr, *Dx = nullptr, *Ds = nullptr, *R = nullptr, *M1 = nullptr, *M2 = nullptr;
-  double *Eg = nullptr, *EV = nullptr, *Vprev = nullptr;
-  bool have_prev = false;   // Vprev holds the eigenvectors of the previous iteration's W
+  double *Eg = nullptr, *EV = nullptr, *Vprev = nullptr, *Uprev = nullptr;
+  bool have_prev = false;   // Vprev, Uprev hold the eigenvectors of the previous W and L^T S L
   double *lam = nullptr, *gam = nullptr, *g = nullptr, *q = nullptr, *qi = nullptr, *elam = nullptr;
   double *rp = nullptr, *dy = nullptr, *dya = nullptr, *Ax = nullptr, *rownrm = nullptr;
   double *zsvec = nullptr, *partY = nullptr, *partA = nullptr;
@@ -357,7 +357,7 @@ sdp_status ensure_workspace(sdp_handle* h) {
       {&w->L, nn}, {&w->Linv, nn}, {&w->T, nn}, {&w->U, nn}, {&w->G, nn}, {&w->Ginv, nn}, {&w->Wm, nn},
       {&w->V, nn}, {&w->Rd, nn}, {&w->Ct, nn}, {&w->Y, nn}, {&w->dX, nn}, {&w->dS, nn}, {&w->dSs, nn},
       {&w->dXa, nn}, {&w->dSa, nn}, {&w->Dx, nn}, {&w->Ds, nn}, {&w->R, nn}, {&w->M1, nn}, {&w->M2, nn},
-      {&w->Eg, nn}, {&w->EV, nn}, {&w->Vprev, nn}, {&w->lam, (size_t)n}, {&w->gam, (size_t)n}, {&w->g, (size_t)n},
+      {&w->Eg, nn}, {&w->EV, nn}, {&w->Vprev, nn}, {&w->Uprev, nn}, {&w->lam, (size_t)n}, {&w->gam, (size_t)n}, {&w->g, (size_t)n},
       {&w->q, (size_t)n}, {&w->qi, (size_t)n}, {&w->elam, (size_t)n}, {&w->rp, (size_t)m}, {&w->dy, (size_t)m},
       {&w->dya, (size_t)m}, {&w->Ax, (size_t)m}, {&w->rownrm, (size_t)m}, {&w->eigw, w->eigw_elems},
       {&w->chw, w->chw_elems}, {&w->lzw, w->lzw_elems}, {&w->dots, (size_t)kDots}, {&w->dpart, (size_t)kDots * kDotBlocks}};
@@ -439,14 +439,15 @@ void fill_info(sdp_ipm_info* info, const Measures& M) {
 
 // one predictor-corrector step from (X, y, S) whose residuals w->Rd, w->rp and measures M
 // are current
-sdp_status step(Ctx& c, double* X, double* y, double* S, const Measures& Mz, sdp_ipm_info* info) {
+// NT scaling of (X, S) (Section 3, eq. newt): X = L L^T, L^T S L = U Gamma U^T,
+// G = L U Gamma^{-1/4}, W = G G^T, and eig(W) = (V, lam).  Both eigen-decompositions start from
+// the previous call's eigenvectors when there are any (the iterates move little along the path).
+sdp_status scaling(Ctx& c, const double* X, const double* S, int* sweeps) {
   sdp_handle* h = c.h;
   IpmWork* w = c.w;
   const int n = c.n;
   const int64_t nn = (int64_t)n * n;
   const size_t bytes = (size_t)nn * sizeof(double);
-  const double mu = Mz.mu;
-  int sweeps = 0;
   double off = 0.0;
   // ---- NT scaling: X = L L^T, L^T S L = U Gamma U^T, G = L U Gamma^{-1/4}, W = G G^T
   CUI(cudaMemsetAsync(w->status, 0, sizeof(int32_t), c.st));
@@ -455,8 +456,18 @@ sdp_status step(Ctx& c, double* X, double* y, double* S, const Measures& Mz, sdp
   CUI(gemm(c, false, false, S, w->L, w->M1));
   CUI(gemm(c, true, false, w->L, w->M1, w->T));
   int sw = 0;
+  // eig(L^T S L), started like eig(W) below from the previous iteration's eigenvectors
+  if (w->have_prev) {
+    CUI(gemm(c, false, false, w->T, w->Uprev, w->M1));
+    CUI(gemm(c, true, false, w->Uprev, w->M1, w->T));
+  }
   CUI(eigh_jacobi(c.st, n, w->T, w->U, w->gam, 1e-14, 40, w->eigw, w->eigw_elems, &sw, &off, c.L, &w->eg[0], !h->no_coop));
-  sweeps += sw;
+  *sweeps += sw;
+  if (w->have_prev) {
+    CUI(gemm(c, false, false, w->Uprev, w->U, w->M1));
+    CUI(cudaMemcpyAsync(w->U, w->M1, bytes, cudaMemcpyDeviceToDevice, c.st));
+  }
+  CUI(cudaMemcpyAsync(w->Uprev, w->U, bytes, cudaMemcpyDeviceToDevice, c.st));
   gamma_kernel<<<nb(n), IT, 0, c.st>>>(n, w->gam, w->g, w->q, w->qi, w->status);
   ++*c.L;
   CUI(gemm(c, false, false, w->L, w->U, w->M1));
@@ -474,7 +485,7 @@ sdp_status step(Ctx& c, double* X, double* y, double* S, const Measures& Mz, sdp
     CUI(cudaMemcpyAsync(w->Eg, w->Wm, bytes, cudaMemcpyDeviceToDevice, c.st));
   }
   CUI(eigh_jacobi(c.st, n, w->Eg, w->EV, w->lam, 1e-14, 40, w->eigw, w->eigw_elems, &sw, &off, c.L, &w->eg[1], !h->no_coop));
-  sweeps += sw;
+  *sweeps += sw;
   if (w->have_prev) CUI(gemm(c, false, false, w->Vprev, w->EV, w->V));
   else CUI(cudaMemcpyAsync(w->V, w->EV, bytes, cudaMemcpyDeviceToDevice, c.st));
   CUI(cudaMemcpyAsync(w->Vprev, w->V, bytes, cudaMemcpyDeviceToDevice, c.st));
@@ -483,6 +494,20 @@ sdp_status step(Ctx& c, double* X, double* y, double* S, const Measures& Mz, sdp
   CUI(cudaMemcpyAsync(&st_h, w->status, sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
   CUI(cudaStreamSynchronize(c.st));
   if (st_h != 0) return wc_fail(h, SDP_ENUMERIC, "X is not positive definite or L^T S L is singular");
+  return SDP_OK;
+}
+
+sdp_status step(Ctx& c, double* X, double* y, double* S, const Measures& Mz, sdp_ipm_info* info) {
+  sdp_handle* h = c.h;
+  IpmWork* w = c.w;
+  const int n = c.n;
+  const int64_t nn = (int64_t)n * n;
+  const size_t bytes = (size_t)nn * sizeof(double);
+  const double mu = Mz.mu;
+  int sweeps = 0;
+  double off = 0.0;
+  sdp_status s0 = scaling(c, X, S, &sweeps);
+  if (s0 != SDP_OK) return s0;
 
   // ---- predictor: C~ = R_d + S, b~ = r_p
   lincomb_kernel<<<nb(nn), IT, 0, c.st>>>(nn, 1.0, w->Rd, 1.0, S, 0.0, nullptr, w->Ct);
@@ -659,6 +684,25 @@ extern "C" sdp_status sdp_solve(sdp_handle* h, const double* b, const double* C,
   loc.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = loc;
   return loc.converged ? SDP_OK : SDP_ENOTCONV;
+}
+
+extern "C" sdp_status sdp_scaling_point(sdp_handle* h, const double* X, const double* S, double* V, double* lam) {
+  if (!h) return wc_fail(nullptr, SDP_EINVAL, "NULL handle");
+  if (!X || !S || !V || !lam) return wc_fail(h, SDP_EINVAL, "NULL array argument");
+  sdp_status s = ensure_workspace(h);
+  if (s != SDP_OK) return s;
+  int64_t L = 0;
+  IpmWork* w = h->ipm;
+  Ctx c{h, w, h->n, h->m, h->st, &L};
+  int sweeps = 0;
+  s = scaling(c, X, S, &sweeps);
+  if (s != SDP_OK) return s;
+  const size_t nn = (size_t)h->n * h->n;
+  if (cudaMemcpyAsync(V, w->V, nn * sizeof(double), cudaMemcpyDeviceToDevice, h->st) != cudaSuccess ||
+      cudaMemcpyAsync(lam, w->lam, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st) != cudaSuccess ||
+      cudaStreamSynchronize(h->st) != cudaSuccess)
+    return wc_fail(h, SDP_ECUDA, "copying the scaling point failed");
+  return SDP_OK;
 }
 
 extern "C" sdp_status sdp_solve_batch(int32_t count, sdp_handle* const* hs, const double* const* b,

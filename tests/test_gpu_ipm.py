@@ -103,3 +103,31 @@ def test_sdp_solve_matches_oracle(name, mk, rh):
         m_edges = len(prob.meta["edges"])
         assert abs(pobj + m_edges) <= 1e-7 * m_edges        # value -|E| (connected bipartite, unit weights)
     s.close()
+
+
+def test_scaling_point_and_adjoint_at_the_final_iterate():
+    """sdp_scaling_point gives the eigen-decomposition of the NT scaling of an iterate (compared
+    with the oracle's NT scaling); the whole GPU chain sdp_solve -> sdp_scaling_point -> sdp_grad
+    satisfies the envelope theorem at the final (uncentred, gap 1e-8) iterate: with
+    (gX, gy) = (C, 0), gb = y* and with (0, b), gC = X*, to the O(mu)-type error of the
+    linearisation there (1e-5 on the oracle for this instance; bound 1e-4)."""
+    from paper_2407_14013_gb300 import NewtonSolver
+    from oracle import newton as onewton
+    prob = W.maxcut(40, 0.15, 2719)
+    ref = oipm.ipm_solve(prob, tol=1e-8, max_iter=200)
+    # a centred iterate at mu = 1e-4: both NT-scaling routes are accurate there (near the end of
+    # the path L^T S L is nearly singular and the two routes agree only to ~cond(W) eps)
+    st = oipm.center(prob, oipm.IPMState(ref.X, ref.y, ref.S), 1e-4)
+    s = NewtonSolver(prob, r_hat=8)
+    V, lam = s.scaling_point(_t(st.X), _t(st.S))
+    Vh, lh = V.cpu().numpy(), lam.cpu().numpy()
+    assert np.max(np.abs(Vh.T @ Vh - np.eye(prob.n))) < 1e-12
+    assert rel((Vh * lh) @ Vh.T, onewton.nt_scaling(st.X, st.S)) < 1e-9
+    X, y, S, info = s.solve_sdp(_t(prob.b), _t(prob.C), gap_tol=1e-8, max_iter=100)
+    assert info["converged"] == 1
+    V, lam = s.scaling_point(X, S)
+    gC, gb = s.grad(V, lam, _t(prob.C), _t(np.zeros(prob.m)))
+    assert rel(gb.cpu().numpy(), y.cpu().numpy()) < 1e-4
+    gC, gb = s.grad(V, lam, _t(np.zeros((prob.n, prob.n))), _t(prob.b))
+    assert rel(gC.cpu().numpy(), X.cpu().numpy()) < 1e-4
+    s.close()
