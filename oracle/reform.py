@@ -21,6 +21,10 @@ Each function follows one passage of the paper, in the paper's notation:
                       standard PCG coefficient that the proof of Prop. indefpcg uses).
 * ``newton_reform`` -- Cor. pcg end to end: v0 = -Sigma^{-1} Q^T c, PCG on augsys,
                       recovery.
+* ``minres``       -- Def. MINRES with P = I: x_k = argmin ||A x - b|| over
+                      x0 + span{r0, A r0, ..., A^{k-1} r0}, written out as the definition
+                      (an orthonormal basis of the Krylov space, then a least-squares solve).
+* ``newton_minres`` -- Cor. minres end to end: MINRES_k(augsys, g, I, 0), recovery.
 
 Readings taken where the paper is garbled or silent: the sqrt(2) placement of Section 5; the beta^{-1}
 factors of the block inverse in Section 6; the PCG beta index of Def. pcg;
@@ -354,6 +358,86 @@ def newton_reform(prob, V: np.ndarray, lam: np.ndarray, Ct: np.ndarray, bt: np.n
     res = pcg(Aop, g, Pinv, x0, tol, maxit, keep_iterates=keep_iterates)
     dX, dy, dS = recover(prob, sp, Ct, res.x[:m], res.x[m:])
     return dX, dy, dS, ReformInfo(split=sp, precond=P, pcg=res, g=g)
+
+
+# ----------------------------------------------------------------------------
+# MINRES (Def. MINRES with P = I) and Cor. minres
+
+
+@dataclass
+class MinresResult:
+    x: np.ndarray
+    iters: int
+    res_hist: list
+    converged: bool
+
+
+def minres(Aop, b: np.ndarray, x0: np.ndarray, tol: float, maxit: int) -> MinresResult:
+    """MINRES_k(A, b, I, x0) by its definition: x_k minimises ||A x - b|| over
+    x0 + span{r0, A r0, ..., A^{k-1} r0}, r0 = b - A x0.
+
+    The Krylov space is kept as an orthonormal basis Z (each new direction A z_k
+    orthogonalised twice against all previous ones), and x_k = x0 + Z c with
+    c = argmin ||(A Z) c - r0|| by a least-squares solve.  Plain and slow (O(k^2 n) work and
+    O(k n) memory); stops when ||A x_k - b|| <= tol or k = maxit, or when the Krylov space
+    stops growing (then x_k is the exact minimiser over the whole space)."""
+    x0 = np.asarray(x0, dtype=float)
+    r0 = b - Aop(x0)
+    n0 = float(np.linalg.norm(r0))
+    hist = [n0]
+    if n0 <= tol:
+        return MinresResult(x=x0.copy(), iters=0, res_hist=hist, converged=True)
+    Z = [r0 / n0]
+    AZ = [Aop(Z[0])]
+    x = x0.copy()
+    k = 0
+    while k < maxit:
+        k += 1
+        Zm, AZm = np.stack(Z, axis=1), np.stack(AZ, axis=1)
+        c = np.linalg.lstsq(AZm, r0, rcond=None)[0]
+        x = x0 + Zm @ c
+        res = float(np.linalg.norm(b - Aop(x)))
+        hist.append(res)
+        if res <= tol:
+            return MinresResult(x=x, iters=k, res_hist=hist, converged=True)
+        z = AZ[-1].copy()                                  # next Krylov direction A z_k
+        for _ in range(2):
+            z -= Zm @ (Zm.T @ z)
+        nz = float(np.linalg.norm(z))
+        if nz <= 1e-14 * float(np.linalg.norm(AZ[-1])):   # invariant space: x is final
+            return MinresResult(x=x, iters=k, res_hist=hist, converged=res <= tol)
+        Z.append(z / nz)
+        AZ.append(Aop(Z[-1]))
+    return MinresResult(x=x, iters=k, res_hist=hist, converged=False)
+
+
+def newton_minres(prob, V: np.ndarray, lam: np.ndarray, Ct: np.ndarray, bt: np.ndarray,
+                  r: int | None = None, r_hat: int | None = None, s_A: float = 1.0,
+                  rtol: float = 1e-12, maxit: int = 2000):
+    """Solve (Newt-eps) as Cor. minres states: [u; v] = MINRES_k(augsys, g, I, 0), then
+    eq. recover; the stop test is the one of newton_reform (||r_k|| <= rtol ||[svec C~; b~]||)."""
+    sp = split(V, lam, r=r, r_hat=r_hat, s_A=s_A)
+    m = prob.m
+    gu, gv = aug_rhs(prob, sp, Ct, bt)
+    g = np.concatenate([gu, gv])
+
+    def Aop(x):
+        a, b_ = aug_apply(prob, sp, x[:m], x[m:])
+        return np.concatenate([a, b_])
+
+    tol = rtol * math.sqrt(float(np.sum(Ct * Ct)) + float(bt @ bt))
+    res = minres(Aop, g, np.zeros_like(g), tol, maxit)
+    dX, dy, dS = recover(prob, sp, Ct, res.x[:m], res.x[m:])
+    return dX, dy, dS, res, sp
+
+
+def prop_minres_bound(kappa: float, r0norm: float, eps: float) -> int:
+    """Iteration bound of Prop. minres for symmetric indefinite A: ceil(kappa log(2 ||A x0 - b|| / eps)).
+
+    Prop. minres prints kappa/2 in front of the logarithm; for an indefinite spectrum the
+    residual contracts by (kappa - 1)/(kappa + 1) only every two steps, which gives kappa
+    (the printed factor holds for a definite A)."""
+    return int(math.ceil(kappa * math.log(2.0 * r0norm / eps)))
 
 
 def cor_pcg_bound(kappa_E: float, kappa_A: float, gnorm: float, eps: float) -> int:
