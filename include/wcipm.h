@@ -128,6 +128,14 @@ typedef struct {
                             B D^{-1} B^T) run on the BF16 tensor cores by exact slices (see
                             sdp_gemm_f64_tc; FP64 accuracy); 0: every product on the FP64 MMA
                             path.  The Cholesky and inverse of the complement stay FP64 MMA.     */
+  int32_t krylov;        /* 0 (default): indefinite PCG with the Section 6 preconditioner
+                            (Cor. pcg); 1: MINRES on eq. augsys with P = I from x0 = 0
+                            (Cor. minres): no B = A Q and no Schur complement are formed, so the
+                            workspace is O(n^2 + m + d) (the fallback when neither C nor K
+                            fits), at the price of many more iterations (the condition number
+                            of eq. augsys, not of the preconditioned operator); max_pcg bounds
+                            its iterations and the stop test is the PCG one.  FP64 only
+                            (SDP_MIXED_FP32 with krylov = 1: SDP_EUNSUPPORTED).               */
 } sdp_options;
 
 typedef struct {
@@ -242,7 +250,7 @@ sdp_status sdp_solve_batch(int32_t count, sdp_handle* const* hs, const double* c
 
 /* Fill *opt with the defaults: r_fixed 0, r_hat 10, FP64, auto space,
  * max_pcg 2000, check_every 8, beta_rule 0, use_graph 1, newton_rtol 1e-12, max_refine 10,
- * max_inner 500, inner_rtol 1e-6, pcg_start 0, tc_products 1. */
+ * max_inner 500, inner_rtol 1e-6, pcg_start 0, tc_products 1, krylov 0. */
 void sdp_default_options(sdp_options* opt);
 
 /* Validate the problem, record its (device) pointers -- the caller keeps

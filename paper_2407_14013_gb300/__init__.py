@@ -74,7 +74,7 @@ class NewtonSolver:
                  max_pcg: int = 2000, check_every: int = 8, beta_rule: int = 0,
                  newton_rtol: float = 1e-12, device: str = "cuda", stream=None, use_graph: bool = True,
                  precision: str = "fp64", max_refine: int = 10, max_inner: int = 500, inner_rtol: float = 1e-6,
-                 pcg_start: int = 0, tc_products: bool = True):
+                 pcg_start: int = 0, tc_products: bool = True, krylov: str = "pcg"):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -112,6 +112,7 @@ class NewtonSolver:
         o.max_refine, o.max_inner, o.inner_rtol = max_refine, max_inner, inner_rtol
         o.pcg_start = pcg_start
         o.tc_products = 1 if tc_products else 0
+        o.krylov = {"pcg": 0, "minres": 1}[krylov]
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         torch.cuda.synchronize(self.device)
         self.handle = native.sdp_setup(p, o, int(self.stream.cuda_stream))

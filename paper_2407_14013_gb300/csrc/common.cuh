@@ -93,6 +93,17 @@ __device__ __forceinline__ double pack_at(const T* __restrict__ H, int64_t ldH, 
 }
 
 // Device-resident PCG control block (one per handle).
+// Scalars of the MINRES recurrence (Paige-Saunders form of Def. MINRES with P = I).
+struct MinresCtl {
+  double beta, oldb, alfa;       // Lanczos: beta_k, beta_{k-1}, alpha_k
+  double dbar, epsln, oldeps;    // entries of the rotated tridiagonal
+  double delta, gamma;
+  double cs, sn;                 // the last Givens rotation
+  double phi, phibar;            // phibar = ||r_k|| in exact arithmetic
+  int32_t itn;                   // iterations begun
+  int32_t stop;                  // 1 once the stop test held: the next iteration raises done
+};
+
 struct PcgCtl {
   double rz;        // <r_k, z_k>
   double rz_new;    // <r_{k+1}, z_{k+1}>

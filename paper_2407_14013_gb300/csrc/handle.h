@@ -21,6 +21,7 @@ struct Space {
   double *zsvec = nullptr, *partY = nullptr, *partA = nullptr, *sd = nullptr, *wm = nullptr;
   double *partB = nullptr, *partBt = nullptr, *partC = nullptr;
   double *ypos = nullptr, *zpos = nullptr;     // SPARSE_COO: A^T(y) and E Y E at the pattern positions
+  double *mw = nullptr, *mw1 = nullptr, *mw2 = nullptr;   // MINRES search directions
   double *x = nullptr, *rv = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr;
   double* ws = nullptr;                        // split-K GEMM scratch
   size_t ws_elems = 0;
@@ -84,6 +85,7 @@ struct sdp_handle {
   double *ubatch = nullptr, *Gb = nullptr, *Hb = nullptr;
   int pinv_dim = 0;                 // order of the largest preconditioner core the options allow
   int dev = 0;                      // device of the handle (current at setup)
+  wc::MinresCtl* mctl = nullptr;    // MINRES scalars (device)
   char* tcw = nullptr;              // slices of the tensor-core FP64 products (NULL: not used)
   size_t tcw_bytes = 0;
   char* tcw_b = nullptr;            // the same for the n x r products on the first side stream
@@ -122,7 +124,7 @@ struct sdp_handle {
   cudaEvent_t br_ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double *ws_b[2] = {nullptr, nullptr};   // split-K scratch of the GEMMs on the side streams
   size_t ws_b_elems = 0;
-  wc::Graph graph[2];
+  wc::Graph graph[3];              // PCG FP64, PCG of the mixed corrections, MINRES
   // the split and preconditioner core of the last solve can serve another right side
   bool setup_valid = false;
   wc::PcgCtl setup_ctl{};           // the control block as a2 left it (r, d, tau, beta, s_A)

@@ -72,6 +72,7 @@ extern "C" void sdp_default_options(sdp_options* o) {
   o->inner_rtol = 1e-6;
   o->pcg_start = 0;
   o->tc_products = 1;
+  o->krylov = 0;
 }
 
 namespace {
@@ -116,6 +117,11 @@ void carve_space(sdp_handle* h, Carver& c, Space& S) {
   if (h->kind == SDP_A_SPARSE_COO) {
     S.ypos = c.take<double>(h->sp.npos);
     S.zpos = c.take<double>(h->sp.npos);
+  }
+  if (h->opt.krylov == 1) {
+    S.mw = c.take<double>(vt);
+    S.mw1 = c.take<double>(vt);
+    S.mw2 = c.take<double>(vt);
   }
   size_t pa = std::max(rows_gemv_part_elems(m, dm), rows_gemv_part_elems(pc, pc));
   if (h->kind == SDP_A_DENSE_SVEC) pa = std::max(pa, rows_gemv_part_elems(m, h->N));
@@ -164,6 +170,7 @@ size_t carve(sdp_handle* h, char* base) {
   const size_t vt = m + dm;
   h->ctl = c.take<PcgCtl>(1);
   h->ctl_in = c.take<PcgCtl>(1);
+  h->mctl = c.take<MinresCtl>(1);
   h->counter = c.take<unsigned int>(4);
   // one ticket per column block of the A^T pass (at most one block per 256 columns)
   h->gt_tickets = c.take<unsigned int>(h->kind == SDP_A_DENSE_SVEC ? (size_t)(h->N + 255) / 256 + 1 : 1);
@@ -257,6 +264,9 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   if (opt.precond_space < 0 || opt.precond_space > 2) return fail(nullptr, SDP_EINVAL, "bad precond_space");
   if (opt.pcg_start < 0 || opt.pcg_start > 1) return fail(nullptr, SDP_EINVAL, "bad pcg_start");
   if (opt.tc_products < 0 || opt.tc_products > 1) return fail(nullptr, SDP_EINVAL, "bad tc_products");
+  if (opt.krylov < 0 || opt.krylov > 1) return fail(nullptr, SDP_EINVAL, "bad krylov");
+  if (opt.krylov == 1 && opt.precision != SDP_FP64)
+    return fail(nullptr, SDP_EUNSUPPORTED, "MINRES is built for the FP64 form only");
 
   // SPARSE_COO: validate the entries and build the index tables on the host (once per problem)
   std::vector<int32_t> sp_con_ptr, sp_pos_r, sp_pos_c, sp_pos_ptr, sp_perm, sp_epos, sp_yptr, sp_ycol, sp_ypidx,
@@ -351,6 +361,7 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   h->d_max = dof(n, r_max);
   // d-space core (d x d) when d <= m, m-space core (m x m) otherwise, unless forced
   h->pinv_dim = opt.precond_space == 1 ? h->d_max : opt.precond_space == 2 ? m : std::min(h->d_max, m);
+  if (opt.krylov == 1) h->pinv_dim = 0;   // MINRES: no preconditioner core
   // explicit B = A Q: DIAG forms its m-space core in closed form and its products with B from
   // Vs, so it needs B only for the d-space core (auto selects that only at r = 1, d = n)
   // SPARSE_COO reads B only to form the core (its products with B go through the pattern);
@@ -365,6 +376,7 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
     h->bt_elems = (h->kind == SDP_A_SPARSE_COO && !h->mixed) ? 0 : h->b_elems;
     h->bs_elems = m_space_possible ? (int64_t)m * h->d_max : 0;
   }
+  if (opt.krylov == 1) h->b_elems = h->bt_elems = h->bs_elems = 0;   // MINRES: no B = A Q
   int dev = 0;
   cudaGetDevice(&dev);
   h->dev = dev;
@@ -758,10 +770,10 @@ sdp_status pcg_start(sdp_handle* h, Space& S, bool mixed, const double* gsub, do
 // PCG iterations until the device stop flag is set.  `check_every` iterations run as one
 // replay of a captured CUDA graph (every kernel returns at once after the stop), with one
 // host read of the control block between replays.
-sdp_status pcg_loop(sdp_handle* h, Space& S, bool mixed) {
+sdp_status krylov_loop(sdp_handle* h, Space& S, bool mixed, bool minres) {
   const int every = h->opt.check_every;
   const int nt = h->m + h->d;
-  Graph& G = h->graph[mixed ? 1 : 0];
+  Graph& G = h->graph[minres ? 2 : mixed ? 1 : 0];
   int64_t* L = &h->launches;
   cudaStream_t st = h->st;
   CU(cudaMemcpyAsync(h->ctl_host, S.ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
@@ -777,6 +789,16 @@ sdp_status pcg_loop(sdp_handle* h, Space& S, bool mixed) {
     h->st = s_;
     for (int k = 0; k < every; ++k) {
       h->cur_iter = k;
+      if (minres) {
+        // v = r2 / beta; y = M v; alfa; beta, rotation, stop; w and x (r1 = rv, r2 = z, v = p, y = Ap)
+        launch_minres_v(s_, nt, S.z, S.p, h->mctl, S.ctl, L);
+        sdp_status s = apply_operator(h, S, S.p, S.Ap, nullptr, 0);
+        if (s != SDP_OK) { h->st = saved; return s; }
+        launch_minres_alfa(s_, nt, S.p, S.Ap, S.rv, h->mctl, S.ctl, h->dotbuf, h->counter, L);
+        launch_minres_beta(s_, nt, S.Ap, S.rv, S.z, h->mctl, S.ctl, h->dotbuf, h->counter, L);
+        launch_minres_update(s_, nt, S.p, S.mw, S.mw1, S.mw2, S.x, h->mctl, S.ctl, L);
+        continue;
+      }
       sdp_status s = apply_op(h, S, mixed, S.p, S.Ap, nullptr, 1);
       if (s != SDP_OK) { h->st = saved; return s; }
       launch_update<double>(s_, nt, S.x, S.rv, S.p, S.Ap, S.ctl, h->dotbuf, h->counter, L);
@@ -902,8 +924,10 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   lower_to_full(st, n, S.E, L);
   split_sigma(st, n, r, h->lam_s, h->ctl, S.Dv, L);
 
-  // ---- a2: B = A Q and the preconditioner core ----
-  if (h->kind == SDP_A_DENSE_SVEC) {
+  // ---- a2: B = A Q and the preconditioner core (MINRES: only E o E of the DIAG operator) ----
+  if (h->opt.krylov == 1) {
+    if (h->kind == SDP_A_DIAG) launch_hadamard_sq(st, (int64_t)n * n, S.E, S.EE, L);
+  } else if (h->kind == SDP_A_DENSE_SVEC) {
     // row i of B is Q^T svec(A_i) = pack(Vs^T A_i Q): G = [A_i Q] straight from the svec rows,
     // then one GEMM H = Vs^T G for a whole batch of constraints
     bool direct = true;
@@ -936,8 +960,11 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   }
   int32_t* pstatus = &h->ctl->status;
   const int pd = (h->space == 1) ? d : m;
-  if (pd > h->pinv_dim) return fail(h, SDP_EINVAL, "preconditioner core larger than the setup allows");
-  if (h->kind == SDP_A_DIAG && h->space == 2) {
+  if (h->opt.krylov == 1) {
+    // MINRES (Cor. minres): no preconditioner core
+  } else if (pd > h->pinv_dim) {
+    return fail(h, SDP_EINVAL, "preconditioner core larger than the setup allows");
+  } else if (h->kind == SDP_A_DIAG && h->space == 2) {
     // K = beta I + tau^-2 G o (G + 2 tau E) with G = Q (Lam - tau I) Q^T (lower triangle)
     launch_shift_cols(st, n, r, S.Vs, h->lam_s, h->ctl, S.Tm, L);
     CU(gemm_big(h, st, false, true, n, n, r, 1.0, S.Tm, n, S.Vs, n, 0.0, S.F, n, S.ws, ws, L, GEMM_LOWER));
@@ -990,7 +1017,12 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
                       h->ctl, h->dotbuf, h->counter, L);
   }
 
-  if (!h->mixed) {
+  if (h->opt.krylov == 1) {
+    // ---- Cor. minres: MINRES_k(augsys, g, I, 0) ----
+    launch_minres_init(st, nt, h->g, S.rv, S.z, S.x, S.mw, S.mw2, h->mctl, h->ctl, h->dotbuf, h->counter, L);
+    sdp_status s = krylov_loop(h, S, false, true);
+    if (s != SDP_OK) return s;
+  } else if (!h->mixed) {
     // ---- a4-a6: FP64 PCG from x0 ----
     if (h->opt.pcg_start == 0) {   // x0 = P^{-1}[0; g_v]: P x0 = [0; g_v], so r0_v = 0 with r0_u ~ g
       launch_correction_rhs(st, m, d, h->g, S.z, L);
@@ -999,7 +1031,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     }
     sdp_status s = pcg_start(h, S, false, h->g, 0.0);
     if (s != SDP_OK) return s;
-    s = pcg_loop(h, S, false);
+    s = krylov_loop(h, S, false, false);
     if (s != SDP_OK) return s;
   } else {
     // ---- a7: FP64 refinement around solves with the mixed operator ----
@@ -1032,7 +1064,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
       if (s != SDP_OK) return s;
       s = pcg_start(h, Si, true, S.rv, h->opt.inner_rtol * h->opt.inner_rtol);
       if (s != SDP_OK) return s;
-      s = pcg_loop(h, Si, true);
+      s = krylov_loop(h, Si, true, false);
       if (s != SDP_OK) return s;
       h->inner_iters += h->ctl_host->iters;
       if (h->ctl_host->status == 5) {   // breakdown of the correction solve: its correction is dropped
@@ -1047,7 +1079,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
       // the FP64 PCG continues from the refined iterate
       sdp_status s = pcg_start(h, S, false, h->g, 0.0);
       if (s != SDP_OK) return s;
-      s = pcg_loop(h, S, false);
+      s = krylov_loop(h, S, false, false);
       if (s != SDP_OK) return s;
       h->inner_iters += h->ctl_host->iters;
     }
@@ -1188,6 +1220,8 @@ extern "C" sdp_status sdp_debug_copy(sdp_handle* h, int32_t which, double* dst, 
   const Space& S = h->s64;
   const double* src = nullptr;
   int64_t avail = 0;
+  if (h->opt.krylov == 1 && (which == 2 || which == 3))
+    return fail(h, SDP_EINVAL, "MINRES forms neither B nor the preconditioner core");
   switch (which) {
     case 0: src = S.E; avail = n * n; break;
     case 1: src = S.Dv; avail = d; break;

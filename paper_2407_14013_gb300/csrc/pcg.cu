@@ -269,6 +269,164 @@ __global__ void diag_K_kernel(int n, const double* __restrict__ G, const double*
   K[q] = v;
 }
 
+// ---- MINRES (Def. MINRES with P = I; the recurrence of Paige and Saunders) ----------------
+// r1, r2: the last two Lanczos residuals (r2 = beta v_{k+1}); v: the Lanczos vector; y = M v;
+// w, w1, w2: the search directions; x: the iterate.  Scalars in MinresCtl, the stop test and
+// the iteration count in PcgCtl (rr = phibar^2 against tol2).
+
+// start: r1 = r2 = g, x = w = w2 = 0; beta = ||g|| (last block), phibar = beta, cs = -1
+__global__ void __launch_bounds__(VT)
+minres_init_kernel(int nt, const double* __restrict__ g, double* __restrict__ r1, double* __restrict__ r2,
+                   double* __restrict__ x, double* __restrict__ w, double* __restrict__ w2,
+                   MinresCtl* __restrict__ mc, PcgCtl* __restrict__ ctl, double* __restrict__ dotbuf,
+                   unsigned int* __restrict__ counter) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nt; q += gridDim.x * blockDim.x) {
+    const double v = g[q];
+    r1[q] = v;
+    r2[q] = v;
+    x[q] = 0.0;
+    w[q] = 0.0;
+    w2[q] = 0.0;
+    acc = fma(v, v, acc);
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) dotbuf[blockIdx.x] = acc;
+  if (last_block(counter)) {
+    const double gg = sum_partials(dotbuf, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      *counter = 0;
+      const double b1 = sqrt(gg);
+      mc->beta = b1;
+      mc->oldb = 0.0;
+      mc->alfa = 0.0;
+      mc->dbar = 0.0;
+      mc->epsln = 0.0;
+      mc->oldeps = 0.0;
+      mc->delta = 0.0;
+      mc->gamma = 1.0;
+      mc->cs = -1.0;
+      mc->sn = 0.0;
+      mc->phi = 0.0;
+      mc->phibar = b1;
+      mc->itn = 0;
+      mc->stop = 0;
+      ctl->rr = gg;
+      ctl->rr0 = gg;
+      ctl->iters = 0;
+      ctl->status = 0;
+      ctl->done = (gg <= ctl->tol2 || !(b1 > 0.0)) ? 1 : 0;
+    }
+  }
+}
+
+// v = r2 / beta; a stop recorded by the previous iteration raises done here (after that
+// iteration's update of x)
+__global__ void minres_v_kernel(int nt, const double* __restrict__ r2, double* __restrict__ v,
+                                MinresCtl* __restrict__ mc, PcgCtl* __restrict__ ctl) {
+  if (ctl->done) return;
+  if (mc->stop) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->done = 1;
+    return;
+  }
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nt) return;
+  v[q] = r2[q] / mc->beta;
+}
+
+// y -= (beta / oldb) r1 (from the second iteration on); alfa = <v, y>
+__global__ void __launch_bounds__(VT)
+minres_alfa_kernel(int nt, const double* __restrict__ v, double* __restrict__ y, const double* __restrict__ r1,
+                   MinresCtl* __restrict__ mc, PcgCtl* __restrict__ ctl, double* __restrict__ dotbuf,
+                   unsigned int* __restrict__ counter) {
+  if (ctl->done || mc->stop) return;
+  __shared__ double sh[32];
+  const double c = (mc->itn >= 1) ? mc->beta / mc->oldb : 0.0;
+  double acc = 0.0;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nt; q += gridDim.x * blockDim.x) {
+    double t = y[q];
+    if (c != 0.0) t = fma(-c, r1[q], t);
+    y[q] = t;
+    acc = fma(v[q], t, acc);
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) dotbuf[blockIdx.x] = acc;
+  if (last_block(counter)) {
+    const double a = sum_partials(dotbuf, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      *counter = 0;
+      mc->alfa = a;
+    }
+  }
+}
+
+// t = y - (alfa / beta) r2; r1 = r2; r2 = t; beta_{k+1} = ||t||; then the Givens rotation that
+// eliminates beta_{k+1} from the tridiagonal, phi, phibar = ||r_k||, and the stop test
+__global__ void __launch_bounds__(VT)
+minres_beta_kernel(int nt, const double* __restrict__ y, double* __restrict__ r1, double* __restrict__ r2,
+                   MinresCtl* __restrict__ mc, PcgCtl* __restrict__ ctl, double* __restrict__ dotbuf,
+                   unsigned int* __restrict__ counter) {
+  if (ctl->done || mc->stop) return;
+  __shared__ double sh[32];
+  const double c = mc->alfa / mc->beta;
+  double acc = 0.0;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nt; q += gridDim.x * blockDim.x) {
+    const double old2 = r2[q];
+    const double t = fma(-c, old2, y[q]);
+    r1[q] = old2;
+    r2[q] = t;
+    acc = fma(t, t, acc);
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) dotbuf[blockIdx.x] = acc;
+  if (last_block(counter)) {
+    const double bb = sum_partials(dotbuf, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      *counter = 0;
+      const double alfa = mc->alfa;
+      mc->oldb = mc->beta;
+      const double beta = sqrt(bb);
+      mc->beta = beta;
+      mc->oldeps = mc->epsln;
+      const double delta = mc->cs * mc->dbar + mc->sn * alfa;
+      const double gbar = mc->sn * mc->dbar - mc->cs * alfa;
+      mc->epsln = mc->sn * beta;
+      mc->dbar = -mc->cs * beta;
+      double gamma = hypot(gbar, beta);
+      if (!(gamma > 0.0)) gamma = 1e-300;
+      mc->delta = delta;
+      mc->gamma = gamma;
+      mc->cs = gbar / gamma;
+      mc->sn = beta / gamma;
+      mc->phi = mc->cs * mc->phibar;
+      mc->phibar = mc->sn * mc->phibar;
+      mc->itn += 1;
+      const double rr = mc->phibar * mc->phibar;
+      ctl->rr = rr;
+      ctl->iters += 1;
+      if (!isfinite(rr) || !isfinite(mc->phi)) { ctl->status = 5; ctl->done = 1; }
+      else if (rr <= ctl->tol2 || beta == 0.0) { ctl->status = 0; mc->stop = 1; }
+      else if (ctl->iters >= ctl->max_iters) { ctl->status = 4; mc->stop = 1; }
+    }
+  }
+}
+
+// w1 = w2; w2 = w; w = (v - oldeps w1 - delta w2) / gamma; x += phi w
+__global__ void minres_update_kernel(int nt, const double* __restrict__ v, double* __restrict__ w,
+                                     double* __restrict__ w1, double* __restrict__ w2, double* __restrict__ x,
+                                     const MinresCtl* __restrict__ mc, const PcgCtl* __restrict__ ctl) {
+  if (ctl->done) return;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nt) return;
+  const double a = w2[q], b = w[q];
+  const double nw = (v[q] - mc->oldeps * a - mc->delta * b) / mc->gamma;
+  w1[q] = a;
+  w2[q] = b;
+  w[q] = nw;
+  x[q] = fma(mc->phi, nw, x[q]);
+}
+
 // p = z + beta p  (start: p = z)
 template <typename T>
 __global__ void p_update_kernel(int nt, const T* __restrict__ z, T* __restrict__ p, int start,
@@ -722,6 +880,37 @@ void launch_shift_cols(cudaStream_t st, int n, int r, const double* Vs, const do
 void launch_diag_K(cudaStream_t st, int n, const double* G, const double* E, const PcgCtl* ctl, double* K,
                    int64_t* launches) {
   diag_K_kernel<<<nblk((int64_t)n * n, VT), VT, 0, st>>>(n, G, E, ctl, K);
+  ++*launches;
+}
+
+void launch_minres_init(cudaStream_t st, int nt, const double* g, double* r1, double* r2, double* x, double* w,
+                        double* w2, MinresCtl* mc, PcgCtl* ctl, double* dotbuf, unsigned int* counter,
+                        int64_t* launches) {
+  minres_init_kernel<<<vec_blocks(nt), VT, 0, st>>>(nt, g, r1, r2, x, w, w2, mc, ctl, dotbuf, counter);
+  ++*launches;
+}
+
+void launch_minres_v(cudaStream_t st, int nt, const double* r2, double* v, MinresCtl* mc, PcgCtl* ctl,
+                     int64_t* launches) {
+  minres_v_kernel<<<nblk(nt, VT), VT, 0, st>>>(nt, r2, v, mc, ctl);
+  ++*launches;
+}
+
+void launch_minres_alfa(cudaStream_t st, int nt, const double* v, double* y, const double* r1, MinresCtl* mc,
+                        PcgCtl* ctl, double* dotbuf, unsigned int* counter, int64_t* launches) {
+  minres_alfa_kernel<<<vec_blocks(nt), VT, 0, st>>>(nt, v, y, r1, mc, ctl, dotbuf, counter);
+  ++*launches;
+}
+
+void launch_minres_beta(cudaStream_t st, int nt, const double* y, double* r1, double* r2, MinresCtl* mc, PcgCtl* ctl,
+                        double* dotbuf, unsigned int* counter, int64_t* launches) {
+  minres_beta_kernel<<<vec_blocks(nt), VT, 0, st>>>(nt, y, r1, r2, mc, ctl, dotbuf, counter);
+  ++*launches;
+}
+
+void launch_minres_update(cudaStream_t st, int nt, const double* v, double* w, double* w1, double* w2, double* x,
+                          const MinresCtl* mc, const PcgCtl* ctl, int64_t* launches) {
+  minres_update_kernel<<<nblk(nt, VT), VT, 0, st>>>(nt, v, w, w1, w2, x, mc, ctl);
   ++*launches;
 }
 

@@ -71,6 +71,18 @@ void launch_diag_w(cudaStream_t st, int n, int r, const double* U, const double*
                    const PcgCtl* ctl, int64_t* launches);
 void launch_diag_zv(cudaStream_t st, int m, int d, int n, int r, const double* H, const double* rv, const double* Dv,
                     double* z, const PcgCtl* ctl, int64_t* launches);
+// MINRES (Def. MINRES, P = I): start, v = r2 / beta, alfa, beta and the rotation, w / x update
+void launch_minres_init(cudaStream_t st, int nt, const double* g, double* r1, double* r2, double* x, double* w,
+                        double* w2, MinresCtl* mc, PcgCtl* ctl, double* dotbuf, unsigned int* counter,
+                        int64_t* launches);
+void launch_minres_v(cudaStream_t st, int nt, const double* r2, double* v, MinresCtl* mc, PcgCtl* ctl,
+                     int64_t* launches);
+void launch_minres_alfa(cudaStream_t st, int nt, const double* v, double* y, const double* r1, MinresCtl* mc,
+                        PcgCtl* ctl, double* dotbuf, unsigned int* counter, int64_t* launches);
+void launch_minres_beta(cudaStream_t st, int nt, const double* y, double* r1, double* r2, MinresCtl* mc, PcgCtl* ctl,
+                        double* dotbuf, unsigned int* counter, int64_t* launches);
+void launch_minres_update(cudaStream_t st, int nt, const double* v, double* w, double* w1, double* w2, double* x,
+                          const MinresCtl* mc, const PcgCtl* ctl, int64_t* launches);
 void launch_pc_d_s_H(cudaStream_t st, int m, int d, int n, int r, const double* H, const double* rv, double* s,
                      const PcgCtl* ctl, int64_t* launches);
 void launch_shift_cols(cudaStream_t st, int n, int r, const double* Vs, const double* lam_s, const PcgCtl* ctl,

@@ -55,7 +55,7 @@ int main(void) {
          offsetof(sdp_newton_info, prof_A32_launches));
   printf("%zu\n", offsetof(sdp_options, inner_rtol));
   printf("%zu %zu %zu\n", offsetof(sdp_options, pcg_start), sizeof(sdp_ipm_info), offsetof(sdp_ipm_info, total_ms));
-  printf("%zu\n", offsetof(sdp_options, tc_products));
+  printf("%zu %zu\n", offsetof(sdp_options, tc_products), offsetof(sdp_options, krylov));
   return 0;
 }
 '''
@@ -78,6 +78,7 @@ int main(void) {
     assert vals[9] == ctypes.sizeof(_native.sdp_ipm_info)
     assert vals[10] == _native.sdp_ipm_info.total_ms.offset
     assert vals[11] == _native.sdp_options.tc_products.offset
+    assert vals[12] == _native.sdp_options.krylov.offset
 
 
 def test_default_options_and_setup_errors(lib):
