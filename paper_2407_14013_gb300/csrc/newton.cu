@@ -394,13 +394,16 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   }
   // slices of the tensor-core products: the n^3 products, and the complement B^T B or
   // B D^{-1} B^T (processed in K-chunks when the whole K does not fit in 4 GiB)
-  if (opt.tc_products && n >= kTcMin) {
-    size_t need = tc_gemm_work_bytes(n, n, n);
-    if (h->kind != SDP_A_DIAG) {
-      if (h->pinv_dim >= kTcMin && std::min(h->d_max, m) == h->pinv_dim)
-        need = std::max(need, tc_gemm_work_bytes(h->pinv_dim, h->pinv_dim, std::max(h->d_max, m)));
+  const bool big_core = h->kind != SDP_A_DIAG && h->pinv_dim >= kTcMin;
+  if (opt.tc_products && (n >= kTcMin || big_core)) {
+    size_t need = n >= kTcMin ? tc_gemm_work_bytes(n, n, n) : 0;
+    if (big_core) {
+      need = std::max(need, tc_gemm_work_bytes(h->pinv_dim, h->pinv_dim, std::max(h->d_max, m)));
+      need = std::max(need, tc_gemm_work_bytes(h->pinv_dim, h->pinv_dim, h->pinv_dim));
     }
-    h->tcw_bytes = std::min(need, std::max(tc_gemm_work_bytes(n, n, n), (size_t)4 << 30));
+    if (h->kind == SDP_A_DENSE_SVEC)   // H = Vs^T [A_i Q] for a batch of constraints
+      need = std::max(need, tc_gemm_work_bytes(n, h->mb2 * r_max, n));
+    h->tcw_bytes = std::min(need, std::max(n >= kTcMin ? tc_gemm_work_bytes(n, n, n) : need, (size_t)4 << 30));
     if (r_max >= 64) h->tcw_b_bytes = tc_gemm_work_bytes(n, r_max, n);
     if (tc_prepare() != cudaSuccess) {   // no tensor-map encoder: every product on the FP64 MMA path
       cudaGetLastError();
@@ -935,7 +938,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
       const int mb = std::min(h->mb2, m - i0);
       direct = dense_AiQ(st, h->a_dense, n, i0, mb, r, S.Vs, h->Gb, L);
       if (!direct) break;
-      CU(gemm_f64(st, true, false, n, mb * r, n, 1.0, S.Vs, n, h->Gb, n, 0.0, h->Hb, n, S.ws, ws, L));
+      CU(gemm_big(h, st, true, false, n, mb * r, n, 1.0, S.Vs, n, h->Gb, n, 0.0, h->Hb, n, S.ws, ws, L));
       h_pack_rows(st, n, r, mb, i0, h->Hb, S.B, d, S.Bt, m, L);
     }
     if (!direct) {   // n r too large for the shared-memory accumulators: unpack, then GEMM

@@ -232,6 +232,7 @@ cudaError_t gemm_any(const TcCtx* tc, cudaStream_t st, bool tA, bool tB, int M, 
 }  // namespace
 
 size_t spd_inverse_tc_work(int n) {
+  if (n < 2 * NB2) return spd_inverse_work(n);
   const size_t nb2 = (size_t)(n + NB2 - 1) / NB2;
   // X (n x n), panel T (n x NB2), U (NB2 x n), the diagonal-block inverses, the inner temporaries
   return (size_t)n * n + 2 * (size_t)n * NB2 + nb2 * NB2 * NB2 + 2 * (size_t)NB2 * NB + (size_t)(NB2 / NB) * NB * NB;
@@ -239,8 +240,21 @@ size_t spd_inverse_tc_work(int n) {
 
 cudaError_t spd_inverse_tc(cudaStream_t st, int n, double* A, double* work, size_t work_elems, double* gemm_ws,
                            size_t gemm_ws_elems, const TcCtx* tc, int32_t* status, int64_t* launches) {
-  if (n < 2 * NB2) return spd_inverse(st, n, A, work, work_elems, gemm_ws, gemm_ws_elems, status, launches);
   if (spd_inverse_tc_work(n) > work_elems) return cudaErrorInvalidValue;
+  if (n < 2 * NB2) {   // one level of 32-wide panels; only X^T X on the tensor cores
+    double* X = work;
+    double* T = X + (size_t)n * n;
+    double* U = T + (size_t)n * NB;
+    double* Li = U + (size_t)n * NB;
+    cudaError_t e = cholesky_and_inverse(st, n, n, A, X, n, T, U, Li, gemm_ws, gemm_ws_elems, status, launches);
+    if (e != cudaSuccess) return e;
+    e = gemm_any(tc, st, true, false, n, n, n, 1.0, X, n, X, n, 0.0, A, n, gemm_ws, gemm_ws_elems, launches,
+                 GEMM_LOWER | GEMM_KSTART_ROW | GEMM_KSTART_COL);
+    if (e != cudaSuccess) return e;
+    lower_to_full_kernel<<<nblk((int64_t)n * n, 256), 256, 0, st>>>(n, A);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+  }
   double* X = work;                                       // n x n, becomes L^{-1}
   double* T = X + (size_t)n * n;                          // rest x NB2 panel
   double* U = T + (size_t)n * NB2;                        // NB2 x i0
