@@ -200,6 +200,9 @@ def other_configs(dev, reps: int = 2, only=None, tc_n: int = 5000):
     # the dense FP64 product on the tensor cores (the n^3 products of the n = 5000 workload)
     if want("tc_gemm"):
         out[f"tc_gemm_{tc_n}"] = _tc_gemm(dev, tc_n)
+    # a 32-instance slice of the batched workload (the whole 256 on request)
+    if want("batch32"):
+        out["batch32"] = _batch256(dev, precs=("mixed_fp32",), count=32)
     # the completion SDP solved to a 1e-8 gap and differentiated at its optimum (minutes: on request)
     if only == "completion2000_solve":
         out["completion2000_solve"] = _completion_solve(dev)
@@ -295,7 +298,7 @@ def _tc_gemm(dev, n, reps=3):
             "max_rel_err_sampled_rows": err, "work_GB": wb / 1e9}
 
 
-def _batch256(dev, precs=("mixed_fp32", "fp64")):
+def _batch256(dev, precs=("mixed_fp32", "fp64"), count=256):
     """The batched workload (workloads.batch_specs): 128 MaxCut (n in 32..512) and 128 sensing
     (n in 32..256, m = 10 n, drawn on the GPU) SDPs, each on its own handle and stream, solved
     to a 1e-8 gap by sdp_solve_batch with 16 host workers; wall time of the whole batch."""
@@ -305,6 +308,9 @@ def _batch256(dev, precs=("mixed_fp32", "fp64")):
     from paper_2407_14013_gb300 import NewtonSolver, solve_sdp_batch
     t0 = time.perf_counter()
     specs = W.batch_specs()
+    if count < len(specs):   # the same mix: the first count/2 of each half
+        half = len(specs) // 2
+        specs = specs[:count // 2] + specs[half:half + count - count // 2]
     probs = []
     for fam, n, seed in specs:
         if fam == "maxcut":
@@ -319,9 +325,9 @@ def _batch256(dev, precs=("mixed_fp32", "fp64")):
     # rank bound: r_hat = 10, raised for MaxCut to ceil(sqrt(2 m)), the bound on the rank of an
     # extreme optimal solution (the split needs r >= rank(X*))
     rh = [max(10, math.ceil(math.sqrt(2 * p.m))) if p.kind == "diag" else 10 for p in probs]
-    res = {"workload": "128 MaxCut (n ~ U{32..512}, G(n,0.05), unit weights, r_hat = max(10, ceil(sqrt(2n)))) + "
-                       "128 matrix sensing (n ~ U{32..256}, m = 10 n, rank 2, r_hat = 10), gap 1e-8, one handle "
-                       "and stream per instance, 16 host workers",
+    res = {"workload": f"{len(probs) // 2} MaxCut (n ~ U{{32..512}}, G(n,0.05), unit weights, r_hat = max(10, "
+                       f"ceil(sqrt(2n)))) + {len(probs) - len(probs) // 2} matrix sensing (n ~ U{{32..256}}, m = 10 n, "
+                       "rank 2, r_hat = 10), gap 1e-8, one handle and stream per instance, 16 host workers",
            "generation_s": gen_s}
     for prec in precs:
         solvers = [NewtonSolver(p, r_hat=r_, device=str(dev), stream=torch.cuda.Stream(dev), precision=prec)
@@ -640,8 +646,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
     ap.add_argument("--no-ttg", action="store_true", help="skip the time-to-gap solves")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads (MaxCut 64 / 5000, completion)")
-    ap.add_argument("--only", choices=["maxcut64", "maxcut5000", "completion2000", "tc_gemm", "completion2000_solve",
-                                       "batch256"],
+    ap.add_argument("--only", choices=["maxcut64", "maxcut5000", "completion2000", "tc_gemm", "batch32",
+                                       "completion2000_solve", "batch256"],
                     help="measure only this other workload (one JSON object; no headline line)")
     ap.add_argument("--reps", type=int, default=2, help="timed Newton solves per row of the other workloads")
     ap.add_argument("--tc-n", type=int, default=5000, help="order of the tensor-core product row (--only tc_gemm)")
