@@ -17,10 +17,11 @@
 // large internal dynamic range (use gemm_f64 where they do).
 //
 // Kernel.  One CTA per 128 x 128 output tile, 9 warps: warp 8 (one lane) issues the TMA loads
-// of 128 x 64 BF16 slice tiles (128-byte swizzle) into a 4-stage ring and the 128x128x16
+// of 128 x 64 BF16 slice tiles (128-byte swizzle) into a 3-stage ring and the 128x128x16
 // tcgen05.mma steps into one of two TMEM accumulators (256 columns); warps 0-7 drain a finished
-// accumulator (tcgen05.ld, 32 lanes x 32 columns per load) into FP64 registers while the tensor
-// core fills the other.  Every wait is bounded (about 2 s, %globaltimer): on expiry the kernel
+// accumulator (tcgen05.ld, 32 lanes x 32 columns per load) while the tensor core fills the
+// other: the products of one weight class s + t in a K-chunk are summed exactly as int32, then
+// added once to FP64 accumulators of the tile in shared memory (128 KB).  Every wait is bounded (about 2 s, %globaltimer): on expiry the kernel
 // sets an error word, stops issuing, waits (bounded) for its own copies and products in flight,
 // frees its TMEM and returns.
 #include <cuda.h>
@@ -41,12 +42,13 @@ namespace {
 constexpr int S = 8;                  // slices per operand
 constexpr int KC = 4096;              // exact K-chunk of one slice product
 constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int STAGES = 4;
+constexpr int STAGES = 3;
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = (EPI_WARPS + 1) * 32;
 constexpr int TILE_BYTES = BM * BK * 2;                 // 16 KB per operand tile
 constexpr int STAGE_BYTES = 2 * TILE_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;  // + alignment slack
+constexpr int FACC_BYTES = BM * BN * 8;                  // FP64 accumulators of the tile
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + FACC_BYTES + 1024;  // + alignment slack
 constexpr int TMEM_COLS = 256;                           // two 128-column FP32 accumulators
 constexpr int NPAIRS = S * (S + 1) / 2;                  // s + t <= S + 1
 constexpr unsigned long long WAIT_NS = 2000000000ull;
@@ -362,45 +364,68 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       }
     }
   } else {
-    // ---- drain accumulators into FP64 (warps 0-7) ----
+    // ---- drain accumulators (warps 0-7) ----
+    // The products of one weight class g = s + t in one K-chunk are summed exactly as integers
+    // (at most 8 of them, each |.| <= 2^24: the sum fits int32), then added once to the FP64
+    // accumulators of the tile, kept in shared memory (column-major, conflict-free rows).
     const int lg = warp & 3;                         // TMEM lanes 32 lg .. 32 lg + 31 = tile rows
     const int cg = warp >> 2;                        // columns 64 cg .. 64 cg + 63
-    double acc[64];
+    double* facc = reinterpret_cast<double*>(smem_raw + (base - smem_u32(smem_raw)) + STAGES * STAGE_BYTES);
+    const int trow = 32 * lg + lane;
+#pragma unroll 8
+    for (int j = 0; j < 64; ++j) facc[(cg * 64 + j) * BM + trow] = 0.0;
+    int gacc[64];
 #pragma unroll
-    for (int j = 0; j < 64; ++j) acc[j] = 0.0;
+    for (int j = 0; j < 64; ++j) gacc[j] = 0;
     for (int u = 0; u < units; ++u) {
       const int buf = u & 1;
       if (!mbar_wait(smem_u32(&accf_bar[buf]), (u >> 1) & 1, &abort_flag, err)) break;
       tc_fence_after();
-      int s, t;
-      pair_of(u % NPAIRS, s, t);
-      const double w = scalbn(1.0, -(7 * (s + t) - 2));
       const uint32_t taddr = tmem + (uint32_t)(buf * BN + cg * 64) + ((uint32_t)(32 * lg) << 16);
       uint32_t r[32];
       WC_TMEM_LD32(taddr, r);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int j = 0; j < 32; ++j) acc[j] = fma(w, (double)__uint_as_float(r[j]), acc[j]);
+      for (int j = 0; j < 32; ++j) gacc[j] += __float2int_rn(__uint_as_float(r[j]));   // exact integers
       WC_TMEM_LD32(taddr + 32, r);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&acce_bar[buf]));
 #pragma unroll
-      for (int j = 0; j < 32; ++j) acc[32 + j] = fma(w, (double)__uint_as_float(r[j]), acc[32 + j]);
+      for (int j = 0; j < 32; ++j) gacc[32 + j] += __float2int_rn(__uint_as_float(r[j]));
+      // the class ends with this unit: a new chunk, a new g, or the last unit
+      int s, t;
+      pair_of(u % NPAIRS, s, t);
+      bool last_of_class = (u + 1 == units) || ((u + 1) % NPAIRS == 0);
+      if (!last_of_class) {
+        int s2, t2;
+        pair_of((u + 1) % NPAIRS, s2, t2);
+        last_of_class = (s2 + t2 != s + t);
+      }
+      if (last_of_class) {
+        const double w = scalbn(1.0, -(7 * (s + t) - 2));
+#pragma unroll
+        for (int j = 0; j < 64; ++j) {
+          double* f = facc + (cg * 64 + j) * BM + trow;
+          *f = fma(w, (double)gacc[j], *f);
+          gacc[j] = 0;
+        }
+      }
     }
     if (!abort_flag) {
-      const int row = m0 + 32 * lg + lane;
+      const int row = m0 + trow;
       if (row < M) {
         const int er = ea[row];
-#pragma unroll
+#pragma unroll 4
         for (int j = 0; j < 64; ++j) {
           const int col = n0 + cg * 64 + j;
           if (col < N) {
+            const double a = facc[(cg * 64 + j) * BM + trow];
             if (part) {                              // partial tile of this K range
-              part[(int64_t)blockIdx.z * M * N + row + (int64_t)col * M] = scalbn(acc[j], er + eb[col]);
+              part[(int64_t)blockIdx.z * M * N + row + (int64_t)col * M] = scalbn(a, er + eb[col]);
             } else {
-              const double v = alpha * scalbn(acc[j], er + eb[col]);
+              const double v = alpha * scalbn(a, er + eb[col]);
               double* cp = C + (int64_t)row + (int64_t)col * ldc;
               *cp = (beta == 0.0) ? v : v + beta * *cp;
             }
