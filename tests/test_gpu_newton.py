@@ -319,3 +319,38 @@ def test_tensor_core_products_match_fp64_mma_and_oracle(name, mk, rt, rh):
     assert rel(X1, rX) < TOL and rel(y1, ry) < TOL and rel(S1, rS) < TOL
     s1.close()
     s0.close()
+
+
+def test_edge_cases_diag_and_sparse_kinds():
+    """DIAG at r = 1 (d = n = m: the d-space core with the explicit B of the DIAG kind) and at
+    r = n - 1; SPARSE_COO with one constraint and at r = 1; each against the plain definition."""
+    cases = [
+        (lambda: W.maxcut(9, 0.5, 611), 1, 1),        # d = n = m -> d-space, explicit B
+        (lambda: W.maxcut(9, 0.5, 612), 1, 8),        # r = n - 1
+        (lambda: W.random_sparse(7, 1, 3, 613), 1, 1),
+        (lambda: W.random_sparse(10, 12, 2, 614), 1, 1),
+    ]
+    for mk, rt, rfix in cases:
+        prob = mk()
+        sp = W.scaling_point(prob.n, rt, 1e-2, 620 + prob.n + prob.m)
+        Ct, bt = W.newton_rhs(prob.n, prob.m, 621 + prob.n + prob.m)
+        s, (dX, dy, dS, info) = gpu_solve(prob, sp, Ct, bt, r_fixed=rfix)
+        assert info.r == rfix and info.converged, (prob.kind, prob.n, prob.m, rfix)
+        rX, ry, rS = onewton.newton_direct(prob, w_of(sp), Ct, bt)
+        assert rel(dX, rX) < TOL and rel(dy, ry) < TOL and rel(dS, rS) < TOL, (prob.kind, prob.n, prob.m, rfix)
+        if prob.kind == "diag" and rfix == 1:
+            assert info.space == 1
+        s.close()
+
+
+def test_minres_with_tensor_core_products():
+    """MINRES at n >= 512: E and the recovery on the tensor cores, the operator in the captured
+    Krylov graph; the direction equals the plain definition."""
+    prob = W.maxcut(601, 0.014, 105, weights="gauss")
+    sp = W.scaling_point(prob.n, 37, 1e-1, 1301)
+    Ct, bt = W.newton_rhs(prob.n, prob.m, 1302)
+    s, (dX, dy, dS, info) = gpu_solve(prob, sp, Ct, bt, r_hat=40, krylov="minres", max_pcg=50000)
+    assert info.converged and info.r == 37
+    rX, ry, rS = onewton.newton_direct(prob, w_of(sp), Ct, bt)
+    assert rel(dX, rX) < TOL and rel(dy, ry) < TOL and rel(dS, rS) < TOL
+    s.close()
