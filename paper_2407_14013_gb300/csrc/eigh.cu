@@ -585,6 +585,73 @@ double tridiag_min(const std::vector<double>& a, const std::vector<double>& b, i
   return 0.5 * (lo + hi);
 }
 
+// The same Lanczos steps k0 .. k1 - 1 in ONE block (block barriers instead of grid barriers):
+// for problems run side by side on their own streams, where no launch may wait for the whole
+// GPU.  Same start vector, recurrence and re-orthogonalisation as the cooperative kernel.
+constexpr int LT = 1024;
+__global__ void __launch_bounds__(LT)
+lanczos_block_kernel(int n, const double* __restrict__ M, double* __restrict__ Vb, double* __restrict__ alpha,
+                     double* __restrict__ beta, double* __restrict__ w, double* __restrict__ hbuf, int k0, int k1) {
+  __shared__ double sh[32];
+  const int t = threadIdx.x, T = blockDim.x, lane = t & 31, wid = t >> 5, nw = T >> 5;
+  if (k0 == 0) {
+    double loc = 0.0;
+    for (int i = t; i < n; i += T) {
+      const double v = 1.0 + 0.5 * sin(0.7 * (double)i + 0.3);
+      Vb[i] = v;
+      loc = fma(v, v, loc);
+    }
+    const double nrm = sqrt(block_sum(loc, sh));
+    for (int i = t; i < n; i += T) Vb[i] /= nrm;
+    __syncthreads();
+  }
+  for (int k = k0; k < k1; ++k) {
+    const double* vk = Vb + (int64_t)k * n;
+    for (int i = wid; i < n; i += nw) {   // w = M v_k, one warp per row (M symmetric)
+      const double* row = M + (int64_t)i * n;
+      double acc = 0.0;
+      for (int j = lane; j < n; j += 32) acc = fma(row[j], vk[j], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) w[i] = acc;
+    }
+    __syncthreads();
+    double loc = 0.0;
+    for (int i = t; i < n; i += T) loc = fma(vk[i], w[i], loc);
+    const double a = block_sum(loc, sh);
+    const double bprev = (k > 0) ? beta[k - 1] : 0.0;
+    for (int i = t; i < n; i += T) {
+      double v = w[i] - a * vk[i];
+      if (k > 0) v -= bprev * Vb[(int64_t)(k - 1) * n + i];
+      w[i] = v;
+    }
+    if (t == 0) alpha[k] = a;
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {   // full re-orthogonalisation against v_0 .. v_k, twice
+      for (int j = wid; j <= k; j += nw) {
+        const double* vj = Vb + (int64_t)j * n;
+        double acc = 0.0;
+        for (int i = lane; i < n; i += 32) acc = fma(vj[i], w[i], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) hbuf[j] = acc;
+      }
+      __syncthreads();
+      for (int i = t; i < n; i += T) {
+        double v = w[i];
+        for (int j = 0; j <= k; ++j) v = fma(-hbuf[j], Vb[(int64_t)j * n + i], v);
+        w[i] = v;
+      }
+      __syncthreads();
+    }
+    loc = 0.0;
+    for (int i = t; i < n; i += T) loc = fma(w[i], w[i], loc);
+    const double b = sqrt(block_sum(loc, sh));
+    if (t == 0) beta[k] = b;
+    double* vn = Vb + (int64_t)(k + 1) * n;
+    for (int i = t; i < n; i += T) vn[i] = (b > 0.0) ? w[i] / b : 0.0;
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 size_t lanczos_work_elems(int n) {
@@ -593,7 +660,7 @@ size_t lanczos_work_elems(int n) {
 }
 
 cudaError_t lanczos_min(cudaStream_t st, int n, const double* M, double* work, size_t work_elems, double* lmin,
-                        int* iters, int64_t* launches) {
+                        int* iters, int64_t* launches, bool allow_coop) {
   if (n < 1 || work_elems < lanczos_work_elems(n)) return cudaErrorInvalidValue;
   const int K = n;   // at most n vectors span R^n
   double* Vb = work;
@@ -603,21 +670,33 @@ cudaError_t lanczos_min(cudaStream_t st, int n, const double* M, double* work, s
   double* w = hbuf + K + 1;
   double* red = w + n;
   int dev = 0, coop = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-  if (!coop) return cudaErrorNotSupported;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_coop_kernel, ET, 0);
-  if (e != cudaSuccess || per_sm < 1) return cudaErrorNotSupported;
+  cudaError_t e = cudaSuccess;
+  if (allow_coop) {
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (coop) {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_coop_kernel, ET, 0);
+      if (e != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        coop = 0;
+      }
+    }
+  }
   const int want = (int)std::max<int64_t>(1, ((int64_t)n * 32 + ET - 1) / ET);   // one warp per row
-  const int blocks = std::min({want, per_sm * g_num_sms, kCoopMaxBlocks});
+  const int blocks = coop ? std::min({want, per_sm * g_num_sms, kCoopMaxBlocks}) : 1;
   std::vector<double> ah(K + 1), bh(K + 1);
   double prev = INFINITY, prev2 = INFINITY, theta = 0.0;
   int k = 0;
   const int chunk = 32;
   while (k < K) {
     int k0 = k, k1 = std::min(K, k + chunk);
-    void* args[] = {&n, (void*)&M, &Vb, &alpha, &beta, &w, &hbuf, &red, &k0, &k1};
-    e = cudaLaunchCooperativeKernel((const void*)lanczos_coop_kernel, dim3(blocks), dim3(ET), args, 0, st);
+    if (coop) {
+      void* args[] = {&n, (void*)&M, &Vb, &alpha, &beta, &w, &hbuf, &red, &k0, &k1};
+      e = cudaLaunchCooperativeKernel((const void*)lanczos_coop_kernel, dim3(blocks), dim3(ET), args, 0, st);
+    } else {
+      lanczos_block_kernel<<<1, LT, 0, st>>>(n, M, Vb, alpha, beta, w, hbuf, k0, k1);
+      e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return e;
     if (launches) ++*launches;
     e = cudaMemcpyAsync(ah.data(), alpha, k1 * sizeof(double), cudaMemcpyDeviceToHost, st);

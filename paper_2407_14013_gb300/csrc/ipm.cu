@@ -261,18 +261,12 @@ sdp_status lam_min_jacobi(Ctx& c, const double* M, double* out, int* sweeps) {
   return SDP_OK;
 }
 
-// smallest eigenvalue of M: Lanczos, or Jacobi where cooperative launches are unavailable
+// smallest eigenvalue of M by Lanczos (one block per launch in batched solves)
 sdp_status lam_min(Ctx& c, const double* M, double* out, int* sweeps) {
+  (void)sweeps;
   sdp_handle* h = c.h;
-  IpmWork* w = c.w;
   int it = 0;
-  if (h->no_coop) return lam_min_jacobi(c, M, out, sweeps);
-  cudaError_t e = lanczos_min(c.st, c.n, M, w->lzw, w->lzw_elems, out, &it, c.L);
-  if (e == cudaErrorNotSupported) {
-    cudaGetLastError();
-    return lam_min_jacobi(c, M, out, sweeps);
-  }
-  CUI(e);
+  CUI(lanczos_min(c.st, c.n, M, c.w->lzw, c.w->lzw_elems, out, &it, c.L, !h->no_coop));
   return SDP_OK;
 }
 

@@ -209,11 +209,11 @@ struct EighGraph {
   const void *A = nullptr, *V = nullptr, *work = nullptr;
 };
 void eigh_graph_release(EighGraph* g);
-// Smallest eigenvalue of the symmetric M (n x n) by Lanczos with full re-orthogonalisation
-// (cooperative launches; cudaErrorNotSupported when the device cannot run them).
+// Smallest eigenvalue of the symmetric M (n x n) by Lanczos with full re-orthogonalisation:
+// cooperative launches over the GPU when allowed and supported, else one block per launch.
 size_t lanczos_work_elems(int n);
 cudaError_t lanczos_min(cudaStream_t st, int n, const double* M, double* work, size_t work_elems, double* lmin,
-                        int* iters, int64_t* launches);
+                        int* iters, int64_t* launches, bool allow_coop = true);
 size_t eigh_work_elems(int n);
 cudaError_t eigh_jacobi(cudaStream_t st, int n, double* A, double* V, double* lam, double tol, int max_sweeps,
                         double* work, size_t work_elems, int* sweeps_out, double* off_out, int64_t* launches,
