@@ -136,6 +136,14 @@ typedef struct {
                             of eq. augsys, not of the preconditioned operator); max_pcg bounds
                             its iterations and the stop test is the PCG one.  FP64 only
                             (SDP_MIXED_FP32 with krylov = 1: SDP_EUNSUPPORTED).               */
+  int32_t int_passes;    /* DENSE_SVEC kind, FP64 operator (the FP64 form, and the FP64 residuals
+                            of the mixed form): 1 (default) = the two passes over the svec rows,
+                            A(Z) and A^T(y), stream an integer copy of A made at setup (two int32
+                            digits per entry with a power-of-two scale per row, 8 bytes per
+                            entry) and sum exact int64 digit products, whose error is within the
+                            FP64 dot-product bound measured against the largest entry of the row
+                            and of the vector; GB300's integer pipe keeps up with HBM where its
+                            FP64 pipe does not.  0 = FP64 FMAs over the caller's A (no copy).   */
 } sdp_options;
 
 typedef struct {
@@ -250,7 +258,7 @@ sdp_status sdp_solve_batch(int32_t count, sdp_handle* const* hs, const double* c
 
 /* Fill *opt with the defaults: r_fixed 0, r_hat 10, FP64, auto space,
  * max_pcg 2000, check_every 8, beta_rule 0, use_graph 1, newton_rtol 1e-12, max_refine 10,
- * max_inner 500, inner_rtol 1e-6, pcg_start 0, tc_products 1, krylov 0. */
+ * max_inner 500, inner_rtol 1e-6, pcg_start 0, tc_products 1, krylov 0, int_passes 1. */
 void sdp_default_options(sdp_options* opt);
 
 /* Validate the problem, record its (device) pointers -- the caller keeps

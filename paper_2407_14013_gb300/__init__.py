@@ -74,7 +74,7 @@ class NewtonSolver:
                  max_pcg: int = 2000, check_every: int = 8, beta_rule: int = 0,
                  newton_rtol: float = 1e-12, device: str = "cuda", stream=None, use_graph: bool = True,
                  precision: str = "fp64", max_refine: int = 10, max_inner: int = 500, inner_rtol: float = 1e-6,
-                 pcg_start: int = 0, tc_products: bool = True, krylov: str = "pcg"):
+                 pcg_start: int = 0, tc_products: bool = True, krylov: str = "pcg", int_passes: bool = True):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -113,6 +113,7 @@ class NewtonSolver:
         o.pcg_start = pcg_start
         o.tc_products = 1 if tc_products else 0
         o.krylov = {"pcg": 0, "minres": 1}[krylov]
+        o.int_passes = 1 if int_passes else 0
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         torch.cuda.synchronize(self.device)
         self.handle = native.sdp_setup(p, o, int(self.stream.cuda_stream))

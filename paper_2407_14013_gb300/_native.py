@@ -31,7 +31,7 @@ class sdp_options(Structure):
                 ("max_pcg", c_int32), ("check_every", c_int32), ("beta_rule", c_int32), ("use_graph", c_int32),
                 ("newton_rtol", c_double), ("max_refine", c_int32), ("max_inner", c_int32),
                 ("inner_rtol", c_double), ("pcg_start", c_int32), ("tc_products", c_int32),
-                ("krylov", c_int32)]
+                ("krylov", c_int32), ("int_passes", c_int32)]
 
 
 class sdp_newton_info(Structure):

@@ -63,6 +63,14 @@ __device__ __forceinline__ double ld_stream_d(const double* p, uint64_t pol) {
   return v;
 }
 
+// 16-byte streaming load of four int32 (evict-first L2 policy, no L1 allocation).
+__device__ __forceinline__ int4 ld_stream_i4(const int4* p, uint64_t pol) {
+  int4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p), "l"(pol));
+  return v;
+}
+
 // 16-byte streaming load of four floats (evict-first L2 policy, no L1 allocation).
 __device__ __forceinline__ float4 ld_stream_f4(const float4* p, uint64_t pol) {
   float4 v;

@@ -22,6 +22,7 @@ struct Space {
   double *partB = nullptr, *partBt = nullptr, *partC = nullptr;
   double *ypos = nullptr, *zpos = nullptr;     // SPARSE_COO: A^T(y) and E Y E at the pattern positions
   double *mw = nullptr, *mw1 = nullptr, *mw2 = nullptr;   // MINRES search directions
+  int* fxe = nullptr;                          // exponents of the vectors of the integer passes over A
   double *x = nullptr, *rv = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr;
   double* ws = nullptr;                        // split-K GEMM scratch
   size_t ws_elems = 0;
@@ -95,6 +96,9 @@ struct sdp_handle {
   int64_t b_elems = 0;              // capacity of the explicit B = A Q (m x d)
   int64_t bt_elems = 0;             // capacity of B^T (d x m)
   int64_t bs_elems = 0;             // capacity of D^{-1/2} B^T (m-space core by a product)
+  bool fx = false;                  // DENSE_SVEC: the FP64 passes over A run on its integer copy
+  int2* a_fx = nullptr;             // digits of A (m rows of fx_row_len(N) entries)
+  int* a_fx_e = nullptr;            // row exponents
   wc::Space s64;                        // FP64 solve, outer refinement of the mixed form
   wc::Space sin;                        // inner solve of the mixed form (own vectors and control block)
   wc::Mixed32 m32;

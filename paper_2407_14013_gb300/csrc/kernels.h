@@ -66,6 +66,21 @@ template <typename T>
 void rows_gemvT_unpack(cudaStream_t st, const T* A, int m, int64_t L, const T* p, T* part, int groups, int n,
                        double scale, T* Y, unsigned int* tickets, const int32_t* done, int64_t* launches);
 int rows_gemvT_blocks(int64_t L, int esize);
+// Exact fixed-point forms of the FP64 passes over dense rows (rows.cu): A (m x L) split once into
+// two int32 digits per entry (rows of fx_row_len(L) entries) with a power-of-two exponent per
+// row; a pass takes its vector's exponent from fx_exponent (the device int *f), splits the vector
+// as it stages it, and sums exact int64 digit products.  Same outputs and partial-sum layouts as
+// rows_gemv<double> and rows_gemvT_unpack<double>, with an error within the FP64 dot-product bound.
+int64_t fx_row_len(int64_t L);
+int fx_rows_gemv_slabs(int m, int64_t L);   // slab partial sums written by fx_rows_gemv
+void fx_split_rows(cudaStream_t st, const double* A, int m, int64_t L, int2* Ai, int* ea, int64_t* launches);
+void fx_exponent(cudaStream_t st, const double* x, const int* ex, int64_t len, int* f, const int32_t* done,
+                 int64_t* launches);
+void fx_rows_gemv(cudaStream_t st, const int2* Ai, const int* ea, int m, int64_t L, const double* x, const int* f,
+                  double* part, const int32_t* done, int64_t* launches);
+void fx_rows_gemvT_unpack(cudaStream_t st, const int2* Ai, const int* ea, int m, int64_t L, const double* y,
+                          const int* f, double* part, int groups, int n, double scale, double* Y,
+                          unsigned int* tickets, const int32_t* done, int64_t* launches);
 // sum_i ||row_i||^2
 void rows_sumsq(cudaStream_t st, const double* A, int m, int64_t L, double* out, double* scratch,
                 int64_t* launches);

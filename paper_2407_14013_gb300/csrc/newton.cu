@@ -73,6 +73,7 @@ extern "C" void sdp_default_options(sdp_options* o) {
   o->pcg_start = 0;
   o->tc_products = 1;
   o->krylov = 0;
+  o->int_passes = 1;
 }
 
 namespace {
@@ -114,6 +115,7 @@ void carve_space(sdp_handle* h, Carver& c, Space& S) {
     S.zsvec = c.take<double>(h->N);
     S.partY = c.take<double>((size_t)h->GY * h->N);
   }
+  if (h->fx) S.fxe = c.take<int>(2);
   if (h->kind == SDP_A_SPARSE_COO) {
     S.ypos = c.take<double>(h->sp.npos);
     S.zpos = c.take<double>(h->sp.npos);
@@ -197,6 +199,10 @@ size_t carve(sdp_handle* h, char* base) {
     h->sp.ypidx = c.take<int32_t>(h->sp.nnzY);
   }
   h->gj_work = c.take<double>(h->gj_work_elems);
+  if (h->fx) {
+    h->a_fx = c.take<int2>((size_t)m * fx_row_len(h->N));
+    h->a_fx_e = c.take<int>(m);
+  }
   if (h->kind == SDP_A_DENSE_SVEC) {
     h->ubatch = c.take<double>((size_t)h->mb * nn);
     h->Gb = c.take<double>((size_t)h->mb2 * n * rm);
@@ -265,6 +271,7 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   if (opt.pcg_start < 0 || opt.pcg_start > 1) return fail(nullptr, SDP_EINVAL, "bad pcg_start");
   if (opt.tc_products < 0 || opt.tc_products > 1) return fail(nullptr, SDP_EINVAL, "bad tc_products");
   if (opt.krylov < 0 || opt.krylov > 1) return fail(nullptr, SDP_EINVAL, "bad krylov");
+  if (opt.int_passes < 0 || opt.int_passes > 1) return fail(nullptr, SDP_EINVAL, "bad int_passes");
   if (opt.krylov == 1 && opt.precision != SDP_FP64)
     return fail(nullptr, SDP_EUNSUPPORTED, "MINRES is built for the FP64 form only");
 
@@ -357,6 +364,7 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   h->mixed = (opt.precision == SDP_MIXED_FP32);
   h->st = static_cast<cudaStream_t>(stream);
   h->N = (int64_t)n * (n + 1) / 2;
+  h->fx = (h->kind == SDP_A_DENSE_SVEC && opt.int_passes == 1);
   h->r_max = r_max;
   h->d_max = dof(n, r_max);
   // d-space core (d x d) when d <= m, m-space core (m x m) otherwise, unless forced
@@ -383,7 +391,7 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (h->kind == SDP_A_DENSE_SVEC) {
     h->GY = rows_gemvT_groups(m, h->N, 8);
-    h->SA = rows_gemv_slabs(m, h->N, 8);
+    h->SA = h->fx ? fx_rows_gemv_slabs(m, h->N) : rows_gemv_slabs(m, h->N, 8);
     h->GY32 = rows_gemvT_groups(m, h->N, 4);
     h->SA32 = rows_gemv_slabs(m, h->N, 4);
     // batch of constraints unpacked to full matrices while forming B (at most ~64 MB)
@@ -465,6 +473,7 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
       return fail(nullptr, SDP_EINVAL, "A has a zero or non-finite Frobenius norm");
     }
     if (h->mixed) convert<float, double>(h->st, (int64_t)m * h->N, h->a_dense, h->m32.A, &h->launches);
+    if (h->fx) fx_split_rows(h->st, h->a_dense, m, h->N, h->a_fx, h->a_fx_e, &h->launches);
   } else if (h->kind == SDP_A_SPARSE_COO) {
     sparse_sumsq(h->st, h->sp, h->dotbuf, h->scratch, &h->launches);
     double tot = 0.0;
@@ -561,9 +570,31 @@ cudaError_t spd_inverse_any(sdp_handle* h, cudaStream_t st, int dim, double* P, 
 
 // Y = A^T(u) as a full n x n matrix (DENSE kind).
 void adjoint_dense(sdp_handle* h, Space& S, const double* u, double* Y, const int32_t* done) {
+  if (h->fx) {
+    fx_exponent(h->st, u, h->a_fx_e, h->m, S.fxe, done, &h->launches);
+    prof_begin(h, 0);
+    fx_rows_gemvT_unpack(h->st, h->a_fx, h->a_fx_e, h->m, h->N, u, S.fxe, S.partY, h->GY, h->n, 1.0, Y, h->gt_tickets,
+                         done, &h->launches);
+    prof_end(h);
+    return;
+  }
   prof_begin(h, 0);
   rows_gemvT_unpack<double>(h->st, h->a_dense, h->m, h->N, u, S.partY, h->GY, h->n, 1.0, Y, h->gt_tickets, done,
                             &h->launches);
+  prof_end(h);
+}
+
+// partA = the slab partial sums of A(z) for z = svec(.) of length N (DENSE kind)
+void apply_dense(sdp_handle* h, Space& S, cudaStream_t st, const double* z, const int32_t* done, int64_t* L) {
+  if (h->fx) {
+    fx_exponent(st, z, nullptr, h->N, S.fxe + 1, done, L);
+    prof_begin(h, 1);
+    fx_rows_gemv(st, h->a_fx, h->a_fx_e, h->m, h->N, z, S.fxe + 1, S.partA, done, L);
+    prof_end(h);
+    return;
+  }
+  prof_begin(h, 1);
+  rows_gemv<double>(st, h->a_dense, h->m, h->N, z, S.partA, done, L);
   prof_end(h);
 }
 
@@ -594,9 +625,7 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
     join(h, 0, 2);
     join(h, 1, 3);
     svec_pack_plus<double>(st, n, r, S.Z, S.Up, Q, S.zsvec, done, L);    // svec(E Y E + sym(Up Q^T))
-    prof_begin(h, 1);
-    rows_gemv<double>(st, h->a_dense, m, h->N, S.zsvec, S.partA, done, L);
-    prof_end(h);
+    apply_dense(h, S, st, S.zsvec, done, L);
     launch_ap_finish<double>(st, m, d, n, r, S.partA, h->SA, nullptr, S.Vs, S.H, S.Dv, pin, gsub, out, mode, S.ctl,
                              h->dotbuf, h->counter, L);
   } else if (h->kind == SDP_A_SPARSE_COO) {
@@ -1005,9 +1034,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   if (h->kind == SDP_A_DENSE_SVEC) {
     CU(gemm_big(h, st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, ws, L, GEMM_LOWER));
     svec_pack_plus<double>(st, n, r, S.Z, nullptr, nullptr, S.zsvec, nullptr, L);
-    prof_begin(h, 1);
-    rows_gemv<double>(st, h->a_dense, m, h->N, S.zsvec, S.partA, nullptr, L);
-    prof_end(h);
+    apply_dense(h, S, st, S.zsvec, nullptr, L);
     launch_rhs_finish(st, m, d, n, r, S.partA, h->SA, nullptr, nullptr, bt, Ct, S.H, S.Dv, h->g, S.x,
                       h->opt.newton_rtol, h->ctl, h->dotbuf, h->counter, L);
   } else if (h->kind == SDP_A_SPARSE_COO) {

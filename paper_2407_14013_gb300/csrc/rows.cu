@@ -369,6 +369,299 @@ GvPlan gv_plan(int m, int64_t L, int esize) {
   return P;
 }
 
+// ---- exact fixed-point passes -------------------------------------------------------------
+//
+// GB300 issues one FP64 FMA per element at 1.26 TFLOP/s, which caps an FP64 pass over A near
+// 5 TB/s; its integer pipe has several times that rate.  So the FP64 operator can stream an
+// integer copy of A instead: row i of A is scaled by 2^-e_i (2^e_i > max_k |A_ik|) and every
+// entry written as N = rint(2^52 A_ik 2^-e_i) = hi 2^26 + lo (|hi| <= 2^26, -2^25 <= lo < 2^25),
+// once at setup, 8 bytes per entry as in FP64.  A vector x of the pass gets one exponent f
+// (2^f > max_k |x_k|, for the A^T pass after folding 2^e_i into x_i) and the same two digits.
+// Then x . a = 2^(f + e) 2^-104 sum_k (hi 2^26 + lo)(xh 2^26 + xl), whose two leading parts
+//   T1 = sum hi xh,  T2 = sum (hi xl + lo xh)      (every product below 2^52 in magnitude)
+// are accumulated exactly in int64 (at most FX_FLUSH terms per accumulator), converted once
+// to FP64 and scaled by 2^(f + e - 52) and 2^(f + e - 78).  Dropped: lo xl 2^-104 per term and
+// the two roundings to 53 bits, so each output is within about 3 K 2^-53 2^(f+e) of the exact
+// product with the unrounded A and x: the FP64 error bound of a K-term dot product measured
+// against the largest entry of the row and of the vector.
+constexpr int FX_FLUSH = 1024;
+constexpr int FX_BAD = 0x7fffffff;          // the vector had a non-finite entry: outputs are NaN
+constexpr int FX_NONE = INT_MIN;            // no nonzero entry
+
+// e with |x| < 2^e from the IEEE fields (x finite and nonzero)
+__device__ __forceinline__ int fx_expo_bits(unsigned long long b) {
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex) return ex - 1022;
+  const unsigned long long mnt = b & 0xFFFFFFFFFFFFFull;   // subnormal: mnt 2^-1074
+  return (63 - __clzll((long long)mnt)) - 1073;
+}
+
+// N = rint(x 2^(52 + adj - F)) by integer shifts of the IEEE fields, for |x| 2^adj < 2^F
+// (so |N| <= 2^52); halves round away from zero
+__device__ __forceinline__ long long fx_fixed(double x, int adj, int F) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  unsigned long long mnt = b & 0xFFFFFFFFFFFFFull;
+  if (ex) mnt |= 1ull << 52;
+  if (mnt == 0ull) return 0;
+  const int sh = (ex ? ex : 1) - 1023 + adj - F;          // x 2^(52+adj-F) = mnt 2^sh
+  long long N;
+  if (sh >= 0) N = sh < 64 ? (long long)(mnt << sh) : 0;      // sh >= 0 only for subnormal x
+  else if (sh <= -64) N = 0;
+  else N = (long long)((mnt + (1ull << (-sh - 1))) >> (-sh));
+  return (b >> 63) ? -N : N;
+}
+
+__device__ __forceinline__ int2 fx_split(long long N) {   // |N| <= 2^52
+  const long long hi = (N + (1ll << 25)) >> 26;
+  return make_int2((int)hi, (int)(N - (hi << 26)));
+}
+
+__device__ __forceinline__ double fx_value(long long t1, long long t2) {
+  return fma((double)t1, 0x1p-52, (double)t2 * 0x1p-78);
+}
+
+__device__ __forceinline__ void fx_acc2(long long& t1, long long& t2, const int4& a, const int4& w) {
+  t1 += (long long)a.x * w.x;
+  t2 += (long long)a.x * w.y + (long long)a.y * w.x;
+  t1 += (long long)a.z * w.z;
+  t2 += (long long)a.z * w.w + (long long)a.w * w.z;
+}
+
+__device__ __forceinline__ int block_max_int(int v, int* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = __reduce_max_sync(0xffffffffu, v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  int t = (threadIdx.x < nw) ? sh[threadIdx.x] : INT_MIN;
+  if (wid == 0) t = __reduce_max_sync(0xffffffffu, t);
+  if (threadIdx.x == 0) sh[0] = t;
+  __syncthreads();
+  const int r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ double fx_out(double d, int F, int e) {
+  return F == FX_BAD ? __longlong_as_double(0x7ff8000000000000ll) : (F == FX_NONE ? 0.0 : ldexp(d, F + e));
+}
+
+// setup: row i of A (m x L, row-major) -> digits (row length Lp = L rounded up to even, the pad
+// entry zero) and its exponent e_i (0 for a zero row)
+__global__ void __launch_bounds__(256) fx_split_rows_kernel(int64_t L, int64_t Lp, const double* __restrict__ A,
+                                                            int2* __restrict__ Ai, int* __restrict__ ea) {
+  __shared__ int sh[32];
+  const int i = blockIdx.x;
+  const double* row = A + (int64_t)i * L;
+  int e = INT_MIN;
+  for (int64_t c = threadIdx.x; c < L; c += blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(row[c]) & 0x7FFFFFFFFFFFFFFFull;
+    if (b) e = max(e, fx_expo_bits(b));
+  }
+  e = block_max_int(e, sh);
+  if (e == INT_MIN) e = 0;
+  if (threadIdx.x == 0) ea[i] = e;
+  int2* out = Ai + (int64_t)i * Lp;
+  for (int64_t c = threadIdx.x; c < Lp; c += blockDim.x) out[c] = fx_split(c < L ? fx_fixed(row[c], 0, e) : 0);
+}
+
+// one block, integer operations only: *fout = F with |x_k| 2^(ex_k) < 2^F for every k (ex may be
+// NULL), FX_NONE when x is zero, FX_BAD when x has a non-finite entry
+__global__ void __launch_bounds__(1024) fx_exponent_kernel(int64_t len, const double* __restrict__ x,
+                                                           const int* __restrict__ ex, int* __restrict__ fout,
+                                                           const int32_t* __restrict__ done) {
+  if (done && *done) return;
+  __shared__ int sh[32];
+  int f = INT_MIN, bad = 0;
+  constexpr int U = 8;                      // loads in flight per thread
+  for (int64_t j0 = 0; j0 < len; j0 += (int64_t)U * blockDim.x) {
+    unsigned long long b[U];
+    int e[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t j = j0 + (int64_t)u * blockDim.x + threadIdx.x;
+      b[u] = j < len ? (unsigned long long)__double_as_longlong(x[j]) & 0x7FFFFFFFFFFFFFFFull : 0ull;
+      e[u] = (ex && j < len) ? ex[j] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (b[u] >= 0x7FF0000000000000ull) bad = 1;
+      else if (b[u]) f = max(f, fx_expo_bits(b[u]) + e[u]);
+    }
+  }
+  f = block_max_int(f, sh);
+  bad = block_max_int(bad, sh);
+  if (threadIdx.x == 0) *fout = bad ? FX_BAD : f;
+}
+
+// A x from the digits: the slab / row-block layout of rows_gemv_kernel (partial sums
+// part[s * m + i] for slab s), two rows in flight per warp
+template <bool STREAM>
+__global__ void __launch_bounds__(GV_WARPS * 32)
+fx_rows_gemv_kernel(const int2* __restrict__ Ai, const int* __restrict__ ea, int m, int64_t L, int64_t Lp,
+                    const double* __restrict__ x, const int* __restrict__ fptr, double* __restrict__ part, int SW,
+                    int R, const int32_t* __restrict__ done) {
+  if (done && *done) return;
+  const uint64_t pol = STREAM ? evict_first_policy() : 0;
+  __shared__ __align__(16) int2 xs[GV_SWMAX];
+  const int s = blockIdx.x;
+  const int64_t k0 = (int64_t)s * SW;
+  const int lenp = (int)((Lp - k0) < (int64_t)SW ? (Lp - k0) : (int64_t)SW);   // even
+  const int f = *fptr;
+  const int F = (f == FX_BAD || f == FX_NONE) ? 0 : f;
+  for (int q = threadIdx.x; q < lenp; q += blockDim.x)    // the digits of x 2^-F for this slab
+    xs[q] = fx_split(k0 + q < L ? fx_fixed(x[k0 + q], 0, F) : 0);
+  __syncthreads();
+  const int np = lenp >> 1;
+  const int4* xv = reinterpret_cast<const int4*>(xs);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rbase = blockIdx.y * R;
+  for (int t = warp; t < R; t += 2 * GV_WARPS) {
+    const int ia = rbase + t;
+    if (ia >= m) break;
+    const int ib = rbase + t + GV_WARPS;
+    const bool hb = (t + GV_WARPS < R) && (ib < m);
+    const int4* va = reinterpret_cast<const int4*>(Ai + (int64_t)ia * Lp + k0);
+    long long a1 = 0, a2 = 0, b1 = 0, b2 = 0;
+    if (hb) {   // warp-uniform
+      const int4* vb = reinterpret_cast<const int4*>(Ai + (int64_t)ib * Lp + k0);
+      int q = lane;
+      for (; q + 32 < np; q += 64) {
+        const int4 u0 = STREAM ? ld_stream_i4(va + q, pol) : __ldg(va + q);
+        const int4 u1 = STREAM ? ld_stream_i4(va + q + 32, pol) : __ldg(va + q + 32);
+        const int4 v0 = STREAM ? ld_stream_i4(vb + q, pol) : __ldg(vb + q);
+        const int4 v1 = STREAM ? ld_stream_i4(vb + q + 32, pol) : __ldg(vb + q + 32);
+        const int4 w0 = xv[q], w1 = xv[q + 32];
+        fx_acc2(a1, a2, u0, w0);
+        fx_acc2(b1, b2, v0, w0);
+        fx_acc2(a1, a2, u1, w1);
+        fx_acc2(b1, b2, v1, w1);
+      }
+      for (; q < np; q += 32) {
+        const int4 u0 = STREAM ? ld_stream_i4(va + q, pol) : __ldg(va + q);
+        const int4 v0 = STREAM ? ld_stream_i4(vb + q, pol) : __ldg(vb + q);
+        fx_acc2(a1, a2, u0, xv[q]);
+        fx_acc2(b1, b2, v0, xv[q]);
+      }
+    } else {
+      int q = lane;
+      for (; q + 96 < np; q += 128) {
+        const int4 u0 = STREAM ? ld_stream_i4(va + q, pol) : __ldg(va + q);
+        const int4 u1 = STREAM ? ld_stream_i4(va + q + 32, pol) : __ldg(va + q + 32);
+        const int4 u2 = STREAM ? ld_stream_i4(va + q + 64, pol) : __ldg(va + q + 64);
+        const int4 u3 = STREAM ? ld_stream_i4(va + q + 96, pol) : __ldg(va + q + 96);
+        fx_acc2(a1, a2, u0, xv[q]);
+        fx_acc2(b1, b2, u1, xv[q + 32]);
+        fx_acc2(a1, a2, u2, xv[q + 64]);
+        fx_acc2(b1, b2, u3, xv[q + 96]);
+      }
+      for (; q < np; q += 32) fx_acc2(a1, a2, STREAM ? ld_stream_i4(va + q, pol) : __ldg(va + q), xv[q]);
+    }
+    // per lane at most 2 * ceil(np / 32) <= 128 terms per accumulator (SW <= 4096)
+    double da = fx_value(a1, a2), db = fx_value(b1, b2);
+    if (!hb) {
+      da += db;
+      db = 0.0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      da += __shfl_xor_sync(0xffffffffu, da, o);
+      db += __shfl_xor_sync(0xffffffffu, db, o);
+    }
+    if (lane == 0) {
+      part[(int64_t)s * m + ia] = fx_out(da, f, ea[ia]);
+      if (hb) part[(int64_t)s * m + ib] = fx_out(db, f, ea[ib]);
+    }
+  }
+}
+
+// A^T y from the digits (y's digits carry the row exponents): the row-group layout of
+// rows_gemvT_kernel (partials part[g * L + c]), two columns per thread, and the same
+// last-CTA unpack into the symmetric matrix Y
+template <bool STREAM>
+__global__ void __launch_bounds__(GT_THREADS)
+fx_rows_gemvT_kernel(const int2* __restrict__ Ai, const int* __restrict__ ea, int m, int64_t L, int64_t Lp,
+                     const double* __restrict__ y, const int* __restrict__ fptr, double* __restrict__ part,
+                     int rows_per_group, const int32_t* __restrict__ done, int n, double scale,
+                     double* __restrict__ Y, unsigned int* __restrict__ tickets) {
+  if (done && *done) return;
+  const uint64_t pol = STREAM ? evict_first_policy() : 0;
+  __shared__ int2 ys[FX_FLUSH];
+  const int g = blockIdx.y;
+  const int i0 = g * rows_per_group;
+  const int i1 = min(m, i0 + rows_per_group);
+  const int64_t c = ((int64_t)blockIdx.x * GT_THREADS + threadIdx.x) * 2;   // c < Lp: c < L
+  const int f = *fptr;
+  const int F = (f == FX_BAD || f == FX_NONE) ? 0 : f;
+  const int4* base = reinterpret_cast<const int4*>(Ai + c);
+  const int64_t stv = Lp / 2;
+  double d0 = 0.0, d1 = 0.0;
+  for (int ic = i0; ic < i1; ic += FX_FLUSH) {
+    const int ie = min(i1, ic + FX_FLUSH);
+    __syncthreads();
+    for (int q = threadIdx.x; q < ie - ic; q += blockDim.x)   // digits of y_i 2^(e_i - F)
+      ys[q] = fx_split(fx_fixed(y[ic + q], ea[ic + q], F));
+    __syncthreads();
+    if (c < Lp) {
+      long long p1 = 0, p2 = 0, q1 = 0, q2 = 0;
+      int i = ic;
+      for (; i + 7 < ie; i += 8) {
+        int4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int4* ptr = base + (int64_t)(i + u) * stv;
+          v[u] = STREAM ? ld_stream_i4(ptr, pol) : __ldg(ptr);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int2 w = ys[i + u - ic];
+          p1 += (long long)v[u].x * w.x;
+          p2 += (long long)v[u].x * w.y + (long long)v[u].y * w.x;
+          q1 += (long long)v[u].z * w.x;
+          q2 += (long long)v[u].z * w.y + (long long)v[u].w * w.x;
+        }
+      }
+      for (; i < ie; ++i) {
+        const int4* ptr = base + (int64_t)i * stv;
+        const int4 v = STREAM ? ld_stream_i4(ptr, pol) : __ldg(ptr);
+        const int2 w = ys[i - ic];
+        p1 += (long long)v.x * w.x;
+        p2 += (long long)v.x * w.y + (long long)v.y * w.x;
+        q1 += (long long)v.z * w.x;
+        q2 += (long long)v.z * w.y + (long long)v.w * w.x;
+      }
+      d0 += fx_value(p1, p2);
+      d1 += fx_value(q1, q2);
+    }
+  }
+  if (c < Lp) {
+    part[(int64_t)g * L + c] = fx_out(d0, f, 0);
+    if (c + 1 < L) part[(int64_t)g * L + c + 1] = fx_out(d1, f, 0);
+  }
+  if (!Y) return;
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(tickets + blockIdx.x, 1u) == gridDim.y - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int64_t c0 = (int64_t)blockIdx.x * GT_THREADS * 2;
+  for (int u = threadIdx.x; u < GT_THREADS * 2; u += GT_THREADS) {
+    const int64_t cc = c0 + u;
+    if (cc >= L) break;
+    double sum = 0.0;
+    for (int gg = 0; gg < (int)gridDim.y; ++gg) sum += __ldcg(part + (int64_t)gg * L + cc);
+    int a, b;
+    svec_pos(n, cc, a, b);
+    const double v = (a == b ? sum : sum * WC_RSQRT2) * scale;
+    Y[a + (int64_t)b * n] = v;
+    Y[b + (int64_t)a * n] = v;
+  }
+  if (threadIdx.x == 0) tickets[blockIdx.x] = 0u;
+}
+
 }  // namespace
 
 int rows_gemv_slabs(int m, int64_t L, int esize) { return gv_plan(m, L, esize).slabs; }
@@ -457,6 +750,84 @@ template <typename T>
 void rows_gemvT_unpack(cudaStream_t st, const T* A, int m, int64_t L, const T* p, T* part, int groups, int n,
                        double scale, T* Y, unsigned int* tickets, const int32_t* done, int64_t* launches) {
   rows_gemvT_impl<T>(st, A, m, L, p, part, groups, done, launches, n, scale, Y, tickets);
+}
+
+int64_t fx_row_len(int64_t L) { return (L + 1) & ~(int64_t)1; }
+
+static GvPlan fx_plan(int m, int64_t L);
+int fx_rows_gemv_slabs(int m, int64_t L) { return fx_plan(m, L).slabs; }
+
+void fx_split_rows(cudaStream_t st, const double* A, int m, int64_t L, int2* Ai, int* ea, int64_t* launches) {
+  fx_split_rows_kernel<<<m, 256, 0, st>>>(L, fx_row_len(L), A, Ai, ea);
+  if (launches) ++*launches;
+}
+
+void fx_exponent(cudaStream_t st, const double* x, const int* ex, int64_t len, int* f, const int32_t* done,
+                 int64_t* launches) {
+  fx_exponent_kernel<<<1, 1024, 0, st>>>(len, x, ex, f, done);
+  if (launches) ++*launches;
+}
+
+// Launch shape of fx_rows_gemv: the CTAs of one launch are all resident at once (CTAs per SM
+// from the occupancy of the kernel), so the (slab width, rows per CTA) pair is chosen to fill
+// whole waves of resident CTAs: a partial last wave leaves most SMs idle while it runs.
+static GvPlan fx_plan(int m, int64_t L) {
+  static int occ = 0;
+  if (occ == 0) {
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fx_rows_gemv_kernel<true>, GV_WARPS * 32, 0) != cudaSuccess ||
+        o < 1) {
+      cudaGetLastError();
+      o = 1;
+    }
+    occ = o;
+  }
+  GvPlan P = gv_plan(m, L, 8);
+  if (!P.stream) return P;            // L2-resident: the plan of rows_gemv<double>
+  // the widest slab (fewest partial sums) whose best row split fills >= 95% of its waves, else
+  // the best-filling split
+  const int64_t cap = (int64_t)occ * g_num_sms;
+  double best = -1.0;
+  bool good = false;
+  for (int sw = GV_SWMAX; sw >= 1024; sw /= 2) {
+    const int64_t slabs = (L + sw - 1) / sw;
+    for (int R = 8; R <= 64; ++R) {
+      const int64_t units = slabs * ((m + R - 1) / R);
+      const int64_t waves = (units + cap - 1) / cap;
+      const double eff = (double)units / (double)(waves * cap);
+      if (!good && eff > best + 1e-9) { best = eff; P.SW = sw; P.R = R; P.slabs = (int)slabs; }
+    }
+    if (best >= 0.95) good = true;
+  }
+  return P;
+}
+
+void fx_rows_gemv(cudaStream_t st, const int2* Ai, const int* ea, int m, int64_t L, const double* x, const int* f,
+                  double* part, const int32_t* done, int64_t* launches) {
+  const GvPlan P = fx_plan(m, L);
+  dim3 grid(P.slabs, (m + P.R - 1) / P.R);
+  const int64_t Lp = fx_row_len(L);
+  if (P.stream)
+    fx_rows_gemv_kernel<true><<<grid, GV_WARPS * 32, 0, st>>>(Ai, ea, m, L, Lp, x, f, part, P.SW, P.R, done);
+  else
+    fx_rows_gemv_kernel<false><<<grid, GV_WARPS * 32, 0, st>>>(Ai, ea, m, L, Lp, x, f, part, P.SW, P.R, done);
+  if (launches) ++*launches;
+}
+
+void fx_rows_gemvT_unpack(cudaStream_t st, const int2* Ai, const int* ea, int m, int64_t L, const double* y,
+                          const int* f, double* part, int groups, int n, double scale, double* Y,
+                          unsigned int* tickets, const int32_t* done, int64_t* launches) {
+  const int rpg = (m + groups - 1) / groups;
+  const int64_t Lp = fx_row_len(L);
+  const bool stream = (int64_t)m * L * 8 > (int64_t)64 << 20;
+  dim3 grid((unsigned)((Lp / 2 + GT_THREADS - 1) / GT_THREADS), groups);   // = rows_gemvT_blocks(L, 8)
+  if (stream)
+    fx_rows_gemvT_kernel<true><<<grid, GT_THREADS, 0, st>>>(Ai, ea, m, L, Lp, y, f, part, rpg, done, n, scale, Y,
+                                                            tickets);
+  else
+    fx_rows_gemvT_kernel<false><<<grid, GT_THREADS, 0, st>>>(Ai, ea, m, L, Lp, y, f, part, rpg, done, n, scale, Y,
+                                                             tickets);
+  if (launches) ++*launches;
 }
 
 int rows_gemvT_blocks(int64_t L, int esize) {

@@ -175,27 +175,52 @@ __device__ __forceinline__ void pair_of(int q, int& s, int& t) {
 // the rounding of N (at most 2^-56).  Integer arithmetic only (no FP64 pipe); the BF16 bits of
 // -64..64 come from a shared-memory table.
 
+// max_k |op(X)[r, k]| as IEEE bits (monotone for non-negative doubles), over blocks of 32 rows x
+// 256 entries of K: lanes run along whichever axis is contiguous, and one atomic per row and warp
+// merges the blocks.
 __global__ void __launch_bounds__(256) rowmax_kernel(int R, int K, const double* __restrict__ X, int64_t rs,
                                                      int64_t ks, unsigned long long* __restrict__ rmax,
                                                      const int32_t* __restrict__ done) {
   if (done && *done) return;
-  __shared__ unsigned long long sm[32];
-  const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 256, tid = threadIdx.x;
-  if (tid < 32) sm[tid] = 0ull;
-  __syncthreads();
-  const bool rows_contig = (rs == 1);
-  for (int q = tid; q < 32 * 256; q += 256) {
-    int r, k;
-    if (rows_contig) { r = q % 32; k = q / 32; } else { k = q % 256; r = q / 256; }
-    const int gr = r0 + r, gk = k0 + k;
-    if (gr < R && gk < K) {
-      const unsigned long long b = (unsigned long long)__double_as_longlong(X[(int64_t)gr * rs + (int64_t)gk * ks]) &
-                                   0x7FFFFFFFFFFFFFFFull;
-      if (b) atomicMax(&sm[r], b);
+  __shared__ unsigned long long sm[8][32];
+  const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 256, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
+  if (rs == 1) {                           // rows contiguous: lane <-> row, the warps split K
+    const int gr = r0 + lane;
+    unsigned long long mx = 0ull;
+    if (gr < R)
+      for (int k = warp; k < 256; k += 8) {
+        const int gk = k0 + k;
+        if (gk >= K) break;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(X[gr + (int64_t)gk * ks]) & ABS;
+        mx = b > mx ? b : mx;
+      }
+    sm[warp][lane] = mx;
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int w = 1; w < 8; ++w) mx = sm[w][lane] > mx ? sm[w][lane] : mx;
+      if (gr < R && mx) atomicMax(&rmax[gr], mx);
+    }
+  } else {                                 // K contiguous: warp <-> row, lanes along K
+    for (int r = warp; r < 32; r += 8) {
+      const int gr = r0 + r;
+      if (gr >= R) break;
+      unsigned long long mx = 0ull;
+      for (int k = lane; k < 256; k += 32) {
+        const int gk = k0 + k;
+        if (gk >= K) break;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(X[(int64_t)gr * rs + (int64_t)gk * ks]) & ABS;
+        mx = b > mx ? b : mx;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = v > mx ? v : mx;
+      }
+      if (lane == 0 && mx) atomicMax(&rmax[gr], mx);
     }
   }
-  __syncthreads();
-  if (tid < 32 && r0 + tid < R && sm[tid]) atomicMax(&rmax[r0 + tid], sm[tid]);
 }
 
 __device__ __forceinline__ int row_exponent(unsigned long long mbits) {
@@ -203,6 +228,23 @@ __device__ __forceinline__ int row_exponent(unsigned long long mbits) {
   return ilogb(__longlong_as_double((long long)mbits)) + 1;
 }
 
+// N = round(x 2^(55 - e)) from the IEEE fields of x: |x| = m 2^(ex - 1075), m < 2^53
+__device__ __forceinline__ long long fixed_point(double x, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  if (ex) m |= 1ull << 52;
+  const int sh = (ex ? ex : 1) - 1075 + 55 - e;
+  long long Nv;
+  if (m == 0ull || sh <= -64) Nv = 0;
+  else if (sh >= 0) Nv = (long long)(m << sh);                         // sh <= 2: |N| < 2^55
+  else Nv = (long long)((m + (1ull << (-sh - 1))) >> (-sh));          // rounded
+  return (b >> 63) ? -Nv : Nv;
+}
+
+// One block per 32 rows x BK entries of op(X): the tile is staged in shared memory (coalesced
+// whichever of rows or K is contiguous), then each thread turns 8 consecutive entries of one
+// row into their 8 slices and writes each slice plane with one 16-byte store.
 __global__ void __launch_bounds__(256) slice_kernel(int R, int K, int Kpad, const double* __restrict__ X,
                                                     int64_t rs, int64_t ks,
                                                     const unsigned long long* __restrict__ rmax,
@@ -227,30 +269,31 @@ __global__ void __launch_bounds__(256) slice_kernel(int R, int K, int Kpad, cons
     tile[r][k] = (gr < R && gk < K) ? X[(int64_t)gr * rs + (int64_t)gk * ks] : 0.0;
   }
   __syncthreads();
-  const int64_t plane = (int64_t)R * Kpad;
-  for (int q = tid; q < 32 * BK; q += 256) {
-    const int r = q / BK, k = q % BK;
-    const int gr = r0 + r;
-    if (gr >= R) continue;
-    // N = round(x 2^(55 - e)) from the IEEE fields: |x| = m 2^(ex - 1075), m < 2^53
-    const unsigned long long b = (unsigned long long)__double_as_longlong(tile[r][k]);
-    const int ex = (int)((b >> 52) & 0x7FF);
-    unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-    if (ex) m |= 1ull << 52;
-    const int sh = (ex ? ex : 1) - 1075 + 55 - rexp[r];
-    long long Nv;
-    if (m == 0ull || sh <= -64) Nv = 0;
-    else if (sh >= 0) Nv = (long long)(m << sh);                       // sh <= 2: |N| < 2^55
-    else Nv = (long long)((m + (1ull << (-sh - 1))) >> (-sh));        // rounded
-    if (b >> 63) Nv = -Nv;
-    __nv_bfloat16* o = out + (int64_t)gr * Kpad + k0 + k;
+  static_assert(BK == 64, "8 threads x 8 entries per row");
+  const int r = tid >> 3, g = tid & 7;
+  const int gr = r0 + r;
+  if (gr >= R) return;
+  long long Nv[8];
 #pragma unroll
-    for (int sidx = S - 1; sidx >= 1; --sidx) {                        // a_8 .. a_2
-      const long long a = ((Nv + 64) & 127) - 64;
-      o[sidx * plane] = __ushort_as_bfloat16(bf[a + 64]);
-      Nv = (Nv - a) >> 7;                                              // exact
+  for (int j = 0; j < 8; ++j) Nv[j] = fixed_point(tile[r][g * 8 + j], rexp[r]);
+  // Kpad is a multiple of BK, so every row, plane and group of 8 starts on 16 bytes
+  const int64_t plane16 = (int64_t)R * Kpad / 8;
+  uint4* o = reinterpret_cast<uint4*>(out + (int64_t)gr * Kpad + k0 + g * 8);
+#pragma unroll
+  for (int sidx = S - 1; sidx >= 0; --sidx) {                           // a_8 .. a_1
+    uint32_t wv[4];
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      long long a0 = Nv[j], a1 = Nv[j + 1];
+      if (sidx > 0) {
+        a0 = ((Nv[j] + 64) & 127) - 64;
+        a1 = ((Nv[j + 1] + 64) & 127) - 64;
+        Nv[j] = (Nv[j] - a0) >> 7;                                     // exact
+        Nv[j + 1] = (Nv[j + 1] - a1) >> 7;
+      }                                                                 // else a_1, |a_1| <= 64
+      wv[j / 2] = (uint32_t)bf[a0 + 64] | ((uint32_t)bf[a1 + 64] << 16);
     }
-    o[0] = __ushort_as_bfloat16(bf[Nv + 64]);                          // a_1, |a_1| <= 64
+    o[sidx * plane16] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
   }
 }
 
@@ -579,11 +622,19 @@ cudaError_t gemm_f64_tc_one(cudaStream_t st, bool tA, bool tB, int M, int N, int
   if (e != cudaSuccess) return e;
   const int64_t ars = tA ? lda : 1, aks = tA ? 1 : lda, brs = tB ? 1 : ldb, bks = tB ? ldb : 1;
   const unsigned kb = (unsigned)((std::max(K, 1) + 255) / 256), kp64 = (unsigned)(Kp / BK);
+  // op(A) = op(B)^T (C = X^T X or X X^T): one operand, sliced once
+  const bool same = (A == B && M == N && ars == brs && aks == bks);
   rowmax_kernel<<<dim3((M + 31) / 32, kb), 256, 0, st>>>(M, K, A, ars, aks, rmA, done);
-  rowmax_kernel<<<dim3((N + 31) / 32, kb), 256, 0, st>>>(N, K, B, brs, bks, rmB, done);
   slice_kernel<<<dim3((M + 31) / 32, kp64), 256, 0, st>>>(M, K, Kp, A, ars, aks, rmA, sa, ea, done);
-  slice_kernel<<<dim3((N + 31) / 32, kp64), 256, 0, st>>>(N, K, Kp, B, brs, bks, rmB, sb, eb, done);
-  if (launches) *launches += 4;
+  if (launches) *launches += 2;
+  if (same) {
+    sb = sa;
+    eb = ea;
+  } else {
+    rowmax_kernel<<<dim3((N + 31) / 32, kb), 256, 0, st>>>(N, K, B, brs, bks, rmB, done);
+    slice_kernel<<<dim3((N + 31) / 32, kp64), 256, 0, st>>>(N, K, Kp, B, brs, bks, rmB, sb, eb, done);
+    if (launches) *launches += 2;
+  }
   CUtensorMap mapA, mapB;
   e = make_map(&mapA, sa, M, Kp);
   if (e == cudaSuccess) e = make_map(&mapB, sb, N, Kp);

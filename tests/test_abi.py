@@ -55,7 +55,8 @@ int main(void) {
          offsetof(sdp_newton_info, prof_A32_launches));
   printf("%zu\n", offsetof(sdp_options, inner_rtol));
   printf("%zu %zu %zu\n", offsetof(sdp_options, pcg_start), sizeof(sdp_ipm_info), offsetof(sdp_ipm_info, total_ms));
-  printf("%zu %zu\n", offsetof(sdp_options, tc_products), offsetof(sdp_options, krylov));
+  printf("%zu %zu %zu\n", offsetof(sdp_options, tc_products), offsetof(sdp_options, krylov),
+         offsetof(sdp_options, int_passes));
   return 0;
 }
 '''
@@ -79,13 +80,14 @@ int main(void) {
     assert vals[10] == _native.sdp_ipm_info.total_ms.offset
     assert vals[11] == _native.sdp_options.tc_products.offset
     assert vals[12] == _native.sdp_options.krylov.offset
+    assert vals[13] == _native.sdp_options.int_passes.offset
 
 
 def test_default_options_and_setup_errors(lib):
     """Host-side validation needs no GPU: bad shapes are rejected before any CUDA call."""
     from paper_2407_14013_gb300 import _native
     o = _native.sdp_default_options()
-    assert o.r_hat == 10 and o.max_pcg == 2000 and o.newton_rtol == 1e-12
+    assert o.r_hat == 10 and o.max_pcg == 2000 and o.newton_rtol == 1e-12 and o.int_passes == 1
     p = _native.sdp_problem()
     p.n, p.m, p.kind = 1, 1, _native.SDP_A_DIAG
     with pytest.raises(_native.SdpError) as e:

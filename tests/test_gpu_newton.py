@@ -321,6 +321,41 @@ def test_tensor_core_products_match_fp64_mma_and_oracle(name, mk, rt, rh):
     s0.close()
 
 
+def _row_scaled(prob, seed, spread):
+    """The same constraints with row i multiplied by 10^u_i, u_i ~ U(-spread, spread): rows of
+    very different size exercise the per-row exponents of the integer passes."""
+    g = np.random.default_rng(seed)
+    prob.a_dense = prob.a_dense * (10.0 ** g.uniform(-spread, spread, prob.m))[:, None]
+    return prob
+
+
+INT_CASES = [
+    # name, problem factory, r_true, r_hat; odd n(n+1)/2 (padded rows), streamed A (> 64 MB)
+    ("sensing10_odd_rows", lambda: W.sensing(10, 30, 2, 131), 2, 3),
+    ("sensing37_scaled_rows", lambda: _row_scaled(W.sensing(37, 150, 3, 132), 7, 1.0), 3, 5),
+    ("sensing120_streamed", lambda: W.sensing(120, 1500, 2, 133), 2, 4),
+]
+
+
+@pytest.mark.parametrize("name,mk,rt,rh", INT_CASES, ids=[c[0] for c in INT_CASES])
+def test_integer_passes_match_fp64_passes_and_oracle(name, mk, rt, rh):
+    """The FP64 operator's passes over A on the integer copy (exact int64 sums of two-digit
+    products) give the same Newton direction as FP64 FMAs over A, to far below the FP64
+    tolerance, and the oracle's plain definition to it; both stop at the same 1e-12 test."""
+    prob = mk()
+    sp = W.scaling_point(prob.n, rt, 1e-3, 950 + prob.n)
+    Ct, bt = W.newton_rhs(prob.n, prob.m, 951 + prob.n)
+    s1, (X1, y1, S1, i1) = gpu_solve(prob, sp, Ct, bt, r_hat=rh, int_passes=True)
+    s0, (X0, y0, S0, i0) = gpu_solve(prob, sp, Ct, bt, r_hat=rh, int_passes=False)
+    assert i1.converged and i0.converged and i1.r == rt
+    assert abs(i1.pcg_iters - i0.pcg_iters) <= max(2, i0.pcg_iters // 20)   # rounding differs, not the method
+    assert rel(X1, X0) < 1e-10 and rel(y1, y0) < 1e-10 and rel(S1, S0) < 1e-10
+    rX, ry, rS = onewton.newton_direct(prob, w_of(sp), Ct, bt)
+    assert rel(X1, rX) < TOL and rel(y1, ry) < TOL and rel(S1, rS) < TOL
+    s1.close()
+    s0.close()
+
+
 def test_edge_cases_diag_and_sparse_kinds():
     """DIAG at r = 1 (d = n = m: the d-space core with the explicit B of the DIAG kind) and at
     r = n - 1; SPARSE_COO with one constraint and at r = 1; each against the plain definition."""
