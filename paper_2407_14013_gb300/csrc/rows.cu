@@ -277,16 +277,41 @@ rows_gemvT_kernel(const T* __restrict__ A, int m, int64_t L, const T* __restrict
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // the group partials of this CTA's columns (up to four per thread), summed in group order with
+  // sixteen loads in flight
   const int per = VEC ? V16<T>::W : 1;
   const int64_t c0 = (int64_t)blockIdx.x * GT_THREADS * per;
-  for (int u = threadIdx.x; u < GT_THREADS * per; u += GT_THREADS) {
-    const int64_t c = c0 + u;
-    if (c >= L) break;
-    double sum = 0.0;
-    for (int gg = 0; gg < (int)gridDim.y; ++gg) sum += (double)__ldcg(part + (int64_t)gg * L + c);
+  const int G = (int)gridDim.y;
+  int64_t cols[4];
+  bool has[4];
+  double sum[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    cols[k] = c0 + (int64_t)k * GT_THREADS + threadIdx.x;
+    has[k] = (k < per) && (cols[k] < L);
+  }
+  int gg = 0;
+  for (; gg + 3 < G; gg += 4) {
+    double v[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[j][k] = has[k] ? (double)__ldcg(part + (int64_t)(gg + j) * L + cols[k]) : 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) sum[k] += v[j][k];
+  }
+  for (; gg < G; ++gg)
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (has[k]) sum[k] += (double)__ldcg(part + (int64_t)gg * L + cols[k]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (!has[k]) continue;
     int a, b;
-    svec_pos(n, c, a, b);
-    const T v = (T)((a == b ? sum : sum * WC_RSQRT2) * scale);
+    svec_pos(n, cols[k], a, b);
+    const T v = (T)((a == b ? sum[k] : sum[k] * WC_RSQRT2) * scale);
     Y[a + (int64_t)b * n] = v;
     Y[b + (int64_t)a * n] = v;
   }
@@ -647,14 +672,36 @@ fx_rows_gemvT_kernel(const int2* __restrict__ Ai, const int* __restrict__ ea, in
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // the group partials of this CTA's columns, summed in group order with eight loads in flight
   const int64_t c0 = (int64_t)blockIdx.x * GT_THREADS * 2;
-  for (int u = threadIdx.x; u < GT_THREADS * 2; u += GT_THREADS) {
-    const int64_t cc = c0 + u;
+  const int G = (int)gridDim.y;
+  const int64_t ca = c0 + threadIdx.x, cb = c0 + GT_THREADS + threadIdx.x;
+  const bool ha = ca < L, hbb = cb < L;
+  double sa = 0.0, sb = 0.0;
+  int gg = 0;
+  for (; gg + 7 < G; gg += 8) {
+    double va[8], vb[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      va[k] = ha ? __ldcg(part + (int64_t)(gg + k) * L + ca) : 0.0;
+      vb[k] = hbb ? __ldcg(part + (int64_t)(gg + k) * L + cb) : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      sa += va[k];
+      sb += vb[k];
+    }
+  }
+  for (; gg < G; ++gg) {
+    if (ha) sa += __ldcg(part + (int64_t)gg * L + ca);
+    if (hbb) sb += __ldcg(part + (int64_t)gg * L + cb);
+  }
+  for (int h2 = 0; h2 < 2; ++h2) {
+    const int64_t cc = h2 ? cb : ca;
     if (cc >= L) break;
-    double sum = 0.0;
-    for (int gg = 0; gg < (int)gridDim.y; ++gg) sum += __ldcg(part + (int64_t)gg * L + cc);
     int a, b;
     svec_pos(n, cc, a, b);
+    const double sum = h2 ? sb : sa;
     const double v = (a == b ? sum : sum * WC_RSQRT2) * scale;
     Y[a + (int64_t)b * n] = v;
     Y[b + (int64_t)a * n] = v;
