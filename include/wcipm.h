@@ -143,7 +143,9 @@ typedef struct {
                             entry) and sum exact int64 digit products, whose error is within the
                             FP64 dot-product bound measured against the largest entry of the row
                             and of the vector; GB300's integer pipe keeps up with HBM where its
-                            FP64 pipe does not.  0 = FP64 FMAs over the caller's A (no copy).   */
+                            FP64 pipe does not.  The products E Y E of the operator (n < 512) are
+                            summed the same way.  0 = FP64 FMAs over the caller's A (no copy)
+                            and FP64 MMA products.                                              */
 } sdp_options;
 
 typedef struct {

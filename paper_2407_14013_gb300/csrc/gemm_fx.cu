@@ -1,0 +1,134 @@
+// Small dense FP64 products C = A B (column-major, no transposes) summed exactly in integers.
+//
+// GB300 issues FP64 FMAs at 2 per SM per clock (1.26 TFLOP/s for the GPU), so the n^3 products of
+// the FP64 operator (E Y E of Section 5 at n of a few hundred) are bound by the FP64 pipe.  Here
+// every row i of A is scaled by 2^-ea_i and every column j of B by 2^-eb_j (2^ea_i > max_k |A_ik|,
+// 2^eb_j > max_k |B_kj|), both are written as two int32 digits (fx.cuh), and
+//   C_ij = 2^(ea_i + eb_j) sum_k (hi_ik hi'_kj 2^-52 + (hi_ik lo'_kj + lo_ik hi'_kj) 2^-78)
+// with both sums exact in int64 (flushed to FP64 every FX_FLUSH terms) on the integer pipe.  The
+// error of an entry is within about K 2^-53 2^(ea_i + eb_j): the FP64 bound of a K-term dot
+// product measured against the largest entry of the row of A and of the column of B.
+//
+// One CTA per 16 x 16 output tile, one output per thread.  A CTA reads its 16-row panel of A and
+// 16-column panel of B twice from L2: once for their exponents (so no separate launch is needed),
+// then in K-chunks of 128 that it splits into digits in shared memory.  LOWER skips tiles above
+// the diagonal and writes only entries with i >= j.  A row or column with a non-finite entry
+// gives NaN outputs.
+#include "common.cuh"
+#include "fx.cuh"
+#include "kernels.h"
+
+namespace wc {
+
+namespace {
+
+constexpr int TB = 16;
+constexpr int KC = 128;
+constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
+constexpr unsigned long long INF_BITS = 0x7FF0000000000000ull;
+
+__global__ void __launch_bounds__(TB * TB)
+fx_gemm_kernel(int M, int N, int K, const double* __restrict__ A, int64_t lda, const double* __restrict__ B,
+               int64_t ldb, double* __restrict__ C, int64_t ldc, int lower, const int32_t* __restrict__ done) {
+  if (done && *done) return;
+  const int i0 = blockIdx.x * TB, j0 = blockIdx.y * TB;
+  if (lower && i0 + TB - 1 < j0) return;            // tile strictly above the diagonal
+  __shared__ int2 As[KC][TB];
+  __shared__ int2 Bs[KC][TB + 1];
+  __shared__ int ered[TB][TB + 1];
+  __shared__ int ea[TB], eb[TB];
+  const int t = threadIdx.x;
+  // ---- exponents: rows of the A panel (lanes along i), columns of the B panel (lanes along k)
+  {
+    const int r = t & 15, part = t >> 4;
+    const int gi = i0 + r;
+    int e = INT_MIN;
+    if (gi < M)
+      for (int k = part; k < K; k += 16) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(A[gi + (int64_t)k * lda]) & ABS;
+        if (b >= INF_BITS) e = FX_BAD;
+        else if (b && e != FX_BAD) e = max(e, fx_expo_bits(b));
+      }
+    ered[part][r] = e;
+    const int c = t >> 4, kp = t & 15;
+    const int gj = j0 + c;
+    int f = INT_MIN;
+    if (gj < N)
+      for (int k = kp; k < K; k += 16) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(B[k + (int64_t)gj * ldb]) & ABS;
+        if (b >= INF_BITS) f = FX_BAD;
+        else if (b && f != FX_BAD) f = max(f, fx_expo_bits(b));
+      }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {   // within the 16 lanes of column c (FX_BAD is the largest int)
+      const int g = __shfl_xor_sync(0xffffffffu, f, o);
+      f = max(f, g);
+    }
+    if (kp == 0) eb[c] = f;
+    __syncthreads();
+    if (t < TB) {
+      int m = INT_MIN;
+      for (int p = 0; p < 16; ++p) m = max(m, ered[p][t]);
+      ea[t] = m;
+    }
+    __syncthreads();
+  }
+  const int ti = t & 15, tj = t >> 4;
+  const int ra = ea[ti], rb = eb[tj];
+  long long T1 = 0, T2 = 0;
+  double acc = 0.0;
+  int since = 0;
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    const int kc = min(KC, K - k0);
+    __syncthreads();
+    for (int q = t; q < TB * kc; q += TB * TB) {       // A chunk: lanes along i
+      const int r = q & 15, k = q >> 4;
+      const int gi = i0 + r;
+      const int F = ea[r];
+      const double v = (gi < M && F != FX_BAD) ? A[gi + (int64_t)(k0 + k) * lda] : 0.0;
+      As[k][r] = fx_split(F == INT_MIN ? 0 : fx_fixed(v, 0, F));
+    }
+    for (int q = t; q < TB * kc; q += TB * TB) {       // B chunk: lanes along k
+      const int k = q % kc, c = q / kc;
+      const int gj = j0 + c;
+      const int F = eb[c];
+      const double v = (gj < N && F != FX_BAD) ? B[(k0 + k) + (int64_t)gj * ldb] : 0.0;
+      Bs[k][c] = fx_split(F == INT_MIN ? 0 : fx_fixed(v, 0, F));
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < kc; ++k) {
+      const int2 a = As[k][ti], b = Bs[k][tj];
+      T1 += (long long)a.x * b.x;
+      T2 += (long long)a.x * b.y + (long long)a.y * b.x;
+    }
+    since += kc;
+    if (since >= FX_FLUSH) {                           // KC divides FX_FLUSH
+      acc += fx_value(T1, T2);
+      T1 = T2 = 0;
+      since = 0;
+    }
+  }
+  acc += fx_value(T1, T2);
+  const int gi = i0 + ti, gj = j0 + tj;
+  if (gi >= M || gj >= N || (lower && gi < gj)) return;
+  double v;
+  if (ra == FX_BAD || rb == FX_BAD) v = __longlong_as_double(0x7ff8000000000000ll);
+  else if (ra == INT_MIN || rb == INT_MIN) v = 0.0;
+  else v = ldexp(acc, ra + rb);
+  C[gi + (int64_t)gj * ldc] = v;
+}
+
+}  // namespace
+
+cudaError_t fx_gemm(cudaStream_t st, int M, int N, int K, const double* A, int64_t lda, const double* B, int64_t ldb,
+                    double* C, int64_t ldc, bool lower, const int32_t* done, int64_t* launches) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (K < 0) return cudaErrorInvalidValue;
+  dim3 grid((M + TB - 1) / TB, (N + TB - 1) / TB);
+  fx_gemm_kernel<<<grid, TB * TB, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, lower ? 1 : 0, done);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+}  // namespace wc

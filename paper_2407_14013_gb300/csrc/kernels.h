@@ -71,6 +71,11 @@ int rows_gemvT_blocks(int64_t L, int esize);
 // row; a pass takes its vector's exponent from fx_exponent (the device int *f), splits the vector
 // as it stages it, and sums exact int64 digit products.  Same outputs and partial-sum layouts as
 // rows_gemv<double> and rows_gemvT_unpack<double>, with an error within the FP64 dot-product bound.
+// C = A B (column-major, M x N x K, no transposes) from exact int64 sums of two-digit products
+// (gemm_fx.cu); `lower` writes only the entries i >= j.  Error within the FP64 dot-product bound
+// measured against the largest entry of each row of A and column of B.
+cudaError_t fx_gemm(cudaStream_t st, int M, int N, int K, const double* A, int64_t lda, const double* B, int64_t ldb,
+                    double* C, int64_t ldc, bool lower, const int32_t* done, int64_t* launches);
 int64_t fx_row_len(int64_t L);
 int fx_rows_gemv_slabs(int m, int64_t L);   // slab partial sums written by fx_rows_gemv
 void fx_split_rows(cudaStream_t st, const double* A, int m, int64_t L, int2* Ai, int* ea, int64_t* launches);

@@ -619,9 +619,14 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
     cudaStream_t s1 = fork(h, 1, 1);
     CU(gemm_f64(s1, false, false, n, r, n, 1.0, S.Y, n, Q, n, 0.0, S.Tm, n, h->ws_b[1], h->ws_b_elems, L, done));
     CU(gemm_f64(s1, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, h->ws_b[1], h->ws_b_elems, L, done));
-    CU(gemm_f64(st, false, false, n, n, n, 1.0, S.E, n, S.Y, n, 0.0, S.F, n, S.ws, S.ws_elems, L, done));
-    CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, S.ws_elems, L, done,
-                GEMM_LOWER));                                          // E Y E is symmetric: lower triangle
+    if (h->fx && n < kTcMin) {   // E Y E from exact integer sums (the integer pipe outruns the FP64 one)
+      CU(fx_gemm(st, n, n, n, S.E, n, S.Y, n, S.F, n, false, done, L));
+      CU(fx_gemm(st, n, n, n, S.F, n, S.E, n, S.Z, n, true, done, L));
+    } else {
+      CU(gemm_f64(st, false, false, n, n, n, 1.0, S.E, n, S.Y, n, 0.0, S.F, n, S.ws, S.ws_elems, L, done));
+      CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, S.ws_elems, L, done,
+                  GEMM_LOWER));                                        // E Y E is symmetric: lower triangle
+    }
     join(h, 0, 2);
     join(h, 1, 3);
     svec_pack_plus<double>(st, n, r, S.Z, S.Up, Q, S.zsvec, done, L);    // svec(E Y E + sym(Up Q^T))
