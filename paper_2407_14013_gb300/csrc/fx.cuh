@@ -15,6 +15,10 @@ namespace wc {
 constexpr int FX_FLUSH = 1024;
 constexpr int FX_BAD = 0x7fffffff;          // the vector had a non-finite entry: outputs are NaN
 constexpr int FX_NONE = INT_MIN;            // no nonzero entry
+constexpr int FX_NONE_MAX = -8192;          // any exponent at or below this also means "no nonzero entry"
+                                            // (a 4-byte memset to 0x80 gives one)
+
+__device__ __forceinline__ bool fx_none(int f) { return f <= FX_NONE_MAX; }
 
 // e with |x| < 2^e from the IEEE fields (x finite and nonzero)
 __device__ __forceinline__ int fx_expo_bits(unsigned long long b) {

@@ -68,8 +68,9 @@ void rows_gemvT_unpack(cudaStream_t st, const T* A, int m, int64_t L, const T* p
 int rows_gemvT_blocks(int64_t L, int esize);
 // Exact fixed-point forms of the FP64 passes over dense rows (rows.cu): A (m x L) split once into
 // two int32 digits per entry (rows of fx_row_len(L) entries) with a power-of-two exponent per
-// row; a pass takes its vector's exponent from fx_exponent (the device int *f), splits the vector
-// as it stages it, and sums exact int64 digit products.  Same outputs and partial-sum layouts as
+// row; a pass takes its vector's exponent (the device int *f) from fx_exponent, from the kernel
+// that produced the vector, or finds it itself, splits the vector as it stages it, and sums
+// exact int64 digit products.  Same outputs and partial-sum layouts as
 // rows_gemv<double> and rows_gemvT_unpack<double>, with an error within the FP64 dot-product bound.
 // C = A B (column-major, M x N x K, no transposes) from exact int64 sums of two-digit products
 // (gemm_fx.cu); `lower` writes only the entries i >= j.  Error within the FP64 dot-product bound
@@ -84,8 +85,8 @@ void fx_exponent(cudaStream_t st, const double* x, const int* ex, int64_t len, i
 void fx_rows_gemv(cudaStream_t st, const int2* Ai, const int* ea, int m, int64_t L, const double* x, const int* f,
                   double* part, const int32_t* done, int64_t* launches);
 void fx_rows_gemvT_unpack(cudaStream_t st, const int2* Ai, const int* ea, int m, int64_t L, const double* y,
-                          const int* f, double* part, int groups, int n, double scale, double* Y,
-                          unsigned int* tickets, const int32_t* done, int64_t* launches);
+                          int* f, double* part, int groups, int n, double scale, double* Y, const int32_t* done,
+                          int64_t* launches);
 // sum_i ||row_i||^2
 void rows_sumsq(cudaStream_t st, const double* A, int m, int64_t L, double* out, double* scratch,
                 int64_t* launches);
@@ -96,10 +97,12 @@ template <typename T>
 void svec_unpack_sum(cudaStream_t st, int n, const T* part, int groups, double scale, T* Y,
                      const int32_t* done, int64_t* launches);
 // out(svec, N) = svec(Z + sym(U Q^T)) with U, Q n x r (U may be NULL); Z is symmetric and only
-// its lower triangle is read.
+// its lower triangle is read.  With expo (FP64 only), atomically raises *expo to the exponent e
+// (|out_k| < 2^e) of every nonzero output, or to INT_MAX for a non-finite one: the caller sets
+// *expo below FX_NONE_MAX first (the exponent of the integer A pass).
 template <typename T>
 void svec_pack_plus(cudaStream_t st, int n, int r, const T* Z, const T* U, const T* Q, T* out,
-                    const int32_t* done, int64_t* launches);
+                    const int32_t* done, int64_t* launches, int* expo = nullptr);
 // Stack of full matrices from svec rows i0 .. i0+mb-1: out[b * (mb n) + il * n + a] = A_{i0+il}[a, b].
 void svec_rows_unpack(cudaStream_t st, const double* A, int n, int i0, int mb, double* out,
                       int64_t* launches);

@@ -433,7 +433,7 @@ __device__ __forceinline__ int block_max_int(int v, int* sh) {
 }
 
 __device__ __forceinline__ double fx_out(double d, int F, int e) {
-  return F == FX_BAD ? __longlong_as_double(0x7ff8000000000000ll) : (F == FX_NONE ? 0.0 : ldexp(d, F + e));
+  return F == FX_BAD ? __longlong_as_double(0x7ff8000000000000ll) : (fx_none(F) ? 0.0 : ldexp(d, F + e));
 }
 
 // setup: row i of A (m x L, row-major) -> digits (row length Lp = L rounded up to even, the pad
@@ -498,7 +498,7 @@ fx_rows_gemv_kernel(const int2* __restrict__ Ai, const int* __restrict__ ea, int
   const int64_t k0 = (int64_t)s * SW;
   const int lenp = (int)((Lp - k0) < (int64_t)SW ? (Lp - k0) : (int64_t)SW);   // even
   const int f = *fptr;
-  const int F = (f == FX_BAD || f == FX_NONE) ? 0 : f;
+  const int F = (f == FX_BAD || fx_none(f)) ? 0 : f;
   for (int q = threadIdx.x; q < lenp; q += blockDim.x)    // the digits of x 2^-F for this slab
     xs[q] = fx_split(k0 + q < L ? fx_fixed(x[k0 + q], 0, F) : 0);
   __syncthreads();
@@ -566,23 +566,48 @@ fx_rows_gemv_kernel(const int2* __restrict__ Ai, const int* __restrict__ ea, int
 }
 
 // A^T y from the digits (y's digits carry the row exponents): the row-group layout of
-// rows_gemvT_kernel (partials part[g * L + c]), two columns per thread, and the same
-// last-CTA unpack into the symmetric matrix Y
+// rows_gemvT_kernel (partials part[g * L + c]), two columns per thread.  With fptr == NULL every
+// CTA finds the exponent of y itself (one scan of the m entries of y and of the row exponents,
+// from L2), which saves a launch for the small m of the dense kind.
 template <bool STREAM>
 __global__ void __launch_bounds__(GT_THREADS)
 fx_rows_gemvT_kernel(const int2* __restrict__ Ai, const int* __restrict__ ea, int m, int64_t L, int64_t Lp,
                      const double* __restrict__ y, const int* __restrict__ fptr, double* __restrict__ part,
-                     int rows_per_group, const int32_t* __restrict__ done, int n, double scale,
-                     double* __restrict__ Y, unsigned int* __restrict__ tickets) {
+                     int rows_per_group, const int32_t* __restrict__ done) {
   if (done && *done) return;
   const uint64_t pol = STREAM ? evict_first_policy() : 0;
   __shared__ int2 ys[FX_FLUSH];
+  __shared__ int shf[32];
   const int g = blockIdx.y;
   const int i0 = g * rows_per_group;
   const int i1 = min(m, i0 + rows_per_group);
   const int64_t c = ((int64_t)blockIdx.x * GT_THREADS + threadIdx.x) * 2;   // c < Lp: c < L
-  const int f = *fptr;
-  const int F = (f == FX_BAD || f == FX_NONE) ? 0 : f;
+  int f;
+  if (fptr) {
+    f = *fptr;
+  } else {
+    int e = INT_MIN, bad = 0;
+    constexpr int U = 8;
+    for (int j0 = 0; j0 < m; j0 += U * GT_THREADS) {
+      unsigned long long b[U];
+      int ex[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int j = j0 + u * GT_THREADS + threadIdx.x;
+        b[u] = j < m ? (unsigned long long)__double_as_longlong(y[j]) & 0x7FFFFFFFFFFFFFFFull : 0ull;
+        ex[u] = j < m ? ea[j] : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (b[u] >= 0x7FF0000000000000ull) bad = 1;
+        else if (b[u]) e = max(e, fx_expo_bits(b[u]) + ex[u]);
+      }
+    }
+    e = block_max_int(e, shf);
+    bad = block_max_int(bad, shf);
+    f = bad ? FX_BAD : e;
+  }
+  const int F = (f == FX_BAD || fx_none(f)) ? 0 : f;
   const int4* base = reinterpret_cast<const int4*>(Ai + c);
   const int64_t stv = Lp / 2;
   double d0 = 0.0, d1 = 0.0;
@@ -628,49 +653,31 @@ fx_rows_gemvT_kernel(const int2* __restrict__ Ai, const int* __restrict__ ea, in
     part[(int64_t)g * L + c] = fx_out(d0, f, 0);
     if (c + 1 < L) part[(int64_t)g * L + c + 1] = fx_out(d1, f, 0);
   }
-  if (!Y) return;
-  __shared__ bool last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(tickets + blockIdx.x, 1u) == gridDim.y - 1);
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  // the group partials of this CTA's columns, summed in group order with eight loads in flight
-  const int64_t c0 = (int64_t)blockIdx.x * GT_THREADS * 2;
-  const int G = (int)gridDim.y;
-  const int64_t ca = c0 + threadIdx.x, cb = c0 + GT_THREADS + threadIdx.x;
-  const bool ha = ca < L, hbb = cb < L;
-  double sa = 0.0, sb = 0.0;
+}
+
+// Y = smat(scale * sum_g part[g * L + .]) (both triangles), one thread per svec position, the
+// groups summed in order with eight loads in flight
+__global__ void __launch_bounds__(GT_THREADS)
+svec_groups_unpack_kernel(int n, int64_t L, const double* __restrict__ part, int G, double scale,
+                          double* __restrict__ Y, const int32_t* __restrict__ done) {
+  if (done && *done) return;
+  const int64_t c = (int64_t)blockIdx.x * GT_THREADS + threadIdx.x;
+  if (c >= L) return;
+  double s = 0.0;
   int gg = 0;
   for (; gg + 7 < G; gg += 8) {
-    double va[8], vb[8];
+    double v[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      va[k] = ha ? __ldcg(part + (int64_t)(gg + k) * L + ca) : 0.0;
-      vb[k] = hbb ? __ldcg(part + (int64_t)(gg + k) * L + cb) : 0.0;
-    }
+    for (int k = 0; k < 8; ++k) v[k] = __ldcg(part + (int64_t)(gg + k) * L + c);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      sa += va[k];
-      sb += vb[k];
-    }
+    for (int k = 0; k < 8; ++k) s += v[k];
   }
-  for (; gg < G; ++gg) {
-    if (ha) sa += __ldcg(part + (int64_t)gg * L + ca);
-    if (hbb) sb += __ldcg(part + (int64_t)gg * L + cb);
-  }
-  for (int h2 = 0; h2 < 2; ++h2) {
-    const int64_t cc = h2 ? cb : ca;
-    if (cc >= L) break;
-    int a, b;
-    svec_pos(n, cc, a, b);
-    const double sum = h2 ? sb : sa;
-    const double v = (a == b ? sum : sum * WC_RSQRT2) * scale;
-    Y[a + (int64_t)b * n] = v;
-    Y[b + (int64_t)a * n] = v;
-  }
-  if (threadIdx.x == 0) tickets[blockIdx.x] = 0u;
+  for (; gg < G; ++gg) s += __ldcg(part + (int64_t)gg * L + c);
+  int a, b;
+  svec_pos(n, c, a, b);
+  const double v = (a == b ? s : s * WC_RSQRT2) * scale;
+  Y[a + (int64_t)b * n] = v;
+  Y[b + (int64_t)a * n] = v;
 }
 
 }  // namespace
@@ -826,19 +833,25 @@ void fx_rows_gemv(cudaStream_t st, const int2* Ai, const int* ea, int m, int64_t
 }
 
 void fx_rows_gemvT_unpack(cudaStream_t st, const int2* Ai, const int* ea, int m, int64_t L, const double* y,
-                          const int* f, double* part, int groups, int n, double scale, double* Y,
-                          unsigned int* tickets, const int32_t* done, int64_t* launches) {
+                          int* f, double* part, int groups, int n, double scale, double* Y, const int32_t* done,
+                          int64_t* launches) {
   const int rpg = (m + groups - 1) / groups;
   const int64_t Lp = fx_row_len(L);
   const bool stream = (int64_t)m * L * 8 > (int64_t)64 << 20;
-  dim3 grid((unsigned)((Lp / 2 + GT_THREADS - 1) / GT_THREADS), groups);   // = rows_gemvT_blocks(L, 8)
+  // each CTA scans y for its exponent when y is short; else one exponent launch first
+  const int* fp = nullptr;
+  if (m > 8192) {
+    fx_exponent(st, y, ea, m, f, done, launches);
+    fp = f;
+  }
+  dim3 grid((unsigned)((Lp / 2 + GT_THREADS - 1) / GT_THREADS), groups);
   if (stream)
-    fx_rows_gemvT_kernel<true><<<grid, GT_THREADS, 0, st>>>(Ai, ea, m, L, Lp, y, f, part, rpg, done, n, scale, Y,
-                                                            tickets);
+    fx_rows_gemvT_kernel<true><<<grid, GT_THREADS, 0, st>>>(Ai, ea, m, L, Lp, y, fp, part, rpg, done);
   else
-    fx_rows_gemvT_kernel<false><<<grid, GT_THREADS, 0, st>>>(Ai, ea, m, L, Lp, y, f, part, rpg, done, n, scale, Y,
-                                                             tickets);
-  if (launches) ++*launches;
+    fx_rows_gemvT_kernel<false><<<grid, GT_THREADS, 0, st>>>(Ai, ea, m, L, Lp, y, fp, part, rpg, done);
+  svec_groups_unpack_kernel<<<(unsigned)((L + GT_THREADS - 1) / GT_THREADS), GT_THREADS, 0, st>>>(n, L, part, groups,
+                                                                                                scale, Y, done);
+  if (launches) *launches += 2;
 }
 
 int rows_gemvT_blocks(int64_t L, int esize) {

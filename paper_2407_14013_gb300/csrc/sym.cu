@@ -2,6 +2,7 @@
 // svec stacks the lower triangle column by column, off-diagonal entries times sqrt(2);
 // svec of a non-symmetric matrix is svec of its symmetric part).
 #include "common.cuh"
+#include "fx.cuh"
 #include "kernels.h"
 
 namespace wc {
@@ -26,21 +27,33 @@ __global__ void svec_unpack_sum_kernel(int n, const T* __restrict__ part, int gr
 template <typename T>
 __global__ void svec_pack_plus_kernel(int n, int r, const T* __restrict__ Z, const T* __restrict__ U,
                                       const T* __restrict__ Q, T* __restrict__ out,
-                                      const int32_t* __restrict__ done) {
+                                      const int32_t* __restrict__ done, int* __restrict__ expo) {
   if (done && *done) return;
-  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= (int64_t)n * n) return;
-  int a = (int)(q % n), b = (int)(q / n);
-  if (a < b) return;
-  double v = (double)Z[a + (int64_t)b * n];   // lower triangle (a >= b) of the symmetric Z
-  if (U) {
-    double t = 0.0;
-    for (int k = 0; k < r; ++k)
-      t += (double)U[a + (int64_t)k * n] * (double)Q[b + (int64_t)k * n] +
-           (double)Q[a + (int64_t)k * n] * (double)U[b + (int64_t)k * n];
-    v += 0.5 * t;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int e = INT_MIN;
+  if (q < (int64_t)n * n) {
+    const int a = (int)(q % n), b = (int)(q / n);
+    if (a >= b) {
+      double v = (double)Z[a + (int64_t)b * n];   // lower triangle (a >= b) of the symmetric Z
+      if (U) {
+        double t = 0.0;
+        for (int k = 0; k < r; ++k)
+          t += (double)U[a + (int64_t)k * n] * (double)Q[b + (int64_t)k * n] +
+               (double)Q[a + (int64_t)k * n] * (double)U[b + (int64_t)k * n];
+        v += 0.5 * t;
+      }
+      const T o = (T)((a == b) ? v : v * WC_SQRT2);
+      out[svec_index(n, a, b)] = o;
+      if (expo) {
+        const unsigned long long bits = (unsigned long long)__double_as_longlong((double)o) & 0x7FFFFFFFFFFFFFFFull;
+        e = bits >= 0x7FF0000000000000ull ? INT_MAX : (bits ? fx_expo_bits(bits) : INT_MIN);
+      }
+    }
   }
-  out[svec_index(n, a, b)] = (T)((a == b) ? v : v * WC_SQRT2);
+  if (expo) {   // one atomic per warp (no thread has returned)
+    e = __reduce_max_sync(0xffffffffu, e);
+    if ((threadIdx.x & 31) == 0 && e != INT_MIN) atomicMax(expo, e);
+  }
 }
 
 __global__ void svec_rows_unpack_kernel(const double* __restrict__ A, int n, int64_t N, int i0, int mb,
@@ -71,8 +84,8 @@ void svec_unpack_sum(cudaStream_t st, int n, const T* part, int groups, double s
 
 template <typename T>
 void svec_pack_plus(cudaStream_t st, int n, int r, const T* Z, const T* U, const T* Q, T* out,
-                    const int32_t* done, int64_t* launches) {
-  svec_pack_plus_kernel<T><<<nblk((int64_t)n * n, 256), 256, 0, st>>>(n, r, Z, U, Q, out, done);
+                    const int32_t* done, int64_t* launches, int* expo) {
+  svec_pack_plus_kernel<T><<<nblk((int64_t)n * n, 256), 256, 0, st>>>(n, r, Z, U, Q, out, done, expo);
   if (launches) ++*launches;
 }
 
@@ -80,9 +93,9 @@ template void svec_unpack_sum<double>(cudaStream_t, int, const double*, int, dou
                                       int64_t*);
 template void svec_unpack_sum<float>(cudaStream_t, int, const float*, int, double, float*, const int32_t*, int64_t*);
 template void svec_pack_plus<double>(cudaStream_t, int, int, const double*, const double*, const double*, double*,
-                                     const int32_t*, int64_t*);
+                                     const int32_t*, int64_t*, int*);
 template void svec_pack_plus<float>(cudaStream_t, int, int, const float*, const float*, const float*, float*,
-                                    const int32_t*, int64_t*);
+                                    const int32_t*, int64_t*, int*);
 
 namespace {
 template <typename To, typename From>
