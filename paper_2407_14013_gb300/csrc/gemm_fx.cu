@@ -38,26 +38,44 @@ fx_gemm_kernel(int M, int N, int K, const double* __restrict__ A, int64_t lda, c
   __shared__ int ered[TB][TB + 1];
   __shared__ int ea[TB], eb[TB];
   const int t = threadIdx.x;
-  // ---- exponents: rows of the A panel (lanes along i), columns of the B panel (lanes along k)
+  // ---- exponents: rows of the A panel (lanes along i), columns of the B panel (lanes along k),
+  // eight independent loads in flight per thread
+  constexpr int UE = 8;
   {
     const int r = t & 15, part = t >> 4;
     const int gi = i0 + r;
     int e = INT_MIN;
     if (gi < M)
-      for (int k = part; k < K; k += 16) {
-        const unsigned long long b = (unsigned long long)__double_as_longlong(A[gi + (int64_t)k * lda]) & ABS;
-        if (b >= INF_BITS) e = FX_BAD;
-        else if (b && e != FX_BAD) e = max(e, fx_expo_bits(b));
+      for (int kb = part; kb < K; kb += 16 * UE) {
+        unsigned long long b[UE];
+#pragma unroll
+        for (int u = 0; u < UE; ++u) {
+          const int k = kb + 16 * u;
+          b[u] = k < K ? (unsigned long long)__double_as_longlong(A[gi + (int64_t)k * lda]) & ABS : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < UE; ++u) {
+          if (b[u] >= INF_BITS) e = FX_BAD;
+          else if (b[u] && e != FX_BAD) e = max(e, fx_expo_bits(b[u]));
+        }
       }
     ered[part][r] = e;
     const int c = t >> 4, kp = t & 15;
     const int gj = j0 + c;
     int f = INT_MIN;
     if (gj < N)
-      for (int k = kp; k < K; k += 16) {
-        const unsigned long long b = (unsigned long long)__double_as_longlong(B[k + (int64_t)gj * ldb]) & ABS;
-        if (b >= INF_BITS) f = FX_BAD;
-        else if (b && f != FX_BAD) f = max(f, fx_expo_bits(b));
+      for (int kb = kp; kb < K; kb += 16 * UE) {
+        unsigned long long b[UE];
+#pragma unroll
+        for (int u = 0; u < UE; ++u) {
+          const int k = kb + 16 * u;
+          b[u] = k < K ? (unsigned long long)__double_as_longlong(B[k + (int64_t)gj * ldb]) & ABS : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < UE; ++u) {
+          if (b[u] >= INF_BITS) f = FX_BAD;
+          else if (b[u] && f != FX_BAD) f = max(f, fx_expo_bits(b[u]));
+        }
       }
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) {   // within the 16 lanes of column c (FX_BAD is the largest int)
@@ -81,19 +99,29 @@ fx_gemm_kernel(int M, int N, int K, const double* __restrict__ A, int64_t lda, c
   for (int k0 = 0; k0 < K; k0 += KC) {
     const int kc = min(KC, K - k0);
     __syncthreads();
-    for (int q = t; q < TB * kc; q += TB * TB) {       // A chunk: lanes along i
-      const int r = q & 15, k = q >> 4;
-      const int gi = i0 + r;
-      const int F = ea[r];
-      const double v = (gi < M && F != FX_BAD) ? A[gi + (int64_t)(k0 + k) * lda] : 0.0;
-      As[k][r] = fx_split(F == INT_MIN ? 0 : fx_fixed(v, 0, F));
-    }
-    for (int q = t; q < TB * kc; q += TB * TB) {       // B chunk: lanes along k
-      const int k = q % kc, c = q / kc;
-      const int gj = j0 + c;
-      const int F = eb[c];
-      const double v = (gj < N && F != FX_BAD) ? B[(k0 + k) + (int64_t)gj * ldb] : 0.0;
-      Bs[k][c] = fx_split(F == INT_MIN ? 0 : fx_fixed(v, 0, F));
+    {   // A chunk (lanes along i) and B chunk (lanes along k): all loads first, then the digits
+      constexpr int US = KC * TB / (TB * TB);          // entries per thread per operand (8)
+      double va[US], vb[US];
+#pragma unroll
+      for (int u = 0; u < US; ++u) {
+        const int q = t + u * TB * TB;
+        const int r = q & 15, k = q >> 4;
+        const int gi = i0 + r;
+        va[u] = (k < kc && gi < M && ea[r] != FX_BAD) ? A[gi + (int64_t)(k0 + k) * lda] : 0.0;
+        const int kk = q % KC, c = q / KC;
+        const int gj = j0 + c;
+        vb[u] = (kk < kc && gj < N && eb[c] != FX_BAD) ? B[(k0 + kk) + (int64_t)gj * ldb] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < US; ++u) {
+        const int q = t + u * TB * TB;
+        const int r = q & 15, k = q >> 4;
+        const int F = ea[r];
+        As[k][r] = fx_split((F == INT_MIN || F == FX_BAD) ? 0 : fx_fixed(va[u], 0, F));
+        const int kk = q % KC, c = q / KC;
+        const int G = eb[c];
+        Bs[kk][c] = fx_split((G == INT_MIN || G == FX_BAD) ? 0 : fx_fixed(vb[u], 0, G));
+      }
     }
     __syncthreads();
 #pragma unroll 4
