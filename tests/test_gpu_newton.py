@@ -198,6 +198,31 @@ def test_errors_are_reported():
     s2.close()
 
 
+@pytest.mark.parametrize("int_passes", [True, False])
+def test_zero_and_non_finite_right_sides(int_passes):
+    """A zero right side gives the zero direction (the passes' vectors are all zero: no exponent);
+    a NaN in C~ is reported as SDP_ENUMERIC (the integer passes turn a non-finite vector into
+    NaN outputs, as FP64 arithmetic does) and leaves the handle usable for a good right side."""
+    from paper_2407_14013_gb300 import NewtonSolver, SdpError, native
+    prob = W.sensing(12, 40, 2, 710)
+    sp = W.scaling_point(12, 2, 1e-3, 711)
+    Ct, bt = W.newton_rhs(12, 40, 712)
+    s = NewtonSolver(prob, r_hat=3, int_passes=int_passes)
+    dX, dy, dS, info = s.solve(_t(sp.V), _t(sp.lam), _t(np.zeros_like(Ct)), _t(np.zeros_like(bt)))
+    assert info.converged and info.status == 0
+    assert not np.any(dX.cpu().numpy()) and not np.any(dy.cpu().numpy()) and not np.any(dS.cpu().numpy())
+    Cn = Ct.copy()
+    Cn[3, 5] = Cn[5, 3] = np.nan
+    with pytest.raises(SdpError) as e:
+        s.solve(_t(sp.V), _t(sp.lam), _t(Cn), _t(bt))
+    assert e.value.status == native.SDP_ENUMERIC
+    dX, dy, dS, info = s.solve(_t(sp.V), _t(sp.lam), _t(Ct), _t(bt))
+    assert info.converged
+    rX, ry, rS = onewton.newton_direct(prob, w_of(sp), Ct, bt)
+    assert rel(dX.cpu().numpy(), rX) < TOL and rel(dy.cpu().numpy(), ry) < TOL
+    s.close()
+
+
 def test_graph_replay_matches_plain_launches():
     """The PCG iterations replayed from a captured CUDA graph give the same bits as plain launches."""
     prob = W.sensing(40, 200, 2, 801)
