@@ -468,10 +468,12 @@ cudaError_t eigh_jacobi(cudaStream_t st, int n, double* A, double* V, double* la
 // lambda_min(M) for a symmetric M (n x n): Lanczos on the Krylov space of a fixed start vector,
 // with full re-orthogonalisation (classical Gram-Schmidt applied twice), run in chunks of
 // iterations by one cooperative launch each; after each chunk the host finds the smallest
-// eigenvalue of the tridiagonal T_k (bisection on Sturm counts).  It stops when that value has
-// not moved for two chunks (relative 1e-14), when the basis spans R^n (k = n, then T_n is
+// eigenvalue of the tridiagonal T_k (bisection on Sturm counts).  It stops when that value moved by
+// at most 1e-12 of its size over the last 8 steps, when the basis spans R^n (k = n, then T_n is
 // similar to M), or on breakdown (beta_k = 0: an invariant subspace).  Ritz values of a
-// symmetric matrix decrease monotonically to lambda_min as k grows.
+// symmetric matrix decrease monotonically to lambda_min as k grows, so the value returned is
+// never below lambda_min; the step-length rule that uses it takes 0.98 of the bound and checks the
+// shortened step by a Cholesky factorisation.
 
 namespace wc {
 
@@ -685,9 +687,9 @@ cudaError_t lanczos_min(cudaStream_t st, int n, const double* M, double* work, s
   const int want = (int)std::max<int64_t>(1, ((int64_t)n * 32 + ET - 1) / ET);   // one warp per row
   const int blocks = coop ? std::min({want, per_sm * g_num_sms, kCoopMaxBlocks}) : 1;
   std::vector<double> ah(K + 1), bh(K + 1);
-  double prev = INFINITY, prev2 = INFINITY, theta = 0.0;
+  double theta = 0.0;
   int k = 0;
-  const int chunk = 32;
+  const int chunk = 16;
   while (k < K) {
     int k0 = k, k1 = std::min(K, k + chunk);
     if (coop) {
@@ -713,10 +715,12 @@ cudaError_t lanczos_min(cudaStream_t st, int n, const double* M, double* work, s
     theta = tridiag_min(ah, bh, kk);
     k = k1;
     if (kk < k1) break;
-    const double scale = std::max(std::fabs(theta), 1e-300);
-    if (std::fabs(theta - prev) <= 1e-14 * scale && std::fabs(prev - prev2) <= 1e-14 * scale) break;
-    prev2 = prev;
-    prev = theta;
+    // converged when the smallest Ritz value (which decreases towards lambda_min) moved by at
+    // most 1e-12 of its size over the last half chunk
+    if (kk >= 24) {
+      const double earlier = tridiag_min(ah, bh, kk - chunk / 2);
+      if (std::fabs(theta - earlier) <= 1e-12 * std::max(std::fabs(theta), 1e-300)) break;
+    }
   }
   *lmin = theta;
   if (iters) *iters = k;
