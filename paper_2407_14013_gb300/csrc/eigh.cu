@@ -656,6 +656,8 @@ lanczos_block_kernel(int n, const double* __restrict__ M, double* __restrict__ V
 
 }  // namespace
 
+constexpr int kLanczosBlockMax = 128;
+
 size_t lanczos_work_elems(int n) {
   const size_t K = (size_t)n + 1;
   return (size_t)n * (K + 1) + 3 * K + (size_t)n + 2 * kCoopMaxBlocks + 64;
@@ -673,7 +675,8 @@ cudaError_t lanczos_min(cudaStream_t st, int n, const double* M, double* work, s
   double* red = w + n;
   int dev = 0, coop = 0, per_sm = 0;
   cudaError_t e = cudaSuccess;
-  if (allow_coop) {
+  // small n: one block per launch (block barriers) beats grid barriers across the GPU
+  if (allow_coop && n > kLanczosBlockMax) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if (coop) {
