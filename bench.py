@@ -53,6 +53,28 @@ def make_inputs():
     return prob, ins
 
 
+def newton_residuals(prob, V, lam, Ct, bt, dX, dy):
+    """Residuals of the Newton system (Newt-eps) for a GPU direction, in plain numpy FP64 on the
+    host: primal ||A(dX) - b~|| / ||b~||, dual ||dX - W (A^T(dy) - C~) W||_F / ||dX||_F with
+    W = V diag(lam) V^T (the second block written without W^{-1}, which is ill-conditioned)."""
+    import numpy as np
+    n = dX.shape[0]
+    rows, cols = np.tril_indices(n)
+    order = np.lexsort((rows, cols))                 # column by column, as svec stacks them
+    rows, cols = rows[order], cols[order]
+    wgt = np.where(rows == cols, 1.0, np.sqrt(2.0))
+    A = prob.a_dense
+    x = dX[rows, cols] * wgt
+    primal = float(np.linalg.norm(A @ x - bt) / max(np.linalg.norm(bt), 1e-300))
+    yv = (A.T @ dy) / wgt
+    Y = np.zeros((n, n))
+    Y[rows, cols] = yv
+    Y[cols, rows] = yv
+    Wm = (V * lam) @ V.T
+    dual = float(np.linalg.norm(dX - Wm @ (Y - Ct) @ Wm) / max(np.linalg.norm(dX), 1e-300))
+    return primal, dual
+
+
 def read_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -569,6 +591,14 @@ def run_ours(args):
 
     others = other_configs(dev, args.reps) if (rank == 0 and not args.no_configs) else None
 
+    # parity of the timed path: Newton-system residuals of one direction of the bench inputs
+    V0, lam0, Ct0, bt0 = ins[0]
+    pdX, pdy, _, pinfo = solver.solve(*dins[0])
+    pr, du = newton_residuals(prob, V0, lam0, Ct0, bt0, pdX.cpu().numpy(), pdy.cpu().numpy())
+    parity = {"newt_eps_primal_rel": pr, "newt_eps_dual_rel": du, "pcg_iters": pinfo.pcg_iters,
+              "how": "||A(dX) - b~||/||b~|| and ||dX - W(A^T dy - C~)W||_F/||dX||_F of one GPU direction, "
+                     "numpy FP64 on the host (tests/ compare the directions with the oracle)"}
+
     # end to end through the C ABI with pinned host buffers (H2D and D2H inside the call)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     hins = [(pin(V.T).t(), pin(lam), pin(Ct), pin(bt)) for (V, lam, Ct, bt) in ins]
@@ -627,6 +657,7 @@ def run_ours(args):
         "e2e": {"value": e2e_iters / e2e_s if e2e_steps else None, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
         "wall_s_timed": wall,
+        "parity": parity,
         "mixed_fp32": mixed,
         "time_to_gap_1e-8": ttg,
         "other_configs": others,

@@ -585,22 +585,24 @@ void adjoint_dense(sdp_handle* h, Space& S, const double* u, double* Y, const in
 
 // z = svec(Z + sym(U Q^T)) (U may be NULL), then partA = the slab partial sums of A(z) (DENSE
 // kind); on the integer path the packing kernel also gives the exponent of z
-void pack_apply_dense(sdp_handle* h, Space& S, cudaStream_t st, int r, const double* U, const double* Q,
-                      const int32_t* done, int64_t* L) {
+cudaError_t pack_apply_dense(sdp_handle* h, Space& S, cudaStream_t st, int r, const double* U, const double* Q,
+                             const int32_t* done, int64_t* L) {
   const int n = h->n;
   const double* z = S.zsvec;
   if (h->fx) {
-    cudaMemsetAsync(S.fxe + 1, 0x80, sizeof(int), st);   // below FX_NONE_MAX: no entry yet
+    cudaError_t e = cudaMemsetAsync(S.fxe + 1, 0x80, sizeof(int), st);   // below FX_NONE_MAX: no entry yet
+    if (e != cudaSuccess) return e;
     svec_pack_plus<double>(st, n, r, S.Z, U, Q, S.zsvec, done, L, S.fxe + 1);
     prof_begin(h, 1);
     fx_rows_gemv(st, h->a_fx, h->a_fx_e, h->m, h->N, z, S.fxe + 1, S.partA, done, L);
     prof_end(h);
-    return;
+    return cudaGetLastError();
   }
   svec_pack_plus<double>(st, n, r, S.Z, U, Q, S.zsvec, done, L);
   prof_begin(h, 1);
   rows_gemv<double>(st, h->a_dense, h->m, h->N, z, S.partA, done, L);
   prof_end(h);
+  return cudaGetLastError();
 }
 
 // out = M pin (mode 1 also computes alpha) or out = g - M pin (mode 0, g != NULL), in FP64.
@@ -634,7 +636,7 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
     }
     join(h, 0, 2);
     join(h, 1, 3);
-    pack_apply_dense(h, S, st, r, S.Up, Q, done, L);                   // A(svec(E Y E + sym(Up Q^T)))
+    CU(pack_apply_dense(h, S, st, r, S.Up, Q, done, L));               // A(svec(E Y E + sym(Up Q^T)))
     launch_ap_finish<double>(st, m, d, n, r, S.partA, h->SA, nullptr, S.Vs, S.H, S.Dv, pin, gsub, out, mode, S.ctl,
                              h->dotbuf, h->counter, L);
   } else if (h->kind == SDP_A_SPARSE_COO) {
@@ -1042,7 +1044,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   CU(gemm_big(h, st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, ws, L));
   if (h->kind == SDP_A_DENSE_SVEC) {
     CU(gemm_big(h, st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, ws, L, GEMM_LOWER));
-    pack_apply_dense(h, S, st, r, nullptr, nullptr, nullptr, L);
+    CU(pack_apply_dense(h, S, st, r, nullptr, nullptr, nullptr, L));
     launch_rhs_finish(st, m, d, n, r, S.partA, h->SA, nullptr, nullptr, bt, Ct, S.H, S.Dv, h->g, S.x,
                       h->opt.newton_rtol, h->ctl, h->dotbuf, h->counter, L);
   } else if (h->kind == SDP_A_SPARSE_COO) {
