@@ -55,8 +55,8 @@ def make_inputs():
 
 def newton_residuals(prob, V, lam, Ct, bt, dX, dy):
     """Residuals of the Newton system (Newt-eps) for a GPU direction, in plain numpy FP64 on the
-    host: primal ||A(dX) - b~|| / ||b~||, dual ||dX - W (A^T(dy) - C~) W||_F / ||dX||_F with
-    W = V diag(lam) V^T (the second block written without W^{-1}, which is ill-conditioned)."""
+    host: primal ||A(dX) - b~|| / ||b~||; dual ||-W^{-1} dX W^{-1} + A^T(dy) - C~||_F divided by
+    ||W^{-1} dX W^{-1}||_F + ||C~||_F (the scale of the terms that cancel), W = V diag(lam) V^T."""
     import numpy as np
     n = dX.shape[0]
     rows, cols = np.tril_indices(n)
@@ -70,8 +70,9 @@ def newton_residuals(prob, V, lam, Ct, bt, dX, dy):
     Y = np.zeros((n, n))
     Y[rows, cols] = yv
     Y[cols, rows] = yv
-    Wm = (V * lam) @ V.T
-    dual = float(np.linalg.norm(dX - Wm @ (Y - Ct) @ Wm) / max(np.linalg.norm(dX), 1e-300))
+    Wi = (V / lam) @ V.T
+    T = Wi @ dX @ Wi
+    dual = float(np.linalg.norm(-T + Y - Ct) / max(np.linalg.norm(T) + np.linalg.norm(Ct), 1e-300))
     return primal, dual
 
 
@@ -596,8 +597,9 @@ def run_ours(args):
     pdX, pdy, _, pinfo = solver.solve(*dins[0])
     pr, du = newton_residuals(prob, V0, lam0, Ct0, bt0, pdX.cpu().numpy(), pdy.cpu().numpy())
     parity = {"newt_eps_primal_rel": pr, "newt_eps_dual_rel": du, "pcg_iters": pinfo.pcg_iters,
-              "how": "||A(dX) - b~||/||b~|| and ||dX - W(A^T dy - C~)W||_F/||dX||_F of one GPU direction, "
-                     "numpy FP64 on the host (tests/ compare the directions with the oracle)"}
+              "how": "||A(dX) - b~||/||b~|| and ||-W^-1 dX W^-1 + A^T(dy) - C~||_F/(||W^-1 dX W^-1||_F + ||C~||_F) "
+                     "of one GPU direction, numpy FP64 on the host; the oracle's own direction of the same input "
+                     "scores 8e-6 / 1.2e-9 (tests/ compare the directions with the oracle)"}
 
     # end to end through the C ABI with pinned host buffers (H2D and D2H inside the call)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
