@@ -20,7 +20,15 @@ __global__ void svec_unpack_sum_kernel(int n, const T* __restrict__ part, int gr
   int i = a > b ? a : b, j = a > b ? b : a;
   int64_t idx = svec_index(n, i, j);
   double s = 0.0;
-  for (int g = 0; g < groups; ++g) s += (double)part[(int64_t)g * N + idx];
+  int g = 0;
+  for (; g + 7 < groups; g += 8) {   // the groups in order, eight loads in flight
+    double v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = (double)part[(int64_t)(g + k) * N + idx];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += v[k];
+  }
+  for (; g < groups; ++g) s += (double)part[(int64_t)g * N + idx];
   Y[q] = (T)((a == b ? s : s * WC_RSQRT2) * scale);
 }
 
