@@ -431,6 +431,21 @@ def cpu_baseline(prob, ins, budget_s: float = 15.0, max_solves: int = 8):
                       f"BLAS threads) of the same workload, {iters} PCG iterations in {dt:.1f} s"}
 
 
+def combine_ranks(dev_s, iters, wall, world, device):
+    """Whole-job figures over `world` ranks, each timing its own replica between barriers: the
+    slowest rank's device time (max) and the PCG iterations of all ranks (sum)."""
+    if world <= 1:
+        return dev_s, float(iters)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([dev_s, float(iters), wall], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    tsum = t.clone()
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[1])
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -528,15 +543,7 @@ def run_ours(args):
     iters, launches, wall = res["iters"], res["launches"], res["wall"]
     dev_s = sum(res["ms"]) / 1e3
     prof = res
-    t_tot = torch.tensor([dev_s, float(iters), wall], dtype=f64, device=dev)
-    if world > 1:
-        tmax = t_tot.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t_tot.clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        dev_s_max, iters_all = float(tmax[0]), float(tsum[1])
-    else:
-        dev_s_max, iters_all = dev_s, float(iters)
+    dev_s_max, iters_all = combine_ranks(dev_s, iters, wall, world, dev)
     value = iters_all / dev_s_max
 
     # the mixed-precision form (FP32 A E A^T block in the correction solves, FP64 refinement)
