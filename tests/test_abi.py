@@ -114,6 +114,12 @@ def test_default_options_and_setup_errors(lib):
     o.precision = _native.SDP_FP64
     p.nnz, p.a_con, p.a_row, p.a_col, p.a_val = 0, 0, 0, 0, 0
     p.kind = _native.SDP_A_DIAG
+    for field, bad in (("int_passes", 2), ("tc_products", -1), ("krylov", 3), ("pcg_start", 2)):
+        o2 = _native.sdp_default_options()
+        setattr(o2, field, bad)
+        with pytest.raises(_native.SdpError) as e:
+            _native.sdp_setup(p, o2, 0)
+        assert e.value.status == _native.SDP_EINVAL and field in str(e.value), field
     o.r_fixed = 4                                        # r must be < n
     with pytest.raises(_native.SdpError) as e:
         _native.sdp_setup(p, o, 0)
