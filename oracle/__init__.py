@@ -18,6 +18,9 @@ reform     the paper's reformulation, step by step: the split (eq. EQSigdef),
            the matrix-free products of Section 5, the augmented system and the
            recovery (eq. augsys / recover), the block preconditioner of
            Section 6 and the indefinite PCG of Cor. pcg / Def. pcg.
+lpcone     the nonnegative variables of Section 7's robust problems (eq. rmc-sdp)
+           in the Newton system: plain definition, dense KKT, and the
+           reformulation with the linear block and its preconditioner.
 ipm        a textbook infeasible primal-dual NT path-following method (the
            outer loop; the paper leaves it to SeDuMi, so its details are the
            oracle's own definitions -- parity unpinned beyond its invariants).

@@ -149,6 +149,36 @@ def completion(n1: int, n2: int, rank: int, frac: float, seed: int) -> Problem:
                    meta={"family": "completion", "F1": F1, "F2": F2, "n1": n1, "n2": n2})
 
 
+def rmc(n: int, m: int, m_o: int, seed: int, rank: int = 2, lam: float = 1.0) -> Problem:
+    """Robust matrix completion as Section 7 generates it (eq. rmc-sdp): X* = G G^T with G n x rank,
+    entries N(0, 10^2); A(X) = m entries of svec(X) sampled without replacement (<A_i, X> =
+    svec(X)_k: X_aa on the diagonal, sqrt2 X_ab off it); b = A(X*) + eps with m_o entries of eps
+    drawn N(0, 10^4) and the rest zero; C = lam I.  The nonnegative variables x = [v; w] enter as
+    A(X) + G_l x = b with G_l = [I, -I] and cost c_l = 1 (meta["G_l"], meta["c_l"])."""
+    g = rng(seed)
+    Gm = 10.0 * g.standard_normal((n, rank))
+    Xs = Gm @ Gm.T
+    N = svec_len(n)
+    flat = np.sort(g.choice(N, size=m, replace=False))
+    # svec position k -> (a, b), a >= b, column by column
+    cols = np.repeat(np.arange(n), np.arange(n, 0, -1))
+    starts = np.concatenate([[0], np.cumsum(np.arange(n, 0, -1))[:-1]])
+    rows = np.arange(N) - starts[cols] + cols
+    a_idx, b_idx = rows[flat], cols[flat]
+    diag = a_idx == b_idx
+    val = np.where(diag, 1.0, 1.0 / math.sqrt(2.0))        # <A_i, X> = sum val X_rc (1 or 2 for r != c)
+    b = np.where(diag, Xs[a_idx, b_idx], math.sqrt(2.0) * Xs[a_idx, b_idx])
+    eps = np.zeros(m)
+    out = g.choice(m, size=min(m_o, m), replace=False)
+    eps[out] = 100.0 * g.standard_normal(out.size)
+    Gl = np.hstack([np.eye(m), -np.eye(m)])
+    return Problem(kind="sparse", n=n, m=m, b=b + eps, C=lam * np.eye(n),
+                   a_con=np.arange(m, dtype=np.int32), a_row=a_idx.astype(np.int32),
+                   a_col=b_idx.astype(np.int32), a_val=val,
+                   meta={"family": "rmc", "Xs": Xs, "outliers": out, "eps": eps, "G_l": Gl,
+                         "c_l": np.ones(2 * m)})
+
+
 def random_sparse(n: int, m: int, per_con: int, seed: int) -> Problem:
     """Generic sparse constraints (several lower-triangle entries per A_i) for tests."""
     g = rng(seed)
