@@ -230,6 +230,21 @@ sdp_status ipm_step(sdp_handle* h, const double* b, const double* C, double* X, 
 sdp_status sdp_solve(sdp_handle* h, const double* b, const double* C, double* X, double* y, double* S,
                      double gap_tol, int32_t max_iter, sdp_ipm_info* info);
 
+/* Linear block of the Newton system: nonnegative variables x >= 0 entering the constraints as
+ * A(X) + G x = b, as in the robust problems of Section 7 (eq. rmc-sdp: x = [v; w], G = [I, -I]).
+ * With D = diag(x / z) (NT scaling of the orthant), eliminating dx adds G D G^T to the Schur
+ * matrix: the solve becomes (A (W (x)s W) A^T + diag(delta)) dy = b~ + A(W C~ W) with
+ * delta = diag(G D G^T) (each variable in one constraint, so G D G^T is diagonal; for eq. rmc-sdp
+ * delta = d_v + d_w).  In eq. augsys this is tau^-2 diag(delta) added to the (1,1) block, and the
+ * Section 6 preconditioner takes Lam = beta I + tau^-2 diag(delta) in place of beta I (d-space:
+ * C = tau^2 Sigma + B^T Lam^{-1} B; m-space: K = Lam + B (tau^2 Sigma)^{-1} B^T).  The caller
+ * folds the linear block's right side into b~ (b~ + G D c~) and forms dx = D(G^T dy - c~).
+ * delta: device pointer to m values >= 0, owned by the caller and read by every later Newton solve
+ * of the handle, or NULL to remove the block.  DENSE_SVEC kind, FP64 form and PCG only
+ * (otherwise SDP_EUNSUPPORTED); the setup of the next solve is redone (no resolve before it).
+ * SDP_ENOMEM if the workspace of the block (m + m d_max doubles) cannot be allocated. */
+sdp_status sdp_set_linear_diag(sdp_handle* h, const double* delta);
+
 /* The NT scaling point of an iterate (eq. newt), as the Newton solve and the adjoint take it:
  * W = L (L^T S L)^{-1/2} L^T with X = L L^T, computed as G G^T with G = L U Gamma^{-1/4}
  * (L^T S L = U Gamma U^T), and its eigen-decomposition W = V diag(lam) V^T (Jacobi, FP64; both

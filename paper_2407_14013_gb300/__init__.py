@@ -236,6 +236,19 @@ class NewtonSolver:
         info["status"] = st
         return X, y, S, info
 
+    def set_linear_diag(self, delta=None):
+        """Nonnegative variables entering the constraints (sdp_set_linear_diag): every later solve
+        adds diag(delta) to the Schur matrix, delta = diag(G D G^T) >= 0 (m values).  The caller
+        folds G D c~ into b~ and forms dx = D(G^T dy - c~).  None removes the block."""
+        torch = self.torch
+        if delta is None:
+            self._lin = None
+            native.sdp_set_linear_diag(self.handle, 0)
+            return
+        t = delta if isinstance(delta, torch.Tensor) else torch.from_numpy(delta)
+        self._lin = t.to(device=self.device, dtype=torch.float64).contiguous()
+        native.sdp_set_linear_diag(self.handle, _ptr(self._lin))
+
     def scaling_point(self, X, S):
         """Eigen-decomposition (V, lam) of the NT scaling point of (X, S) (sdp_scaling_point), the
         input that solve() and grad() take."""

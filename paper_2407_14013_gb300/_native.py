@@ -60,6 +60,7 @@ class sdp_ipm_info(ctypes.Structure):
 
 EXPORTS = {
     "sdp_default_options": (None, [POINTER(sdp_options)]),
+    "sdp_set_linear_diag": (c_int32, [c_void_p, c_void_p]),
     "sdp_setup": (c_int32, [POINTER(sdp_problem), POINTER(sdp_options), c_void_p, POINTER(c_void_p)]),
     "sdp_newton_solve": (c_int32, [c_void_p] + [c_void_p] * 7 + [POINTER(sdp_newton_info)]),
     "sdp_newton_solve_host": (c_int32, [c_void_p] + [c_void_p] * 7 + [POINTER(sdp_newton_info)]),
@@ -185,6 +186,14 @@ def sdp_solve(h: int, b: int, C: int, X: int, y: int, S: int, gap_tol: float, ma
     if st != SDP_OK and not (allow_notconv and st == SDP_ENOTCONV):
         raise SdpError(st, lib.sdp_last_error(c_void_p(h)).decode())
     return st
+
+
+def sdp_set_linear_diag(h: int, delta: int) -> None:
+    """Linear block delta (device pointer to m doubles, or 0 to remove it)."""
+    lib = load()
+    st = lib.sdp_set_linear_diag(c_void_p(h), c_void_p(delta) if delta else None)
+    if st != SDP_OK:
+        raise SdpError(st, lib.sdp_last_error(c_void_p(h) if h else None).decode())
 
 
 def sdp_scaling_point(h: int, X: int, S: int, V: int, lam: int) -> None:

@@ -96,6 +96,9 @@ struct sdp_handle {
   int64_t b_elems = 0;              // capacity of the explicit B = A Q (m x d)
   int64_t bt_elems = 0;             // capacity of B^T (d x m)
   int64_t bs_elems = 0;             // capacity of D^{-1/2} B^T (m-space core by a product)
+  const double* lin = nullptr;      // linear block delta (m, caller-owned device memory) or NULL
+  double* lin_lam = nullptr;        // Lam = beta + tau^-2 delta (m)
+  double* lin_Bw = nullptr;         // B with row i scaled by Lam_i^-1/2 (d-space complement)
   bool fx = false;                  // DENSE_SVEC: the FP64 passes over A run on its integer copy
   int2* a_fx = nullptr;             // digits of A (m rows of fx_row_len(N) entries)
   int* a_fx_e = nullptr;            // row exponents

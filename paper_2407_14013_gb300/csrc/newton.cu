@@ -638,7 +638,7 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
     join(h, 1, 3);
     CU(pack_apply_dense(h, S, st, r, S.Up, Q, done, L));               // A(svec(E Y E + sym(Up Q^T)))
     launch_ap_finish<double>(st, m, d, n, r, S.partA, h->SA, nullptr, S.Vs, S.H, S.Dv, pin, gsub, out, mode, S.ctl,
-                             h->dotbuf, h->counter, L);
+                             h->dotbuf, h->counter, L, nullptr, 0, h->lin);   // + tau^-2 delta p_u
   } else if (h->kind == SDP_A_SPARSE_COO) {
     // Y = A^T(p_u) kept as its pattern values; E Y E only at the pattern positions
     sparse_posval(st, h->sp, pu, S.ypos, done, L);
@@ -765,14 +765,20 @@ sdp_status apply_precond(sdp_handle* h, Space& S, const double* rin, double* zou
       launch_pc_zu_dot<double>(st, m, d, 0, nullptr, 2, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L);
     }
   } else if (h->space == 1) {
-    rows_gemv<double>(st, S.Bt, d, m, rin, S.partB, done, L);              // B^T r_u (rows of B^T)
-    // C^{-1} s with s = r_v - beta^{-1} B^T r_u formed while staged
-    rows_gemv_formed(st, S.Pinv, d, d, rin + m, S.partB, Sm, -1.0, &S.ctl->beta_pc, nullptr, S.partC, done, L);
+    if (h->lin) {   // linear block: s = r_v - B^T (Lam^{-1} r_u), z_u = Lam^{-1}(r_u - B z_v)
+      launch_lin_div(st, m, rin, h->lin_lam, S.wm, S.ctl, L);
+      rows_gemv<double>(st, S.Bt, d, m, S.wm, S.partB, done, L);
+      rows_gemv_formed(st, S.Pinv, d, d, rin + m, S.partB, Sm, -1.0, nullptr, nullptr, S.partC, done, L);
+    } else {
+      rows_gemv<double>(st, S.Bt, d, m, rin, S.partB, done, L);            // B^T r_u (rows of B^T)
+      // C^{-1} s with s = r_v - beta^{-1} B^T r_u formed while staged
+      rows_gemv_formed(st, S.Pinv, d, d, rin + m, S.partB, Sm, -1.0, &S.ctl->beta_pc, nullptr, S.partC, done, L);
+    }
     // B z_v with z_v = -(C^{-1} s) formed while staged and stored
     rows_gemv_formed(st, S.B, m, d, nullptr, S.partC, rows_gemv_slabs(d, d), -1.0, nullptr, zout + m, S.partA, done,
                      L);
     launch_pc_zu_dot<double>(st, m, d, rows_gemv_slabs(m, d), S.partA, 1, rin, zout, mode, S.ctl, h->dotbuf,
-                             h->counter, L);
+                             h->counter, L, h->lin ? h->lin_lam : nullptr);
   } else if (h->kind == SDP_A_DIAG) {
     // the products with B from Vs: B t = rowdot(Vs unpack(t), Q), B^T u = pack(Vs^T diag(u) Q)
     const int n = h->n, r = h->r;
@@ -1003,6 +1009,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   }
   int32_t* pstatus = &h->ctl->status;
   const int pd = (h->space == 1) ? d : m;
+  if (h->lin) launch_lin_lam(st, m, h->lin, h->ctl, h->lin_lam, L);   // Lam = beta + tau^-2 delta
   if (h->opt.krylov == 1) {
     // MINRES (Cor. minres): no preconditioner core
   } else if (pd > h->pinv_dim) {
@@ -1014,10 +1021,17 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     launch_diag_K(st, n, S.F, S.E, h->ctl, S.Pinv, L);
     CU(spd_inverse_any(h, st, m, S.Pinv, S.ws, ws, pstatus, L));
   } else if (h->space == 1) {
-    // C = beta^{-1} B^T B + tau^2 Sigma  (B row-major m x d == column-major d x m)
-    const double beta = h->ctl_host->beta_pc;
-    CU(gemm_big(h, st, false, true, d, d, m, 1.0 / beta, S.B, d, S.B, d, 0.0, S.Pinv, d, S.ws, ws, L,
-                GEMM_LOWER));   // the Cholesky reads the lower triangle only
+    // C = beta^{-1} B^T B + tau^2 Sigma  (B row-major m x d == column-major d x m); with a linear
+    // block, C = B^T Lam^{-1} B + tau^2 Sigma
+    if (h->lin) {
+      launch_lin_scale_rows(st, m, d, S.B, h->lin_lam, h->lin_Bw, L);
+      CU(gemm_big(h, st, false, true, d, d, m, 1.0, h->lin_Bw, d, h->lin_Bw, d, 0.0, S.Pinv, d, S.ws, ws, L,
+                  GEMM_LOWER));
+    } else {
+      const double beta = h->ctl_host->beta_pc;
+      CU(gemm_big(h, st, false, true, d, d, m, 1.0 / beta, S.B, d, S.B, d, 0.0, S.Pinv, d, S.ws, ws, L,
+                  GEMM_LOWER));   // the Cholesky reads the lower triangle only
+    }
     launch_add_diag(st, d, S.Pinv, S.Dv, 0.0, L);
     CU(spd_inverse_any(h, st, d, S.Pinv, S.ws, ws, pstatus, L));
   } else {
@@ -1025,7 +1039,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     if ((int64_t)m * d > h->bs_elems) return fail(h, SDP_EINVAL, "m-space core larger than the setup allows");
     launch_scale_B(st, m, d, S.B, S.Dv, h->Bs, L);
     CU(gemm_big(h, st, true, false, m, m, d, 1.0, h->Bs, d, h->Bs, d, 0.0, S.Pinv, m, S.ws, ws, L, GEMM_LOWER));
-    launch_add_diag(st, m, S.Pinv, nullptr, h->ctl_host->beta_pc, L);
+    launch_add_diag(st, m, S.Pinv, h->lin ? h->lin_lam : nullptr, h->lin ? 0.0 : h->ctl_host->beta_pc, L);  // + Lam
     CU(spd_inverse_any(h, st, m, S.Pinv, S.ws, ws, pstatus, L));
   }
   if (h->mixed) {   // FP32 copies for the A E A^T block of the mixed operator
@@ -1304,10 +1318,36 @@ extern "C" const char* sdp_last_error(const sdp_handle* h) {
   return h ? h->err.c_str() : g_setup_err.c_str();
 }
 
+extern "C" sdp_status sdp_set_linear_diag(sdp_handle* h, const double* delta) {
+  if (!h) return fail(nullptr, SDP_EINVAL, "NULL handle");
+  if (delta) {
+    if (h->kind != SDP_A_DENSE_SVEC || h->mixed || h->opt.krylov != 0)
+      return fail(h, SDP_EUNSUPPORTED, "a linear block is built for the DENSE_SVEC kind, the FP64 form and PCG");
+    if (!h->lin_lam) {
+      cudaError_t e = cudaMalloc(&h->lin_lam, (size_t)h->m * sizeof(double));
+      if (e == cudaSuccess && h->b_elems > 0) e = cudaMalloc(&h->lin_Bw, (size_t)h->b_elems * sizeof(double));
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, SDP_ENOMEM, std::string("linear block workspace: ") + cudaGetErrorString(e));
+      }
+    }
+  }
+  h->lin = delta;
+  h->setup_valid = false;           // the preconditioner core depends on delta
+  for (auto& G : h->graph)          // captured graphs hold the old pointer
+    if (G.exec) {
+      cudaGraphExecDestroy(G.exec);
+      G.exec = nullptr;
+    }
+  return SDP_OK;
+}
+
 extern "C" void sdp_destroy(sdp_handle* h) {
   if (!h) return;
   if (h->st) cudaStreamSynchronize(h->st);
   if (h->pool) cudaFree(h->pool);
+  if (h->lin_lam) cudaFree(h->lin_lam);
+  if (h->lin_Bw) cudaFree(h->lin_Bw);
   if (h->ctl_host) cudaFreeHost(h->ctl_host);
   for (auto& e : h->ev) cudaEventDestroy(e);
   for (auto& e : h->ev_phase)

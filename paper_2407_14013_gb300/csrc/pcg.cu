@@ -42,10 +42,11 @@ ap_finish_kernel(int m, int d, int n, int r, const T* __restrict__ partA, int S,
                  const T* __restrict__ Vs, const T* __restrict__ H, const T* __restrict__ Dv,
                  const T* __restrict__ p, const T* __restrict__ g, T* __restrict__ out, int mode,
                  PcgCtl* __restrict__ ctl, double* __restrict__ dotbuf, unsigned int* __restrict__ counter,
-                 const float* __restrict__ partA32, int S32) {
+                 const float* __restrict__ partA32, int S32, const double* __restrict__ lin) {
   if (ctl->done) return;
   __shared__ double sh[32];
   const int nt = m + d;
+  const double itau2 = lin ? 1.0 / (ctl->tau * ctl->tau) : 0.0;
   double acc = 0.0;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nt; q += gridDim.x * blockDim.x) {
     double v;
@@ -53,6 +54,7 @@ ap_finish_kernel(int m, int d, int n, int r, const T* __restrict__ partA, int S,
       v = 0.0;
       for (int s = 0; s < S; ++s) v += (double)partA[(int64_t)s * m + q];
       for (int s = 0; s < S32; ++s) v += (double)partA32[(int64_t)s * m + q];
+      if (lin) v += lin[q] * itau2 * (double)p[q];   // linear block: tau^-2 diag(delta) p_u
       if (Up) {   // DIAG: A(sym(U Q^T)) = diag(U Q^T)
         for (int k = 0; k < r; ++k) v += (double)Up[q + (int64_t)k * n] * (double)Vs[q + (int64_t)k * n];
       }
@@ -138,13 +140,14 @@ __global__ void pc_d_zv_kernel(int m, int d, int S, const T* __restrict__ partC,
   z[m + h] = (T)(-t);
 }
 
-// z_u (d-space: beta^{-1}(r_u - B z_v); m-space: already formed) then <r, z> -> beta_pcg.
+// z_u (d-space: beta^{-1}(r_u - B z_v), or Lam^{-1}(r_u - B z_v) with a linear block; m-space:
+// already formed) then <r, z> -> beta_pcg.
 // mode 0 (start): rz = <r0, z0>;  mode 1 (iteration): beta = <r_{k+1}, z_{k+1}> / <r_k, z_k>.
 template <typename T>
 __global__ void __launch_bounds__(VT)
 pc_zu_dot_kernel(int m, int d, int S, const T* __restrict__ partU, int space, const T* __restrict__ rv,
                  T* __restrict__ z, int mode, PcgCtl* __restrict__ ctl, double* __restrict__ dotbuf,
-                 unsigned int* __restrict__ counter) {
+                 unsigned int* __restrict__ counter, const double* __restrict__ lam) {
   if (ctl->done) return;
   __shared__ double sh[32];
   const int nt = m + d;
@@ -155,7 +158,7 @@ pc_zu_dot_kernel(int m, int d, int S, const T* __restrict__ partU, int space, co
     if (q < m && partU) {
       double t = 0.0;
       for (int s = 0; s < S; ++s) t += (double)partU[(int64_t)s * m + q];
-      zq = (space == 1) ? ((double)rv[q] - t) * ib : t;
+      zq = (space == 1) ? ((double)rv[q] - t) * (lam ? 1.0 / lam[q] : ib) : t;
       z[q] = (T)zq;
     } else {
       zq = (double)z[q];
@@ -572,6 +575,29 @@ __global__ void recover_F_kernel(int n, const double* __restrict__ EYu, const do
 }
 
 // C += diag(Dv) * c_d + c_i * I  on an n x n matrix
+// linear block of the Newton system: Lam = beta + tau^-2 delta (the (1,1) block of the preconditioner)
+__global__ void lin_lam_kernel(int m, const double* __restrict__ delta, const PcgCtl* __restrict__ ctl,
+                               double* __restrict__ lam) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) lam[i] = ctl->beta_pc + delta[i] / (ctl->tau * ctl->tau);
+}
+
+// out = r_u / Lam (the first block of r only)
+__global__ void lin_div_kernel(int m, const double* __restrict__ r, const double* __restrict__ lam,
+                               double* __restrict__ out, const PcgCtl* __restrict__ ctl) {
+  if (ctl->done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) out[i] = r[i] / lam[i];
+}
+
+// Bw (d x m, col-major view of B row-major) = B with row i scaled by Lam_i^-1/2
+__global__ void lin_scale_rows_kernel(int m, int d, const double* __restrict__ B, const double* __restrict__ lam,
+                                      double* __restrict__ Bw) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)m * d) return;
+  Bw[q] = B[q] / sqrt(lam[q / d]);
+}
+
 __global__ void add_diag_kernel(int n, double* __restrict__ C, const double* __restrict__ Dv, double c_i) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -686,9 +712,10 @@ inline int vec_blocks(int nt) {
 template <typename T>
 void launch_ap_finish(cudaStream_t st, int m, int d, int n, int r, const T* partA, int S, const T* Up, const T* Vs,
                       const T* H, const T* Dv, const T* p, const T* g, T* out, int mode, PcgCtl* ctl,
-                      double* dotbuf, unsigned int* counter, int64_t* launches, const float* partA32, int S32) {
+                      double* dotbuf, unsigned int* counter, int64_t* launches, const float* partA32, int S32,
+                      const double* lin) {
   ap_finish_kernel<T><<<vec_blocks(m + d), VT, 0, st>>>(m, d, n, r, partA, S, Up, Vs, H, Dv, p, g, out, mode, ctl,
-                                                       dotbuf, counter, partA32, S32);
+                                                       dotbuf, counter, partA32, S32, lin);
   ++*launches;
 }
 
@@ -715,8 +742,9 @@ void launch_pc_d_zv(cudaStream_t st, int m, int d, int S, const T* partC, T* z, 
 
 template <typename T>
 void launch_pc_zu_dot(cudaStream_t st, int m, int d, int S, const T* partU, int space, const T* rv, T* z, int mode,
-                      PcgCtl* ctl, double* dotbuf, unsigned int* counter, int64_t* launches) {
-  pc_zu_dot_kernel<T><<<vec_blocks(m + d), VT, 0, st>>>(m, d, S, partU, space, rv, z, mode, ctl, dotbuf, counter);
+                      PcgCtl* ctl, double* dotbuf, unsigned int* counter, int64_t* launches, const double* lam) {
+  pc_zu_dot_kernel<T><<<vec_blocks(m + d), VT, 0, st>>>(m, d, S, partU, space, rv, z, mode, ctl, dotbuf, counter,
+                                                       lam);
   ++*launches;
 }
 
@@ -764,13 +792,13 @@ void launch_diag_scale_rows(cudaStream_t st, int n, int r, const T* pu, const T*
 #define WC_INSTANTIATE(T)                                                                                          \
   template void launch_ap_finish<T>(cudaStream_t, int, int, int, int, const T*, int, const T*, const T*, const T*,  \
                                     const T*, const T*, const T*, T*, int, PcgCtl*, double*, unsigned int*,          \
-                                    int64_t*, const float*, int);                                                   \
+                                    int64_t*, const float*, int, const double*);                                    \
   template void launch_update<T>(cudaStream_t, int, T*, T*, const T*, const T*, PcgCtl*, double*, unsigned int*,   \
                                  int64_t*);                                                                         \
   template void launch_pc_d_s<T>(cudaStream_t, int, int, int, const T*, const T*, T*, const PcgCtl*, int64_t*);      \
   template void launch_pc_d_zv<T>(cudaStream_t, int, int, int, const T*, T*, const PcgCtl*, int64_t*);              \
   template void launch_pc_zu_dot<T>(cudaStream_t, int, int, int, const T*, int, const T*, T*, int, PcgCtl*, double*, \
-                                    unsigned int*, int64_t*);                                                       \
+                                    unsigned int*, int64_t*, const double*);                                        \
   template void launch_pc_m_tv<T>(cudaStream_t, int, int, const T*, const T*, T*, const PcgCtl*, int64_t*);         \
   template void launch_pc_m_w<T>(cudaStream_t, int, int, const T*, const T*, T*, const PcgCtl*, int64_t*);          \
   template void launch_pc_m_zv<T>(cudaStream_t, int, int, int, const T*, const T*, const T*, T*, const PcgCtl*,     \
@@ -811,6 +839,23 @@ void launch_recover_pre(cudaStream_t st, int n, int m, const double* Yu, const d
 void launch_recover_F(cudaStream_t st, int n, const double* EYu, const double* E, const double* u, double* F,
                       const PcgCtl* ctl, int64_t* launches) {
   recover_F_kernel<<<nblk((int64_t)n * n, VT), VT, 0, st>>>(n, EYu, E, u, F, ctl);
+  ++*launches;
+}
+
+void launch_lin_lam(cudaStream_t st, int m, const double* delta, const PcgCtl* ctl, double* lam, int64_t* launches) {
+  lin_lam_kernel<<<nblk(m, VT), VT, 0, st>>>(m, delta, ctl, lam);
+  ++*launches;
+}
+
+void launch_lin_div(cudaStream_t st, int m, const double* r, const double* lam, double* out, const PcgCtl* ctl,
+                    int64_t* launches) {
+  lin_div_kernel<<<nblk(m, VT), VT, 0, st>>>(m, r, lam, out, ctl);
+  ++*launches;
+}
+
+void launch_lin_scale_rows(cudaStream_t st, int m, int d, const double* B, const double* lam, double* Bw,
+                           int64_t* launches) {
+  lin_scale_rows_kernel<<<nblk((int64_t)m * d, VT), VT, 0, st>>>(m, d, B, lam, Bw);
   ++*launches;
 }
 

@@ -13,7 +13,7 @@ template <typename T>
 void launch_ap_finish(cudaStream_t st, int m, int d, int n, int r, const T* partA, int S, const T* Up, const T* Vs,
                       const T* H, const T* Dv, const T* p, const T* g, T* out, int mode, PcgCtl* ctl,
                       double* dotbuf, unsigned int* counter, int64_t* launches, const float* partA32 = nullptr,
-                      int S32 = 0);
+                      int S32 = 0, const double* lin = nullptr);
 template <typename T>
 void launch_update(cudaStream_t st, int nt, T* x, T* rv, const T* p, const T* Ap, PcgCtl* ctl, double* dotbuf,
                    unsigned int* counter, int64_t* launches);
@@ -24,7 +24,8 @@ template <typename T>
 void launch_pc_d_zv(cudaStream_t st, int m, int d, int S, const T* partC, T* z, const PcgCtl* ctl, int64_t* launches);
 template <typename T>
 void launch_pc_zu_dot(cudaStream_t st, int m, int d, int S, const T* partU, int space, const T* rv, T* z, int mode,
-                      PcgCtl* ctl, double* dotbuf, unsigned int* counter, int64_t* launches);
+                      PcgCtl* ctl, double* dotbuf, unsigned int* counter, int64_t* launches,
+                      const double* lam = nullptr);
 template <typename T>
 void launch_pc_m_tv(cudaStream_t st, int m, int d, const T* rv, const T* Dv, T* t, const PcgCtl* ctl,
                     int64_t* launches);
@@ -54,6 +55,13 @@ void launch_recover_pre(cudaStream_t st, int n, int m, const double* Yu, const d
 // F = E A^T(u) - tau^2 F (EYu = E A^T(u), or NULL for the DIAG kind: E diag(u))
 void launch_recover_F(cudaStream_t st, int n, const double* EYu, const double* E, const double* u, double* F,
                       const PcgCtl* ctl, int64_t* launches);
+// Linear block of the Newton system (the nonnegative variables of Section 7's robust problems):
+// Lam = beta + tau^-2 delta; out = r_u / Lam; Bw = B with row i scaled by Lam_i^-1/2.
+void launch_lin_lam(cudaStream_t st, int m, const double* delta, const PcgCtl* ctl, double* lam, int64_t* launches);
+void launch_lin_div(cudaStream_t st, int m, const double* r, const double* lam, double* out, const PcgCtl* ctl,
+                    int64_t* launches);
+void launch_lin_scale_rows(cudaStream_t st, int m, int d, const double* B, const double* lam, double* Bw,
+                           int64_t* launches);
 void launch_add_diag(cudaStream_t st, int n, double* C, const double* Dv, double c_i, int64_t* launches);
 void launch_scale_B(cudaStream_t st, int m, int d, const double* B, const double* Dv, double* Bs, int64_t* launches);
 void launch_correction_rhs(cudaStream_t st, int m, int d, const double* rho, double* out, int64_t* launches);

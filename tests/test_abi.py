@@ -157,3 +157,11 @@ def test_batch_argument_errors_without_gpu():
     assert e.value.status == _native.SDP_EINVAL and "twice" in str(e.value)
     with pytest.raises(_native.SdpError):
         _native.sdp_solve_batch([16], [8], [8], [8], [8], [8], -1.0, 10)
+
+
+def test_linear_block_setter_validates_without_gpu():
+    """sdp_set_linear_diag refuses a NULL handle before any CUDA call."""
+    from paper_2407_14013_gb300 import _native
+    with pytest.raises(_native.SdpError) as e:
+        _native.sdp_set_linear_diag(0, 8)
+    assert e.value.status == _native.SDP_EINVAL and "NULL handle" in str(e.value)

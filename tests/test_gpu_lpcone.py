@@ -1,0 +1,74 @@
+"""GPU parity of the linear block of the Newton system (the nonnegative variables of Section 7's
+robust problems, eq. rmc-sdp): with sdp_set_linear_diag the Newton direction equals the oracle's
+plain definition (Schur system with G D G^T, oracle/lpcone.py) to the FP64 tolerance, in both
+preconditioner spaces; combinations that are not built are refused."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import lpcone
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-8
+
+
+def _t(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+CASES = [
+    # name, problem, r_true, mu, r_hat, preconditioner space (1 = d, 2 = m)
+    ("sensing12_d", lambda: W.sensing(12, 40, 2, 1201), 2, 1e-3, 4, 1),
+    ("sensing12_m", lambda: W.sensing(12, 40, 2, 1201), 2, 1e-3, 4, 2),
+    ("sensing37_d", lambda: W.sensing(37, 150, 3, 1202), 3, 1e-2, 5, 1),
+]
+
+
+@pytest.mark.parametrize("name,mk,rt,mu,rh,space", CASES, ids=[c[0] for c in CASES])
+def test_linear_block_direction_matches_definition(name, mk, rt, mu, rh, space):
+    from paper_2407_14013_gb300 import NewtonSolver
+    prob = mk()
+    m = prob.m
+    sp = W.scaling_point(prob.n, rt, mu, 1300 + prob.n)
+    Ct, bt = W.newton_rhs(prob.n, m, 1301 + prob.n)
+    g = np.random.default_rng(1302 + prob.n)
+    G = np.hstack([np.eye(m), -np.eye(m)])                # eq. rmc-sdp: x = [v; w]
+    d = 10.0 ** g.uniform(-3, 3, 2 * m)
+    ct = g.standard_normal(2 * m)
+    Wm = (sp.V * sp.lam) @ sp.V.T
+    rX, rx, ry = lpcone.newton_direct_lp(prob, Wm, Ct, bt, G, d, ct)
+    s = NewtonSolver(prob, r_hat=rh, precond_space=space)
+    s.set_linear_diag(d[:m] + d[m:])                      # delta = diag(G D G^T)
+    btl = bt + G @ (d * ct)                               # the caller folds G D c~ into b~
+    dX, dy, dS, info = s.solve(_t(sp.V), _t(sp.lam), _t(Ct), _t(btl))
+    assert info.converged and info.space == space
+    dX, dy = dX.cpu().numpy(), dy.cpu().numpy()
+    dx = d * (G.T @ dy - ct)
+    assert rel(dX, rX) < TOL and rel(dy, ry) < TOL and rel(dx, rx) < TOL
+    # removing the block gives back the semidefinite direction
+    s.set_linear_diag(None)
+    dX0, dy0, _, i0 = s.solve(_t(sp.V), _t(sp.lam), _t(Ct), _t(bt))
+    from oracle import newton as onewton
+    sX, sy, _ = onewton.newton_direct(prob, Wm, Ct, bt)
+    assert i0.converged and rel(dX0.cpu().numpy(), sX) < TOL and rel(dy0.cpu().numpy(), sy) < TOL
+    s.close()
+
+
+def test_linear_block_refused_where_not_built():
+    from paper_2407_14013_gb300 import NewtonSolver, SdpError, native
+    import torch
+    delta = torch.ones(20, dtype=torch.float64, device="cuda")
+    for kw, prob in ((dict(precision="mixed_fp32"), W.sensing(8, 20, 2, 1400)),
+                     (dict(krylov="minres"), W.sensing(8, 20, 2, 1401)),
+                     ({}, W.maxcut(20, 0.3, 1402))):
+        s = NewtonSolver(prob, r_hat=3, **kw)
+        with pytest.raises(SdpError) as e:
+            s.set_linear_diag(delta[:prob.m])
+        assert e.value.status == native.SDP_EUNSUPPORTED
+        s.close()
