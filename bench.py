@@ -232,7 +232,57 @@ def other_configs(dev, reps: int = 2, only=None, tc_n: int = 5000):
     # 256 independent SDPs of uneven size solved by sdp_solve_batch (minutes: only on request)
     if only == "batch256":
         out["batch256"] = _batch256(dev)
+    # the headline workload with a linear block of outlier slacks (eq. rmc-sdp form, dense A; on request)
+    if only == "lp_sensing200":
+        out["lp_sensing200"] = _lp_sensing(dev, reps)
     return out
+
+
+def _lp_sensing(dev, reps):
+    """Newton solves of the n = 200, m = 2000 sensing workload with nonnegative slacks v, w entering
+    as A(X) + v - w = b (the form of eq. rmc-sdp): delta = d_v + d_w with d = x / z spread over
+    1e-3 .. 1e3, the caller's right side b~ + G D c~, and dx = D(G^T dy - c~) formed on the host.
+    Reports the time per solve, the PCG iterations, and the residual of the first primal block
+    ||A(dX) + G dx - b~|| / ||b~|| (numpy FP64 on the host)."""
+    import numpy as np
+    import torch
+    from paper_2407_14013_gb300 import NewtonSolver
+    prob, ins = make_inputs()
+    m = prob.m
+    g = np.random.default_rng(4242)
+    d = 10.0 ** g.uniform(-3, 3, 2 * m)
+    ct = g.standard_normal(2 * m)
+    dv, dw, cv, cw = d[:m], d[m:], ct[:m], ct[m:]
+    s = NewtonSolver(prob, r_hat=RANK, device=str(dev))
+    s.set_linear_diag(dv + dw)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    args = [(t(V), t(lam), t(Ct), t(bt + dv * cv - dw * cw)) for (V, lam, Ct, bt) in ins]
+    s.solve(*args[0])
+    torch.cuda.synchronize(dev)
+    ms, iters = [], 0
+    for k in range(max(reps, 3)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        dX, dy, _, info = s.solve(*args[k % len(args)])
+        e1.record(s.stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        iters += info.pcg_iters
+        assert info.converged, "Newton solve with the linear block did not converge"
+    V, lam, Ct, bt = ins[(len(ms) - 1) % len(args)]
+    dyh = dy.cpu().numpy()
+    Gdx = dv * (dyh - cv) - dw * (-dyh - cw)              # G dx with dx = D(G^T dy - c~), G = [I, -I]
+    n = prob.n
+    rows, cols = np.tril_indices(n)
+    order = np.lexsort((rows, cols))
+    rows, cols = rows[order], cols[order]
+    x = dX.cpu().numpy()[rows, cols] * np.where(rows == cols, 1.0, np.sqrt(2.0))
+    primal = float(np.linalg.norm(prob.a_dense @ x + Gdx - bt) / np.linalg.norm(bt))
+    s.close()
+    return {"workload": "matrix sensing n=200 m=2000 with slacks v, w >= 0 (A(X) + v - w = b), d = x/z in "
+                        "1e-3..1e3, r_hat=3, FP64",
+            "ms_per_solve": sum(ms) / len(ms), "pcg_iters_per_solve": iters / len(ms),
+            "matvecs_per_s": iters / (sum(ms) / 1e3), "primal_rel_residual": primal}
 
 
 def _completion_solve(dev):
@@ -690,7 +740,7 @@ def main():
     ap.add_argument("--no-ttg", action="store_true", help="skip the time-to-gap solves")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads (MaxCut 64 / 5000, completion)")
     ap.add_argument("--only", choices=["maxcut64", "maxcut5000", "completion2000", "tc_gemm", "batch32",
-                                       "completion2000_solve", "batch256"],
+                                       "completion2000_solve", "batch256", "lp_sensing200"],
                     help="measure only this other workload (one JSON object; no headline line)")
     ap.add_argument("--reps", type=int, default=2, help="timed Newton solves per row of the other workloads")
     ap.add_argument("--tc-n", type=int, default=5000, help="order of the tensor-core product row (--only tc_gemm)")
