@@ -240,8 +240,9 @@ sdp_status sdp_solve(sdp_handle* h, const double* b, const double* C, double* X,
  * C = tau^2 Sigma + B^T Lam^{-1} B; m-space: K = Lam + B (tau^2 Sigma)^{-1} B^T).  The caller
  * folds the linear block's right side into b~ (b~ + G D c~) and forms dx = D(G^T dy - c~).
  * delta: device pointer to m values >= 0, owned by the caller and read by every later Newton solve
- * of the handle, or NULL to remove the block.  DENSE_SVEC kind, FP64 form and PCG only
- * (otherwise SDP_EUNSUPPORTED); the setup of the next solve is redone (no resolve before it).
+ * of the handle, or NULL to remove the block.  DENSE_SVEC and SPARSE_COO kinds, FP64 form and
+ * PCG only (otherwise SDP_EUNSUPPORTED); the setup of the next solve is redone (no resolve
+ * before it).
  * SDP_ENOMEM if the workspace of the block (m + m d_max doubles) cannot be allocated. */
 sdp_status sdp_set_linear_diag(sdp_handle* h, const double* delta);
 

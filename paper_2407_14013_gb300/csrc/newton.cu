@@ -652,7 +652,7 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
     join(h, 1, 3);
     sparse_apply_pos(st, h->sp, n, m, r, S.zpos, S.Up, Q, S.partA, done, L);   // A(E Y E + sym(Up Q^T))
     launch_ap_finish<double>(st, m, d, n, r, S.partA, 1, nullptr, S.Vs, S.H, S.Dv, pin, gsub, out, mode, S.ctl,
-                             h->dotbuf, h->counter, L);
+                             h->dotbuf, h->counter, L, nullptr, 0, h->lin);   // + tau^-2 delta p_u
   } else {
     launch_diag_scale_rows<double>(st, n, r, pu, S.Vs, S.Tm, done, L);  // A^T(p_u) Q = diag(p_u) Q
     CU(gemm_big(h, st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, 0, done));
@@ -741,16 +741,18 @@ sdp_status apply_precond(sdp_handle* h, Space& S, const double* rin, double* zou
     const int n = h->n, r = h->r;
     const double* Q = S.Vs;
     if (h->space == 1) {
-      sparse_posval(st, h->sp, rin, S.ypos, done, L);
+      if (h->lin) launch_lin_div(st, m, rin, h->lin_lam, S.wm, S.ctl, L);   // Lam^{-1} r_u (linear block)
+      sparse_posval(st, h->sp, h->lin ? S.wm : rin, S.ypos, done, L);
       sparse_sym_spmm(st, h->sp, n, r, S.ypos, Q, n, S.Tm, n, done, L);
       CU(gemm_big(h, st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, 0, done));
-      launch_pc_d_s_H(st, m, d, n, r, S.H, rin, S.sd, S.ctl, L);           // s = r_v - beta^{-1} B^T r_u
+      launch_pc_d_s_H(st, m, d, n, r, S.H, rin, S.sd, S.ctl, L, h->lin != nullptr);   // s = r_v - B^T Lam^{-1} r_u
       rows_gemv<double>(st, S.Pinv, d, d, S.sd, S.partC, done, L);          // C^{-1} s
       launch_pc_d_zv<double>(st, m, d, rows_gemv_slabs(d, d), S.partC, zout, S.ctl, L);   // z_v = -C^{-1} s
       h_unpack<double>(st, n, r, zout + m, S.Hp, done, L);
       CU(gemm_big(h, st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, S.ws_elems, L, 0, done));
       sparse_apply_pos(st, h->sp, n, m, r, nullptr, S.Up, Q, S.partA, done, L);  // B z_v
-      launch_pc_zu_dot<double>(st, m, d, 1, S.partA, 1, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L);
+      launch_pc_zu_dot<double>(st, m, d, 1, S.partA, 1, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L,
+                               h->lin ? h->lin_lam : nullptr);
     } else {
       h_unpack<double>(st, n, r, rin + m, S.Hp, done, L, S.Dv);            // unpack(D^{-1} r_v)
       CU(gemm_big(h, st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, S.ws_elems, L, 0, done));
@@ -1321,8 +1323,9 @@ extern "C" const char* sdp_last_error(const sdp_handle* h) {
 extern "C" sdp_status sdp_set_linear_diag(sdp_handle* h, const double* delta) {
   if (!h) return fail(nullptr, SDP_EINVAL, "NULL handle");
   if (delta) {
-    if (h->kind != SDP_A_DENSE_SVEC || h->mixed || h->opt.krylov != 0)
-      return fail(h, SDP_EUNSUPPORTED, "a linear block is built for the DENSE_SVEC kind, the FP64 form and PCG");
+    if (h->kind == SDP_A_DIAG || h->mixed || h->opt.krylov != 0)
+      return fail(h, SDP_EUNSUPPORTED,
+                  "a linear block is built for the DENSE_SVEC and SPARSE_COO kinds, the FP64 form and PCG");
     if (!h->lin_lam) {
       cudaError_t e = cudaMalloc(&h->lin_lam, (size_t)h->m * sizeof(double));
       if (e == cudaSuccess && h->b_elems > 0) e = cudaMalloc(&h->lin_Bw, (size_t)h->b_elems * sizeof(double));

@@ -237,11 +237,12 @@ __global__ void diag_zv_kernel(int m, int d, int n, int r, const double* __restr
 // d-space with B^T r_u = pack(H): s = r_v - beta^{-1} pack(H)
 __global__ void pc_d_s_H_kernel(int m, int d, int n, int r, const double* __restrict__ H,
                                 const double* __restrict__ rv, double* __restrict__ s,
-                                const PcgCtl* __restrict__ ctl) {
+                                const PcgCtl* __restrict__ ctl, int scaled) {
   if (ctl->done) return;
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= d) return;
-  s[h] = rv[m + h] - pack_at(H, n, n, r, h) / ctl->beta_pc;
+  // scaled: H came from Lam^{-1} r_u (linear block), so no division by beta
+  s[h] = rv[m + h] - (scaled ? pack_at(H, n, n, r, h) : pack_at(H, n, n, r, h) / ctl->beta_pc);
 }
 
 // Tm = Q (Lam - tau I): the first r columns of Vs scaled by lam_j - tau
@@ -911,8 +912,8 @@ void launch_diag_zv(cudaStream_t st, int m, int d, int n, int r, const double* H
 }
 
 void launch_pc_d_s_H(cudaStream_t st, int m, int d, int n, int r, const double* H, const double* rv, double* s,
-                     const PcgCtl* ctl, int64_t* launches) {
-  pc_d_s_H_kernel<<<nblk(d, VT), VT, 0, st>>>(m, d, n, r, H, rv, s, ctl);
+                     const PcgCtl* ctl, int64_t* launches, bool scaled) {
+  pc_d_s_H_kernel<<<nblk(d, VT), VT, 0, st>>>(m, d, n, r, H, rv, s, ctl, scaled ? 1 : 0);
   ++*launches;
 }
 

@@ -92,7 +92,7 @@ void launch_minres_beta(cudaStream_t st, int nt, const double* y, double* r1, do
 void launch_minres_update(cudaStream_t st, int nt, const double* v, double* w, double* w1, double* w2, double* x,
                           const MinresCtl* mc, const PcgCtl* ctl, int64_t* launches);
 void launch_pc_d_s_H(cudaStream_t st, int m, int d, int n, int r, const double* H, const double* rv, double* s,
-                     const PcgCtl* ctl, int64_t* launches);
+                     const PcgCtl* ctl, int64_t* launches, bool scaled = false);
 void launch_shift_cols(cudaStream_t st, int n, int r, const double* Vs, const double* lam_s, const PcgCtl* ctl,
                        double* Tm, int64_t* launches);
 void launch_diag_K(cudaStream_t st, int n, const double* G, const double* E, const PcgCtl* ctl, double* K,

@@ -1,7 +1,8 @@
 """GPU parity of the linear block of the Newton system (the nonnegative variables of Section 7's
 robust problems, eq. rmc-sdp): with sdp_set_linear_diag the Newton direction equals the oracle's
 plain definition (Schur system with G D G^T, oracle/lpcone.py) to the FP64 tolerance, in both
-preconditioner spaces; combinations that are not built are refused."""
+preconditioner spaces, for dense constraints and for robust matrix completion (SPARSE_COO);
+combinations that are not built are refused."""
 import numpy as np
 import pytest
 
@@ -27,6 +28,9 @@ CASES = [
     ("sensing12_d", lambda: W.sensing(12, 40, 2, 1201), 2, 1e-3, 4, 1),
     ("sensing12_m", lambda: W.sensing(12, 40, 2, 1201), 2, 1e-3, 4, 2),
     ("sensing37_d", lambda: W.sensing(37, 150, 3, 1202), 3, 1e-2, 5, 1),
+    # robust matrix completion (Section 7, eq. rmc-sdp): single svec entries, SPARSE_COO kind
+    ("rmc20_d", lambda: W.rmc(20, 90, 5, 1203), 2, 1e-3, 3, 1),
+    ("rmc20_m", lambda: W.rmc(20, 60, 4, 1204), 2, 1e-3, 3, 2),
 ]
 
 
