@@ -82,3 +82,56 @@ def test_extended_preconditioner_is_the_exact_block_inverse(space):
     assert np.linalg.norm(back - z) <= 1e-10 * np.linalg.norm(z) * np.linalg.cond(Pm) ** 0.5
     with pytest.raises(ValueError):
         lpcone.precond_setup_lp(prob, s, np.ones((prob.m, 2)), np.ones(2))   # a variable in every row
+
+
+def _solve_rmc(n, m, m_o, seed):
+    from oracle import ipm_lp
+    prob = W.rmc(n, m, m_o, seed)
+    res = ipm_lp.ipm_solve_lp(prob, prob.meta["G_l"], prob.meta["c_l"], tol=1e-8)
+    return prob, res
+
+
+def test_rmc_without_outliers_recovers_the_planted_matrix():
+    """Exact measurements of a rank-2 matrix on 45 of the 55 svec coordinates (n = 10): the
+    robust-completion SDP returns X* (recovery expected at this sampling), v = w = 0, and a dual
+    point with |y_i| <= 1 (the dual constraints of v, w >= 0 with unit cost)."""
+    prob, res = _solve_rmc(10, 45, 0, 7)
+    Xs = prob.meta["Xs"]
+    assert res.converged
+    assert np.linalg.norm(res.X - Xs) <= 1e-6 * np.linalg.norm(Xs)
+    m = prob.m
+    assert np.abs(res.x[:m] - res.x[m:]).max() <= 1e-6 * (1 + np.abs(prob.b).max())
+    assert np.abs(res.y).max() <= 1 + 1e-8
+
+
+def test_rmc_with_outliers_finds_them_and_the_matrix():
+    """Three gross outliers among 70 measurements (n = 12): X* is still recovered, v - w is the
+    outlier vector (its support is the outlier set), |y_i| = 1 on the outliers (complementary
+    slackness with the unit cost of v, w), and the optimal value is tr X* + sum |eps_i|
+    (lambda = 1), the objective of the recovered point."""
+    prob, res = _solve_rmc(12, 70, 3, 9)
+    m = prob.m
+    Xs, eps, out = prob.meta["Xs"], prob.meta["eps"], prob.meta["outliers"]
+    assert res.converged
+    assert np.linalg.norm(res.X - Xs) <= 1e-6 * np.linalg.norm(Xs)
+    vw = res.x[:m] - res.x[m:]
+    assert set(np.where(np.abs(vw) > 1e-3)[0].tolist()) == set(out.tolist())
+    assert np.allclose(vw[out], eps[out], rtol=1e-6, atol=1e-6)
+    assert np.allclose(np.abs(res.y[out]), 1.0, atol=1e-6) and np.abs(res.y).max() <= 1 + 1e-8
+    pobj = float(np.trace(res.X) + res.x.sum())
+    assert abs(pobj - (np.trace(Xs) + np.abs(eps).sum())) <= 1e-6 * pobj
+
+
+def test_lp_outer_loop_meets_the_optimality_conditions():
+    """At the returned point: primal and dual feasibility and the relative gap within 1e-8,
+    X, S positive semidefinite, x, z positive, and small complementarity."""
+    prob, res = _solve_rmc(10, 45, 2, 8)
+    from oracle import ipm_lp
+    G, cl = prob.meta["G_l"], prob.meta["c_l"]
+    st = ipm_lp.LPState(X=res.X, x=res.x, y=res.y, S=res.S, z=res.z)
+    pobj, dobj, gap, pinf, dinf, *_ = ipm_lp.lp_measures(prob, G, cl, st)
+    assert res.converged and gap <= 1e-8 and pinf <= 1e-8 and dinf <= 1e-8
+    assert np.linalg.eigvalsh(res.X).min() > -1e-10 and np.linalg.eigvalsh(res.S).min() > -1e-10
+    assert res.x.min() > 0 and res.z.min() > 0
+    comp = float(np.sum(res.X * res.S) + res.x @ res.z)
+    assert comp <= 1e-6 * (1 + abs(pobj))
