@@ -242,7 +242,8 @@ sdp_status sdp_solve(sdp_handle* h, const double* b, const double* C, double* X,
  * delta: device pointer to m values >= 0, owned by the caller and read by every later Newton solve
  * of the handle, or NULL to remove the block.  DENSE_SVEC and SPARSE_COO kinds, FP64 form and
  * PCG only (otherwise SDP_EUNSUPPORTED); the setup of the next solve is redone (no resolve
- * before it).
+ * before it).  While a block is set, sdp_solve, ipm_step, sdp_solve_batch and sdp_grad (which
+ * have no nonnegative variables) return SDP_EUNSUPPORTED.
  * SDP_ENOMEM if the workspace of the block (m + m d_max doubles) cannot be allocated. */
 sdp_status sdp_set_linear_diag(sdp_handle* h, const double* delta);
 

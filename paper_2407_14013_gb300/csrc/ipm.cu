@@ -571,6 +571,9 @@ sdp_status check_args(sdp_handle* h, const double* b, const double* C, double* X
   if (!b || !C || !X || !y || !S) return wc_fail(h, SDP_EINVAL, "NULL array argument");
   if (h->kind != SDP_A_DENSE_SVEC && h->kind != SDP_A_DIAG && h->kind != SDP_A_SPARSE_COO)
     return wc_fail(h, SDP_EUNSUPPORTED, "constraint kind not built");
+  if (h->lin)
+    return wc_fail(h, SDP_EUNSUPPORTED,
+                   "the outer loop has no nonnegative variables: remove the linear block first");
   return ensure_workspace(h);
 }
 
@@ -718,6 +721,8 @@ extern "C" sdp_status sdp_solve_batch(int32_t count, sdp_handle* const* hs, cons
   // the interior-point workspaces first (allocation is not left to the concurrent solves)
   for (int32_t i = 0; i < count; ++i) {
     sdp_handle* h = hs[i];
+    if (h->lin)
+      return wc_fail(nullptr, SDP_EUNSUPPORTED, "the outer loop has no nonnegative variables: remove the linear block");
     if (cudaSetDevice(h->dev) != cudaSuccess) return wc_fail(nullptr, SDP_ECUDA, "cudaSetDevice failed");
     sdp_status s = ensure_workspace(h);
     if (s != SDP_OK) {

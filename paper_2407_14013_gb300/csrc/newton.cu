@@ -1263,6 +1263,7 @@ extern "C" sdp_status sdp_grad(sdp_handle* h, const double* V, const double* lam
                                const double* gy, double* gC, double* gb, sdp_newton_info* info) {
   if (!h) return fail(nullptr, SDP_EINVAL, "NULL handle");
   if (!V || !lam || !gX || !gy || !gC || !gb) return fail(h, SDP_EINVAL, "NULL array argument");
+  if (h->lin) return fail(h, SDP_EUNSUPPORTED, "the adjoint has no nonnegative variables: remove the linear block");
   // (C~, b~) = (sym gX, gy); the handle's host-staging buffers hold sym gX and the unused dS
   launch_sym_copy(h->st, h->n, gX, h->hCt, &h->launches);
   CU(cudaGetLastError());

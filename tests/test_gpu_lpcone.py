@@ -55,6 +55,11 @@ def test_linear_block_direction_matches_definition(name, mk, rt, mu, rh, space):
     dX, dy = dX.cpu().numpy(), dy.cpu().numpy()
     dx = d * (G.T @ dy - ct)
     assert rel(dX, rX) < TOL and rel(dy, ry) < TOL and rel(dx, rx) < TOL
+    # the outer loop and the adjoint have no nonnegative variables: refused while the block is set
+    from paper_2407_14013_gb300 import SdpError, native
+    with pytest.raises(SdpError) as e:
+        s.solve_sdp(_t(prob.b), _t(prob.C), gap_tol=1e-2, max_iter=1)
+    assert e.value.status == native.SDP_EUNSUPPORTED
     # removing the block gives back the semidefinite direction
     s.set_linear_diag(None)
     dX0, dy0, _, i0 = s.solve(_t(sp.V), _t(sp.lam), _t(Ct), _t(bt))
