@@ -247,6 +247,19 @@ sdp_status sdp_solve(sdp_handle* h, const double* b, const double* C, double* X,
  * SDP_ENOMEM if the workspace of the block (m + m d_max doubles) cannot be allocated. */
 sdp_status sdp_set_linear_diag(sdp_handle* h, const double* delta);
 
+/* Whole solve of the robust form with slacks (Section 7, eq. rmc-sdp):
+ *   min <C, X> + cv^T v + cw^T w   s.t.   A(X) + v - w = b,   X PSD,   v, w >= 0
+ * (dual: max b^T y with C - A^T(y) = S PSD, zv = cv - y >= 0, zw = cw + y >= 0).  The method of
+ * sdp_solve with the orthant added: mu = (<X, S> + v^T zv + w^T zw) / (n + 2 m), the Newton
+ * directions with the linear block delta = v/zv + w/zw (sdp_set_linear_diag, set and removed by
+ * this call), the ratio test for v, w (primal) and zv, zw (dual), and the stop test of sdp_solve
+ * with the slack terms in the objective and in the dual residual.  Start X = S = xi I, y = 0,
+ * v = w = zv = zw = xi.  cv, cw: device inputs (m, > 0); X, y, S, v, w, zv, zw: device outputs.
+ * DENSE_SVEC and SPARSE_COO kinds, FP64 form, PCG (as sdp_set_linear_diag). */
+sdp_status sdp_solve_slack(sdp_handle* h, const double* b, const double* C, const double* cv, const double* cw,
+                           double* X, double* y, double* S, double* v, double* w, double* zv, double* zw,
+                           double gap_tol, int32_t max_iter, sdp_ipm_info* info);
+
 /* The NT scaling point of an iterate (eq. newt), as the Newton solve and the adjoint take it:
  * W = L (L^T S L)^{-1/2} L^T with X = L L^T, computed as G G^T with G = L U Gamma^{-1/4}
  * (L^T S L = U Gamma U^T), and its eigen-decomposition W = V diag(lam) V^T (Jacobi, FP64; both

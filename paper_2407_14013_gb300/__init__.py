@@ -236,6 +236,23 @@ class NewtonSolver:
         info["status"] = st
         return X, y, S, info
 
+    def solve_slack(self, b, C, cv, cw, gap_tol: float = 1e-8, max_iter: int = 100, allow_notconv: bool = False):
+        """Whole solve of min <C,X> + cv^T v + cw^T w s.t. A(X) + v - w = b, X PSD, v, w >= 0 (the
+        robust form of Section 7, sdp_solve_slack); returns (X, y, S, v, w, zv, zw, info)."""
+        torch = self.torch
+        f64 = torch.float64
+        n, m = self.n, self.m
+        b, C, cv, cw = (t.to(device=self.device, dtype=f64).contiguous() for t in (b, C, cv, cw))
+        X = torch.empty((n, n), dtype=f64, device=self.device)
+        S = torch.empty((n, n), dtype=f64, device=self.device)
+        y, v, w, zv, zw = (torch.empty(m, dtype=f64, device=self.device) for _ in range(5))
+        ci = native.sdp_ipm_info()
+        st = native.sdp_solve_slack(self.handle, [_ptr(t) for t in (b, C, cv, cw, X, y, S, v, w, zv, zw)], gap_tol,
+                                    max_iter, ci, allow_notconv=allow_notconv)
+        info = ci.as_dict()
+        info["status"] = st
+        return X, y, S, v, w, zv, zw, info
+
     def set_linear_diag(self, delta=None):
         """Nonnegative variables entering the constraints (sdp_set_linear_diag): every later solve
         adds diag(delta) to the Schur matrix, delta = diag(G D G^T) >= 0 (m values).  The caller

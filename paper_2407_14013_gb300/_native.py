@@ -61,6 +61,7 @@ class sdp_ipm_info(ctypes.Structure):
 EXPORTS = {
     "sdp_default_options": (None, [POINTER(sdp_options)]),
     "sdp_set_linear_diag": (c_int32, [c_void_p, c_void_p]),
+    "sdp_solve_slack": (c_int32, [c_void_p] + [c_void_p] * 11 + [c_double, c_int32, POINTER(sdp_ipm_info)]),
     "sdp_setup": (c_int32, [POINTER(sdp_problem), POINTER(sdp_options), c_void_p, POINTER(c_void_p)]),
     "sdp_newton_solve": (c_int32, [c_void_p] + [c_void_p] * 7 + [POINTER(sdp_newton_info)]),
     "sdp_newton_solve_host": (c_int32, [c_void_p] + [c_void_p] * 7 + [POINTER(sdp_newton_info)]),
@@ -183,6 +184,16 @@ def sdp_solve(h: int, b: int, C: int, X: int, y: int, S: int, gap_tol: float, ma
     lib = load()
     st = lib.sdp_solve(c_void_p(h), c_void_p(b), c_void_p(C), c_void_p(X), c_void_p(y), c_void_p(S), gap_tol,
                        max_iter, ctypes.byref(info))
+    if st != SDP_OK and not (allow_notconv and st == SDP_ENOTCONV):
+        raise SdpError(st, lib.sdp_last_error(c_void_p(h)).decode())
+    return st
+
+
+def sdp_solve_slack(h: int, ptrs, gap_tol: float, max_iter: int, info: sdp_ipm_info,
+                    allow_notconv: bool = False) -> int:
+    """sdp_solve_slack with ptrs = (b, C, cv, cw, X, y, S, v, w, zv, zw) device pointers."""
+    lib = load()
+    st = lib.sdp_solve_slack(c_void_p(h), *[c_void_p(p) for p in ptrs], gap_tol, max_iter, ctypes.byref(info))
     if st != SDP_OK and not (allow_notconv and st == SDP_ENOTCONV):
         raise SdpError(st, lib.sdp_last_error(c_void_p(h)).decode())
     return st

@@ -53,6 +53,11 @@ struct IpmWork {
   int32_t* status = nullptr;
   double xi = 0.0;
   EighGraph eg[2];   // Jacobi sweeps for L^T S L, and for W and the step-length matrices
+  // slack variables of the robust form (sdp_solve_slack), allocated on first use
+  double* lp_pool = nullptr;
+  double *delta = nullptr, *rlv = nullptr, *rlw = nullptr, *ctv = nullptr, *ctw = nullptr, *btl = nullptr;
+  double *dv = nullptr, *dw = nullptr, *dzv = nullptr, *dzw = nullptr;
+  double *dva = nullptr, *dwa = nullptr, *dzva = nullptr, *dzwa = nullptr;
 };
 
 }  // namespace wc
@@ -61,7 +66,7 @@ namespace {
 
 constexpr int IT = 256;
 constexpr int kDotBlocks = 128;
-constexpr int kDots = 16;
+constexpr int kDots = 32;
 
 inline unsigned nb(int64_t total) { return (unsigned)((total + IT - 1) / IT); }
 
@@ -192,6 +197,122 @@ __global__ void row_sumsq_kernel(const double* __restrict__ A, int m, int64_t N,
   for (int64_t k = lane; k < N; k += 32) acc = fma(row[k], row[k], acc);
   acc = warp_sum(acc);
   if (lane == 0) out[w] = acc;
+}
+
+// ---- slack variables of the robust form: A(X) + v - w = b, v, w >= 0 (eq. rmc-sdp) ----
+
+// rp -= v - w;  rlv = cv - y - zv;  rlw = cw + y - zw  (the dual constraints of v and w)
+__global__ void slack_resid_kernel(int m, const double* __restrict__ v, const double* __restrict__ w,
+                                   const double* __restrict__ y, const double* __restrict__ zv,
+                                   const double* __restrict__ zw, const double* __restrict__ cv,
+                                   const double* __restrict__ cw, double* __restrict__ rp, double* __restrict__ rlv,
+                                   double* __restrict__ rlw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  rp[i] -= v[i] - w[i];
+  rlv[i] = cv[i] - y[i] - zv[i];
+  rlw[i] = cw[i] + y[i] - zw[i];
+}
+
+// delta = v / zv + w / zw  (diag(G D G^T) with G = [I, -I], D = diag(x / z))
+__global__ void slack_delta_kernel(int m, const double* __restrict__ v, const double* __restrict__ w,
+                                   const double* __restrict__ zv, const double* __restrict__ zw,
+                                   double* __restrict__ delta) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) delta[i] = v[i] / zv[i] + w[i] / zw[i];
+}
+
+// right side of the Newton system: r_x = smu - x z (- dx_a dz_a in the corrector),
+// c~ = r_l - r_x / x, and b~ = r_p + G D c~ = r_p + d_v c~_v - d_w c~_w
+__global__ void slack_rhs_kernel(int m, double smu, int corr, const double* __restrict__ v,
+                                 const double* __restrict__ w, const double* __restrict__ zv,
+                                 const double* __restrict__ zw, const double* __restrict__ dva,
+                                 const double* __restrict__ dwa, const double* __restrict__ dzva,
+                                 const double* __restrict__ dzwa, const double* __restrict__ rlv,
+                                 const double* __restrict__ rlw, const double* __restrict__ rp,
+                                 double* __restrict__ ctv, double* __restrict__ ctw, double* __restrict__ btl) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const double rxv = smu - v[i] * zv[i] - (corr ? dva[i] * dzva[i] : 0.0);
+  const double rxw = smu - w[i] * zw[i] - (corr ? dwa[i] * dzwa[i] : 0.0);
+  const double cv_ = rlv[i] - rxv / v[i], cw_ = rlw[i] - rxw / w[i];
+  ctv[i] = cv_;
+  ctw[i] = cw_;
+  btl[i] = rp[i] + (v[i] / zv[i]) * cv_ - (w[i] / zw[i]) * cw_;
+}
+
+// dx = D (G^T dy - c~):  dv = d_v (dy - c~_v), dw = d_w (-dy - c~_w);  dz = r_l - G^T dy
+__global__ void slack_dir_kernel(int m, const double* __restrict__ v, const double* __restrict__ w,
+                                 const double* __restrict__ zv, const double* __restrict__ zw,
+                                 const double* __restrict__ ctv, const double* __restrict__ ctw,
+                                 const double* __restrict__ rlv, const double* __restrict__ rlw,
+                                 const double* __restrict__ dy, double* __restrict__ dv, double* __restrict__ dw,
+                                 double* __restrict__ dzv, double* __restrict__ dzw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  dv[i] = (v[i] / zv[i]) * (dy[i] - ctv[i]);
+  dw[i] = (w[i] / zw[i]) * (-dy[i] - ctw[i]);
+  dzv[i] = rlv[i] - dy[i];
+  dzw[i] = rlw[i] + dy[i];
+}
+
+__device__ __forceinline__ double block_min(double v, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = (threadIdx.x < nw) ? sh[threadIdx.x] : INFINITY;
+  if (wid == 0)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fmin(t, __shfl_xor_sync(0xffffffffu, t, o));
+  if (threadIdx.x == 0) sh[0] = t;
+  __syncthreads();
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// ratio test: min over i of -a_i / da_i (da_i < 0) and -b_i / db_i (db_i < 0), per block
+__global__ void ratio_partial_kernel(int m, const double* __restrict__ a, const double* __restrict__ da,
+                                     const double* __restrict__ b, const double* __restrict__ db,
+                                     double* __restrict__ part) {
+  __shared__ double sh[32];
+  double r = INFINITY;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    if (da[i] < 0.0) r = fmin(r, -a[i] / da[i]);
+    if (db[i] < 0.0) r = fmin(r, -b[i] / db[i]);
+  }
+  r = block_min(r, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = r;
+}
+
+__global__ void min_final_kernel(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double r = INFINITY;
+  for (int q = threadIdx.x; q < nparts; q += blockDim.x) r = fmin(r, part[q]);
+  r = block_min(r, sh);
+  if (threadIdx.x == 0) *out = r;
+}
+
+// sum of (v + ap dv)(zv + ad dzv) + (w + ap dw)(zw + ad dzw), per block
+__global__ void slack_muaff_kernel(int m, double ap, double ad, const double* __restrict__ v,
+                                   const double* __restrict__ dv, const double* __restrict__ zv,
+                                   const double* __restrict__ dzv, const double* __restrict__ w,
+                                   const double* __restrict__ dw, const double* __restrict__ zw,
+                                   const double* __restrict__ dzw, double* __restrict__ part) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    acc += (v[i] + ap * dv[i]) * (zv[i] + ad * dzv[i]) + (w[i] + ap * dw[i]) * (zw[i] + ad * dzw[i]);
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void fill_kernel(int m, double val, double* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) x[i] = val;
 }
 
 struct Ctx {
@@ -566,6 +687,207 @@ sdp_status step(Ctx& c, double* X, double* y, double* S, const Measures& Mz, sdp
   return SDP_OK;
 }
 
+// start X = S = xi I, y = 0, xi = max(10, sqrt n, max_i (1+|b_i|)/(1+||A_i||_F), (1+||C||_F)/sqrt n)
+sdp_status start(Ctx& c, const double* b, const double* C, double* X, double* y, double* S) {
+  sdp_handle* h = c.h;
+  IpmWork* w = c.w;
+  const int n = c.n, m = c.m;
+  std::vector<double> bh(m), rn(m, 1.0);
+  CUI(cudaMemcpyAsync(bh.data(), b, m * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  if (h->kind == SDP_A_DENSE_SVEC) {
+    row_sumsq_kernel<<<(unsigned)((m * 32 + IT - 1) / IT), IT, 0, h->st>>>(h->a_dense, m, h->N, w->rownrm);
+    CUI(cudaMemcpyAsync(rn.data(), w->rownrm, m * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  }
+  dot(c, (int64_t)n * n, C, nullptr, 6);
+  double cc = 0.0;
+  CUI(cudaMemcpyAsync(&cc, w->dots + 6, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CUI(cudaStreamSynchronize(h->st));
+  double xi = std::max(10.0, std::sqrt((double)n));
+  for (int i = 0; i < m; ++i) {
+    const double an = (h->kind == SDP_A_DENSE_SVEC) ? std::sqrt(rn[i])
+                      : (h->kind == SDP_A_SPARSE_COO) ? std::sqrt(h->sp_rownorm2[i]) : 1.0;
+    xi = std::max(xi, (1.0 + std::fabs(bh[i])) / (1.0 + an));
+  }
+  xi = std::max(xi, (1.0 + std::sqrt(cc)) / std::sqrt((double)n));
+  w->xi = xi;
+  w->have_prev = false;
+  scaled_identity_kernel<<<nb((int64_t)n * n), IT, 0, h->st>>>(n, xi, X);
+  scaled_identity_kernel<<<nb((int64_t)n * n), IT, 0, h->st>>>(n, xi, S);
+  *c.L += 2;
+  CUI(cudaMemsetAsync(y, 0, m * sizeof(double), h->st));
+  return SDP_OK;
+}
+
+// ---- the robust form with slacks: A(X) + v - w = b, v, w >= 0, costs cv, cw (eq. rmc-sdp) ----
+
+struct Slack {
+  double *v, *w, *zv, *zw;
+  const double *cv, *cw;
+  double xz;   // v^T zv + w^T zw
+  double xs;   // <X, S>
+};
+
+sdp_status ensure_slack_workspace(sdp_handle* h) {
+  IpmWork* w = h->ipm;
+  if (w->lp_pool) return SDP_OK;
+  const size_t m = (size_t)h->m, mp = (m + 31) & ~size_t(31);
+  double* pool = nullptr;
+  cudaError_t e = cudaMalloc(&pool, 14 * mp * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return wc_fail(h, SDP_ENOMEM, std::string("slack workspace: ") + cudaGetErrorString(e));
+  }
+  w->lp_pool = pool;
+  double** bufs[14] = {&w->delta, &w->rlv, &w->rlw, &w->ctv, &w->ctw, &w->btl, &w->dv,
+                       &w->dw,    &w->dzv, &w->dzw, &w->dva, &w->dwa, &w->dzva, &w->dzwa};
+  for (int k = 0; k < 14; ++k) *bufs[k] = pool + k * mp;
+  return SDP_OK;
+}
+
+// the slack terms of the residuals and measures (after residuals(): w->rp = b - A(X), w->Rd)
+sdp_status slack_measures(Ctx& c, const double* y, Slack& sl, Measures* M) {
+  sdp_handle* h = c.h;
+  IpmWork* w = c.w;
+  const int m = c.m;
+  const double rd2 = std::pow(M->dinf * (1.0 + M->nc), 2.0);
+  const double xs = M->mu * c.n;
+  slack_resid_kernel<<<nb(m), IT, 0, c.st>>>(m, sl.v, sl.w, y, sl.zv, sl.zw, sl.cv, sl.cw, w->rp, w->rlv, w->rlw);
+  ++*c.L;
+  dot(c, m, w->rp, nullptr, 16);
+  dot(c, m, sl.cv, sl.v, 17);
+  dot(c, m, sl.cw, sl.w, 18);
+  dot(c, m, w->rlv, nullptr, 19);
+  dot(c, m, w->rlw, nullptr, 20);
+  dot(c, m, sl.v, sl.zv, 21);
+  dot(c, m, sl.w, sl.zw, 22);
+  dot(c, m, sl.cv, nullptr, 23);
+  dot(c, m, sl.cw, nullptr, 24);
+  double d[9];
+  CUI(cudaMemcpyAsync(d, w->dots + 16, 9 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+  CUI(cudaStreamSynchronize(c.st));
+  M->pobj += d[1] + d[2];
+  M->gap = std::fabs(M->pobj - M->dobj) / (1.0 + std::fabs(M->pobj) + std::fabs(M->dobj));
+  M->pinf = std::sqrt(d[0]) / (1.0 + M->nb);
+  M->dinf = std::sqrt(rd2 + d[3] + d[4]) / (1.0 + M->nc + std::sqrt(d[7] + d[8]));
+  sl.xs = xs;
+  sl.xz = d[5] + d[6];
+  M->mu = (xs + sl.xz) / (c.n + 2.0 * m);
+  return SDP_OK;
+}
+
+// sup{a : x + a dx >= 0} over two vector pairs
+sdp_status ratio_step(Ctx& c, const double* a, const double* da, const double* b, const double* db, double* out) {
+  sdp_handle* h = c.h;
+  ratio_partial_kernel<<<kDotBlocks, IT, 0, c.st>>>(c.m, a, da, b, db, c.w->dpart + 25 * kDotBlocks);
+  min_final_kernel<<<1, IT, 0, c.st>>>(c.w->dpart + 25 * kDotBlocks, kDotBlocks, c.w->dots + 25);
+  *c.L += 2;
+  CUI(cudaMemcpyAsync(out, c.w->dots + 25, sizeof(double), cudaMemcpyDeviceToHost, c.st));
+  CUI(cudaStreamSynchronize(c.st));
+  return SDP_OK;
+}
+
+// one predictor-corrector step of the robust form (the method of step() with the orthant)
+sdp_status step_slack(Ctx& c, double* X, double* y, double* S, Slack& sl, const Measures& Mz, sdp_ipm_info* info) {
+  sdp_handle* h = c.h;
+  IpmWork* w = c.w;
+  const int n = c.n, m = c.m;
+  const int64_t nn = (int64_t)n * n;
+  const size_t bytes = (size_t)nn * sizeof(double);
+  const double mu = Mz.mu;
+  int sweeps = 0;
+  sdp_status s0 = scaling(c, X, S, &sweeps);
+  if (s0 != SDP_OK) return s0;
+  slack_delta_kernel<<<nb(m), IT, 0, c.st>>>(m, sl.v, sl.w, sl.zv, sl.zw, w->delta);   // the linear block
+  ++*c.L;
+
+  // ---- predictor: C~ = R_d + S (R_c = -X), r_x = -x z
+  lincomb_kernel<<<nb(nn), IT, 0, c.st>>>(nn, 1.0, w->Rd, 1.0, S, 0.0, nullptr, w->Ct);
+  slack_rhs_kernel<<<nb(m), IT, 0, c.st>>>(m, 0.0, 0, sl.v, sl.w, sl.zv, sl.zw, nullptr, nullptr, nullptr, nullptr,
+                                           w->rlv, w->rlw, w->rp, w->ctv, w->ctw, w->btl);
+  *c.L += 2;
+  sdp_status s = newton(c, w->Ct, w->btl, w->dXa, w->dya, w->dSs, info);
+  if (s != SDP_OK) return s;
+  lincomb_kernel<<<nb(nn), IT, 0, c.st>>>(nn, 1.0, w->dSs, -1.0, S, 0.0, nullptr, w->dSa);   // R_d - A^T dy
+  slack_dir_kernel<<<nb(m), IT, 0, c.st>>>(m, sl.v, sl.w, sl.zv, sl.zw, w->ctv, w->ctw, w->rlv, w->rlw, w->dya,
+                                           w->dva, w->dwa, w->dzva, w->dzwa);
+  *c.L += 2;
+  CUI(gemm(c, false, false, w->Ginv, w->dXa, w->M1));
+  CUI(gemm(c, false, true, w->M1, w->Ginv, w->Dx));                              // Dx = G^{-1} dX G^{-T}
+  CUI(gemm(c, true, false, w->G, w->dSa, w->M1));
+  CUI(gemm(c, false, false, w->M1, w->G, w->Ds));                                // Ds = G^T dS G
+  double ap = 0.0, ad = 0.0, rp_ = 0.0, rd_ = 0.0;
+  s = max_step(c, w->Dx, 1.0, &ap, &sweeps);
+  if (s != SDP_OK) return s;
+  s = max_step(c, w->Ds, 1.0, &ad, &sweeps);
+  if (s != SDP_OK) return s;
+  s = ratio_step(c, sl.v, w->dva, sl.w, w->dwa, &rp_);
+  if (s != SDP_OK) return s;
+  s = ratio_step(c, sl.zv, w->dzva, sl.zw, w->dzwa, &rd_);
+  if (s != SDP_OK) return s;
+  ap = std::min({1.0, ap, rp_});
+  ad = std::min({1.0, ad, rd_});
+  // mu_aff = (<X + ap dX, S + ad dS> + (x + ap dx)^T (z + ad dz)) / (n + 2m)
+  dot(c, nn, X, w->dSa, 7);
+  dot(c, nn, w->dXa, S, 8);
+  dot(c, nn, w->dXa, w->dSa, 9);
+  slack_muaff_kernel<<<kDotBlocks, IT, 0, c.st>>>(m, ap, ad, sl.v, w->dva, sl.zv, w->dzva, sl.w, w->dwa, sl.zw,
+                                                  w->dzwa, w->dpart + 10 * kDotBlocks);
+  dot_final_kernel<<<1, IT, 0, c.st>>>(w->dpart + 10 * kDotBlocks, kDotBlocks, w->dots + 10);
+  *c.L += 2;
+  double d4[4];
+  CUI(cudaMemcpyAsync(d4, w->dots + 7, 4 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+  CUI(cudaStreamSynchronize(c.st));
+  const double mu_aff = (sl.xs + ad * d4[0] + ap * d4[1] + ap * ad * d4[2] + d4[3]) / (n + 2.0 * m);
+  const double sigma = std::min(1.0, std::pow(mu_aff / mu, 3.0));
+
+  // ---- corrector: Lam R + R Lam = 2 sigma mu I - 2 Lam^2 - (Dx Ds + Ds Dx);
+  //      r_x = sigma mu - x z - dx_a dz_a
+  CUI(gemm(c, false, false, w->Dx, w->Ds, w->M1));
+  lyap_kernel<<<nb(nn), IT, 0, c.st>>>(n, 2.0 * sigma * mu, w->g, w->M1, w->R);
+  ++*c.L;
+  CUI(gemm(c, false, false, w->R, w->Ginv, w->M1));
+  CUI(gemm(c, true, false, w->Ginv, w->M1, w->M2));                             // G^{-T} R G^{-1}
+  lincomb_kernel<<<nb(nn), IT, 0, c.st>>>(nn, 1.0, w->Rd, -1.0, w->M2, 0.0, nullptr, w->Ct);
+  slack_rhs_kernel<<<nb(m), IT, 0, c.st>>>(m, sigma * mu, 1, sl.v, sl.w, sl.zv, sl.zw, w->dva, w->dwa, w->dzva,
+                                           w->dzwa, w->rlv, w->rlw, w->rp, w->ctv, w->ctw, w->btl);
+  *c.L += 2;
+  CUI(cudaMemcpyAsync(w->T, w->M2, bytes, cudaMemcpyDeviceToDevice, c.st));    // keep G^{-T} R G^{-1}
+  s = newton(c, w->Ct, w->btl, w->dX, w->dy, w->dSs, info, true);
+  if (s != SDP_OK) return s;
+  lincomb_kernel<<<nb(nn), IT, 0, c.st>>>(nn, 1.0, w->dSs, 1.0, w->T, 0.0, nullptr, w->dS);  // R_d - A^T dy
+  slack_dir_kernel<<<nb(m), IT, 0, c.st>>>(m, sl.v, sl.w, sl.zv, sl.zw, w->ctv, w->ctw, w->rlv, w->rlw, w->dy,
+                                           w->dv, w->dw, w->dzv, w->dzw);
+  *c.L += 2;
+  CUI(gemm(c, false, false, w->Ginv, w->dX, w->M1));
+  CUI(gemm(c, false, true, w->M1, w->Ginv, w->Dx));
+  CUI(gemm(c, true, false, w->G, w->dS, w->M1));
+  CUI(gemm(c, false, false, w->M1, w->G, w->Ds));
+  s = max_step(c, w->Dx, 0.98, &ap, &sweeps);
+  if (s != SDP_OK) return s;
+  s = max_step(c, w->Ds, 0.98, &ad, &sweeps);
+  if (s != SDP_OK) return s;
+  s = ratio_step(c, sl.v, w->dv, sl.w, w->dw, &rp_);
+  if (s != SDP_OK) return s;
+  s = ratio_step(c, sl.zv, w->dzv, sl.zw, w->dzw, &rd_);
+  if (s != SDP_OK) return s;
+  ap = std::min(1.0, 0.98 * std::min(ap, rp_));
+  ad = std::min(1.0, 0.98 * std::min(ad, rd_));
+  sym_axpy_kernel<<<nb(nn), IT, 0, c.st>>>(n, ap, w->dX, X);
+  sym_axpy_kernel<<<nb(nn), IT, 0, c.st>>>(n, ad, w->dS, S);
+  axpy_kernel<<<nb(m), IT, 0, c.st>>>(m, ad, w->dy, y);
+  axpy_kernel<<<nb(m), IT, 0, c.st>>>(m, ap, w->dv, sl.v);
+  axpy_kernel<<<nb(m), IT, 0, c.st>>>(m, ap, w->dw, sl.w);
+  axpy_kernel<<<nb(m), IT, 0, c.st>>>(m, ad, w->dzv, sl.zv);
+  axpy_kernel<<<nb(m), IT, 0, c.st>>>(m, ad, w->dzw, sl.zw);
+  *c.L += 7;
+  CUI(cudaGetLastError());
+  info->alpha_p = ap;
+  info->alpha_d = ad;
+  info->sigma = sigma;
+  info->eig_sweeps += sweeps;
+  return SDP_OK;
+}
+
 sdp_status check_args(sdp_handle* h, const double* b, const double* C, double* X, double* y, double* S) {
   if (!h) return wc_fail(nullptr, SDP_EINVAL, "NULL handle");
   if (!b || !C || !X || !y || !S) return wc_fail(h, SDP_EINVAL, "NULL array argument");
@@ -583,6 +905,7 @@ void wc_ipm_free(sdp_handle* h) {
   if (!h || !h->ipm) return;
   for (auto& g : h->ipm->eg) eigh_graph_release(&g);
   if (h->ipm->pool) cudaFree(h->ipm->pool);
+  if (h->ipm->lp_pool) cudaFree(h->ipm->lp_pool);
   delete h->ipm;
   h->ipm = nullptr;
 }
@@ -633,30 +956,8 @@ extern "C" sdp_status sdp_solve(sdp_handle* h, const double* b, const double* C,
   int64_t L = 0;
   IpmWork* w = h->ipm;
   Ctx c{h, w, h->n, h->m, h->st, &L};
-  const int n = h->n, m = h->m;
-  // ---- start X = S = xi I, y = 0
-  std::vector<double> bh(m), rn(m, 1.0);
-  CUI(cudaMemcpyAsync(bh.data(), b, m * sizeof(double), cudaMemcpyDeviceToHost, h->st));
-  if (h->kind == SDP_A_DENSE_SVEC) {
-    row_sumsq_kernel<<<(unsigned)((m * 32 + IT - 1) / IT), IT, 0, h->st>>>(h->a_dense, m, h->N, w->rownrm);
-    CUI(cudaMemcpyAsync(rn.data(), w->rownrm, m * sizeof(double), cudaMemcpyDeviceToHost, h->st));
-  }
-  dot(c, (int64_t)n * n, C, nullptr, 6);
-  double cc = 0.0;
-  CUI(cudaMemcpyAsync(&cc, w->dots + 6, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-  CUI(cudaStreamSynchronize(h->st));
-  double xi = std::max(10.0, std::sqrt((double)n));
-  for (int i = 0; i < m; ++i) {
-    const double an = (h->kind == SDP_A_DENSE_SVEC) ? std::sqrt(rn[i])
-                      : (h->kind == SDP_A_SPARSE_COO) ? std::sqrt(h->sp_rownorm2[i]) : 1.0;
-    xi = std::max(xi, (1.0 + std::fabs(bh[i])) / (1.0 + an));
-  }
-  xi = std::max(xi, (1.0 + std::sqrt(cc)) / std::sqrt((double)n));
-  w->xi = xi;
-  w->have_prev = false;
-  scaled_identity_kernel<<<nb((int64_t)n * n), IT, 0, h->st>>>(n, xi, X);
-  scaled_identity_kernel<<<nb((int64_t)n * n), IT, 0, h->st>>>(n, xi, S);
-  CUI(cudaMemsetAsync(y, 0, m * sizeof(double), h->st));
+  s = start(c, b, C, X, y, S);
+  if (s != SDP_OK) return s;
   sdp_ipm_info loc;
   std::memset(&loc, 0, sizeof(loc));
   Measures M;
@@ -680,6 +981,56 @@ extern "C" sdp_status sdp_solve(sdp_handle* h, const double* b, const double* C,
   loc.iters = it;
   loc.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = loc;
+  return loc.converged ? SDP_OK : SDP_ENOTCONV;
+}
+
+extern "C" sdp_status sdp_solve_slack(sdp_handle* h, const double* b, const double* C, const double* cv,
+                                      const double* cw, double* X, double* y, double* S, double* v, double* wv,
+                                      double* zv, double* zw, double gap_tol, int32_t max_iter, sdp_ipm_info* info) {
+  if (!h) return wc_fail(nullptr, SDP_EINVAL, "NULL handle");
+  if (!cv || !cw || !v || !wv || !zv || !zw) return wc_fail(h, SDP_EINVAL, "NULL array argument");
+  sdp_status s = check_args(h, b, C, X, y, S);   // also refuses a linear block set by the caller
+  if (s != SDP_OK) return s;
+  if (!(gap_tol > 0.0) || max_iter < 0) return wc_fail(h, SDP_EINVAL, "bad gap_tol or max_iter");
+  s = ensure_slack_workspace(h);
+  if (s != SDP_OK) return s;
+  const auto t0 = std::chrono::steady_clock::now();
+  int64_t L = 0;
+  IpmWork* w = h->ipm;
+  Ctx c{h, w, h->n, h->m, h->st, &L};
+  const int m = h->m;
+  s = start(c, b, C, X, y, S);
+  if (s != SDP_OK) return s;
+  for (double* x : {v, wv, zv, zw}) fill_kernel<<<nb(m), IT, 0, h->st>>>(m, w->xi, x);   // x = z = xi 1
+  L += 4;
+  // the Newton solves of this loop carry the linear block delta = v/zv + w/zw (updated in place)
+  s = sdp_set_linear_diag(h, w->delta);
+  if (s != SDP_OK) return s;
+  Slack sl{v, wv, zv, zw, cv, cw, 0.0, 0.0};
+  sdp_ipm_info loc;
+  std::memset(&loc, 0, sizeof(loc));
+  Measures M;
+  int it = 0;
+  for (;; ++it) {
+    s = residuals(c, b, C, X, y, S, &M);
+    if (s == SDP_OK) s = slack_measures(c, y, sl, &M);
+    if (s != SDP_OK) break;
+    fill_info(&loc, M);
+    if (M.gap <= gap_tol && M.pinf <= gap_tol && M.dinf <= gap_tol) {
+      loc.converged = 1;
+      break;
+    }
+    if (it >= max_iter) break;
+    s = step_slack(c, X, y, S, sl, M, &loc);
+    if (s != SDP_OK) break;
+  }
+  const std::string err = h->err;
+  sdp_set_linear_diag(h, nullptr);   // the handle is left as the caller set it up
+  h->err = err;
+  loc.iters = it;
+  loc.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = loc;
+  if (s != SDP_OK) return s;
   return loc.converged ? SDP_OK : SDP_ENOTCONV;
 }
 

@@ -81,3 +81,54 @@ def test_linear_block_refused_where_not_built():
             s.set_linear_diag(delta[:prob.m])
         assert e.value.status == native.SDP_EUNSUPPORTED
         s.close()
+
+
+def test_slack_solve_recovers_rmc_and_matches_the_oracle():
+    """sdp_solve_slack on robust completion (n = 12, 70 measurements, 3 gross outliers): converges
+    to a 1e-8 gap, recovers X*, puts v - w exactly on the outliers with |y| <= 1, and agrees with
+    the oracle's outer loop (oracle/ipm_lp.py); a second call on the same handle gives the same
+    point (the handle is left without the linear block)."""
+    from oracle import ipm_lp
+    from paper_2407_14013_gb300 import NewtonSolver
+    prob = W.rmc(12, 70, 3, 9)
+    m = prob.m
+    ones = np.ones(m)
+    s = NewtonSolver(prob, r_hat=3)
+    X, y, S, v, w, zv, zw, info = s.solve_slack(_t(prob.b), _t(prob.C), _t(ones), _t(ones))
+    assert info["status"] == 0 and info["converged"] == 1 and info["rel_gap"] <= 1e-8
+    Xh = X.cpu().numpy()
+    Xs, eps, out = prob.meta["Xs"], prob.meta["eps"], prob.meta["outliers"]
+    assert rel(Xh, Xs) <= 1e-6
+    vw = (v - w).cpu().numpy()
+    assert set(np.where(np.abs(vw) > 1e-3)[0].tolist()) == set(out.tolist())
+    assert np.allclose(vw[out], eps[out], rtol=1e-6, atol=1e-6)
+    assert np.abs(y.cpu().numpy()).max() <= 1 + 1e-8
+    assert min(float(v.min()), float(w.min()), float(zv.min()), float(zw.min())) > 0
+    res = ipm_lp.ipm_solve_lp(prob, prob.meta["G_l"], prob.meta["c_l"])
+    assert rel(Xh, res.X) <= 1e-6
+    X2, *_, info2 = s.solve_slack(_t(prob.b), _t(prob.C), _t(ones), _t(ones))
+    assert info2["converged"] == 1 and rel(X2.cpu().numpy(), Xh) <= 1e-9
+    s.close()
+
+
+def test_slack_solve_dense_constraints_matches_the_oracle():
+    """The same loop on dense constraints (matrix sensing with two gross outliers in b): converges
+    and agrees with the oracle's outer loop on X and on the slacks."""
+    from oracle import ipm_lp
+    from paper_2407_14013_gb300 import NewtonSolver
+    prob = W.sensing(10, 40, 2, 1501)
+    g = np.random.default_rng(1502)
+    b = prob.b.copy()
+    b[g.choice(prob.m, 2, replace=False)] += 50.0 * g.standard_normal(2)
+    prob.b = b
+    m = prob.m
+    G = np.hstack([np.eye(m), -np.eye(m)])
+    cl = np.ones(2 * m)
+    res = ipm_lp.ipm_solve_lp(prob, G, cl)
+    assert res.converged
+    s = NewtonSolver(prob, r_hat=3)
+    X, y, S, v, w, zv, zw, info = s.solve_slack(_t(prob.b), _t(prob.C), _t(cl[:m]), _t(cl[m:]))
+    assert info["converged"] == 1
+    assert rel(X.cpu().numpy(), res.X) <= 1e-6
+    assert np.allclose((v - w).cpu().numpy(), res.x[:m] - res.x[m:], rtol=0, atol=1e-6 * (1 + np.abs(b).max()))
+    s.close()
