@@ -255,7 +255,11 @@ sdp_status sdp_set_linear_diag(sdp_handle* h, const double* delta);
  * this call), the ratio test for v, w (primal) and zv, zw (dual), and the stop test of sdp_solve
  * with the slack terms in the objective and in the dual residual.  Start X = S = xi I, y = 0,
  * v = w = zv = zw = xi.  cv, cw: device inputs (m, > 0); X, y, S, v, w, zv, zw: device outputs.
- * DENSE_SVEC and SPARSE_COO kinds, FP64 form, PCG (as sdp_set_linear_diag). */
+ * DENSE_SVEC and SPARSE_COO kinds, FP64 form, PCG (as sdp_set_linear_diag; otherwise
+ * SDP_EUNSUPPORTED before any output is written).  SDP_EINVAL for a NULL handle or array, a
+ * gap_tol <= 0 or max_iter < 0, SDP_EUNSUPPORTED while the caller has a linear block set,
+ * SDP_ENOTCONV after max_iter iterations (outputs hold the last iterate), SDP_ENOMEM if the 14 m
+ * doubles of the slack workspace cannot be allocated. */
 sdp_status sdp_solve_slack(sdp_handle* h, const double* b, const double* C, const double* cv, const double* cw,
                            double* X, double* y, double* S, double* v, double* w, double* zv, double* zw,
                            double gap_tol, int32_t max_iter, sdp_ipm_info* info);

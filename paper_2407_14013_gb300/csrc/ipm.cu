@@ -989,6 +989,10 @@ extern "C" sdp_status sdp_solve_slack(sdp_handle* h, const double* b, const doub
                                       double* zv, double* zw, double gap_tol, int32_t max_iter, sdp_ipm_info* info) {
   if (!h) return wc_fail(nullptr, SDP_EINVAL, "NULL handle");
   if (!cv || !cw || !v || !wv || !zv || !zw) return wc_fail(h, SDP_EINVAL, "NULL array argument");
+  // what the linear block supports, checked before X, y, S are written
+  if (h->kind == SDP_A_DIAG || h->mixed || h->opt.krylov != 0)
+    return wc_fail(h, SDP_EUNSUPPORTED,
+                   "nonnegative variables are built for the DENSE_SVEC and SPARSE_COO kinds, the FP64 form and PCG");
   sdp_status s = check_args(h, b, C, X, y, S);   // also refuses a linear block set by the caller
   if (s != SDP_OK) return s;
   if (!(gap_tol > 0.0) || max_iter < 0) return wc_fail(h, SDP_EINVAL, "bad gap_tol or max_iter");

@@ -165,3 +165,12 @@ def test_linear_block_setter_validates_without_gpu():
     with pytest.raises(_native.SdpError) as e:
         _native.sdp_set_linear_diag(0, 8)
     assert e.value.status == _native.SDP_EINVAL and "NULL handle" in str(e.value)
+
+
+def test_slack_solve_validates_without_gpu():
+    """sdp_solve_slack refuses a NULL handle before any CUDA call."""
+    from paper_2407_14013_gb300 import _native
+    info = _native.sdp_ipm_info()
+    with pytest.raises(_native.SdpError) as e:
+        _native.sdp_solve_slack(0, [8] * 11, 1e-8, 10, info)
+    assert e.value.status == _native.SDP_EINVAL and "NULL handle" in str(e.value)

@@ -80,6 +80,10 @@ def test_linear_block_refused_where_not_built():
         with pytest.raises(SdpError) as e:
             s.set_linear_diag(delta[:prob.m])
         assert e.value.status == native.SDP_EUNSUPPORTED
+        ones = _t(np.ones(prob.m))
+        with pytest.raises(SdpError) as e:              # refused before any output is written
+            s.solve_slack(_t(prob.b), _t(prob.C), ones, ones)
+        assert e.value.status == native.SDP_EUNSUPPORTED
         s.close()
 
 
