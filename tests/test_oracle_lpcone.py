@@ -135,3 +135,48 @@ def test_lp_outer_loop_meets_the_optimality_conditions():
     assert res.x.min() > 0 and res.z.min() > 0
     comp = float(np.sum(res.X * res.S) + res.x @ res.z)
     assert comp <= 1e-6 * (1 + abs(pobj))
+
+
+def test_linear_block_conditioning_along_the_path():
+    """Section 4's point carried to the orthant, on the outer loop's own iterates (robust
+    completion, 3 outliers): the Schur matrix A (W (x)s W) A^T + G D G^T grows ill-conditioned as
+    mu -> 0 (past 1e15 by mu ~ 1e-5), and so does the extended augmented matrix, whose (1,1) block
+    gains tau^-2 diag(delta) with delta = x/z of order 1/mu on the outliers.  That growth sits in
+    a diagonal block the preconditioner inverts exactly, so the spectrum of P^{-1} K stays inside
+    the mediant bound [min(1, l_min), max(1, l_max)] of A E A^T / beta at every iterate.  The plain
+    Schur route of the same outer loop breaks down before the 1e-8 gap."""
+    from oracle import ipm_lp, reform
+    from oracle.newton import nt_scaling, schur_matrix
+    from oracle.operators import At_op, row_norm_scale
+    prob = W.rmc(12, 70, 3, 9)
+    G, cl, m = prob.meta["G_l"], prob.meta["c_l"], prob.m
+    sA = row_norm_scale(prob)
+    condM = []
+    for k in (1, 5, 9, 11):
+        res = ipm_lp.ipm_solve_lp(prob, G, cl, tol=1e-8, max_iter=k)
+        Wm = nt_scaling(res.X, res.S)
+        d = res.x / res.z
+        GDG = lpcone.gdg(G, d)
+        condM.append(np.linalg.cond(schur_matrix(prob, Wm) + GDG))
+        lw, Vw = np.linalg.eigh(Wm)
+        s = reform.split(Vw, lw, r_hat=3, s_A=sA)
+        K = np.zeros((m + s.d, m + s.d))
+        for j in range(m + s.d):
+            e = np.zeros(m + s.d)
+            e[j] = 1.0
+            a, b = reform.aug_apply(prob, s, e[:m], e[m:])
+            K[:, j] = np.concatenate([a + GDG @ e[:m] / s.tau ** 2, b])
+        AEA = np.column_stack([A_op(prob, reform.E_op(s, At_op(prob, e))) for e in np.eye(m)])
+        ae = np.linalg.eigvalsh(0.5 * (AEA + AEA.T))
+        lo, hi = min(1.0, ae[0] / s.beta), max(1.0, ae[-1] / s.beta)
+        P = lpcone.precond_setup_lp(prob, s, G, d, space="d")
+        ev = np.linalg.eigvals(np.linalg.solve(lpcone.precond_matrix_lp(P), K))
+        assert np.abs(ev.imag).max() <= 1e-6 * np.abs(ev).max()
+        assert ev.real.min() >= lo * (1 - 1e-6) and ev.real.max() <= hi * (1 + 1e-6), k
+        assert ev.real.max() / ev.real.min() <= 10.0
+    assert condM[0] < 1e2 and condM[-1] > 1e15
+    try:
+        schur = ipm_lp.ipm_solve_lp(prob, G, cl, tol=1e-8, max_iter=60, direction_by="schur")
+        assert not schur.converged
+    except np.linalg.LinAlgError:          # here: the Cholesky factor of a Schur matrix fails
+        pass
