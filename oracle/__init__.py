@@ -22,7 +22,11 @@ lpcone     the nonnegative variables of Section 7's robust problems (eq. rmc-sdp
            in the Newton system: plain definition, dense KKT, and the
            reformulation with the linear block and its preconditioner.
 ipm_lp     the outer loop with those variables (the method of ipm.py plus the
-           orthant), its directions from the reformulated solve.
+           orthant), its directions from the reformulated solve, and the
+           re-centring at a fixed mu used by the derivative pins.
+grad       the implicit derivative of the optimum (vector-Jacobian product):
+           one Newton solve at the final scaling point, with and without the
+           orthant.
 ipm        a textbook infeasible primal-dual NT path-following method (the
            outer loop; the paper leaves it to SeDuMi, so its details are the
            oracle's own definitions -- parity unpinned beyond its invariants).

@@ -39,3 +39,24 @@ def vjp_at_scaling(prob, W: np.ndarray, gX: np.ndarray, gy: np.ndarray):
     gXs = 0.5 * (gX + gX.T)
     dX, dy, _ = newton_direct(prob, W, gXs, np.asarray(gy, dtype=float))
     return 0.5 * (dX + dX.T), dy
+
+
+def vjp_lp(prob, X: np.ndarray, S: np.ndarray, x: np.ndarray, z: np.ndarray, G: np.ndarray,
+           gX: np.ndarray, gx: np.ndarray, gy: np.ndarray, r_hat: int = 3, space: str = "d"):
+    """The same product for the problem with the orthant (nonnegative x entering as A(X) + G x = b,
+    cost c_l, dual slack z = c_l - G^T y).  Linearising the optimality conditions at the NT
+    scaling point (W for (X, S), d = x / z for the orthant) gives the KKT matrix
+    [[-(W (x)s W)^{-1}, 0, A^T], [0, -D^{-1}, G^T], [A, G, 0]] acting on (dX, dx, dy) with right
+    side (dC, dc_l, db).  It is symmetric, so the cotangent of the data (gC, gc_l, gb) is the
+    Newton direction (dX, dx, dy) of the system with (C~, c~, b~) = (sym gX, gx, gy).  It is
+    computed by the reformulated solve with the linear block (well conditioned as mu -> 0, where
+    the plain Schur route of this system breaks down), in the preconditioner space `space`."""
+    from .lpcone import newton_reform_lp
+    from .operators import row_norm_scale
+    W = nt_scaling(X, S)
+    lw, Vw = np.linalg.eigh(W)
+    gXs = 0.5 * (gX + gX.T)
+    dX, dx, dy, _ = newton_reform_lp(prob, Vw, lw, gXs, np.asarray(gy, dtype=float), G, x / z,
+                                     np.asarray(gx, dtype=float), r_hat=r_hat, s_A=row_norm_scale(prob),
+                                     space=space)
+    return 0.5 * (dX + dX.T), dx, dy

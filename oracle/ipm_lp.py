@@ -149,3 +149,43 @@ def ipm_solve_lp(prob, G: np.ndarray, cl: np.ndarray, tol: float = 1e-8, max_ite
         st = LPState(X=0.5 * (Xn + Xn.T), x=x + ap * dx, y=y + ad * dy, S=0.5 * (Sn + Sn.T), z=z + ad * dz)
         log.append(dict(it=it, mu=mu, rel_gap=gap, pinf=pinf, dinf=dinf, alpha_p=ap, alpha_d=ad, sigma=sigma))
     return LPResult(X=st.X, x=st.x, y=st.y, S=st.S, z=st.z, iters=it, converged=converged, log=log)
+
+
+def center_lp(prob, G: np.ndarray, cl: np.ndarray, st: LPState, mu: float, max_iter: int = 60,
+              tol: float = 1e-12, r_hat: int = 3) -> LPState:
+    """Newton steps towards the central-path point of parameter mu of the problem with the orthant:
+    A(X) + G x = b, A^T y + S = C, G^T y + z = c_l, X S = mu I, x z = mu 1 (NT direction with
+    R_c = mu S^{-1} - X and r_x = mu - x z, no second-order terms), by the reformulated solve, with
+    step lengths that keep X, S, x, z in the interior.  Stops when the residuals and the scaled
+    centrality of both cones fall below tol."""
+    n = prob.n
+    sA = row_norm_scale(prob)
+    X, x, y, S, z = st.X, st.x, st.y, st.S, st.z
+    for _ in range(max_iter):
+        rp = prob.b - A_op(prob, X) - G @ x
+        Rd = prob.C - At_op(prob, y) - S
+        rl = cl - G.T @ y - z
+        W = nt_scaling(X, S)
+        Gs = sqrtm_psd(W)
+        Lam = Gs @ S @ Gs
+        Lam = 0.5 * (Lam + Lam.T)
+        cen = max(float(np.linalg.norm(Lam @ Lam - mu * np.eye(n))), float(np.abs(x * z - mu).max())) / mu
+        res = max(float(np.linalg.norm(rp)) / (1 + np.linalg.norm(prob.b)),
+                  math.sqrt(float(np.sum(Rd * Rd)) + float(rl @ rl)) / (1 + np.linalg.norm(prob.C) + np.linalg.norm(cl)))
+        if cen <= tol and res <= tol:
+            break
+        Wi = np.linalg.inv(W)
+        Rc = mu * np.linalg.inv(S) - X
+        Rc = 0.5 * (Rc + Rc.T)
+        Ct = Rd - Wi @ Rc @ Wi
+        rx = mu - x * z
+        lw, Vw = np.linalg.eigh(W)
+        dX, dx, dy, _ = newton_reform_lp(prob, Vw, lw, 0.5 * (Ct + Ct.T), rp, G, x / z, rl - rx / x,
+                                         r_hat=r_hat, s_A=sA)
+        dS = Rd - At_op(prob, dy)
+        dS = 0.5 * (dS + dS.T)
+        dz = rl - G.T @ dy
+        a = min(1.0, 0.95 * min(max_step(X, dX), ratio_step(x, dx)), 0.95 * min(max_step(S, dS), ratio_step(z, dz)))
+        X, x, y, S, z = X + a * dX, x + a * dx, y + a * dy, S + a * dS, z + a * dz
+        X, S = 0.5 * (X + X.T), 0.5 * (S + S.T)
+    return LPState(X=X, x=x, y=y, S=S, z=z)
