@@ -143,13 +143,27 @@ class ReformLPInfo:
     pcg: object
 
 
+def choose_space_lp(sp, G: np.ndarray, d: np.ndarray, m: int, dominance: float = 1e8) -> str:
+    """Preconditioner space with the linear block.  Rows where tau^{-2} delta_i exceeds
+    `dominance` * beta are fixed by their slack (Lam is exact there); the d-space elimination then
+    rests on the m_free remaining rows, and when m_free < d it loses the direction to rounding
+    at small mu (the analogue of A11 failing) while the m-space complement, nearly diagonal on
+    the fixed rows, stays accurate.  "m" when m_free < d, else "d"."""
+    delta = np.diag(gdg(G, d))
+    m_free = int(np.count_nonzero(delta / sp.tau ** 2 <= dominance * sp.beta))
+    return "m" if m_free < sp.d else "d"
+
+
 def newton_reform_lp(prob, V: np.ndarray, lam: np.ndarray, Ct: np.ndarray, bt: np.ndarray, G: np.ndarray,
                      d: np.ndarray, ct: np.ndarray, r: int | None = None, r_hat: int | None = None,
                      s_A: float = 1.0, rtol: float = 1e-12, maxit: int = 2000, space: str = "d"):
     """The Newton direction through eq. augsys with the linear block (module docstring), by the
     indefinite PCG of Cor. pcg started from x0 = P^{-1}[0; g_v], then eq. recover and
-    dx = D(G^T dy - c~).  Returns (dX, dx, dy, info)."""
+    dx = D(G^T dy - c~).  space: "d", "m" or "auto" (``choose_space_lp``).  Returns
+    (dX, dx, dy, info)."""
     sp = split(V, lam, r=r, r_hat=r_hat, s_A=s_A)
+    if space == "auto":
+        space = choose_space_lp(sp, G, d, prob.m)
     P = precond_setup_lp(prob, sp, G, d, space=space)
     m = prob.m
     GDG = gdg(G, d)

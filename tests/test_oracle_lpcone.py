@@ -180,3 +180,48 @@ def test_linear_block_conditioning_along_the_path():
         assert not schur.converged
     except np.linalg.LinAlgError:          # here: the Cholesky factor of a Schur matrix fails
         pass
+
+
+def test_space_rule_with_many_active_slacks():
+    """Six of eight constraints carry an active slack (sensing n = 6 with two gross outliers and a
+    cheap slack cost), so only two rows are left to the semidefinite part against d = 6.  At
+    mu = 1e-9 on the central path, with the right side (0, 0, b), the d-space elimination loses
+    the direction to rounding (PCG does not reach 1e-12 in 200 iterations) although P^{-1} K is
+    the identity to 1e-8; the rule
+    picks the m-space complement there, which converges at once to the right direction, and
+    keeps the d-space form on robust completion (three outliers among 70 rows)."""
+    from oracle import ipm_lp, reform
+    from oracle.newton import nt_scaling
+    from oracle.operators import row_norm_scale
+    p0 = W.sensing(6, 8, 2, 77)
+    b = p0.b.copy()
+    b[0] += 5.0
+    b[3] -= 4.0
+    prob = W.Problem(kind=p0.kind, n=p0.n, m=p0.m, b=b, C=p0.C, a_dense=p0.a_dense)
+    m = prob.m
+    G = np.hstack([np.eye(m), -np.eye(m)])
+    cl = 0.5 * np.ones(2 * m)
+    res = ipm_lp.ipm_solve_lp(prob, G, cl, tol=1e-9, max_iter=200)
+    st = ipm_lp.center_lp(prob, G, cl, ipm_lp.LPState(res.X, res.x, res.y, res.S, res.z), 1e-9)
+    Wm = nt_scaling(st.X, st.S)
+    lw, Vw = np.linalg.eigh(Wm)
+    d = st.x / st.z
+    Ct, bt, ct = np.zeros((6, 6)), prob.b, np.zeros(2 * m)      # the right side of dp*/dC (envelope)
+    kw = dict(r_hat=3, s_A=row_norm_scale(prob), maxit=200)
+    *_, info_d = lpcone.newton_reform_lp(prob, Vw, lw, Ct, bt, G, d, ct, space="d", **kw)
+    assert not info_d.pcg.converged
+    dX, dx, dy, info = lpcone.newton_reform_lp(prob, Vw, lw, Ct, bt, G, d, ct, space="auto", **kw)
+    assert info.precond.space == "m" and info.pcg.converged and info.pcg.iters <= 3
+    # the dense KKT matrix has condition ~1e28 here, so the direction is checked by the envelope
+    # theorem (this right side is the cotangent of b^T y: (dX, dx, dy) -> (X*, x*, 0) up to O(mu))
+    # and by the primal block equation A(dX) + G dx = b
+    kX, kx, ky = lpcone.newton_kkt_dense_lp(prob, Wm, Ct, bt, G, d, ct)
+    rel = lambda a, b_: np.linalg.norm(a - b_) / np.linalg.norm(b_)
+    assert rel(dX, kX) <= 1e-6 and rel(dX, st.X) <= 1e-6 and rel(dx, st.x) <= 1e-6
+    assert np.linalg.norm(dy) <= 1e-6 * np.linalg.norm(st.y)
+    assert rel(A_op(prob, dX) + G @ dx, bt) <= 1e-9
+    r2 = W.rmc(12, 70, 3, 9)
+    res2 = ipm_lp.ipm_solve_lp(r2, r2.meta["G_l"], r2.meta["c_l"], tol=1e-8)
+    lw2, Vw2 = np.linalg.eigh(nt_scaling(res2.X, res2.S))
+    sp2 = reform.split(Vw2, lw2, r_hat=3, s_A=row_norm_scale(r2))
+    assert lpcone.choose_space_lp(sp2, r2.meta["G_l"], res2.x / res2.z, r2.m) == "d"
