@@ -174,3 +174,16 @@ def test_slack_solve_validates_without_gpu():
     with pytest.raises(_native.SdpError) as e:
         _native.sdp_solve_slack(0, [8] * 11, 1e-8, 10, info)
     assert e.value.status == _native.SDP_EINVAL and "NULL handle" in str(e.value)
+
+
+@pytest.mark.parametrize("lang,std", [("c", "-std=c99"), ("c++", "-std=c++17")])
+def test_header_is_strict_c_and_cpp(lang, std, tmp_path):
+    """include/wcipm.h is a plain C interface: it compiles alone, warning-free, as pedantic C99
+    and as C++17 (no CUDA or torch types in the signatures)."""
+    src = tmp_path / "h.c"
+    src.write_text('#include "wcipm.h"\nint main(void) { return 0; }\n')
+    cc = "gcc" if lang == "c" else "g++"
+    r = subprocess.run([cc, std, "-Wall", "-Wextra", "-Werror", "-pedantic", "-x", lang, "-I",
+                        os.path.join(ROOT, "include"), str(src), "-o", str(tmp_path / "h")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
