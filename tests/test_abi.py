@@ -133,6 +133,13 @@ def test_product_path_does_not_touch_the_oracle():
         if f.endswith(".py"):
             src = open(os.path.join(pkg, f)).read()
             assert not re.search(r"^\s*(import|from)\s+oracle", src, flags=re.M), f
+    for d in ("oracle", "workloads"):                  # neither side reaches into the other
+        for f in os.listdir(os.path.join(ROOT, d)):
+            if f.endswith(".py"):
+                src = open(os.path.join(ROOT, d, f)).read()
+                assert "paper_2407_14013_gb300" not in src, f
+                if d == "workloads":
+                    assert not re.search(r"^\s*(import|from)\s+oracle", src, flags=re.M), f
     from paper_2407_14013_gb300 import _native
     saved = _native._lib
     try:
