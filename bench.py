@@ -235,7 +235,42 @@ def other_configs(dev, reps: int = 2, only=None, tc_n: int = 5000):
     # the headline workload with a linear block of outlier slacks (eq. rmc-sdp form, dense A; on request)
     if only == "lp_sensing200":
         out["lp_sensing200"] = _lp_sensing(dev, reps)
+    # robust completion solved whole with its slacks (sdp_solve_slack; on request)
+    if only == "rmc_slack100":
+        out["rmc_slack100"] = _rmc_slack(dev, 100, 3000, 15, 71)
     return out
+
+
+def _rmc_slack(dev, n, m, m_o, seed):
+    """Robust completion (eq. rmc-sdp: m svec entries of a rank-2 X*, m_o of them gross outliers)
+    solved to a 1e-8 gap by sdp_solve_slack; a first untimed call, then one timed call (host wall
+    clock around a synchronised call).  Reports the recovery error of X* and whether v - w is
+    supported exactly on the outliers."""
+    import time
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2407_14013_gb300 import NewtonSolver
+    prob = W.rmc(n, m, m_o, seed)
+    s = NewtonSolver(prob, r_hat=3, device=str(dev))
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    b, C, ones = t(prob.b), t(prob.C), t(np.ones(m))
+    s.solve_slack(b, C, ones, ones, allow_notconv=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    X, y, S, v, w, zv, zw, info = s.solve_slack(b, C, ones, ones, allow_notconv=True)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    Xs, eps = prob.meta["Xs"], prob.meta["eps"]
+    vw = (v - w).cpu().numpy()
+    found = set(np.where(np.abs(vw) > 1e-3 * np.abs(eps).max())[0].tolist())
+    s.close()
+    return {"workload": f"robust completion n={n}, m={m} svec entries of a rank-2 X*, {m_o} gross outliers, "
+                        "slacks v, w >= 0 (A(X) + v - w = b), r_hat=3, FP64",
+            "seconds": wall, "converged": bool(info["converged"]), "outer_iters": info["iters"],
+            "rel_gap": info["rel_gap"], "pcg_iters": info["pcg_iters"],
+            "recovery_err": float(np.linalg.norm(X.cpu().numpy() - Xs) / np.linalg.norm(Xs)),
+            "outliers_found": found == set(prob.meta["outliers"].tolist())}
 
 
 def _lp_sensing(dev, reps):
@@ -740,7 +775,7 @@ def main():
     ap.add_argument("--no-ttg", action="store_true", help="skip the time-to-gap solves")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads (MaxCut 64 / 5000, completion)")
     ap.add_argument("--only", choices=["maxcut64", "maxcut5000", "completion2000", "tc_gemm", "batch32",
-                                       "completion2000_solve", "batch256", "lp_sensing200"],
+                                       "completion2000_solve", "batch256", "lp_sensing200", "rmc_slack100"],
                     help="measure only this other workload (one JSON object; no headline line)")
     ap.add_argument("--reps", type=int, default=2, help="timed Newton solves per row of the other workloads")
     ap.add_argument("--tc-n", type=int, default=5000, help="order of the tensor-core product row (--only tc_gemm)")
