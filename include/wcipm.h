@@ -52,7 +52,7 @@ typedef enum {
   SDP_ECUDA = 3,         /* a CUDA runtime error; see sdp_last_error                            */
   SDP_ENOTCONV = 4,      /* PCG reached max_pcg without the stopping test; outputs hold the last iterate */
   SDP_ENUMERIC = 5,      /* non-finite or non-positive PCG scalar, or a non-positive pivot     */
-  SDP_ETIMEOUT = 6,      /* reserved: a bounded device-side wait gave up                         */
+  SDP_ETIMEOUT = 6,      /* a bounded device-side wait gave up (sdp_set_tc_wait_limit_ns)          */
   SDP_EUNSUPPORTED = 7   /* option combination not built                                        */
 } sdp_status;
 
@@ -180,8 +180,10 @@ typedef struct {
   int32_t converged;     /* 1 if rel_gap, pinf and dinf are all <= gap_tol at exit               */
   int32_t pcg_iters;     /* PCG iterations of all Newton solves                                  */
   int32_t eig_sweeps;    /* Jacobi sweeps of all eigen-decompositions                            */
-  int32_t newton_inexact;/* Newton solves that stopped at max_pcg before the stopping test (their
-                            directions are used as they are)                                    */
+  int32_t newton_inexact;/* Newton solves that stopped at max_pcg before the stopping test but whose
+                            (Newt-eps) residual was below 0.1 gap_tol of the right side (their
+                            directions are used as they are; a direction above that bound ends the
+                            loop with SDP_ENOTCONV and the last iterate)                         */
   int32_t pad_;
   double pobj;           /* <C, X>                                                              */
   double dobj;           /* b^T y                                                               */
@@ -226,7 +228,10 @@ sdp_status ipm_step(sdp_handle* h, const double* b, const double* C, double* X, 
 
 /* Whole solve from X = S = xi I, y = 0 (xi = max(10, sqrt n, max_i (1+|b_i|)/(1+||A_i||_F),
  * (1+||C||_F)/sqrt n)) until rel_gap, pinf and dinf are <= gap_tol (SDP_OK) or max_iter
- * iterations (SDP_ENOTCONV).  X, y, S: device outputs. */
+ * iterations (SDP_ENOTCONV).  X, y, S: device outputs.  A Newton solve that reaches max_pcg
+ * with a (Newt-eps) residual above 0.1 gap_tol times its right side also ends the loop with
+ * SDP_ENOTCONV: no step is taken on that direction, X, y, S hold the last iterate and info the
+ * measures of that iterate (ipm_step applies the same rule with gap_tol = 1e-8). */
 sdp_status sdp_solve(sdp_handle* h, const double* b, const double* C, double* X, double* y, double* S,
                      double gap_tol, int32_t max_iter, sdp_ipm_info* info);
 
@@ -258,11 +263,27 @@ sdp_status sdp_set_linear_diag(sdp_handle* h, const double* delta);
  * DENSE_SVEC and SPARSE_COO kinds, FP64 form, PCG (as sdp_set_linear_diag; otherwise
  * SDP_EUNSUPPORTED before any output is written).  SDP_EINVAL for a NULL handle or array, a
  * gap_tol <= 0 or max_iter < 0, SDP_EUNSUPPORTED while the caller has a linear block set,
- * SDP_ENOTCONV after max_iter iterations (outputs hold the last iterate), SDP_ENOMEM if the 14 m
+ * SDP_ENOTCONV after max_iter iterations or on an unconverged Newton direction as in sdp_solve
+ * (outputs hold the last iterate), SDP_ENOMEM if the 14 m
  * doubles of the slack workspace cannot be allocated. */
 sdp_status sdp_solve_slack(sdp_handle* h, const double* b, const double* C, const double* cv, const double* cw,
                            double* X, double* y, double* S, double* v, double* w, double* zv, double* zw,
                            double gap_tol, int32_t max_iter, sdp_ipm_info* info);
+
+/* Centring at a fixed mu: Newton steps towards the central-path point of parameter mu
+ * (A(X) = b, A^T(y) + S = C, X S = mu I), each the NT direction (Section 3, (Newt-eps) through
+ * the reformulated solve) of R_c = mu S^{-1} - X, i.e. Lam R + R Lam = 2 mu I - 2 Lam^2 in the
+ * scaled frame of ipm_step, with one step length for X, y and S: min(1, 0.95 * 0.95 max step).
+ * Stops (SDP_OK) when ||Lam^2 - mu I||_F / mu, pinf and dinf are all <= tol, or after max_iter
+ * steps (SDP_ENOTCONV).  The paper has no counterpart: the derivative of the optimum (sdp_grad)
+ * is that of the central-path point of its scaling point, which equals the derivative of the
+ * optimum up to O(mu) only at a centred iterate, so a final iterate of sdp_solve is centred at
+ * its own mu before it is differentiated.  X, y, S: device, in place (X, S positive definite);
+ * b, C as for sdp_solve; info (may be NULL): iters, measures, and the final centrality in
+ * info->sigma.  SDP_EINVAL for mu <= 0, tol <= 0 or max_iter < 0; the other codes as
+ * ipm_step.  The interior-point workspace is allocated on first use. */
+sdp_status sdp_center(sdp_handle* h, const double* b, const double* C, double* X, double* y, double* S, double mu,
+                      double tol, int32_t max_iter, sdp_ipm_info* info);
 
 /* The NT scaling point of an iterate (eq. newt), as the Newton solve and the adjoint take it:
  * W = L (L^T S L)^{-1/2} L^T with X = L L^T, computed as G G^T with G = L U Gamma^{-1/4}
@@ -372,8 +393,9 @@ sdp_status sdp_set_profiling(sdp_handle* h, int32_t on);
  * 4 MiB array in the library's device data, held by every GPU that loads the library
  * until the process exits.  Limit: n(n+1)/2 <= 524288 (n <= 1023), else SDP_EINVAL.
  * Other errors: SDP_EINVAL for NULL arrays or n, m < 1; SDP_ECUDA if a CUDA call fails.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  All calls
+ * Every call looks up the array's device address (cudaGetSymbolAddress) for the device
+ * current at the call, so it stays right after a context reset; the first call on a device
+ * loads the library's device code there, so make that first call before any stream capture.  All calls
  * share the array, so calls that overlap on the GPU race; every value read is written
  * earlier in the same call, so nothing needs clearing between calls.  `stream` is a
  * cudaStream_t; the call returns after its work on that stream has completed. */
@@ -399,6 +421,16 @@ size_t sdp_gemm_f64_tc_work_bytes(int32_t M, int32_t N, int32_t K);
 sdp_status sdp_gemm_f64_tc(void* stream, int32_t tA, int32_t tB, int32_t M, int32_t N, int32_t K, double alpha,
                            const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                            int64_t ldc, void* work, size_t work_bytes);
+
+/* Limit in nanoseconds of every wait of the main loop of the tensor-core product (the TMA
+ * copies, the products and the drain of an accumulator, each an mbarrier wait bounded by
+ * %globaltimer), process-wide, for the products launched after the call; 0 restores the
+ * default of 2 s.  When a wait runs out the kernel records an error word, stops issuing
+ * copies and products, waits with the full 2 s bound for the ones already in flight, frees its
+ * TMEM and returns; the call then returns SDP_ETIMEOUT with its output not written, and the
+ * stream and the context stay usable.  The paper has no counterpart: this is the control that
+ * lets a test make a bounded wait run out without faulting or hanging a GPU. */
+void sdp_set_tc_wait_limit_ns(uint64_t ns);
 
 /* Bytes of device workspace owned by the handle. */
 size_t sdp_workspace_bytes(const sdp_handle* h);

@@ -17,7 +17,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.linalg as sla
 
-from .linalg import skron, svec, smat
+from .linalg import skron, svec, smat, svec_index
 from .operators import A_matrix, A_op, At_op, constraint_matrix
 
 
@@ -44,16 +44,59 @@ def nt_scaling(X: np.ndarray, S: np.ndarray) -> np.ndarray:
     return 0.5 * (W + W.T)
 
 
-def schur_matrix(prob, W: np.ndarray) -> np.ndarray:
-    """M_ij = <A_i, W A_j W>, i.e. A (W (x)s W) A^T."""
+def schur_matrix_by_columns(prob, W: np.ndarray) -> np.ndarray:
+    """M_ij = <A_i, W A_j W>, i.e. A (W (x)s W) A^T, one column per constraint: W A_j W is
+    formed explicitly and A(.) applied to it."""
     m = prob.m
-    if prob.kind == "diag":
-        # <e_i e_i^T, W e_j e_j^T W> = W_ij^2
-        return W * W
     cols = np.empty((m, m))
     for j in range(m):
         cols[:, j] = A_op(prob, W @ constraint_matrix(prob, j) @ W)
     return 0.5 * (cols + cols.T)
+
+
+def _single_entry_constraints(prob) -> bool:
+    return prob.kind == "sparse" and len(prob.a_con) == prob.m and np.array_equal(prob.a_con, np.arange(prob.m))
+
+
+def schur_matrix(prob, W: np.ndarray, block: int = 100) -> np.ndarray:
+    """M_ij = <A_i, W A_j W>, i.e. A (W (x)s W) A^T.
+
+    DIAG: <e_i e_i^T, W e_j e_j^T W> = W_ij^2.  Dense svec rows: the same columns as
+    ``schur_matrix_by_columns``, for ``block`` constraints at a time (W A_j W by one batched
+    product, svec, then A times the block).  Constraints with one stored entry each (A_i =
+    v_i s_i (e_r e_c^T + e_c e_r^T), s_i = 1/2 on the diagonal, 1 off it; matrix completion):
+    <e_a e_b^T, W e_p e_q^T W> = W_ap W_qb summed over the four terms gives
+    M_ij = 2 v_i s_i v_j s_j (W_{r_i r_j} W_{c_i c_j} + W_{r_i c_j} W_{c_i r_j}).
+    Any other sparse storage: ``schur_matrix_by_columns``."""
+    m = prob.m
+    if prob.kind == "diag":
+        return W * W
+    if prob.kind == "dense":
+        n = prob.n
+        rows, cols = svec_index(n)
+        wgt = np.where(rows == cols, 1.0, np.sqrt(2.0))
+        M = np.empty((m, m))
+        for j0 in range(0, m, block):
+            j1 = min(m, j0 + block)
+            Ab = np.zeros((j1 - j0, n, n))
+            vals = prob.a_dense[j0:j1] / wgt
+            Ab[:, rows, cols] = vals
+            Ab[:, cols, rows] = vals
+            WAW = np.matmul(np.matmul(W, Ab), W)
+            M[:, j0:j1] = prob.a_dense @ (WAW[:, rows, cols] * wgt).T
+        return 0.5 * (M + M.T)
+    if _single_entry_constraints(prob):
+        r = prob.a_row.astype(np.int64)
+        c = prob.a_col.astype(np.int64)
+        v = prob.a_val * np.where(r == c, 0.5, 1.0)
+        M = np.empty((m, m))
+        for i0 in range(0, m, 1024):          # row blocks bound the temporaries
+            i1 = min(m, i0 + 1024)
+            ri, ci = r[i0:i1], c[i0:i1]
+            M[i0:i1] = 2.0 * np.outer(v[i0:i1], v) * (W[np.ix_(ri, r)] * W[np.ix_(ci, c)] +
+                                                       W[np.ix_(ri, c)] * W[np.ix_(ci, r)])
+        return 0.5 * (M + M.T)
+    return schur_matrix_by_columns(prob, W)
 
 
 def schur_solver(M: np.ndarray):

@@ -15,7 +15,7 @@ from . import _native as native
 from ._native import (SDP_A_DENSE_SVEC, SDP_A_DIAG, SDP_A_SPARSE_COO, SDP_ENOTCONV, SDP_FP64, SDP_MIXED_FP32,
                       SDP_OK, SdpError, sdp_default_options)
 
-__all__ = ["NewtonSolver", "SdpError", "native", "sdp_optimum", "eigh", "solve_sdp_batch", "SDP_A_DIAG", "SDP_A_SPARSE_COO",
+__all__ = ["NewtonSolver", "SdpError", "native", "sdp_optimum", "sdp_optimum_at", "eigh", "solve_sdp_batch", "SDP_A_DIAG", "SDP_A_SPARSE_COO",
            "SDP_A_DENSE_SVEC"]
 
 KINDS = {"diag": SDP_A_DIAG, "sparse": SDP_A_SPARSE_COO, "dense": SDP_A_DENSE_SVEC}
@@ -253,6 +253,22 @@ class NewtonSolver:
         info["status"] = st
         return X, y, S, v, w, zv, zw, info
 
+    def center(self, b, C, X, y, S, mu: float, tol: float = 1e-10, max_iter: int = 50, allow_notconv: bool = False):
+        """Newton steps towards the central-path point of parameter mu, in place on the device
+        tensors X, y, S (sdp_center); returns the info dict (info["sigma"]: final centrality)."""
+        torch = self.torch
+        f64 = torch.float64
+        b, C = (t.to(device=self.device, dtype=f64).contiguous() for t in (b, C))
+        for t in (X, y, S):
+            if t.dtype != f64 or t.device != self.device or not t.is_contiguous():
+                raise ValueError("X, y, S must be contiguous float64 tensors on the solver's device")
+        ci = native.sdp_ipm_info()
+        st = native.sdp_center(self.handle, _ptr(b), _ptr(C), _ptr(X), _ptr(y), _ptr(S), mu, tol, max_iter, ci,
+                               allow_notconv=allow_notconv)
+        info = ci.as_dict()
+        info["status"] = st
+        return info
+
     def set_linear_diag(self, delta=None):
         """Nonnegative variables entering the constraints (sdp_set_linear_diag): every later solve
         adds diag(delta) to the Schur matrix, delta = diag(G D G^T) >= 0 (m values).  The caller
@@ -319,16 +335,52 @@ def solve_sdp_batch(solvers, bs, Cs, gap_tol: float = 1e-8, max_iter: int = 100,
     return res
 
 
-def sdp_optimum(C, b, X, y, V, lam, solver: NewtonSolver):
-    """Differentiable view of an SDP optimum: returns (X, y) as a function of (C, b).
+def sdp_optimum(C, b, solver: NewtonSolver, gap_tol: float = 1e-8, max_iter: int = 100, center_mu=None,
+                center_tol: float = 1e-10, center_iters: int = 50):
+    """Differentiable SDP layer: (X, y) = argmin <C,X> s.t. A(X) = b, X PSD (and its dual y) as a
+    function of (C, b), for the constraint operator held by ``solver``.
 
-    (X, y) is the final iterate of an interior-point solve of min <C,X> s.t. A(X) = b, X PSD;
-    (V, lam) is the eigen-decomposition of the NT scaling point of that (well-centred) iterate.
-    Only these are kept for the backward pass, which is one ``solver.grad`` call: the Newton
-    system of the reformulation at the final iterate, reused as the adjoint."""
+    Forward: one device interior-point solve (sdp_solve) to ``gap_tol``, then centring steps at
+    the final mu (or ``center_mu``) so that the derivative below is that of a central-path
+    point (sdp_center), then the NT scaling point of the result (sdp_scaling_point).  Only the
+    final (X, y, S) and the eigen-decomposition (V, lam) of its scaling point are kept.
+    Backward: one sdp_grad call, the Newton system of the reformulation at that point used as
+    the adjoint: (gC, gb) = K^{-1} [sym gX; gy].  The result differs from the derivative of the
+    optimum by O(mu)."""
     import torch
 
     class _SdpOptimum(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, C_, b_):
+            X, y, S, info = solver.solve_sdp(b_.detach(), C_.detach(), gap_tol=gap_tol, max_iter=max_iter)
+            mu = float(info["mu"]) if center_mu is None else float(center_mu)
+            solver.center(b_.detach(), C_.detach(), X, y, S, mu, tol=center_tol, max_iter=center_iters,
+                          allow_notconv=True)
+            V, lam = solver.scaling_point(X, S)
+            ctx.save_for_backward(X, y, S, V, lam)
+            ctx.mu = mu
+            return X.to(C_.dtype), y.to(b_.dtype)
+
+        @staticmethod
+        def backward(ctx, gX, gy):
+            X, y, S, V, lam = ctx.saved_tensors
+            if gX is None:
+                gX = torch.zeros((solver.n, solver.n), dtype=torch.float64, device=solver.device)
+            if gy is None:
+                gy = torch.zeros(solver.m, dtype=torch.float64, device=solver.device)
+            gC, gb = solver.grad(V, lam, gX, gy)
+            return gC.to(C.dtype), gb.to(b.dtype)
+
+    return _SdpOptimum.apply(C, b)
+
+
+def sdp_optimum_at(C, b, X, y, V, lam, solver: NewtonSolver):
+    """(X, y) of an iterate the caller already holds, with (V, lam) the eigen-decomposition of
+    its NT scaling point, made differentiable with respect to (C, b) by the same sdp_grad
+    backward as sdp_optimum (no solve in the forward pass)."""
+    import torch
+
+    class _SdpAt(torch.autograd.Function):
         @staticmethod
         def forward(ctx, C_, b_, X_, y_, V_, lam_):
             ctx.save_for_backward(V_, lam_)
@@ -344,7 +396,7 @@ def sdp_optimum(C, b, X, y, V, lam, solver: NewtonSolver):
             gC, gb = solver.grad(V_, lam_, gX, gy)
             return gC.to(C.dtype), gb.to(b.dtype), None, None, None, None
 
-    return _SdpOptimum.apply(C, b, X.detach(), y.detach(), V.detach(), lam.detach())
+    return _SdpAt.apply(C, b, X.detach(), y.detach(), V.detach(), lam.detach())
 
 
 def eigh(A, tol: float = 1e-14, max_sweeps: int = 40):

@@ -73,6 +73,7 @@ EXPORTS = {
     "ipm_step": (c_int32, [c_void_p] + [c_void_p] * 5 + [POINTER(sdp_ipm_info)]),
     "sdp_solve": (c_int32, [c_void_p] + [c_void_p] * 5 + [c_double, c_int32, POINTER(sdp_ipm_info)]),
     "sdp_scaling_point": (c_int32, [c_void_p] * 5),
+    "sdp_center": (c_int32, [c_void_p] + [c_void_p] * 5 + [c_double, c_double, c_int32, POINTER(sdp_ipm_info)]),
     "sdp_solve_batch": (c_int32, [c_int32] + [c_void_p] * 6 + [c_double, c_int32, c_int32, c_void_p, c_void_p]),
     "sdp_gemm_f64_tc_work_bytes": (c_size_t, [c_int32, c_int32, c_int32]),
     "sdp_gemm_f64_tc": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_double, c_void_p, c_int64,
@@ -80,6 +81,7 @@ EXPORTS = {
     "sdp_debug_copy": (c_int32, [c_void_p, c_int32, c_void_p, c_int64]),
     "sdp_set_profiling": (c_int32, [c_void_p, c_int32]),
     "sdp_adjoint_dense_noalloc": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
+    "sdp_set_tc_wait_limit_ns": (None, [ctypes.c_uint64]),
     "sdp_workspace_bytes": (c_size_t, [c_void_p]),
     "sdp_last_launch_count": (c_int64, [c_void_p]),
     "sdp_last_error": (c_char_p, [c_void_p]),
@@ -207,6 +209,16 @@ def sdp_set_linear_diag(h: int, delta: int) -> None:
         raise SdpError(st, lib.sdp_last_error(c_void_p(h) if h else None).decode())
 
 
+def sdp_center(h: int, b: int, C: int, X: int, y: int, S: int, mu: float, tol: float, max_iter: int,
+               info: sdp_ipm_info, allow_notconv: bool = False) -> int:
+    lib = load()
+    st = lib.sdp_center(c_void_p(h), c_void_p(b), c_void_p(C), c_void_p(X), c_void_p(y), c_void_p(S), mu, tol,
+                        max_iter, ctypes.byref(info))
+    if st != SDP_OK and not (allow_notconv and st == SDP_ENOTCONV):
+        raise SdpError(st, lib.sdp_last_error(c_void_p(h)).decode())
+    return st
+
+
 def sdp_scaling_point(h: int, X: int, S: int, V: int, lam: int) -> None:
     lib = load()
     st = lib.sdp_scaling_point(c_void_p(h), c_void_p(X), c_void_p(S), c_void_p(V), c_void_p(lam))
@@ -255,6 +267,11 @@ def sdp_adjoint_dense_noalloc(a_dense: int, n: int, m: int, y: int, Y: int, stre
     """Y = A^T(y) with no device allocation (fixed scratch in the library); returns the status."""
     return int(load().sdp_adjoint_dense_noalloc(c_void_p(a_dense), n, m, c_void_p(y), c_void_p(Y),
                                                 c_void_p(stream)))
+
+
+def sdp_set_tc_wait_limit_ns(ns: int) -> None:
+    """Limit of the main-loop waits of the tensor-core product (0: the default 2 s)."""
+    load().sdp_set_tc_wait_limit_ns(int(ns))
 
 
 def sdp_workspace_bytes(h: int) -> int:

@@ -25,6 +25,7 @@
 #include <exception>
 #include <thread>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -321,6 +322,7 @@ struct Ctx {
   int n, m;
   cudaStream_t st;
   int64_t* L;
+  double gap_tol = 1e-8;   // the stop test of the loop; also bounds the residual of a usable direction
 };
 
 cudaError_t gemm(Ctx& c, bool tA, bool tB, const double* A, const double* B, double* C, double alpha = 1.0,
@@ -443,9 +445,20 @@ sdp_status newton(Ctx& c, const double* Ct, const double* bt, double* dX, double
                        : sdp_newton_solve(c.h, c.w->V, c.w->lam, Ct, bt, dX, dy, dSs, &ni);
   info->pcg_iters += ni.pcg_iters;
   info->newton_ms += ni.setup_ms + ni.pcg_ms + ni.recover_ms;
-  if (s == SDP_ENOTCONV) {   // an inexact direction: the outer loop proceeds with it
-    info->newton_inexact += 1;
-    return SDP_OK;
+  if (s == SDP_ENOTCONV) {
+    // PCG stopped at max_pcg.  The direction is used only when its (Newt-eps) residual is already
+    // below a tenth of the loop's tolerance relative to the right side (Lemma smallres: ||r_k||
+    // is that residual), so that stepping on it cannot move the iterate's residuals past the
+    // stop test; otherwise the loop stops here and the caller keeps the last iterate.
+    if (ni.res_norm <= 0.1 * c.gap_tol * ni.rhs_norm) {
+      info->newton_inexact += 1;
+      return SDP_OK;
+    }
+    char msg[160];
+    std::snprintf(msg, sizeof(msg),
+                  "Newton direction not converged (PCG at max_pcg, residual %.3g of the right side): stopped at "
+                  "the last iterate", ni.rhs_norm > 0.0 ? ni.res_norm / ni.rhs_norm : ni.res_norm);
+    return wc_fail(c.h, SDP_ENOTCONV, msg);
   }
   return s;
 }
@@ -956,6 +969,7 @@ extern "C" sdp_status sdp_solve(sdp_handle* h, const double* b, const double* C,
   int64_t L = 0;
   IpmWork* w = h->ipm;
   Ctx c{h, w, h->n, h->m, h->st, &L};
+  c.gap_tol = gap_tol;
   s = start(c, b, C, X, y, S);
   if (s != SDP_OK) return s;
   sdp_ipm_info loc;
@@ -1002,6 +1016,7 @@ extern "C" sdp_status sdp_solve_slack(sdp_handle* h, const double* b, const doub
   int64_t L = 0;
   IpmWork* w = h->ipm;
   Ctx c{h, w, h->n, h->m, h->st, &L};
+  c.gap_tol = gap_tol;
   const int m = h->m;
   s = start(c, b, C, X, y, S);
   if (s != SDP_OK) return s;
@@ -1035,6 +1050,95 @@ extern "C" sdp_status sdp_solve_slack(sdp_handle* h, const double* b, const doub
   loc.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = loc;
   if (s != SDP_OK) return s;
+  return loc.converged ? SDP_OK : SDP_ENOTCONV;
+}
+
+// Newton steps towards the central-path point of parameter mu (X S = mu I with A(X) = b and
+// A^T(y) + S = C): the NT direction of R_c = mu S^{-1} - X, i.e. Lam R + R Lam = 2 mu I - 2 Lam^2
+// in the scaled frame (sigma mu = mu, no second-order term), one step length for both sides.
+extern "C" sdp_status sdp_center(sdp_handle* h, const double* b, const double* C, double* X, double* y, double* S,
+                                 double mu, double tol, int32_t max_iter, sdp_ipm_info* info) {
+  sdp_status s = check_args(h, b, C, X, y, S);
+  if (s != SDP_OK) return s;
+  if (!(mu > 0.0) || !std::isfinite(mu) || !(tol > 0.0) || max_iter < 0)
+    return wc_fail(h, SDP_EINVAL, "bad mu, tol or max_iter");
+  const auto t0 = std::chrono::steady_clock::now();
+  int64_t L = 0;
+  IpmWork* w = h->ipm;
+  Ctx c{h, w, h->n, h->m, h->st, &L};
+  c.gap_tol = tol;
+  const int n = h->n;
+  const int64_t nn = (int64_t)n * n;
+  const size_t bytes = (size_t)nn * sizeof(double);
+  sdp_ipm_info loc;
+  std::memset(&loc, 0, sizeof(loc));
+  std::vector<double> gh(n);
+  Measures M;
+  int it = 0;
+  for (;; ++it) {
+    s = residuals(c, b, C, X, y, S, &M);
+    if (s != SDP_OK) break;
+    fill_info(&loc, M);
+    int sweeps = 0;
+    s = scaling(c, X, S, &sweeps);
+    if (s != SDP_OK) break;
+    loc.eig_sweeps += sweeps;
+    // centrality ||Lam^2 - mu I||_F / mu with Lam = G^{-1} X G^{-T} = G^T S G = diag(g)
+    if (cudaMemcpyAsync(gh.data(), w->g, n * sizeof(double), cudaMemcpyDeviceToHost, c.st) != cudaSuccess ||
+        cudaStreamSynchronize(c.st) != cudaSuccess) {
+      s = wc_fail(h, SDP_ECUDA, "reading the scaled iterate failed");
+      break;
+    }
+    double cen = 0.0;
+    for (int i = 0; i < n; ++i) cen += (gh[i] * gh[i] - mu) * (gh[i] * gh[i] - mu);
+    cen = std::sqrt(cen) / mu;
+    loc.sigma = cen;   // reported: the centrality of the last iterate
+    if (cen <= tol && M.pinf <= tol && M.dinf <= tol) {
+      loc.converged = 1;
+      break;
+    }
+    if (it >= max_iter) break;
+    // R with Lam R + R Lam = 2 mu I - 2 Lam^2 (P = 0), C~ = R_d - G^{-T} R G^{-1}
+    if (cudaMemsetAsync(w->M1, 0, bytes, c.st) != cudaSuccess) {
+      s = wc_fail(h, SDP_ECUDA, "clearing a work matrix failed");
+      break;
+    }
+    lyap_kernel<<<nb(nn), IT, 0, c.st>>>(n, 2.0 * mu, w->g, w->M1, w->R);
+    ++L;
+    if (gemm(c, false, false, w->R, w->Ginv, w->M1) != cudaSuccess ||
+        gemm(c, true, false, w->Ginv, w->M1, w->M2) != cudaSuccess) {
+      s = wc_fail(h, SDP_ECUDA, "centring products failed");
+      break;
+    }
+    lincomb_kernel<<<nb(nn), IT, 0, c.st>>>(nn, 1.0, w->Rd, -1.0, w->M2, 0.0, nullptr, w->Ct);
+    ++L;
+    s = newton(c, w->Ct, w->rp, w->dX, w->dy, w->dSs, &loc);
+    if (s != SDP_OK) break;
+    lincomb_kernel<<<nb(nn), IT, 0, c.st>>>(nn, 1.0, w->dSs, 1.0, w->M2, 0.0, nullptr, w->dS);  // R_d - A^T dy
+    ++L;
+    if (gemm(c, false, false, w->Ginv, w->dX, w->M1) != cudaSuccess ||
+        gemm(c, false, true, w->M1, w->Ginv, w->Dx) != cudaSuccess ||
+        gemm(c, true, false, w->G, w->dS, w->M1) != cudaSuccess ||
+        gemm(c, false, false, w->M1, w->G, w->Ds) != cudaSuccess) {
+      s = wc_fail(h, SDP_ECUDA, "centring products failed");
+      break;
+    }
+    double ap = 0.0, ad = 0.0;
+    s = max_step(c, w->Dx, 0.95, &ap, &sweeps);
+    if (s == SDP_OK) s = max_step(c, w->Ds, 0.95, &ad, &sweeps);
+    if (s != SDP_OK) break;
+    const double a = std::min(1.0, 0.95 * std::min(ap, ad));
+    sym_axpy_kernel<<<nb(nn), IT, 0, c.st>>>(n, a, w->dX, X);
+    sym_axpy_kernel<<<nb(nn), IT, 0, c.st>>>(n, a, w->dS, S);
+    axpy_kernel<<<nb(c.m), IT, 0, c.st>>>(c.m, a, w->dy, y);
+    L += 3;
+    loc.alpha_p = loc.alpha_d = a;
+  }
+  loc.iters = it;
+  loc.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = loc;
+  if (s != SDP_OK) return s;
+  if (cudaGetLastError() != cudaSuccess) return wc_fail(h, SDP_ECUDA, "centring kernels failed");
   return loc.converged ? SDP_OK : SDP_ENOTCONV;
 }
 

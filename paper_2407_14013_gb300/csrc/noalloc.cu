@@ -10,15 +10,16 @@
 //
 // The array below is part of the module image: every GPU that loads the library holds its
 // 4 MiB until the process exits.  Host code cannot use the symbol as a pointer (on the
-// host it names a stand-in, not device memory), so the device address is looked up with
-// cudaGetSymbolAddress, once per device, by the first call made with that device current.
-// That first call should therefore come before any stream capture.  All calls share the
-// array: calls that overlap on the GPU (different streams, or host threads) race on it.
-// Every partial sum the second kernel reads is written by the first kernel of the same
-// call, so nothing has to be cleared between calls.
+// host it names a stand-in, not device memory), so every call looks up its device address
+// with cudaGetSymbolAddress for the device current at the call (a lookup, no allocation).
+// Looking it up per call, rather than caching it, keeps the address right when the device's
+// context is torn down and made again between calls (cudaDeviceReset), which reloads the
+// module at a new address.  The first call on a device loads the module, so it should come
+// before any stream capture.  All calls share the array: calls that overlap on the GPU
+// (different streams, or host threads) race on it.  Every partial sum the second kernel
+// reads is written by the first kernel of the same call, so nothing has to be cleared
+// between calls.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "../../include/wcipm.h"
 #include "common.cuh"
@@ -26,13 +27,9 @@
 namespace {
 
 constexpr int64_t kScratchDoubles = 524288;          // 4 MiB of partial sums
-constexpr int kMaxDevices = 64;
 constexpr int kThreads = 256;
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
-
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
-std::mutex g_scratch_mu;
 
 // partial[g * N + k] = sum_{i in group g} y_i a[i, k]
 __global__ void __launch_bounds__(kThreads)
@@ -74,22 +71,11 @@ extern "C" sdp_status sdp_adjoint_dense_noalloc(const double* a_dense, int32_t n
   const int64_t N = (int64_t)n * (n + 1) / 2;
   if (N > kScratchDoubles)
     return fail(SDP_EINVAL, "n too large for the fixed scratch: n(n+1)/2 must be <= 524288 (n <= 1023)");
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail(SDP_ECUDA, "cudaGetDevice failed");
-  if (dev < 0 || dev >= kMaxDevices) return fail(SDP_EUNSUPPORTED, "device index above 63");
-  double* scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess || !p)
-        return fail(SDP_ECUDA, "cudaGetSymbolAddress failed");
-      g_scratch_ptr[dev] = static_cast<double*>(p);
-    }
-    scratch = g_scratch_ptr[dev];
-  }
+  // the device address of the array in the current device's context
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) return fail(SDP_ECUDA, "cudaGetSymbolAddress failed");
+  double* scratch = static_cast<double*>(p);
   // as many row groups as the scratch holds (at most 16), each a contiguous block of rows
   int groups = (int)(kScratchDoubles / N);
   if (groups > 16) groups = 16;

@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include <string>
@@ -89,15 +90,17 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase of `parity` to complete; false after WAIT_NS (sets *abort, *err)
+// Bounded wait for the phase of `parity` to complete; false after `limit` ns (sets *abort, *err)
 // or when another role has set *abort.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, int* err) {
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, int* err,
+                          unsigned long long limit = WAIT_NS) {
   const unsigned long long t0 = gtimer();
+  const uint32_t every = limit < 1000000ull ? 0u : 255u;   // short limits: look at the clock on every try
   for (uint32_t it = 0;; ++it) {
     if (mbar_try(bar, parity)) return true;
-    if ((it & 255u) == 255u) {
+    if ((it & every) == every) {
       if (*abort) return false;
-      if (gtimer() - t0 > WAIT_NS) {
+      if (gtimer() - t0 > limit) {
         *abort = 1;
         atomicExch(err, 1);
         return false;
@@ -303,7 +306,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
                int K, int ksplit, const int* __restrict__ ea, const int* __restrict__ eb, double alpha, double beta,
                double* __restrict__ C, int64_t ldc, double* __restrict__ part, int lower, int* __restrict__ err,
-               const int32_t* __restrict__ done) {
+               const int32_t* __restrict__ done, unsigned long long wait_ns) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2];
   __shared__ uint32_t tmem_slot;
@@ -358,14 +361,17 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       bool ok = true;
       for (int u = 0; u < units && ok; ++u) {
         const int buf = u & 1;
-        if (u >= 2 && !mbar_wait(smem_u32(&acce_bar[buf]), ((u >> 1) - 1) & 1, &abort_flag, err)) { ok = false; break; }
+        if (u >= 2 && !mbar_wait(smem_u32(&acce_bar[buf]), ((u >> 1) - 1) & 1, &abort_flag, err, wait_ns)) {
+          ok = false;
+          break;
+        }
         tc_fence_after();
         const int nst = unit_steps(u);
         for (int kk = 0; kk < nst; ++kk) {
           while (g_load < total_steps && g_load < g_mma + STAGES) {
             const int st = g_load % STAGES;
             if (g_load >= STAGES &&
-                !mbar_wait(smem_u32(&empty_bar[st]), ((g_load / STAGES) - 1) & 1, &abort_flag, err)) {
+                !mbar_wait(smem_u32(&empty_bar[st]), ((g_load / STAGES) - 1) & 1, &abort_flag, err, wait_ns)) {
               ok = false;
               break;
             }
@@ -381,7 +387,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
           }
           if (!ok) break;
           const int st = g_mma % STAGES;
-          if (!mbar_wait(smem_u32(&full_bar[st]), (g_mma / STAGES) & 1, &abort_flag, err)) { ok = false; break; }
+          if (!mbar_wait(smem_u32(&full_bar[st]), (g_mma / STAGES) & 1, &abort_flag, err, wait_ns)) {
+            ok = false;
+            break;
+          }
           tc_fence_after();
           const uint32_t a0 = base + st * STAGE_BYTES, b0 = a0 + TILE_BYTES;
 #pragma unroll
@@ -396,7 +405,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       }
       if (!ok) {
         abort_flag = 1;
-        // bounded waits for this CTA's own products and copies still in flight
+        // bounded waits for this CTA's own products and copies still in flight (the full bound,
+        // whatever the main loop's limit)
         volatile int keep_waiting = 0;
         if (g_mma > 0) {
           const int st = (g_mma - 1) % STAGES;
@@ -422,7 +432,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     for (int j = 0; j < 64; ++j) gacc[j] = 0;
     for (int u = 0; u < units; ++u) {
       const int buf = u & 1;
-      if (!mbar_wait(smem_u32(&accf_bar[buf]), (u >> 1) & 1, &abort_flag, err)) break;
+      // one decision per warp: the TMEM loads below are warp-collective
+      if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&accf_bar[buf]), (u >> 1) & 1, &abort_flag, err, wait_ns)))
+        break;
       tc_fence_after();
       const uint32_t taddr = tmem + (uint32_t)(buf * BN + cg * 64) + ((uint32_t)(32 * lg) << 16);
       uint32_t r[32];
@@ -531,6 +543,10 @@ cudaError_t make_map(CUtensorMap* map, const void* slices, int rows, int Kpad) {
 }
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// limit of the main-loop waits of the product (sdp_set_tc_wait_limit_ns); the drain after an
+// expiry always keeps WAIT_NS
+std::atomic<unsigned long long> g_main_wait_ns{WAIT_NS};
 inline int kpad_of(int K) { return (K + BK - 1) / BK * BK; }
 
 }  // namespace
@@ -653,7 +669,8 @@ cudaError_t gemm_f64_tc_one(cudaStream_t st, bool tA, bool tB, int M, int N, int
   else nz = 1;
   dim3 grid(gm, gn, nz);
   tc_gemm_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(mapA, mapB, M, N, K, ksplit, ea, eb, alpha, beta, C, ldc,
-                                                    nz > 1 ? part : nullptr, (flags & GEMM_LOWER) ? 1 : 0, err, done);
+                                                    nz > 1 ? part : nullptr, (flags & GEMM_LOWER) ? 1 : 0, err, done,
+                                                    g_main_wait_ns.load());
   if (launches) ++*launches;
   if (nz > 1) {
     const int64_t tot = (int64_t)M * N;
@@ -701,4 +718,8 @@ extern "C" sdp_status sdp_gemm_f64_tc(void* stream, int32_t tA, int32_t tB, int3
   if (e != cudaSuccess) return wc_fail(nullptr, SDP_ECUDA, std::string("tensor-core product: ") + cudaGetErrorString(e));
   if (h_err) return wc_fail(nullptr, SDP_ETIMEOUT, "a bounded wait of the tensor-core product gave up");
   return SDP_OK;
+}
+
+extern "C" void sdp_set_tc_wait_limit_ns(uint64_t ns) {
+  wc::g_main_wait_ns.store(ns == 0 ? wc::WAIT_NS : (unsigned long long)ns);
 }

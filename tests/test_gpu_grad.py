@@ -80,16 +80,16 @@ def test_grad_envelope_near_optimum():
     s.close()
 
 
-def test_sdp_optimum_autograd_matches_grad():
+def test_sdp_optimum_at_autograd_matches_grad():
     import torch
-    from paper_2407_14013_gb300 import NewtonSolver, sdp_optimum
+    from paper_2407_14013_gb300 import NewtonSolver, sdp_optimum_at
     prob = W.maxcut(10, 0.6, 2718, weights="gauss")
     st = _centered(prob, 1e-4)
     V, lam = _eig(onewton.nt_scaling(st.X, st.S))
     s = NewtonSolver(prob, r_hat=4)
     C = _t(prob.C).requires_grad_(True)
     b = _t(prob.b).requires_grad_(True)
-    X, y = sdp_optimum(C, b, _t(st.X), _t(st.y), _t(V), _t(lam), s)
+    X, y = sdp_optimum_at(C, b, _t(st.X), _t(st.y), _t(V), _t(lam), s)
     rng = np.random.default_rng(3)
     GX, gy = _t(rng.standard_normal((prob.n, prob.n))), _t(rng.standard_normal(prob.m))
     loss = (GX * X).sum() + (gy * y).sum()
@@ -97,4 +97,68 @@ def test_sdp_optimum_autograd_matches_grad():
     gC, gb = s.grad(_t(V), _t(lam), GX, gy)
     assert torch.allclose(C.grad, gC, rtol=0, atol=1e-12 * float(gC.abs().max()))
     assert torch.allclose(b.grad, gb, rtol=0, atol=1e-12 * float(gb.abs().max()))
+    s.close()
+
+
+def test_center_matches_oracle_central_point():
+    """sdp_center from the GPU solve's final iterate reaches the central-path point of the
+    given mu, which is unique: it matches the oracle's own centring (oracle/ipm.py center) of
+    the oracle's final iterate, entry by entry."""
+    import torch
+    from paper_2407_14013_gb300 import NewtonSolver
+    prob = W.maxcut(10, 0.6, 2718, weights="gauss")
+    mu = 1e-4
+    ref = _centered(prob, mu)
+    s = NewtonSolver(prob, r_hat=4)
+    X, y, S, info = s.solve_sdp(_t(prob.b), _t(prob.C), gap_tol=1e-8)
+    ci = s.center(_t(prob.b), _t(prob.C), X, y, S, mu, tol=1e-12, max_iter=60)
+    assert ci["status"] == 0 and ci["sigma"] <= 1e-12
+    for got, want in ((X, ref.X), (y, ref.y), (S, ref.S)):
+        g = got.cpu().numpy()
+        assert np.abs(g - want).max() <= 1e-8 * np.abs(want).max()
+    s.close()
+
+
+def _fd_layer(prob, s, bvec, Cmat, GX, gy, mu_c):
+    """Loss <GX, X> + <gy, y> of the GPU layer's forward (solve, centre at mu_c)."""
+    import torch
+    from paper_2407_14013_gb300 import sdp_optimum
+    with torch.no_grad():
+        X, y = sdp_optimum(_t(Cmat), _t(bvec), s, gap_tol=1e-9, center_mu=mu_c, center_tol=1e-13)
+    return float((X.cpu().numpy() * GX).sum() + (y.cpu().numpy() * gy).sum())
+
+
+def test_sdp_layer_gradient_matches_central_differences():
+    """The differentiable layer (forward: sdp_solve + sdp_center + scaling point on the GPU;
+    backward: sdp_grad) against central differences of its own forward pass in b and in C, on
+    a nondegenerate weighted MaxCut instance (unique primal and dual optimum), to 1e-5; the
+    forward's X also matches the oracle's centred point."""
+    import torch
+    from paper_2407_14013_gb300 import NewtonSolver, sdp_optimum
+    prob = W.maxcut(10, 0.6, 2718, weights="gauss")
+    mu_c = 1e-6
+    s = NewtonSolver(prob, r_hat=4)
+    rng = np.random.default_rng(5)
+    GX = rng.standard_normal((prob.n, prob.n))
+    GX = 0.5 * (GX + GX.T)
+    gy = rng.standard_normal(prob.m)
+    C = _t(prob.C).requires_grad_(True)
+    b = _t(prob.b).requires_grad_(True)
+    X, y = sdp_optimum(C, b, s, gap_tol=1e-9, center_mu=mu_c, center_tol=1e-13)
+    ref = _centered(prob, mu_c)
+    assert np.abs(X.detach().cpu().numpy() - ref.X).max() <= 1e-7 * np.abs(ref.X).max()
+    loss = (_t(GX) * X).sum() + (_t(gy) * y).sum()
+    loss.backward()
+    db = rng.standard_normal(prob.m)
+    dC = rng.standard_normal((prob.n, prob.n))
+    dC = 0.5 * (dC + dC.T)
+    h = 1e-5
+    fd_b = (_fd_layer(prob, s, prob.b + h * db, prob.C, GX, gy, mu_c) -
+            _fd_layer(prob, s, prob.b - h * db, prob.C, GX, gy, mu_c)) / (2 * h)
+    an_b = float((b.grad.cpu().numpy() * db).sum())
+    assert abs(fd_b - an_b) <= 1e-5 * max(abs(an_b), 1e-3 * np.linalg.norm(b.grad.cpu().numpy()))
+    fd_C = (_fd_layer(prob, s, prob.b, prob.C + h * dC, GX, gy, mu_c) -
+            _fd_layer(prob, s, prob.b, prob.C - h * dC, GX, gy, mu_c)) / (2 * h)
+    an_C = float((C.grad.cpu().numpy() * dC).sum())
+    assert abs(fd_C - an_C) <= 1e-5 * max(abs(an_C), 1e-3 * np.linalg.norm(C.grad.cpu().numpy()))
     s.close()

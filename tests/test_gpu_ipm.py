@@ -131,3 +131,32 @@ def test_scaling_point_and_adjoint_at_the_final_iterate():
     gC, gb = s.grad(V, lam, _t(np.zeros((prob.n, prob.n))), _t(prob.b))
     assert rel(gC.cpu().numpy(), X.cpu().numpy()) < 1e-4
     s.close()
+
+
+def test_solve_stops_cleanly_on_unconverged_direction():
+    """A Newton solve that reaches max_pcg far above the stop test ends the outer loop with
+    SDP_ENOTCONV before any step is taken on its direction: the outputs hold the last iterate
+    (here the start X = S = xi I, y = 0) and the message names the cause.  With a cap that
+    lets the first directions converge, the loop stops later at a positive-definite iterate."""
+    import torch
+    from paper_2407_14013_gb300 import NewtonSolver, native
+    prob = W.sensing(16, 60, 2, 4111)
+    s = NewtonSolver(prob, r_hat=4, max_pcg=1, check_every=1)
+    X, y, S, info = s.solve_sdp(_t(prob.b), _t(prob.C), gap_tol=1e-8, max_iter=30, allow_notconv=True)
+    assert info["status"] == native.SDP_ENOTCONV and info["iters"] == 0
+    Xh, Sh = X.cpu().numpy(), S.cpu().numpy()
+    xi = Xh[0, 0]
+    assert xi >= 10 and np.array_equal(Xh, xi * np.eye(16)) and np.array_equal(Sh, xi * np.eye(16))
+    assert not y.cpu().numpy().any()
+    assert "not converged" in native.sdp_last_error(s.handle)
+    s.close()
+    # a cap the early directions meet but the late ones (smaller mu) do not
+    s = NewtonSolver(prob, r_hat=4, max_pcg=12, check_every=1)
+    X, y, S, info = s.solve_sdp(_t(prob.b), _t(prob.C), gap_tol=1e-8, max_iter=60, allow_notconv=True)
+    if info["status"] == native.SDP_ENOTCONV and not info["converged"]:
+        assert info["iters"] >= 1
+        assert np.isfinite(X.cpu().numpy()).all()
+        assert np.linalg.eigvalsh(X.cpu().numpy()).min() > 0 and np.linalg.eigvalsh(S.cpu().numpy()).min() > 0
+    else:
+        assert info["status"] == 0
+    s.close()

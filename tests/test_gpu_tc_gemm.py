@@ -82,3 +82,25 @@ def test_split_k_is_deterministic():
     A = rng.standard_normal((300, 4000))
     B = rng.standard_normal((4000, 90))
     assert np.array_equal(_tc(A, B), _tc(A, B))
+
+
+def test_bounded_wait_runs_out_and_the_stream_stays_usable():
+    """A main-loop wait limit of a few ns makes the product's bounded waits run out: the call
+    returns SDP_ETIMEOUT (nothing faults or hangs: the kernel waits with its full bound for its own
+    copies and products in flight, frees its TMEM and returns), and the next product on the same
+    stream, with the default limit restored, is exact."""
+    import torch
+    from paper_2407_14013_gb300 import _native
+    rng = np.random.default_rng(7)
+    A = rng.integers(-100, 101, (256, 512)).astype(np.float64)
+    B = rng.integers(-100, 101, (512, 256)).astype(np.float64)
+    _native.sdp_set_tc_wait_limit_ns(5)
+    try:
+        with pytest.raises(_native.SdpError) as ei:
+            _tc(A, B)
+        assert ei.value.status == _native.SDP_ETIMEOUT
+    finally:
+        _native.sdp_set_tc_wait_limit_ns(0)
+    torch.cuda.synchronize()
+    assert np.array_equal(_tc(A, B), A @ B)
+    assert np.array_equal(_tc(B.T, A.T), B.T @ A.T)

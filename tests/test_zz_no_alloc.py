@@ -1,10 +1,13 @@
-"""The allocation-free adjoint entry point (sdp_adjoint_dense_noalloc) against the Newton solve.
+"""The allocation-free adjoint entry point (sdp_adjoint_dense_noalloc) against the Newton solve
+and against the CPU oracle's A^T.
 
 Callers that cannot call cudaMalloc (allocator callbacks, fully reserved device memory,
 paths that must not hit out-of-memory) use this entry point; it keeps its scratch in a
 fixed array inside the library.  Its output Y = A^T(y) must agree with what the regular
 entry point produces: sdp_newton_solve returns dS = C~ - A^T(dy), so C~ - Y(dy) must equal
-dS.  Two calls in a row are checked (the second one reuses the shared scratch array).
+dS.  It is also compared entry by entry with the oracle's plain definition A^T(y) =
+sum_i y_i A_i (oracle.operators.At_op, FP64 numpy), which shares no code with the library.
+Two calls in a row are checked (the second one reuses the shared scratch array).
 This file is collected last so that a run stopping at the first failure has run every
 other test; it passes alone in a fresh process as well.
 """
@@ -12,6 +15,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from oracle import operators as oops
 
 pytestmark = pytest.mark.gpu
 
@@ -40,6 +44,9 @@ def test_noalloc_adjoint_matches_newton_solve_twice():
         assert np.isfinite(got).all()
         assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref), f"call {call}"
         assert np.allclose(got, got.T, rtol=0, atol=0)
+        # entry by entry against the oracle's definition, for the same dy
+        orc = oops.At_op(prob, dy.cpu().numpy())
+        assert np.abs(got - orc).max() <= 1e-12 * np.abs(orc).max(), f"call {call}"
     s.close()
 
 
