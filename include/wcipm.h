@@ -66,7 +66,7 @@ typedef enum {
                             out-of-range con, col > row, row >= n, a non-finite val, a constraint
                             with no entry, nnz < 1 or nnz > 2^31 - 1) and uploads two index tables
                             into the workspace (entries by constraint, entries by position); the
-                            handle keeps reading the caller's four arrays.  SDP_MIXED_FP32 is not
+                            handle keeps reading the caller's four arrays.  The mixed forms are not
                             built for this kind (EUNSUPPORTED).                                    */
   SDP_A_DENSE_SVEC = 2   /* a_dense: m x n(n+1)/2 row-major, row i = svec(A_i): lower triangle
                             column by column, off-diagonal entries times sqrt(2) (Notations)     */
@@ -74,7 +74,7 @@ typedef enum {
 
 typedef enum {
   SDP_FP64 = 0,          /* every product in FP64 (the plain form)                                */
-  SDP_MIXED_FP32 = 1     /* FP64 iterative refinement of the augmented-system solution from x = 0:
+  SDP_MIXED_FP32 = 1,    /* FP64 iterative refinement of the augmented-system solution from x = 0:
                             the FP64 residual rho = g - M x, then the same PCG on M~ delta = rho
                             from delta0 = P^{-1}[0; rho_v], x += delta, until the FP64 residual
                             passes the stop test.  M~ forms the block A E A^T from an FP32 copy
@@ -83,6 +83,16 @@ typedef enum {
                             If a correction solve breaks down, or max_refine corrections do not
                             reach the stop test, the FP64 PCG continues from the refined iterate
                             (its iterations count in pcg_iters).                              */
+  SDP_MIXED_TF32 = 2,    /* as SDP_MIXED_FP32, with the n^3 products E Y E of the correction
+                            operator (DENSE kind) run on the tensor cores (tcgen05 kind::tf32:
+                            FP32 operands read as TF32, FP32 accumulation in TMEM); the passes
+                            over A stream its FP32 copy.  DIAG kind: the same as SDP_MIXED_FP32
+                            (its A E A^T block, (E o E) p_u, has no matrix product)          */
+  SDP_MIXED_BF16 = 3     /* as SDP_MIXED_FP32 with a BF16 copy of A (DENSE kind, 2 bytes per
+                            entry, rows zero-padded to a multiple of 8 entries) or of E o E
+                            (DIAG kind), BF16 products summed in FP32 in the passes, and E Y E
+                            as BF16 tensor-core products (tcgen05 kind::f16, FP32 accumulation);
+                            the FP64 refinement recovers the accuracy of the direction        */
 } sdp_precision;
 
 typedef struct {
@@ -135,7 +145,7 @@ typedef struct {
                             fits), at the price of many more iterations (the condition number
                             of eq. augsys, not of the preconditioned operator); max_pcg bounds
                             its iterations and the stop test is the PCG one.  FP64 only
-                            (SDP_MIXED_FP32 with krylov = 1: SDP_EUNSUPPORTED).               */
+                            (a mixed form with krylov = 1: SDP_EUNSUPPORTED).               */
   int32_t int_passes;    /* DENSE_SVEC kind, FP64 operator (the FP64 form, and the FP64 residuals
                             of the mixed form): 1 (default) = the two passes over the svec rows,
                             A(Z) and A^T(y), stream an integer copy of A made at setup (two int32
@@ -172,6 +182,10 @@ typedef struct {
   double prof_A32_ms;
   int32_t prof_At32_launches;
   int32_t prof_A32_launches;
+  double refine_rate;    /* mixed forms: (||rho_k|| / ||g||)^(1/k) after k corrections, the mean
+                            contraction of the FP64 residual per correction solve -- the error of
+                            the low-precision correction operator as the refinement sees it
+                            (0 in the plain form)                                            */
 } sdp_newton_info;
 
 /* One outer interior-point iteration (ipm_step) or a whole solve (sdp_solve). */
@@ -431,6 +445,19 @@ sdp_status sdp_gemm_f64_tc(void* stream, int32_t tA, int32_t tB, int32_t M, int3
  * stream and the context stay usable.  The paper has no counterpart: this is the control that
  * lets a test make a bounded wait run out without faulting or hanging a GPU. */
 void sdp_set_tc_wait_limit_ns(uint64_t ns);
+
+/* Low-precision matrix product on the tensor cores, as the TF32 and BF16 forms run it (tcgen05 with
+ * FP32 accumulators in TMEM, operands staged by TMA): C = alpha A_s^T B_s for A_s (K x M) and B_s
+ * (K x N) column-major with leading dimensions lda, ldb, i.e. the rows of op(A) and the columns of
+ * op(B) K-contiguous.  tf32 = 1: A_s, B_s are FP32 and read as TF32 (kind::tf32); tf32 = 0: they are
+ * BF16 (kind::f16).  C: FP32, M x N column-major, ldc >= M.  Each product of two operands is exact
+ * in the FP32 accumulator; the sums are FP32.  The paper has no counterpart (its products are
+ * FP64); this entry point exposes the mixed forms' product for tests.  err_word: a device int32
+ * (the bounded-wait error word, cleared by the call).  lda, ldb >= K with 16-byte rows, A and B
+ * 16-byte aligned, M, N, K >= 1, else SDP_EINVAL; SDP_EUNSUPPORTED on a GPU that is not sm_10x;
+ * SDP_ETIMEOUT as sdp_gemm_f64_tc.  Returns after the work on `stream` has completed. */
+sdp_status sdp_gemm_tn_lp(void* stream, int32_t tf32, int32_t M, int32_t N, int32_t K, float alpha, const void* A,
+                          int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int32_t* err_word);
 
 /* Bytes of device workspace owned by the handle. */
 size_t sdp_workspace_bytes(const sdp_handle* h);

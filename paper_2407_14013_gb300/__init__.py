@@ -12,13 +12,18 @@ from dataclasses import dataclass
 from typing import Optional
 
 from . import _native as native
-from ._native import (SDP_A_DENSE_SVEC, SDP_A_DIAG, SDP_A_SPARSE_COO, SDP_ENOTCONV, SDP_FP64, SDP_MIXED_FP32,
-                      SDP_OK, SdpError, sdp_default_options)
+from ._native import (SDP_A_DENSE_SVEC, SDP_A_DIAG, SDP_A_SPARSE_COO, SDP_ENOTCONV, SDP_FP64, SDP_MIXED_BF16,
+                      SDP_MIXED_FP32, SDP_MIXED_TF32, SDP_OK, SdpError, sdp_default_options)
 
 __all__ = ["NewtonSolver", "SdpError", "native", "sdp_optimum", "sdp_optimum_at", "eigh", "solve_sdp_batch", "SDP_A_DIAG", "SDP_A_SPARSE_COO",
            "SDP_A_DENSE_SVEC"]
 
 KINDS = {"diag": SDP_A_DIAG, "sparse": SDP_A_SPARSE_COO, "dense": SDP_A_DENSE_SVEC}
+PRECISIONS = {"fp64": SDP_FP64, "mixed_fp32": SDP_MIXED_FP32, "mixed_tf32": SDP_MIXED_TF32,
+              "mixed_bf16": SDP_MIXED_BF16}
+# refinement defaults of the mixed forms: each correction solve is taken about as far as the
+# precision of its operator carries it (BF16 ~ 4e-3, TF32 ~ 5e-4, FP32 ~ 6e-8 relative)
+MIXED_DEFAULTS = {"mixed_fp32": (10, 1e-6), "mixed_tf32": (20, 1e-3), "mixed_bf16": (30, 1e-2)}
 
 
 @dataclass
@@ -48,6 +53,7 @@ class NewtonInfo:
     prof_A32_ms: float = 0.0
     prof_At32_launches: int = 0
     prof_A32_launches: int = 0
+    refine_rate: float = 0.0
 
 
 def _ptr(t) -> int:
@@ -73,7 +79,8 @@ class NewtonSolver:
     def __init__(self, prob, r_fixed: int = 0, r_hat: int = 10, precond_space: int = 0,
                  max_pcg: int = 2000, check_every: int = 8, beta_rule: int = 0,
                  newton_rtol: float = 1e-12, device: str = "cuda", stream=None, use_graph: bool = True,
-                 precision: str = "fp64", max_refine: int = 10, max_inner: int = 500, inner_rtol: float = 1e-6,
+                 precision: str = "fp64", max_refine: Optional[int] = None, max_inner: int = 500,
+                 inner_rtol: Optional[float] = None,
                  pcg_start: int = 0, tc_products: bool = True, krylov: str = "pcg", int_passes: bool = True):
         import torch
         self.torch = torch
@@ -108,8 +115,11 @@ class NewtonSolver:
         o.max_pcg, o.check_every, o.beta_rule = max_pcg, check_every, beta_rule
         o.newton_rtol = newton_rtol
         o.use_graph = 1 if use_graph else 0
-        o.precision = {"fp64": SDP_FP64, "mixed_fp32": SDP_MIXED_FP32}[precision]
-        o.max_refine, o.max_inner, o.inner_rtol = max_refine, max_inner, inner_rtol
+        o.precision = PRECISIONS[precision]
+        dr, dt = MIXED_DEFAULTS.get(precision, (10, 1e-6))
+        o.max_refine = dr if max_refine is None else max_refine
+        o.max_inner = max_inner
+        o.inner_rtol = dt if inner_rtol is None else inner_rtol
         o.pcg_start = pcg_start
         o.tc_products = 1 if tc_products else 0
         o.krylov = {"pcg": 0, "minres": 1}[krylov]
@@ -140,7 +150,8 @@ class NewtonSolver:
                           prof_At_ms=ci.prof_At_ms, prof_A_ms=ci.prof_A_ms,
                           prof_At_launches=ci.prof_At_launches, prof_A_launches=ci.prof_A_launches,
                           refine_steps=ci.refine_steps, prof_At32_ms=ci.prof_At32_ms, prof_A32_ms=ci.prof_A32_ms,
-                          prof_At32_launches=ci.prof_At32_launches, prof_A32_launches=ci.prof_A32_launches)
+                          prof_At32_launches=ci.prof_At32_launches, prof_A32_launches=ci.prof_A32_launches,
+                          refine_rate=ci.refine_rate)
 
     def solve(self, V, lam, Ct, bt, out=None, allow_notconv: bool = False):
         """Newton direction (dX, dy, dS) of (Newt-eps) for W = V diag(lam) V^T; device tensors.

@@ -17,7 +17,7 @@ SDP_OK, SDP_EINVAL, SDP_ENOMEM, SDP_ECUDA, SDP_ENOTCONV, SDP_ENUMERIC, SDP_ETIME
 STATUS_NAMES = ["SDP_OK", "SDP_EINVAL", "SDP_ENOMEM", "SDP_ECUDA", "SDP_ENOTCONV", "SDP_ENUMERIC",
                 "SDP_ETIMEOUT", "SDP_EUNSUPPORTED"]
 SDP_A_DIAG, SDP_A_SPARSE_COO, SDP_A_DENSE_SVEC = 0, 1, 2
-SDP_FP64, SDP_MIXED_FP32 = 0, 1
+SDP_FP64, SDP_MIXED_FP32, SDP_MIXED_TF32, SDP_MIXED_BF16 = 0, 1, 2, 3
 
 
 class sdp_problem(Structure):
@@ -42,7 +42,7 @@ class sdp_newton_info(Structure):
                 ("prof_At_ms", c_double), ("prof_A_ms", c_double),
                 ("prof_At_launches", c_int32), ("prof_A_launches", c_int32),
                 ("prof_At32_ms", c_double), ("prof_A32_ms", c_double),
-                ("prof_At32_launches", c_int32), ("prof_A32_launches", c_int32)]
+                ("prof_At32_launches", c_int32), ("prof_A32_launches", c_int32), ("refine_rate", c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
@@ -78,6 +78,8 @@ EXPORTS = {
     "sdp_gemm_f64_tc_work_bytes": (c_size_t, [c_int32, c_int32, c_int32]),
     "sdp_gemm_f64_tc": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_double, c_void_p, c_int64,
                                   c_void_p, c_int64, c_double, c_void_p, c_int64, c_void_p, c_size_t]),
+    "sdp_gemm_tn_lp": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, ctypes.c_float, c_void_p, c_int64,
+                                 c_void_p, c_int64, c_void_p, c_int64, c_void_p]),
     "sdp_debug_copy": (c_int32, [c_void_p, c_int32, c_void_p, c_int64]),
     "sdp_set_profiling": (c_int32, [c_void_p, c_int32]),
     "sdp_adjoint_dense_noalloc": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
@@ -245,6 +247,15 @@ def sdp_gemm_f64_tc(stream: int, tA: bool, tB: bool, M: int, N: int, K: int, alp
     lib = load()
     st = lib.sdp_gemm_f64_tc(c_void_p(stream), int(tA), int(tB), M, N, K, alpha, c_void_p(A), lda, c_void_p(B), ldb,
                              beta, c_void_p(C), ldc, c_void_p(work), work_bytes)
+    if st != SDP_OK:
+        raise SdpError(st, lib.sdp_last_error(None).decode())
+
+
+def sdp_gemm_tn_lp(stream: int, tf32: bool, M: int, N: int, K: int, alpha: float, A: int, lda: int, B: int, ldb: int,
+                   C: int, ldc: int, err_word: int) -> None:
+    lib = load()
+    st = lib.sdp_gemm_tn_lp(c_void_p(stream), int(tf32), M, N, K, alpha, c_void_p(A), lda, c_void_p(B), ldb,
+                            c_void_p(C), ldc, c_void_p(err_word))
     if st != SDP_OK:
         raise SdpError(st, lib.sdp_last_error(None).decode())
 

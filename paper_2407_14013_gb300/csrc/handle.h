@@ -29,13 +29,23 @@ struct Space {
   PcgCtl* ctl = nullptr;
 };
 
-// FP32 data of the mixed form's A E A^T block, plus its FP64 partial sums of B p_v, B^T p_u.
+// Low-precision data of the mixed forms' A E A^T block, plus their FP64 partial sums of B p_v,
+// B^T p_u.  FP32 form: FP32 copies and FFMA products; TF32 form: the same FP32 copy of A with the
+// n^3 products on the tensor cores (TF32 operands); BF16 form: a BF16 copy of A (or of E o E) and
+// BF16 tensor-core products.  Every low-precision sum is accumulated in FP32.
 struct Mixed32 {
-  float* A = nullptr;                          // FP32 copy of the svec rows (DENSE kind)
+  float* A = nullptr;                          // FP32 copy of the svec rows (DENSE kind; FP32, TF32)
+  void* A16 = nullptr;                         // BF16 copy of the svec rows, pitch Lp (BF16)
+  void* EE16 = nullptr;                        // BF16 copy of E o E, pitch ldk (DIAG kind, BF16)
+  void *Elp = nullptr, *Ylp = nullptr, *Glp = nullptr;   // tensor-core operands, n x n, pitch ldk
   float *E = nullptr, *EE = nullptr, *Y = nullptr, *F = nullptr, *Z = nullptr;
   float *zsvec = nullptr, *partY = nullptr, *partA = nullptr, *pu = nullptr;
   float* ws = nullptr;
   size_t ws_elems = 0;
+  int64_t Lp = 0;                              // row pitch of the BF16 rows (elements, multiple of 8)
+  int ldk = 0;                                 // pitch of the tensor-core operands (multiple of 8)
+  int G16 = 1;                                 // row groups of the BF16 A^T pass
+  int* err = nullptr;                          // set by a tensor-core product whose bounded wait gave up
   double *partBv = nullptr, *partBu = nullptr;
 };
 
@@ -68,6 +78,7 @@ struct sdp_handle {
   std::vector<double> sp_rownorm2;  // SPARSE_COO: ||A_i||_F^2 (start point of the outer loop)
   sdp_options opt{};
   bool mixed = false;
+  int lp = 0;                       // sdp_precision of the handle
   cudaStream_t st = nullptr;
   int r_max = 0, d_max = 0, mb = 0, mb2 = 0;
   double s_A = 1.0;
@@ -112,6 +123,7 @@ struct sdp_handle {
   int64_t launches = 0;
   int space = 1, r = 0, d = 0;
   int refine_steps = 0, inner_iters = 0;
+  double refine_rate = 0.0, refine_rr0 = 0.0;   // mixed forms: contraction of the FP64 residual
   std::string err;
   // optional CUDA-event timing of the constraint-operator passes (sdp_set_profiling)
   bool prof = false;

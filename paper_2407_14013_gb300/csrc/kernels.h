@@ -1,6 +1,7 @@
 // Internal launch wrappers shared by the translation units of the library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,6 +35,34 @@ cudaError_t gemm_f64(cudaStream_t st, bool tA, bool tB, int M, int N, int K, dou
 // before any stream capture.
 size_t tc_gemm_work_bytes(int M, int N, int K);
 cudaError_t tc_prepare();
+// 2-D TMA tensor map (128-byte swizzle, zero fill outside) over `rows` rows of `inner` BF16 or FP32
+// elements, `pitch_bytes` apart (a multiple of 16), boxes of box_inner x box_rows
+cudaError_t tmap_2d(CUtensorMap* map, bool f32, const void* base, uint64_t inner, uint64_t rows, uint64_t pitch_bytes,
+                    uint32_t box_inner, uint32_t box_rows);
+
+// ---- lp_gemm.cu: BF16 / TF32 tensor-core products with FP32 accumulation (mixed form) -----------
+// C (M x N, column-major, pitch ldc; FP32, or BF16 when out_bf16) = alpha op(A) op(B), op(A) given
+// by its rows and op(B) by its columns, both K-contiguous with pitches lda, ldb (elements; 16-byte
+// rows): C = A_s^T B_s for A_s (K x M) and B_s (K x N) column-major.  tf32: FP32 operands read as
+// TF32 (kind::tf32); else BF16 operands (kind::f16).  K >= 1; err as for gemm_f64_tc.
+cudaError_t lp_prepare();
+cudaError_t lp_gemm(cudaStream_t st, bool tf32, int M, int N, int K, float alpha, const void* A, int64_t lda,
+                    const void* B, int64_t ldb, void* C, int64_t ldc, bool out_bf16, int* err, int64_t* launches,
+                    const int32_t* done = nullptr);
+// Passes over a BF16 copy of the svec rows (m rows, pitch Lp, a multiple of 8, zero padded):
+// part[g * Lp + c] = sum_{i in group g} p_i a[i, c] (FP32), and out[i] = <a[i, :], z> (z FP32 of
+// length Lp, zero padded)
+int bf16_gemvT_groups(int m, int64_t Lp);
+void bf16_gemvT(cudaStream_t st, const void* A16, int m, int64_t Lp, const float* p, float* part, int groups,
+                const int32_t* done, int64_t* launches);
+void bf16_gemv(cudaStream_t st, const void* A16, int m, int64_t Lp, const float* z, float* out, const int32_t* done,
+               int64_t* launches);
+// Y (n x n, pitch ldk, BF16 or FP32, both triangles) = smat(sum_g part[g * Lp + .])
+void lp_unpack(cudaStream_t st, int n, const float* part, int groups, int64_t Lp, void* Y, int ldk, bool bf16,
+               const int32_t* done, int64_t* launches);
+// X (rows x cols FP64, pitch ldx) -> Y (BF16 or FP32, pitch ldy); columns cols .. ldy-1 of Y are zeroed
+void lp_convert(cudaStream_t st, int rows, int cols, const double* X, int64_t ldx, void* Y, int64_t ldy, bool bf16,
+                int64_t* launches);
 cudaError_t gemm_f64_tc(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
                         int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* work,
                         size_t work_bytes, int* err, int flags, int64_t* launches, const int32_t* done = nullptr);

@@ -145,24 +145,42 @@ void carve_space(sdp_handle* h, Carver& c, Space& S) {
 
 void carve_mixed(sdp_handle* h, Carver& c, Mixed32& M) {
   const size_t n = h->n, m = h->m, nn = n * n, dm = h->d_max;
+  const bool bf = h->lp == SDP_MIXED_BF16, tc = h->lp == SDP_MIXED_TF32 || bf;
+  M.ldk = (int)((n + 7) / 8 * 8);                  // pitch of the tensor-core operands (16-byte rows)
+  M.Lp = (h->N + 7) / 8 * 8;                       // pitch of the BF16 rows of A
+  const size_t esz = bf ? 2 : 4;
   if (h->kind == SDP_A_DENSE_SVEC) {
-    M.A = c.take<float>((size_t)m * h->N);
-    M.E = c.take<float>(nn);
-    M.Y = c.take<float>(nn);
-    M.F = c.take<float>(nn);
+    if (bf) {
+      M.A16 = c.take<char>((size_t)m * M.Lp * 2);
+      M.G16 = bf16_gemvT_groups(h->m, M.Lp);
+      M.partY = c.take<float>((size_t)M.G16 * M.Lp);
+    } else {
+      M.A = c.take<float>((size_t)m * h->N);
+      M.partY = c.take<float>((size_t)h->GY32 * h->N);
+    }
+    if (!tc) {
+      M.E = c.take<float>(nn);
+      M.Y = c.take<float>(nn);
+      M.F = c.take<float>(nn);
+    } else {
+      M.Elp = c.take<char>(n * M.ldk * esz);
+      M.Ylp = c.take<char>(n * M.ldk * esz);
+      M.Glp = c.take<char>(n * M.ldk * esz);
+    }
     M.Z = c.take<float>(nn);
-    M.zsvec = c.take<float>(h->N);
-    M.partY = c.take<float>((size_t)h->GY32 * h->N);
+    M.zsvec = c.take<float>(M.Lp);                 // the tail beyond n(n+1)/2 stays zero
     M.partA = c.take<float>(rows_gemv_part_elems(m, h->N));
   } else {
-    M.EE = c.take<float>(nn);
+    if (bf) M.EE16 = c.take<char>(n * M.ldk * 2);
+    else M.EE = c.take<float>(nn);
     M.partA = c.take<float>(rows_gemv_part_elems(n, n));
   }
-  M.pu = c.take<float>(m);
+  M.pu = c.take<float>(std::max(m, (size_t)M.ldk));   // zero tail: the BF16 GEMV over E o E reads ldk
   M.ws_elems = 4 * nn;
   M.ws = c.take<float>(M.ws_elems);
   M.partBv = c.take<double>(rows_gemv_part_elems(m, dm));
   M.partBu = c.take<double>(rows_gemv_part_elems(dm, m));
+  M.err = c.take<int>(4);
 }
 
 // Lay out every buffer; with base == nullptr only the size is computed.
@@ -254,16 +272,17 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   if (prob->kind == SDP_A_SPARSE_COO) {
     if (prob->nnz < 1 || prob->nnz > INT32_MAX || !prob->a_con || !prob->a_row || !prob->a_col || !prob->a_val)
       return fail(nullptr, SDP_EINVAL, "SPARSE_COO needs 1 <= nnz < 2^31 and all four entry arrays");
-    if (opt_in && opt_in->precision == SDP_MIXED_FP32)
-      return fail(nullptr, SDP_EUNSUPPORTED, "the mixed form is built for the DIAG and DENSE_SVEC kinds");
+    if (opt_in && opt_in->precision != SDP_FP64)
+      return fail(nullptr, SDP_EUNSUPPORTED, "the mixed forms are built for the DIAG and DENSE_SVEC kinds");
   }
   if (prob->kind == SDP_A_DIAG && m != n) return fail(nullptr, SDP_EINVAL, "DIAG kind needs m == n");
   if (prob->kind == SDP_A_DENSE_SVEC && !prob->a_dense) return fail(nullptr, SDP_EINVAL, "a_dense is NULL");
-  if (opt.precision != SDP_FP64 && opt.precision != SDP_MIXED_FP32)
+  if (opt.precision != SDP_FP64 && opt.precision != SDP_MIXED_FP32 && opt.precision != SDP_MIXED_TF32 &&
+      opt.precision != SDP_MIXED_BF16)
     return fail(nullptr, SDP_EUNSUPPORTED, "precision not built");
   if (opt.max_pcg < 1 || opt.check_every < 1 || !(opt.newton_rtol >= 0.0))
     return fail(nullptr, SDP_EINVAL, "bad PCG options");
-  if (opt.precision == SDP_MIXED_FP32 && (opt.max_refine < 1 || opt.max_inner < 1 || !(opt.inner_rtol > 0.0)))
+  if (opt.precision != SDP_FP64 && (opt.max_refine < 1 || opt.max_inner < 1 || !(opt.inner_rtol > 0.0)))
     return fail(nullptr, SDP_EINVAL, "bad refinement options");
   const int r_max = opt.r_fixed > 0 ? opt.r_fixed : std::min(opt.r_hat, n - 1);
   if (r_max < 1 || r_max >= n) return fail(nullptr, SDP_EINVAL, "rank parameter out of range [1, n)");
@@ -361,7 +380,8 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   h->a_con = prob->a_con; h->a_row = prob->a_row; h->a_col = prob->a_col; h->a_val = prob->a_val;
   h->a_dense = prob->a_dense;
   h->opt = opt;
-  h->mixed = (opt.precision == SDP_MIXED_FP32);
+  h->mixed = (opt.precision != SDP_FP64);
+  h->lp = opt.precision;
   h->st = static_cast<cudaStream_t>(stream);
   h->N = (int64_t)n * (n + 1) / 2;
   h->fx = (h->kind == SDP_A_DENSE_SVEC && opt.int_passes == 1);
@@ -418,6 +438,13 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
       h->tcw_bytes = h->tcw_b_bytes = 0;
     }
   }
+  if (h->lp == SDP_MIXED_TF32 || h->lp == SDP_MIXED_BF16) {
+    if (prob->kind == SDP_A_DENSE_SVEC && (tc_prepare() != cudaSuccess || lp_prepare() != cudaSuccess)) {
+      cudaGetLastError();
+      delete h;
+      return fail(nullptr, SDP_EUNSUPPORTED, "the TF32 / BF16 forms need tcgen05 (a Blackwell GPU)");
+    }
+  }
   h->pool_bytes = carve(h, nullptr);
   cudaError_t e = cudaMalloc(&h->pool, h->pool_bytes);
   if (e != cudaSuccess) {
@@ -472,7 +499,10 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
       sdp_destroy(h);
       return fail(nullptr, SDP_EINVAL, "A has a zero or non-finite Frobenius norm");
     }
-    if (h->mixed) convert<float, double>(h->st, (int64_t)m * h->N, h->a_dense, h->m32.A, &h->launches);
+    if (h->mixed && h->lp == SDP_MIXED_BF16)   // BF16 rows, zero padded to a 16-byte pitch
+      lp_convert(h->st, m, (int)h->N, h->a_dense, h->N, h->m32.A16, h->m32.Lp, true, &h->launches);
+    else if (h->mixed)
+      convert<float, double>(h->st, (int64_t)m * h->N, h->a_dense, h->m32.A, &h->launches);
     if (h->fx) fx_split_rows(h->st, h->a_dense, m, h->N, h->a_fx, h->a_fx_e, &h->launches);
   } else if (h->kind == SDP_A_SPARSE_COO) {
     sparse_sumsq(h->st, h->sp, h->dotbuf, h->scratch, &h->launches);
@@ -685,12 +715,19 @@ sdp_status apply_operator_mixed(sdp_handle* h, Space& S, const double* pin, doub
     CU(gemm_big(h, s0, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, h->ws_b[0], h->ws_b_elems, L, 0,
                 done, 1));
     launch_to_float(st, m, pu, M.pu, done, L);
-    rows_gemv<float>(st, M.EE, n, n, M.pu, M.partA, done, L);               // (E o E) p_u
+    int S32;
+    if (M.EE16) {                                                            // (E o E) p_u, BF16 copy
+      bf16_gemv(st, M.EE16, n, M.ldk, M.pu, M.partA, done, L);
+      S32 = 1;
+    } else {                                                                 // (E o E) p_u, FP32 copy
+      rows_gemv<float>(st, M.EE, n, n, M.pu, M.partA, done, L);
+      S32 = rows_gemv_slabs(n, n, 4);
+    }
     launch_diag_scale_rows<double>(st, n, r, pu, S.Vs, S.Tm, done, L);
     CU(gemm_big(h, st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, 0, done));
     join(h, 0, 2);
     launch_ap_finish<double>(st, m, d, n, r, nullptr, 0, S.Up, S.Vs, S.H, S.Dv, pin, gsub, out, mode, S.ctl,
-                             h->dotbuf, h->counter, L, M.partA, rows_gemv_slabs(n, n, 4));
+                             h->dotbuf, h->counter, L, M.partA, S32);
     return SDP_OK;
   }
   // side branch: the FP64 rows with B, beside the FP32 A E A^T chain on the main stream
@@ -699,7 +736,7 @@ sdp_status apply_operator_mixed(sdp_handle* h, Space& S, const double* pin, doub
   rows_gemv<double>(s0, S.Bt, d, m, pu, M.partBu, done, L);                 // B^T p_u
   launch_to_float(st, m, pu, M.pu, done, L);
   int SA;
-  if (h->kind == SDP_A_DENSE_SVEC) {
+  if (h->kind == SDP_A_DENSE_SVEC && h->lp == SDP_MIXED_FP32) {
     prof_begin(h, 2);
     // A^T(p_u); the FP32 pass has twice the row groups of the FP64 one, and a separate unpack
     // (all SMs) reduces them faster than the last CTA of each column block would
@@ -713,6 +750,28 @@ sdp_status apply_operator_mixed(sdp_handle* h, Space& S, const double* pin, doub
     rows_gemv<float>(st, M.A, m, h->N, M.zsvec, M.partA, done, L);          // A(E Y E)
     prof_end(h);
     SA = h->SA32;
+  } else if (h->kind == SDP_A_DENSE_SVEC) {
+    // TF32 / BF16 forms: Y = A^T(p_u) in the operand layout of the tensor cores, G = Y E and
+    // Z = E G as tcgen05 products with FP32 accumulation, then A(Z)
+    const bool bf = h->lp == SDP_MIXED_BF16;
+    prof_begin(h, 2);
+    if (bf) bf16_gemvT(st, M.A16, m, M.Lp, M.pu, M.partY, M.G16, done, L);
+    else rows_gemvT<float>(st, M.A, m, h->N, M.pu, M.partY, h->GY32, done, L);
+    prof_end(h);
+    lp_unpack(st, n, M.partY, bf ? M.G16 : h->GY32, bf ? M.Lp : h->N, M.Ylp, M.ldk, bf, done, L);
+    // K runs over the whole pitch: the entries n .. ldk - 1 of every operand column are zero
+    CU(lp_gemm(st, !bf, n, n, M.ldk, 1.f, M.Ylp, M.ldk, M.Elp, M.ldk, M.Glp, M.ldk, bf, M.err, L, done));   // G = Y E
+    CU(lp_gemm(st, !bf, n, n, M.ldk, 1.f, M.Elp, M.ldk, M.Glp, M.ldk, M.Z, n, false, M.err, L, done));      // Z = E G
+    svec_pack_plus<float>(st, n, 0, M.Z, nullptr, nullptr, M.zsvec, done, L);
+    prof_begin(h, 3);
+    if (bf) {
+      bf16_gemv(st, M.A16, m, M.Lp, M.zsvec, M.partA, done, L);              // A(E Y E)
+      SA = 1;
+    } else {
+      rows_gemv<float>(st, M.A, m, h->N, M.zsvec, M.partA, done, L);
+      SA = h->SA32;
+    }
+    prof_end(h);
   } else {
     rows_gemv<float>(st, M.EE, n, n, M.pu, M.partA, done, L);               // (E o E) p_u
     SA = rows_gemv_slabs(n, n, 4);
@@ -935,6 +994,8 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   for (int k = 0; k < 4; ++k) { h->prof_ms[k] = 0.0; h->prof_n[k] = 0; }
   h->refine_steps = 0;
   h->inner_iters = 0;
+  h->refine_rate = 0.0;
+  h->refine_rr0 = 0.0;
   if (!h->ev_phase[0])
     for (auto& e : h->ev_phase) CU(cudaEventCreate(&e));
   CU(cudaEventRecord(h->ev_phase[0], st));
@@ -1044,9 +1105,12 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     launch_add_diag(st, m, S.Pinv, h->lin ? h->lin_lam : nullptr, h->lin ? 0.0 : h->ctl_host->beta_pc, L);  // + Lam
     CU(spd_inverse_any(h, st, m, S.Pinv, S.ws, ws, pstatus, L));
   }
-  if (h->mixed) {   // FP32 copies for the A E A^T block of the mixed operator
-    if (S.EE) convert<float, double>(st, (int64_t)n * n, S.EE, h->m32.EE, L);
-    else convert<float, double>(st, (int64_t)n * n, S.E, h->m32.E, L);
+  if (h->mixed) {   // low-precision copies for the A E A^T block of the mixed operator
+    Mixed32& M = h->m32;
+    if (S.EE && M.EE16) lp_convert(st, n, n, S.EE, n, M.EE16, M.ldk, true, L);
+    else if (S.EE) convert<float, double>(st, (int64_t)n * n, S.EE, M.EE, L);
+    else if (M.Elp) lp_convert(st, n, n, S.E, n, M.Elp, M.ldk, h->lp == SDP_MIXED_BF16, L);
+    else convert<float, double>(st, (int64_t)n * n, S.E, M.E, L);
   }
   CU(cudaEventRecord(h->ev_phase[1], st));
   CU(cudaMemcpyAsync(&h->setup_ctl, h->ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
@@ -1108,6 +1172,8 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
       launch_norm_check<double>(st, nt, S.rv, 0.0, h->ctl, h->dotbuf, h->counter, L);
       CU(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
       CU(cudaStreamSynchronize(st));
+      if (h->refine_steps == 0) h->refine_rr0 = h->ctl_host->rr;
+      else h->refine_rate = std::pow(std::sqrt(h->ctl_host->rr / h->refine_rr0), 1.0 / h->refine_steps);
       if (h->ctl_host->done) break;
       if (h->refine_steps >= h->opt.max_refine) {
         fallback = true;
@@ -1172,12 +1238,13 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   lower_to_full(st, n, dX, L);
   CU(cudaEventRecord(h->ev_phase[3], st));
   CU(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
-  int tc_err = 0;
+  int tc_err = 0, lp_err = 0;
   if (h->tc_err) CU(cudaMemcpyAsync(&tc_err, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (h->m32.err) CU(cudaMemcpyAsync(&lp_err, h->m32.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
   CU(cudaGetLastError());
 
-  if (tc_err) return fail(h, SDP_ETIMEOUT, "a bounded wait inside a tensor-core product gave up");
+  if (tc_err || lp_err) return fail(h, SDP_ETIMEOUT, "a bounded wait inside a tensor-core product gave up");
   const PcgCtl& c = *h->ctl_host;
   for (int q = 0; q < 3; ++q) {
     float ms = 0.f;
@@ -1212,6 +1279,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     info->prof_A32_ms = h->prof_ms[3];
     info->prof_At32_launches = (int32_t)h->prof_n[2];
     info->prof_A32_launches = (int32_t)h->prof_n[3];
+    info->refine_rate = h->refine_rate;
   }
   // the split and the preconditioner core stay usable for another right side (sdp_newton_resolve)
   // unless the factorisation failed

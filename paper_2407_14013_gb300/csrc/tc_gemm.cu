@@ -35,6 +35,7 @@
 #include <string>
 
 #include "handle.h"
+#include "tc_ptx.cuh"
 
 namespace wc {
 
@@ -52,85 +53,11 @@ constexpr int FACC_BYTES = BM * BN * 8;                  // FP64 accumulators of
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + FACC_BYTES + 1024;  // + alignment slack
 constexpr int TMEM_COLS = 256;                           // two 128-column FP32 accumulators
 constexpr int NPAIRS = S * (S + 1) / 2;                  // s + t <= S + 1
-constexpr unsigned long long WAIT_NS = 2000000000ull;
+constexpr unsigned long long WAIT_NS = tcx::kWaitNs;
 
-// ---- PTX wrappers --------------------------------------------------------------------------
+// ---- PTX wrappers: tc_ptx.cuh; the MMA of this kernel ----------------------------------------
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait for the phase of `parity` to complete; false after `limit` ns (sets *abort, *err)
-// or when another role has set *abort.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, int* err,
-                          unsigned long long limit = WAIT_NS) {
-  const unsigned long long t0 = gtimer();
-  const uint32_t every = limit < 1000000ull ? 0u : 255u;   // short limits: look at the clock on every try
-  for (uint32_t it = 0;; ++it) {
-    if (mbar_try(bar, parity)) return true;
-    if ((it & every) == every) {
-      if (*abort) return false;
-      if (gtimer() - t0 > limit) {
-        *abort = 1;
-        atomicExch(err, 1);
-        return false;
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
-                                            uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-      "[%5];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFFu);      // start address
-  d |= (uint64_t)1u << 16;                      // leading byte offset (unused for this layout)
-  d |= (uint64_t)(1024u >> 4) << 32;            // stride byte offset
-  d |= (uint64_t)1u << 46;                      // descriptor version
-  d |= (uint64_t)2u << 61;                      // 128-byte swizzle
-  return d;
-}
+using namespace tcx;
 
 // Instruction descriptor: kind::f16 with BF16 A and B (K-major), FP32 D, M = 128, N = 128.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -145,19 +72,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
       : "memory");
 }
 
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-#define WC_TMEM_LD32(taddr, r)                                                                                  \
-  asm volatile(                                                                                                 \
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, " \
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"           \
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),          \
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),    \
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),  \
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])   \
-      : "r"(taddr))
 
 // ---- pair table: (s, t) with s + t <= S + 1 (1-based), largest weights first ---------------
 
@@ -499,8 +413,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 // C = alpha sum_z part[z] + beta C over the split K ranges, in z order (deterministic); tiles
 // above the diagonal are skipped when `lower` is set, as in the product.
 __global__ void tc_reduce_kernel(int M, int N, int nz, const double* __restrict__ part, double alpha, double beta,
-                                 double* __restrict__ C, int64_t ldc, int lower, const int32_t* __restrict__ done) {
+                                 double* __restrict__ C, int64_t ldc, int lower, const int32_t* __restrict__ done,
+                                 const int* __restrict__ err) {
   if (done && *done) return;
+  if (*err) return;                          // a product tile gave up: its partials are not written
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (int64_t)M * N) return;
   const int row = (int)(q % M), col = (int)(q / M);
@@ -543,6 +459,28 @@ cudaError_t make_map(CUtensorMap* map, const void* slices, int rows, int Kpad) {
 }
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+// 2-D tiled tensor map (128-byte swizzle) over a row-pitched matrix: `rows` rows of `inner`
+// elements (BF16 or FP32), `pitch_bytes` apart; boxes of box_inner x box_rows.  Reads outside the
+// matrix return zeros.
+cudaError_t tmap_2d(CUtensorMap* map, bool f32, const void* base, uint64_t inner, uint64_t rows, uint64_t pitch_bytes,
+                    uint32_t box_inner, uint32_t box_rows) {
+  cudaError_t e = encode_fn();
+  if (e != cudaSuccess) return e;
+  const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch_bytes};
+  const cuuint32_t box[2] = {box_inner, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                        const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+namespace {
 
 // limit of the main-loop waits of the product (sdp_set_tc_wait_limit_ns); the drain after an
 // expiry always keeps WAIT_NS
@@ -675,7 +613,7 @@ cudaError_t gemm_f64_tc_one(cudaStream_t st, bool tA, bool tB, int M, int N, int
   if (nz > 1) {
     const int64_t tot = (int64_t)M * N;
     tc_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, nz, part, alpha, beta, C, ldc,
-                                                                    (flags & GEMM_LOWER) ? 1 : 0, done);
+                                                                    (flags & GEMM_LOWER) ? 1 : 0, done, err);
     if (launches) ++*launches;
   }
   return cudaGetLastError();
@@ -720,6 +658,12 @@ extern "C" sdp_status sdp_gemm_f64_tc(void* stream, int32_t tA, int32_t tB, int3
   return SDP_OK;
 }
 
+namespace wc {
+extern std::atomic<unsigned long long> g_main_wait_ns_lp;   // lp_gemm.cu
+}
+
 extern "C" void sdp_set_tc_wait_limit_ns(uint64_t ns) {
-  wc::g_main_wait_ns.store(ns == 0 ? wc::WAIT_NS : (unsigned long long)ns);
+  const unsigned long long v = ns == 0 ? wc::WAIT_NS : (unsigned long long)ns;
+  wc::g_main_wait_ns.store(v);
+  wc::g_main_wait_ns_lp.store(v);
 }
