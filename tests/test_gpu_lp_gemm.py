@@ -86,8 +86,9 @@ def test_bounded_wait_of_the_lp_product():
     SDP_ETIMEOUT (no fault, no hang); with the default restored the next product is exact."""
     from paper_2407_14013_gb300 import _native
     rng = np.random.default_rng(3)
-    As = rng.integers(-8, 9, (512, 256)).astype(np.float64)
-    Bs = rng.integers(-8, 9, (512, 256)).astype(np.float64)
+    # a long K (1024 K-slices per tile) keeps the product running far longer than the limit
+    As = rng.integers(-8, 9, (65536, 256)).astype(np.float64)
+    Bs = rng.integers(-8, 9, (65536, 256)).astype(np.float64)
     _native.sdp_set_tc_wait_limit_ns(5)
     try:
         with pytest.raises(_native.SdpError) as ei:
