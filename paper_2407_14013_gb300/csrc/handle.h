@@ -103,6 +103,8 @@ struct sdp_handle {
   char* tcw_b = nullptr;            // the same for the n x r products on the first side stream
   size_t tcw_b_bytes = 0;
   int* tc_err = nullptr;            // set by a tensor-core product whose bounded wait gave up
+  char* vs_mem[2] = {nullptr, nullptr};   // slices of the sorted eigenvectors Vs, made once per split:
+  wc::TcSlices vs_sl[2];                  // [0] rows of Vs (op = Vs), [1] rows of Vs^T (op = Vs^T)
   bool no_coop = false;             // batched solves: no cooperative (grid-barrier) launches
   int64_t b_elems = 0;              // capacity of the explicit B = A Q (m x d)
   int64_t bt_elems = 0;             // capacity of B^T (d x m)

@@ -33,6 +33,16 @@ cudaError_t gemm_f64(cudaStream_t st, bool tA, bool tB, int M, int N, int K, dou
 // order).  done: device stop flag (may be NULL): every kernel returns at once when it is set.
 // tc_prepare(): the one-time setup (driver entry point, shared-memory attribute); call it
 // before any stream capture.
+// Slices of an operand made once and reused by later products over the same K (rows of op(X)).
+struct TcSlices {
+  void* s = nullptr;      // 8 planes of rows x kpad(K) BF16 digits
+  int* e = nullptr;       // per-row power-of-two exponents
+  int rows = 0, K = 0;
+  bool valid = false;
+};
+size_t tc_slices_bytes(int R, int K);
+cudaError_t tc_make_slices(cudaStream_t st, int R, int K, const double* X, int64_t rs, int64_t ks, void* mem,
+                           TcSlices* out, int64_t* launches);
 size_t tc_gemm_work_bytes(int M, int N, int K);
 cudaError_t tc_prepare();
 // 2-D TMA tensor map (128-byte swizzle, zero fill outside) over `rows` rows of `inner` BF16 or FP32
@@ -65,7 +75,8 @@ void lp_convert(cudaStream_t st, int rows, int cols, const double* X, int64_t ld
                 int64_t* launches);
 cudaError_t gemm_f64_tc(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
                         int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* work,
-                        size_t work_bytes, int* err, int flags, int64_t* launches, const int32_t* done = nullptr);
+                        size_t work_bytes, int* err, int flags, int64_t* launches, const int32_t* done = nullptr,
+                        const TcSlices* cA = nullptr, const TcSlices* cB = nullptr);
 
 // ---- rows.cu: products with row-major matrices streamed from memory ---------------------------
 // Partial sums of y_i = <row_i(A), x>: part[s * m + i] over column slabs s.  The slab count

@@ -245,6 +245,10 @@ size_t carve(sdp_handle* h, char* base) {
     h->tc_err = c.take<int>(64);
     h->tcw = c.take<char>(h->tcw_bytes);
     if (h->tcw_b_bytes) h->tcw_b = c.take<char>(h->tcw_b_bytes);
+    if (n >= (size_t)kTcMin) {
+      h->vs_mem[0] = c.take<char>(tc_slices_bytes(h->n, h->n));
+      h->vs_mem[1] = c.take<char>(tc_slices_bytes(h->n, h->n));
+    }
   }
   h->hV = c.take<double>(nn);
   h->hlam = c.take<double>(n);
@@ -579,8 +583,14 @@ cudaError_t gemm_big(sdp_handle* h, cudaStream_t st, bool tA, bool tB, int M, in
   char* w = slot == 0 ? h->tcw : h->tcw_b;
   const size_t wb = slot == 0 ? h->tcw_bytes : h->tcw_b_bytes;
   if (w && M >= 64 && N >= 64 && K >= 64 && (double)M * N * K >= kTcMinWork &&
-      !(flags & (GEMM_KSTART_ROW | GEMM_KSTART_COL)) && tc_gemm_work_bytes(M, N, std::min(K, 4096)) <= wb)
-    return gemm_f64_tc(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, w, wb, h->tc_err, flags, L, done);
+      !(flags & (GEMM_KSTART_ROW | GEMM_KSTART_COL)) && tc_gemm_work_bytes(M, N, std::min(K, 4096)) <= wb) {
+    // the eigenvectors Vs of this solve enter many products: their slices are made once per split
+    const double* Vs = h->s64.Vs;
+    const TcSlices* cA = (A == Vs && lda == h->n) ? &h->vs_sl[tA ? 1 : 0] : nullptr;
+    const TcSlices* cB = (B == Vs && ldb == h->n) ? &h->vs_sl[tB ? 0 : 1] : nullptr;
+    return gemm_f64_tc(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, w, wb, h->tc_err, flags, L, done,
+                       cA, cB);
+  }
   return gemm_f64(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, L, done, flags);
 }
 
@@ -1030,6 +1040,11 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   h->r = r;
   h->d = d;
   h->space = h->opt.precond_space == 0 ? (d <= m ? 1 : 2) : h->opt.precond_space;
+  h->vs_sl[0].valid = h->vs_sl[1].valid = false;
+  if (h->vs_mem[0]) {   // slices of Vs (rows of Vs and of Vs^T) for every tensor-core product with it
+    CU(tc_make_slices(st, n, n, S.Vs, 1, n, h->vs_mem[0], &h->vs_sl[0], L));
+    CU(tc_make_slices(st, n, n, S.Vs, n, 1, h->vs_mem[1], &h->vs_sl[1], L));
+  }
   split_scale_cols(st, n, S.Vs, h->e, h->Ve, L);
   // E = Ve Vs^T is symmetric: the lower triangle by the product, the upper by a mirror
   CU(gemm_big(h, st, false, true, n, n, n, 1.0, h->Ve, n, S.Vs, n, 0.0, S.E, n, S.ws, ws, L, GEMM_LOWER));

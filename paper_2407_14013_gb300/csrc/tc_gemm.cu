@@ -190,9 +190,16 @@ __global__ void __launch_bounds__(256) slice_kernel(int R, int K, int Kpad, cons
   const int r = tid >> 3, g = tid & 7;
   const int gr = r0 + r;
   if (gr >= R) return;
-  long long Nv[8];
+  // N = hi 2^28 + lo with 0 <= lo < 2^28: the four low digits come from lo and carry into hi
+  // (at most 1), the four high ones from hi; the same centred digits as the 64-bit recursion,
+  // in 32-bit integer arithmetic
+  int hi[8], lo[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) Nv[j] = fixed_point(tile[r][g * 8 + j], rexp[r]);
+  for (int j = 0; j < 8; ++j) {
+    const long long Nv = fixed_point(tile[r][g * 8 + j], rexp[r]);
+    hi[j] = (int)(Nv >> 28);
+    lo[j] = (int)(Nv & 0xFFFFFFFll);
+  }
   // Kpad is a multiple of BK, so every row, plane and group of 8 starts on 16 bytes
   const int64_t plane16 = (int64_t)R * Kpad / 8;
   uint4* o = reinterpret_cast<uint4*>(out + (int64_t)gr * Kpad + k0 + g * 8);
@@ -201,14 +208,22 @@ __global__ void __launch_bounds__(256) slice_kernel(int R, int K, int Kpad, cons
     uint32_t wv[4];
 #pragma unroll
     for (int j = 0; j < 8; j += 2) {
-      long long a0 = Nv[j], a1 = Nv[j + 1];
-      if (sidx > 0) {
-        a0 = ((Nv[j] + 64) & 127) - 64;
-        a1 = ((Nv[j + 1] + 64) & 127) - 64;
-        Nv[j] = (Nv[j] - a0) >> 7;                                     // exact
-        Nv[j + 1] = (Nv[j + 1] - a1) >> 7;
-      }                                                                 // else a_1, |a_1| <= 64
-      wv[j / 2] = (uint32_t)bf[a0 + 64] | ((uint32_t)bf[a1 + 64] << 16);
+      int a[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        int& x = sidx >= 4 ? lo[j + u] : hi[j + u];
+        if (sidx > 0) {
+          a[u] = ((x + 64) & 127) - 64;
+          x = (x - a[u]) >> 7;                                         // exact
+        } else {
+          a[u] = x;                                                     // a_1, |a_1| <= 64
+        }
+      }
+      if (sidx == 4) {                                                  // lo is spent: its carry goes up
+        hi[j] += lo[j];
+        hi[j + 1] += lo[j + 1];
+      }
+      wv[j / 2] = (uint32_t)bf[a[0] + 64] | ((uint32_t)bf[a[1] + 64] << 16);
     }
     o[sidx * plane16] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
   }
@@ -514,19 +529,55 @@ namespace {
 
 cudaError_t gemm_f64_tc_one(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
                             int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
-                            void* work, int* err, int flags, int64_t* launches, const int32_t* done);
+                            void* work, int* err, int flags, int64_t* launches, const int32_t* done,
+                            const TcSlices* cA = nullptr, const TcSlices* cB = nullptr);
 
 }  // namespace
+
+size_t tc_slices_bytes(int R, int K) {
+  const size_t kp = (size_t)kpad_of(K > 0 ? K : 1);
+  return align256((size_t)S * R * kp * 2) + align256((size_t)R * 4) + align256((size_t)R * 8);
+}
+
+// The slices of op(X) (R rows of K entries, X(r, k) = X[r rs + k ks]) made once into `mem`
+// (tc_slices_bytes(R, K) bytes, 256-byte aligned), for products that reuse the operand.
+cudaError_t tc_make_slices(cudaStream_t st, int R, int K, const double* X, int64_t rs, int64_t ks, void* mem,
+                           TcSlices* out, int64_t* launches) {
+  if (R < 1 || K < 1 || !X || !mem || !out) return cudaErrorInvalidValue;
+  const int Kp = kpad_of(K);
+  char* w = static_cast<char*>(mem);
+  __nv_bfloat16* sl = reinterpret_cast<__nv_bfloat16*>(w);
+  w += align256((size_t)S * R * Kp * 2);
+  int* ex = reinterpret_cast<int*>(w);
+  w += align256((size_t)R * 4);
+  unsigned long long* rm = reinterpret_cast<unsigned long long*>(w);
+  cudaError_t e = cudaMemsetAsync(rm, 0, (size_t)R * 8, st);
+  if (e != cudaSuccess) return e;
+  const unsigned kb = (unsigned)((K + 255) / 256), kp64 = (unsigned)(Kp / BK);
+  rowmax_kernel<<<dim3((R + 31) / 32, kb), 256, 0, st>>>(R, K, X, rs, ks, rm, nullptr);
+  slice_kernel<<<dim3((R + 31) / 32, kp64), 256, 0, st>>>(R, K, Kp, X, rs, ks, rm, sl, ex, nullptr);
+  if (launches) *launches += 2;
+  out->s = sl;
+  out->e = ex;
+  out->rows = R;
+  out->K = K;
+  out->valid = true;
+  return cudaGetLastError();
+}
 
 // K is processed in host chunks small enough for `work` (each chunk's FP64 result is added to C).
 cudaError_t gemm_f64_tc(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
                         int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* work,
-                        size_t work_bytes, int* err, int flags, int64_t* launches, const int32_t* done) {
+                        size_t work_bytes, int* err, int flags, int64_t* launches, const int32_t* done,
+                        const TcSlices* cA, const TcSlices* cB) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (K < 0 || !work || !err) return cudaErrorInvalidValue;
+  // slices made earlier serve only a product over their whole K in one piece
+  if (cA && !(cA->valid && cA->rows == M && cA->K == K)) cA = nullptr;
+  if (cB && !(cB->valid && cB->rows == N && cB->K == K)) cB = nullptr;
   if (work_bytes >= tc_gemm_work_bytes(M, N, K))
     return gemm_f64_tc_one(st, tA, tB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, work, err, flags, launches,
-                           done);
+                           done, cA, cB);
   const size_t per_k = (size_t)S * (M + N) * 2;           // slice bytes per unit of K
   const size_t fixed = 256 + align256((size_t)M * 4) + align256((size_t)N * 4) + align256((size_t)M * 8) +
                        align256((size_t)N * 8) + align256(kPartElems * 8) + 512;
@@ -551,7 +602,8 @@ namespace {
 
 cudaError_t gemm_f64_tc_one(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
                             int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
-                            void* work, int* err, int flags, int64_t* launches, const int32_t* done) {
+                            void* work, int* err, int flags, int64_t* launches, const int32_t* done,
+                            const TcSlices* cA, const TcSlices* cB) {
   cudaError_t e = tc_prepare();
   if (e != cudaSuccess) return e;
   const int Kp = kpad_of(K > 0 ? K : 1);
@@ -576,12 +628,21 @@ cudaError_t gemm_f64_tc_one(cudaStream_t st, bool tA, bool tB, int M, int N, int
   if (e != cudaSuccess) return e;
   const int64_t ars = tA ? lda : 1, aks = tA ? 1 : lda, brs = tB ? 1 : ldb, bks = tB ? ldb : 1;
   const unsigned kb = (unsigned)((std::max(K, 1) + 255) / 256), kp64 = (unsigned)(Kp / BK);
-  // op(A) = op(B)^T (C = X^T X or X X^T): one operand, sliced once
+  // op(A) = op(B)^T (C = X^T X or X X^T): one operand, sliced once; operands sliced earlier
+  // (cA, cB) are used as they are
   const bool same = (A == B && M == N && ars == brs && aks == bks);
-  rowmax_kernel<<<dim3((M + 31) / 32, kb), 256, 0, st>>>(M, K, A, ars, aks, rmA, done);
-  slice_kernel<<<dim3((M + 31) / 32, kp64), 256, 0, st>>>(M, K, Kp, A, ars, aks, rmA, sa, ea, done);
-  if (launches) *launches += 2;
-  if (same) {
+  if (cA) {
+    sa = static_cast<__nv_bfloat16*>(cA->s);
+    ea = cA->e;
+  } else {
+    rowmax_kernel<<<dim3((M + 31) / 32, kb), 256, 0, st>>>(M, K, A, ars, aks, rmA, done);
+    slice_kernel<<<dim3((M + 31) / 32, kp64), 256, 0, st>>>(M, K, Kp, A, ars, aks, rmA, sa, ea, done);
+    if (launches) *launches += 2;
+  }
+  if (cB) {
+    sb = static_cast<__nv_bfloat16*>(cB->s);
+    eb = cB->e;
+  } else if (same) {
     sb = sa;
     eb = ea;
   } else {
