@@ -84,10 +84,12 @@ typedef enum {
                             reach the stop test, the FP64 PCG continues from the refined iterate
                             (its iterations count in pcg_iters).                              */
   SDP_MIXED_TF32 = 2,    /* as SDP_MIXED_FP32, with the n^3 products E Y E of the correction
-                            operator (DENSE kind) run on the tensor cores (tcgen05 kind::tf32:
-                            FP32 operands read as TF32, FP32 accumulation in TMEM); the passes
-                            over A stream its FP32 copy.  DIAG kind: the same as SDP_MIXED_FP32
-                            (its A E A^T block, (E o E) p_u, has no matrix product)          */
+                            operator (DENSE kind) run on the tensor cores (tcgen05 kind::tf32,
+                            FP32 accumulation in TMEM), each FP32 operand split into TF32 parts
+                            hi + lo and the product taken as hi hi + hi lo + lo hi (three MMAs
+                            per step, about FP32 accuracy); the passes over A stream its FP32
+                            copy.  DIAG kind: the same as SDP_MIXED_FP32 (its A E A^T block,
+                            (E o E) p_u, has no matrix product)                              */
   SDP_MIXED_BF16 = 3     /* as SDP_MIXED_FP32 with a BF16 copy of A (DENSE kind, 2 bytes per
                             entry, rows zero-padded to a multiple of 8 entries) or of E o E
                             (DIAG kind), BF16 products summed in FP32 in the passes, and E Y E
@@ -382,6 +384,22 @@ sdp_status sdp_newton_solve_host(sdp_handle* h, const double* V, const double* l
  * All arrays are device pointers.  Same status codes as sdp_newton_solve. */
 sdp_status sdp_grad(sdp_handle* h, const double* V, const double* lam, const double* gX, const double* gy,
                     double* gC, double* gb, sdp_newton_info* info);
+
+/* Vector-Jacobian product of the optimum of the robust form with slacks (Section 7, eq. rmc-sdp:
+ * min <C, X> + cv^T v + cw^T w  s.t.  A(X) + v - w = b, X PSD, v, w >= 0) with respect to its
+ * data (C, b, cv, cw), at the scaling point of a final iterate: W = V diag(lam) V^T for (X, S) and
+ * D = diag(d_v, d_w) with d_v = v / zv, d_w = w / zw for the orthant.  The linearised optimality
+ * conditions have the symmetric KKT matrix of (Newt-eps) with the linear block, so the cotangents
+ * of the data are one Newton solve with (C~, c~, b~) = (sym gX, (g_v, g_w), g_y): the linear
+ * block delta = d_v + d_w is set for the solve, b~ = g_y + d_v g_v - d_w g_w, and then
+ *   gC = dX,  gb = dy,  (gcv, gcw) = D (G^T dy - c~) = (d_v (dy - g_v), d_w (-dy - g_w)).
+ * The paper has no such product; it reuses its Newton system.  V, lam as for sdp_newton_solve;
+ * dv, dw, gy, gv, gw, gb, gcv, gcw: m (device); gX, gC: n x n (device).  DENSE_SVEC and SPARSE_COO
+ * kinds, FP64 form, PCG (as sdp_set_linear_diag); SDP_EUNSUPPORTED while the caller has a linear
+ * block set (it is set and removed by this call).  Same status codes as sdp_newton_solve. */
+sdp_status sdp_grad_slack(sdp_handle* h, const double* V, const double* lam, const double* dv, const double* dw,
+                          const double* gX, const double* gy, const double* gv, const double* gw, double* gC,
+                          double* gb, double* gcv, double* gcw, sdp_newton_info* info);
 
 /* Diagnostics: copy `count` doubles of an internal buffer of the most recent solve into the
  * device array `dst` (stream-ordered, synchronous).  which: 0 = E (n x n), 1 = D = tau^2 Sigma

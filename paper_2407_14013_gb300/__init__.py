@@ -22,8 +22,8 @@ KINDS = {"diag": SDP_A_DIAG, "sparse": SDP_A_SPARSE_COO, "dense": SDP_A_DENSE_SV
 PRECISIONS = {"fp64": SDP_FP64, "mixed_fp32": SDP_MIXED_FP32, "mixed_tf32": SDP_MIXED_TF32,
               "mixed_bf16": SDP_MIXED_BF16}
 # refinement defaults of the mixed forms: each correction solve is taken about as far as the
-# precision of its operator carries it (BF16 ~ 4e-3, TF32 ~ 5e-4, FP32 ~ 6e-8 relative)
-MIXED_DEFAULTS = {"mixed_fp32": (10, 1e-6), "mixed_tf32": (20, 1e-3), "mixed_bf16": (30, 1e-2)}
+# precision of its operator carries it (BF16 ~ 4e-3; split TF32 and FP32 ~ 1e-7 relative)
+MIXED_DEFAULTS = {"mixed_fp32": (10, 1e-6), "mixed_tf32": (10, 1e-6), "mixed_bf16": (30, 1e-2)}
 
 
 @dataclass
@@ -217,6 +217,24 @@ class NewtonSolver:
                              allow_notconv=allow_notconv)
         self.last_info = self._info(ci, st)
         return gC, gb
+
+    def grad_slack(self, V, lam, dv, dw, gX, gy, gv, gw, allow_notconv: bool = False):
+        """Cotangents (gC, gb, gcv, gcw) of the data of the robust form with slacks (eq. rmc-sdp)
+        for cotangents (gX, gy, gv, gw) of its optimum (X, y, v, w), at the scaling point
+        W = V diag(lam) V^T, d_v = v / zv, d_w = w / zw (sdp_grad_slack)."""
+        torch = self.torch
+        n, m = self.n, self.m
+        f64 = torch.float64
+        lam, dv, dw, gX, gy, gv, gw = (t.to(device=self.device, dtype=f64).contiguous()
+                                       for t in (lam, dv, dw, gX, gy, gv, gw))
+        V = _colmajor(V.to(device=self.device, dtype=f64))
+        gC = torch.empty((n, n), dtype=f64, device=self.device)
+        gb, gcv, gcw = (torch.empty(m, dtype=f64, device=self.device) for _ in range(3))
+        ci = native.sdp_newton_info()
+        st = native.sdp_grad_slack(self.handle, [_ptr(t) for t in (V, lam, dv, dw, gX, gy, gv, gw, gC, gb, gcv, gcw)],
+                                   ci, allow_notconv=allow_notconv)
+        self.last_info = self._info(ci, st)
+        return gC, gb, gcv, gcw
 
     def ipm_step(self, b, C, X, y, S):
         """One outer interior-point iteration in place on the device tensors X, y, S (ipm_step)."""

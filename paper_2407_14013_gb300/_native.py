@@ -66,6 +66,7 @@ EXPORTS = {
     "sdp_newton_solve": (c_int32, [c_void_p] + [c_void_p] * 7 + [POINTER(sdp_newton_info)]),
     "sdp_newton_solve_host": (c_int32, [c_void_p] + [c_void_p] * 7 + [POINTER(sdp_newton_info)]),
     "sdp_grad": (c_int32, [c_void_p] + [c_void_p] * 6 + [POINTER(sdp_newton_info)]),
+    "sdp_grad_slack": (c_int32, [c_void_p] + [c_void_p] * 12 + [POINTER(sdp_newton_info)]),
     "sdp_newton_resolve": (c_int32, [c_void_p] + [c_void_p] * 5 + [POINTER(sdp_newton_info)]),
     "sdp_eigh_work_elems": (c_int64, [c_int32]),
     "sdp_eigh": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_double, c_int32, c_void_p, c_int64,
@@ -151,6 +152,15 @@ def sdp_newton_solve_host(h: int, V: int, lam: int, Ct: int, bt: int, dX: int, d
 def sdp_newton_resolve(h: int, Ct: int, bt: int, dX: int, dy: int, dS: int, info: sdp_newton_info,
                        allow_notconv: bool = False) -> int:
     return _solve("sdp_newton_resolve", h, (Ct, bt, dX, dy, dS), info, allow_notconv)
+
+
+def sdp_grad_slack(h: int, ptrs, info: sdp_newton_info, allow_notconv: bool = False) -> int:
+    """sdp_grad_slack with ptrs = (V, lam, dv, dw, gX, gy, gv, gw, gC, gb, gcv, gcw) device pointers."""
+    lib = load()
+    st = lib.sdp_grad_slack(c_void_p(h), *[c_void_p(p) for p in ptrs], ctypes.byref(info))
+    if st != SDP_OK and not (allow_notconv and st == SDP_ENOTCONV):
+        raise SdpError(st, lib.sdp_last_error(c_void_p(h)).decode())
+    return st
 
 
 def sdp_grad(h: int, V: int, lam: int, gX: int, gy: int, gC: int, gb: int, info: sdp_newton_info,

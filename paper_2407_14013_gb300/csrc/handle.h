@@ -31,13 +31,15 @@ struct Space {
 
 // Low-precision data of the mixed forms' A E A^T block, plus their FP64 partial sums of B p_v,
 // B^T p_u.  FP32 form: FP32 copies and FFMA products; TF32 form: the same FP32 copy of A with the
-// n^3 products on the tensor cores (TF32 operands); BF16 form: a BF16 copy of A (or of E o E) and
+// n^3 products on the tensor cores (each FP32 operand as a TF32 pair hi + lo, three MMAs per step);
+// BF16 form: a BF16 copy of A (or of E o E) and
 // BF16 tensor-core products.  Every low-precision sum is accumulated in FP32.
 struct Mixed32 {
   float* A = nullptr;                          // FP32 copy of the svec rows (DENSE kind; FP32, TF32)
   void* A16 = nullptr;                         // BF16 copy of the svec rows, pitch Lp (BF16)
   void* EE16 = nullptr;                        // BF16 copy of E o E, pitch ldk (DIAG kind, BF16)
   void *Elp = nullptr, *Ylp = nullptr, *Glp = nullptr;   // tensor-core operands, n x n, pitch ldk
+  float *Elo = nullptr, *Ylo = nullptr, *Glo = nullptr;  // TF32 form: their FP32 remainders (hi + lo)
   float *E = nullptr, *EE = nullptr, *Y = nullptr, *F = nullptr, *Z = nullptr;
   float *zsvec = nullptr, *partY = nullptr, *partA = nullptr, *pu = nullptr;
   float* ws = nullptr;
@@ -125,6 +127,7 @@ struct sdp_handle {
   int64_t launches = 0;
   int space = 1, r = 0, d = 0;
   int refine_steps = 0, inner_iters = 0;
+  bool fuse = false;                // inside the PCG loop: update and p-update in the finishing kernels
   double refine_rate = 0.0, refine_rr0 = 0.0;   // mixed forms: contraction of the FP64 residual
   std::string err;
   // optional CUDA-event timing of the constraint-operator passes (sdp_set_profiling)

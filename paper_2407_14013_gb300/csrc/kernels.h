@@ -50,29 +50,34 @@ cudaError_t tc_prepare();
 cudaError_t tmap_2d(CUtensorMap* map, bool f32, const void* base, uint64_t inner, uint64_t rows, uint64_t pitch_bytes,
                     uint32_t box_inner, uint32_t box_rows);
 
-// ---- lp_gemm.cu: BF16 / TF32 tensor-core products with FP32 accumulation (mixed form) -----------
-// C (M x N, column-major, pitch ldc; FP32, or BF16 when out_bf16) = alpha op(A) op(B), op(A) given
-// by its rows and op(B) by its columns, both K-contiguous with pitches lda, ldb (elements; 16-byte
-// rows): C = A_s^T B_s for A_s (K x M) and B_s (K x N) column-major.  tf32: FP32 operands read as
-// TF32 (kind::tf32); else BF16 operands (kind::f16).  K >= 1; err as for gemm_f64_tc.
+// ---- lp_gemm.cu: BF16 / TF32 tensor-core products with FP32 accumulation (mixed forms) -----------
+// C (M x N, column-major, pitch ldc) = alpha op(A) op(B), op(A) given by its rows and op(B) by its
+// columns, both K-contiguous with pitches lda, ldb (elements; 16-byte rows): C = A_s^T B_s for
+// A_s (K x M) and B_s (K x N) column-major.  mode 0: BF16 operands (kind::f16); 1: FP32 operands
+// read as TF32 (kind::tf32); 2: FP32 operands given as TF32-exact (hi, lo) pairs (A, Alo), (B, Blo),
+// product hi hi + hi lo + lo hi (about FP32 accuracy).  out_mode 0: FP32 C; 1: BF16 C; 2: FP32 as
+// the pair (C, Clo) with C TF32-exact.  K >= 1; err as for gemm_f64_tc.
 cudaError_t lp_prepare();
-cudaError_t lp_gemm(cudaStream_t st, bool tf32, int M, int N, int K, float alpha, const void* A, int64_t lda,
-                    const void* B, int64_t ldb, void* C, int64_t ldc, bool out_bf16, int* err, int64_t* launches,
-                    const int32_t* done = nullptr);
+cudaError_t lp_gemm(cudaStream_t st, int mode, int M, int N, int K, float alpha, const void* A, const void* Alo,
+                    int64_t lda, const void* B, const void* Blo, int64_t ldb, void* C, void* Clo, int64_t ldc,
+                    int out_mode, int* err, int64_t* launches, const int32_t* done = nullptr);
 // Passes over a BF16 copy of the svec rows (m rows, pitch Lp, a multiple of 8, zero padded):
 // part[g * Lp + c] = sum_{i in group g} p_i a[i, c] (FP32), and out[i] = <a[i, :], z> (z FP32 of
-// length Lp, zero padded)
+// length Lp, zero padded), in column slabs
 int bf16_gemvT_groups(int m, int64_t Lp);
 void bf16_gemvT(cudaStream_t st, const void* A16, int m, int64_t Lp, const float* p, float* part, int groups,
                 const int32_t* done, int64_t* launches);
-void bf16_gemv(cudaStream_t st, const void* A16, int m, int64_t Lp, const float* z, float* out, const int32_t* done,
-               int64_t* launches);
-// Y (n x n, pitch ldk, BF16 or FP32, both triangles) = smat(sum_g part[g * Lp + .])
-void lp_unpack(cudaStream_t st, int n, const float* part, int groups, int64_t Lp, void* Y, int ldk, bool bf16,
+int bf16_gemv_slabs(int m, int64_t Lp);   // column slabs of the A pass: out holds slabs x m partial sums
+void bf16_gemv(cudaStream_t st, const void* A16, int m, int64_t Lp, const float* z, float* out, int slabs,
                const int32_t* done, int64_t* launches);
-// X (rows x cols FP64, pitch ldx) -> Y (BF16 or FP32, pitch ldy); columns cols .. ldy-1 of Y are zeroed
+// Y (n x n, pitch ldk, BF16 or FP32, both triangles) = smat(sum_g part[g * Lp + .]); with Ylo (FP32)
+// Y is written as the pair (TF32-exact hi, FP32 remainder)
+void lp_unpack(cudaStream_t st, int n, const float* part, int groups, int64_t Lp, void* Y, int ldk, bool bf16,
+               float* Ylo, const int32_t* done, int64_t* launches);
+// X (rows x cols FP64, pitch ldx) -> Y (BF16 or FP32, pitch ldy); columns cols .. ldy-1 of Y are zeroed;
+// with Ylo (FP32) as the pair (TF32-exact hi, FP32 remainder)
 void lp_convert(cudaStream_t st, int rows, int cols, const double* X, int64_t ldx, void* Y, int64_t ldy, bool bf16,
-                int64_t* launches);
+                float* Ylo, int64_t* launches);
 cudaError_t gemm_f64_tc(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
                         int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* work,
                         size_t work_bytes, int* err, int flags, int64_t* launches, const int32_t* done = nullptr,
@@ -180,6 +185,10 @@ void h_pack_rows_diag(cudaStream_t st, int n, int r, const double* Vs, double* B
 // false when n r is too large for the shared-memory accumulators.
 bool dense_AiQ(cudaStream_t st, const double* A, int n, int i0, int mb, int r, const double* Q, double* G,
                int64_t* launches);
+// The same from the integer digits of the rows (fx_split_rows) on the integer pipe; false when
+// the row does not fit in shared memory or n > 1024 (then use dense_AiQ).
+bool fx_AiQ(cudaStream_t st, const int2* Ad, const int* ea, int n, int64_t Lp, int i0, int mb, int r, const double* Q,
+            double* G, int64_t* launches);
 
 // ---- gemm_f32.cu: FP32 GEMM (FFMA tiles, FP32 accumulation), same conventions as gemm_f64 ----
 cudaError_t gemm_f32(cudaStream_t st, bool tA, bool tB, int M, int N, int K, float alpha,

@@ -40,6 +40,7 @@ static std::string g_setup_err;
 // products go to the tensor cores for n >= kTcMin and M N K >= kTcMinWork (all three >= 64)
 constexpr int kTcMin = 512;
 constexpr double kTcMinWork = 134217728.0;   // 512^3
+constexpr int kFuseMax = 65536;              // PCG vectors short enough for one block's update
 
 static sdp_status fail(sdp_handle* h, sdp_status s, const std::string& msg) {
   if (h) h->err = msg; else g_setup_err = msg;
@@ -166,14 +167,19 @@ void carve_mixed(sdp_handle* h, Carver& c, Mixed32& M) {
       M.Elp = c.take<char>(n * M.ldk * esz);
       M.Ylp = c.take<char>(n * M.ldk * esz);
       M.Glp = c.take<char>(n * M.ldk * esz);
+      if (!bf) {                                   // TF32: the FP32 remainders of (hi, lo) pairs
+        M.Elo = c.take<float>(n * M.ldk);
+        M.Ylo = c.take<float>(n * M.ldk);
+        M.Glo = c.take<float>(n * M.ldk);
+      }
     }
     M.Z = c.take<float>(nn);
     M.zsvec = c.take<float>(M.Lp);                 // the tail beyond n(n+1)/2 stays zero
-    M.partA = c.take<float>(rows_gemv_part_elems(m, h->N));
+    M.partA = c.take<float>(std::max(rows_gemv_part_elems(m, h->N), (size_t)16 * m));
   } else {
     if (bf) M.EE16 = c.take<char>(n * M.ldk * 2);
     else M.EE = c.take<float>(nn);
-    M.partA = c.take<float>(rows_gemv_part_elems(n, n));
+    M.partA = c.take<float>(std::max(rows_gemv_part_elems(n, n), (size_t)16 * n));
   }
   M.pu = c.take<float>(std::max(m, (size_t)M.ldk));   // zero tail: the BF16 GEMV over E o E reads ldk
   M.ws_elems = 4 * nn;
@@ -504,7 +510,7 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
       return fail(nullptr, SDP_EINVAL, "A has a zero or non-finite Frobenius norm");
     }
     if (h->mixed && h->lp == SDP_MIXED_BF16)   // BF16 rows, zero padded to a 16-byte pitch
-      lp_convert(h->st, m, (int)h->N, h->a_dense, h->N, h->m32.A16, h->m32.Lp, true, &h->launches);
+      lp_convert(h->st, m, (int)h->N, h->a_dense, h->N, h->m32.A16, h->m32.Lp, true, nullptr, &h->launches);
     else if (h->mixed)
       convert<float, double>(h->st, (int64_t)m * h->N, h->a_dense, h->m32.A, &h->launches);
     if (h->fx) fx_split_rows(h->st, h->a_dense, m, h->N, h->a_fx, h->a_fx_e, &h->launches);
@@ -678,7 +684,8 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
     join(h, 1, 3);
     CU(pack_apply_dense(h, S, st, r, S.Up, Q, done, L));               // A(svec(E Y E + sym(Up Q^T)))
     launch_ap_finish<double>(st, m, d, n, r, S.partA, h->SA, nullptr, S.Vs, S.H, S.Dv, pin, gsub, out, mode, S.ctl,
-                             h->dotbuf, h->counter, L, nullptr, 0, h->lin);   // + tau^-2 delta p_u
+                             h->dotbuf, h->counter, L, nullptr, 0, h->lin,   // + tau^-2 delta p_u
+                             h->fuse ? S.x : nullptr, S.rv);
   } else if (h->kind == SDP_A_SPARSE_COO) {
     // Y = A^T(p_u) kept as its pattern values; E Y E only at the pattern positions
     sparse_posval(st, h->sp, pu, S.ypos, done, L);
@@ -692,14 +699,16 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
     join(h, 1, 3);
     sparse_apply_pos(st, h->sp, n, m, r, S.zpos, S.Up, Q, S.partA, done, L);   // A(E Y E + sym(Up Q^T))
     launch_ap_finish<double>(st, m, d, n, r, S.partA, 1, nullptr, S.Vs, S.H, S.Dv, pin, gsub, out, mode, S.ctl,
-                             h->dotbuf, h->counter, L, nullptr, 0, h->lin);   // + tau^-2 delta p_u
+                             h->dotbuf, h->counter, L, nullptr, 0, h->lin,   // + tau^-2 delta p_u
+                             h->fuse ? S.x : nullptr, S.rv);
   } else {
     launch_diag_scale_rows<double>(st, n, r, pu, S.Vs, S.Tm, done, L);  // A^T(p_u) Q = diag(p_u) Q
     CU(gemm_big(h, st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, 0, done));
     rows_gemv<double>(st, S.EE, n, n, pu, S.partA, done, L);              // diag(E diag(p_u) E) = (E o E) p_u
     join(h, 0, 2);
     launch_ap_finish<double>(st, m, d, n, r, S.partA, rows_gemv_slabs(n, n), S.Up, S.Vs, S.H, S.Dv, pin, gsub, out,
-                             mode, S.ctl, h->dotbuf, h->counter, L);
+                             mode, S.ctl, h->dotbuf, h->counter, L, nullptr, 0, nullptr,
+                             h->fuse ? S.x : nullptr, S.rv);
   }
   return SDP_OK;
 }
@@ -727,8 +736,8 @@ sdp_status apply_operator_mixed(sdp_handle* h, Space& S, const double* pin, doub
     launch_to_float(st, m, pu, M.pu, done, L);
     int S32;
     if (M.EE16) {                                                            // (E o E) p_u, BF16 copy
-      bf16_gemv(st, M.EE16, n, M.ldk, M.pu, M.partA, done, L);
-      S32 = 1;
+      S32 = bf16_gemv_slabs(n, M.ldk);
+      bf16_gemv(st, M.EE16, n, M.ldk, M.pu, M.partA, S32, done, L);
     } else {                                                                 // (E o E) p_u, FP32 copy
       rows_gemv<float>(st, M.EE, n, n, M.pu, M.partA, done, L);
       S32 = rows_gemv_slabs(n, n, 4);
@@ -737,7 +746,8 @@ sdp_status apply_operator_mixed(sdp_handle* h, Space& S, const double* pin, doub
     CU(gemm_big(h, st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, 0, done));
     join(h, 0, 2);
     launch_ap_finish<double>(st, m, d, n, r, nullptr, 0, S.Up, S.Vs, S.H, S.Dv, pin, gsub, out, mode, S.ctl,
-                             h->dotbuf, h->counter, L, M.partA, S32);
+                             h->dotbuf, h->counter, L, M.partA, S32, nullptr,
+                             h->fuse ? S.x : nullptr, S.rv);
     return SDP_OK;
   }
   // side branch: the FP64 rows with B, beside the FP32 A E A^T chain on the main stream
@@ -768,15 +778,19 @@ sdp_status apply_operator_mixed(sdp_handle* h, Space& S, const double* pin, doub
     if (bf) bf16_gemvT(st, M.A16, m, M.Lp, M.pu, M.partY, M.G16, done, L);
     else rows_gemvT<float>(st, M.A, m, h->N, M.pu, M.partY, h->GY32, done, L);
     prof_end(h);
-    lp_unpack(st, n, M.partY, bf ? M.G16 : h->GY32, bf ? M.Lp : h->N, M.Ylp, M.ldk, bf, done, L);
-    // K runs over the whole pitch: the entries n .. ldk - 1 of every operand column are zero
-    CU(lp_gemm(st, !bf, n, n, M.ldk, 1.f, M.Ylp, M.ldk, M.Elp, M.ldk, M.Glp, M.ldk, bf, M.err, L, done));   // G = Y E
-    CU(lp_gemm(st, !bf, n, n, M.ldk, 1.f, M.Elp, M.ldk, M.Glp, M.ldk, M.Z, n, false, M.err, L, done));      // Z = E G
+    lp_unpack(st, n, M.partY, bf ? M.G16 : h->GY32, bf ? M.Lp : h->N, M.Ylp, M.ldk, bf, M.Ylo, done, L);
+    // K runs over the whole pitch: the entries n .. ldk - 1 of every operand column are zero.
+    // BF16: one kind::f16 product each; TF32: (hi, lo) operand pairs, three kind::tf32 MMAs a step
+    const int mode = bf ? 0 : 2;
+    CU(lp_gemm(st, mode, n, n, M.ldk, 1.f, M.Ylp, M.Ylo, M.ldk, M.Elp, M.Elo, M.ldk, M.Glp, M.Glo, M.ldk,
+               bf ? 1 : 2, M.err, L, done));                                                          // G = Y E
+    CU(lp_gemm(st, mode, n, n, M.ldk, 1.f, M.Elp, M.Elo, M.ldk, M.Glp, M.Glo, M.ldk, M.Z, nullptr, n, 0, M.err,
+               L, done));                                                                              // Z = E G
     svec_pack_plus<float>(st, n, 0, M.Z, nullptr, nullptr, M.zsvec, done, L);
     prof_begin(h, 3);
     if (bf) {
-      bf16_gemv(st, M.A16, m, M.Lp, M.zsvec, M.partA, done, L);              // A(E Y E)
-      SA = 1;
+      SA = bf16_gemv_slabs(m, M.Lp);
+      bf16_gemv(st, M.A16, m, M.Lp, M.zsvec, M.partA, SA, done, L);          // A(E Y E)
     } else {
       rows_gemv<float>(st, M.A, m, h->N, M.zsvec, M.partA, done, L);
       SA = h->SA32;
@@ -788,7 +802,7 @@ sdp_status apply_operator_mixed(sdp_handle* h, Space& S, const double* pin, doub
   }
   join(h, 0, 2);
   launch_mixed_finish(st, m, d, M.partA, SA, M.partBv, rows_gemv_slabs(m, d), M.partBu, rows_gemv_slabs(d, m), S.Dv, pin,
-                      gsub, out, mode, S.ctl, h->dotbuf, h->counter, L);
+                      gsub, out, mode, S.ctl, h->dotbuf, h->counter, L, h->fuse ? S.x : nullptr, S.rv);
   return SDP_OK;
 }
 
@@ -821,7 +835,7 @@ sdp_status apply_precond(sdp_handle* h, Space& S, const double* rin, double* zou
       CU(gemm_big(h, st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, S.ws_elems, L, 0, done));
       sparse_apply_pos(st, h->sp, n, m, r, nullptr, S.Up, Q, S.partA, done, L);  // B z_v
       launch_pc_zu_dot<double>(st, m, d, 1, S.partA, 1, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L,
-                               h->lin ? h->lin_lam : nullptr);
+                               h->lin ? h->lin_lam : nullptr, h->fuse ? S.p : nullptr);
     } else {
       h_unpack<double>(st, n, r, rin + m, S.Hp, done, L, S.Dv);            // unpack(D^{-1} r_v)
       CU(gemm_big(h, st, false, false, n, r, n, 1.0, S.Vs, n, S.Hp, n, 0.0, S.Up, n, S.ws, S.ws_elems, L, 0, done));
@@ -833,7 +847,7 @@ sdp_status apply_precond(sdp_handle* h, Space& S, const double* rin, double* zou
       sparse_sym_spmm(st, h->sp, n, r, S.ypos, Q, n, S.Tm, n, done, L);
       CU(gemm_big(h, st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, 0, done));
       launch_diag_zv(st, m, d, n, r, S.H, rin, S.Dv, zout, S.ctl, L);      // z_v = D^{-1}(B^T z_u - r_v)
-      launch_pc_zu_dot<double>(st, m, d, 0, nullptr, 2, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L);
+      launch_pc_zu_dot<double>(st, m, d, 0, nullptr, 2, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L, nullptr, h->fuse ? S.p : nullptr);
     }
   } else if (h->space == 1) {
     if (h->lin) {   // linear block: s = r_v - B^T (Lam^{-1} r_u), z_u = Lam^{-1}(r_u - B z_v)
@@ -849,7 +863,7 @@ sdp_status apply_precond(sdp_handle* h, Space& S, const double* rin, double* zou
     rows_gemv_formed(st, S.B, m, d, nullptr, S.partC, rows_gemv_slabs(d, d), -1.0, nullptr, zout + m, S.partA, done,
                      L);
     launch_pc_zu_dot<double>(st, m, d, rows_gemv_slabs(m, d), S.partA, 1, rin, zout, mode, S.ctl, h->dotbuf,
-                             h->counter, L, h->lin ? h->lin_lam : nullptr);
+                             h->counter, L, h->lin ? h->lin_lam : nullptr, h->fuse ? S.p : nullptr);
   } else if (h->kind == SDP_A_DIAG) {
     // the products with B from Vs: B t = rowdot(Vs unpack(t), Q), B^T u = pack(Vs^T diag(u) Q)
     const int n = h->n, r = h->r;
@@ -862,7 +876,7 @@ sdp_status apply_precond(sdp_handle* h, Space& S, const double* rin, double* zou
     launch_diag_scale_rows<double>(st, n, r, zout, S.Vs, S.Tm, done, L);  // diag(z_u) Q
     CU(gemm_big(h, st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, 0, done));
     launch_diag_zv(st, m, d, n, r, S.H, rin, S.Dv, zout, S.ctl, L);        // z_v = D^{-1}(B^T z_u - r_v)
-    launch_pc_zu_dot<double>(st, m, d, 0, nullptr, 2, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L);
+    launch_pc_zu_dot<double>(st, m, d, 0, nullptr, 2, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L, nullptr, h->fuse ? S.p : nullptr);
   } else {
     launch_pc_m_tv<double>(st, m, d, rin, S.Dv, S.sd, S.ctl, L);           // t = D^{-1} r_v
     rows_gemv<double>(st, S.B, m, d, S.sd, S.partA, done, L);              // B t
@@ -871,7 +885,7 @@ sdp_status apply_precond(sdp_handle* h, Space& S, const double* rin, double* zou
     launch_pc_m_w<double>(st, m, rows_gemv_slabs(m, m), S.partC, nullptr, zout, S.ctl, L);  // z_u
     rows_gemv<double>(st, S.Bt, d, m, zout, S.partBt, done, L);            // B^T z_u (rows of B^T)
     launch_pc_m_zv<double>(st, m, d, Sm, S.partBt, rin, S.Dv, zout, S.ctl, L);  // z_v = D^{-1}(B^T z_u - r_v)
-    launch_pc_zu_dot<double>(st, m, d, 0, nullptr, 2, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L);
+    launch_pc_zu_dot<double>(st, m, d, 0, nullptr, 2, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L, nullptr, h->fuse ? S.p : nullptr);
   }
   return SDP_OK;
 }
@@ -894,6 +908,9 @@ sdp_status krylov_loop(sdp_handle* h, Space& S, bool mixed, bool minres) {
   const int every = h->opt.check_every;
   const int nt = h->m + h->d;
   Graph& G = h->graph[minres ? 2 : mixed ? 1 : 0];
+  // short vectors: the PCG update and p = z + beta p run in the last block of the operator's and
+  // the preconditioner's finishing kernels (two launches fewer per iteration)
+  h->fuse = !minres && nt <= kFuseMax;
   int64_t* L = &h->launches;
   cudaStream_t st = h->st;
   CU(cudaMemcpyAsync(h->ctl_host, S.ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
@@ -921,10 +938,10 @@ sdp_status krylov_loop(sdp_handle* h, Space& S, bool mixed, bool minres) {
       }
       sdp_status s = apply_op(h, S, mixed, S.p, S.Ap, nullptr, 1);
       if (s != SDP_OK) { h->st = saved; return s; }
-      launch_update<double>(s_, nt, S.x, S.rv, S.p, S.Ap, S.ctl, h->dotbuf, h->counter, L);
+      if (!h->fuse) launch_update<double>(s_, nt, S.x, S.rv, S.p, S.Ap, S.ctl, h->dotbuf, h->counter, L);
       s = apply_precond(h, S, S.rv, S.z, 1);
       if (s != SDP_OK) { h->st = saved; return s; }
-      launch_p_update<double>(s_, nt, S.z, S.p, 0, S.ctl, L);
+      if (!h->fuse) launch_p_update<double>(s_, nt, S.z, S.p, 0, S.ctl, L);
     }
     h->st = saved;
     h->cur_iter = -1;
@@ -978,6 +995,7 @@ sdp_status krylov_loop(sdp_handle* h, Space& S, bool mixed, bool minres) {
     }
     base += every;
   }
+  h->fuse = false;
   // later profiled launches take events after the ones the graph records into
   h->prof_entries.assign(h->opt.use_graph ? G.prof_last : 0, ProfEntry{0, 0});
   h->prof_base = h->prof_entries.size();
@@ -1021,6 +1039,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     CU(cudaEventRecord(h->ev_phase[1], st));
   }
   int r = h->r, d = h->d;
+  bool rhs_side = false;   // the right side's products run beside the preconditioner setup
   if (!reuse) {
   h->setup_valid = false;
   // ---- a1: split ----
@@ -1051,6 +1070,21 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   lower_to_full(st, n, S.E, L);
   split_sigma(st, n, r, h->lam_s, h->ctl, S.Dv, L);
 
+  // ---- a3 products on a side stream, beside a2 (DENSE kind, FP64 MMA products): the right side
+  // needs E, Q and D only, and the factorisation of a2 is a chain of small launches that leaves
+  // most of the GPU idle.  The finishing kernel (which reads the factorisation's status) stays on
+  // the handle's stream after the join.
+  rhs_side = !h->prof && h->kind == SDP_A_DENSE_SVEC && n < kTcMin && h->opt.krylov != 1;
+  if (rhs_side) {
+    cudaStream_t s0 = fork(h, 0, 4);
+    CU(gemm_big(h, s0, false, false, n, n, n, 1.0, S.E, n, Ct, n, 0.0, S.F, n, h->ws_b[0], h->ws_b_elems, L));
+    CU(gemm_big(h, s0, false, false, n, r, n, 1.0, Ct, n, S.Vs, n, 0.0, S.Tm, n, h->ws_b[0], h->ws_b_elems, L));
+    CU(gemm_big(h, s0, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, h->ws_b[0], h->ws_b_elems, L));
+    CU(gemm_big(h, s0, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, h->ws_b[0], h->ws_b_elems, L,
+                GEMM_LOWER));
+    CU(pack_apply_dense(h, S, s0, r, nullptr, nullptr, nullptr, L));
+  }
+
   // ---- a2: B = A Q and the preconditioner core (MINRES: only E o E of the DIAG operator) ----
   if (h->opt.krylov == 1) {
     if (h->kind == SDP_A_DIAG) launch_hadamard_sq(st, (int64_t)n * n, S.E, S.EE, L);
@@ -1060,7 +1094,8 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     bool direct = true;
     for (int i0 = 0; i0 < m && direct; i0 += h->mb2) {
       const int mb = std::min(h->mb2, m - i0);
-      direct = dense_AiQ(st, h->a_dense, n, i0, mb, r, S.Vs, h->Gb, L);
+      direct = (h->fx && fx_AiQ(st, h->a_fx, h->a_fx_e, n, fx_row_len(h->N), i0, mb, r, S.Vs, h->Gb, L)) ||
+               dense_AiQ(st, h->a_dense, n, i0, mb, r, S.Vs, h->Gb, L);
       if (!direct) break;
       CU(gemm_big(h, st, true, false, n, mb * r, n, 1.0, S.Vs, n, h->Gb, n, 0.0, h->Hb, n, S.ws, ws, L));
       h_pack_rows(st, n, r, mb, i0, h->Hb, S.B, d, S.Bt, m, L);
@@ -1122,9 +1157,9 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   }
   if (h->mixed) {   // low-precision copies for the A E A^T block of the mixed operator
     Mixed32& M = h->m32;
-    if (S.EE && M.EE16) lp_convert(st, n, n, S.EE, n, M.EE16, M.ldk, true, L);
+    if (S.EE && M.EE16) lp_convert(st, n, n, S.EE, n, M.EE16, M.ldk, true, nullptr, L);
     else if (S.EE) convert<float, double>(st, (int64_t)n * n, S.EE, M.EE, L);
-    else if (M.Elp) lp_convert(st, n, n, S.E, n, M.Elp, M.ldk, h->lp == SDP_MIXED_BF16, L);
+    else if (M.Elp) lp_convert(st, n, n, S.E, n, M.Elp, M.ldk, h->lp == SDP_MIXED_BF16, M.Elo, L);
     else convert<float, double>(st, (int64_t)n * n, S.E, M.E, L);
   }
   CU(cudaEventRecord(h->ev_phase[1], st));
@@ -1134,12 +1169,18 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
 
   // ---- a3: right-hand side and start ----
   const double* Q = S.Vs;
-  CU(gemm_big(h, st, false, false, n, n, n, 1.0, S.E, n, Ct, n, 0.0, S.F, n, S.ws, ws, L));
-  CU(gemm_big(h, st, false, false, n, r, n, 1.0, Ct, n, Q, n, 0.0, S.Tm, n, S.ws, ws, L));
-  CU(gemm_big(h, st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, ws, L));
+  if (rhs_side) {
+    join(h, 0, 5);
+  } else {
+    CU(gemm_big(h, st, false, false, n, n, n, 1.0, S.E, n, Ct, n, 0.0, S.F, n, S.ws, ws, L));
+    CU(gemm_big(h, st, false, false, n, r, n, 1.0, Ct, n, Q, n, 0.0, S.Tm, n, S.ws, ws, L));
+    CU(gemm_big(h, st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, ws, L));
+  }
   if (h->kind == SDP_A_DENSE_SVEC) {
-    CU(gemm_big(h, st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, ws, L, GEMM_LOWER));
-    CU(pack_apply_dense(h, S, st, r, nullptr, nullptr, nullptr, L));
+    if (!rhs_side) {
+      CU(gemm_big(h, st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, ws, L, GEMM_LOWER));
+      CU(pack_apply_dense(h, S, st, r, nullptr, nullptr, nullptr, L));
+    }
     launch_rhs_finish(st, m, d, n, r, S.partA, h->SA, nullptr, nullptr, bt, Ct, S.H, S.Dv, h->g, S.x,
                       h->opt.newton_rtol, h->ctl, h->dotbuf, h->counter, L);
   } else if (h->kind == SDP_A_SPARSE_COO) {
@@ -1351,6 +1392,31 @@ extern "C" sdp_status sdp_grad(sdp_handle* h, const double* V, const double* lam
   launch_sym_copy(h->st, h->n, gX, h->hCt, &h->launches);
   CU(cudaGetLastError());
   return sdp_newton_solve(h, V, lam, h->hCt, gy, gC, gb, h->hdS, info);
+}
+
+extern "C" sdp_status sdp_grad_slack(sdp_handle* h, const double* V, const double* lam, const double* dv,
+                                     const double* dw, const double* gX, const double* gy, const double* gv,
+                                     const double* gw, double* gC, double* gb, double* gcv, double* gcw,
+                                     sdp_newton_info* info) {
+  if (!h) return fail(nullptr, SDP_EINVAL, "NULL handle");
+  if (!V || !lam || !dv || !dw || !gX || !gy || !gv || !gw || !gC || !gb || !gcv || !gcw)
+    return fail(h, SDP_EINVAL, "NULL array argument");
+  if (h->lin) return fail(h, SDP_EUNSUPPORTED, "remove the caller's linear block first");
+  // staging buffers of the host entry point: hdy = delta, hbt = b~, hCt = sym gX, hdS = the unused dS
+  launch_slack_grad_rhs(h->st, h->m, dv, dw, gy, gv, gw, h->hdy, h->hbt, &h->launches);
+  launch_sym_copy(h->st, h->n, gX, h->hCt, &h->launches);
+  CU(cudaGetLastError());
+  sdp_status s = sdp_set_linear_diag(h, h->hdy);
+  if (s != SDP_OK) return s;
+  s = newton_solve_impl(h, V, lam, h->hCt, h->hbt, gC, gb, h->hdS, info, false);
+  const std::string err = h->err;
+  sdp_set_linear_diag(h, nullptr);   // the handle is left as the caller set it up
+  h->err = err;
+  if (s != SDP_OK && s != SDP_ENOTCONV) return s;
+  launch_slack_grad_out(h->st, h->m, dv, dw, gb, gv, gw, gcv, gcw, &h->launches);   // dx = D(G^T dy - c~)
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(h->st));
+  return s;
 }
 
 extern "C" sdp_status sdp_debug_copy(sdp_handle* h, int32_t which, double* dst, int64_t count) {

@@ -35,6 +35,31 @@ __device__ __forceinline__ double sum_partials(const double* part, int nb, doubl
   return block_sum(s, sh);
 }
 
+// The PCG update x += alpha p, r -= alpha Ap, ||r||^2 and the stop test (update_kernel's work),
+// done by the one block that finished a reduction last, when the vectors are short enough for
+// one block (saves a launch per iteration).  Every thread of the block calls it.
+__device__ void update_tail(int nt, double* __restrict__ x, double* __restrict__ rv, const double* __restrict__ p,
+                            const double* __restrict__ Ap, PcgCtl* __restrict__ ctl, double* sh) {
+  __syncthreads();
+  if (ctl->done) return;                   // uniform: written before the barrier
+  const double alpha = ctl->alpha;
+  double acc = 0.0;
+  for (int q = threadIdx.x; q < nt; q += blockDim.x) {
+    x[q] = fma(alpha, p[q], x[q]);
+    const double rr = fma(-alpha, __ldcg(Ap + q), rv[q]);   // Ap: written by the other blocks
+    rv[q] = rr;
+    acc = fma(rr, rr, acc);
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    ctl->rr = acc;
+    ctl->iters += 1;
+    if (!isfinite(acc)) { ctl->status = 5; ctl->done = 1; }
+    else if (acc <= ctl->tol2) { ctl->status = 0; ctl->done = 1; }
+    else if (ctl->iters >= ctl->max_iters) { ctl->status = 4; ctl->done = 1; }
+  }
+}
+
 // out = [u_src; pack(H) - D p_v] (optionally g - that), and in mode 1 the dot <p, out> -> alpha.
 template <typename T>
 __global__ void __launch_bounds__(VT)
@@ -42,7 +67,8 @@ ap_finish_kernel(int m, int d, int n, int r, const T* __restrict__ partA, int S,
                  const T* __restrict__ Vs, const T* __restrict__ H, const T* __restrict__ Dv,
                  const T* __restrict__ p, const T* __restrict__ g, T* __restrict__ out, int mode,
                  PcgCtl* __restrict__ ctl, double* __restrict__ dotbuf, unsigned int* __restrict__ counter,
-                 const float* __restrict__ partA32, int S32, const double* __restrict__ lin) {
+                 const float* __restrict__ partA32, int S32, const double* __restrict__ lin,
+                 double* __restrict__ ux, double* __restrict__ ur) {
   if (ctl->done) return;
   __shared__ double sh[32];
   const int nt = m + d;
@@ -83,6 +109,7 @@ ap_finish_kernel(int m, int d, int n, int r, const T* __restrict__ partA, int S,
         ctl->alpha = ctl->rz / pAp;
       }
     }
+    if (ux) update_tail(nt, ux, ur, reinterpret_cast<const double*>(p), reinterpret_cast<const double*>(out), ctl, sh);
   }
 }
 
@@ -147,7 +174,7 @@ template <typename T>
 __global__ void __launch_bounds__(VT)
 pc_zu_dot_kernel(int m, int d, int S, const T* __restrict__ partU, int space, const T* __restrict__ rv,
                  T* __restrict__ z, int mode, PcgCtl* __restrict__ ctl, double* __restrict__ dotbuf,
-                 unsigned int* __restrict__ counter, const double* __restrict__ lam) {
+                 unsigned int* __restrict__ counter, const double* __restrict__ lam, T* __restrict__ pf) {
   if (ctl->done) return;
   __shared__ double sh[32];
   const int nt = m + d;
@@ -174,6 +201,12 @@ pc_zu_dot_kernel(int m, int d, int S, const T* __restrict__ partU, int space, co
       if (!isfinite(rz)) { ctl->status = 5; ctl->done = 1; }
       if (mode == 0) { ctl->rz = rz; ctl->beta = 0.0; }
       else { ctl->rz_new = rz; ctl->beta = rz / ctl->rz; ctl->rz = rz; }
+    }
+    if (pf && mode == 1) {   // p = z + beta p in this block (p_update_kernel's work, one launch fewer)
+      __syncthreads();
+      if (ctl->done) return;
+      const double beta = ctl->beta;
+      for (int q = threadIdx.x; q < nt; q += blockDim.x) pf[q] = (T)fma(beta, (double)pf[q], (double)__ldcg(z + q));
     }
   }
 }
@@ -646,7 +679,8 @@ __global__ void __launch_bounds__(VT)
 mixed_finish_kernel(int m, int d, const float* __restrict__ partA32, int SA, const double* __restrict__ partBv,
                     int SB, const double* __restrict__ partBu, int SBu, const double* __restrict__ Dv,
                     const double* __restrict__ p, const double* __restrict__ g, double* __restrict__ out, int mode,
-                    PcgCtl* __restrict__ ctl, double* __restrict__ dotbuf, unsigned int* __restrict__ counter) {
+                    PcgCtl* __restrict__ ctl, double* __restrict__ dotbuf, unsigned int* __restrict__ counter,
+                    double* __restrict__ ux, double* __restrict__ ur) {
   if (ctl->done) return;
   __shared__ double sh[32];
   const int nt = m + d;
@@ -680,6 +714,7 @@ mixed_finish_kernel(int m, int d, const float* __restrict__ partA32, int SA, con
         ctl->alpha = ctl->rz / pAp;
       }
     }
+    if (ux) update_tail(nt, ux, ur, p, out, ctl, sh);
   }
 }
 
@@ -708,15 +743,38 @@ inline int vec_blocks(int nt) {
   return b > 256 ? 256 : b;
 }
 
+// The adjoint with the slacks of eq. rmc-sdp (G = [I, -I], D = diag(d_v, d_w)): delta = d_v + d_w,
+// b~ = g_y + G D c~ with c~ = (g_v, g_w); afterwards dx = D(G^T dy - c~).
+__global__ void slack_grad_rhs_kernel(int m, const double* __restrict__ dv, const double* __restrict__ dw,
+                                      const double* __restrict__ gy, const double* __restrict__ gv,
+                                      const double* __restrict__ gw, double* __restrict__ delta,
+                                      double* __restrict__ bt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  delta[i] = dv[i] + dw[i];
+  bt[i] = gy[i] + dv[i] * gv[i] - dw[i] * gw[i];
+}
+
+__global__ void slack_grad_out_kernel(int m, const double* __restrict__ dv, const double* __restrict__ dw,
+                                      const double* __restrict__ dy, const double* __restrict__ gv,
+                                      const double* __restrict__ gw, double* __restrict__ ov,
+                                      double* __restrict__ ow) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  ov[i] = dv[i] * (dy[i] - gv[i]);
+  ow[i] = dw[i] * (-dy[i] - gw[i]);
+}
+
 }  // namespace
 
 template <typename T>
 void launch_ap_finish(cudaStream_t st, int m, int d, int n, int r, const T* partA, int S, const T* Up, const T* Vs,
                       const T* H, const T* Dv, const T* p, const T* g, T* out, int mode, PcgCtl* ctl,
                       double* dotbuf, unsigned int* counter, int64_t* launches, const float* partA32, int S32,
-                      const double* lin) {
+                      const double* lin, double* ux, double* ur) {
   ap_finish_kernel<T><<<vec_blocks(m + d), VT, 0, st>>>(m, d, n, r, partA, S, Up, Vs, H, Dv, p, g, out, mode, ctl,
-                                                       dotbuf, counter, partA32, S32, lin);
+                                                       dotbuf, counter, partA32, S32, lin, mode == 1 ? ux : nullptr,
+                                                       ur);
   ++*launches;
 }
 
@@ -743,9 +801,10 @@ void launch_pc_d_zv(cudaStream_t st, int m, int d, int S, const T* partC, T* z, 
 
 template <typename T>
 void launch_pc_zu_dot(cudaStream_t st, int m, int d, int S, const T* partU, int space, const T* rv, T* z, int mode,
-                      PcgCtl* ctl, double* dotbuf, unsigned int* counter, int64_t* launches, const double* lam) {
+                      PcgCtl* ctl, double* dotbuf, unsigned int* counter, int64_t* launches, const double* lam,
+                      T* pf) {
   pc_zu_dot_kernel<T><<<vec_blocks(m + d), VT, 0, st>>>(m, d, S, partU, space, rv, z, mode, ctl, dotbuf, counter,
-                                                       lam);
+                                                       lam, pf);
   ++*launches;
 }
 
@@ -793,13 +852,13 @@ void launch_diag_scale_rows(cudaStream_t st, int n, int r, const T* pu, const T*
 #define WC_INSTANTIATE(T)                                                                                          \
   template void launch_ap_finish<T>(cudaStream_t, int, int, int, int, const T*, int, const T*, const T*, const T*,  \
                                     const T*, const T*, const T*, T*, int, PcgCtl*, double*, unsigned int*,          \
-                                    int64_t*, const float*, int, const double*);                                    \
+                                    int64_t*, const float*, int, const double*, double*, double*);                  \
   template void launch_update<T>(cudaStream_t, int, T*, T*, const T*, const T*, PcgCtl*, double*, unsigned int*,   \
                                  int64_t*);                                                                         \
   template void launch_pc_d_s<T>(cudaStream_t, int, int, int, const T*, const T*, T*, const PcgCtl*, int64_t*);      \
   template void launch_pc_d_zv<T>(cudaStream_t, int, int, int, const T*, T*, const PcgCtl*, int64_t*);              \
   template void launch_pc_zu_dot<T>(cudaStream_t, int, int, int, const T*, int, const T*, T*, int, PcgCtl*, double*, \
-                                    unsigned int*, int64_t*, const double*);                                        \
+                                    unsigned int*, int64_t*, const double*, T*);                                    \
   template void launch_pc_m_tv<T>(cudaStream_t, int, int, const T*, const T*, T*, const PcgCtl*, int64_t*);         \
   template void launch_pc_m_w<T>(cudaStream_t, int, int, const T*, const T*, T*, const PcgCtl*, int64_t*);          \
   template void launch_pc_m_zv<T>(cudaStream_t, int, int, int, const T*, const T*, const T*, T*, const PcgCtl*,     \
@@ -878,9 +937,9 @@ void launch_correction_rhs(cudaStream_t st, int m, int d, const double* rho, dou
 void launch_mixed_finish(cudaStream_t st, int m, int d, const float* partA32, int SA, const double* partBv, int SB,
                          const double* partBu, int SBu, const double* Dv, const double* p, const double* g,
                          double* out, int mode, PcgCtl* ctl, double* dotbuf, unsigned int* counter,
-                         int64_t* launches) {
+                         int64_t* launches, double* ux, double* ur) {
   mixed_finish_kernel<<<vec_blocks(m + d), VT, 0, st>>>(m, d, partA32, SA, partBv, SB, partBu, SBu, Dv, p, g, out,
-                                                       mode, ctl, dotbuf, counter);
+                                                       mode, ctl, dotbuf, counter, mode == 1 ? ux : nullptr, ur);
   ++*launches;
 }
 
@@ -963,6 +1022,18 @@ void launch_minres_update(cudaStream_t st, int nt, const double* v, double* w, d
 void launch_ctl_reset(cudaStream_t st, PcgCtl* dst, const PcgCtl* src, int max_iters, int64_t* launches) {
   ctl_reset_kernel<<<1, 32, 0, st>>>(dst, src, max_iters);
   ++*launches;
+}
+
+void launch_slack_grad_rhs(cudaStream_t st, int m, const double* dv, const double* dw, const double* gy,
+                           const double* gv, const double* gw, double* delta, double* bt, int64_t* launches) {
+  slack_grad_rhs_kernel<<<(m + VT - 1) / VT, VT, 0, st>>>(m, dv, dw, gy, gv, gw, delta, bt);
+  if (launches) ++*launches;
+}
+
+void launch_slack_grad_out(cudaStream_t st, int m, const double* dv, const double* dw, const double* dy,
+                           const double* gv, const double* gw, double* ov, double* ow, int64_t* launches) {
+  slack_grad_out_kernel<<<(m + VT - 1) / VT, VT, 0, st>>>(m, dv, dw, dy, gv, gw, ov, ow);
+  if (launches) ++*launches;
 }
 
 }  // namespace wc

@@ -1,4 +1,6 @@
-// Launch wrappers of pcg.cu (internal).  The PCG vectors and scalars are FP64 in both forms;
+// Launch wrappers of pcg.cu (internal).  The finishing kernels of the operator (ap_finish,
+// mixed_finish) take optional x, r to do the PCG update in their last block, and pc_zu_dot an
+// optional p to do p = z + beta p there (mode 1), when the vectors are short.  The PCG vectors and scalars are FP64 in both forms;
 // the mixed form computes only the A E A^T block of its inner operator in FP32.
 #pragma once
 
@@ -13,7 +15,7 @@ template <typename T>
 void launch_ap_finish(cudaStream_t st, int m, int d, int n, int r, const T* partA, int S, const T* Up, const T* Vs,
                       const T* H, const T* Dv, const T* p, const T* g, T* out, int mode, PcgCtl* ctl,
                       double* dotbuf, unsigned int* counter, int64_t* launches, const float* partA32 = nullptr,
-                      int S32 = 0, const double* lin = nullptr);
+                      int S32 = 0, const double* lin = nullptr, double* ux = nullptr, double* ur = nullptr);
 template <typename T>
 void launch_update(cudaStream_t st, int nt, T* x, T* rv, const T* p, const T* Ap, PcgCtl* ctl, double* dotbuf,
                    unsigned int* counter, int64_t* launches);
@@ -25,7 +27,7 @@ void launch_pc_d_zv(cudaStream_t st, int m, int d, int S, const T* partC, T* z, 
 template <typename T>
 void launch_pc_zu_dot(cudaStream_t st, int m, int d, int S, const T* partU, int space, const T* rv, T* z, int mode,
                       PcgCtl* ctl, double* dotbuf, unsigned int* counter, int64_t* launches,
-                      const double* lam = nullptr);
+                      const double* lam = nullptr, T* pf = nullptr);
 template <typename T>
 void launch_pc_m_tv(cudaStream_t st, int m, int d, const T* rv, const T* Dv, T* t, const PcgCtl* ctl,
                     int64_t* launches);
@@ -69,7 +71,13 @@ void launch_add_correction(cudaStream_t st, int nt, const double* delta, double*
 void launch_mixed_finish(cudaStream_t st, int m, int d, const float* partA32, int SA, const double* partBv, int SB,
                          const double* partBu, int SBu, const double* Dv, const double* p, const double* g,
                          double* out, int mode, PcgCtl* ctl, double* dotbuf, unsigned int* counter,
-                         int64_t* launches);
+                         int64_t* launches, double* ux = nullptr, double* ur = nullptr);
+// The adjoint with the slacks of eq. rmc-sdp (G = [I, -I]): delta = d_v + d_w and
+// b~ = g_y + d_v g_v - d_w g_w; then the cotangents of the slack costs dx = D(G^T dy - c~)
+void launch_slack_grad_rhs(cudaStream_t st, int m, const double* dv, const double* dw, const double* gy,
+                           const double* gv, const double* gw, double* delta, double* bt, int64_t* launches);
+void launch_slack_grad_out(cudaStream_t st, int m, const double* dv, const double* dw, const double* dy,
+                           const double* gv, const double* gw, double* ov, double* ow, int64_t* launches);
 void launch_to_float(cudaStream_t st, int cnt, const double* src, float* dst, const int32_t* done, int64_t* launches);
 void launch_sym_copy(cudaStream_t st, int n, const double* g, double* out, int64_t* launches);
 void launch_ctl_reset(cudaStream_t st, PcgCtl* dst, const PcgCtl* src, int max_iters, int64_t* launches);

@@ -192,6 +192,82 @@ dense_AiQ_kernel(const double* __restrict__ A, int n, int64_t N, int i0, int mb,
   }
 }
 
+// The same product from the integer digits of the svec row (the copy the FP64 passes stream:
+// N_ab = rint(a_ab 2^(52 - e_i)) = hi 2^26 + lo, row exponent e_i) and of the columns of Q
+// (exponent f_j per column), summed exactly in int64 as the passes do (hi hi' and hi lo' + lo hi',
+// at most n <= 1024 terms per accumulator), so the n^2 r multiply-adds run on the integer pipe.
+// Off-diagonal (sqrt2-scaled) and diagonal entries keep separate sums, combined in FP64 at the end
+// as G = off / sqrt2 + diag.
+template <int r>
+__global__ void __launch_bounds__(AQ_THREADS)
+fx_AiQ_kernel(const int2* __restrict__ Ad, const int* __restrict__ ea, int n, int64_t Lp, int i0, int mb,
+              const double* __restrict__ Q, double* __restrict__ G) {
+  extern __shared__ __align__(16) int2 smi[];
+  int2* As = smi;                                   // digits of the svec row, Lp entries
+  int2* Qd = smi + Lp;                              // digits of Q, n x r row-major
+  __shared__ int fq[r];
+  const int il = blockIdx.x, i = i0 + il;
+  const int4* src = reinterpret_cast<const int4*>(Ad + (int64_t)i * Lp);   // Lp even: 16-byte rows
+  int4* dst = reinterpret_cast<int4*>(As);
+  for (int64_t q = threadIdx.x; q < Lp / 2; q += blockDim.x) dst[q] = __ldg(src + q);
+  if (threadIdx.x < r) fq[threadIdx.x] = INT_MIN;
+  __syncthreads();
+  for (int q = threadIdx.x; q < n * r; q += blockDim.x) {   // exponents of the columns of Q
+    const int b = q / r, j = q % r;
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(Q[b + (int64_t)j * n]) &
+                                    0x7FFFFFFFFFFFFFFFull;
+    if (bits) atomicMax(&fq[j], fx_expo_bits(bits));
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < n * r; q += blockDim.x) {
+    const int b = q / r, j = q % r;
+    const int f = fq[j] == INT_MIN ? 0 : fq[j];
+    Qd[q] = fx_split(fx_fixed(Q[b + (int64_t)j * n], 0, f));
+  }
+  __syncthreads();
+  const int e = ea[i];
+  for (int a = threadIdx.x; a < n; a += blockDim.x) {
+    long long o1[r], o2[r], d1[r], d2[r];
+#pragma unroll
+    for (int j = 0; j < r; ++j) o1[j] = o2[j] = 0;
+    int64_t idx = a;                                // (a, b = 0) in column 0
+    for (int b = 0; b < a; ++b) {
+      const int2 s = As[idx];
+#pragma unroll
+      for (int j = 0; j < r; ++j) {
+        const int2 q = Qd[b * r + j];
+        o1[j] += (long long)s.x * q.x;
+        o2[j] += (long long)s.x * q.y + (long long)s.y * q.x;
+      }
+      idx += n - b - 1;                             // (a, b + 1) in column b + 1
+    }
+    {
+      const int2 s = As[idx];                       // diagonal (a, a)
+#pragma unroll
+      for (int j = 0; j < r; ++j) {
+        const int2 q = Qd[a * r + j];
+        d1[j] = (long long)s.x * q.x;
+        d2[j] = (long long)s.x * q.y + (long long)s.y * q.x;
+      }
+    }
+    for (int b = a + 1; b < n; ++b) {               // (b, a) in column a
+      const int2 s = As[idx + (b - a)];
+#pragma unroll
+      for (int j = 0; j < r; ++j) {
+        const int2 q = Qd[b * r + j];
+        o1[j] += (long long)s.x * q.x;
+        o2[j] += (long long)s.x * q.y + (long long)s.y * q.x;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < r; ++j) {
+      const int sc = e + (fq[j] == INT_MIN ? 0 : fq[j]);
+      const double off = ldexp(fx_value(o1[j], o2[j]), sc), dg = ldexp(fx_value(d1[j], d2[j]), sc);
+      G[a + ((int64_t)j * mb + il) * n] = fma(off, WC_RSQRT2, dg);
+    }
+  }
+}
+
 }  // namespace
 
 static size_t dense_AiQ_smem(int n, int r) {
@@ -214,6 +290,30 @@ bool dense_AiQ(cudaStream_t st, const double* A, int n, int i0, int mb, int r, c
     WC_AIQ_CASE(7) WC_AIQ_CASE(8) WC_AIQ_CASE(9) WC_AIQ_CASE(10) WC_AIQ_CASE(11) WC_AIQ_CASE(12)
     WC_AIQ_CASE(13) WC_AIQ_CASE(14) WC_AIQ_CASE(15) WC_AIQ_CASE(16)
 #undef WC_AIQ_CASE
+    default: return false;
+  }
+  if (launches) ++*launches;
+  return true;
+}
+
+}  // namespace wc
+
+namespace wc {
+
+bool fx_AiQ(cudaStream_t st, const int2* Ad, const int* ea, int n, int64_t Lp, int i0, int mb, int r, const double* Q,
+            double* G, int64_t* launches) {
+  const size_t smem = (size_t)(Lp + (int64_t)n * r) * sizeof(int2);
+  if (r < 1 || r > 16 || n > FX_FLUSH || (Lp & 1) || smem > 220 * 1024) return false;
+  switch (r) {
+#define WC_FXAIQ_CASE(R)                                                                            \
+    case R:                                                                                         \
+      cudaFuncSetAttribute(fx_AiQ_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+      fx_AiQ_kernel<R><<<mb, AQ_THREADS, smem, st>>>(Ad, ea, n, Lp, i0, mb, Q, G);                    \
+      break;
+    WC_FXAIQ_CASE(1) WC_FXAIQ_CASE(2) WC_FXAIQ_CASE(3) WC_FXAIQ_CASE(4) WC_FXAIQ_CASE(5) WC_FXAIQ_CASE(6)
+    WC_FXAIQ_CASE(7) WC_FXAIQ_CASE(8) WC_FXAIQ_CASE(9) WC_FXAIQ_CASE(10) WC_FXAIQ_CASE(11) WC_FXAIQ_CASE(12)
+    WC_FXAIQ_CASE(13) WC_FXAIQ_CASE(14) WC_FXAIQ_CASE(15) WC_FXAIQ_CASE(16)
+#undef WC_FXAIQ_CASE
     default: return false;
   }
   if (launches) ++*launches;

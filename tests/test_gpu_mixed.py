@@ -3,7 +3,8 @@
 Each form runs the correction solves of an FP64 iterative refinement with a low-precision
 A E A^T block (Section 3 eq. augsys; the refinement is not in the paper):
   mixed_fp32  FP32 copies of A (or E o E), FP32 FFMA products;
-  mixed_tf32  the FP32 copy of A, E Y E on the tensor cores with TF32 operands;
+  mixed_tf32  the FP32 copy of A, E Y E on the tensor cores with split TF32 operands (hi + lo,
+              three MMAs per step);
   mixed_bf16  a BF16 copy of A (or E o E), E Y E on the tensor cores with BF16 operands;
 all with FP32 accumulation.  The refinement stops on the FP64 residual with the stop test of the
 FP64 form, so every form must give the oracle's direction to the FP64 bar, entry by entry
@@ -21,7 +22,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = 1e-8
 # bound on the mean contraction per correction solve, by form
-RATE = {"mixed_fp32": 1e-3, "mixed_tf32": 0.2, "mixed_bf16": 0.5}
+RATE = {"mixed_fp32": 1e-3, "mixed_tf32": 1e-3, "mixed_bf16": 0.5}
 
 
 def _t(a):
