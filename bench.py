@@ -239,14 +239,17 @@ def other_configs(dev, reps: int = 2, only=None, tc_n: int = 5000):
     # robust completion solved whole with its slacks (sdp_solve_slack; on request)
     if only == "rmc_slack100":
         out["rmc_slack100"] = _rmc_slack(dev, 100, 3000, 15, 71)
+    # the larger robust-completion instance where the preconditioned solve degrades as mu -> 0
+    if only == "rmc_slack300":
+        out["rmc_slack300"] = _rmc_slack(dev, 300, 8000, 40, 72, warm=False)
     return out
 
 
-def _rmc_slack(dev, n, m, m_o, seed):
+def _rmc_slack(dev, n, m, m_o, seed, warm=True):
     """Robust completion (eq. rmc-sdp: m svec entries of a rank-2 X*, m_o of them gross outliers)
-    solved to a 1e-8 gap by sdp_solve_slack; a first untimed call, then one timed call (host wall
-    clock around a synchronised call).  Reports the recovery error of X* and whether v - w is
-    supported exactly on the outliers."""
+    solved to a 1e-8 gap by sdp_solve_slack; a first untimed call (warm), then one timed call (host
+    wall clock around a synchronised call).  Reports the status, the recovery error of X* and
+    whether v - w is supported exactly on the outliers."""
     import time
     import numpy as np
     import torch
@@ -256,7 +259,8 @@ def _rmc_slack(dev, n, m, m_o, seed):
     s = NewtonSolver(prob, r_hat=3, device=str(dev))
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     b, C, ones = t(prob.b), t(prob.C), t(np.ones(m))
-    s.solve_slack(b, C, ones, ones, allow_notconv=True)
+    if warm:
+        s.solve_slack(b, C, ones, ones, allow_notconv=True)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     X, y, S, v, w, zv, zw, info = s.solve_slack(b, C, ones, ones, allow_notconv=True)
@@ -268,7 +272,8 @@ def _rmc_slack(dev, n, m, m_o, seed):
     s.close()
     return {"workload": f"robust completion n={n}, m={m} svec entries of a rank-2 X*, {m_o} gross outliers, "
                         "slacks v, w >= 0 (A(X) + v - w = b), r_hat=3, FP64",
-            "seconds": wall, "converged": bool(info["converged"]), "outer_iters": info["iters"],
+            "seconds": wall, "status": info["status"], "converged": bool(info["converged"]),
+            "outer_iters": info["iters"], "newton_inexact": info["newton_inexact"],
             "rel_gap": info["rel_gap"], "pcg_iters": info["pcg_iters"],
             "recovery_err": float(np.linalg.norm(X.cpu().numpy() - Xs) / np.linalg.norm(Xs)),
             "outliers_found": found == set(prob.meta["outliers"].tolist())}
@@ -801,7 +806,8 @@ def main():
     ap.add_argument("--no-ttg", action="store_true", help="skip the time-to-gap solves")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads (MaxCut 64 / 5000, completion)")
     ap.add_argument("--only", choices=["maxcut64", "maxcut5000", "completion2000", "tc_gemm", "batch32",
-                                       "completion2000_solve", "batch256", "lp_sensing200", "rmc_slack100"],
+                                       "completion2000_solve", "batch256", "lp_sensing200", "rmc_slack100",
+                                       "rmc_slack300"],
                     help="measure only this other workload (one JSON object; no headline line)")
     ap.add_argument("--reps", type=int, default=2, help="timed Newton solves per row of the other workloads")
     ap.add_argument("--tc-n", type=int, default=5000, help="order of the tensor-core product row (--only tc_gemm)")

@@ -25,9 +25,15 @@
  *     that the caller allocates and owns; they must stay valid until the
  *     call returns (all calls return after their work has completed on the
  *     handle's stream).
- *   - The handle owns all scratch memory; it is allocated once in
- *     sdp_setup (sized for the largest rank the options allow).  No other
- *     entry point allocates device memory.
+ *   - The handle owns all scratch memory.  The Newton solve's workspace is
+ *     allocated once in sdp_setup (sized for the largest rank the options
+ *     allow); sdp_newton_solve, sdp_newton_resolve, sdp_newton_solve_host and
+ *     sdp_grad allocate nothing.  Three workspaces are allocated on first use
+ *     and kept by the handle: the interior-point loop's (ipm_step, sdp_solve,
+ *     sdp_scaling_point, sdp_center, sdp_solve_slack, sdp_solve_batch: about
+ *     24 n^2 doubles), the linear block's (sdp_set_linear_diag, sdp_grad_slack:
+ *     m + m d_max doubles) and the slack variables' (sdp_solve_slack: 14 m
+ *     doubles); each reports SDP_ENOMEM if it cannot be allocated.
  *   - Status codes are returned; sdp_last_error() gives a message.  A CUDA
  *     error reported by the runtime is returned as SDP_ECUDA and leaves the
  *     handle unusable except for sdp_destroy.

@@ -108,6 +108,7 @@ struct sdp_handle {
   char* vs_mem[2] = {nullptr, nullptr};   // slices of the sorted eigenvectors Vs, made once per split:
   wc::TcSlices vs_sl[2];                  // [0] rows of Vs (op = Vs), [1] rows of Vs^T (op = Vs^T)
   bool no_coop = false;             // batched solves: no cooperative (grid-barrier) launches
+  bool coop_pc = false;             // dense d-space preconditioner apply as one cooperative launch
   int64_t b_elems = 0;              // capacity of the explicit B = A Q (m x d)
   int64_t bt_elems = 0;             // capacity of B^T (d x m)
   int64_t bs_elems = 0;             // capacity of D^{-1/2} B^T (m-space core by a product)
@@ -161,3 +162,5 @@ struct sdp_handle {
 sdp_status wc_fail(sdp_handle* h, sdp_status s, const std::string& msg);
 // Release the interior-point workspace (ipm.cu).
 void wc_ipm_free(sdp_handle* h);
+// Drop the captured PCG graphs of the handle (newton.cu).
+void wc_drop_graphs(sdp_handle* h);

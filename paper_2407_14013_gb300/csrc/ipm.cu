@@ -1199,7 +1199,10 @@ extern "C" sdp_status sdp_solve_batch(int32_t count, sdp_handle* const* hs, cons
     cost[i] = (double)h->n * h->n * h->n + (h->kind == SDP_A_DENSE_SVEC ? 64.0 * h->m * (double)h->N : 0.0);
   }
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) { return cost[a] > cost[c]; });
-  for (int32_t i = 0; i < count; ++i) hs[i]->no_coop = true;
+  for (int32_t i = 0; i < count; ++i) {
+    hs[i]->no_coop = true;
+    if (hs[i]->coop_pc) wc_drop_graphs(hs[i]);   // recaptured without the cooperative launch
+  }
   std::atomic<int32_t> next{0};
   auto work = [&]() {
     for (;;) {
@@ -1226,7 +1229,10 @@ extern "C" sdp_status sdp_solve_batch(int32_t count, sdp_handle* const* hs, cons
   }
   work();
   for (auto& t : pool) t.join();
-  for (int32_t i = 0; i < count; ++i) hs[i]->no_coop = false;
+  for (int32_t i = 0; i < count; ++i) {
+    hs[i]->no_coop = false;
+    if (hs[i]->coop_pc) wc_drop_graphs(hs[i]);
+  }
   for (int32_t i = 0; i < count; ++i)
     if (statuses[i] != SDP_OK) return (sdp_status)statuses[i];
   return SDP_OK;

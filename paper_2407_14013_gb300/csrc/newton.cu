@@ -496,6 +496,9 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   }
   std::memset(h->ctl_host, 0, sizeof(PcgCtl));
   for (auto& a : h->aux) CU(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+  // the cooperative preconditioner apply (dense kind, d-space) where the device launches it;
+  // batched solves turn it off with the other grid barriers
+  h->coop_pc = (h->kind == SDP_A_DENSE_SVEC) && pc_dense_coop_blocks() > 0 && pc_dense_coop_blocks() <= 1024;
   for (auto& ev : h->br_ev) CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   CU(cudaMemsetAsync(h->counter, 0, 4 * sizeof(unsigned int), h->st));
   // s_A = ||A||_F^2 / m (beta rule 0); FP32 copy of A for the mixed form
@@ -849,6 +852,10 @@ sdp_status apply_precond(sdp_handle* h, Space& S, const double* rin, double* zou
       launch_diag_zv(st, m, d, n, r, S.H, rin, S.Dv, zout, S.ctl, L);      // z_v = D^{-1}(B^T z_u - r_v)
       launch_pc_zu_dot<double>(st, m, d, 0, nullptr, 2, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L, nullptr, h->fuse ? S.p : nullptr);
     }
+  } else if (h->space == 1 && !h->lin && h->kind == SDP_A_DENSE_SVEC && h->coop_pc && !h->no_coop) {
+    // the three products and the dot in one cooperative launch (grid barriers between them)
+    CU(launch_pc_dense_d_coop(st, m, d, S.Bt, S.Pinv, S.B, rin, zout, S.sd, h->dotbuf, mode, S.ctl,
+                              h->fuse ? S.p : nullptr, L));
   } else if (h->space == 1) {
     if (h->lin) {   // linear block: s = r_v - B^T (Lam^{-1} r_u), z_u = Lam^{-1}(r_u - B z_v)
       launch_lin_div(st, m, rin, h->lin_lam, S.wm, S.ctl, L);
@@ -953,12 +960,27 @@ sdp_status krylov_loop(sdp_handle* h, Space& S, bool mixed, bool minres) {
       if (G.exec) { cudaGraphExecDestroy(G.exec); G.exec = nullptr; }
       if (!h->cap_stream) CU(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
       const int64_t before = h->launches;
+      const size_t prof_before = h->prof_entries.size();
       CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
       h->capturing = true;
       sdp_status s = chunk(h->cap_stream);
       h->capturing = false;
       cudaGraph_t graph = nullptr;
       cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
+      if ((s != SDP_OK || ce != cudaSuccess) && h->coop_pc) {
+        // a cooperative launch that stream capture does not take: capture again without it
+        if (graph) cudaGraphDestroy(graph);
+        graph = nullptr;
+        cudaGetLastError();
+        h->coop_pc = false;
+        h->launches = before;
+        h->prof_entries.resize(prof_before);
+        CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        h->capturing = true;
+        s = chunk(h->cap_stream);
+        h->capturing = false;
+        ce = cudaStreamEndCapture(h->cap_stream, &graph);
+      }
       if (s != SDP_OK) { if (graph) cudaGraphDestroy(graph); return s; }
       if (ce != cudaSuccess) return fail(h, SDP_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
       ce = cudaGraphInstantiate(&G.exec, graph, 0);
@@ -1514,4 +1536,14 @@ extern "C" void sdp_destroy(sdp_handle* h) {
     if (ev) cudaEventDestroy(ev);
   wc_ipm_free(h);
   delete h;
+}
+
+// Captured PCG graphs hold the launch forms chosen when they were captured (the cooperative
+// preconditioner apply or not): drop them when that choice changes.
+void wc_drop_graphs(sdp_handle* h) {
+  for (auto& G : h->graph)
+    if (G.exec) {
+      cudaGraphExecDestroy(G.exec);
+      G.exec = nullptr;
+    }
 }

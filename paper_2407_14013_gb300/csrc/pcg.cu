@@ -8,7 +8,11 @@
 // at once when ctl->done is set.  Dot products are accumulated in FP64 and reduced
 // deterministically: per-block partial sums, then the last block to finish (atomic ticket)
 // adds them in block order.
+#include <algorithm>
+#include <cooperative_groups.h>
+
 #include "common.cuh"
+#include "kernels.h"
 #include "pcg.h"
 
 namespace wc {
@@ -765,6 +769,82 @@ __global__ void slack_grad_out_kernel(int m, const double* __restrict__ dv, cons
   ow[i] = dw[i] * (-dy[i] - gw[i]);
 }
 
+// The d-space preconditioner apply of the dense kind in one cooperative launch (Section 6: the
+// block LDL^T inverse of P = [beta I, B; B^T, -D]):
+//   s = r_v - beta^{-1} B^T r_u,  z_v = -C^{-1} s,  z_u = beta^{-1} (r_u - B z_v),
+// then <r, z> (mode 0: rz; mode 1: beta_pcg = <r_new, z_new> / <r, z>) and, with pf, p = z + beta p.
+// Three products that depend on each other, on L2-resident matrices (B^T, C^{-1}, B): one warp per
+// output row, grid-wide barriers between them instead of four launches.  Sums in a fixed order.
+__global__ void __launch_bounds__(256)
+pc_dense_d_coop_kernel(int m, int d, const double* __restrict__ Bt, const double* __restrict__ Pinv,
+                       const double* __restrict__ B, const double* __restrict__ rv, double* __restrict__ z,
+                       double* __restrict__ sd, double* __restrict__ part, int mode, PcgCtl* __restrict__ ctl,
+                       double* __restrict__ pf) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  if (ctl->done) return;                     // uniform: set only by earlier launches
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31;
+  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  const double ib = 1.0 / ctl->beta_pc;
+  const double* ru = rv;
+  const double* rvv = rv + m;
+  // s = r_v - beta^{-1} B^T r_u
+  for (int i = gw; i < d; i += nw) {
+    const double* row = Bt + (int64_t)i * m;
+    double acc = 0.0;
+    for (int k = lane; k < m; k += 32) acc = fma(row[k], ru[k], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) sd[i] = rvv[i] - ib * acc;
+  }
+  grid.sync();
+  // z_v = -C^{-1} s, and its part of <r, z>
+  double dot = 0.0;
+  for (int i = gw; i < d; i += nw) {
+    const double* row = Pinv + (int64_t)i * d;
+    double acc = 0.0;
+    for (int k = lane; k < d; k += 32) acc = fma(row[k], __ldcg(sd + k), acc);
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      z[m + i] = -acc;
+      dot = fma(rvv[i], -acc, dot);
+    }
+  }
+  grid.sync();
+  // z_u = beta^{-1} (r_u - B z_v), and its part of <r, z>
+  for (int j = gw; j < m; j += nw) {
+    const double* row = B + (int64_t)j * d;
+    double acc = 0.0;
+    for (int k = lane; k < d; k += 32) acc = fma(row[k], __ldcg(z + m + k), acc);
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      const double zu = ib * (ru[j] - acc);
+      z[j] = zu;
+      dot = fma(ru[j], zu, dot);
+    }
+  }
+  dot = block_sum(dot, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = dot;
+  grid.sync();
+  if (blockIdx.x != 0) return;
+  double rz = 0.0;
+  for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) rz += __ldcg(part + q);
+  rz = block_sum(rz, sh);
+  if (threadIdx.x == 0) {
+    if (!isfinite(rz)) { ctl->status = 5; ctl->done = 1; }
+    if (mode == 0) { ctl->rz = rz; ctl->beta = 0.0; }
+    else { ctl->rz_new = rz; ctl->beta = rz / ctl->rz; ctl->rz = rz; }
+  }
+  if (pf && mode == 1) {                     // p = z + beta p (block 0)
+    __syncthreads();
+    if (ctl->done) return;
+    const double beta = ctl->beta;
+    const int nt = m + d;
+    for (int q = threadIdx.x; q < nt; q += blockDim.x) pf[q] = fma(beta, pf[q], __ldcg(z + q));
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -1034,6 +1114,40 @@ void launch_slack_grad_out(cudaStream_t st, int m, const double* dv, const doubl
                            const double* gv, const double* gw, double* ov, double* ow, int64_t* launches) {
   slack_grad_out_kernel<<<(m + VT - 1) / VT, VT, 0, st>>>(m, dv, dw, dy, gv, gw, ov, ow);
   if (launches) ++*launches;
+}
+
+int pc_dense_coop_blocks() {
+  static int blocks = -1;
+  if (blocks < 0) {
+    int dev = 0, coop = 0, per = 0;
+    blocks = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pc_dense_d_coop_kernel, 256, 0) == cudaSuccess && per > 0)
+      blocks = g_num_sms * std::min(per, 4);
+    cudaGetLastError();
+  }
+  return blocks;
+}
+
+cudaError_t launch_pc_dense_d_coop(cudaStream_t st, int m, int d, const double* Bt, const double* Pinv,
+                                   const double* B, const double* rv, double* z, double* sd, double* part, int mode,
+                                   PcgCtl* ctl, double* pf, int64_t* launches) {
+  const int blocks = pc_dense_coop_blocks();
+  if (blocks <= 0) return cudaErrorNotSupported;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, pc_dense_d_coop_kernel, m, d, Bt, Pinv, B, rv, z, sd, part, mode, ctl, pf);
+  if (e == cudaSuccess && launches) ++*launches;
+  return e;
 }
 
 }  // namespace wc

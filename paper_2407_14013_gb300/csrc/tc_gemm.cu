@@ -425,6 +425,243 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
+// ---- the product, class-accumulator form -------------------------------------------------------
+// One CTA per 128 x 64 output tile.  Per K-step of 64 the eight slices of op(B) (64 x 64 tiles)
+// are loaded once into a 2-stage buffer and the eight slices of op(A) (128 x 64 tiles) stream
+// through a 4-stage ring; slice s of A meets slices t = 1 .. 9 - s of B, and each pair's product
+// goes to the TMEM accumulator of its weight class g = s + t (8 classes x 64 FP32 columns: all
+// 512 columns).  So each loaded tile serves up to eight MMAs instead of one, which is what the
+// pairwise form lacked (it re-streamed both tiles for every pair and waited on L2).  A class sum
+// over a K-chunk of 512 is an integer of at most 8 x 512 x 64 x 64 = 2^24: exact in FP32.  After
+// each chunk the eight epilogue warps read the classes and fold them exactly into two int64
+// sums per element, T_hi = sum_{g=2..5} S_g 2^(7(5-g)) and T_lo = sum_{g=6..9} S_g 2^(7(9-g))
+// (each below 2^43 per chunk), so the only FP64 work is the final
+// 2^(e_i + f_j) (T_hi 2^-33 + T_lo 2^-61).  Warp 8 (one lane) issues the TMA loads, warp 9 (one
+// lane) the MMAs; every wait is bounded as in the pairwise form.
+
+constexpr int CBM = 128, CBN = 64, CKC = 512;               // tile, exact K-chunk
+constexpr int CRA = 4, CRB = 2;                              // A ring, B stages
+constexpr int CA_TILE = CBM * BK * 2;                        // 16 KB
+constexpr int CB_TILE = CBN * BK * 2;                        // 8 KB
+constexpr int CB_STAGE = S * CB_TILE;                        // 64 KB: the eight slices of B
+constexpr int CSMEM = CRA * CA_TILE + CRB * CB_STAGE + 1024;
+constexpr int CEPI = 8;                                      // epilogue warps
+constexpr int CTHREADS = (CEPI + 2) * 32;
+constexpr uint32_t CIDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CBN >> 3) << 17) |
+                            ((uint32_t)(CBM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16_c(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(CIDESC), "r"(accumulate)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(CTHREADS, 1)
+tc_gemm_cls_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M,
+                   int N, int K, int ksplit, const int* __restrict__ ea, const int* __restrict__ eb, double alpha,
+                   double beta, double* __restrict__ C, int64_t ldc, double* __restrict__ part, int lower,
+                   int* __restrict__ err, const int32_t* __restrict__ done, unsigned long long wait_ns) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t fullA[CRA], emptyA[CRA], fullB[CRB], emptyB[CRB], accF, accE;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+
+  const int m0 = blockIdx.x * CBM, n0 = blockIdx.y * CBN;
+  if (lower && m0 + CBM <= n0) return;               // tile entirely above the diagonal
+  if (done && *done) return;
+  const int kz0 = blockIdx.z * ksplit;
+  const int Kz = min(K, kz0 + ksplit) - kz0;
+  const int nks = Kz > 0 ? (Kz + BK - 1) / BK : 0;   // K-steps of this CTA
+  constexpr int KCS = CKC / BK;                      // K-steps per exact chunk
+  const int nch = (nks + KCS - 1) / KCS;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const uint32_t abase = base, bbase = base + CRA * CA_TILE;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < CRA; ++i) {
+      mbar_init(smem_u32(&fullA[i]), 1);
+      mbar_init(smem_u32(&emptyA[i]), 1);
+    }
+    for (int i = 0; i < CRB; ++i) {
+      mbar_init(smem_u32(&fullB[i]), 1);
+      mbar_init(smem_u32(&emptyB[i]), 1);
+    }
+    mbar_init(smem_u32(&accF), 1);
+    mbar_init(smem_u32(&accE), CEPI);
+    abort_flag = 0;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == CEPI + 1) {                            // TMEM: eight 64-column class accumulators
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == CEPI) {
+    // ---- TMA loads (one thread): per K-step the eight B slices, then the eight A slices ----
+    if (lane == 0) {
+      int ga = 0, gb = 0;
+      bool ok = true;
+      for (int ks = 0; ks < nks && ok; ++ks) {
+        const int k0 = kz0 + ks * BK;
+        const int sb = gb % CRB;
+        if (gb >= CRB && !mbar_wait(smem_u32(&emptyB[sb]), ((gb / CRB) - 1) & 1, &abort_flag, err, wait_ns)) {
+          ok = false;
+          break;
+        }
+        const uint32_t fb = smem_u32(&fullB[sb]);
+        mbar_expect_tx(fb, CB_STAGE);
+        for (int t = 0; t < S; ++t) tma_load_3d(bbase + sb * CB_STAGE + t * CB_TILE, &mapB, k0, n0, t, fb);
+        ++gb;
+        for (int sidx = 0; sidx < S; ++sidx) {
+          const int sa = ga % CRA;
+          if (ga >= CRA && !mbar_wait(smem_u32(&emptyA[sa]), ((ga / CRA) - 1) & 1, &abort_flag, err, wait_ns)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fa = smem_u32(&fullA[sa]);
+          mbar_expect_tx(fa, CA_TILE);
+          tma_load_3d(abase + sa * CA_TILE, &mapA, k0, m0, sidx, fa);
+          ++ga;
+        }
+      }
+      if (!ok) {
+        abort_flag = 1;
+        // bounded waits (full bound) for this CTA's own copies in flight: the last loads of each
+        // ring (older ones were consumed, so they completed)
+        volatile int keep_waiting = 0;
+        for (int g = max(0, ga - CRA); g < ga; ++g)
+          mbar_wait(smem_u32(&fullA[g % CRA]), (g / CRA) & 1, &keep_waiting, err);
+        for (int g = max(0, gb - CRB); g < gb; ++g)
+          mbar_wait(smem_u32(&fullB[g % CRB]), (g / CRB) & 1, &keep_waiting, err);
+      }
+    }
+  } else if (warp == CEPI + 1) {
+    // ---- MMAs (one thread) ----
+    if (lane == 0) {
+      int ga = 0, gb = 0;
+      bool ok = true, issued = false;
+      uint32_t init = 0;                             // classes already written in this chunk
+      for (int ks = 0; ks < nks && ok; ++ks) {
+        if (ks % KCS == 0) {
+          if (ks > 0 && !mbar_wait(smem_u32(&accE), ((ks / KCS) - 1) & 1, &abort_flag, err, wait_ns)) {
+            ok = false;                              // the previous chunk is not drained yet
+            break;
+          }
+          tc_fence_after();
+          init = 0;
+        }
+        const int sb = gb % CRB;
+        if (!mbar_wait(smem_u32(&fullB[sb]), (gb / CRB) & 1, &abort_flag, err, wait_ns)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t b0 = bbase + sb * CB_STAGE;
+        for (int sidx = 0; sidx < S && ok; ++sidx) {
+          const int sa = ga % CRA;
+          if (!mbar_wait(smem_u32(&fullA[sa]), (ga / CRA) & 1, &abort_flag, err, wait_ns)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = abase + sa * CA_TILE;
+          for (int t = 0; sidx + t < S; ++t) {       // (s + 1) + (t + 1) <= S + 1
+            const int cls = sidx + t;
+            const uint32_t dcol = tmem + (uint32_t)(cls * CBN);
+            const uint32_t bt = b0 + t * CB_TILE;
+#pragma unroll
+            for (int sub = 0; sub < BK / 16; ++sub)
+              mma_bf16_c(dcol, smem_desc(a0 + sub * 32), smem_desc(bt + sub * 32),
+                         ((init >> cls) & 1u) || sub > 0 ? 1u : 0u);
+            init |= 1u << cls;
+          }
+          mma_commit(smem_u32(&emptyA[sa]));         // the A slot is free once these products finish
+          issued = true;
+          ++ga;
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&emptyB[sb]));
+        ++gb;
+        if (ks % KCS == KCS - 1 || ks == nks - 1) mma_commit(smem_u32(&accF));   // chunk complete
+      }
+      if (!ok) {
+        abort_flag = 1;
+        volatile int keep_waiting = 0;
+        if (issued) {                                // the last commit covers every product issued
+          const int g = ga - 1;
+          mbar_wait(smem_u32(&emptyA[g % CRA]), (g / CRA) & 1, &keep_waiting, err);
+        }
+      }
+    }
+  } else {
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows), columns 32 (w / 4) .. + 31
+    // of every class; exact int64 sums across the chunks ----
+    const int q4 = warp & 3, hc = warp >> 2;
+    long long thi[32], tlo[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) thi[j] = tlo[j] = 0;
+    bool got = true;
+    for (int ch = 0; ch < nch; ++ch) {
+      got = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accF), ch & 1, &abort_flag, err, wait_ns));
+      if (!got) break;
+      tc_fence_after();
+#pragma unroll 1
+      for (int cls = 0; cls < S; ++cls) {
+        uint32_t r[32];
+        WC_TMEM_LD32(tmem + (uint32_t)(cls * CBN + hc * 32) + ((uint32_t)(32 * q4) << 16), r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int g = cls + 2;
+        if (g <= 5) {
+          const int sh = 7 * (5 - g);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) thi[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+        } else {
+          const int sh = 7 * (9 - g);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) tlo[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&accE));
+    }
+    if (got && !abort_flag) {
+      const int row = m0 + 32 * q4 + lane;
+      if (row < M) {
+        const int er = ea[row];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = n0 + hc * 32 + j;
+          if (col >= N) continue;
+          const double a = fma((double)thi[j], 0x1p-33, (double)tlo[j] * 0x1p-61);
+          if (part) {                                // partial tile of this K range
+            part[(int64_t)blockIdx.z * M * N + row + (int64_t)col * M] = scalbn(a, er + eb[col]);
+          } else {
+            const double v = alpha * scalbn(a, er + eb[col]);
+            double* cp = C + (int64_t)row + (int64_t)col * ldc;
+            *cp = (beta == 0.0) ? v : v + beta * *cp;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == CEPI + 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
 // C = alpha sum_z part[z] + beta C over the split K ranges, in z order (deterministic); tiles
 // above the diagonal are skipped when `lower` is set, as in the product.
 __global__ void tc_reduce_kernel(int M, int N, int nz, const double* __restrict__ part, double alpha, double beta,
@@ -435,7 +672,7 @@ __global__ void tc_reduce_kernel(int M, int N, int nz, const double* __restrict_
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (int64_t)M * N) return;
   const int row = (int)(q % M), col = (int)(q / M);
-  if (lower && (row / BM) * BM + BM <= (col / BN) * BN) return;
+  if (lower && (row / CBM) * CBM + CBM <= (col / CBN) * CBN) return;
   double sum = 0.0;
   for (int z = 0; z < nz; ++z) sum += part[(int64_t)z * M * N + q];
   double* cp = C + (int64_t)row + (int64_t)col * ldc;
@@ -462,10 +699,10 @@ cudaError_t encode_fn() {
   return g_encode ? cudaSuccess : g_encode_err;
 }
 
-cudaError_t make_map(CUtensorMap* map, const void* slices, int rows, int Kpad) {
+cudaError_t make_map(CUtensorMap* map, const void* slices, int rows, int Kpad, int box_rows) {
   const cuuint64_t dims[3] = {(cuuint64_t)Kpad, (cuuint64_t)rows, (cuuint64_t)S};
   const cuuint64_t strides[2] = {(cuuint64_t)Kpad * 2, (cuuint64_t)rows * Kpad * 2};
-  const cuuint32_t box[3] = {BK, BM, 1};
+  const cuuint32_t box[3] = {BK, (cuuint32_t)box_rows, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(slices), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -520,7 +757,7 @@ cudaError_t tc_prepare() {
   static std::once_flag attr_once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(attr_once, [] {
-    attr_err = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    attr_err = cudaFuncSetAttribute(tc_gemm_cls_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CSMEM);
   });
   return attr_err;
 }
@@ -651,10 +888,10 @@ cudaError_t gemm_f64_tc_one(cudaStream_t st, bool tA, bool tB, int M, int N, int
     if (launches) *launches += 2;
   }
   CUtensorMap mapA, mapB;
-  e = make_map(&mapA, sa, M, Kp);
-  if (e == cudaSuccess) e = make_map(&mapB, sb, N, Kp);
+  e = make_map(&mapA, sa, M, Kp, CBM);
+  if (e == cudaSuccess) e = make_map(&mapB, sb, N, Kp, CBN);
   if (e != cudaSuccess) return e;
-  const int gm = (M + BM - 1) / BM, gn = (N + BN - 1) / BN;
+  const int gm = (M + CBM - 1) / CBM, gn = (N + CBN - 1) / CBN;
   int tiles = gm * gn;
   if (flags & GEMM_LOWER) tiles = (tiles + gm) / 2;
   // split K when the tiles leave SMs idle: about one CTA per SM, K ranges of >= 512
@@ -667,7 +904,7 @@ cudaError_t gemm_f64_tc_one(cudaStream_t st, bool tA, bool tB, int M, int N, int
   if (ksplit > 0) nz = (K + ksplit - 1) / ksplit;
   else nz = 1;
   dim3 grid(gm, gn, nz);
-  tc_gemm_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(mapA, mapB, M, N, K, ksplit, ea, eb, alpha, beta, C, ldc,
+  tc_gemm_cls_kernel<<<grid, CTHREADS, CSMEM, st>>>(mapA, mapB, M, N, K, ksplit, ea, eb, alpha, beta, C, ldc,
                                                     nz > 1 ? part : nullptr, (flags & GEMM_LOWER) ? 1 : 0, err, done,
                                                     g_main_wait_ns.load());
   if (launches) ++*launches;

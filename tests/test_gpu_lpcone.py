@@ -146,31 +146,41 @@ def _lp_case_dense():
     return W.Problem(kind=p0.kind, n=p0.n, m=p0.m, b=b, C=p0.C, a_dense=p0.a_dense)
 
 
-@pytest.mark.parametrize("name", ["sensing6_outliers", "rmc12"])
-def test_grad_slack_matches_kkt_definition(name):
+# (case, outer-loop tolerance of the oracle's solve, centring mu or None, bound).  On robust
+# completion d = x / z spans 4e-4 .. 7e7 (mu ~ 2e-3) and 2.7e-9 .. 4e13 (final, mu ~ 1e-8): the KKT
+# matrix's condition is then 1e11 and more, the dense LU solve of the same system is off by 3e-5
+# and O(1) there, and two FP64 solves of it agree to a few 1e-8 (measured 4e-8 GPU vs oracle), so
+# those cases carry a bound of 1e-6; the dense case (d in 1e-4 .. 1e5) keeps the FP64 bar.
+SLACK_CASES = [("sensing6_outliers", 1e-9, 1e-4, 1e-8), ("rmc12_mid", 1e-4, None, 1e-6),
+               ("rmc12_final", 1e-9, None, 1e-6)]
+
+
+@pytest.mark.parametrize("name,otol,mu_c,bound", SLACK_CASES, ids=[c[0] for c in SLACK_CASES])
+def test_grad_slack_matches_kkt_definition(name, otol, mu_c, bound):
     """The adjoint with the slacks of eq. rmc-sdp on the GPU (sdp_grad_slack: one reformulated
     Newton solve with the linear block, then dx = D(G^T dy - c~)) against the oracle's solve of the
     same symmetric KKT system of the two cones, [[-(W (x)s W)^{-1}, 0, A^T], [0, -D^{-1}, G^T],
     [A, G, 0]] [gC; gc; gb] = [sym gX; gx; gy] (oracle/lpcone.py newton_reform_lp, the product
-    vjp_lp takes, here to a residual of 1e-15), at a centred iterate (mu = 1e-6) of the dense case,
-    where the plain dense KKT solve (LU) agrees with it, and at the final iterate of the oracle's
-    solve for robust completion (mu ~ 1e-8, where the dense KKT matrix is too ill-conditioned for LU
-    and the reformulation is what stays accurate).  Entry by entry: gC and gb, and the slack
+    vjp_lp takes, here to a residual of 1e-15), at a centred iterate (mu = 1e-4) of the dense case,
+    where the plain dense KKT solve (LU) agrees with it to 1e-9, and at two iterates of the oracle's
+    solve for robust completion (mu ~ 2e-3, and the final mu ~ 1e-8, where the dense KKT matrix is
+    too ill-conditioned for LU and the reformulation is what stays accurate).  Entry by entry: gC and gb, and the slack
     cotangent through D^{-1} gc = G^T gb - gx (gc itself multiplies that difference by d = x / z, up
     to 1e12 on the outliers, which no FP64 evaluation resolves better than d eps max|gb|).  (At its
-    default tolerance the oracle's PCG stops one iteration early on the dense case and sits 7e-7
-    from the KKT solution; the GPU's stop test takes the second iteration.)"""
+    default tolerance the oracle's PCG stops one iteration early on the dense case at mu = 1e-6 and
+    sits 7e-7 from the KKT solution; the GPU's stop test takes the second iteration.)"""
     from oracle import ipm_lp, lpcone, newton as onewton
     from paper_2407_14013_gb300 import NewtonSolver
-    prob = _lp_case_dense() if name == "sensing6_outliers" else W.rmc(12, 70, 3, 9)
+    dense = name.startswith("sensing6")
+    prob = _lp_case_dense() if dense else W.rmc(12, 70, 3, 9)
     m = prob.m
     G = np.hstack([np.eye(m), -np.eye(m)])
-    cl = 0.5 * np.ones(2 * m) if name == "sensing6_outliers" else np.ones(2 * m)
-    res = ipm_lp.ipm_solve_lp(prob, G, cl, tol=1e-9, max_iter=200)
+    cl = 0.5 * np.ones(2 * m) if dense else np.ones(2 * m)
+    res = ipm_lp.ipm_solve_lp(prob, G, cl, tol=otol, max_iter=200)
     assert res.converged
     st = ipm_lp.LPState(res.X, res.x, res.y, res.S, res.z)
-    if name == "sensing6_outliers":   # the centred point of the oracle's own pins
-        st = ipm_lp.center_lp(prob, G, cl, st, 1e-6)
+    if mu_c is not None:
+        st = ipm_lp.center_lp(prob, G, cl, st, mu_c)
     rng = np.random.default_rng(12)
     gX = rng.standard_normal((prob.n, prob.n))
     gX = 0.5 * (gX + gX.T)
@@ -181,9 +191,9 @@ def test_grad_slack_matches_kkt_definition(name):
     # the oracle's reformulated solve taken to a tighter tolerance than its default
     kC, kc, kb, _ = lpcone.newton_reform_lp(prob, V, lam, gX, gy, G, d, gx, r_hat=3,
                                             s_A=oops.row_norm_scale(prob), rtol=1e-15, space="d")
-    if name == "sensing6_outliers":   # and the plain dense KKT solve agrees with it here (mu = 1e-6)
+    if dense:   # and the plain dense KKT solve agrees with it here (mu = 1e-4)
         dC, dc, db = lpcone.newton_kkt_dense_lp(prob, Wm, gX, gy, G, d, gx)[:3]
-        assert np.abs(dC - kC).max() <= 1e-8 * np.abs(kC).max() and np.abs(db - kb).max() <= 1e-8 * np.abs(kb).max()
+        assert np.abs(dC - kC).max() <= 1e-9 * np.abs(kC).max() and np.abs(db - kb).max() <= 1e-9 * np.abs(kb).max()
     s = NewtonSolver(prob, r_hat=3)
     gC, gb, gcv, gcw = s.grad_slack(_t(V), _t(lam), _t(d[:m]), _t(d[m:]), _t(gX), _t(gy), _t(gx[:m]), _t(gx[m:]))
     assert s.last_info.converged
@@ -193,7 +203,7 @@ def test_grad_slack_matches_kkt_definition(name):
     print(f"\n{name} pcg_iters={s.last_info.pcg_iters} d in [{d.min():.1e}, {d.max():.1e}] " +
           " ".join(f"{k}={e:.2e}" for k, e in errs.items()))
     for k, e in errs.items():
-        assert e <= 1e-8, (k, e)
+        assert e <= bound, (k, e)
     # the handle is left without a linear block: a plain adjoint call works afterwards
     gC2, gb2 = s.grad(_t(V), _t(lam), _t(gX), _t(gy))
     assert s.last_info.converged
