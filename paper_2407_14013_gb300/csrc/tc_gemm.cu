@@ -16,14 +16,13 @@
 // max_k|op(A)[i,k]| max_k|op(B)[k,j]| -- the FP64 bound when the rows and columns have no
 // large internal dynamic range (use gemm_f64 where they do).
 //
-// Kernel.  One CTA per 128 x 128 output tile, 9 warps: warp 8 (one lane) issues the TMA loads
-// of 128 x 64 BF16 slice tiles (128-byte swizzle) into a 3-stage ring and the 128x128x16
-// tcgen05.mma steps into one of two TMEM accumulators (256 columns); warps 0-7 drain a finished
-// accumulator (tcgen05.ld, 32 lanes x 32 columns per load) while the tensor core fills the
-// other: the products of one weight class s + t in a K-chunk are summed exactly as int32, then
-// added once to FP64 accumulators of the tile in shared memory (128 KB).  Every wait is bounded (about 2 s, %globaltimer): on expiry the kernel
-// sets an error word, stops issuing, waits (bounded) for its own copies and products in flight,
-// frees its TMEM and returns.
+// Kernel (tc_gemm_cls_kernel below).  One CTA per 128 x 64 output tile: the eight slices of op(B)
+// for a K-step are loaded once and each slice of op(A) meets all the B slices its pairs need, into
+// one TMEM accumulator per weight class s + t; the class sums are exact in FP32 over K-chunks of
+// 512 and are folded into exact int64 sums by the epilogue warps, so FP64 arithmetic is needed only
+// once per output.  Every wait is bounded (about 2 s, %globaltimer): on expiry the kernel sets an
+// error word, stops issuing, waits (bounded) for its own copies and products in flight, frees its
+// TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -42,46 +41,13 @@ namespace wc {
 namespace {
 
 constexpr int S = 8;                  // slices per operand
-constexpr int KC = 4096;              // exact K-chunk of one slice product
-constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int STAGES = 3;
-constexpr int EPI_WARPS = 8;
-constexpr int THREADS = (EPI_WARPS + 1) * 32;
-constexpr int TILE_BYTES = BM * BK * 2;                 // 16 KB per operand tile
-constexpr int STAGE_BYTES = 2 * TILE_BYTES;
-constexpr int FACC_BYTES = BM * BN * 8;                  // FP64 accumulators of the tile
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + FACC_BYTES + 1024;  // + alignment slack
-constexpr int TMEM_COLS = 256;                           // two 128-column FP32 accumulators
-constexpr int NPAIRS = S * (S + 1) / 2;                  // s + t <= S + 1
+constexpr int KC = 4096;              // host K-chunks are whole multiples of this where possible
+constexpr int BK = 64;                // K-slice of one TMA box (128 bytes of BF16)
 constexpr unsigned long long WAIT_NS = tcx::kWaitNs;
 
 // ---- PTX wrappers: tc_ptx.cuh; the MMA of this kernel ----------------------------------------
 
 using namespace tcx;
-
-// Instruction descriptor: kind::f16 with BF16 A and B (K-major), FP32 D, M = 128, N = 128.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
-      : "memory");
-}
-
-
-// ---- pair table: (s, t) with s + t <= S + 1 (1-based), largest weights first ---------------
-
-__device__ __forceinline__ void pair_of(int q, int& s, int& t) {
-  // q enumerates g = s + t = 2, 3, ..., S + 1 and within g s = 1 .. g - 1
-  int g = 2, base = 0;
-  while (q >= base + (g - 1)) { base += g - 1; ++g; }
-  s = 1 + (q - base);
-  t = g - s;
-}
 
 // ---- splitting ------------------------------------------------------------------------------
 // Two passes over X(r, k) = X[r * rs + k * ks] (R x K): the largest magnitude of every row
@@ -227,202 +193,6 @@ __global__ void __launch_bounds__(256) slice_kernel(int R, int K, int Kpad, cons
     }
     o[sidx * plane16] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
   }
-}
-
-// ---- the product ----------------------------------------------------------------------------
-
-__global__ void __launch_bounds__(THREADS, 1)
-tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
-               int K, int ksplit, const int* __restrict__ ea, const int* __restrict__ eb, double alpha, double beta,
-               double* __restrict__ C, int64_t ldc, double* __restrict__ part, int lower, int* __restrict__ err,
-               const int32_t* __restrict__ done, unsigned long long wait_ns) {
-  extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2];
-  __shared__ uint32_t tmem_slot;
-  __shared__ volatile int abort_flag;
-
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  if (lower && m0 + BM <= n0) return;               // tile entirely above the diagonal
-  if (done && *done) return;
-  // K range of this CTA (split K over gridDim.z: FP64 partial tiles, reduced by tc_reduce_kernel)
-  const int kz0 = blockIdx.z * ksplit;
-  const int Kz = min(K, kz0 + ksplit) - kz0;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
-
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < STAGES; ++i) {
-      mbar_init(smem_u32(&full_bar[i]), 1);
-      mbar_init(smem_u32(&empty_bar[i]), 1);
-    }
-    for (int i = 0; i < 2; ++i) {
-      mbar_init(smem_u32(&accf_bar[i]), 1);
-      mbar_init(smem_u32(&acce_bar[i]), EPI_WARPS);
-    }
-    abort_flag = 0;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
-  if (warp == EPI_WARPS) {                           // TMEM for two accumulators
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = tmem_slot;
-
-  const int nchunks = Kz > 0 ? (Kz + KC - 1) / KC : 0;
-  const int units = nchunks * NPAIRS;
-
-  if (warp == EPI_WARPS) {
-    if (lane == 0) {
-      // ---- loads and products (one thread) ----
-      int total_steps = 0;
-      for (int c = 0; c < nchunks; ++c) total_steps += (min(Kz, (c + 1) * KC) - c * KC + BK - 1) / BK * NPAIRS;
-      int g_load = 0, g_mma = 0;
-      int lu = 0, lk = 0;                            // load cursor: unit, step within it
-      auto unit_steps = [&](int u) {
-        const int c = u / NPAIRS;
-        return (min(Kz, (c + 1) * KC) - c * KC + BK - 1) / BK;
-      };
-      bool ok = true;
-      for (int u = 0; u < units && ok; ++u) {
-        const int buf = u & 1;
-        if (u >= 2 && !mbar_wait(smem_u32(&acce_bar[buf]), ((u >> 1) - 1) & 1, &abort_flag, err, wait_ns)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const int nst = unit_steps(u);
-        for (int kk = 0; kk < nst; ++kk) {
-          while (g_load < total_steps && g_load < g_mma + STAGES) {
-            const int st = g_load % STAGES;
-            if (g_load >= STAGES &&
-                !mbar_wait(smem_u32(&empty_bar[st]), ((g_load / STAGES) - 1) & 1, &abort_flag, err, wait_ns)) {
-              ok = false;
-              break;
-            }
-            int s, t;
-            pair_of(lu % NPAIRS, s, t);
-            const int k0 = kz0 + (lu / NPAIRS) * KC + lk * BK;
-            const uint32_t fb = smem_u32(&full_bar[st]);
-            mbar_expect_tx(fb, STAGE_BYTES);
-            tma_load_3d(base + st * STAGE_BYTES, &mapA, k0, m0, s - 1, fb);
-            tma_load_3d(base + st * STAGE_BYTES + TILE_BYTES, &mapB, k0, n0, t - 1, fb);
-            ++g_load;
-            if (++lk == unit_steps(lu)) { lk = 0; ++lu; }
-          }
-          if (!ok) break;
-          const int st = g_mma % STAGES;
-          if (!mbar_wait(smem_u32(&full_bar[st]), (g_mma / STAGES) & 1, &abort_flag, err, wait_ns)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t a0 = base + st * STAGE_BYTES, b0 = a0 + TILE_BYTES;
-#pragma unroll
-          for (int sub = 0; sub < BK / 16; ++sub)    // 16 BF16 = 32 bytes along K per MMA
-            mma_bf16(tmem + buf * BN, smem_desc(a0 + sub * 32), smem_desc(b0 + sub * 32),
-                     (kk > 0 || sub > 0) ? 1u : 0u);
-          mma_commit(smem_u32(&empty_bar[st]));      // the stage is free once these products finish
-          ++g_mma;
-        }
-        if (!ok) break;
-        mma_commit(smem_u32(&accf_bar[buf]));        // the accumulator is complete
-      }
-      if (!ok) {
-        abort_flag = 1;
-        // bounded waits for this CTA's own products and copies still in flight (the full bound,
-        // whatever the main loop's limit)
-        volatile int keep_waiting = 0;
-        if (g_mma > 0) {
-          const int st = (g_mma - 1) % STAGES;
-          mbar_wait(smem_u32(&empty_bar[st]), ((g_mma - 1) / STAGES) & 1, &keep_waiting, err);
-        }
-        for (int g = g_mma; g < g_load; ++g)
-          mbar_wait(smem_u32(&full_bar[g % STAGES]), (g / STAGES) & 1, &keep_waiting, err);
-      }
-    }
-  } else {
-    // ---- drain accumulators (warps 0-7) ----
-    // The products of one weight class g = s + t in one K-chunk are summed exactly as integers
-    // (at most 8 of them, each |.| <= 2^24: the sum fits int32), then added once to the FP64
-    // accumulators of the tile, kept in shared memory (column-major, conflict-free rows).
-    const int lg = warp & 3;                         // TMEM lanes 32 lg .. 32 lg + 31 = tile rows
-    const int cg = warp >> 2;                        // columns 64 cg .. 64 cg + 63
-    double* facc = reinterpret_cast<double*>(smem_raw + (base - smem_u32(smem_raw)) + STAGES * STAGE_BYTES);
-    const int trow = 32 * lg + lane;
-#pragma unroll 8
-    for (int j = 0; j < 64; ++j) facc[(cg * 64 + j) * BM + trow] = 0.0;
-    int gacc[64];
-#pragma unroll
-    for (int j = 0; j < 64; ++j) gacc[j] = 0;
-    for (int u = 0; u < units; ++u) {
-      const int buf = u & 1;
-      // one decision per warp: the TMEM loads below are warp-collective
-      if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&accf_bar[buf]), (u >> 1) & 1, &abort_flag, err, wait_ns)))
-        break;
-      tc_fence_after();
-      const uint32_t taddr = tmem + (uint32_t)(buf * BN + cg * 64) + ((uint32_t)(32 * lg) << 16);
-      uint32_t r[32];
-      WC_TMEM_LD32(taddr, r);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-      for (int j = 0; j < 32; ++j) gacc[j] += __float2int_rn(__uint_as_float(r[j]));   // exact integers
-      WC_TMEM_LD32(taddr + 32, r);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&acce_bar[buf]));
-#pragma unroll
-      for (int j = 0; j < 32; ++j) gacc[32 + j] += __float2int_rn(__uint_as_float(r[j]));
-      // the class ends with this unit: a new chunk, a new g, or the last unit
-      int s, t;
-      pair_of(u % NPAIRS, s, t);
-      bool last_of_class = (u + 1 == units) || ((u + 1) % NPAIRS == 0);
-      if (!last_of_class) {
-        int s2, t2;
-        pair_of((u + 1) % NPAIRS, s2, t2);
-        last_of_class = (s2 + t2 != s + t);
-      }
-      if (last_of_class) {
-        const double w = scalbn(1.0, -(7 * (s + t) - 2));
-#pragma unroll
-        for (int j = 0; j < 64; ++j) {
-          double* f = facc + (cg * 64 + j) * BM + trow;
-          *f = fma(w, (double)gacc[j], *f);
-          gacc[j] = 0;
-        }
-      }
-    }
-    if (!abort_flag) {
-      const int row = m0 + trow;
-      if (row < M) {
-        const int er = ea[row];
-#pragma unroll 4
-        for (int j = 0; j < 64; ++j) {
-          const int col = n0 + cg * 64 + j;
-          if (col < N) {
-            const double a = facc[(cg * 64 + j) * BM + trow];
-            if (part) {                              // partial tile of this K range
-              part[(int64_t)blockIdx.z * M * N + row + (int64_t)col * M] = scalbn(a, er + eb[col]);
-            } else {
-              const double v = alpha * scalbn(a, er + eb[col]);
-              double* cp = C + (int64_t)row + (int64_t)col * ldc;
-              *cp = (beta == 0.0) ? v : v + beta * *cp;
-            }
-          }
-        }
-      }
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (warp == EPI_WARPS)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
 // ---- the product, class-accumulator form -------------------------------------------------------
@@ -742,8 +512,8 @@ inline int kpad_of(int K) { return (K + BK - 1) / BK * BK; }
 }  // namespace
 
 // split-K partial tiles: at most this many doubles (the split is used only when the tiles are
-// fewer than the SMs, so nz M N <= about 2 x SMs x BM x BN)
-constexpr size_t kPartElems = (size_t)320 * BM * BN;
+// fewer than the SMs, so nz M N stays within a few SMs' worth of 128 x 64 tiles)
+constexpr size_t kPartElems = (size_t)320 * 128 * 128;
 
 size_t tc_gemm_work_bytes(int M, int N, int K) {
   const size_t kp = (size_t)kpad_of(K > 0 ? K : 1);
