@@ -460,6 +460,25 @@ sdp_status sdp_gemm_f64_tc(void* stream, int32_t tA, int32_t tB, int32_t M, int3
                            const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                            int64_t ldc, void* work, size_t work_bytes);
 
+/* Inverse or Cholesky factor of a symmetric positive definite matrix, as the Newton solve forms
+ * its preconditioner core (Section 6: C = tau^2 Sigma + beta^{-1} B^T B in the d-space, or the
+ * m-space K, is inverted once per Newton solve so that every PCG application is one product).
+ *   A      n x n, column-major, device; only the lower triangle is read.
+ *          mode 0: overwritten with A^{-1} (both triangles);
+ *          mode 1: overwritten with the Cholesky factor L (A = L L^T, lower, upper zeroed).
+ *   Linv   mode 1 only, NULL or n x n device: L^{-1} (lower, upper zeroed).
+ *   coop   1: for n <= 1024, one cooperative launch over the whole GPU (blocked right-looking
+ *          Cholesky, L^{-1} by block forward substitution and L^{-T} L^{-1}, advanced together
+ *          in 32-wide block steps); 0, larger n, or a device without cooperative launches: the
+ *          chain of one-CTA diagonal-block factorisations and FP64 products.
+ *   work   device scratch of sdp_spd_inverse_work_bytes(n) bytes, 256-byte aligned.
+ * FP64 throughout.  Returns after the work on `stream` has completed; SDP_ENUMERIC when a pivot
+ * is not positive and finite (A is not SPD to working precision; the output is then not
+ * meaningful), SDP_EINVAL for bad arguments. */
+size_t sdp_spd_inverse_work_bytes(int32_t n);
+sdp_status sdp_spd_inverse(void* stream, int32_t n, double* A, double* Linv, int32_t mode, int32_t coop, void* work,
+                           size_t work_bytes);
+
 /* Limit in nanoseconds of every wait of the main loop of the tensor-core product (the TMA
  * copies, the products and the drain of an accumulator, each an mbarrier wait bounded by
  * %globaltimer), process-wide, for the products launched after the call; 0 restores the

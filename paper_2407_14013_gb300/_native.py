@@ -81,6 +81,8 @@ EXPORTS = {
                                   c_void_p, c_int64, c_double, c_void_p, c_int64, c_void_p, c_size_t]),
     "sdp_gemm_tn_lp": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, ctypes.c_float, c_void_p, c_int64,
                                  c_void_p, c_int64, c_void_p, c_int64, c_void_p]),
+    "sdp_spd_inverse_work_bytes": (c_size_t, [c_int32]),
+    "sdp_spd_inverse": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_size_t]),
     "sdp_debug_copy": (c_int32, [c_void_p, c_int32, c_void_p, c_int64]),
     "sdp_set_profiling": (c_int32, [c_void_p, c_int32]),
     "sdp_adjoint_dense_noalloc": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
@@ -266,6 +268,15 @@ def sdp_gemm_tn_lp(stream: int, tf32: bool, M: int, N: int, K: int, alpha: float
     lib = load()
     st = lib.sdp_gemm_tn_lp(c_void_p(stream), int(tf32), M, N, K, alpha, c_void_p(A), lda, c_void_p(B), ldb,
                             c_void_p(C), ldc, c_void_p(err_word))
+    if st != SDP_OK:
+        raise SdpError(st, lib.sdp_last_error(None).decode())
+
+
+def sdp_spd_inverse(stream: int, n: int, A: int, Linv: int, mode: int, coop: bool, work: int, work_bytes: int) -> None:
+    """mode 0: A := A^{-1}; mode 1: A := L (A = L L^T), Linv := L^{-1} when non-zero (device pointers)."""
+    lib = load()
+    st = lib.sdp_spd_inverse(c_void_p(stream), n, c_void_p(A), c_void_p(Linv or None), mode, int(coop),
+                             c_void_p(work), work_bytes)
     if st != SDP_OK:
         raise SdpError(st, lib.sdp_last_error(None).decode())
 

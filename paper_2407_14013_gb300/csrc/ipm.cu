@@ -404,7 +404,8 @@ sdp_status max_step(Ctx& c, const double* D, double f, double* a, int* sweeps) {
   shift_identity_kernel<<<nb(nn), IT, 0, c.st>>>(c.n, 1.0 / f, w->M2, w->Eg);   // Eg = I + M / f
   *c.L += 2;
   CUI(cudaMemsetAsync(w->status, 0, sizeof(int32_t), c.st));
-  CUI(spd_cholesky(c.st, c.n, w->Eg, nullptr, w->chw, w->chw_elems, h->s64.ws, h->s64.ws_elems, w->status, c.L));
+  CUI(spd_cholesky(c.st, c.n, w->Eg, nullptr, w->chw, w->chw_elems, h->s64.ws, h->s64.ws_elems, w->status, c.L,
+                   !h->no_coop));
   int32_t st_h = 0;
   CUI(cudaMemcpyAsync(&st_h, w->status, sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
   CUI(cudaStreamSynchronize(c.st));
@@ -422,7 +423,8 @@ sdp_status max_step(Ctx& c, const double* D, double f, double* a, int* sweeps) {
     shift_identity_kernel<<<nb(nn), IT, 0, c.st>>>(c.n, f * *a, w->M2, w->Eg);
     ++*c.L;
     CUI(cudaMemsetAsync(w->status, 0, sizeof(int32_t), c.st));
-    CUI(spd_cholesky(c.st, c.n, w->Eg, nullptr, w->chw, w->chw_elems, h->s64.ws, h->s64.ws_elems, w->status, c.L));
+    CUI(spd_cholesky(c.st, c.n, w->Eg, nullptr, w->chw, w->chw_elems, h->s64.ws, h->s64.ws_elems, w->status, c.L,
+                   !h->no_coop));
     int32_t ok = 0;
     CUI(cudaMemcpyAsync(&ok, w->status, sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
     CUI(cudaStreamSynchronize(c.st));
@@ -580,7 +582,8 @@ sdp_status scaling(Ctx& c, const double* X, const double* S, int* sweeps) {
   // ---- NT scaling: X = L L^T, L^T S L = U Gamma U^T, G = L U Gamma^{-1/4}, W = G G^T
   CUI(cudaMemsetAsync(w->status, 0, sizeof(int32_t), c.st));
   CUI(cudaMemcpyAsync(w->L, X, bytes, cudaMemcpyDeviceToDevice, c.st));
-  CUI(spd_cholesky(c.st, n, w->L, w->Linv, w->chw, w->chw_elems, h->s64.ws, h->s64.ws_elems, w->status, c.L));
+  CUI(spd_cholesky(c.st, n, w->L, w->Linv, w->chw, w->chw_elems, h->s64.ws, h->s64.ws_elems, w->status, c.L,
+                   !h->no_coop));
   CUI(gemm(c, false, false, S, w->L, w->M1));
   CUI(gemm(c, true, false, w->L, w->M1, w->T));
   int sw = 0;

@@ -250,8 +250,11 @@ void sparse_sumsq(cudaStream_t st, const SparseA& S, double* out, double* scratc
 // In-place inverse of an SPD matrix (n x n, column-major, ld = n) through its Cholesky factor;
 // work must hold spd_inverse_work(n) doubles.
 size_t spd_inverse_work(int n);
+// n <= 1024 with allow_coop: one cooperative launch (falls back to the launch chain when the
+// cooperative launch is not possible).
 cudaError_t spd_inverse(cudaStream_t st, int n, double* A, double* work, size_t work_elems,
-                        double* gemm_ws, size_t gemm_ws_elems, int32_t* status, int64_t* launches);
+                        double* gemm_ws, size_t gemm_ws_elems, int32_t* status, int64_t* launches,
+                        bool allow_coop = true);
 // A[j, i] = A[i, j] for i > j (n x n, column-major): the upper triangle from the lower.
 void lower_to_full(cudaStream_t st, int n, double* A, int64_t* launches);
 // The same for large n with 512-wide outer panels: the panel solves, trailing updates, the
@@ -264,10 +267,12 @@ struct TcCtx {
 };
 size_t spd_inverse_tc_work(int n);
 cudaError_t spd_inverse_tc(cudaStream_t st, int n, double* A, double* work, size_t work_elems, double* gemm_ws,
-                           size_t gemm_ws_elems, const TcCtx* tc, int32_t* status, int64_t* launches);
-// Cholesky A = L L^T (L into A, upper zeroed) and Linv = L^{-1}; same workspace.
+                           size_t gemm_ws_elems, const TcCtx* tc, int32_t* status, int64_t* launches,
+                           bool allow_coop = true);
+// Cholesky A = L L^T (L into A, upper zeroed) and Linv = L^{-1} (NULL: factor only); same workspace.
 cudaError_t spd_cholesky(cudaStream_t st, int n, double* A, double* Linv, double* work, size_t work_elems,
-                         double* gemm_ws, size_t gemm_ws_elems, int32_t* status, int64_t* launches);
+                         double* gemm_ws, size_t gemm_ws_elems, int32_t* status, int64_t* launches,
+                         bool allow_coop = true);
 
 // ---- eigh.cu: symmetric eigen-decomposition (parallel cyclic Jacobi, FP64) ------------------
 // A (n x n, symmetric, destroyed) = V diag(lam) V^T; stops when ||offdiag A||_F <= tol ||A||_F

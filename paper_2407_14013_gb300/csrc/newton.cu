@@ -612,9 +612,9 @@ cudaError_t spd_inverse_any(sdp_handle* h, cudaStream_t st, int dim, double* P, 
     tc.work = h->tcw;
     tc.bytes = h->tcw_bytes;
     tc.err = h->tc_err;
-    return spd_inverse_tc(st, dim, P, h->gj_work, h->gj_work_elems, ws, ws_elems, &tc, status, L);
+    return spd_inverse_tc(st, dim, P, h->gj_work, h->gj_work_elems, ws, ws_elems, &tc, status, L, !h->no_coop);
   }
-  return spd_inverse(st, dim, P, h->gj_work, h->gj_work_elems, ws, ws_elems, status, L);
+  return spd_inverse(st, dim, P, h->gj_work, h->gj_work_elems, ws, ws_elems, status, L, !h->no_coop);
 }
 
 // Y = A^T(u) as a full n x n matrix (DENSE kind).
