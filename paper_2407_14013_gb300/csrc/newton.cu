@@ -654,6 +654,15 @@ cudaError_t pack_apply_dense(sdp_handle* h, Space& S, cudaStream_t st, int r, co
   return cudaGetLastError();
 }
 
+// The dense d-space preconditioner apply runs as one cooperative launch.
+bool pc_coop_on(const sdp_handle* h) {
+  return h->space == 1 && !h->lin && h->kind == SDP_A_DENSE_SVEC && h->coop_pc && !h->no_coop;
+}
+
+// Inside the PCG loop the update x += alpha p, r -= alpha Ap runs in the last block of the
+// operator's finishing kernel, or, with the cooperative preconditioner apply, inside that launch.
+double* fuse_x(const sdp_handle* h, Space& S) { return h->fuse && !pc_coop_on(h) ? S.x : nullptr; }
+
 // out = M pin (mode 1 also computes alpha) or out = g - M pin (mode 0, g != NULL), in FP64.
 sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* out, const double* gsub, int mode) {
   const int n = h->n, m = h->m, r = h->r, d = h->d;
@@ -688,7 +697,7 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
     CU(pack_apply_dense(h, S, st, r, S.Up, Q, done, L));               // A(svec(E Y E + sym(Up Q^T)))
     launch_ap_finish<double>(st, m, d, n, r, S.partA, h->SA, nullptr, S.Vs, S.H, S.Dv, pin, gsub, out, mode, S.ctl,
                              h->dotbuf, h->counter, L, nullptr, 0, h->lin,   // + tau^-2 delta p_u
-                             h->fuse ? S.x : nullptr, S.rv);
+                             fuse_x(h, S), S.rv);
   } else if (h->kind == SDP_A_SPARSE_COO) {
     // Y = A^T(p_u) kept as its pattern values; E Y E only at the pattern positions
     sparse_posval(st, h->sp, pu, S.ypos, done, L);
@@ -703,7 +712,7 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
     sparse_apply_pos(st, h->sp, n, m, r, S.zpos, S.Up, Q, S.partA, done, L);   // A(E Y E + sym(Up Q^T))
     launch_ap_finish<double>(st, m, d, n, r, S.partA, 1, nullptr, S.Vs, S.H, S.Dv, pin, gsub, out, mode, S.ctl,
                              h->dotbuf, h->counter, L, nullptr, 0, h->lin,   // + tau^-2 delta p_u
-                             h->fuse ? S.x : nullptr, S.rv);
+                             fuse_x(h, S), S.rv);
   } else {
     launch_diag_scale_rows<double>(st, n, r, pu, S.Vs, S.Tm, done, L);  // A^T(p_u) Q = diag(p_u) Q
     CU(gemm_big(h, st, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, S.ws, S.ws_elems, L, 0, done));
@@ -711,7 +720,7 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
     join(h, 0, 2);
     launch_ap_finish<double>(st, m, d, n, r, S.partA, rows_gemv_slabs(n, n), S.Up, S.Vs, S.H, S.Dv, pin, gsub, out,
                              mode, S.ctl, h->dotbuf, h->counter, L, nullptr, 0, nullptr,
-                             h->fuse ? S.x : nullptr, S.rv);
+                             fuse_x(h, S), S.rv);
   }
   return SDP_OK;
 }
@@ -750,7 +759,7 @@ sdp_status apply_operator_mixed(sdp_handle* h, Space& S, const double* pin, doub
     join(h, 0, 2);
     launch_ap_finish<double>(st, m, d, n, r, nullptr, 0, S.Up, S.Vs, S.H, S.Dv, pin, gsub, out, mode, S.ctl,
                              h->dotbuf, h->counter, L, M.partA, S32, nullptr,
-                             h->fuse ? S.x : nullptr, S.rv);
+                             fuse_x(h, S), S.rv);
     return SDP_OK;
   }
   // side branch: the FP64 rows with B, beside the FP32 A E A^T chain on the main stream
@@ -805,7 +814,7 @@ sdp_status apply_operator_mixed(sdp_handle* h, Space& S, const double* pin, doub
   }
   join(h, 0, 2);
   launch_mixed_finish(st, m, d, M.partA, SA, M.partBv, rows_gemv_slabs(m, d), M.partBu, rows_gemv_slabs(d, m), S.Dv, pin,
-                      gsub, out, mode, S.ctl, h->dotbuf, h->counter, L, h->fuse ? S.x : nullptr, S.rv);
+                      gsub, out, mode, S.ctl, h->dotbuf, h->counter, L, fuse_x(h, S), S.rv);
   return SDP_OK;
 }
 
@@ -852,10 +861,13 @@ sdp_status apply_precond(sdp_handle* h, Space& S, const double* rin, double* zou
       launch_diag_zv(st, m, d, n, r, S.H, rin, S.Dv, zout, S.ctl, L);      // z_v = D^{-1}(B^T z_u - r_v)
       launch_pc_zu_dot<double>(st, m, d, 0, nullptr, 2, rin, zout, mode, S.ctl, h->dotbuf, h->counter, L, nullptr, h->fuse ? S.p : nullptr);
     }
-  } else if (h->space == 1 && !h->lin && h->kind == SDP_A_DENSE_SVEC && h->coop_pc && !h->no_coop) {
-    // the three products and the dot in one cooperative launch (grid barriers between them)
-    CU(launch_pc_dense_d_coop(st, m, d, S.Bt, S.Pinv, S.B, rin, zout, S.sd, h->dotbuf, mode, S.ctl,
-                              h->fuse ? S.p : nullptr, L));
+  } else if (pc_coop_on(h)) {
+    // the three products and the dot in one cooperative launch (grid barriers between them); in
+    // the PCG loop it also takes the update of x and r (the operator's finishing kernel skips it)
+    const bool upd = h->fuse && mode == 1 && rin == S.rv;
+    CU(launch_pc_dense_d_coop(st, m, d, S.Bt, S.Pinv, S.B, upd ? S.rv : const_cast<double*>(rin), zout, S.sd,
+                              h->dotbuf, mode, S.ctl, h->fuse ? S.p : nullptr, upd ? S.x : nullptr,
+                              upd ? S.Ap : nullptr, L));
   } else if (h->space == 1) {
     if (h->lin) {   // linear block: s = r_v - B^T (Lam^{-1} r_u), z_u = Lam^{-1}(r_u - B z_v)
       launch_lin_div(st, m, rin, h->lin_lam, S.wm, S.ctl, L);

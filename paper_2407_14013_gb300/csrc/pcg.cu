@@ -773,30 +773,66 @@ __global__ void slack_grad_out_kernel(int m, const double* __restrict__ dv, cons
 // block LDL^T inverse of P = [beta I, B; B^T, -D]):
 //   s = r_v - beta^{-1} B^T r_u,  z_v = -C^{-1} s,  z_u = beta^{-1} (r_u - B z_v),
 // then <r, z> (mode 0: rz; mode 1: beta_pcg = <r_new, z_new> / <r, z>) and, with pf, p = z + beta p.
-// Three products that depend on each other, on L2-resident matrices (B^T, C^{-1}, B): one warp per
-// output row, grid-wide barriers between them instead of four launches.  Sums in a fixed order.
+// With ux (mode 1 inside the PCG loop) the launch first does the PCG update x += alpha p,
+// r -= alpha Ap with ||r||^2 and the stop test, so that no single block of the operator's
+// finishing kernel walks the whole vectors.  Three products that depend on each other, on
+// L2-resident matrices (B^T, C^{-1}, B): one warp per output row, grid-wide barriers between the
+// steps.  Every block reduces the per-block partial sums itself, in block order, so all blocks
+// take the same decisions from bit-identical scalars; only block 0 writes the control block.
 __global__ void __launch_bounds__(256)
 pc_dense_d_coop_kernel(int m, int d, const double* __restrict__ Bt, const double* __restrict__ Pinv,
-                       const double* __restrict__ B, const double* __restrict__ rv, double* __restrict__ z,
+                       const double* __restrict__ B, double* __restrict__ rv, double* __restrict__ z,
                        double* __restrict__ sd, double* __restrict__ part, int mode, PcgCtl* __restrict__ ctl,
-                       double* __restrict__ pf) {
+                       double* __restrict__ pf, double* __restrict__ ux, const double* __restrict__ Ap) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   if (ctl->done) return;                     // uniform: set only by earlier launches
   __shared__ double sh[32];
+  const int G = (int)gridDim.x, bid = (int)blockIdx.x;
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  const int gt = (int)(blockIdx.x * blockDim.x + threadIdx.x), nthr = (int)(gridDim.x * blockDim.x);
+  const int nt = m + d;
+  // the scalars this launch needs, read before block 0 writes any of them
   const double ib = 1.0 / ctl->beta_pc;
+  const double rz_old = ctl->rz;
+  if (ux) {
+    const double alpha = ctl->alpha, tol2 = ctl->tol2;
+    const int iters = ctl->iters, max_iters = ctl->max_iters;
+    double acc = 0.0;
+    for (int q = gt; q < nt; q += nthr) {
+      ux[q] = fma(alpha, pf[q], ux[q]);
+      const double rr = fma(-alpha, Ap[q], rv[q]);
+      rv[q] = rr;
+      acc = fma(rr, rr, acc);
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[G + bid] = acc;
+    grid.sync();
+    double rr = 0.0;
+    for (int q = threadIdx.x; q < G; q += blockDim.x) rr += __ldcg(part + G + q);
+    rr = block_sum(rr, sh);
+    int stop = -1;
+    if (!isfinite(rr)) stop = 5;
+    else if (rr <= tol2) stop = 0;
+    else if (iters + 1 >= max_iters) stop = 4;
+    if (bid == 0 && threadIdx.x == 0) {
+      ctl->rr = rr;
+      ctl->iters = iters + 1;
+      if (stop >= 0) { ctl->status = stop; ctl->done = 1; }
+    }
+    if (stop >= 0) return;                   // uniform: every block reduced the same partials
+  }
   const double* ru = rv;
   const double* rvv = rv + m;
   // s = r_v - beta^{-1} B^T r_u
   for (int i = gw; i < d; i += nw) {
     const double* row = Bt + (int64_t)i * m;
     double acc = 0.0;
-    for (int k = lane; k < m; k += 32) acc = fma(row[k], ru[k], acc);
+    for (int k = lane; k < m; k += 32) acc = fma(row[k], __ldcg(ru + k), acc);
     acc = warp_sum(acc);
-    if (lane == 0) sd[i] = rvv[i] - ib * acc;
+    if (lane == 0) sd[i] = __ldcg(rvv + i) - ib * acc;
   }
   grid.sync();
   // z_v = -C^{-1} s, and its part of <r, z>
@@ -808,7 +844,7 @@ pc_dense_d_coop_kernel(int m, int d, const double* __restrict__ Bt, const double
     acc = warp_sum(acc);
     if (lane == 0) {
       z[m + i] = -acc;
-      dot = fma(rvv[i], -acc, dot);
+      dot = fma(__ldcg(rvv + i), -acc, dot);
     }
   }
   grid.sync();
@@ -819,30 +855,27 @@ pc_dense_d_coop_kernel(int m, int d, const double* __restrict__ Bt, const double
     for (int k = lane; k < d; k += 32) acc = fma(row[k], __ldcg(z + m + k), acc);
     acc = warp_sum(acc);
     if (lane == 0) {
-      const double zu = ib * (ru[j] - acc);
+      const double u = __ldcg(ru + j);
+      const double zu = ib * (u - acc);
       z[j] = zu;
-      dot = fma(ru[j], zu, dot);
+      dot = fma(u, zu, dot);
     }
   }
   dot = block_sum(dot, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = dot;
+  if (threadIdx.x == 0) part[bid] = dot;
   grid.sync();
-  if (blockIdx.x != 0) return;
   double rz = 0.0;
-  for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) rz += __ldcg(part + q);
+  for (int q = threadIdx.x; q < G; q += blockDim.x) rz += __ldcg(part + q);
   rz = block_sum(rz, sh);
-  if (threadIdx.x == 0) {
-    if (!isfinite(rz)) { ctl->status = 5; ctl->done = 1; }
+  const bool ok = isfinite(rz);
+  const double beta = mode == 0 ? 0.0 : rz / rz_old;
+  if (bid == 0 && threadIdx.x == 0) {
+    if (!ok) { ctl->status = 5; ctl->done = 1; }
     if (mode == 0) { ctl->rz = rz; ctl->beta = 0.0; }
-    else { ctl->rz_new = rz; ctl->beta = rz / ctl->rz; ctl->rz = rz; }
+    else { ctl->rz_new = rz; ctl->beta = beta; ctl->rz = rz; }
   }
-  if (pf && mode == 1) {                     // p = z + beta p (block 0)
-    __syncthreads();
-    if (ctl->done) return;
-    const double beta = ctl->beta;
-    const int nt = m + d;
-    for (int q = threadIdx.x; q < nt; q += blockDim.x) pf[q] = fma(beta, pf[q], __ldcg(z + q));
-  }
+  if (pf && mode == 1 && ok)                 // p = z + beta p, every block its slice
+    for (int q = gt; q < nt; q += nthr) pf[q] = fma(beta, pf[q], __ldcg(z + q));
 }
 
 }  // namespace
@@ -1124,15 +1157,15 @@ int pc_dense_coop_blocks() {
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pc_dense_d_coop_kernel, 256, 0) == cudaSuccess && per > 0)
-      blocks = g_num_sms * std::min(per, 4);
+      blocks = std::min(g_num_sms * std::min(per, 2), 512);   // the partial sums take 2 x blocks of dotbuf
     cudaGetLastError();
   }
   return blocks;
 }
 
 cudaError_t launch_pc_dense_d_coop(cudaStream_t st, int m, int d, const double* Bt, const double* Pinv,
-                                   const double* B, const double* rv, double* z, double* sd, double* part, int mode,
-                                   PcgCtl* ctl, double* pf, int64_t* launches) {
+                                   const double* B, double* rv, double* z, double* sd, double* part, int mode,
+                                   PcgCtl* ctl, double* pf, double* ux, const double* Ap, int64_t* launches) {
   const int blocks = pc_dense_coop_blocks();
   if (blocks <= 0) return cudaErrorNotSupported;
   cudaLaunchConfig_t cfg = {};
@@ -1145,7 +1178,8 @@ cudaError_t launch_pc_dense_d_coop(cudaStream_t st, int m, int d, const double* 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, pc_dense_d_coop_kernel, m, d, Bt, Pinv, B, rv, z, sd, part, mode, ctl, pf);
+  cudaError_t e =
+      cudaLaunchKernelEx(&cfg, pc_dense_d_coop_kernel, m, d, Bt, Pinv, B, rv, z, sd, part, mode, ctl, pf, ux, Ap);
   if (e == cudaSuccess && launches) ++*launches;
   return e;
 }

@@ -79,12 +79,14 @@ void launch_slack_grad_rhs(cudaStream_t st, int m, const double* dv, const doubl
 void launch_slack_grad_out(cudaStream_t st, int m, const double* dv, const double* dw, const double* dy,
                            const double* gv, const double* gw, double* ov, double* ow, int64_t* launches);
 // The dense kind's d-space preconditioner apply in one cooperative launch (B^T r_u, C^{-1} s, B z_v,
-// <r, z>, and with pf the p update); part: at least pc_dense_coop_blocks() doubles.  Returns
-// cudaErrorNotSupported where the device has no cooperative launch.
+// <r, z>, and with pf the p update); with ux (mode 1) it first does the PCG update x += alpha p,
+// rv -= alpha Ap and the stop test (rv is written only then).  part: at least
+// 2 pc_dense_coop_blocks() doubles.  Returns cudaErrorNotSupported where the device has no
+// cooperative launch.
 int pc_dense_coop_blocks();
 cudaError_t launch_pc_dense_d_coop(cudaStream_t st, int m, int d, const double* Bt, const double* Pinv,
-                                   const double* B, const double* rv, double* z, double* sd, double* part, int mode,
-                                   PcgCtl* ctl, double* pf, int64_t* launches);
+                                   const double* B, double* rv, double* z, double* sd, double* part, int mode,
+                                   PcgCtl* ctl, double* pf, double* ux, const double* Ap, int64_t* launches);
 void launch_to_float(cudaStream_t st, int cnt, const double* src, float* dst, const int32_t* done, int64_t* launches);
 void launch_sym_copy(cudaStream_t st, int n, const double* g, double* out, int64_t* launches);
 void launch_ctl_reset(cudaStream_t st, PcgCtl* dst, const PcgCtl* src, int max_iters, int64_t* launches);

@@ -25,18 +25,35 @@ namespace {
 
 constexpr int NB = 32;
 
-// 1/v by Newton's iteration for the reciprocal, r <- r + r (1 - v r), started from the FP32
-// reciprocal (relative error below 2^-22: two steps bring it to the FP64 rounding level, so r is
-// within an ulp or so of 1/v, exact when 1/v is a power of two).  A pivot's reciprocal sits on
-// the critical path of the one-CTA factorisation below, where the four dependent FMAs are much
-// shorter than a full-precision division.  Outside the FP32 range: the division.
+// 1/v for a positive normal v by Newton's iteration for the reciprocal, r <- r + r (1 - v r), from
+// a seed built without FP64 arithmetic: the FP32 reciprocal of v's leading 24 significand bits
+// (rcp.approx, relative error about 2^-22 with the truncation), with v's exponent applied to it in
+// the integer domain.  Two steps bring the error to the FP64 rounding level (within an ulp or so;
+// exact when 1/v is a power of two).  On GB300 every FP64 operation carries a long latency, and a
+// pivot's reciprocal sits on the critical path of the one-CTA factorisation below: four dependent
+// FMAs are much shorter than a full-precision division.  Pivots with exponents near the ends of the
+// range take the division.
 __device__ __forceinline__ double recip_newton(double v) {
-  if (!(fabs(v) > 1e-30 && fabs(v) < 1e30)) return 1.0 / v;
-  double r = (double)__frcp_rn((float)v);
-  double e = fma(-v, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-v, r, 1.0);
-  return fma(r, e, r);
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e < 4 || e > 2040) return 1.0 / v;
+  const float mant = __int_as_float(0x3F800000 | (int)((b >> 29) & 0x7FFFFF));   // in [1, 2)
+  float rm;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rm) : "f"(mant));                      // in (0.5, 1]
+  const int fb = __float_as_int(rm);
+  const long long de = (long long)(((fb >> 23) & 0xFF) - 127 + 2046 - e);     // exponent of rm 2^(1023 - e)
+  double r = __longlong_as_double((de << 52) | ((long long)(fb & 0x7FFFFF) << 29) | (b & (1ll << 63)));
+  double q = fma(-v, r, 1.0);
+  r = fma(r, q, r);
+  q = fma(-v, r, 1.0);
+  return fma(r, q, r);
+}
+
+// A pivot is usable when it is positive and finite; tested on its bits (integer operations), so
+// the check stays off the FP64 pipe.
+__device__ __forceinline__ bool pivot_ok(double v) {
+  const long long b = __double_as_longlong(v);
+  return b > 0 && ((b >> 52) & 0x7FF) != 0x7FF;
 }
 
 // Factor the w x w diagonal block at k0 (already updated by earlier blocks): L_KK into the
@@ -44,14 +61,14 @@ __device__ __forceinline__ double recip_newton(double v) {
 //
 // GB300 issues FP64 arithmetic at 2 lane-operations per SM per clock and a warp instruction
 // costs its full width even with lanes masked off, so this routine, which runs on one SM,
-// enumerates exactly the active entries of each step and spends one FMA on each.  Step p:
-//   (a) l_i = S_ip / S_pp for i > p (one warp),
-//   (b) the LDL^T update S_ij -= l_i S_jp (p < j <= i) and the inverse sweep X~_ij -= l_i X~_pj
-//       (i > p >= j),
+// enumerates exactly the active entries of each step.  Step p (one barrier) does
+//   the LDL^T update S_ij -= l_i S_jp (p < j <= i) and the inverse sweep X~_ij -= l_i X~_pj
+//   (i > p >= j), with l_i = S_ip / S_pp formed by each thread from the pivot's reciprocal,
 // so that X~ = L~^{-1} for the unit lower factor L~ = [l]; then L = L~ D^{1/2} and
-// L^{-1} = D^{-1/2} X~ with D = diag(S_pp).  The lower pairs are tabled column by column, so
-// the pairs of step p are a suffix of the table whose first entry is the next pivot
-// (p+1, p+1): thread 0 updates it first and takes its reciprocal while the rest of the step runs.
+// L^{-1} = D^{-1/2} X~ with D = diag(S_pp).  The step's latency is the chain of the next pivot
+// (its update, its reciprocal), so the lower pairs are tabled column by column: the pairs of
+// step p are a suffix of the table whose first entry is the next pivot (p+1, p+1), and thread 0
+// takes it first while the rest of the step runs.
 //
 // Li gets L_KK^{-1} with leading dimension ldl; X2 (may be NULL) a second copy with ldx2.  A is
 // read through L2 (another CTA of a cooperative launch may have just written the block).  Every
@@ -60,7 +77,7 @@ __device__ void chol_block_dev(int64_t n, int k0, int w, double* __restrict__ A,
                                int64_t ldl, double* __restrict__ X2, int64_t ldx2, int32_t* __restrict__ status) {
   __shared__ double S[NB][NB + 1];
   __shared__ double X[NB][NB + 1];
-  __shared__ double inv[NB], dsq[NB], rdsq[NB], lcol[NB];
+  __shared__ double inv[NB], dsq[NB], rdsq[NB];
   __shared__ unsigned char ti[NB * (NB + 1) / 2], tj[NB * (NB + 1) / 2];
   __shared__ int bad;
   const int ww = w * w;
@@ -78,34 +95,31 @@ __device__ void chol_block_dev(int64_t n, int k0, int w, double* __restrict__ A,
   __syncthreads();
   if (threadIdx.x == 0) {
     const double piv = S[0][0];
-    if (!(piv > 0.0) || !isfinite(piv)) bad = 1;
-    inv[0] = (piv > 0.0 && isfinite(piv)) ? recip_newton(piv) : 1.0;
+    const bool ok = pivot_ok(piv);
+    if (!ok) bad = 1;
+    inv[0] = ok ? recip_newton(piv) : 1.0;
   }
   __syncthreads();
-  for (int p = 0; p < w; ++p) {
+  for (int p = 0; p < w - 1; ++p) {
     const int k = w - 1 - p;
-    if (k == 0) break;
-    if (threadIdx.x < k) {
-      const int i = p + 1 + threadIdx.x;
-      lcol[i] = S[i][p] * inv[p];
-    }
-    __syncthreads();
+    const double ip = inv[p];
     const int start = (p + 1) * w - (p + 1) * p / 2;   // off(p + 1)
     const int cnt_a = k * (k + 1) / 2;                 // pairs with j > p
     const int cnt = cnt_a + k * (p + 1);               // plus the k x (p + 1) block of the sweep
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
       if (t < cnt_a) {
         const int i = ti[start + t], j = tj[start + t];
-        const double v = fma(-lcol[i], S[j][p], S[i][j]);
+        const double v = fma(-(S[i][p] * ip), S[j][p], S[i][j]);
         S[i][j] = v;
         if (t == 0) {                      // (p+1, p+1): the next pivot is final now
-          if (!(v > 0.0) || !isfinite(v)) bad = 1;
-          inv[p + 1] = (v > 0.0 && isfinite(v)) ? recip_newton(v) : 1.0;
+          const bool ok = pivot_ok(v);
+          if (!ok) bad = 1;
+          inv[p + 1] = ok ? recip_newton(v) : 1.0;
         }
       } else {
         const int u = t - cnt_a;
         const int i = p + 1 + u % k, j = u / k;
-        X[i][j] = fma(-lcol[i], X[p][j], X[i][j]);
+        X[i][j] = fma(-(S[i][p] * ip), X[p][j], X[i][j]);
       }
     }
     __syncthreads();
