@@ -10,6 +10,9 @@
 // 32 x 8 for the n x r factors) and the grid is filled by splitting a long K across CTAs
 // when the M x N tile count is small; the K-slices write partial tiles to scratch and the
 // last slice of each tile adds them in a fixed order (results are bitwise reproducible).
+#include <mutex>
+#include <unordered_map>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -202,6 +205,17 @@ cudaError_t launch(cudaStream_t st, bool tA, bool tB, int M, int N, int K, doubl
 }  // namespace
 
 int g_num_sms = 152;
+
+cudaError_t raise_dyn_smem(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> limit;
+  std::lock_guard<std::mutex> lock(mu);
+  int& cur = limit[func];
+  if (bytes <= cur) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
 
 cudaError_t gemm_f64(cudaStream_t st, bool tA, bool tB, int M, int N, int K, double alpha,
                      const double* A, int64_t lda, const double* B, int64_t ldb, double beta,

@@ -10,6 +10,10 @@
 namespace wc {
 
 extern int g_num_sms;
+// Raise a kernel's limit of dynamic shared memory to at least `bytes`, never lowering it, under a
+// lock: handles of different sizes set it from several host threads, and a limit lowered by one
+// of them between another's set and launch would fail that launch.
+cudaError_t raise_dyn_smem(const void* func, int bytes);
 
 // ---- gemm_f64.cu -----------------------------------------------------------------------------
 // C = alpha op(A) op(B) + beta C (column-major).  ws: split-K partial tiles, its last 16 KB the

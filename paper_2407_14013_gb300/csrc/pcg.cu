@@ -769,6 +769,71 @@ __global__ void slack_grad_out_kernel(int m, const double* __restrict__ dv, cons
   ow[i] = dw[i] * (-dy[i] - gw[i]);
 }
 
+// y_i = <row i of M, v> for i < rows (M row-major, leading dimension ld), this CTA's share, with
+// every output passed to out(i, y_i) by one thread.  The rows spread over the whole grid: the
+// CTA's 8 warps form groups of g warps (g = the grid's warps per row, a power of two <= 8), group
+// q of CTA b takes rows (t G + b) (8 / g) + q, and the 32 g lanes of a group stride over the row
+// with four independent accumulators (on GB300 a dependent FP64 FMA waits about 140 clocks and an
+// L2 load several hundred, so one warp walking a long row alone would set the time).  v (written
+// by other blocks of the launch) is read through L2, once per CTA into shared memory when it fits.
+// The partial sums are combined in a fixed order.
+constexpr int kStageMax = 4096;   // vectors up to this length are staged in shared memory
+
+template <typename Out>
+__device__ void cta_rows_dot(int rows, int len, const double* __restrict__ M, int64_t ld,
+                             const double* __restrict__ vg, Out out, double* sh /* >= 8 doubles */,
+                             double* vs /* kStageMax doubles of shared memory */) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int G = (int)gridDim.x;
+  int g = (G * 8) / max(rows, 1);
+  g = g >= 8 ? 8 : g >= 4 ? 4 : g >= 2 ? 2 : 1;
+  const int gpc = 8 / g, q = warp / g, wi = warp % g, step = 32 * g;
+  const int slots = (rows + gpc - 1) / gpc;
+  // v is read by every row: once per CTA into shared memory (all loads issued before the stores)
+  const double* v = vg;
+  if (len <= kStageMax && (int)blockIdx.x < slots) {
+    for (int k0 = threadIdx.x; k0 < len; k0 += 8 * blockDim.x) {
+      double t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = k0 + u * blockDim.x;
+        t[u] = k < len ? __ldcg(vg + k) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = k0 + u * blockDim.x;
+        if (k < len) vs[k] = t[u];
+      }
+    }
+    __syncthreads();
+    v = vs;
+  }
+  for (int t = blockIdx.x; t < slots; t += G) {       // the same trip count in every thread of the CTA
+    const int i = t * gpc + q;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    if (i < rows) {
+      const double* row = M + (int64_t)i * ld;
+      int k = wi * 32 + lane;
+      for (; k + 3 * step < len; k += 4 * step) {
+        a0 = fma(row[k], v[k], a0);
+        a1 = fma(row[k + step], v[k + step], a1);
+        a2 = fma(row[k + 2 * step], v[k + 2 * step], a2);
+        a3 = fma(row[k + 3 * step], v[k + 3 * step], a3);
+      }
+      for (; k < len; k += step) a0 = fma(row[k], v[k], a0);
+    }
+    const double acc = warp_sum((a0 + a1) + (a2 + a3));
+    if (lane == 0) sh[warp] = acc;
+    __syncthreads();
+    if (wi == 0 && lane == 0 && i < rows) {
+      double y = 0.0;
+      for (int w = 0; w < g; ++w) y += sh[q * g + w];
+      out(i, y);
+    }
+    __syncthreads();
+  }
+}
+
 // The d-space preconditioner apply of the dense kind in one cooperative launch (Section 6: the
 // block LDL^T inverse of P = [beta I, B; B^T, -D]):
 //   s = r_v - beta^{-1} B^T r_u,  z_v = -C^{-1} s,  z_u = beta^{-1} (r_u - B z_v),
@@ -789,9 +854,6 @@ pc_dense_d_coop_kernel(int m, int d, const double* __restrict__ Bt, const double
   if (ctl->done) return;                     // uniform: set only by earlier launches
   __shared__ double sh[32];
   const int G = (int)gridDim.x, bid = (int)blockIdx.x;
-  const int lane = threadIdx.x & 31;
-  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   const int gt = (int)(blockIdx.x * blockDim.x + threadIdx.x), nthr = (int)(gridDim.x * blockDim.x);
   const int nt = m + d;
   // the scalars this launch needs, read before block 0 writes any of them
@@ -826,41 +888,25 @@ pc_dense_d_coop_kernel(int m, int d, const double* __restrict__ Bt, const double
   }
   const double* ru = rv;
   const double* rvv = rv + m;
+  __shared__ double shw[8];
+  __shared__ double vstage[kStageMax];
   // s = r_v - beta^{-1} B^T r_u
-  for (int i = gw; i < d; i += nw) {
-    const double* row = Bt + (int64_t)i * m;
-    double acc = 0.0;
-    for (int k = lane; k < m; k += 32) acc = fma(row[k], __ldcg(ru + k), acc);
-    acc = warp_sum(acc);
-    if (lane == 0) sd[i] = __ldcg(rvv + i) - ib * acc;
-  }
+  cta_rows_dot(d, m, Bt, m, ru, [&](int i, double y) { sd[i] = __ldcg(rvv + i) - ib * y; }, shw, vstage);
   grid.sync();
   // z_v = -C^{-1} s, and its part of <r, z>
   double dot = 0.0;
-  for (int i = gw; i < d; i += nw) {
-    const double* row = Pinv + (int64_t)i * d;
-    double acc = 0.0;
-    for (int k = lane; k < d; k += 32) acc = fma(row[k], __ldcg(sd + k), acc);
-    acc = warp_sum(acc);
-    if (lane == 0) {
-      z[m + i] = -acc;
-      dot = fma(__ldcg(rvv + i), -acc, dot);
-    }
-  }
+  cta_rows_dot(d, d, Pinv, d, sd, [&](int i, double y) {
+    z[m + i] = -y;
+    dot = fma(__ldcg(rvv + i), -y, dot);
+  }, shw, vstage);
   grid.sync();
   // z_u = beta^{-1} (r_u - B z_v), and its part of <r, z>
-  for (int j = gw; j < m; j += nw) {
-    const double* row = B + (int64_t)j * d;
-    double acc = 0.0;
-    for (int k = lane; k < d; k += 32) acc = fma(row[k], __ldcg(z + m + k), acc);
-    acc = warp_sum(acc);
-    if (lane == 0) {
-      const double u = __ldcg(ru + j);
-      const double zu = ib * (u - acc);
-      z[j] = zu;
-      dot = fma(u, zu, dot);
-    }
-  }
+  cta_rows_dot(m, d, B, d, z + m, [&](int j, double y) {
+    const double u = __ldcg(ru + j);
+    const double zu = ib * (u - y);
+    z[j] = zu;
+    dot = fma(u, zu, dot);
+  }, shw, vstage);
   dot = block_sum(dot, sh);
   if (threadIdx.x == 0) part[bid] = dot;
   grid.sync();

@@ -289,7 +289,7 @@ void sparse_EY(cudaStream_t st, const SparseA& S, int n, const double* ypos, con
 cudaError_t sparse_prepare(int n) {
   const size_t smem = (size_t)n * sizeof(double);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(pos_dots_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return raise_dyn_smem((const void*)pos_dots_col_kernel, (int)smem);
 }
 
 cudaError_t sparse_pos_dots_col(cudaStream_t st, const SparseA& S, int n, const double* E, const double* F,

@@ -207,9 +207,16 @@ fx_AiQ_kernel(const int2* __restrict__ Ad, const int* __restrict__ ea, int n, in
   int2* Qd = smi + Lp;                              // digits of Q, n x r row-major
   __shared__ int fq[r];
   const int il = blockIdx.x, i = i0 + il;
-  const int4* src = reinterpret_cast<const int4*>(Ad + (int64_t)i * Lp);   // Lp even: 16-byte rows
-  int4* dst = reinterpret_cast<int4*>(As);
-  for (int64_t q = threadIdx.x; q < Lp / 2; q += blockDim.x) dst[q] = __ldg(src + q);
+  // the row (Lp even: 16-byte aligned rows) by asynchronous 16-byte copies, all issued before
+  // any is waited for, while the digits of Q are made
+  {
+    const char* src = reinterpret_cast<const char*>(Ad + (int64_t)i * Lp);
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(As);
+    for (int64_t q = threadIdx.x; q < Lp / 2; q += blockDim.x)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + (uint32_t)(q * 16)), "l"(src + q * 16)
+                   : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
   if (threadIdx.x < r) fq[threadIdx.x] = INT_MIN;
   __syncthreads();
   for (int q = threadIdx.x; q < n * r; q += blockDim.x) {   // exponents of the columns of Q
@@ -224,6 +231,7 @@ fx_AiQ_kernel(const int2* __restrict__ Ad, const int* __restrict__ ea, int n, in
     const int f = fq[j] == INT_MIN ? 0 : fq[j];
     Qd[q] = fx_split(fx_fixed(Q[b + (int64_t)j * n], 0, f));
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
   const int e = ea[i];
   for (int a = threadIdx.x; a < n; a += blockDim.x) {
@@ -283,7 +291,7 @@ bool dense_AiQ(cudaStream_t st, const double* A, int n, int i0, int mb, int r, c
   switch (r) {
 #define WC_AIQ_CASE(R)                                                                              \
     case R:                                                                                         \
-      cudaFuncSetAttribute(dense_AiQ_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+      raise_dyn_smem((const void*)dense_AiQ_kernel<R>, (int)smem);                                 \
       dense_AiQ_kernel<R><<<mb, AQ_THREADS, smem, st>>>(A, n, N, i0, mb, Q, G);                      \
       break;
     WC_AIQ_CASE(1) WC_AIQ_CASE(2) WC_AIQ_CASE(3) WC_AIQ_CASE(4) WC_AIQ_CASE(5) WC_AIQ_CASE(6)
@@ -307,7 +315,7 @@ bool fx_AiQ(cudaStream_t st, const int2* Ad, const int* ea, int n, int64_t Lp, i
   switch (r) {
 #define WC_FXAIQ_CASE(R)                                                                            \
     case R:                                                                                         \
-      cudaFuncSetAttribute(fx_AiQ_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+      raise_dyn_smem((const void*)fx_AiQ_kernel<R>, (int)smem);                                 \
       fx_AiQ_kernel<R><<<mb, AQ_THREADS, smem, st>>>(Ad, ea, n, Lp, i0, mb, Q, G);                    \
       break;
     WC_FXAIQ_CASE(1) WC_FXAIQ_CASE(2) WC_FXAIQ_CASE(3) WC_FXAIQ_CASE(4) WC_FXAIQ_CASE(5) WC_FXAIQ_CASE(6)
