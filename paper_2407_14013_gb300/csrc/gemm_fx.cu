@@ -27,9 +27,13 @@ constexpr int KC = 128;
 constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
 constexpr unsigned long long INF_BITS = 0x7FF0000000000000ull;
 
+// PRE = 1: A is given by its row digits (Dd[i K + k], exponents De[i]); PRE = 2: B by its column
+// digits (Dd[j K + k], exponents De[j]); the CTA then scans and splits only the other operand.
+template <int PRE>
 __global__ void __launch_bounds__(TB * TB)
 fx_gemm_kernel(int M, int N, int K, const double* __restrict__ A, int64_t lda, const double* __restrict__ B,
-               int64_t ldb, double* __restrict__ C, int64_t ldc, int lower, const int32_t* __restrict__ done) {
+               int64_t ldb, double* __restrict__ C, int64_t ldc, int lower, const int32_t* __restrict__ done,
+               const int2* __restrict__ Dd, const int* __restrict__ De) {
   if (done && *done) return;
   const int i0 = blockIdx.x * TB, j0 = blockIdx.y * TB;
   if (lower && i0 + TB - 1 < j0) return;            // tile strictly above the diagonal
@@ -45,7 +49,7 @@ fx_gemm_kernel(int M, int N, int K, const double* __restrict__ A, int64_t lda, c
     const int r = t & 15, part = t >> 4;
     const int gi = i0 + r;
     int e = INT_MIN;
-    if (gi < M)
+    if (gi < M && PRE != 1)
       for (int kb = part; kb < K; kb += 16 * UE) {
         unsigned long long b[UE];
 #pragma unroll
@@ -63,7 +67,7 @@ fx_gemm_kernel(int M, int N, int K, const double* __restrict__ A, int64_t lda, c
     const int c = t >> 4, kp = t & 15;
     const int gj = j0 + c;
     int f = INT_MIN;
-    if (gj < N)
+    if (gj < N && PRE != 2)
       for (int kb = kp; kb < K; kb += 16 * UE) {
         unsigned long long b[UE];
 #pragma unroll
@@ -82,12 +86,12 @@ fx_gemm_kernel(int M, int N, int K, const double* __restrict__ A, int64_t lda, c
       const int g = __shfl_xor_sync(0xffffffffu, f, o);
       f = max(f, g);
     }
-    if (kp == 0) eb[c] = f;
+    if (kp == 0) eb[c] = (PRE == 2) ? (gj < N ? De[gj] : INT_MIN) : f;
     __syncthreads();
     if (t < TB) {
       int m = INT_MIN;
       for (int p = 0; p < 16; ++p) m = max(m, ered[p][t]);
-      ea[t] = m;
+      ea[t] = (PRE == 1) ? (i0 + t < M ? De[i0 + t] : INT_MIN) : m;
     }
     __syncthreads();
   }
@@ -102,25 +106,41 @@ fx_gemm_kernel(int M, int N, int K, const double* __restrict__ A, int64_t lda, c
     {   // A chunk (lanes along i) and B chunk (lanes along k): all loads first, then the digits
       constexpr int US = KC * TB / (TB * TB);          // entries per thread per operand (8)
       double va[US], vb[US];
+      int2 da[US], db[US];
 #pragma unroll
       for (int u = 0; u < US; ++u) {
         const int q = t + u * TB * TB;
-        const int r = q & 15, k = q >> 4;
-        const int gi = i0 + r;
-        va[u] = (k < kc && gi < M && ea[r] != FX_BAD) ? A[gi + (int64_t)(k0 + k) * lda] : 0.0;
+        if (PRE == 1) {                                  // given digits, k contiguous per row
+          const int k = q % KC, r = q / KC;
+          const int gi = i0 + r;
+          da[u] = (k < kc && gi < M) ? Dd[(int64_t)gi * K + k0 + k] : make_int2(0, 0);
+        } else {
+          const int r = q & 15, k = q >> 4;
+          const int gi = i0 + r;
+          va[u] = (k < kc && gi < M && ea[r] != FX_BAD) ? A[gi + (int64_t)(k0 + k) * lda] : 0.0;
+        }
         const int kk = q % KC, c = q / KC;
         const int gj = j0 + c;
-        vb[u] = (kk < kc && gj < N && eb[c] != FX_BAD) ? B[(k0 + kk) + (int64_t)gj * ldb] : 0.0;
+        if (PRE == 2) db[u] = (kk < kc && gj < N) ? Dd[(int64_t)gj * K + k0 + kk] : make_int2(0, 0);
+        else vb[u] = (kk < kc && gj < N && eb[c] != FX_BAD) ? B[(k0 + kk) + (int64_t)gj * ldb] : 0.0;
       }
 #pragma unroll
       for (int u = 0; u < US; ++u) {
         const int q = t + u * TB * TB;
-        const int r = q & 15, k = q >> 4;
-        const int F = ea[r];
-        As[k][r] = fx_split((F == INT_MIN || F == FX_BAD) ? 0 : fx_fixed(va[u], 0, F));
+        if (PRE == 1) {
+          As[q % KC][q / KC] = da[u];
+        } else {
+          const int r = q & 15, k = q >> 4;
+          const int F = ea[r];
+          As[k][r] = fx_split((F == INT_MIN || F == FX_BAD) ? 0 : fx_fixed(va[u], 0, F));
+        }
         const int kk = q % KC, c = q / KC;
-        const int G = eb[c];
-        Bs[kk][c] = fx_split((G == INT_MIN || G == FX_BAD) ? 0 : fx_fixed(vb[u], 0, G));
+        if (PRE == 2) {
+          Bs[kk][c] = db[u];
+        } else {
+          const int G = eb[c];
+          Bs[kk][c] = fx_split((G == INT_MIN || G == FX_BAD) ? 0 : fx_fixed(vb[u], 0, G));
+        }
       }
     }
     __syncthreads();
@@ -150,13 +170,60 @@ fx_gemm_kernel(int M, int N, int K, const double* __restrict__ A, int64_t lda, c
 }  // namespace
 
 cudaError_t fx_gemm(cudaStream_t st, int M, int N, int K, const double* A, int64_t lda, const double* B, int64_t ldb,
-                    double* C, int64_t ldc, bool lower, const int32_t* done, int64_t* launches) {
+                    double* C, int64_t ldc, bool lower, const int32_t* done, int64_t* launches, int pre,
+                    const int2* Dd, const int* De) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  if (K < 0) return cudaErrorInvalidValue;
+  if (K < 0 || (pre != 0 && (!Dd || !De))) return cudaErrorInvalidValue;
   dim3 grid((M + TB - 1) / TB, (N + TB - 1) / TB);
-  fx_gemm_kernel<<<grid, TB * TB, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, lower ? 1 : 0, done);
+  const int lw = lower ? 1 : 0;
+  if (pre == 1) fx_gemm_kernel<1><<<grid, TB * TB, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, lw, done, Dd, De);
+  else if (pre == 2) fx_gemm_kernel<2><<<grid, TB * TB, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, lw, done, Dd, De);
+  else fx_gemm_kernel<0><<<grid, TB * TB, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, lw, done, Dd, De);
   if (launches) ++*launches;
   return cudaGetLastError();
+}
+
+namespace {
+
+// Exponent and digits of column j of M (n x n, column-major, n <= 512), one warp per column: the
+// same exponent (the column's largest) and digits fx_gemm_kernel forms for a B panel, so digits
+// made once can stand for that work in every product with M.
+__global__ void col_digits_kernel(int n, const double* __restrict__ M, int2* __restrict__ D, int* __restrict__ e) {
+  const int j = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (j >= n) return;                                  // whole warps
+  const int lane = threadIdx.x & 31;
+  constexpr int VL = 16;
+  double v[VL];
+#pragma unroll
+  for (int u = 0; u < VL; ++u) {
+    const int k = lane + 32 * u;
+    v[u] = k < n ? M[(int64_t)j * n + k] : 0.0;
+  }
+  int f = INT_MIN;
+#pragma unroll
+  for (int u = 0; u < VL; ++u) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v[u]) & ABS;
+    if (b >= INF_BITS) f = FX_BAD;
+    else if (b && f != FX_BAD) f = max(f, fx_expo_bits(b));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) f = max(f, __shfl_xor_sync(0xffffffffu, f, o));   // FX_BAD is the largest int
+  const bool zero = (f == INT_MIN || f == FX_BAD);
+#pragma unroll
+  for (int u = 0; u < VL; ++u) {
+    const int k = lane + 32 * u;
+    if (k < n) D[(int64_t)j * n + k] = zero ? make_int2(0, 0) : fx_split(fx_fixed(v[u], 0, f));
+  }
+  if (lane == 0) e[j] = f;
+}
+
+}  // namespace
+
+bool fx_col_digits(cudaStream_t st, int n, const double* M, int2* D, int* e, int64_t* launches) {
+  if (n <= 0 || n > 512) return false;
+  col_digits_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(n, M, D, e);
+  if (launches) ++*launches;
+  return true;
 }
 
 }  // namespace wc

@@ -23,6 +23,9 @@ struct Space {
   double *ypos = nullptr, *zpos = nullptr;     // SPARSE_COO: A^T(y) and E Y E at the pattern positions
   double *mw = nullptr, *mw1 = nullptr, *mw2 = nullptr;   // MINRES search directions
   int* fxe = nullptr;                          // exponents of the vectors of the integer passes over A
+  int2* Ed = nullptr;                          // digits of E's columns (made once per Newton solve)
+  int* eE = nullptr;                           // their exponents
+  bool ed_valid = false;                       // Ed, eE hold this solve's E
   double *x = nullptr, *rv = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr;
   double* ws = nullptr;                        // split-K GEMM scratch
   size_t ws_elems = 0;

@@ -123,9 +123,15 @@ int rows_gemvT_blocks(int64_t L, int esize);
 // rows_gemv<double> and rows_gemvT_unpack<double>, with an error within the FP64 dot-product bound.
 // C = A B (column-major, M x N x K, no transposes) from exact int64 sums of two-digit products
 // (gemm_fx.cu); `lower` writes only the entries i >= j.  Error within the FP64 dot-product bound
-// measured against the largest entry of each row of A and column of B.
+// measured against the largest entry of each row of A and column of B.  pre = 1: A is given by
+// its row digits (Dd[i K + k], exponents De[i]); pre = 2: B by its column digits (Dd[j K + k],
+// De[j]), as fx_col_digits makes them (the same bits as without them).
 cudaError_t fx_gemm(cudaStream_t st, int M, int N, int K, const double* A, int64_t lda, const double* B, int64_t ldb,
-                    double* C, int64_t ldc, bool lower, const int32_t* done, int64_t* launches);
+                    double* C, int64_t ldc, bool lower, const int32_t* done, int64_t* launches, int pre = 0,
+                    const int2* Dd = nullptr, const int* De = nullptr);
+// Digits of the columns of M (n x n, column-major, n <= 512; false otherwise): exponents e[j]
+// (2^e[j] > max_k |M_kj|) and int32 digit pairs D[j n + k], those fx_gemm forms for M's columns.
+bool fx_col_digits(cudaStream_t st, int n, const double* M, int2* D, int* e, int64_t* launches);
 int64_t fx_row_len(int64_t L);
 int fx_rows_gemv_slabs(int m, int64_t L);   // slab partial sums written by fx_rows_gemv
 void fx_split_rows(cudaStream_t st, const double* A, int m, int64_t L, int2* Ai, int* ea, int64_t* launches);

@@ -117,6 +117,10 @@ void carve_space(sdp_handle* h, Carver& c, Space& S) {
     S.partY = c.take<double>((size_t)h->GY * h->N);
   }
   if (h->fx) S.fxe = c.take<int>(2);
+  if (h->fx && n <= 512) {   // digits of E for the integer-digit E Y E
+    S.Ed = c.take<int2>(nn);
+    S.eE = c.take<int>(n);
+  }
   if (h->kind == SDP_A_SPARSE_COO) {
     S.ypos = c.take<double>(h->sp.npos);
     S.zpos = c.take<double>(h->sp.npos);
@@ -685,8 +689,9 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
     CU(gemm_f64(s1, false, false, n, r, n, 1.0, S.Y, n, Q, n, 0.0, S.Tm, n, h->ws_b[1], h->ws_b_elems, L, done));
     CU(gemm_f64(s1, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, h->ws_b[1], h->ws_b_elems, L, done));
     if (h->fx && n < kTcMin) {   // E Y E from exact integer sums (the integer pipe outruns the FP64 one)
-      CU(fx_gemm(st, n, n, n, S.E, n, S.Y, n, S.F, n, false, done, L));
-      CU(fx_gemm(st, n, n, n, S.F, n, S.E, n, S.Z, n, true, done, L));
+      const int pa = S.ed_valid ? 1 : 0, pb = S.ed_valid ? 2 : 0;   // E's digits made at setup
+      CU(fx_gemm(st, n, n, n, S.E, n, S.Y, n, S.F, n, false, done, L, pa, S.Ed, S.eE));
+      CU(fx_gemm(st, n, n, n, S.F, n, S.E, n, S.Z, n, true, done, L, pb, S.Ed, S.eE));
     } else {
       CU(gemm_f64(st, false, false, n, n, n, 1.0, S.E, n, S.Y, n, 0.0, S.F, n, S.ws, S.ws_elems, L, done));
       CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, S.ws_elems, L, done,
@@ -1102,6 +1107,9 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   // E = Ve Vs^T is symmetric: the lower triangle by the product, the upper by a mirror
   CU(gemm_big(h, st, false, true, n, n, n, 1.0, h->Ve, n, S.Vs, n, 0.0, S.E, n, S.ws, ws, L, GEMM_LOWER));
   lower_to_full(st, n, S.E, L);
+  // digits of E's columns (E is symmetric: its rows too) for every E Y E of this solve
+  S.ed_valid = S.Ed && h->fx && n < kTcMin && fx_col_digits(st, n, S.E, S.Ed, S.eE, L);
+  if (h->mixed) h->sin.ed_valid = S.ed_valid;
   split_sigma(st, n, r, h->lam_s, h->ctl, S.Dv, L);
 
   // ---- a3 products on a side stream, beside a2 (DENSE kind, FP64 MMA products): the right side

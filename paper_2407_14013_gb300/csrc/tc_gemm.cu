@@ -664,10 +664,10 @@ cudaError_t gemm_f64_tc_one(cudaStream_t st, bool tA, bool tB, int M, int N, int
   const int gm = (M + CBM - 1) / CBM, gn = (N + CBN - 1) / CBN;
   int tiles = gm * gn;
   if (flags & GEMM_LOWER) tiles = (tiles + gm) / 2;
-  // split K when the tiles leave SMs idle: about one CTA per SM, K ranges of >= 512
+  // split K when the tiles leave SMs idle: about one CTA per SM, K ranges of >= 256
   int nz = 1;
-  if (tiles < g_num_sms && K >= 2 * 512) {
-    nz = std::min((g_num_sms + tiles - 1) / tiles, K / 512);
+  if (tiles < g_num_sms && K >= 2 * 256) {
+    nz = std::min((g_num_sms + tiles - 1) / tiles, K / 256);
     while (nz > 1 && (size_t)nz * M * N > kPartElems) --nz;
   }
   int ksplit = K > 0 ? ((K + nz - 1) / nz + BK - 1) / BK * BK : 0;
