@@ -33,7 +33,7 @@ template <int PRE>
 __global__ void __launch_bounds__(TB * TB)
 fx_gemm_kernel(int M, int N, int K, const double* __restrict__ A, int64_t lda, const double* __restrict__ B,
                int64_t ldb, double* __restrict__ C, int64_t ldc, int lower, const int32_t* __restrict__ done,
-               const int2* __restrict__ Dd, const int* __restrict__ De) {
+               const int2* __restrict__ Dd, const int* __restrict__ De, FxPack pk) {
   if (done && *done) return;
   const int i0 = blockIdx.x * TB, j0 = blockIdx.y * TB;
   if (lower && i0 + TB - 1 < j0) return;            // tile strictly above the diagonal
@@ -159,26 +159,52 @@ fx_gemm_kernel(int M, int N, int K, const double* __restrict__ A, int64_t lda, c
   }
   acc += fx_value(T1, T2);
   const int gi = i0 + ti, gj = j0 + tj;
-  if (gi >= M || gj >= N || (lower && gi < gj)) return;
-  double v;
-  if (ra == FX_BAD || rb == FX_BAD) v = __longlong_as_double(0x7ff8000000000000ll);
-  else if (ra == INT_MIN || rb == INT_MIN) v = 0.0;
-  else v = ldexp(acc, ra + rb);
-  C[gi + (int64_t)gj * ldc] = v;
+  const bool act = gi < M && gj < N && !(lower && gi < gj);
+  double v = 0.0;
+  if (act) {
+    if (ra == FX_BAD || rb == FX_BAD) v = __longlong_as_double(0x7ff8000000000000ll);
+    else if (ra == INT_MIN || rb == INT_MIN) v = 0.0;
+    else v = ldexp(acc, ra + rb);
+  }
+  if (pk.out) {
+    // svec(C + sym(U Q^T)) at (gi, gj), gi >= gj, and the exponent of the packed vector, as
+    // svec_pack_plus_kernel forms them from C (same operations, same order)
+    int e = INT_MIN;
+    if (act) {
+      if (pk.U) {
+        double su = 0.0;
+        for (int k = 0; k < pk.r; ++k)
+          su += pk.U[gi + (int64_t)k * M] * pk.Q[gj + (int64_t)k * M] +
+                pk.Q[gi + (int64_t)k * M] * pk.U[gj + (int64_t)k * M];
+        v += 0.5 * su;
+      }
+      const double o = (gi == gj) ? v : v * WC_SQRT2;
+      pk.out[svec_index(M, gi, gj)] = o;
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(o) & ABS;
+      e = bits >= INF_BITS ? INT_MAX : (bits ? fx_expo_bits(bits) : INT_MIN);
+    }
+    if (pk.expo) {   // one atomic per warp (every thread of the tile is here)
+      e = __reduce_max_sync(0xffffffffu, e);
+      if ((t & 31) == 0 && e != INT_MIN) atomicMax(pk.expo, e);
+    }
+    return;
+  }
+  if (act) C[gi + (int64_t)gj * ldc] = v;
 }
 
 }  // namespace
 
 cudaError_t fx_gemm(cudaStream_t st, int M, int N, int K, const double* A, int64_t lda, const double* B, int64_t ldb,
                     double* C, int64_t ldc, bool lower, const int32_t* done, int64_t* launches, int pre,
-                    const int2* Dd, const int* De) {
+                    const int2* Dd, const int* De, const FxPack* pack) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  if (K < 0 || (pre != 0 && (!Dd || !De))) return cudaErrorInvalidValue;
+  if (K < 0 || (pre != 0 && (!Dd || !De)) || (pack && (M != N || !lower))) return cudaErrorInvalidValue;
   dim3 grid((M + TB - 1) / TB, (N + TB - 1) / TB);
   const int lw = lower ? 1 : 0;
-  if (pre == 1) fx_gemm_kernel<1><<<grid, TB * TB, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, lw, done, Dd, De);
-  else if (pre == 2) fx_gemm_kernel<2><<<grid, TB * TB, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, lw, done, Dd, De);
-  else fx_gemm_kernel<0><<<grid, TB * TB, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, lw, done, Dd, De);
+  const FxPack pk = pack ? *pack : FxPack{};
+  if (pre == 1) fx_gemm_kernel<1><<<grid, TB * TB, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, lw, done, Dd, De, pk);
+  else if (pre == 2) fx_gemm_kernel<2><<<grid, TB * TB, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, lw, done, Dd, De, pk);
+  else fx_gemm_kernel<0><<<grid, TB * TB, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, lw, done, Dd, De, pk);
   if (launches) ++*launches;
   return cudaGetLastError();
 }

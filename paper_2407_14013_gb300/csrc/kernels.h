@@ -126,9 +126,18 @@ int rows_gemvT_blocks(int64_t L, int esize);
 // measured against the largest entry of each row of A and column of B.  pre = 1: A is given by
 // its row digits (Dd[i K + k], exponents De[i]); pre = 2: B by its column digits (Dd[j K + k],
 // De[j]), as fx_col_digits makes them (the same bits as without them).
+// With pack (M == N, lower), C is not written: out gets svec(C + sym(U Q^T)) (U, Q: n x r, U may be
+// NULL) and *expo the largest exponent of it, as svec_pack_plus does from C (the same bits).
+struct FxPack {
+  const double* U = nullptr;
+  const double* Q = nullptr;
+  int r = 0;
+  double* out = nullptr;
+  int* expo = nullptr;
+};
 cudaError_t fx_gemm(cudaStream_t st, int M, int N, int K, const double* A, int64_t lda, const double* B, int64_t ldb,
                     double* C, int64_t ldc, bool lower, const int32_t* done, int64_t* launches, int pre = 0,
-                    const int2* Dd = nullptr, const int* De = nullptr);
+                    const int2* Dd = nullptr, const int* De = nullptr, const FxPack* pack = nullptr);
 // Digits of the columns of M (n x n, column-major, n <= 512; false otherwise): exponents e[j]
 // (2^e[j] > max_k |M_kj|) and int32 digit pairs D[j n + k], those fx_gemm forms for M's columns.
 bool fx_col_digits(cudaStream_t st, int n, const double* M, int2* D, int* e, int64_t* launches);

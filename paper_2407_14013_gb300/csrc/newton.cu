@@ -639,13 +639,15 @@ void adjoint_dense(sdp_handle* h, Space& S, const double* u, double* Y, const in
 // z = svec(Z + sym(U Q^T)) (U may be NULL), then partA = the slab partial sums of A(z) (DENSE
 // kind); on the integer path the packing kernel also gives the exponent of z
 cudaError_t pack_apply_dense(sdp_handle* h, Space& S, cudaStream_t st, int r, const double* U, const double* Q,
-                             const int32_t* done, int64_t* L) {
+                             const int32_t* done, int64_t* L, bool packed = false) {
   const int n = h->n;
   const double* z = S.zsvec;
   if (h->fx) {
-    cudaError_t e = cudaMemsetAsync(S.fxe + 1, 0x80, sizeof(int), st);   // below FX_NONE_MAX: no entry yet
-    if (e != cudaSuccess) return e;
-    svec_pack_plus<double>(st, n, r, S.Z, U, Q, S.zsvec, done, L, S.fxe + 1);
+    if (!packed) {   // else the E Y E product packed z and found its exponent
+      cudaError_t e = cudaMemsetAsync(S.fxe + 1, 0x80, sizeof(int), st);   // below FX_NONE_MAX: no entry yet
+      if (e != cudaSuccess) return e;
+      svec_pack_plus<double>(st, n, r, S.Z, U, Q, S.zsvec, done, L, S.fxe + 1);
+    }
     prof_begin(h, 1);
     fx_rows_gemv(st, h->a_fx, h->a_fx_e, h->m, h->N, z, S.fxe + 1, S.partA, done, L);
     prof_end(h);
@@ -688,18 +690,29 @@ sdp_status apply_operator(sdp_handle* h, Space& S, const double* pin, double* ou
     cudaStream_t s1 = fork(h, 1, 1);
     CU(gemm_f64(s1, false, false, n, r, n, 1.0, S.Y, n, Q, n, 0.0, S.Tm, n, h->ws_b[1], h->ws_b_elems, L, done));
     CU(gemm_f64(s1, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, h->ws_b[1], h->ws_b_elems, L, done));
+    bool packed = false;
     if (h->fx && n < kTcMin) {   // E Y E from exact integer sums (the integer pipe outruns the FP64 one)
       const int pa = S.ed_valid ? 1 : 0, pb = S.ed_valid ? 2 : 0;   // E's digits made at setup
       CU(fx_gemm(st, n, n, n, S.E, n, S.Y, n, S.F, n, false, done, L, pa, S.Ed, S.eE));
-      CU(fx_gemm(st, n, n, n, S.F, n, S.E, n, S.Z, n, true, done, L, pb, S.Ed, S.eE));
+      // the second product writes svec(E Y E + sym(Up Q^T)) and its exponent directly (no Z)
+      join(h, 0, 2);
+      CU(cudaMemsetAsync(S.fxe + 1, 0x80, sizeof(int), st));   // below FX_NONE_MAX: no entry yet
+      FxPack pk;
+      pk.U = S.Up;
+      pk.Q = Q;
+      pk.r = r;
+      pk.out = S.zsvec;
+      pk.expo = S.fxe + 1;
+      CU(fx_gemm(st, n, n, n, S.F, n, S.E, n, S.Z, n, true, done, L, pb, S.Ed, S.eE, &pk));
+      packed = true;
     } else {
       CU(gemm_f64(st, false, false, n, n, n, 1.0, S.E, n, S.Y, n, 0.0, S.F, n, S.ws, S.ws_elems, L, done));
       CU(gemm_f64(st, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, S.ws, S.ws_elems, L, done,
                   GEMM_LOWER));                                        // E Y E is symmetric: lower triangle
     }
-    join(h, 0, 2);
+    if (!packed) join(h, 0, 2);
     join(h, 1, 3);
-    CU(pack_apply_dense(h, S, st, r, S.Up, Q, done, L));               // A(svec(E Y E + sym(Up Q^T)))
+    CU(pack_apply_dense(h, S, st, r, S.Up, Q, done, L, packed));       // A(svec(E Y E + sym(Up Q^T)))
     launch_ap_finish<double>(st, m, d, n, r, S.partA, h->SA, nullptr, S.Vs, S.H, S.Dv, pin, gsub, out, mode, S.ctl,
                              h->dotbuf, h->counter, L, nullptr, 0, h->lin,   // + tau^-2 delta p_u
                              fuse_x(h, S), S.rv);
