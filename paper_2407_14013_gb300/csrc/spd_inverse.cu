@@ -266,26 +266,53 @@ __device__ void tile_unit(CoopSmem& sm, int R, int Cc, const double* P, int64_t 
                           const double* Q, int64_t ldq, bool qT, int qc, double* C, int64_t ldc, double sign,
                           bool accumulate) {
   const int t = threadIdx.x;
-  for (int idx = t; idx < R * NB; idx += blockDim.x) {
-    int r, k;
-    if (pT) { k = idx % NB; r = idx / NB; } else { r = idx % R; k = idx / R; }
-    double v = 0.0;
-    if (r < pr && k < pk) v = pT ? P[k + (int64_t)r * ldp] : P[r + (int64_t)k * ldp];
-    sm.P[r][k] = v;
+  // every load of the unit issued before any is stored (R NB, NB Cc <= 4 blockDim.x): one L2
+  // round trip instead of one per entry a thread stages
+  double pv[4], qv[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int idx = t + u * (int)blockDim.x;
+    pv[u] = 0.0;
+    if (idx < R * NB) {
+      int r, k;
+      if (pT) { k = idx % NB; r = idx / NB; } else { r = idx % R; k = idx / R; }
+      if (r < pr && k < pk) pv[u] = pT ? P[k + (int64_t)r * ldp] : P[r + (int64_t)k * ldp];
+    }
+    qv[u] = 0.0;
+    if (idx < NB * Cc) {
+      int k, c;
+      if (qT) { c = idx % Cc; k = idx / Cc; } else { k = idx % NB; c = idx / NB; }
+      if (k < pk && c < qc) qv[u] = qT ? Q[c + (int64_t)k * ldq] : Q[k + (int64_t)c * ldq];
+    }
   }
-  for (int idx = t; idx < NB * Cc; idx += blockDim.x) {
-    int k, c;
-    if (qT) { c = idx % Cc; k = idx / Cc; } else { k = idx % NB; c = idx / NB; }
-    double v = 0.0;
-    if (k < pk && c < qc) v = qT ? Q[c + (int64_t)k * ldq] : Q[k + (int64_t)c * ldq];
-    sm.Q[k][c] = v;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int idx = t + u * (int)blockDim.x;
+    if (idx < R * NB) {
+      int r, k;
+      if (pT) { k = idx % NB; r = idx / NB; } else { r = idx % R; k = idx / R; }
+      sm.P[r][k] = pv[u];
+    }
+    if (idx < NB * Cc) {
+      int k, c;
+      if (qT) { c = idx % Cc; k = idx / Cc; } else { k = idx % NB; c = idx / NB; }
+      sm.Q[k][c] = qv[u];
+    }
   }
   __syncthreads();
   {
+    // four independent FMA chains: on GB300 a dependent FP64 FMA waits about 140 clocks, so one
+    // chain of 32 would set the time of the unit
     const int r = t / Cc, c = t % Cc;
-    double acc = 0.0;
-#pragma unroll 8
-    for (int k = 0; k < NB; ++k) acc = fma(sm.P[r][k], sm.Q[k][c], acc);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll
+    for (int k = 0; k < NB; k += 4) {
+      a0 = fma(sm.P[r][k], sm.Q[k][c], a0);
+      a1 = fma(sm.P[r][k + 1], sm.Q[k + 1][c], a1);
+      a2 = fma(sm.P[r][k + 2], sm.Q[k + 2][c], a2);
+      a3 = fma(sm.P[r][k + 3], sm.Q[k + 3][c], a3);
+    }
+    const double acc = (a0 + a1) + (a2 + a3);
     if (r < pr && c < qc) {
       double* o = C + r + (int64_t)c * ldc;
       *o = accumulate ? fma(sign, acc, *o) : sign * acc;
