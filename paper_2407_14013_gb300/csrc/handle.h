@@ -63,6 +63,11 @@ struct Graph {
   cudaGraphExec_t exec = nullptr;
   int key[4] = {-1, -1, -1, -1};
   int64_t launches = 0;
+  // the whole PCG loop as one graph: a WHILE conditional node whose body is one iteration and
+  // whose condition a last kernel sets from the device stop flag (no host read between iterations)
+  cudaGraphExec_t wexec = nullptr;
+  int wkey[4] = {-1, -1, -1, -1};
+  int64_t wlaunches = 0;                // launches of one pass of the body
   size_t prof_first = 0, prof_last = 0;
   std::vector<ProfEntry> entries;
 };
@@ -111,6 +116,8 @@ struct sdp_handle {
   char* vs_mem[2] = {nullptr, nullptr};   // slices of the sorted eigenvectors Vs, made once per split:
   wc::TcSlices vs_sl[2];                  // [0] rows of Vs (op = Vs), [1] rows of Vs^T (op = Vs^T)
   bool no_coop = false;             // batched solves: no cooperative (grid-barrier) launches
+  bool while_ok = true;             // the device-side PCG loop graph can be built on this device
+  int* loop_guard = nullptr;        // passes of that loop (a bound independent of the stop flag)
   bool coop_pc = false;             // dense d-space preconditioner apply as one cooperative launch
   int64_t b_elems = 0;              // capacity of the explicit B = A Q (m x d)
   int64_t bt_elems = 0;             // capacity of B^T (d x m)

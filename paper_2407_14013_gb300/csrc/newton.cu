@@ -202,6 +202,7 @@ size_t carve(sdp_handle* h, char* base) {
   h->ctl_in = c.take<PcgCtl>(1);
   h->mctl = c.take<MinresCtl>(1);
   h->counter = c.take<unsigned int>(4);
+  h->loop_guard = c.take<int>(1);
   // one ticket per column block of the A^T pass (at most one block per 256 columns)
   h->gt_tickets = c.take<unsigned int>(h->kind == SDP_A_DENSE_SVEC ? (size_t)(h->N + 255) / 256 + 1 : 1);
   h->lam_s = c.take<double>(n);
@@ -958,10 +959,10 @@ sdp_status krylov_loop(sdp_handle* h, Space& S, bool mixed, bool minres) {
   }
   h->prof_entries.clear();
   h->prof_base = 0;
-  auto chunk = [&](cudaStream_t s_) -> sdp_status {
+  auto chunk = [&](cudaStream_t s_, int iters) -> sdp_status {
     cudaStream_t saved = h->st;
     h->st = s_;
-    for (int k = 0; k < every; ++k) {
+    for (int k = 0; k < iters; ++k) {
       h->cur_iter = k;
       if (minres) {
         // v = r2 / beta; y = M v; alfa; beta, rotation, stop; w and x (r1 = rv, r2 = z, v = p, y = Ap)
@@ -985,6 +986,67 @@ sdp_status krylov_loop(sdp_handle* h, Space& S, bool mixed, bool minres) {
     return SDP_OK;
   };
   const int key[4] = {h->r, h->d, h->space, every * 2 + (h->prof ? 1 : 0)};
+  // The whole loop as one graph: a WHILE conditional node around one iteration, its condition set
+  // on the device from the stop flag, so no host read between iterations and no iteration past the
+  // stop.  Built once per shape; where the device or the driver refuses it (capture or
+  // instantiation fails), the handle keeps the replays of `check_every` iterations below.
+  if (!h->ctl_host->done && h->opt.use_graph && !h->prof && !minres && h->while_ok) {
+    if (G.wexec && std::memcmp(key, G.wkey, sizeof(key)) != 0) {
+      cudaGraphExecDestroy(G.wexec);
+      G.wexec = nullptr;
+    }
+    if (!G.wexec) {
+      if (!h->cap_stream) CU(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+      const int64_t before = h->launches;
+      cudaGraph_t g = nullptr;
+      bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+      cudaGraphConditionalHandle hc{};
+      cudaGraph_t body = nullptr;
+      if (ok) ok = cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+      if (ok) {
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = hc;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cn;
+        ok = cudaGraphAddNode(&cn, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+        if (ok) body = cp.conditional.phGraph_out[0];
+      }
+      if (ok) ok = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
+                                                 cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        h->capturing = true;
+        sdp_status cs = chunk(h->cap_stream, 1);
+        if (cs == SDP_OK) launch_loop_cond(h->cap_stream, hc, S.ctl, h->loop_guard, L);
+        h->capturing = false;
+        cudaGraph_t out = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &out);
+        ok = cs == SDP_OK && ce == cudaSuccess;
+      }
+      if (ok) ok = cudaGraphInstantiate(&G.wexec, g, 0) == cudaSuccess;
+      if (g) cudaGraphDestroy(g);
+      G.wlaunches = h->launches - before;
+      h->launches = before;
+      if (!ok) {
+        cudaGetLastError();
+        if (G.wexec) cudaGraphExecDestroy(G.wexec);
+        G.wexec = nullptr;
+        h->while_ok = false;
+      } else {
+        std::memcpy(G.wkey, key, sizeof(key));
+      }
+    }
+    if (G.wexec) {
+      const int it0 = h->ctl_host->iters;
+      CU(cudaMemsetAsync(h->loop_guard, 0, sizeof(int), st));
+      CU(cudaGraphLaunch(G.wexec, st));
+      CU(cudaMemcpyAsync(h->ctl_host, S.ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
+      CU(cudaStreamSynchronize(st));
+      h->launches += 1 + G.wlaunches * std::max(1, h->ctl_host->iters - it0);
+      // a loop the guard ended without the stop flag continues below, replay by replay
+    }
+  }
   if (!h->ctl_host->done && h->opt.use_graph) {
     if (!G.exec || std::memcmp(key, G.key, sizeof(key)) != 0) {
       if (G.exec) { cudaGraphExecDestroy(G.exec); G.exec = nullptr; }
@@ -993,7 +1055,7 @@ sdp_status krylov_loop(sdp_handle* h, Space& S, bool mixed, bool minres) {
       const size_t prof_before = h->prof_entries.size();
       CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
       h->capturing = true;
-      sdp_status s = chunk(h->cap_stream);
+      sdp_status s = chunk(h->cap_stream, every);
       h->capturing = false;
       cudaGraph_t graph = nullptr;
       cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
@@ -1007,7 +1069,7 @@ sdp_status krylov_loop(sdp_handle* h, Space& S, bool mixed, bool minres) {
         h->prof_entries.resize(prof_before);
         CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
         h->capturing = true;
-        s = chunk(h->cap_stream);
+        s = chunk(h->cap_stream, every);
         h->capturing = false;
         ce = cudaStreamEndCapture(h->cap_stream, &graph);
       }
@@ -1034,7 +1096,7 @@ sdp_status krylov_loop(sdp_handle* h, Space& S, bool mixed, bool minres) {
       last = G.prof_last;
     } else {
       h->prof_entries.clear();
-      sdp_status s = chunk(st);
+      sdp_status s = chunk(st, every);
       if (s != SDP_OK) return s;
       last = h->prof_entries.size();
     }
@@ -1542,11 +1604,7 @@ extern "C" sdp_status sdp_set_linear_diag(sdp_handle* h, const double* delta) {
   }
   h->lin = delta;
   h->setup_valid = false;           // the preconditioner core depends on delta
-  for (auto& G : h->graph)          // captured graphs hold the old pointer
-    if (G.exec) {
-      cudaGraphExecDestroy(G.exec);
-      G.exec = nullptr;
-    }
+  wc_drop_graphs(h);                // captured graphs hold the old pointer
   return SDP_OK;
 }
 
@@ -1560,8 +1618,7 @@ extern "C" void sdp_destroy(sdp_handle* h) {
   for (auto& e : h->ev) cudaEventDestroy(e);
   for (auto& e : h->ev_phase)
     if (e) cudaEventDestroy(e);
-  for (auto& G : h->graph)
-    if (G.exec) cudaGraphExecDestroy(G.exec);
+  wc_drop_graphs(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (auto& a : h->aux)
     if (a) cudaStreamDestroy(a);
@@ -1574,9 +1631,14 @@ extern "C" void sdp_destroy(sdp_handle* h) {
 // Captured PCG graphs hold the launch forms chosen when they were captured (the cooperative
 // preconditioner apply or not): drop them when that choice changes.
 void wc_drop_graphs(sdp_handle* h) {
-  for (auto& G : h->graph)
+  for (auto& G : h->graph) {
     if (G.exec) {
       cudaGraphExecDestroy(G.exec);
       G.exec = nullptr;
     }
+    if (G.wexec) {
+      cudaGraphExecDestroy(G.wexec);
+      G.wexec = nullptr;
+    }
+  }
 }

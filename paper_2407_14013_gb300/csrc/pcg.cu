@@ -924,7 +924,22 @@ pc_dense_d_coop_kernel(int m, int d, const double* __restrict__ Bt, const double
     for (int q = gt; q < nt; q += nthr) pf[q] = fma(beta, pf[q], __ldcg(z + q));
 }
 
+// The condition of the device-side PCG loop (a WHILE graph node around one iteration): go on
+// while the stop flag is clear, and in any case for at most max_iters + 2 passes, counted here
+// independently of the other kernels, so that the loop ends even if no kernel ever set the flag.
+__global__ void loop_cond_kernel(cudaGraphConditionalHandle hc, const PcgCtl* __restrict__ ctl,
+                                 int* __restrict__ guard) {
+  const int passes = ++*guard;
+  cudaGraphSetConditional(hc, (!ctl->done && passes <= ctl->max_iters + 2) ? 1u : 0u);
+}
+
 }  // namespace
+
+void launch_loop_cond(cudaStream_t st, cudaGraphConditionalHandle hc, const PcgCtl* ctl, int* guard,
+                      int64_t* launches) {
+  loop_cond_kernel<<<1, 1, 0, st>>>(hc, ctl, guard);
+  if (launches) ++*launches;
+}
 
 template <typename T>
 void launch_ap_finish(cudaStream_t st, int m, int d, int n, int r, const T* partA, int S, const T* Up, const T* Vs,

@@ -83,6 +83,10 @@ void launch_slack_grad_out(cudaStream_t st, int m, const double* dv, const doubl
 // rv -= alpha Ap and the stop test (rv is written only then).  part: at least
 // 2 pc_dense_coop_blocks() doubles.  Returns cudaErrorNotSupported where the device has no
 // cooperative launch.
+// Last kernel of the body of the device-side PCG loop: sets the WHILE condition from the stop flag
+// (guard: a device counter of passes, zeroed before each launch of the loop).
+void launch_loop_cond(cudaStream_t st, cudaGraphConditionalHandle hc, const PcgCtl* ctl, int* guard,
+                      int64_t* launches);
 int pc_dense_coop_blocks();
 cudaError_t launch_pc_dense_d_coop(cudaStream_t st, int m, int d, const double* Bt, const double* Pinv,
                                    const double* B, double* rv, double* z, double* sd, double* part, int mode,
