@@ -121,7 +121,11 @@ typedef struct {
   int32_t r_hat;         /* r_fixed == 0: r = argmax_{i <= r_hat} lam_i/lam_{i+1} (Section 7)     */
   int32_t precision;     /* sdp_precision                                                       */
   int32_t precond_space; /* 0 = auto (the smaller of m and d), 1 = d x d complement C (Section 6),
-                            2 = m x m complement K = beta I + B D^{-1} B^T (same preconditioner) */
+                            2 = m x m complement K = beta I + B D^{-1} B^T (same preconditioner),
+                            3 = auto with a linear block (sdp_set_linear_diag): the m-space when
+                            fewer than d rows have tau^-2 delta_i <= 1e8 beta (rows the other
+                            slacks fix), else the d-space; without one, as 0.  3 reserves room
+                            for both complements (not for the DIAG kind) */
   int32_t max_pcg;       /* iteration cap                                                       */
   int32_t check_every;   /* PCG iterations between host reads of the stop flag (>= 1)            */
   int32_t beta_rule;     /* 0: beta = median(eig E)^2 * ||A||_F^2/m;  1: median(eig E)^2 (Section 7 as printed) */

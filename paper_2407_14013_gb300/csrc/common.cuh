@@ -129,7 +129,8 @@ struct PcgCtl {
   // split / setup scalars
   double tau, beta_pc, s_A;
   int32_t r, d;
-  int32_t pad0, pad1;
+  int32_t m_free;   // linear block: rows whose slack does not dominate (precond_space 3)
+  int32_t pad1;
 };
 
 }  // namespace wc

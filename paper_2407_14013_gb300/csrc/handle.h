@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <string>
 #include <vector>
 
@@ -74,6 +76,28 @@ struct Graph {
 
 
 struct IpmWork;
+
+// One NVTX range for the life of the object.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// NVTX ranges around the phases of a solve (header-only NVTX v3: nothing happens unless a tool
+// such as Nsight Systems is attached).  next() closes the current range and opens another; the
+// destructor closes the last one, also on an early return.
+struct NvtxPhase {
+  explicit NvtxPhase(const char* name) { nvtxRangePushA(name); }
+  void next(const char* name) {
+    nvtxRangePop();
+    nvtxRangePushA(name);
+  }
+  ~NvtxPhase() { nvtxRangePop(); }
+  NvtxPhase(const NvtxPhase&) = delete;
+  NvtxPhase& operator=(const NvtxPhase&) = delete;
+};
 
 }  // namespace wc
 

@@ -397,6 +397,7 @@ sdp_status lam_min(Ctx& c, const double* M, double* out, int* sweeps) {
 // The caller uses min(1, f sup); when I + M / f is positive definite (a Cholesky factorisation
 // succeeds) that is 1 and the eigenvalue is not needed, so +inf is returned.
 sdp_status max_step(Ctx& c, const double* D, double f, double* a, int* sweeps) {
+  NvtxRange nvtx_range("ipm step length");
   sdp_handle* h = c.h;
   IpmWork* w = c.w;
   const int64_t nn = (int64_t)c.n * c.n;
@@ -573,6 +574,7 @@ void fill_info(sdp_ipm_info* info, const Measures& M) {
 // G = L U Gamma^{-1/4}, W = G G^T, and eig(W) = (V, lam).  Both eigen-decompositions start from
 // the previous call's eigenvectors when there are any (the iterates move little along the path).
 sdp_status scaling(Ctx& c, const double* X, const double* S, int* sweeps) {
+  NvtxRange nvtx_range("ipm scaling point (eigen-decompositions)");
   sdp_handle* h = c.h;
   IpmWork* w = c.w;
   const int n = c.n;
@@ -629,6 +631,7 @@ sdp_status scaling(Ctx& c, const double* X, const double* S, int* sweeps) {
 }
 
 sdp_status step(Ctx& c, double* X, double* y, double* S, const Measures& Mz, sdp_ipm_info* info) {
+  NvtxRange nvtx_range("ipm predictor-corrector step");
   sdp_handle* h = c.h;
   IpmWork* w = c.w;
   const int n = c.n;
@@ -945,6 +948,7 @@ extern "C" sdp_status sdp_eigh(void* stream, int32_t n, double* A, double* V, do
 
 extern "C" sdp_status ipm_step(sdp_handle* h, const double* b, const double* C, double* X, double* y, double* S,
                                sdp_ipm_info* info) {
+  NvtxRange nvtx_range("ipm_step");
   sdp_status s = check_args(h, b, C, X, y, S);
   if (s != SDP_OK) return s;
   const auto t0 = std::chrono::steady_clock::now();
@@ -965,6 +969,7 @@ extern "C" sdp_status ipm_step(sdp_handle* h, const double* b, const double* C, 
 
 extern "C" sdp_status sdp_solve(sdp_handle* h, const double* b, const double* C, double* X, double* y, double* S,
                                 double gap_tol, int32_t max_iter, sdp_ipm_info* info) {
+  NvtxRange nvtx_range("sdp_solve");
   sdp_status s = check_args(h, b, C, X, y, S);
   if (s != SDP_OK) return s;
   if (!(gap_tol > 0.0) || max_iter < 0) return wc_fail(h, SDP_EINVAL, "bad gap_tol or max_iter");

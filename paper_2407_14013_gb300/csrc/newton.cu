@@ -39,6 +39,8 @@ static std::string g_setup_err;
 
 // products go to the tensor cores for n >= kTcMin and M N K >= kTcMinWork (all three >= 64)
 constexpr int kTcMin = 512;
+// a slack "fixes" its row of the linear block when tau^-2 delta_i exceeds this multiple of beta
+constexpr double kLinDominance = 1e8;
 constexpr double kTcMinWork = 134217728.0;   // 512^3
 constexpr int kFuseMax = 65536;              // PCG vectors short enough for one block's update
 
@@ -301,7 +303,9 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
     return fail(nullptr, SDP_EINVAL, "bad refinement options");
   const int r_max = opt.r_fixed > 0 ? opt.r_fixed : std::min(opt.r_hat, n - 1);
   if (r_max < 1 || r_max >= n) return fail(nullptr, SDP_EINVAL, "rank parameter out of range [1, n)");
-  if (opt.precond_space < 0 || opt.precond_space > 2) return fail(nullptr, SDP_EINVAL, "bad precond_space");
+  if (opt.precond_space < 0 || opt.precond_space > 3) return fail(nullptr, SDP_EINVAL, "bad precond_space");
+  if (opt.precond_space == 3 && prob->kind == SDP_A_DIAG)
+    return fail(nullptr, SDP_EINVAL, "precond_space 3 (the linear-block rule) needs a kind with a linear block");
   if (opt.pcg_start < 0 || opt.pcg_start > 1) return fail(nullptr, SDP_EINVAL, "bad pcg_start");
   if (opt.tc_products < 0 || opt.tc_products > 1) return fail(nullptr, SDP_EINVAL, "bad tc_products");
   if (opt.krylov < 0 || opt.krylov > 1) return fail(nullptr, SDP_EINVAL, "bad krylov");
@@ -403,13 +407,15 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
   h->r_max = r_max;
   h->d_max = dof(n, r_max);
   // d-space core (d x d) when d <= m, m-space core (m x m) otherwise, unless forced
-  h->pinv_dim = opt.precond_space == 1 ? h->d_max : opt.precond_space == 2 ? m : std::min(h->d_max, m);
+  h->pinv_dim = opt.precond_space == 1 ? h->d_max : opt.precond_space == 2 ? m
+              : opt.precond_space == 3 ? std::max(h->d_max, m) : std::min(h->d_max, m);
   if (opt.krylov == 1) h->pinv_dim = 0;   // MINRES: no preconditioner core
   // explicit B = A Q: DIAG forms its m-space core in closed form and its products with B from
   // Vs, so it needs B only for the d-space core (auto selects that only at r = 1, d = n)
   // SPARSE_COO reads B only to form the core (its products with B go through the pattern);
   // DENSE_SVEC streams B and B^T in every preconditioner application
-  const bool m_space_possible = opt.precond_space == 2 || (opt.precond_space == 0 && h->d_max > m);
+  const bool m_space_possible = opt.precond_space == 2 || opt.precond_space == 3 ||
+                                (opt.precond_space == 0 && h->d_max > m);
   if (h->kind == SDP_A_DIAG) {
     h->b_elems = opt.precond_space == 2 ? 0 : (int64_t)m * (opt.precond_space == 1 ? h->d_max : dof(n, 1));
     h->bt_elems = h->b_elems;
@@ -1125,6 +1131,8 @@ namespace {
 sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, const double* Ct, const double* bt,
                              double* dX, double* dy, double* dS, sdp_newton_info* info, bool reuse) {
   h->launches = 0;
+  NvtxRange range_solve("sdp newton solve");
+  NvtxPhase phase(reuse ? "a1-a2 setup (reused)" : "a1-a2 split and preconditioner core");
   const int n = h->n, m = h->m;
   cudaStream_t st = h->st;
   int64_t* L = &h->launches;
@@ -1164,6 +1172,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   CU(cudaMemcpyAsync(h->ctl, &init, sizeof(PcgCtl), cudaMemcpyHostToDevice, st));
   split_sort(st, n, V, lam, S.Vs, h->lam_s, L);
   split_params(st, n, h->opt.r_fixed, h->opt.r_hat, h->opt.beta_rule, h->lam_s, h->e, h->ctl, L);
+  if (h->opt.precond_space == 3 && h->lin) launch_lin_free_count(st, m, h->lin, kLinDominance, h->ctl, L);
   CU(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
   if (h->ctl_host->status != 0) return fail(h, SDP_EINVAL, "eigenvalues must be positive and finite, 1 <= r < n");
@@ -1172,7 +1181,15 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   if (r > h->r_max) return fail(h, SDP_EINVAL, "rank above the setup maximum");
   h->r = r;
   h->d = d;
-  h->space = h->opt.precond_space == 0 ? (d <= m ? 1 : 2) : h->opt.precond_space;
+  if (h->opt.precond_space == 3) {
+    // with the linear block: the m-space complement when fewer than d rows are free of their
+    // slack (the d-space elimination rests on those rows and loses the direction to rounding at
+    // small mu, where the m-space complement is nearly diagonal on the fixed rows); else the
+    // smaller space
+    h->space = h->lin ? (h->ctl_host->m_free < d ? 2 : 1) : (d <= m ? 1 : 2);
+  } else {
+    h->space = h->opt.precond_space == 0 ? (d <= m ? 1 : 2) : h->opt.precond_space;
+  }
   h->vs_sl[0].valid = h->vs_sl[1].valid = false;
   if (h->vs_mem[0]) {   // slices of Vs (rows of Vs and of Vs^T) for every tensor-core product with it
     CU(tc_make_slices(st, n, n, S.Vs, 1, n, h->vs_mem[0], &h->vs_sl[0], L));
@@ -1285,6 +1302,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   const int nt = m + d;
 
   // ---- a3: right-hand side and start ----
+  phase.next("a3 right side");
   const double* Q = S.Vs;
   if (rhs_side) {
     join(h, 0, 5);
@@ -1310,6 +1328,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
                       h->ctl, h->dotbuf, h->counter, L);
   }
 
+  phase.next("a4-a7 Krylov solve");
   if (h->opt.krylov == 1) {
     // ---- Cor. minres: MINRES_k(augsys, g, I, 0) ----
     launch_minres_init(st, nt, h->g, S.rv, S.z, S.x, S.mw, S.mw2, h->mctl, h->ctl, h->dotbuf, h->counter, L);
@@ -1384,6 +1403,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   CU(cudaEventRecord(h->ev_phase[2], st));
 
   // ---- a8: recovery ----
+  phase.next("a8 recovery");
   const double* u = S.x;
   const double* v = S.x + m;
   // dX = E Cw E + sym(Up Q^T) with Cw = A^T(u) - tau^2 C~ and Up = Vs unpack(v): E Cw from

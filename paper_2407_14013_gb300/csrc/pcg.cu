@@ -620,6 +620,21 @@ __global__ void lin_lam_kernel(int m, const double* __restrict__ delta, const Pc
   if (i < m) lam[i] = ctl->beta_pc + delta[i] / (ctl->tau * ctl->tau);
 }
 
+// m_free = #{i : tau^-2 delta_i <= dominance beta}: the rows of the linear block not fixed by their
+// slack (one block; deterministic integer count)
+__global__ void lin_free_count_kernel(int m, const double* __restrict__ delta, double dominance,
+                                      PcgCtl* __restrict__ ctl) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  const double lim = dominance * ctl->beta_pc * ctl->tau * ctl->tau;
+  int c = 0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) c += (delta[i] <= lim) ? 1 : 0;
+  atomicAdd(&cnt, c);
+  __syncthreads();
+  if (threadIdx.x == 0) ctl->m_free = cnt;
+}
+
 // out = r_u / Lam (the first block of r only)
 __global__ void lin_div_kernel(int m, const double* __restrict__ r, const double* __restrict__ lam,
                                double* __restrict__ out, const PcgCtl* __restrict__ ctl) {
@@ -1078,6 +1093,12 @@ void launch_recover_F(cudaStream_t st, int n, const double* EYu, const double* E
 
 void launch_lin_lam(cudaStream_t st, int m, const double* delta, const PcgCtl* ctl, double* lam, int64_t* launches) {
   lin_lam_kernel<<<nblk(m, VT), VT, 0, st>>>(m, delta, ctl, lam);
+  ++*launches;
+}
+
+void launch_lin_free_count(cudaStream_t st, int m, const double* delta, double dominance, PcgCtl* ctl,
+                           int64_t* launches) {
+  lin_free_count_kernel<<<1, 1024, 0, st>>>(m, delta, dominance, ctl);
   ++*launches;
 }
 

@@ -60,6 +60,9 @@ void launch_recover_F(cudaStream_t st, int n, const double* EYu, const double* E
 // Linear block of the Newton system (the nonnegative variables of Section 7's robust problems):
 // Lam = beta + tau^-2 delta; out = r_u / Lam; Bw = B with row i scaled by Lam_i^-1/2.
 void launch_lin_lam(cudaStream_t st, int m, const double* delta, const PcgCtl* ctl, double* lam, int64_t* launches);
+// ctl->m_free = #{i : tau^-2 delta_i <= dominance beta} (after the split has set tau and beta)
+void launch_lin_free_count(cudaStream_t st, int m, const double* delta, double dominance, PcgCtl* ctl,
+                           int64_t* launches);
 void launch_lin_div(cudaStream_t st, int m, const double* r, const double* lam, double* out, const PcgCtl* ctl,
                     int64_t* launches);
 void launch_lin_scale_rows(cudaStream_t st, int m, int d, const double* B, const double* lam, double* Bw,

@@ -208,3 +208,48 @@ def test_grad_slack_matches_kkt_definition(name, otol, mu_c, bound):
     gC2, gb2 = s.grad(_t(V), _t(lam), _t(gX), _t(gy))
     assert s.last_info.converged
     s.close()
+
+
+@pytest.mark.parametrize("dominated,expect", [(30, 2), (0, 1)], ids=["most_rows_fixed", "no_row_fixed"])
+def test_space_rule_with_linear_block(dominated, expect):
+    """precond_space = 3: with the linear block the GPU picks the space by the oracle's rule
+    (lpcone.choose_space_lp: the m-space when fewer than d rows have tau^-2 delta_i <= 1e8 beta),
+    here the m-space when 30 of the 40 rows are fixed by a slack (d = 23 > 10 free rows), the
+    d-space when none is, and the direction still equals the oracle's.  Where slacks fix rows
+    (delta_i = 1e14) the plain Schur route of the definition has a matrix of condition ~1e14 and
+    misses the direction by ~3e-4; the reference is then the oracle's reformulated solve at
+    rtol 1e-15, whose two spaces agree to 3e-14 (the Schur route is kept for the case without
+    fixed rows, where all three agree)."""
+    from paper_2407_14013_gb300 import NewtonSolver
+    from oracle.reform import split
+    prob = W.sensing(12, 40, 2, 1201)
+    m = prob.m
+    sp = W.scaling_point(prob.n, 2, 1e-3, 1312)
+    Ct, bt = W.newton_rhs(prob.n, m, 1313)
+    g = np.random.default_rng(1314)
+    G = np.hstack([np.eye(m), -np.eye(m)])
+    d = 10.0 ** g.uniform(-3, 3, 2 * m)
+    d[:dominated] = 1e14                                  # slacks that fix their rows
+    ct = g.standard_normal(2 * m)
+    osp = split(sp.V, sp.lam, r_hat=4, s_A=oops.row_norm_scale(prob))
+    assert lpcone.choose_space_lp(osp, G, d, m) == ("m" if expect == 2 else "d")
+    if dominated:
+        rX, rx, ry, _ = lpcone.newton_reform_lp(prob, sp.V, sp.lam, Ct, bt, G, d, ct, r_hat=4,
+                                                s_A=oops.row_norm_scale(prob), rtol=1e-15, space="auto")
+    else:
+        Wm = (sp.V * sp.lam) @ sp.V.T
+        rX, rx, ry = lpcone.newton_direct_lp(prob, Wm, Ct, bt, G, d, ct)
+    s = NewtonSolver(prob, r_hat=4, precond_space=3)
+    s.set_linear_diag(d[:m] + d[m:])
+    dX, dy, dS, info = s.solve(_t(sp.V), _t(sp.lam), _t(Ct), _t(bt + G @ (d * ct)))
+    assert info.converged and info.space == expect
+    dX, dy = dX.cpu().numpy(), dy.cpu().numpy()
+    dx = d * (G.T @ dy - ct)
+    # dx = D (G^T dy - c~) multiplies the rounding of dy by D (up to 1e14 here): compare D^{-1} dx
+    print(f"\nspace {info.space}: dX {rel(dX, rX):.2e} dy {rel(dy, ry):.2e} D^-1 dx {rel(dx / d, rx / d):.2e}")
+    assert rel(dX, rX) < TOL and rel(dy, ry) < TOL and rel(dx / d, rx / d) < TOL
+    # without the block, precond_space 3 is the plain auto rule (d = 23 <= m = 40: d-space)
+    s.set_linear_diag(None)
+    _, _, _, i0 = s.solve(_t(sp.V), _t(sp.lam), _t(Ct), _t(bt))
+    assert i0.converged and i0.space == 1
+    s.close()
