@@ -506,6 +506,27 @@ void sdp_set_tc_wait_limit_ns(uint64_t ns);
 sdp_status sdp_gemm_tn_lp(void* stream, int32_t tf32, int32_t M, int32_t N, int32_t K, float alpha, const void* A,
                           int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int32_t* err_word);
 
+/* Bounds report of the checked debug build (libwcipm_checked.so: the sparse-operator kernels of
+ * section 4.2's A(.) and A^T(.) for SDP_A_SPARSE_COO compiled with -DSDP_CHECK_BOUNDS).  There,
+ * every index that a gather or a scatter takes from an index table (the entries of a constraint,
+ * the entries and row/column of a matrix position, the CSR pattern of A^T(y)) is compared with
+ * the length of the array it addresses before it is used; an index out of range is skipped (the
+ * access is not made) and recorded in device memory.  The call synchronizes the device, reads and
+ * clears the records, and writes to *first the first violation kept (site << 48 | index mod 2^48,
+ * site >= 1 naming the check; 0 when none) and to *count the number seen since the last call.
+ * Returns SDP_OK when none was seen, SDP_EINVAL when one was (or first or count is NULL),
+ * SDP_ECUDA when reading the records failed, and SDP_EUNSUPPORTED in the default build, which
+ * has no checks (*first = *count = 0).  Not safe to call while another thread launches work. */
+sdp_status sdp_bounds_report(uint64_t* first, uint64_t* count);
+
+/* One bounds check of `index` against [0, bound) by the checked build's sparse translation unit,
+ * with no access behind it: an index outside the range is recorded as a violation (reported by
+ * the next sdp_bounds_report), one inside it is not.  The paper has no counterpart; this lets a
+ * test see the record and the report work without an out-of-range index reaching an access.
+ * Returns after the check on `stream` has completed; SDP_EUNSUPPORTED in the default build,
+ * SDP_EINVAL for bound < 0. */
+sdp_status sdp_bounds_selftest(void* stream, int64_t index, int64_t bound);
+
 /* Bytes of device workspace owned by the handle. */
 size_t sdp_workspace_bytes(const sdp_handle* h);
 

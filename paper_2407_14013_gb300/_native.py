@@ -12,6 +12,9 @@ from ctypes import POINTER, Structure, c_char_p, c_double, c_int32, c_int64, c_s
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libwcipm.so")
+# the bounds-checked debug build (same exports; its sparse-operator gathers and scatters check
+# every table index, see sdp_bounds_report): load(LIB_CHECKED_PATH) before any other call
+LIB_CHECKED_PATH = os.path.join(HERE, "libwcipm_checked.so")
 
 SDP_OK, SDP_EINVAL, SDP_ENOMEM, SDP_ECUDA, SDP_ENOTCONV, SDP_ENUMERIC, SDP_ETIMEOUT, SDP_EUNSUPPORTED = range(8)
 STATUS_NAMES = ["SDP_OK", "SDP_EINVAL", "SDP_ENOMEM", "SDP_ECUDA", "SDP_ENOTCONV", "SDP_ENUMERIC",
@@ -87,6 +90,8 @@ EXPORTS = {
     "sdp_set_profiling": (c_int32, [c_void_p, c_int32]),
     "sdp_adjoint_dense_noalloc": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
     "sdp_set_tc_wait_limit_ns": (None, [ctypes.c_uint64]),
+    "sdp_bounds_report": (c_int32, [POINTER(ctypes.c_uint64), POINTER(ctypes.c_uint64)]),
+    "sdp_bounds_selftest": (c_int32, [c_void_p, c_int64, c_int64]),
     "sdp_workspace_bytes": (c_size_t, [c_void_p]),
     "sdp_last_launch_count": (c_int64, [c_void_p]),
     "sdp_last_error": (c_char_p, [c_void_p]),
@@ -94,13 +99,18 @@ EXPORTS = {
 }
 
 _lib = None
+_lib_path = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libwcipm.so and declare every exported symbol; raises if it is missing."""
-    global _lib
+def load(path: str | None = None):
+    """Load the library (libwcipm.so unless path names another build) and declare every exported
+    symbol; raises if it is missing, or if path names a build other than the one already loaded."""
+    global _lib, _lib_path
     if _lib is not None:
+        if path is not None and os.path.abspath(path) != _lib_path:
+            raise RuntimeError(f"{_lib_path} is already loaded in this process; {path} cannot be")
         return _lib
+    path = os.path.abspath(path or LIB_PATH)
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
     lib = ctypes.CDLL(path)
@@ -108,7 +118,7 @@ def load(path: str = LIB_PATH):
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    _lib = lib
+    _lib, _lib_path = lib, path
     return lib
 
 
@@ -304,6 +314,17 @@ def sdp_adjoint_dense_noalloc(a_dense: int, n: int, m: int, y: int, Y: int, stre
 def sdp_set_tc_wait_limit_ns(ns: int) -> None:
     """Limit of the main-loop waits of the tensor-core product (0: the default 2 s)."""
     load().sdp_set_tc_wait_limit_ns(int(ns))
+
+
+def sdp_bounds_report() -> tuple[int, int, int]:
+    """(status, first violation, count) of the checked build's bounds records (cleared by the call)."""
+    first, count = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    st = load().sdp_bounds_report(ctypes.byref(first), ctypes.byref(count))
+    return int(st), int(first.value), int(count.value)
+
+
+def sdp_bounds_selftest(stream: int, index: int, bound: int) -> int:
+    return int(load().sdp_bounds_selftest(c_void_p(stream), index, bound))
 
 
 def sdp_workspace_bytes(h: int) -> int:

@@ -133,4 +133,49 @@ struct PcgCtl {
   int32_t pad1;
 };
 
+// Bounds-checked gathers and scatters (the debug build: the translation units that address
+// arrays through index tables compiled with -DSDP_CHECK_BOUNDS).  WC_IN(site, i, bound) is true
+// when 0 <= i < bound.  Otherwise it keeps (site, i) as the first violation seen by this
+// translation unit, counts it, and is false: the caller skips the access.  Without the flag it
+// is the constant true and the checks compile away.  Each checked translation unit registers a
+// reader of its record with the library (oob_register); sdp_bounds_report calls the readers.
+typedef int (*OobReader)(unsigned long long* first, unsigned long long* count);
+void oob_register(OobReader rd);
+
+#ifdef SDP_CHECK_BOUNDS
+namespace {
+__device__ unsigned long long oob_rec[2];   // first violation (site << 48 | index mod 2^48), count
+
+__device__ __noinline__ bool oob_fail(int site, int64_t i) {
+  const unsigned long long code = ((unsigned long long)site << 48) | ((unsigned long long)i & 0xFFFFFFFFFFFFull);
+  atomicCAS(&oob_rec[0], 0ull, code);
+  atomicAdd(&oob_rec[1], 1ull);
+  return false;
+}
+
+// Reads and clears this translation unit's record; returns the cudaError_t of the copies.
+int oob_read(unsigned long long* first, unsigned long long* count) {
+  unsigned long long v[2] = {0ull, 0ull};
+  cudaError_t e = cudaMemcpyFromSymbol(v, oob_rec, sizeof v);
+  if (e == cudaSuccess) {
+    const unsigned long long z[2] = {0ull, 0ull};
+    e = cudaMemcpyToSymbol(oob_rec, z, sizeof z);
+  }
+  *first = v[0];
+  *count = v[1];
+  return (int)e;
+}
+
+struct OobRegistration {
+  OobRegistration() { oob_register(&oob_read); }
+};
+OobRegistration oob_registration;
+}  // namespace
+
+#define WC_IN(site, i, bound) \
+  ((uint64_t)(int64_t)(i) < (uint64_t)(int64_t)(bound) ? true : ::wc::oob_fail((site), (int64_t)(i)))
+#else
+#define WC_IN(site, i, bound) true
+#endif
+
 }  // namespace wc

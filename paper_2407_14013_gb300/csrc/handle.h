@@ -141,6 +141,7 @@ struct sdp_handle {
   wc::TcSlices vs_sl[2];                  // [0] rows of Vs (op = Vs), [1] rows of Vs^T (op = Vs^T)
   bool no_coop = false;             // batched solves: no cooperative (grid-barrier) launches
   bool while_ok = true;             // the device-side PCG loop graph can be built on this device
+  bool small_ok = true;             // the one-cluster PCG solve of small DIAG problems launches here
   int* loop_guard = nullptr;        // passes of that loop (a bound independent of the stop flag)
   bool coop_pc = false;             // dense d-space preconditioner apply as one cooperative launch
   int64_t b_elems = 0;              // capacity of the explicit B = A Q (m x d)

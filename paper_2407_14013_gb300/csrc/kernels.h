@@ -226,6 +226,7 @@ struct SparseA {
   int64_t nnz = 0;
   int npos = 0;
   int64_t nnzY = 0;      // nonzeros of the symmetric pattern of A^T(y) (off-diagonal positions twice)
+  int m = 0;             // constraints
   const int32_t *con = nullptr, *row = nullptr, *col = nullptr;
   const double* val = nullptr;
   int32_t *con_ptr = nullptr, *pos_r = nullptr, *pos_c = nullptr, *pos_ptr = nullptr, *perm = nullptr;
@@ -243,6 +244,9 @@ void sparse_apply(cudaStream_t st, const SparseA& S, int n, int m, int r, const 
 // B = A Q (m x d row-major, ld ldB) and B^T (d x m, ld ldBt) in h-coordinates.
 void sparse_B(cudaStream_t st, const SparseA& S, int n, int m, int r, const double* Vs, double* B, int64_t ldB,
               double* Bt, int64_t ldBt, int64_t* launches);
+// One bounds check of index against bound in the sparse translation unit (no access is made);
+// recorded as a violation in the bounds-checked build when index is outside [0, bound).
+cudaError_t sparse_bounds_selftest(cudaStream_t st, int64_t index, int64_t bound);
 // Position values of Y = A^T(y): ypos[p] = sum over the entries e at position p of y[con_e] val_e.
 void sparse_posval(cudaStream_t st, const SparseA& S, const double* y, double* ypos, const int32_t* done,
                    int64_t* launches);

@@ -389,6 +389,7 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
     h->sp.nnz = prob->nnz;
     h->sp.npos = (int)sp_pos_r.size();
     h->sp.nnzY = (int64_t)sp_ycol.size();
+    h->sp.m = m;
     h->sp.con = prob->a_con;
     h->sp.row = prob->a_row;
     h->sp.col = prob->a_col;
@@ -670,6 +671,15 @@ cudaError_t pack_apply_dense(sdp_handle* h, Space& S, cudaStream_t st, int r, co
 // The dense d-space preconditioner apply runs as one cooperative launch.
 bool pc_coop_on(const sdp_handle* h) {
   return h->space == 1 && !h->lin && h->kind == SDP_A_DENSE_SVEC && h->coop_pc && !h->no_coop;
+}
+
+// Small DIAG problems in the m-space form run their whole FP64 PCG solve as one cluster launch
+// (with use_graph: the device-resident form of the loop; use_graph = 0 keeps the launch chain).
+bool small_pcg_on(const sdp_handle* h) {
+  if (h->kind != SDP_A_DIAG || h->mixed || h->opt.krylov != 0 || h->space != 2 || h->lin || h->prof) return false;
+  if (!h->opt.use_graph || !h->small_ok) return false;
+  const size_t b = small_pcg_smem_bytes(h->n, h->r, h->d);
+  return b > 0 && b <= 227 * 1024;
 }
 
 // Inside the PCG loop the update x += alpha p, r -= alpha Ap runs in the last block of the
@@ -1323,9 +1333,10 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     sparse_apply_pos(st, h->sp, n, m, r, S.zpos, nullptr, nullptr, S.partA, nullptr, L);   // A(E C~ E)
     launch_rhs_finish(st, m, d, n, r, S.partA, 1, nullptr, nullptr, bt, Ct, S.H, S.Dv, h->g, S.x,
                       h->opt.newton_rtol, h->ctl, h->dotbuf, h->counter, L);
-  } else {
-    launch_rhs_finish(st, m, d, n, r, nullptr, 0, S.F, S.E, bt, Ct, S.H, S.Dv, h->g, S.x, h->opt.newton_rtol,
-                      h->ctl, h->dotbuf, h->counter, L);
+  } else {   // DIAG: A(E C~ E) = diag(F E), summed in slabs over the whole GPU
+    const int slabs = launch_diag_FE(st, n, S.F, S.E, S.partA, (int)(rows_gemv_part_elems(n, n) / n), L);
+    launch_rhs_finish(st, m, d, n, r, S.partA, slabs, nullptr, nullptr, bt, Ct, S.H, S.Dv, h->g, S.x,
+                      h->opt.newton_rtol, h->ctl, h->dotbuf, h->counter, L);
   }
 
   phase.next("a4-a7 Krylov solve");
@@ -1336,15 +1347,27 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     if (s != SDP_OK) return s;
   } else if (!h->mixed) {
     // ---- a4-a6: FP64 PCG from x0 ----
-    if (h->opt.pcg_start == 0) {   // x0 = P^{-1}[0; g_v]: P x0 = [0; g_v], so r0_v = 0 with r0_u ~ g
-      launch_correction_rhs(st, m, d, h->g, S.z, L);
-      sdp_status s0 = apply_precond(h, S, S.z, S.x, 0);
-      if (s0 != SDP_OK) return s0;
+    bool small = small_pcg_on(h);
+    if (small) {   // the whole solve in one cluster launch
+      const cudaError_t e = launch_small_pcg(st, n, r, d, h->opt.pcg_start == 0 ? 1 : 0, S.Vs, S.EE, S.Pinv, S.Dv,
+                                             h->g, S.x, S.rv, S.z, S.p, S.Ap, S.ctl, L);
+      if (e != cudaSuccess) {   // refused on this device (launch configuration): the launch chain
+        cudaGetLastError();
+        h->small_ok = false;
+        small = false;
+      }   // no host read here: the recovery reads the scalars on the device, the host at the end
     }
-    sdp_status s = pcg_start(h, S, false, h->g, 0.0);
-    if (s != SDP_OK) return s;
-    s = krylov_loop(h, S, false, false);
-    if (s != SDP_OK) return s;
+    if (!small) {
+      if (h->opt.pcg_start == 0) {   // x0 = P^{-1}[0; g_v]: P x0 = [0; g_v], so r0_v = 0 with r0_u ~ g
+        launch_correction_rhs(st, m, d, h->g, S.z, L);
+        sdp_status s0 = apply_precond(h, S, S.z, S.x, 0);
+        if (s0 != SDP_OK) return s0;
+      }
+      sdp_status s = pcg_start(h, S, false, h->g, 0.0);
+      if (s != SDP_OK) return s;
+      s = krylov_loop(h, S, false, false);
+      if (s != SDP_OK) return s;
+    }
   } else {
     // ---- a7: FP64 refinement around solves with the mixed operator ----
     // x starts at 0, so that rho_0 = g and the first correction starts at P^{-1}[0; g_v]: the
@@ -1596,6 +1619,50 @@ extern "C" sdp_status sdp_set_profiling(sdp_handle* h, int32_t on) {
     for (auto& e : h->ev) CU(cudaEventCreate(&e));
   }
   h->prof = on != 0;
+  return SDP_OK;
+}
+
+namespace wc {
+// Readers of the bounds records of the checked translation units (registered while the library
+// loads; none in the default build).
+static std::vector<OobReader>& oob_readers() {
+  static std::vector<OobReader> v;
+  return v;
+}
+void oob_register(OobReader rd) { oob_readers().push_back(rd); }
+}  // namespace wc
+
+extern "C" sdp_status sdp_bounds_report(uint64_t* first, uint64_t* count) {
+  if (!first || !count) return SDP_EINVAL;
+  *first = 0;
+  *count = 0;
+  if (wc::oob_readers().empty()) return SDP_EUNSUPPORTED;
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return SDP_ECUDA;
+  }
+  bool ok = true;
+  for (wc::OobReader rd : wc::oob_readers()) {
+    unsigned long long f = 0, c = 0;
+    if (rd(&f, &c) != (int)cudaSuccess) ok = false;
+    if (!*first) *first = f;
+    *count += c;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    return SDP_ECUDA;
+  }
+  return *count ? SDP_EINVAL : SDP_OK;
+}
+
+extern "C" sdp_status sdp_bounds_selftest(void* stream, int64_t index, int64_t bound) {
+  if (bound < 0) return SDP_EINVAL;
+  if (wc::oob_readers().empty()) return SDP_EUNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (wc::sparse_bounds_selftest(st, index, bound) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return SDP_ECUDA;
+  }
   return SDP_OK;
 }
 

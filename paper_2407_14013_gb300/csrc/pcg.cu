@@ -478,6 +478,27 @@ __global__ void p_update_kernel(int nt, const T* __restrict__ z, T* __restrict__
   p[q] = start ? z[q] : (T)fma(ctl->beta, (double)p[q], (double)z[q]);
 }
 
+// DIAG kind: the slab partial sums of diag(F E) = diag(E C~ E) with F = E C~, E symmetric (stored
+// in full), so that (F E)_qq = sum_k F[q, k] E[q, k]: thread q of slab s sums k in
+// [s KS, (s + 1) KS) with coalesced loads of both operands and four independent chains.
+__global__ void __launch_bounds__(VT)
+diag_FE_kernel(int n, int KS, const double* __restrict__ F, const double* __restrict__ E, double* __restrict__ part) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const int k0 = blockIdx.y * KS, k1 = min(n, k0 + KS);
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int k = k0;
+  for (; k + 3 < k1; k += 4) {
+    const int64_t o = q + (int64_t)k * n;
+    a0 = fma(F[o], E[o], a0);
+    a1 = fma(F[o + n], E[o + n], a1);
+    a2 = fma(F[o + 2 * n], E[o + 2 * n], a2);
+    a3 = fma(F[o + 3 * n], E[o + 3 * n], a3);
+  }
+  for (; k < k1; ++k) a0 = fma(F[q + (int64_t)k * n], E[q + (int64_t)k * n], a0);
+  part[(int64_t)blockIdx.y * n + q] = (a0 + a1) + (a2 + a3);
+}
+
 // Right side of eq. augsys: g = [b~ + tau^2 A(E C~ E); tau^2 pack(H)], x0 = [0; -g_v / D]
 // (v0 = -Sigma^{-1} Q^T c of Cor. pcg), ||g||^2 and the stop threshold.
 __global__ void __launch_bounds__(VT)
@@ -1066,6 +1087,16 @@ void launch_rhs_finish(cudaStream_t st, int m, int d, int n, int r, const double
   rhs_finish_kernel<<<vec_blocks(m + d), VT, 0, st>>>(m, d, n, r, partA, S, F, E, bt, Ct, H, Dv, g, x, rtol, ctl,
                                                      dotbuf, counter);
   ++*launches;
+}
+
+int launch_diag_FE(cudaStream_t st, int n, const double* F, const double* E, double* part, int max_slabs,
+                   int64_t* launches) {
+  int S = std::min(std::min(32, (n + 31) / 32), std::max(1, max_slabs));
+  const int KS = (n + S - 1) / S;
+  S = (n + KS - 1) / KS;
+  diag_FE_kernel<<<dim3((unsigned)((n + VT - 1) / VT), (unsigned)S), VT, 0, st>>>(n, KS, F, E, part);
+  ++*launches;
+  return S;
 }
 
 void launch_diag_matrix(cudaStream_t st, int n, const double* u, double* Y, int64_t* launches) {

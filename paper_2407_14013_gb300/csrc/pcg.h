@@ -97,6 +97,21 @@ cudaError_t launch_pc_dense_d_coop(cudaStream_t st, int m, int d, const double* 
 void launch_to_float(cudaStream_t st, int cnt, const double* src, float* dst, const int32_t* done, int64_t* launches);
 void launch_sym_copy(cudaStream_t st, int n, const double* g, double* out, int64_t* launches);
 void launch_ctl_reset(cudaStream_t st, PcgCtl* dst, const PcgCtl* src, int max_iters, int64_t* launches);
+// DIAG kind: part[s n + q] = the slab-s partial sums of diag(F E) (F = E C~, E symmetric), at most
+// max_slabs slabs of n entries; returns the number of slabs written.
+int launch_diag_FE(cudaStream_t st, int n, const double* F, const double* E, double* part, int max_slabs,
+                   int64_t* launches);
+
+// Small DIAG problems (n <= 128, r <= 16), m-space form, FP64 PCG: the whole solve from the right
+// side (g, and x0 = [0; -g_v / D] unless start0) through the stop test in one launch of one
+// thread-block cluster (small_pcg.cu).  Reads Vs, E o E, K^{-1} (m x m), D and the control block;
+// leaves x, r, z, p, Ap and the PCG scalars as the launch chain of the loop does.
+// small_pcg_smem_bytes: its shared memory for (n, r, d), 0 when the shape is outside its range.
+size_t small_pcg_smem_bytes(int n, int r, int d);
+cudaError_t launch_small_pcg(cudaStream_t st, int n, int r, int d, int start0, const double* Vs, const double* EE,
+                             const double* Pinv, const double* Dv, const double* g, double* x, double* rv, double* z,
+                             double* p, double* Ap, PcgCtl* ctl, int64_t* launches);
+
 // DIAG kind, m-space core without an explicit B: w = r_u + rowdot(U, Q); z_v = (pack(H) - r_v) / D;
 // Tm = Q (Lam - tau I); K = beta I + tau^-2 G o (G + 2 tau E) (lower triangle)
 void launch_diag_w(cudaStream_t st, int n, int r, const double* U, const double* Vs, const double* rv, double* w,

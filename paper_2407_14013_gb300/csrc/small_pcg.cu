@@ -1,0 +1,421 @@
+// The whole FP64 PCG solve of the augmented system (eq. augsys; Def. pcg with Cor. pcg's start)
+// for small DIAG problems (A_i = e_i e_i^T, m = n <= 128) in the m-space preconditioner form, held
+// by one thread-block cluster of SC CTAs: one launch instead of about 16 per iteration.
+//
+// An iteration of the launch chain it replaces is a string of tiny products (n x r outputs of
+// length-n sums) and vector kernels; at n = 64 each one costs its launch and a few FP64 latency
+// chains, so the iteration takes about 100 us while its arithmetic is about 60 K multiply-adds.
+// Here the n rows (and the n columns of Vs for H = Vs^T diag(t) Q) are split over the CTAs of the
+// cluster; each CTA keeps its slices of Vs, E o E and the preconditioner core in shared memory
+// for the whole solve, computes its rows of each product (a warp per row, the lanes splitting the
+// length-n sum, so that no FP64 dependency chain is longer than a few operations), and writes its
+// rows into every CTA's copy of the result through distributed shared memory; a cluster barrier
+// then gives every CTA the whole vector.  The O(m + d) work (the h-coordinate pack and unpack, the
+// dot products, the PCG updates) is done by every CTA on its own copy of the vectors, in the same
+// order, so every CTA holds bit-identical vectors and scalars and takes the same stop decision.
+// Four cluster barriers per iteration; no flag waits.
+//
+// Per iteration, with t = p_u (operator) or z_u (preconditioner), Q = Vs[:, :r]:
+//   operator        Up = Vs unpack(p_v);  H = Vs^T diag(p_u) Q
+//                   (M p)_u = (E o E) p_u + rowdot(Up, Q);  (M p)_v = pack(H) - D p_v
+//   preconditioner  w = r_u + rowdot(Vs unpack(D^{-1} r_v), Q);  z_u = K^{-1} w
+//                   z_v = D^{-1} (pack(Vs^T diag(z_u) Q) - r_v)
+// which is the m-space form P^{-1} = [K^{-1}, K^{-1} B D^{-1}; D^{-1} B^T K^{-1}, D^{-1} B^T K^{-1} B D^{-1} - D^{-1}]
+// applied as in the launch chain (products with B from Vs: B t = rowdot(Vs unpack(t), Q),
+// B^T u = pack(Vs^T diag(u) Q)), and the PCG scalars of Def. pcg.
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "pcg.h"
+
+namespace wc {
+
+namespace {
+
+namespace cg = cooperative_groups;
+
+constexpr int SC = 8;              // CTAs of the cluster (the portable maximum)
+constexpr int SNT = 256;           // threads per CTA
+constexpr int SNW = SNT / 32;
+constexpr int SRMAX = 16;          // largest r
+constexpr int SNMAX = 128;         // largest n
+
+struct SmallArgs {
+  int n, r, d, chunk, start0;
+  const double *Vs, *EE, *Pinv, *Dv, *g;
+  double *x, *rv, *z, *p, *Ap;
+  PcgCtl* ctl;
+};
+
+// Shared-memory layout (doubles): the CTA's slices, then the vectors and scratch.
+struct SmallLayout {
+  int vsr, vsc, q, eer, pir, dv, idv, X, R, Z, P, AP, hp, ha, hq, wb, red, total;
+  __host__ __device__ SmallLayout(int n, int r, int d, int chunk) {
+    const int nt = n + d;
+    int o = 0;
+    vsr = o; o += chunk * n;     // rows i0.. of Vs:          vsr[il n + a] = Vs[i0 + il, a]
+    vsc = o; o += chunk * n;     // columns i0.. of Vs:       vsc[al n + i] = Vs[i, i0 + al]
+    q = o;   o += n * r;         // Q = Vs[:, :r], column-major
+    eer = o; o += chunk * n;     // rows i0.. of E o E (symmetric: its columns)
+    pir = o; o += chunk * n;     // rows i0.. of K^{-1} (symmetric)
+    dv = o;  o += d;
+    idv = o; o += d;             // 1 / D
+    X = o;   o += nt;
+    R = o;   o += nt;
+    Z = o;   o += nt;
+    P = o;   o += nt;
+    AP = o;  o += nt;
+    ha = o;  o += n * r;         // H of the operator (rows from every CTA)
+    hq = o;  o += n * r;         // H of the preconditioner (rows from every CTA)
+    // the unpack of a v-block (every CTA makes its own) shares hq: the unpack is written at the
+    // start of an apply and read before its first cluster barrier, and hq receives the other
+    // CTAs' rows only between the second and third barriers of a preconditioner apply
+    hp = hq;
+    wb = o;  o += n;             // w = r_u + B D^{-1} r_v (rows from every CTA)
+    red = o; o += 64;            // block reductions
+    total = o;
+  }
+};
+
+__device__ __forceinline__ double warp_allsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// What every pass needs to find its data: the shape, this CTA's rows, the shared memory.
+struct SmallCtx {
+  int n, r, d, chunk, i0, rows;
+  double* sm;
+};
+
+// Sum over the CTA's threads, valid in every thread: a butterfly in each warp, then the SNW warp
+// totals by a three-level butterfly (eight dependent additions in all); fixed order, so every CTA
+// of the cluster gets the same bits from the same data.
+__device__ double cta_sum(double v, double* red) {
+  v = warp_allsum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();   // red may still be read by the previous sum
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = red[lane & (SNW - 1)];
+#pragma unroll
+  for (int o = SNW / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
+}
+
+// <a, b> over [0, len), the same bits in every CTA (fixed thread mapping and reduction order)
+__device__ double cta_dot(const double* a, const double* b, int len, double* red) {
+  double s = 0.0;
+  for (int q = threadIdx.x; q < len; q += SNT) s = fma(a[q], b[q], s);
+  return cta_sum(s, red);
+}
+
+// Hp = unpack(v) (n x r, column-major), v scaled by D^{-1} first when idv != NULL
+__device__ void cta_unpack(int n, int r, const double* v, const double* idv, double* Hp) {
+  for (int q = threadIdx.x; q < n * r; q += SNT) {
+    const int j = q / n, a = q - j * n;
+    double val;
+    if (a < r) {
+      const int i = a > j ? a : j, jj = a > j ? j : a;
+      const int k = (int)svec_index(r, i, jj);
+      const double hv = idv ? v[k] * idv[k] : v[k];
+      val = (i == jj) ? hv : hv * WC_RSQRT2;
+    } else {
+      const int k = r * (r + 1) / 2 + (a - r) + j * (n - r);
+      val = WC_SQRT2 * (idv ? v[k] * idv[k] : v[k]);
+    }
+    Hp[q] = val;
+  }
+}
+
+// This CTA's rows i = i0 + il of U = Vs Hp (Hp in shared memory), each finished into one value
+// written at dst[i] in every CTA of the cluster:
+//   OP:  (M v)_u[i] = ((E o E) v_u)[i] + sum_k U[i, k] Q[i, k]     (the operator's u-block)
+//   !OP: w[i]       = v_u[i] + sum_k U[i, k] Q[i, k]               (w = r_u + B D^{-1} r_v)
+// A warp per row: the lanes split the length-n sums (r + 1 independent chains each), then a
+// butterfly sum leaves the totals in every lane.  RB >= r: the width of the accumulator block.
+template <bool OP, int RB>
+__device__ __noinline__ void rows_pass(SmallCtx c, const double* vu, double* dst) {
+  const cg::cluster_group cl = cg::this_cluster();
+  const SmallLayout L(c.n, c.r, c.d, c.chunk);
+  const int n = c.n, r = c.r;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double* Hp = c.sm + L.hp;
+  for (int il = warp; il < c.rows; il += SNW) {
+    const double* vr = c.sm + L.vsr + il * n;
+    const double* er = c.sm + L.eer + il * n;
+    double acc[RB];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) acc[j] = 0.0;
+    double ee = 0.0;
+    for (int a = lane; a < n; a += 32) {
+      const double va = vr[a];
+#pragma unroll
+      for (int j = 0; j < RB; ++j)
+        if (j < r) acc[j] = fma(va, Hp[a + j * n], acc[j]);
+      if (OP) ee = fma(er[a], vu[a], ee);
+    }
+#pragma unroll
+    for (int j = 0; j < RB; ++j)
+      if (j < r) acc[j] = warp_allsum(acc[j]);
+    const int i = c.i0 + il;
+    double v = OP ? warp_allsum(ee) : vu[i];
+#pragma unroll
+    for (int k = 0; k < RB; ++k)
+      if (k < r) v = fma(acc[k], c.sm[L.q + i + k * n], v);
+    if (lane < SC) *cl.map_shared_rank(dst + i, lane) = v;
+  }
+}
+
+// This CTA's rows a = i0 + al of H = Vs^T diag(t) Q (n x r): H[a, j] = sum_i Vs[i, a] (t_i Q[i, j]),
+// written at dstH[a + j n] in every CTA of the cluster.
+template <int RB>
+__device__ __noinline__ void cols_pass(SmallCtx c, const double* t, double* dstH) {
+  const cg::cluster_group cl = cg::this_cluster();
+  const SmallLayout L(c.n, c.r, c.d, c.chunk);
+  const int n = c.n, r = c.r;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int al = warp; al < c.rows; al += SNW) {
+    const double* vc = c.sm + L.vsc + al * n;
+    double acc[RB];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) acc[j] = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      const double w = vc[i], ti = t[i];
+#pragma unroll
+      for (int j = 0; j < RB; ++j)
+        if (j < r) acc[j] = fma(w, ti * c.sm[L.q + i + j * n], acc[j]);
+    }
+    const int a = c.i0 + al;
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+      if (j < r) {
+        const double hj = warp_allsum(acc[j]);
+        if (lane < SC) *cl.map_shared_rank(dstH + a + j * n, lane) = hj;
+      }
+    }
+  }
+}
+
+// This CTA's rows of z_u = K^{-1} w (w gathered in shared memory), written at dst[i] everywhere.
+__device__ void pinv_pass(SmallCtx c, double* dst) {
+  const cg::cluster_group cl = cg::this_cluster();
+  const SmallLayout L(c.n, c.r, c.d, c.chunk);
+  const int n = c.n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int il = warp; il < c.rows; il += SNW) {
+    const double* pr = c.sm + L.pir + il * n;
+    double s = 0.0;
+    for (int l = lane; l < n; l += 32) s = fma(pr[l], c.sm[L.wb + l], s);
+    s = warp_allsum(s);
+    if (lane < SC) *cl.map_shared_rank(dst + c.i0 + il, lane) = s;
+  }
+}
+
+// out = M v, or g - M v when g != NULL (one cluster barrier)
+template <int RB>
+__device__ __noinline__ void op_apply(SmallCtx c, const double* v, double* out, const double* __restrict__ g) {
+  const cg::cluster_group cl = cg::this_cluster();
+  const SmallLayout L(c.n, c.r, c.d, c.chunk);
+  const int n = c.n, r = c.r, d = c.d, m = n;
+  cta_unpack(n, r, v + m, nullptr, c.sm + L.hp);
+  __syncthreads();
+  rows_pass<true, RB>(c, v, out);
+  cols_pass<RB>(c, v, c.sm + L.ha);
+  cl.sync();
+  for (int q = threadIdx.x; q < m + d; q += SNT) {
+    double val = q < m ? out[q] : pack_at(c.sm + L.ha, n, n, r, q - m) - c.sm[L.dv + q - m] * v[q];
+    if (g) val = g[q] - val;
+    out[q] = val;
+  }
+  __syncthreads();
+}
+
+// z = P^{-1} rin in the m-space form (three cluster barriers)
+template <int RB>
+__device__ __noinline__ void pc_apply(SmallCtx c, const double* rin, double* z) {
+  const cg::cluster_group cl = cg::this_cluster();
+  const SmallLayout L(c.n, c.r, c.d, c.chunk);
+  const int n = c.n, r = c.r, d = c.d, m = n;
+  cta_unpack(n, r, rin + m, c.sm + L.idv, c.sm + L.hp);       // unpack(D^{-1} r_v)
+  __syncthreads();
+  rows_pass<false, RB>(c, rin, c.sm + L.wb);                    // w = r_u + B D^{-1} r_v
+  cl.sync();
+  pinv_pass(c, z);                                              // z_u = K^{-1} w
+  cl.sync();
+  cols_pass<RB>(c, z, c.sm + L.hq);                             // Vs^T diag(z_u) Q
+  cl.sync();
+  for (int h = threadIdx.x; h < d; h += SNT)                    // z_v = D^{-1}(B^T z_u - r_v)
+    z[m + h] = (pack_at(c.sm + L.hq, n, n, r, h) - rin[m + h]) * c.sm[L.idv + h];
+  __syncthreads();
+}
+
+template <int RB>
+__global__ void __cluster_dims__(SC, 1, 1) __launch_bounds__(SNT) small_pcg_kernel(SmallArgs A) {
+  const cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ double sm[];
+  PcgCtl* ctl = A.ctl;
+  if (ctl->done) return;   // the right side already ended the solve (the same in every CTA)
+  const int n = A.n, r = A.r, d = A.d, m = n, nt = n + d;
+  const SmallLayout L(n, r, d, A.chunk);
+  const int rank = (int)cl.block_rank();
+  SmallCtx c;
+  c.n = n;
+  c.r = r;
+  c.d = d;
+  c.chunk = A.chunk;
+  c.i0 = rank * A.chunk;
+  c.rows = max(0, min(A.chunk, n - c.i0));
+  c.sm = sm;
+  const int i0 = c.i0, rows = c.rows;
+  // this CTA's slices and the shared operands, kept for the whole solve
+#pragma unroll 4
+  for (int q = threadIdx.x; q < rows * n; q += SNT) {
+    const int il = q % rows, a = q / rows;
+    sm[L.vsr + il * n + a] = A.Vs[(i0 + il) + (int64_t)a * n];
+    const int al = q / n, i = q % n;
+    sm[L.vsc + al * n + i] = A.Vs[i + (int64_t)(i0 + al) * n];
+    sm[L.eer + al * n + i] = A.EE[i + (int64_t)(i0 + al) * n];
+    sm[L.pir + al * n + i] = A.Pinv[i + (int64_t)(i0 + al) * m];
+  }
+  for (int q = threadIdx.x; q < n * r; q += SNT) sm[L.q + q] = A.Vs[q];
+  for (int h = threadIdx.x; h < d; h += SNT) {
+    const double dh = A.Dv[h];
+    sm[L.dv + h] = dh;
+    sm[L.idv + h] = 1.0 / dh;   // the preconditioner multiplies by D^{-1} (one division per entry per solve)
+  }
+  double* X = sm + L.X;
+  double* R = sm + L.R;
+  double* Z = sm + L.Z;
+  double* P = sm + L.P;
+  double* AP = sm + L.AP;
+  double* red = sm + L.red;
+  for (int q = threadIdx.x; q < nt; q += SNT) {
+    X[q] = A.start0 ? 0.0 : A.x[q];
+    Z[q] = q < m ? 0.0 : A.g[q];   // [0; g_v]: the start's correction right side
+  }
+  const double tol2 = ctl->tol2;
+  const int max_iters = ctl->max_iters;
+  int iters = ctl->iters, status = ctl->status, done = 0;
+  double rr = ctl->rr, rr0 = ctl->rr0, rz = ctl->rz, rz_new = ctl->rz_new, beta = ctl->beta;
+  double alpha = ctl->alpha, pAp = ctl->pAp;
+  cl.sync();   // every CTA has started and holds its operands before any writes into it
+  if (A.start0) {   // x0 = P^{-1} [0; g_v], so that P x0 = [0; g_v] and r0_v = 0 (Cor. pcg)
+    pc_apply<RB>(c, Z, X);
+    const double t = cta_dot(Z, X, nt, red);
+    if (!isfinite(t)) { status = 5; done = 1; }
+  }
+  if (!done) {   // r0 = g - M x0, ||r0||^2 and the stop test; z0 = P^{-1} r0; p0 = z0
+    op_apply<RB>(c, X, R, A.g);
+    rr = cta_dot(R, R, nt, red);
+    if (iters == 0) rr0 = rr;
+    if (!isfinite(rr)) { status = 5; done = 1; }
+    else if (rr <= tol2) done = 1;
+  }
+  if (!done) {
+    pc_apply<RB>(c, R, Z);
+    rz = cta_dot(R, Z, nt, red);
+    beta = 0.0;
+    if (!isfinite(rz)) { status = 5; done = 1; }
+    for (int q = threadIdx.x; q < nt; q += SNT) P[q] = Z[q];
+    __syncthreads();
+  }
+  while (!done) {
+    op_apply<RB>(c, P, AP, nullptr);
+    pAp = cta_dot(P, AP, nt, red);
+    // Def. pcg has no sign condition: with the indefinite preconditioner <p, M p> is positive in
+    // exact arithmetic but may change sign at the rounding floor
+    if (pAp == 0.0 || !isfinite(pAp) || !isfinite(rz)) { status = 5; done = 1; break; }
+    alpha = rz / pAp;
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < nt; q += SNT) {
+      X[q] = fma(alpha, P[q], X[q]);
+      const double rq = fma(-alpha, AP[q], R[q]);
+      R[q] = rq;
+      acc = fma(rq, rq, acc);
+    }
+    rr = cta_sum(acc, red);
+    iters += 1;
+    if (!isfinite(rr)) { status = 5; done = 1; }
+    else if (rr <= tol2) { status = 0; done = 1; }
+    else if (iters >= max_iters) { status = 4; done = 1; }
+    if (done) break;
+    pc_apply<RB>(c, R, Z);
+    const double t = cta_dot(R, Z, nt, red);
+    if (!isfinite(t)) { status = 5; done = 1; }
+    rz_new = t;
+    beta = t / rz;
+    rz = t;
+    if (done) break;
+    for (int q = threadIdx.x; q < nt; q += SNT) P[q] = fma(beta, P[q], Z[q]);
+    __syncthreads();
+  }
+  // the iterate and the scalars back to global memory (every CTA holds the same: rank 0 writes)
+  if (rank == 0) {
+    for (int q = threadIdx.x; q < nt; q += SNT) {
+      A.x[q] = X[q];
+      A.rv[q] = R[q];
+      A.z[q] = Z[q];
+      A.p[q] = P[q];
+      A.Ap[q] = AP[q];
+    }
+    if (threadIdx.x == 0) {
+      ctl->rr = rr;
+      ctl->rr0 = rr0;
+      ctl->rz = rz;
+      ctl->rz_new = rz_new;
+      ctl->beta = beta;
+      ctl->alpha = alpha;
+      ctl->pAp = pAp;
+      ctl->iters = iters;
+      ctl->status = status;
+      ctl->done = 1;
+    }
+  }
+  cl.sync();   // no CTA leaves while another may still address its shared memory
+}
+
+}  // namespace
+
+size_t small_pcg_smem_bytes(int n, int r, int d) {
+  if (n < 2 || n > SNMAX || r < 1 || r > SRMAX || r >= n) return 0;
+  const int chunk = (n + SC - 1) / SC;
+  return (size_t)SmallLayout(n, r, d, chunk).total * sizeof(double);
+}
+
+cudaError_t launch_small_pcg(cudaStream_t st, int n, int r, int d, int start0, const double* Vs, const double* EE,
+                             const double* Pinv, const double* Dv, const double* g, double* x, double* rv, double* z,
+                             double* p, double* Ap, PcgCtl* ctl, int64_t* launches) {
+  const size_t bytes = small_pcg_smem_bytes(n, r, d);
+  if (bytes == 0 || bytes > 227 * 1024) return cudaErrorInvalidValue;
+  const void* fn = r <= 4 ? (const void*)small_pcg_kernel<4>
+                  : r <= 8 ? (const void*)small_pcg_kernel<8> : (const void*)small_pcg_kernel<SRMAX>;
+  cudaError_t e = raise_dyn_smem(fn, (int)bytes);
+  if (e != cudaSuccess) return e;
+  SmallArgs A;
+  A.n = n;
+  A.r = r;
+  A.d = d;
+  A.chunk = (n + SC - 1) / SC;
+  A.start0 = start0;
+  A.Vs = Vs;
+  A.EE = EE;
+  A.Pinv = Pinv;
+  A.Dv = Dv;
+  A.g = g;
+  A.x = x;
+  A.rv = rv;
+  A.z = z;
+  A.p = p;
+  A.Ap = Ap;
+  A.ctl = ctl;
+  if (r <= 4) small_pcg_kernel<4><<<SC, SNT, bytes, st>>>(A);
+  else if (r <= 8) small_pcg_kernel<8><<<SC, SNT, bytes, st>>>(A);
+  else small_pcg_kernel<SRMAX><<<SC, SNT, bytes, st>>>(A);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+}  // namespace wc

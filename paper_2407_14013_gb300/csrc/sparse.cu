@@ -28,22 +28,50 @@ constexpr int ST = 256;
 
 inline unsigned nb(int64_t total) { return (unsigned)((total + ST - 1) / ST); }
 
+// Lengths of the arrays that the index tables address (used by the bounds-checked build only).
+struct SpLen {
+  int64_t nnz;    // entries: con, row, col, val, perm, epos
+  int64_t nnzY;   // symmetric pattern: ycol, ypidx
+  int npos;       // distinct positions: pos_r, pos_c, position values
+  int m;          // constraints: y
+};
+
+inline SpLen lens(const SparseA& S) { return SpLen{S.nnz, S.nnzY, S.npos, S.m}; }
+
+// Sites of the checks in the bounds-checked build (the site number kept with a violation)
+enum : int {
+  kAdjPtr = 1, kAdjPerm, kAdjCon, kAdjPos,              // sparse_adjoint_kernel
+  kAppPtr, kAppRC,                                      // sparse_apply_kernel
+  kBPtr, kBRC,                                          // sparse_B_kernel
+  kValPtr, kValPerm, kValCon,                           // sparse_posval_kernel
+  kMmPtr, kMmPidx, kMmCol,                              // sym_spmm_kernel
+  kEyPtr, kEyPidx, kEyCol,                              // sparse_EY_kernel
+  kDotPtr, kDotRow,                                     // pos_dots_col_kernel
+  kApPtr, kApPos, kApRC,                                // sparse_apply_pos_kernel
+  kSelfTest                                             // oob_selftest_kernel
+};
+
 // Y[r, c] = Y[c, r] = sum over the entries e at position (r, c) of y[con_e] val_e (times scale)
 __global__ void sparse_adjoint_kernel(int n, int npos, const int32_t* __restrict__ pos_r,
                                       const int32_t* __restrict__ pos_c, const int32_t* __restrict__ pos_ptr,
                                       const int32_t* __restrict__ perm, const int32_t* __restrict__ con,
                                       const double* __restrict__ val, const double* __restrict__ y, double scale,
-                                      double* __restrict__ Y, const int32_t* __restrict__ done) {
+                                      double* __restrict__ Y, SpLen L, const int32_t* __restrict__ done) {
   if (done && *done) return;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= npos) return;
   double s = 0.0;
   for (int k = pos_ptr[p]; k < pos_ptr[p + 1]; ++k) {
+    if (!WC_IN(kAdjPtr, k, L.nnz)) break;
     const int e = perm[k];
-    s = fma(y[con[e]], val[e], s);
+    if (!WC_IN(kAdjPerm, e, L.nnz)) continue;
+    const int i = con[e];
+    if (!WC_IN(kAdjCon, i, L.m)) continue;
+    s = fma(y[i], val[e], s);
   }
   s *= scale;
   const int r = pos_r[p], c = pos_c[p];
+  if (!WC_IN(kAdjPos, r, n) || !WC_IN(kAdjPos, c, n)) return;
   Y[r + (int64_t)c * n] = s;
   Y[c + (int64_t)r * n] = s;
 }
@@ -54,13 +82,15 @@ __global__ void sparse_apply_kernel(int n, int m, int r, const int32_t* __restri
                                     const int32_t* __restrict__ row, const int32_t* __restrict__ col,
                                     const double* __restrict__ val, const double* __restrict__ Z,
                                     const double* __restrict__ U, const double* __restrict__ Q,
-                                    double* __restrict__ out, const int32_t* __restrict__ done) {
+                                    double* __restrict__ out, SpLen L, const int32_t* __restrict__ done) {
   if (done && *done) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   double s = 0.0;
   for (int e = con_ptr[i]; e < con_ptr[i + 1]; ++e) {
+    if (!WC_IN(kAppPtr, e, L.nnz)) break;
     const int a = row[e], b = col[e];   // a >= b
+    if (!WC_IN(kAppRC, a, n) || !WC_IN(kAppRC, b, n)) continue;
     double z = Z[a + (int64_t)b * n];
     if (U) {
       double t = 0.0;
@@ -77,10 +107,12 @@ __global__ void sparse_apply_kernel(int n, int m, int r, const int32_t* __restri
 // (Vs^T A_i Q)[k, j] = sum_e val_e (Vs[r,k] Q[c,j] + Vs[c,k] Q[r,j])  (one term when r = c)
 __device__ __forceinline__ double sparse_H(int n, int k, int j, int e0, int e1, const int32_t* __restrict__ row,
                                            const int32_t* __restrict__ col, const double* __restrict__ val,
-                                           const double* __restrict__ Vs) {
+                                           const double* __restrict__ Vs, int64_t nnz) {
   double s = 0.0;
   for (int e = e0; e < e1; ++e) {
+    if (!WC_IN(kBPtr, e, nnz)) break;
     const int a = row[e], b = col[e];
+    if (!WC_IN(kBRC, a, n) || !WC_IN(kBRC, b, n)) continue;
     double t = Vs[a + (int64_t)k * n] * Vs[b + (int64_t)j * n];
     if (a != b) t += Vs[b + (int64_t)k * n] * Vs[a + (int64_t)j * n];
     s = fma(val[e], t, s);
@@ -91,7 +123,7 @@ __device__ __forceinline__ double sparse_H(int n, int k, int j, int e0, int e1, 
 __global__ void sparse_B_kernel(int n, int m, int r, const int32_t* __restrict__ con_ptr,
                                 const int32_t* __restrict__ row, const int32_t* __restrict__ col,
                                 const double* __restrict__ val, const double* __restrict__ Vs, double* __restrict__ B,
-                                int64_t ldB, double* __restrict__ Bt, int64_t ldBt) {
+                                int64_t ldB, double* __restrict__ Bt, int64_t ldBt, SpLen L) {
   const int d = n * r - r * (r - 1) / 2;
   const int nb_ = r * (r + 1) / 2;
   const int64_t total = (int64_t)m * d;
@@ -103,12 +135,14 @@ __global__ void sparse_B_kernel(int n, int m, int r, const int32_t* __restrict__
       int j = 0, base = 0;
       while (h >= base + (r - j)) { base += r - j; ++j; }
       const int a = j + (h - base);
-      if (a == j) v = sparse_H(n, a, a, e0, e1, row, col, val, Vs);
-      else v = WC_SQRT2 * 0.5 * (sparse_H(n, a, j, e0, e1, row, col, val, Vs) + sparse_H(n, j, a, e0, e1, row, col, val, Vs));
+      if (a == j) v = sparse_H(n, a, a, e0, e1, row, col, val, Vs, L.nnz);
+      else
+        v = WC_SQRT2 * 0.5 *
+            (sparse_H(n, a, j, e0, e1, row, col, val, Vs, L.nnz) + sparse_H(n, j, a, e0, e1, row, col, val, Vs, L.nnz));
     } else {
       const int qq = h - nb_;
       const int k = qq % (n - r), j = qq / (n - r);
-      v = WC_SQRT2 * sparse_H(n, r + k, j, e0, e1, row, col, val, Vs);
+      v = WC_SQRT2 * sparse_H(n, r + k, j, e0, e1, row, col, val, Vs, L.nnz);
     }
     B[(int64_t)i * ldB + h] = v;
     if (Bt) Bt[(int64_t)h * ldBt + i] = v;
@@ -117,15 +151,19 @@ __global__ void sparse_B_kernel(int n, int m, int r, const int32_t* __restrict__
 
 __global__ void sparse_posval_kernel(int npos, const int32_t* __restrict__ pos_ptr, const int32_t* __restrict__ perm,
                                      const int32_t* __restrict__ con, const double* __restrict__ val,
-                                     const double* __restrict__ y, double* __restrict__ ypos,
+                                     const double* __restrict__ y, double* __restrict__ ypos, SpLen L,
                                      const int32_t* __restrict__ done) {
   if (done && *done) return;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= npos) return;
   double s = 0.0;
   for (int k = pos_ptr[p]; k < pos_ptr[p + 1]; ++k) {
+    if (!WC_IN(kValPtr, k, L.nnz)) break;
     const int e = perm[k];
-    s = fma(y[con[e]], val[e], s);
+    if (!WC_IN(kValPerm, e, L.nnz)) continue;
+    const int i = con[e];
+    if (!WC_IN(kValCon, i, L.m)) continue;
+    s = fma(y[i], val[e], s);
   }
   ypos[p] = s;
 }
@@ -134,14 +172,19 @@ __global__ void sparse_posval_kernel(int npos, const int32_t* __restrict__ pos_p
 __global__ void sym_spmm_kernel(int n, const int32_t* __restrict__ yptr, const int32_t* __restrict__ ycol,
                                 const int32_t* __restrict__ ypidx, const double* __restrict__ ypos,
                                 const double* __restrict__ Bm, int64_t ldb, double* __restrict__ Out, int64_t ldo,
-                                const int32_t* __restrict__ done) {
+                                SpLen L, const int32_t* __restrict__ done) {
   if (done && *done) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int j = blockIdx.y;
   const double* b = Bm + (int64_t)j * ldb;
   double s = 0.0;
-  for (int k = yptr[i]; k < yptr[i + 1]; ++k) s = fma(ypos[ypidx[k]], b[ycol[k]], s);
+  for (int k = yptr[i]; k < yptr[i + 1]; ++k) {
+    if (!WC_IN(kMmPtr, k, L.nnzY)) break;
+    const int p = ypidx[k], c = ycol[k];
+    if (!WC_IN(kMmPidx, p, L.npos) || !WC_IN(kMmCol, c, n)) continue;
+    s = fma(ypos[p], b[c], s);
+  }
   Out[i + (int64_t)j * ldo] = s;
 }
 
@@ -151,7 +194,7 @@ __global__ void sym_spmm_kernel(int n, const int32_t* __restrict__ yptr, const i
 constexpr int EY_ROWS = 4;   // rows per thread
 __global__ void sparse_EY_kernel(int n, const int32_t* __restrict__ yptr, const int32_t* __restrict__ ycol,
                                  const int32_t* __restrict__ ypidx, const double* __restrict__ ypos,
-                                 const double* __restrict__ E, double* __restrict__ F,
+                                 const double* __restrict__ E, double* __restrict__ F, SpLen L,
                                  const int32_t* __restrict__ done) {
   if (done && *done) return;
   const int c = blockIdx.x;
@@ -160,8 +203,11 @@ __global__ void sparse_EY_kernel(int n, const int32_t* __restrict__ yptr, const 
 #pragma unroll
   for (int q = 0; q < EY_ROWS; ++q) acc[q] = 0.0;
   for (int k = yptr[c]; k < yptr[c + 1]; ++k) {
-    const double w = ypos[ypidx[k]];
-    const double* ec = E + (int64_t)ycol[k] * n;
+    if (!WC_IN(kEyPtr, k, L.nnzY)) break;
+    const int p = ypidx[k], col = ycol[k];
+    if (!WC_IN(kEyPidx, p, L.npos) || !WC_IN(kEyCol, col, n)) continue;
+    const double w = ypos[p];
+    const double* ec = E + (int64_t)col * n;
 #pragma unroll
     for (int q = 0; q < EY_ROWS; ++q) {
       const int i = i0 + q * ST;
@@ -179,7 +225,7 @@ __global__ void sparse_EY_kernel(int n, const int32_t* __restrict__ yptr, const 
 // per column b stages row b of F in shared memory, one warp per position reads a column of E.
 __global__ void pos_dots_col_kernel(int n, const int32_t* __restrict__ cptr, const int32_t* __restrict__ pos_r,
                                     const double* __restrict__ E, const double* __restrict__ F,
-                                    double* __restrict__ zpos, const int32_t* __restrict__ done) {
+                                    double* __restrict__ zpos, SpLen L, const int32_t* __restrict__ done) {
   if (done && *done) return;
   extern __shared__ double frow[];
   const int b = blockIdx.x;
@@ -189,7 +235,10 @@ __global__ void pos_dots_col_kernel(int n, const int32_t* __restrict__ cptr, con
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int p = p0 + warp; p < p1; p += nw) {
-    const double* ea = E + (int64_t)pos_r[p] * n;
+    if (!WC_IN(kDotPtr, p, L.npos)) break;
+    const int a = pos_r[p];
+    if (!WC_IN(kDotRow, a, n)) continue;
+    const double* ea = E + (int64_t)a * n;
     double s = 0.0;
     for (int c = lane; c < n; c += 32) s = fma(ea[c], frow[c], s);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -201,15 +250,19 @@ __global__ void sparse_apply_pos_kernel(int n, int m, int r, const int32_t* __re
                                         const int32_t* __restrict__ row, const int32_t* __restrict__ col,
                                         const double* __restrict__ val, const int32_t* __restrict__ epos,
                                         const double* __restrict__ zpos, const double* __restrict__ U,
-                                        const double* __restrict__ Q, double* __restrict__ out,
+                                        const double* __restrict__ Q, double* __restrict__ out, SpLen L,
                                         const int32_t* __restrict__ done) {
   if (done && *done) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   double s = 0.0;
   for (int e = con_ptr[i]; e < con_ptr[i + 1]; ++e) {
+    if (!WC_IN(kApPtr, e, L.nnz)) break;
     const int a = row[e], b = col[e];
-    double z = zpos ? zpos[epos[e]] : 0.0;
+    if (!WC_IN(kApRC, a, n) || !WC_IN(kApRC, b, n)) continue;
+    const int p = zpos ? epos[e] : 0;
+    if (zpos && !WC_IN(kApPos, p, L.npos)) continue;
+    double z = zpos ? zpos[p] : 0.0;
     if (U) {
       double t = 0.0;
       for (int k = 0; k < r; ++k)
@@ -232,6 +285,10 @@ __global__ void sparse_sumsq_kernel(int64_t nnz, const int32_t* __restrict__ row
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
+// One check of index i against bound and nothing else (no memory is addressed): lets a test see
+// a violation recorded and reported without an out-of-range index ever reaching an access.
+__global__ void oob_selftest_kernel(int64_t i, int64_t bound) { (void)WC_IN(kSelfTest, i, bound); }
+
 __global__ void sum_parts_kernel(const double* __restrict__ part, int np, double* __restrict__ out) {
   __shared__ double sh[32];
   double acc = 0.0;
@@ -246,13 +303,13 @@ void sparse_adjoint(cudaStream_t st, const SparseA& S, int n, const double* y, d
                     const int32_t* done, int64_t* launches) {
   if (S.npos > 0)
     sparse_adjoint_kernel<<<nb(S.npos), ST, 0, st>>>(n, S.npos, S.pos_r, S.pos_c, S.pos_ptr, S.perm, S.con, S.val, y,
-                                                     scale, Y, done);
+                                                     scale, Y, lens(S), done);
   if (launches) ++*launches;
 }
 
 void sparse_apply(cudaStream_t st, const SparseA& S, int n, int m, int r, const double* Z, const double* U,
                   const double* Q, double* out, const int32_t* done, int64_t* launches) {
-  sparse_apply_kernel<<<nb(m), ST, 0, st>>>(n, m, r, S.con_ptr, S.row, S.col, S.val, Z, U, Q, out, done);
+  sparse_apply_kernel<<<nb(m), ST, 0, st>>>(n, m, r, S.con_ptr, S.row, S.col, S.val, Z, U, Q, out, lens(S), done);
   if (launches) ++*launches;
 }
 
@@ -261,28 +318,29 @@ void sparse_B(cudaStream_t st, const SparseA& S, int n, int m, int r, const doub
   const int d = n * r - r * (r - 1) / 2;
   int64_t blocks = ((int64_t)m * d + ST - 1) / ST;
   if (blocks > 16 * (int64_t)g_num_sms) blocks = 16 * (int64_t)g_num_sms;
-  sparse_B_kernel<<<(unsigned)blocks, ST, 0, st>>>(n, m, r, S.con_ptr, S.row, S.col, S.val, Vs, B, ldB, Bt, ldBt);
+  sparse_B_kernel<<<(unsigned)blocks, ST, 0, st>>>(n, m, r, S.con_ptr, S.row, S.col, S.val, Vs, B, ldB, Bt, ldBt,
+                                                   lens(S));
   if (launches) ++*launches;
 }
 
 void sparse_posval(cudaStream_t st, const SparseA& S, const double* y, double* ypos, const int32_t* done,
                    int64_t* launches) {
   if (S.npos > 0)
-    sparse_posval_kernel<<<nb(S.npos), ST, 0, st>>>(S.npos, S.pos_ptr, S.perm, S.con, S.val, y, ypos, done);
+    sparse_posval_kernel<<<nb(S.npos), ST, 0, st>>>(S.npos, S.pos_ptr, S.perm, S.con, S.val, y, ypos, lens(S), done);
   if (launches) ++*launches;
 }
 
 void sparse_sym_spmm(cudaStream_t st, const SparseA& S, int n, int ncols, const double* ypos, const double* Bm,
                      int64_t ldb, double* Out, int64_t ldo, const int32_t* done, int64_t* launches) {
   dim3 grid(nb(n), (unsigned)ncols);
-  sym_spmm_kernel<<<grid, ST, 0, st>>>(n, S.yptr, S.ycol, S.ypidx, ypos, Bm, ldb, Out, ldo, done);
+  sym_spmm_kernel<<<grid, ST, 0, st>>>(n, S.yptr, S.ycol, S.ypidx, ypos, Bm, ldb, Out, ldo, lens(S), done);
   if (launches) ++*launches;
 }
 
 void sparse_EY(cudaStream_t st, const SparseA& S, int n, const double* ypos, const double* E, double* F,
                const int32_t* done, int64_t* launches) {
   dim3 grid((unsigned)n, (unsigned)((n + ST * EY_ROWS - 1) / (ST * EY_ROWS)));
-  sparse_EY_kernel<<<grid, ST, 0, st>>>(n, S.yptr, S.ycol, S.ypidx, ypos, E, F, done);
+  sparse_EY_kernel<<<grid, ST, 0, st>>>(n, S.yptr, S.ycol, S.ypidx, ypos, E, F, lens(S), done);
   if (launches) ++*launches;
 }
 
@@ -295,7 +353,7 @@ cudaError_t sparse_prepare(int n) {
 cudaError_t sparse_pos_dots_col(cudaStream_t st, const SparseA& S, int n, const double* E, const double* F,
                                 double* zpos, const int32_t* done, int64_t* launches) {
   const size_t smem = (size_t)n * sizeof(double);
-  pos_dots_col_kernel<<<(unsigned)n, ST, smem, st>>>(n, S.cptr, S.pos_r, E, F, zpos, done);
+  pos_dots_col_kernel<<<(unsigned)n, ST, smem, st>>>(n, S.cptr, S.pos_r, E, F, zpos, lens(S), done);
   if (launches) ++*launches;
   return cudaGetLastError();
 }
@@ -303,8 +361,13 @@ cudaError_t sparse_pos_dots_col(cudaStream_t st, const SparseA& S, int n, const 
 void sparse_apply_pos(cudaStream_t st, const SparseA& S, int n, int m, int r, const double* zpos, const double* U,
                       const double* Q, double* out, const int32_t* done, int64_t* launches) {
   sparse_apply_pos_kernel<<<nb(m), ST, 0, st>>>(n, m, r, S.con_ptr, S.row, S.col, S.val, S.epos, zpos, U, Q, out,
-                                                done);
+                                                lens(S), done);
   if (launches) ++*launches;
+}
+
+cudaError_t sparse_bounds_selftest(cudaStream_t st, int64_t index, int64_t bound) {
+  oob_selftest_kernel<<<1, 1, 0, st>>>(index, bound);
+  return cudaGetLastError();
 }
 
 void sparse_sumsq(cudaStream_t st, const SparseA& S, double* out, double* scratch, int64_t* launches) {

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 import subprocess
+import sys
 
 import pytest
 
@@ -39,6 +40,28 @@ def test_library_exports_every_declared_symbol(lib):
     for name in declared_functions():
         assert name in exported, f"{name} declared in wcipm.h but not exported"
         assert name in _native.EXPORTS, f"{name} has no binding"
+
+
+def test_checked_build_exports_the_same_symbols_and_registers_its_checks(lib):
+    """libwcipm_checked.so (the sparse operator's gathers and scatters compiled with
+    -DSDP_CHECK_BOUNDS) exports the same boundary; in it the bounds records exist, so
+    sdp_bounds_report reaches the device (SDP_ECUDA without one) instead of answering
+    SDP_EUNSUPPORTED as the default build does.  The default build answers SDP_EUNSUPPORTED
+    before any CUDA call."""
+    from paper_2407_14013_gb300 import _native
+    out = subprocess.run(["nm", "-D", "--defined-only", _native.LIB_CHECKED_PATH], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r"\bT (sdp_[a-z_]+)", out))
+    for name in declared_functions():
+        assert name in exported, f"{name} not exported by the checked build"
+    assert _native.sdp_bounds_report() == (_native.SDP_EUNSUPPORTED, 0, 0)
+    assert _native.sdp_bounds_selftest(0, -1, 10) == _native.SDP_EUNSUPPORTED
+    code = ("from paper_2407_14013_gb300 import _native as n; n.load(n.LIB_CHECKED_PATH); "
+            "import torch; g = torch.cuda.is_available(); st, f, c = n.sdp_bounds_report(); "
+            "assert st == (n.SDP_OK if g else n.SDP_ECUDA) and f == c == 0, st; "
+            "assert n.sdp_bounds_selftest(0, 1, -1) == n.SDP_EINVAL; print('ok')")
+    res = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert res.returncode == 0 and res.stdout.strip().endswith("ok"), res.stderr[-2000:]
 
 
 def test_struct_layout_matches_header(lib):
