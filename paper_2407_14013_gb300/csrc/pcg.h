@@ -102,9 +102,9 @@ void launch_ctl_reset(cudaStream_t st, PcgCtl* dst, const PcgCtl* src, int max_i
 int launch_diag_FE(cudaStream_t st, int n, const double* F, const double* E, double* part, int max_slabs,
                    int64_t* launches);
 
-// Small DIAG problems (n <= 128, r <= 16), m-space form, FP64 PCG: the whole solve from the right
-// side (g, and x0 = [0; -g_v / D] unless start0) through the stop test in one launch of one
-// thread-block cluster (small_pcg.cu).  Reads Vs, E o E, K^{-1} (m x m), D and the control block;
+// Small DIAG problems (n <= 128, r <= 16, shared memory <= 227 KB per CTA), m-space form, FP64
+// PCG: the whole solve from the right side (g, and x0 = [0; -g_v / D] unless start0) through the
+// stop test in one launch of one thread-block cluster (small_pcg.cu).  Reads Vs, E o E, K^{-1} (m x m), D and the control block;
 // leaves x, r, z, p, Ap and the PCG scalars as the launch chain of the loop does.
 // small_pcg_smem_bytes: its shared memory for (n, r, d), 0 when the shape is outside its range.
 size_t small_pcg_smem_bytes(int n, int r, int d);

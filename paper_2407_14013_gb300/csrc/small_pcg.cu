@@ -50,7 +50,7 @@ struct SmallArgs {
 
 // Shared-memory layout (doubles): the CTA's slices, then the vectors and scratch.
 struct SmallLayout {
-  int vsr, vsc, q, eer, pir, dv, idv, X, R, Z, P, AP, hp, ha, hq, wb, red, total;
+  int vsr, vsc, q, eer, pir, dv, idv, X, R, Z, P, AP, hp, ha, hq, tq, wb, red, total;
   __host__ __device__ SmallLayout(int n, int r, int d, int chunk) {
     const int nt = n + d;
     int o = 0;
@@ -72,6 +72,7 @@ struct SmallLayout {
     // start of an apply and read before its first cluster barrier, and hq receives the other
     // CTAs' rows only between the second and third barriers of a preconditioner apply
     hp = hq;
+    tq = o;  o += n * r;         // T = diag(t) Q for H = Vs^T T (every CTA makes its own)
     wb = o;  o += n;             // w = r_u + B D^{-1} r_v (rows from every CTA)
     red = o; o += 64;            // block reductions
     total = o;
@@ -130,72 +131,147 @@ __device__ void cta_unpack(int n, int r, const double* v, const double* idv, dou
   }
 }
 
-// This CTA's rows i = i0 + il of U = Vs Hp (Hp in shared memory), each finished into one value
-// written at dst[i] in every CTA of the cluster:
-//   OP:  (M v)_u[i] = ((E o E) v_u)[i] + sum_k U[i, k] Q[i, k]     (the operator's u-block)
-//   !OP: w[i]       = v_u[i] + sum_k U[i, k] Q[i, k]               (w = r_u + B D^{-1} r_v)
-// A warp per row: the lanes split the length-n sums (r + 1 independent chains each), then a
-// butterfly sum leaves the totals in every lane.  RB >= r: the width of the accumulator block.
-template <bool OP, int RB>
+// Transposed butterfly over the warp of K accumulators per lane (K a power of two, 1..32): at
+// each of the first log2 K levels a lane keeps half of its live accumulators (the lower half if
+// its lane bit is clear) and adds the partner's copy of that half, so K - 1 additions leave one
+// accumulator per lane; plain butterfly levels finish it.  Returns the total of component
+// lane >> (5 - log2 K), the same bits in every lane that holds it.  FP64 additions cost a warp
+// instruction each on GB300's narrow FP64 pipe: K - 1 + 5 - log2 K of them instead of 5 K.
+template <int K>
+__device__ __forceinline__ double warp_treduce(double (&a)[K], int lane) {
+#pragma unroll
+  for (int h = K / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const double send = upper ? a[j] : a[j + h];
+      const double keep = upper ? a[j + h] : a[j];
+      a[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  double v = a[0];
+#pragma unroll
+  for (int o = 16 / K; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int K>
+__device__ __forceinline__ int treduce_comp(int lane) {
+  return K == 1 ? 0 : lane >> (5 - (K >= 32 ? 5 : K >= 16 ? 4 : K >= 8 ? 3 : K >= 4 ? 2 : 1));
+}
+
+// Writes the total v of component comp (held by the 32 / K lanes with that component) into
+// dst[off] of every CTA of the cluster: each of those lanes covers SC K / 32 ranks.
+template <int K>
+__device__ __forceinline__ void put_all(const cg::cluster_group& cl, int lane, double v, double* dst) {
+  constexpr int LPC = 32 / K;                       // lanes per component
+  const int t = lane & (LPC - 1);
+#pragma unroll
+  for (int q = t; q < SC; q += LPC) *cl.map_shared_rank(dst, q) = v;
+}
+
+// This CTA's rows i = i0 + il of U = Vs Hp (Hp in shared memory), each finished into
+// w[i] = v_u[i] + sum_k U[i, k] Q[i, k] (w = r_u + B D^{-1} r_v) and written at dst[i] in every
+// CTA of the cluster.  A warp per row: the lanes split the length-n sums (RB independent chains
+// each), a transposed butterfly finds U[i, :], and a butterfly over the components forms the sum.
+template <int RB>
 __device__ __noinline__ void rows_pass(SmallCtx c, const double* vu, double* dst) {
   const cg::cluster_group cl = cg::this_cluster();
   const SmallLayout L(c.n, c.r, c.d, c.chunk);
   const int n = c.n, r = c.r;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double* Hp = c.sm + L.hp;
+  const int comp = treduce_comp<RB>(lane);
   for (int il = warp; il < c.rows; il += SNW) {
     const double* vr = c.sm + L.vsr + il * n;
-    const double* er = c.sm + L.eer + il * n;
     double acc[RB];
 #pragma unroll
     for (int j = 0; j < RB; ++j) acc[j] = 0.0;
-    double ee = 0.0;
     for (int a = lane; a < n; a += 32) {
       const double va = vr[a];
 #pragma unroll
       for (int j = 0; j < RB; ++j)
         if (j < r) acc[j] = fma(va, Hp[a + j * n], acc[j]);
-      if (OP) ee = fma(er[a], vu[a], ee);
     }
-#pragma unroll
-    for (int j = 0; j < RB; ++j)
-      if (j < r) acc[j] = warp_allsum(acc[j]);
     const int i = c.i0 + il;
-    double v = OP ? warp_allsum(ee) : vu[i];
+    const double u = warp_treduce<RB>(acc, lane);                  // U[i, comp]
+    double t = comp < r ? u * c.sm[L.q + i + comp * n] : 0.0;      // U[i, comp] Q[i, comp]
 #pragma unroll
-    for (int k = 0; k < RB; ++k)
-      if (k < r) v = fma(acc[k], c.sm[L.q + i + k * n], v);
+    for (int o = 16; o >= 32 / RB; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    const double v = vu[i] + t;
     if (lane < SC) *cl.map_shared_rank(dst + i, lane) = v;
   }
 }
 
-// This CTA's rows a = i0 + al of H = Vs^T diag(t) Q (n x r): H[a, j] = sum_i Vs[i, a] (t_i Q[i, j]),
-// written at dstH[a + j n] in every CTA of the cluster.
+// This CTA's rows a = i0 + al of H = Vs^T T with T = diag(t) Q (n x r, formed in shared memory
+// beforehand): H[a, j] = sum_i Vs[i, a] T[i, j], written at dstH[a + j n] in every CTA.
 template <int RB>
-__device__ __noinline__ void cols_pass(SmallCtx c, const double* t, double* dstH) {
+__device__ __noinline__ void cols_pass(SmallCtx c, double* dstH) {
   const cg::cluster_group cl = cg::this_cluster();
   const SmallLayout L(c.n, c.r, c.d, c.chunk);
   const int n = c.n, r = c.r;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double* T = c.sm + L.tq;
+  const int comp = treduce_comp<RB>(lane);
   for (int al = warp; al < c.rows; al += SNW) {
     const double* vc = c.sm + L.vsc + al * n;
     double acc[RB];
 #pragma unroll
     for (int j = 0; j < RB; ++j) acc[j] = 0.0;
     for (int i = lane; i < n; i += 32) {
-      const double w = vc[i], ti = t[i];
+      const double w = vc[i];
 #pragma unroll
       for (int j = 0; j < RB; ++j)
-        if (j < r) acc[j] = fma(w, ti * c.sm[L.q + i + j * n], acc[j]);
+        if (j < r) acc[j] = fma(w, T[i + j * n], acc[j]);
     }
     const int a = c.i0 + al;
+    const double h = warp_treduce<RB>(acc, lane);
+    if (comp < r) put_all<RB>(cl, lane, h, dstH + a + comp * n);
+  }
+}
+
+// The operator's two products in one pass over this CTA's rows: row i of U = Vs unpack(v_v) and
+// row i of H = Vs^T T (T = diag(v_u) Q) side by side in one transposed butterfly of 2 RB
+// accumulators, plus ((E o E) v_u)_i; finished into (M v)_u[i] = ((E o E) v_u)_i +
+// sum_k U[i, k] Q[i, k] at dst[i] and H[i, :] at dstH, in every CTA.
+template <int RB>
+__device__ __noinline__ void op_pass(SmallCtx c, const double* v, double* dst, double* dstH) {
+  constexpr int K = 2 * RB;
+  const cg::cluster_group cl = cg::this_cluster();
+  const SmallLayout L(c.n, c.r, c.d, c.chunk);
+  const int n = c.n, r = c.r;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double* Hp = c.sm + L.hp;
+  const double* T = c.sm + L.tq;
+  const int comp = treduce_comp<K>(lane);                          // < RB: U[i, comp]; else H[i, comp - RB]
+  for (int il = warp; il < c.rows; il += SNW) {
+    const double* vr = c.sm + L.vsr + il * n;
+    const double* vc = c.sm + L.vsc + il * n;
+    const double* er = c.sm + L.eer + il * n;
+    double acc[K];
 #pragma unroll
-    for (int j = 0; j < RB; ++j) {
-      if (j < r) {
-        const double hj = warp_allsum(acc[j]);
-        if (lane < SC) *cl.map_shared_rank(dstH + a + j * n, lane) = hj;
+    for (int j = 0; j < K; ++j) acc[j] = 0.0;
+    double ee = 0.0;
+    for (int x = lane; x < n; x += 32) {
+      const double va = vr[x], vcx = vc[x];
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        if (j < r) {
+          acc[j] = fma(va, Hp[x + j * n], acc[j]);
+          acc[RB + j] = fma(vcx, T[x + j * n], acc[RB + j]);
+        }
       }
+      ee = fma(er[x], v[x], ee);
     }
+    const int i = c.i0 + il;
+    const double s = warp_treduce<K>(acc, lane);
+    ee = warp_allsum(ee);
+    // (M v)_u[i]: the terms U[i, k] Q[i, k] sit in the lanes of components k < RB (lanes < 16)
+    double t = comp < r ? s * c.sm[L.q + i + comp * n] : 0.0;
+#pragma unroll
+    for (int o = 8; o >= 32 / K; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane < SC) *cl.map_shared_rank(dst + i, lane) = ee + t;
+    if (comp >= RB && comp - RB < r) put_all<K>(cl, lane, s, dstH + i + (comp - RB) * n);
   }
 }
 
@@ -214,42 +290,61 @@ __device__ void pinv_pass(SmallCtx c, double* dst) {
   }
 }
 
-// out = M v, or g - M v when g != NULL (one cluster barrier)
+// T = diag(t) Q (n x r) in shared memory, every CTA its own copy
+__device__ void cta_scale_q(int n, int r, const double* t, const double* Q, double* T) {
+  for (int q = threadIdx.x; q < n * r; q += SNT) {
+    const int j = q / n, i = q - j * n;
+    T[q] = t[i] * Q[q];
+  }
+}
+
+// out = M v, or g - M v when g != NULL (one cluster barrier); returns <v, out>
 template <int RB>
-__device__ __noinline__ void op_apply(SmallCtx c, const double* v, double* out, const double* __restrict__ g) {
+__device__ __noinline__ double op_apply(SmallCtx c, const double* v, double* out, const double* __restrict__ g) {
   const cg::cluster_group cl = cg::this_cluster();
   const SmallLayout L(c.n, c.r, c.d, c.chunk);
   const int n = c.n, r = c.r, d = c.d, m = n;
   cta_unpack(n, r, v + m, nullptr, c.sm + L.hp);
+  cta_scale_q(n, r, v, c.sm + L.q, c.sm + L.tq);
   __syncthreads();
-  rows_pass<true, RB>(c, v, out);
-  cols_pass<RB>(c, v, c.sm + L.ha);
+  op_pass<RB>(c, v, out, c.sm + L.ha);
   cl.sync();
+  double acc = 0.0;
   for (int q = threadIdx.x; q < m + d; q += SNT) {
     double val = q < m ? out[q] : pack_at(c.sm + L.ha, n, n, r, q - m) - c.sm[L.dv + q - m] * v[q];
     if (g) val = g[q] - val;
     out[q] = val;
+    acc = fma(v[q], val, acc);
   }
-  __syncthreads();
+  return cta_sum(acc, c.sm + L.red);   // its barriers also order the writes above
 }
 
-// z = P^{-1} rin in the m-space form (three cluster barriers)
+// z = P^{-1} rin in the m-space form (three cluster barriers); returns <rin, z>
 template <int RB>
-__device__ __noinline__ void pc_apply(SmallCtx c, const double* rin, double* z) {
+__device__ __noinline__ double pc_apply(SmallCtx c, const double* rin, double* z) {
   const cg::cluster_group cl = cg::this_cluster();
   const SmallLayout L(c.n, c.r, c.d, c.chunk);
   const int n = c.n, r = c.r, d = c.d, m = n;
   cta_unpack(n, r, rin + m, c.sm + L.idv, c.sm + L.hp);       // unpack(D^{-1} r_v)
   __syncthreads();
-  rows_pass<false, RB>(c, rin, c.sm + L.wb);                    // w = r_u + B D^{-1} r_v
+  rows_pass<RB>(c, rin, c.sm + L.wb);                    // w = r_u + B D^{-1} r_v
   cl.sync();
   pinv_pass(c, z);                                              // z_u = K^{-1} w
   cl.sync();
-  cols_pass<RB>(c, z, c.sm + L.hq);                             // Vs^T diag(z_u) Q
-  cl.sync();
-  for (int h = threadIdx.x; h < d; h += SNT)                    // z_v = D^{-1}(B^T z_u - r_v)
-    z[m + h] = (pack_at(c.sm + L.hq, n, n, r, h) - rin[m + h]) * c.sm[L.idv + h];
+  cta_scale_q(n, r, z, c.sm + L.q, c.sm + L.tq);
   __syncthreads();
+  cols_pass<RB>(c, c.sm + L.hq);                                // Vs^T diag(z_u) Q
+  cl.sync();
+  double acc = 0.0;
+  for (int q = threadIdx.x; q < m + d; q += SNT) {              // z_v = D^{-1}(B^T z_u - r_v)
+    double zq = z[q];
+    if (q >= m) {
+      zq = (pack_at(c.sm + L.hq, n, n, r, q - m) - rin[q]) * c.sm[L.idv + q - m];
+      z[q] = zq;
+    }
+    acc = fma(rin[q], zq, acc);
+  }
+  return cta_sum(acc, c.sm + L.red);
 }
 
 template <int RB>
@@ -303,8 +398,7 @@ __global__ void __cluster_dims__(SC, 1, 1) __launch_bounds__(SNT) small_pcg_kern
   double alpha = ctl->alpha, pAp = ctl->pAp;
   cl.sync();   // every CTA has started and holds its operands before any writes into it
   if (A.start0) {   // x0 = P^{-1} [0; g_v], so that P x0 = [0; g_v] and r0_v = 0 (Cor. pcg)
-    pc_apply<RB>(c, Z, X);
-    const double t = cta_dot(Z, X, nt, red);
+    const double t = pc_apply<RB>(c, Z, X);
     if (!isfinite(t)) { status = 5; done = 1; }
   }
   if (!done) {   // r0 = g - M x0, ||r0||^2 and the stop test; z0 = P^{-1} r0; p0 = z0
@@ -315,16 +409,14 @@ __global__ void __cluster_dims__(SC, 1, 1) __launch_bounds__(SNT) small_pcg_kern
     else if (rr <= tol2) done = 1;
   }
   if (!done) {
-    pc_apply<RB>(c, R, Z);
-    rz = cta_dot(R, Z, nt, red);
+    rz = pc_apply<RB>(c, R, Z);
     beta = 0.0;
     if (!isfinite(rz)) { status = 5; done = 1; }
     for (int q = threadIdx.x; q < nt; q += SNT) P[q] = Z[q];
     __syncthreads();
   }
   while (!done) {
-    op_apply<RB>(c, P, AP, nullptr);
-    pAp = cta_dot(P, AP, nt, red);
+    pAp = op_apply<RB>(c, P, AP, nullptr);
     // Def. pcg has no sign condition: with the indefinite preconditioner <p, M p> is positive in
     // exact arithmetic but may change sign at the rounding floor
     if (pAp == 0.0 || !isfinite(pAp) || !isfinite(rz)) { status = 5; done = 1; break; }
@@ -342,8 +434,7 @@ __global__ void __cluster_dims__(SC, 1, 1) __launch_bounds__(SNT) small_pcg_kern
     else if (rr <= tol2) { status = 0; done = 1; }
     else if (iters >= max_iters) { status = 4; done = 1; }
     if (done) break;
-    pc_apply<RB>(c, R, Z);
-    const double t = cta_dot(R, Z, nt, red);
+    const double t = pc_apply<RB>(c, R, Z);
     if (!isfinite(t)) { status = 5; done = 1; }
     rz_new = t;
     beta = t / rz;
