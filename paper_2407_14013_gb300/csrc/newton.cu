@@ -678,8 +678,7 @@ bool pc_coop_on(const sdp_handle* h) {
 bool small_pcg_on(const sdp_handle* h) {
   if (h->kind != SDP_A_DIAG || h->mixed || h->opt.krylov != 0 || h->space != 2 || h->lin || h->prof) return false;
   if (!h->opt.use_graph || !h->small_ok) return false;
-  const size_t b = small_pcg_smem_bytes(h->n, h->r, h->d);
-  return b > 0 && b <= 227 * 1024;
+  return small_pcg_plan(h->n, h->r, h->d, nullptr) > 0;
 }
 
 // Inside the PCG loop the update x += alpha p, r -= alpha Ap runs in the last block of the
@@ -1172,6 +1171,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   }
   int r = h->r, d = h->d;
   bool rhs_side = false;   // the right side's products run beside the preconditioner setup
+  int rhs_slabs = 0;       // DIAG: slabs of diag(F E) left in S.Y by the side stream
   if (!reuse) {
   h->setup_valid = false;
   // ---- a1: split ----
@@ -1218,15 +1218,20 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   // needs E, Q and D only, and the factorisation of a2 is a chain of small launches that leaves
   // most of the GPU idle.  The finishing kernel (which reads the factorisation's status) stays on
   // the handle's stream after the join.
-  rhs_side = !h->prof && h->kind == SDP_A_DENSE_SVEC && n < kTcMin && h->opt.krylov != 1;
+  rhs_side = !h->prof && (h->kind == SDP_A_DENSE_SVEC || h->kind == SDP_A_DIAG) && n < kTcMin &&
+             h->opt.krylov != 1;
   if (rhs_side) {
     cudaStream_t s0 = fork(h, 0, 4);
     CU(gemm_big(h, s0, false, false, n, n, n, 1.0, S.E, n, Ct, n, 0.0, S.F, n, h->ws_b[0], h->ws_b_elems, L));
     CU(gemm_big(h, s0, false, false, n, r, n, 1.0, Ct, n, S.Vs, n, 0.0, S.Tm, n, h->ws_b[0], h->ws_b_elems, L));
     CU(gemm_big(h, s0, true, false, n, r, n, 1.0, S.Vs, n, S.Tm, n, 0.0, S.H, n, h->ws_b[0], h->ws_b_elems, L));
-    CU(gemm_big(h, s0, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, h->ws_b[0], h->ws_b_elems, L,
-                GEMM_LOWER));
-    CU(pack_apply_dense(h, S, s0, r, nullptr, nullptr, nullptr, L));
+    if (h->kind == SDP_A_DIAG) {   // A(E C~ E) = diag(F E) in slabs, into S.Y (free until the recovery)
+      rhs_slabs = launch_diag_FE(s0, n, S.F, S.E, S.Y, n, L);
+    } else {
+      CU(gemm_big(h, s0, false, false, n, n, n, 1.0, S.F, n, S.E, n, 0.0, S.Z, n, h->ws_b[0], h->ws_b_elems, L,
+                  GEMM_LOWER));
+      CU(pack_apply_dense(h, S, s0, r, nullptr, nullptr, nullptr, L));
+    }
   }
 
   // ---- a2: B = A Q and the preconditioner core (MINRES: only E o E of the DIAG operator) ----
@@ -1272,10 +1277,11 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   } else if (pd > h->pinv_dim) {
     return fail(h, SDP_EINVAL, "preconditioner core larger than the setup allows");
   } else if (h->kind == SDP_A_DIAG && h->space == 2) {
-    // K = beta I + tau^-2 G o (G + 2 tau E) with G = Q (Lam - tau I) Q^T (lower triangle)
-    launch_shift_cols(st, n, r, S.Vs, h->lam_s, h->ctl, S.Tm, L);
-    CU(gemm_big(h, st, false, true, n, n, r, 1.0, S.Tm, n, S.Vs, n, 0.0, S.F, n, S.ws, ws, L, GEMM_LOWER));
-    launch_diag_K(st, n, S.F, S.E, h->ctl, S.Pinv, L);
+    // K = beta I + tau^-2 G o (G + 2 tau E) with G = Q (Lam - tau I) Q^T (lower triangle), in
+    // buffers the right side's products (perhaps running beside) do not use
+    launch_shift_cols(st, n, r, S.Vs, h->lam_s, h->ctl, S.Hp, L);
+    CU(gemm_big(h, st, false, true, n, n, r, 1.0, S.Hp, n, S.Vs, n, 0.0, S.Z, n, S.ws, ws, L, GEMM_LOWER));
+    launch_diag_K(st, n, S.Z, S.E, h->ctl, S.Pinv, L);
     CU(spd_inverse_any(h, st, m, S.Pinv, S.ws, ws, pstatus, L));
   } else if (h->space == 1) {
     // C = beta^{-1} B^T B + tau^2 Sigma  (B row-major m x d == column-major d x m); with a linear
@@ -1334,8 +1340,9 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     launch_rhs_finish(st, m, d, n, r, S.partA, 1, nullptr, nullptr, bt, Ct, S.H, S.Dv, h->g, S.x,
                       h->opt.newton_rtol, h->ctl, h->dotbuf, h->counter, L);
   } else {   // DIAG: A(E C~ E) = diag(F E), summed in slabs over the whole GPU
-    const int slabs = launch_diag_FE(st, n, S.F, S.E, S.partA, (int)(rows_gemv_part_elems(n, n) / n), L);
-    launch_rhs_finish(st, m, d, n, r, S.partA, slabs, nullptr, nullptr, bt, Ct, S.H, S.Dv, h->g, S.x,
+    const double* part = S.Y;
+    if (!rhs_side) rhs_slabs = launch_diag_FE(st, n, S.F, S.E, S.Y, n, L);
+    launch_rhs_finish(st, m, d, n, r, part, rhs_slabs, nullptr, nullptr, bt, Ct, S.H, S.Dv, h->g, S.x,
                       h->opt.newton_rtol, h->ctl, h->dotbuf, h->counter, L);
   }
 

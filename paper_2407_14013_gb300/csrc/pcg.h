@@ -106,8 +106,9 @@ int launch_diag_FE(cudaStream_t st, int n, const double* F, const double* E, dou
 // PCG: the whole solve from the right side (g, and x0 = [0; -g_v / D] unless start0) through the
 // stop test in one launch of one thread-block cluster (small_pcg.cu).  Reads Vs, E o E, K^{-1} (m x m), D and the control block;
 // leaves x, r, z, p, Ap and the PCG scalars as the launch chain of the loop does.
-// small_pcg_smem_bytes: its shared memory for (n, r, d), 0 when the shape is outside its range.
-size_t small_pcg_smem_bytes(int n, int r, int d);
+// small_pcg_plan: the cluster size it launches with for (n, r, d) (16 where that cluster can be
+// resident and n > 32, else 8) and its shared memory per CTA; 0 when the shape is outside its range.
+int small_pcg_plan(int n, int r, int d, size_t* bytes);
 cudaError_t launch_small_pcg(cudaStream_t st, int n, int r, int d, int start0, const double* Vs, const double* EE,
                              const double* Pinv, const double* Dv, const double* g, double* x, double* rv, double* z,
                              double* p, double* Ap, PcgCtl* ctl, int64_t* launches);

@@ -1,6 +1,6 @@
 // The whole FP64 PCG solve of the augmented system (eq. augsys; Def. pcg with Cor. pcg's start)
 // for small DIAG problems (A_i = e_i e_i^T, m = n <= 128) in the m-space preconditioner form, held
-// by one thread-block cluster of SC CTAs: one launch instead of about 16 per iteration.
+// by one thread-block cluster of 8 or 16 CTAs: one launch instead of about 16 per iteration.
 //
 // An iteration of the launch chain it replaces is a string of tiny products (n x r outputs of
 // length-n sums) and vector kernels; at n = 64 each one costs its launch and a few FP64 latency
@@ -25,6 +25,9 @@
 // B^T u = pack(Vs^T diag(u) Q)), and the PCG scalars of Def. pcg.
 #include <cooperative_groups.h>
 
+#include <mutex>
+#include <unordered_map>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "pcg.h"
@@ -35,7 +38,7 @@ namespace {
 
 namespace cg = cooperative_groups;
 
-constexpr int SC = 8;              // CTAs of the cluster (the portable maximum)
+constexpr int SCL = 16;            // CTAs of the cluster: 16 (non-portable) where it launches, else 8
 constexpr int SNT = 256;           // threads per CTA
 constexpr int SNW = SNT / 32;
 constexpr int SRMAX = 16;          // largest r
@@ -87,7 +90,7 @@ __device__ __forceinline__ double warp_allsum(double v) {
 
 // What every pass needs to find its data: the shape, this CTA's rows, the shared memory.
 struct SmallCtx {
-  int n, r, d, chunk, i0, rows;
+  int n, r, d, chunk, i0, rows, ncta;
   double* sm;
 };
 
@@ -161,13 +164,12 @@ __device__ __forceinline__ int treduce_comp(int lane) {
 }
 
 // Writes the total v of component comp (held by the 32 / K lanes with that component) into
-// dst[off] of every CTA of the cluster: each of those lanes covers SC K / 32 ranks.
+// dst of every CTA of the cluster (ncta of them): each of those lanes covers ncta K / 32 ranks.
 template <int K>
-__device__ __forceinline__ void put_all(const cg::cluster_group& cl, int lane, double v, double* dst) {
+__device__ __forceinline__ void put_all(const cg::cluster_group& cl, int lane, int ncta, double v, double* dst) {
   constexpr int LPC = 32 / K;                       // lanes per component
   const int t = lane & (LPC - 1);
-#pragma unroll
-  for (int q = t; q < SC; q += LPC) *cl.map_shared_rank(dst, q) = v;
+  for (int q = t; q < ncta; q += LPC) *cl.map_shared_rank(dst, q) = v;
 }
 
 // This CTA's rows i = i0 + il of U = Vs Hp (Hp in shared memory), each finished into
@@ -199,7 +201,7 @@ __device__ __noinline__ void rows_pass(SmallCtx c, const double* vu, double* dst
 #pragma unroll
     for (int o = 16; o >= 32 / RB; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     const double v = vu[i] + t;
-    if (lane < SC) *cl.map_shared_rank(dst + i, lane) = v;
+    if (lane < c.ncta) *cl.map_shared_rank(dst + i, lane) = v;
   }
 }
 
@@ -226,7 +228,7 @@ __device__ __noinline__ void cols_pass(SmallCtx c, double* dstH) {
     }
     const int a = c.i0 + al;
     const double h = warp_treduce<RB>(acc, lane);
-    if (comp < r) put_all<RB>(cl, lane, h, dstH + a + comp * n);
+    if (comp < r) put_all<RB>(cl, lane, c.ncta, h, dstH + a + comp * n);
   }
 }
 
@@ -270,8 +272,8 @@ __device__ __noinline__ void op_pass(SmallCtx c, const double* v, double* dst, d
     double t = comp < r ? s * c.sm[L.q + i + comp * n] : 0.0;
 #pragma unroll
     for (int o = 8; o >= 32 / K; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane < SC) *cl.map_shared_rank(dst + i, lane) = ee + t;
-    if (comp >= RB && comp - RB < r) put_all<K>(cl, lane, s, dstH + i + (comp - RB) * n);
+    if (lane < c.ncta) *cl.map_shared_rank(dst + i, lane) = ee + t;
+    if (comp >= RB && comp - RB < r) put_all<K>(cl, lane, c.ncta, s, dstH + i + (comp - RB) * n);
   }
 }
 
@@ -286,7 +288,7 @@ __device__ void pinv_pass(SmallCtx c, double* dst) {
     double s = 0.0;
     for (int l = lane; l < n; l += 32) s = fma(pr[l], c.sm[L.wb + l], s);
     s = warp_allsum(s);
-    if (lane < SC) *cl.map_shared_rank(dst + c.i0 + il, lane) = s;
+    if (lane < c.ncta) *cl.map_shared_rank(dst + c.i0 + il, lane) = s;
   }
 }
 
@@ -348,7 +350,7 @@ __device__ __noinline__ double pc_apply(SmallCtx c, const double* rin, double* z
 }
 
 template <int RB>
-__global__ void __cluster_dims__(SC, 1, 1) __launch_bounds__(SNT) small_pcg_kernel(SmallArgs A) {
+__global__ void __launch_bounds__(SNT) small_pcg_kernel(SmallArgs A) {
   const cg::cluster_group cl = cg::this_cluster();
   extern __shared__ double sm[];
   PcgCtl* ctl = A.ctl;
@@ -361,6 +363,7 @@ __global__ void __cluster_dims__(SC, 1, 1) __launch_bounds__(SNT) small_pcg_kern
   c.r = r;
   c.d = d;
   c.chunk = A.chunk;
+  c.ncta = (int)cl.num_blocks();
   c.i0 = rank * A.chunk;
   c.rows = max(0, min(A.chunk, n - c.i0));
   c.sm = sm;
@@ -470,26 +473,77 @@ __global__ void __cluster_dims__(SC, 1, 1) __launch_bounds__(SNT) small_pcg_kern
 
 }  // namespace
 
-size_t small_pcg_smem_bytes(int n, int r, int d) {
+namespace {
+
+const void* small_pcg_fn(int r) {
+  return r <= 4 ? (const void*)small_pcg_kernel<4>
+                : r <= 8 ? (const void*)small_pcg_kernel<8> : (const void*)small_pcg_kernel<SRMAX>;
+}
+
+size_t layout_bytes(int n, int r, int d, int ncta) {
+  return (size_t)SmallLayout(n, r, d, (n + ncta - 1) / ncta).total * sizeof(double);
+}
+
+// Whether a 16-CTA cluster of this kernel (one CTA per SM at up to 227 KB of shared memory) can
+// be resident on this device: asked once per kernel, by the occupancy query.
+bool cluster16_ok(const void* fn) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, bool> known;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = known.find(fn);
+  if (it != known.end()) return it->second;
+  bool ok = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+            raise_dyn_smem(fn, 227 * 1024) == cudaSuccess;
+  if (ok) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(SCL);
+    cfg.blockDim = dim3(SNT);
+    cfg.dynamicSmemBytes = 227 * 1024;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = SCL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int num = 0;
+    ok = cudaOccupancyMaxActiveClusters(&num, fn, &cfg) == cudaSuccess && num >= 1;
+  }
+  cudaGetLastError();
+  known[fn] = ok;
+  return ok;
+}
+
+}  // namespace
+
+int small_pcg_plan(int n, int r, int d, size_t* bytes) {
+  if (bytes) *bytes = 0;
   if (n < 2 || n > SNMAX || r < 1 || r > SRMAX || r >= n) return 0;
-  const int chunk = (n + SC - 1) / SC;
-  return (size_t)SmallLayout(n, r, d, chunk).total * sizeof(double);
+  constexpr size_t kMax = 227 * 1024;
+  // 16 CTAs once there are rows for them (twice the FP64 pipes for the products), else 8
+  if (n > 32 && layout_bytes(n, r, d, SCL) <= kMax && cluster16_ok(small_pcg_fn(r))) {
+    if (bytes) *bytes = layout_bytes(n, r, d, SCL);
+    return SCL;
+  }
+  if (layout_bytes(n, r, d, 8) > kMax) return 0;
+  if (bytes) *bytes = layout_bytes(n, r, d, 8);
+  return 8;
 }
 
 cudaError_t launch_small_pcg(cudaStream_t st, int n, int r, int d, int start0, const double* Vs, const double* EE,
                              const double* Pinv, const double* Dv, const double* g, double* x, double* rv, double* z,
                              double* p, double* Ap, PcgCtl* ctl, int64_t* launches) {
-  const size_t bytes = small_pcg_smem_bytes(n, r, d);
-  if (bytes == 0 || bytes > 227 * 1024) return cudaErrorInvalidValue;
-  const void* fn = r <= 4 ? (const void*)small_pcg_kernel<4>
-                  : r <= 8 ? (const void*)small_pcg_kernel<8> : (const void*)small_pcg_kernel<SRMAX>;
+  size_t bytes = 0;
+  const int ncta = small_pcg_plan(n, r, d, &bytes);
+  if (ncta == 0) return cudaErrorInvalidValue;
+  const void* fn = small_pcg_fn(r);
   cudaError_t e = raise_dyn_smem(fn, (int)bytes);
   if (e != cudaSuccess) return e;
   SmallArgs A;
   A.n = n;
   A.r = r;
   A.d = d;
-  A.chunk = (n + SC - 1) / SC;
+  A.chunk = (n + ncta - 1) / ncta;
   A.start0 = start0;
   A.Vs = Vs;
   A.EE = EE;
@@ -502,11 +556,22 @@ cudaError_t launch_small_pcg(cudaStream_t st, int n, int r, int d, int start0, c
   A.p = p;
   A.Ap = Ap;
   A.ctl = ctl;
-  if (r <= 4) small_pcg_kernel<4><<<SC, SNT, bytes, st>>>(A);
-  else if (r <= 8) small_pcg_kernel<8><<<SC, SNT, bytes, st>>>(A);
-  else small_pcg_kernel<SRMAX><<<SC, SNT, bytes, st>>>(A);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ncta);
+  cfg.blockDim = dim3(SNT);
+  cfg.dynamicSmemBytes = bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)ncta;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  void* args[] = {&A};
+  e = cudaLaunchKernelExC(&cfg, fn, args);
   if (launches) ++*launches;
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace wc

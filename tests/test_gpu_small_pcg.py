@@ -5,9 +5,10 @@ x0 through the stop test, as one launch of one thread-block cluster; use_graph =
 launch chain (a dozen kernels per iteration).  Both are checked against the oracle's plain
 definition of the Newton direction (relative 1e-8, the FP64 bar of the other parity tests)
 and against each other (relative 1e-10: the same iteration in another summation order).
-The shapes cover fewer rows than CTAs (n = 5), a ragged last CTA (n = 100), the largest r and
-n that fit in shared memory, both starts of Cor. pcg, the iteration limit, and the shapes that
-fall back to the launch chain.
+The shapes cover fewer rows than CTAs (n = 5), a ragged last CTA (n = 100), the largest n and r
+(n = 128 with r = 16 fits in shared memory with 16 CTAs of 8 rows), 8- and 16-CTA clusters
+(n <= 32 and n > 32), both starts of Cor. pcg, the iteration limit, and the shapes that fall
+back to the launch chain.
 """
 import numpy as np
 import pytest
@@ -46,6 +47,7 @@ CASES = [
     ("maxcut100_ragged", lambda: W.maxcut(100, 0.08, 1303, weights="gauss"), 5, 1e-3, 8),
     ("maxcut120_r16", lambda: W.maxcut(120, 0.06, 1304, weights="gauss"), 16, 1e-3, 16),
     ("maxcut128_r12", lambda: W.maxcut(128, 0.06, 1311, weights="gauss"), 12, 1e-3, 12),
+    ("maxcut128_r16", lambda: W.maxcut(128, 0.06, 1312, weights="gauss"), 16, 1e-3, 16),
 ]
 
 
@@ -81,10 +83,10 @@ def test_cluster_solve_stops_at_the_iteration_limit():
     assert rel(X1, X2) < 1e-10 and rel(y1, y2) < 1e-10
 
 
-@pytest.mark.parametrize("n,rt", [(129, 3), (128, 16)])
+@pytest.mark.parametrize("n,rt", [(129, 3), (130, 16)])
 def test_shapes_outside_the_cluster_range_take_the_launch_chain(n, rt):
-    """n = 129 (above the cluster solve's range) and n = 128 with r = 16 (its shared memory above
-    227 KB per CTA) give the oracle's direction through the launch chain."""
+    """n above 128 (the cluster solve's range) gives the oracle's direction through the launch
+    chain."""
     prob = W.maxcut(n, 0.05, 1308)
     sp = W.scaling_point(n, rt, 1e-3, 1309)
     Ct, bt = W.newton_rhs(n, n, 1310)
