@@ -1340,10 +1340,10 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     launch_rhs_finish(st, m, d, n, r, S.partA, 1, nullptr, nullptr, bt, Ct, S.H, S.Dv, h->g, S.x,
                       h->opt.newton_rtol, h->ctl, h->dotbuf, h->counter, L);
   } else {   // DIAG: A(E C~ E) = diag(F E), summed in slabs over the whole GPU
-    const double* part = S.Y;
     if (!rhs_side) rhs_slabs = launch_diag_FE(st, n, S.F, S.E, S.Y, n, L);
-    launch_rhs_finish(st, m, d, n, r, part, rhs_slabs, nullptr, nullptr, bt, Ct, S.H, S.Dv, h->g, S.x,
-                      h->opt.newton_rtol, h->ctl, h->dotbuf, h->counter, L);
+    if (!small_pcg_on(h))   // else the cluster solve finishes the right side itself
+      launch_rhs_finish(st, m, d, n, r, S.Y, rhs_slabs, nullptr, nullptr, bt, Ct, S.H, S.Dv, h->g, S.x,
+                        h->opt.newton_rtol, h->ctl, h->dotbuf, h->counter, L);
   }
 
   phase.next("a4-a7 Krylov solve");
@@ -1357,11 +1357,14 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
     bool small = small_pcg_on(h);
     if (small) {   // the whole solve in one cluster launch
       const cudaError_t e = launch_small_pcg(st, n, r, d, h->opt.pcg_start == 0 ? 1 : 0, S.Vs, S.EE, S.Pinv, S.Dv,
-                                             h->g, S.x, S.rv, S.z, S.p, S.Ap, S.ctl, L);
+                                             S.Y, rhs_slabs, bt, Ct, S.H, h->opt.newton_rtol, h->g, S.x, S.rv,
+                                             S.z, S.p, S.Ap, S.ctl, L);
       if (e != cudaSuccess) {   // refused on this device (launch configuration): the launch chain
         cudaGetLastError();
         h->small_ok = false;
         small = false;
+        launch_rhs_finish(st, m, d, n, r, S.Y, rhs_slabs, nullptr, nullptr, bt, Ct, S.H, S.Dv, h->g, S.x,
+                          h->opt.newton_rtol, h->ctl, h->dotbuf, h->counter, L);
       }   // no host read here: the recovery reads the scalars on the device, the host at the end
     }
     if (!small) {

@@ -103,15 +103,18 @@ int launch_diag_FE(cudaStream_t st, int n, const double* F, const double* E, dou
                    int64_t* launches);
 
 // Small DIAG problems (n <= 128, r <= 16, shared memory <= 227 KB per CTA), m-space form, FP64
-// PCG: the whole solve from the right side (g, and x0 = [0; -g_v / D] unless start0) through the
-// stop test in one launch of one thread-block cluster (small_pcg.cu).  Reads Vs, E o E, K^{-1} (m x m), D and the control block;
+// PCG: the whole solve in one launch of one thread-block cluster (small_pcg.cu), from the right
+// side's finishing step (rhs_finish's work: g from the slabs of diag(F E), b~ and H = Vs^T C~ Q,
+// x0, ||[svec C~; b~]|| and the stop threshold rtol^2 ||.||^2) through the stop test.  Reads Vs,
+// E o E, K^{-1} (m x m), D and the control block (tau, max_iters, the setup's status);
 // leaves x, r, z, p, Ap and the PCG scalars as the launch chain of the loop does.
 // small_pcg_plan: the cluster size it launches with for (n, r, d) (16 where that cluster can be
 // resident and n > 32, else 8) and its shared memory per CTA; 0 when the shape is outside its range.
 int small_pcg_plan(int n, int r, int d, size_t* bytes);
 cudaError_t launch_small_pcg(cudaStream_t st, int n, int r, int d, int start0, const double* Vs, const double* EE,
-                             const double* Pinv, const double* Dv, const double* g, double* x, double* rv, double* z,
-                             double* p, double* Ap, PcgCtl* ctl, int64_t* launches);
+                             const double* Pinv, const double* Dv, const double* part, int slabs, const double* bt,
+                             const double* Ct, const double* H, double rtol, double* g, double* x, double* rv,
+                             double* z, double* p, double* Ap, PcgCtl* ctl, int64_t* launches);
 
 // DIAG kind, m-space core without an explicit B: w = r_u + rowdot(U, Q); z_v = (pack(H) - r_v) / D;
 // Tm = Q (Lam - tau I); K = beta I + tau^-2 G o (G + 2 tau E) (lower triangle)

@@ -45,15 +45,17 @@ constexpr int SRMAX = 16;          // largest r
 constexpr int SNMAX = 128;         // largest n
 
 struct SmallArgs {
-  int n, r, d, chunk, start0;
-  const double *Vs, *EE, *Pinv, *Dv, *g;
-  double *x, *rv, *z, *p, *Ap;
+  int n, r, d, chunk, start0, slabs;
+  double rtol;
+  const double *Vs, *EE, *Pinv, *Dv;
+  const double *part, *bt, *Ct, *Hg;   // the right side's inputs: diag(F E) slabs, b~, C~, Vs^T C~ Q
+  double *g, *x, *rv, *z, *p, *Ap;
   PcgCtl* ctl;
 };
 
 // Shared-memory layout (doubles): the CTA's slices, then the vectors and scratch.
 struct SmallLayout {
-  int vsr, vsc, q, eer, pir, dv, idv, X, R, Z, P, AP, hp, ha, hq, tq, wb, red, total;
+  int vsr, vsc, q, eer, pir, dv, idv, X, R, Z, P, AP, hp, ha, hq, tq, wb, red, cbp, total;
   __host__ __device__ SmallLayout(int n, int r, int d, int chunk) {
     const int nt = n + d;
     int o = 0;
@@ -78,6 +80,7 @@ struct SmallLayout {
     tq = o;  o += n * r;         // T = diag(t) Q for H = Vs^T T (every CTA makes its own)
     wb = o;  o += n;             // w = r_u + B D^{-1} r_v (rows from every CTA)
     red = o; o += 64;            // block reductions
+    cbp = o; o += 32;            // every CTA's share of ||C~||_F^2 + ||b~||^2
     total = o;
   }
 };
@@ -354,7 +357,6 @@ __global__ void __launch_bounds__(SNT) small_pcg_kernel(SmallArgs A) {
   const cg::cluster_group cl = cg::this_cluster();
   extern __shared__ double sm[];
   PcgCtl* ctl = A.ctl;
-  if (ctl->done) return;   // the right side already ended the solve (the same in every CTA)
   const int n = A.n, r = A.r, d = A.d, m = n, nt = n + d;
   const SmallLayout L(n, r, d, A.chunk);
   const int rank = (int)cl.block_rank();
@@ -390,22 +392,56 @@ __global__ void __launch_bounds__(SNT) small_pcg_kernel(SmallArgs A) {
   double* P = sm + L.P;
   double* AP = sm + L.AP;
   double* red = sm + L.red;
+  // the right side of eq. augsys, g = [b~ + tau^2 diag(F E); tau^2 pack(Vs^T C~ Q)] (kept in AP
+  // until the loop needs it), x0 = [0; -g_v / D] (Cor. pcg's printed start) and [0; g_v] (the
+  // right side of the default start's correction)
+  const double tau = ctl->tau, t2 = tau * tau;
+  __syncthreads();   // D in shared memory
   for (int q = threadIdx.x; q < nt; q += SNT) {
-    X[q] = A.start0 ? 0.0 : A.x[q];
-    Z[q] = q < m ? 0.0 : A.g[q];   // [0; g_v]: the start's correction right side
+    double v;
+    if (q < m) {
+      double a = 0.0;
+      for (int sl = 0; sl < A.slabs; ++sl) a += A.part[(int64_t)sl * m + q];
+      v = A.bt[q] + t2 * a;
+    } else {
+      v = t2 * pack_at(A.Hg, n, n, r, q - m);
+    }
+    AP[q] = v;
+    X[q] = (A.start0 || q < m) ? 0.0 : -v / sm[L.dv + q - m];
+    Z[q] = q < m ? 0.0 : v;
+    if (rank == 0) A.g[q] = v;
   }
-  const double tol2 = ctl->tol2;
+  // ||[svec C~; b~]||^2 (the right side of (Newt-eps)): this CTA's share now, the total after the
+  // next cluster barrier
+  const int64_t ncb = (int64_t)n * n + m, seg = (ncb + c.ncta - 1) / c.ncta;
+  double cpart = 0.0;
+  for (int64_t q = rank * seg + threadIdx.x; q < ncb && q < (rank + 1) * seg; q += SNT) {
+    const double v = q < (int64_t)n * n ? A.Ct[q] : A.bt[q - (int64_t)n * n];
+    cpart = fma(v, v, cpart);
+  }
+  cpart = cta_sum(cpart, red);
+  const double gg = cta_dot(AP, AP, nt, red);
   const int max_iters = ctl->max_iters;
-  int iters = ctl->iters, status = ctl->status, done = 0;
-  double rr = ctl->rr, rr0 = ctl->rr0, rz = ctl->rz, rz_new = ctl->rz_new, beta = ctl->beta;
-  double alpha = ctl->alpha, pAp = ctl->pAp;
+  int iters = 0, status = ctl->status, done = 0;   // status: a non-positive pivot in the setup
+  double rr = 0.0, rr0 = 0.0, rz = 0.0, rz_new = 0.0, beta = 0.0, alpha = 0.0, pAp = 0.0, tol2 = 0.0;
+  if (!isfinite(gg)) status = 5;
+  if (status != 0) done = 1;
   cl.sync();   // every CTA has started and holds its operands before any writes into it
-  if (A.start0) {   // x0 = P^{-1} [0; g_v], so that P x0 = [0; g_v] and r0_v = 0 (Cor. pcg)
+  if (threadIdx.x < c.ncta) *cl.map_shared_rank(sm + L.cbp + rank, (int)threadIdx.x) = cpart;
+  auto rhs_norm2 = [&]() {   // after a cluster barrier that follows the shares' writes
+    double cb = 0.0;
+    for (int k = 0; k < c.ncta; ++k) cb += sm[L.cbp + k];
+    return cb;
+  };
+  if (done) cl.sync();
+  if (A.start0 && !done) {   // x0 = P^{-1} [0; g_v], so that P x0 = [0; g_v] and r0_v = 0 (Cor. pcg)
     const double t = pc_apply<RB>(c, Z, X);
     if (!isfinite(t)) { status = 5; done = 1; }
   }
   if (!done) {   // r0 = g - M x0, ||r0||^2 and the stop test; z0 = P^{-1} r0; p0 = z0
-    op_apply<RB>(c, X, R, A.g);
+    op_apply<RB>(c, X, R, AP);
+    // stop when ||r_k|| <= rtol ||[svec C~; b~]|| (the (Newt-eps) residual of the recovered direction)
+    tol2 = A.rtol * A.rtol * rhs_norm2();
     rr = cta_dot(R, R, nt, red);
     if (iters == 0) rr0 = rr;
     if (!isfinite(rr)) { status = 5; done = 1; }
@@ -456,6 +492,10 @@ __global__ void __launch_bounds__(SNT) small_pcg_kernel(SmallArgs A) {
       A.Ap[q] = AP[q];
     }
     if (threadIdx.x == 0) {
+      const double cb = rhs_norm2();
+      ctl->g_norm2 = gg;
+      ctl->newt_rhs2 = cb;
+      ctl->tol2 = A.rtol * A.rtol * cb;
       ctl->rr = rr;
       ctl->rr0 = rr0;
       ctl->rz = rz;
@@ -531,8 +571,9 @@ int small_pcg_plan(int n, int r, int d, size_t* bytes) {
 }
 
 cudaError_t launch_small_pcg(cudaStream_t st, int n, int r, int d, int start0, const double* Vs, const double* EE,
-                             const double* Pinv, const double* Dv, const double* g, double* x, double* rv, double* z,
-                             double* p, double* Ap, PcgCtl* ctl, int64_t* launches) {
+                             const double* Pinv, const double* Dv, const double* part, int slabs, const double* bt,
+                             const double* Ct, const double* H, double rtol, double* g, double* x, double* rv,
+                             double* z, double* p, double* Ap, PcgCtl* ctl, int64_t* launches) {
   size_t bytes = 0;
   const int ncta = small_pcg_plan(n, r, d, &bytes);
   if (ncta == 0) return cudaErrorInvalidValue;
@@ -545,6 +586,12 @@ cudaError_t launch_small_pcg(cudaStream_t st, int n, int r, int d, int start0, c
   A.d = d;
   A.chunk = (n + ncta - 1) / ncta;
   A.start0 = start0;
+  A.slabs = slabs;
+  A.rtol = rtol;
+  A.part = part;
+  A.bt = bt;
+  A.Ct = Ct;
+  A.Hg = H;
   A.Vs = Vs;
   A.EE = EE;
   A.Pinv = Pinv;
