@@ -485,8 +485,22 @@ int spd_coop_blocks() {
 // launch is not possible here.
 cudaError_t spd_coop(cudaStream_t st, int n, double* A, int64_t lda, double* X, int64_t ldx, double* Li, bool inv,
                      int32_t* status, unsigned int* flag, int64_t* launches) {
-  const int blocks = spd_coop_blocks();
+  int blocks = spd_coop_blocks();
   if (blocks <= 0 || n > kCoopMax || n < 1 || (inv && !X)) return cudaErrorNotSupported;
+  // no more CTAs than the largest phase C has units for (CTA 0 factors the pivot blocks, the others
+  // take the units): the barriers are shorter, and at small n most SMs stay free for the work on
+  // other streams (the right side's products beside the preconditioner setup)
+  {
+    const int nb = (n + NB - 1) / NB;
+    int units = 0;
+    for (int k = 0; k < nb; ++k) {
+      const int mc = nb - k - 1;
+      const int u = 4 * ((mc > 0 ? 1 : 0) + (mc > 0 ? mc * (mc + 1) / 2 - 1 : 0) + (X ? mc * (k + 1) : 0) +
+                         (inv ? (k + 1) * (k + 2) / 2 : 0));
+      units = std::max(units, std::max(u, 4 * (nb - k - 1) + (X ? 4 * k : 0)));   // phases C and B
+    }
+    blocks = std::min(blocks, std::max(16, units + 1));
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(256);
