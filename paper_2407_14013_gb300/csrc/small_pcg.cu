@@ -137,6 +137,30 @@ __device__ void cta_unpack(int n, int r, const double* v, const double* idv, dou
   }
 }
 
+// The unpack of one v-block entry k (value val, already scaled as wanted) into Hp: the thread that
+// makes entry k writes its one or two places, so an update loop can leave the unpack of its vector
+// ready for the next product pass (the inverse of the index map of cta_unpack).
+__device__ __forceinline__ void hp_put(int n, int r, int k, double val, double* Hp) {
+  const int nb = r * (r + 1) / 2;
+  if (k < nb) {
+    int jj = 0, base = 0;
+    while (k >= base + (r - jj)) {
+      base += r - jj;
+      ++jj;
+    }
+    const int i = jj + (k - base);
+    if (i == jj) {
+      Hp[i + jj * n] = val;
+    } else {
+      Hp[i + jj * n] = val * WC_RSQRT2;
+      Hp[jj + i * n] = val * WC_RSQRT2;
+    }
+  } else {
+    const int q = k - nb;
+    Hp[r + q % (n - r) + (q / (n - r)) * n] = WC_SQRT2 * val;
+  }
+}
+
 // Transposed butterfly over the warp of K accumulators per lane (K a power of two, 1..32): at
 // each of the first log2 K levels a lane keeps half of its live accumulators (the lower half if
 // its lane bit is clear) and adds the partner's copy of that half, so K - 1 additions leave one
@@ -305,12 +329,15 @@ __device__ void cta_scale_q(int n, int r, const double* t, const double* Q, doub
 
 // out = M v, or g - M v when g != NULL (one cluster barrier); returns <v, out>
 template <int RB>
-__device__ __noinline__ double op_apply(SmallCtx c, const double* v, double* out, const double* __restrict__ g) {
+__device__ __noinline__ double op_apply(SmallCtx c, const double* v, double* out, const double* __restrict__ g,
+                                        bool ready) {
   const cg::cluster_group cl = cg::this_cluster();
   const SmallLayout L(c.n, c.r, c.d, c.chunk);
   const int n = c.n, r = c.r, d = c.d, m = n;
-  cta_unpack(n, r, v + m, nullptr, c.sm + L.hp);
-  cta_scale_q(n, r, v, c.sm + L.q, c.sm + L.tq);
+  if (!ready) {   // else the update loop that made v left them in place
+    cta_unpack(n, r, v + m, nullptr, c.sm + L.hp);
+    cta_scale_q(n, r, v, c.sm + L.q, c.sm + L.tq);
+  }
   __syncthreads();
   op_pass<RB>(c, v, out, c.sm + L.ha);
   cl.sync();
@@ -326,11 +353,11 @@ __device__ __noinline__ double op_apply(SmallCtx c, const double* v, double* out
 
 // z = P^{-1} rin in the m-space form (three cluster barriers); returns <rin, z>
 template <int RB>
-__device__ __noinline__ double pc_apply(SmallCtx c, const double* rin, double* z) {
+__device__ __noinline__ double pc_apply(SmallCtx c, const double* rin, double* z, bool ready) {
   const cg::cluster_group cl = cg::this_cluster();
   const SmallLayout L(c.n, c.r, c.d, c.chunk);
   const int n = c.n, r = c.r, d = c.d, m = n;
-  cta_unpack(n, r, rin + m, c.sm + L.idv, c.sm + L.hp);       // unpack(D^{-1} r_v)
+  if (!ready) cta_unpack(n, r, rin + m, c.sm + L.idv, c.sm + L.hp);   // unpack(D^{-1} r_v)
   __syncthreads();
   rows_pass<RB>(c, rin, c.sm + L.wb);                    // w = r_u + B D^{-1} r_v
   cl.sync();
@@ -435,11 +462,11 @@ __global__ void __launch_bounds__(SNT) small_pcg_kernel(SmallArgs A) {
   };
   if (done) cl.sync();
   if (A.start0 && !done) {   // x0 = P^{-1} [0; g_v], so that P x0 = [0; g_v] and r0_v = 0 (Cor. pcg)
-    const double t = pc_apply<RB>(c, Z, X);
+    const double t = pc_apply<RB>(c, Z, X, false);
     if (!isfinite(t)) { status = 5; done = 1; }
   }
   if (!done) {   // r0 = g - M x0, ||r0||^2 and the stop test; z0 = P^{-1} r0; p0 = z0
-    op_apply<RB>(c, X, R, AP);
+    op_apply<RB>(c, X, R, AP, false);
     // stop when ||r_k|| <= rtol ||[svec C~; b~]|| (the (Newt-eps) residual of the recovered direction)
     tol2 = A.rtol * A.rtol * rhs_norm2();
     rr = cta_dot(R, R, nt, red);
@@ -448,14 +475,22 @@ __global__ void __launch_bounds__(SNT) small_pcg_kernel(SmallArgs A) {
     else if (rr <= tol2) done = 1;
   }
   if (!done) {
-    rz = pc_apply<RB>(c, R, Z);
+    rz = pc_apply<RB>(c, R, Z, false);
     beta = 0.0;
     if (!isfinite(rz)) { status = 5; done = 1; }
-    for (int q = threadIdx.x; q < nt; q += SNT) P[q] = Z[q];
+    for (int q = threadIdx.x; q < nt; q += SNT) {   // p0 = z0, with its unpack and diag(p_u) Q
+      const double pq = Z[q];
+      P[q] = pq;
+      if (q >= m) {
+        hp_put(n, r, q - m, pq, sm + L.hp);
+      } else {
+        for (int j = 0; j < r; ++j) sm[L.tq + q + j * n] = pq * sm[L.q + q + j * n];
+      }
+    }
     __syncthreads();
   }
   while (!done) {
-    pAp = op_apply<RB>(c, P, AP, nullptr);
+    pAp = op_apply<RB>(c, P, AP, nullptr, true);
     // Def. pcg has no sign condition: with the indefinite preconditioner <p, M p> is positive in
     // exact arithmetic but may change sign at the rounding floor
     if (pAp == 0.0 || !isfinite(pAp) || !isfinite(rz)) { status = 5; done = 1; break; }
@@ -465,6 +500,7 @@ __global__ void __launch_bounds__(SNT) small_pcg_kernel(SmallArgs A) {
       X[q] = fma(alpha, P[q], X[q]);
       const double rq = fma(-alpha, AP[q], R[q]);
       R[q] = rq;
+      if (q >= m) hp_put(n, r, q - m, rq * sm[L.idv + q - m], sm + L.hp);   // unpack(D^{-1} r_v) for the next apply
       acc = fma(rq, rq, acc);
     }
     rr = cta_sum(acc, red);
@@ -473,13 +509,21 @@ __global__ void __launch_bounds__(SNT) small_pcg_kernel(SmallArgs A) {
     else if (rr <= tol2) { status = 0; done = 1; }
     else if (iters >= max_iters) { status = 4; done = 1; }
     if (done) break;
-    const double t = pc_apply<RB>(c, R, Z);
+    const double t = pc_apply<RB>(c, R, Z, true);
     if (!isfinite(t)) { status = 5; done = 1; }
     rz_new = t;
     beta = t / rz;
     rz = t;
     if (done) break;
-    for (int q = threadIdx.x; q < nt; q += SNT) P[q] = fma(beta, P[q], Z[q]);
+    for (int q = threadIdx.x; q < nt; q += SNT) {   // p = z + beta p, with its unpack and diag(p_u) Q
+      const double pq = fma(beta, P[q], Z[q]);
+      P[q] = pq;
+      if (q >= m) {
+        hp_put(n, r, q - m, pq, sm + L.hp);
+      } else {
+        for (int j = 0; j < r; ++j) sm[L.tq + q + j * n] = pq * sm[L.q + q + j * n];
+      }
+    }
     __syncthreads();
   }
   // the iterate and the scalars back to global memory (every CTA holds the same: rank 0 writes)
