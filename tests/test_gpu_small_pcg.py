@@ -95,3 +95,29 @@ def test_shapes_outside_the_cluster_range_take_the_launch_chain(n, rt):
     rX, ry, rS = onewton.newton_direct(prob, (sp.V * sp.lam) @ sp.V.T, Ct, bt)
     assert rel(X1, rX) < TOL and rel(y1, ry) < TOL
     assert l1 > 10 * i1.pcg_iters                      # a dozen launches per iteration
+
+
+def test_cluster_solve_zero_and_non_finite_right_sides():
+    """Through the cluster solve: a zero right side gives the zero direction at once (||r_0|| = 0
+    meets the threshold 0), a NaN in C~ is reported as SDP_ENUMERIC by the right side's finish
+    inside the kernel, and the handle then solves a good right side as before."""
+    import torch
+    from paper_2407_14013_gb300 import NewtonSolver, SdpError, native
+    prob = W.maxcut(40, 0.2, 1313)
+    sp = W.scaling_point(40, 3, 1e-3, 1314)
+    Ct, bt = W.newton_rhs(40, 40, 1315)
+    s = NewtonSolver(prob, r_hat=4, precond_space=2)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    dX, dy, dS, info = s.solve(t(sp.V), t(sp.lam), t(np.zeros_like(Ct)), t(np.zeros_like(bt)))
+    assert info.converged and info.status == 0 and info.pcg_iters == 0
+    assert not np.any(dX.cpu().numpy()) and not np.any(dy.cpu().numpy()) and not np.any(dS.cpu().numpy())
+    Cn = Ct.copy()
+    Cn[3, 5] = Cn[5, 3] = np.nan
+    with pytest.raises(SdpError) as e:
+        s.solve(t(sp.V), t(sp.lam), t(Cn), t(bt))
+    assert e.value.status == native.SDP_ENUMERIC
+    dX, dy, dS, info = s.solve(t(sp.V), t(sp.lam), t(Ct), t(bt))
+    assert info.converged
+    rX, ry, rS = onewton.newton_direct(prob, (sp.V * sp.lam) @ sp.V.T, Ct, bt)
+    assert rel(dX.cpu().numpy(), rX) < TOL and rel(dy.cpu().numpy(), ry) < TOL
+    s.close()
