@@ -502,6 +502,40 @@ def _maxcut64(dev, t, newton_rows):
     return out
 
 
+def apply_rates(solver, dev, reps: int = 20):
+    """Device time of one application of the augmented operator M (eq. augsys) and of the
+    preconditioner P^{-1} at the scaling point of the solver's last solve: `reps` applications
+    enqueued back to back on the solver's stream (sdp_apply_augsys returns without waiting)
+    between two CUDA events; the dense A is larger than L2, so every operator application
+    streams it from HBM."""
+    import statistics
+    import torch
+    d = solver.last_info.d
+    g = torch.Generator(device=dev)
+    g.manual_seed(11)
+    vec = torch.randn(solver.m + d, generator=g, device=dev, dtype=torch.float64)
+    st = torch.cuda.current_stream(dev)
+    out = {}
+    res = torch.empty_like(vec)
+    for which, key in ((0, "operator"), (1, "preconditioner")):
+        solver.apply(vec, which, out=res)
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(reps):
+                solver.apply(vec, which, out=res)
+            e1.record(st)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / reps)
+        ms = statistics.median(ts)
+        out[key] = {"us_per_apply": 1e3 * ms, "applies_per_s": 1e3 / ms}
+    out["timing"] = (f"{reps} applications back to back between two CUDA events (median of 3), launch gaps "
+                     "included; the PCG loop runs the same kernels as one CUDA graph")
+    return out
+
+
 def cpu_baseline(prob, ins, budget_s: float = 15.0, max_solves: int = 8):
     """The oracle's step-by-step reformulation (numpy FP64), timed on the host cores."""
     import numpy as np
@@ -641,6 +675,9 @@ def run_ours(args):
     solver.set_profiling(True)
     prof = timed(solver, max(4, min(args.steps, 10)), 1)
     solver.set_profiling(False)
+    # the operator and the preconditioner alone (one application each at the last solve's scaling
+    # point, through sdp_apply_augsys): the raw operator-only rate beside the PCG-iteration rate
+    op_only = apply_rates(solver, dev)
 
     # the mixed-precision forms (low-precision A E A^T block in the correction solves, FP64
     # refinement) on the same inputs: FP32 FFMA, TF32 and BF16 tensor-core products
@@ -777,6 +814,7 @@ def run_ours(args):
         "phase_ms_per_step": {"setup": res["setup"] / args.steps, "pcg": res["pcg"] / args.steps,
                               "recover": res["rec"] / args.steps},
         "roofline": roofline,
+        "operator_only": op_only,
         "clocks": clk.summary(),
         "gpu_launches": launches,
         "e2e": {"value": e2e_iters / e2e_s if e2e_steps else None, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -372,6 +372,21 @@ sdp_status sdp_newton_solve(sdp_handle* h, const double* V, const double* lam,
 sdp_status sdp_newton_resolve(sdp_handle* h, const double* Ct, const double* bt, double* dX, double* dy, double* dS,
                               sdp_newton_info* info);
 
+/* One application of the augmented operator or of the preconditioner at the scaling point of the
+ * most recent sdp_newton_solve on this handle (its split and preconditioner core): which = 0:
+ * out = M pin with M = [[A E A^T, A Q], [Q^T A^T, -tau^2 Sigma]] (eq. augsys; the operator the
+ * PCG applies, plus tau^-2 diag(delta) in its (1,1) block with a linear block set); which = 1:
+ * out = P^{-1} pin, the block preconditioner of Section 6 in the handle's space (d- or m-space,
+ * sdp_newton_info.space).  pin, out: device vectors of m + d doubles, [u; v] with v in the
+ * h-coordinates [svec B; vec N] of range(Q) (d = sdp_newton_info.d of that solve); they may not
+ * overlap.  FP64 in every precision form.  Asynchronous: the work is enqueued on the handle's
+ * stream and the call returns without waiting (synchronize that stream, or order later work on
+ * it, before reading out).  SDP_EINVAL for a NULL argument, a `which` other than 0 or 1, or a handle without a
+ * usable previous solve; SDP_EUNSUPPORTED for which = 1 on a MINRES handle (no preconditioner).
+ * This is the operator-only and preconditioner-only entry of the bench and of the parity tests
+ * that compare each against the oracle's plain definition. */
+sdp_status sdp_apply_augsys(sdp_handle* h, const double* pin, double* out, int32_t which);
+
 /* Same as sdp_newton_solve with every array argument a HOST pointer
  * (pinned memory gives asynchronous copies); the copies to and from the
  * device are part of the call. */

@@ -142,6 +142,23 @@ class NewtonSolver:
     def workspace_bytes(self) -> int:
         return native.sdp_workspace_bytes(self.handle)
 
+    def apply(self, vec, which: int = 0, out=None):
+        """M vec (which 0: the augmented operator of eq. augsys) or P^{-1} vec (which 1: the
+        preconditioner) at the scaling point of the last solve; vec is a device FP64 vector of
+        m + d entries ([u; v], v in h-coordinates)."""
+        torch = self.torch
+        if vec.dtype != torch.float64 or not vec.is_contiguous() or vec.device != self.device:
+            raise ValueError("vec must be a contiguous float64 tensor on the solver's device")
+        if out is None:
+            out = torch.empty_like(vec)
+        cur = torch.cuda.current_stream(self.device)
+        if self.stream.cuda_stream != cur.cuda_stream:     # vec is complete before the handle's stream reads it
+            self.stream.wait_stream(cur)
+        native.sdp_apply_augsys(self.handle, _ptr(vec), _ptr(out), which)   # enqueued on self.stream
+        if self.stream.cuda_stream != cur.cuda_stream:     # later work on the current stream sees out
+            cur.wait_stream(self.stream)
+        return out
+
     def _info(self, ci, st) -> NewtonInfo:
         return NewtonInfo(r=ci.r, d=ci.d, pcg_iters=ci.pcg_iters, space=ci.space, converged=bool(ci.converged),
                           tau=ci.tau, beta=ci.beta, res_norm=ci.res_norm, rhs_norm=ci.rhs_norm, res0_norm=ci.res0_norm, s_A=ci.s_A,

@@ -90,6 +90,7 @@ EXPORTS = {
     "sdp_set_profiling": (c_int32, [c_void_p, c_int32]),
     "sdp_adjoint_dense_noalloc": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
     "sdp_set_tc_wait_limit_ns": (None, [ctypes.c_uint64]),
+    "sdp_apply_augsys": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32]),
     "sdp_bounds_report": (c_int32, [POINTER(ctypes.c_uint64), POINTER(ctypes.c_uint64)]),
     "sdp_bounds_selftest": (c_int32, [c_void_p, c_int64, c_int64]),
     "sdp_workspace_bytes": (c_size_t, [c_void_p]),
@@ -314,6 +315,15 @@ def sdp_adjoint_dense_noalloc(a_dense: int, n: int, m: int, y: int, Y: int, stre
 def sdp_set_tc_wait_limit_ns(ns: int) -> None:
     """Limit of the main-loop waits of the tensor-core product (0: the default 2 s)."""
     load().sdp_set_tc_wait_limit_ns(int(ns))
+
+
+def sdp_apply_augsys(h: int, pin: int, out: int, which: int) -> int:
+    """out = M pin (which 0) or P^{-1} pin (which 1) at the handle's last scaling point."""
+    lib = load()
+    st = lib.sdp_apply_augsys(c_void_p(h), c_void_p(pin), c_void_p(out), which)
+    if st != SDP_OK:
+        raise SdpError(st, lib.sdp_last_error(c_void_p(h)).decode())
+    return st
 
 
 def sdp_bounds_report() -> tuple[int, int, int]:

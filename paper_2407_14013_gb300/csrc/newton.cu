@@ -1533,6 +1533,25 @@ extern "C" sdp_status sdp_newton_resolve(sdp_handle* h, const double* Ct, const 
   return newton_solve_impl(h, nullptr, nullptr, Ct, bt, dX, dy, dS, info, true);
 }
 
+extern "C" sdp_status sdp_apply_augsys(sdp_handle* h, const double* pin, double* out, int32_t which) {
+  if (!h) return fail(nullptr, SDP_EINVAL, "NULL handle");
+  if (!pin || !out) return fail(h, SDP_EINVAL, "NULL array argument");
+  if (which != 0 && which != 1) return fail(h, SDP_EINVAL, "which must be 0 (operator) or 1 (preconditioner)");
+  if (!h->setup_valid) return fail(h, SDP_EINVAL, "no previous Newton solve on this handle");
+  if (which == 1 && h->opt.krylov == 1) return fail(h, SDP_EUNSUPPORTED, "a MINRES handle has no preconditioner");
+  Space& S = h->s64;
+  cudaStream_t st = h->st;
+  h->launches = 0;
+  h->fuse = false;
+  // every kernel of the applies returns at once while the control block's stop flag is set (it
+  // is, after the solve): clear it for this call
+  CU(cudaMemsetAsync(&S.ctl->done, 0, sizeof(int32_t), st));
+  const sdp_status s = which == 0 ? apply_operator(h, S, pin, out, nullptr, 0) : apply_precond(h, S, pin, out, 0);
+  if (s != SDP_OK) return s;
+  CU(cudaGetLastError());   // enqueued on the handle's stream; the caller orders its reads after it
+  return SDP_OK;
+}
+
 extern "C" sdp_status sdp_newton_solve_host(sdp_handle* h, const double* V, const double* lam, const double* Ct,
                                             const double* bt, double* dX, double* dy, double* dS,
                                             sdp_newton_info* info) {
