@@ -612,13 +612,16 @@ __global__ void recover_pre_kernel(int n, int m, const double* __restrict__ Yu, 
                                    const double* __restrict__ u, double* __restrict__ Cw, double* __restrict__ dy,
                                    double* __restrict__ dS, const PcgCtl* __restrict__ ctl) {
   const double t2 = ctl->tau * ctl->tau;
-  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < (int64_t)n * n) {
-    double y = Yu[q], c = Ct[q];
-    if (Cw) Cw[q] = y - t2 * c;
-    dS[q] = c - y / t2;
+  const double it2 = 1.0 / t2;   // one division per thread, not per entry (FP64 division is a long chain)
+  const int64_t nn = (int64_t)n * n, tot = nn > m ? nn : m;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (int64_t)gridDim.x * blockDim.x) {
+    if (q < nn) {
+      const double y = Yu[q], c = Ct[q];
+      if (Cw) Cw[q] = y - t2 * c;
+      dS[q] = c - y * it2;
+    }
+    if (q < m) dy[q] = u[q] * it2;
   }
-  if (q < m) dy[q] = u[q] / t2;
 }
 
 // E Cw with Cw = A^T(u) - tau^2 C~, from F = E C~ of the right side (overwritten):
@@ -1112,7 +1115,8 @@ void launch_hadamard_sq(cudaStream_t st, int64_t nn, const double* E, double* EE
 void launch_recover_pre(cudaStream_t st, int n, int m, const double* Yu, const double* Ct, const double* u,
                         double* Cw, double* dy, double* dS, const PcgCtl* ctl, int64_t* launches) {
   int64_t tot = (int64_t)n * n > m ? (int64_t)n * n : m;
-  recover_pre_kernel<<<nblk(tot, VT), VT, 0, st>>>(n, m, Yu, Ct, u, Cw, dy, dS, ctl);
+  recover_pre_kernel<<<(unsigned)std::min<int64_t>(nblk(tot, VT), 8 * (int64_t)g_num_sms), VT, 0, st>>>(n, m, Yu, Ct, u,
+                                                                                                 Cw, dy, dS, ctl);
   ++*launches;
 }
 
