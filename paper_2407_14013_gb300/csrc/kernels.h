@@ -234,6 +234,14 @@ struct SparseA {
   int32_t* cptr = nullptr;                                  // positions of column b: cptr[b] .. cptr[b+1]-1
   int32_t *yptr = nullptr, *ycol = nullptr, *ypidx = nullptr;   // CSR of the pattern: row i holds
                                                             // (column, position index) pairs
+  // Term pairs of the constraints for the Gram form of the d-space complement: A_i = sum_t w_t
+  // e_{x_t} e_{y_t}^T over its terms (an off-diagonal entry gives two), and every pair (t, t') of
+  // terms of one constraint, grouped by x_t (CSR over the n rows): x' = x_t', y = y_t, y' = y_t',
+  // w = w_t w_t', con = i.  npairs = 0 when the table was not built (too large).
+  int64_t npairs = 0;
+  int32_t *pptr = nullptr, *pxp = nullptr, *py = nullptr, *pyp = nullptr, *pcon = nullptr;
+  double* pw = nullptr;
+  double* pcf = nullptr;   // scratch: the pairs' coefficients of one column pair (j1, j2)
 };
 // Y = scale * A^T(y) on the pattern positions (both triangles); Y is zero elsewhere already.
 void sparse_adjoint(cudaStream_t st, const SparseA& S, int n, const double* y, double scale, double* Y,
@@ -247,6 +255,16 @@ void sparse_B(cudaStream_t st, const SparseA& S, int n, int m, int r, const doub
 // One bounds check of index against bound in the sparse translation unit (no access is made);
 // recorded as a violation in the bounds-checked build when index is outside [0, bound).
 cudaError_t sparse_bounds_selftest(cudaStream_t st, int64_t index, int64_t bound);
+// Gram form of C = sum_i s_i b_i b_i^T (b_i = row i of B = A Q in h-coordinates, s_i = 1 / beta
+// or 1 / Lam_i): for one column pair (j1, j2) of the n x r matrices H_i = Vs^T A_i Q,
+//   Y = W Vs with W = sum over term pairs p of s_{con_p} w_p Q[y_p, j1] Q[y'_p, j2] e_{x_p} e_{x'_p}^T
+// (sparse_gram_spmm), G = Vs^T Y = sum_i s_i H_i[:, j1] H_i[:, j2]^T (a dense product by the caller),
+// then C[h(a1, j1), h(a2, j2)] += c(a1, j1) c(a2, j2) G[a1, a2] through the h-coordinate map
+// (sparse_gram_scatter; C d x d column-major, zeroed by the caller before the first block).
+void sparse_gram_spmm(cudaStream_t st, const SparseA& S, int n, int j1, int j2, const double* Vs, double inv_beta,
+                      const double* lam, double* Y, int64_t* launches);
+void sparse_gram_scatter(cudaStream_t st, int n, int r, int j1, int j2, const double* G, double* C, int64_t ldc,
+                         int64_t* launches);
 // Position values of Y = A^T(y): ypos[p] = sum over the entries e at position p of y[con_e] val_e.
 void sparse_posval(cudaStream_t st, const SparseA& S, const double* y, double* ypos, const int32_t* done,
                    int64_t* launches);

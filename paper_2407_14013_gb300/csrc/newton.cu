@@ -228,6 +228,15 @@ size_t carve(sdp_handle* h, char* base) {
     h->sp.yptr = c.take<int32_t>(n + 1);
     h->sp.ycol = c.take<int32_t>(h->sp.nnzY);
     h->sp.ypidx = c.take<int32_t>(h->sp.nnzY);
+    if (h->sp.npairs > 0) {
+      h->sp.pptr = c.take<int32_t>(n + 1);
+      h->sp.pxp = c.take<int32_t>(h->sp.npairs);
+      h->sp.py = c.take<int32_t>(h->sp.npairs);
+      h->sp.pyp = c.take<int32_t>(h->sp.npairs);
+      h->sp.pcon = c.take<int32_t>(h->sp.npairs);
+      h->sp.pw = c.take<double>(h->sp.npairs);
+      h->sp.pcf = c.take<double>(h->sp.npairs);
+    }
   }
   h->gj_work = c.take<double>(h->gj_work_elems);
   if (h->fx) {
@@ -315,7 +324,8 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
 
   // SPARSE_COO: validate the entries and build the index tables on the host (once per problem)
   std::vector<int32_t> sp_con_ptr, sp_pos_r, sp_pos_c, sp_pos_ptr, sp_perm, sp_epos, sp_yptr, sp_ycol, sp_ypidx,
-      sp_cptr;
+      sp_cptr, sp_pptr, sp_pxp, sp_py, sp_pyp, sp_pcon;
+  std::vector<double> sp_pw;
   std::vector<double> sp_rownorm2;
   if (prob->kind == SDP_A_SPARSE_COO) {
     const int64_t nnz = prob->nnz;
@@ -381,6 +391,62 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
         sp_ypidx[fill[b]++] = p;
       }
     }
+    // term pairs for the Gram form of the d-space complement: A_i = sum_t w_t e_{x_t} e_{y_t}^T
+    // (an off-diagonal entry (r, c) gives the terms (r, c) and (c, r)), every pair of terms of one
+    // constraint, grouped by x_t; built when the table stays moderate (else the complement is formed
+    // from the explicit B)
+    int64_t np = 0;
+    for (int i = 0; i < m; ++i) {
+      int64_t t = 0;
+      for (int e = sp_con_ptr[i]; e < sp_con_ptr[i + 1]; ++e) t += (row[e] == col[e]) ? 1 : 2;
+      np += t * t;
+    }
+    if (np <= (int64_t)1 << 26) {
+      sp_pptr.assign(n + 1, 0);
+      std::vector<int32_t> tx, ty;
+      std::vector<double> tw;
+      for (int pass = 0; pass < 2; ++pass) {   // counts per row x, then the fill
+        std::vector<int32_t> pos;
+        if (pass == 1) {
+          for (int x = 0; x < n; ++x) sp_pptr[x + 1] += sp_pptr[x];
+          pos.assign(sp_pptr.begin(), sp_pptr.end() - 1);
+          sp_pxp.resize(np);
+          sp_py.resize(np);
+          sp_pyp.resize(np);
+          sp_pcon.resize(np);
+          sp_pw.resize(np);
+        }
+        for (int i = 0; i < m; ++i) {
+          tx.clear();
+          ty.clear();
+          tw.clear();
+          for (int e = sp_con_ptr[i]; e < sp_con_ptr[i + 1]; ++e) {
+            tx.push_back(row[e]);
+            ty.push_back(col[e]);
+            tw.push_back(val[e]);
+            if (row[e] != col[e]) {
+              tx.push_back(col[e]);
+              ty.push_back(row[e]);
+              tw.push_back(val[e]);
+            }
+          }
+          for (size_t t = 0; t < tx.size(); ++t) {
+            if (pass == 0) {
+              sp_pptr[tx[t] + 1] += (int32_t)tx.size();
+              continue;
+            }
+            for (size_t u = 0; u < tx.size(); ++u) {
+              const int32_t q = pos[tx[t]]++;
+              sp_pxp[q] = tx[u];
+              sp_py[q] = ty[t];
+              sp_pyp[q] = ty[u];
+              sp_pcon[q] = i;
+              sp_pw[q] = tw[t] * tw[u];
+            }
+          }
+        }
+      }
+    }
   }
 
   h = new (std::nothrow) sdp_handle();
@@ -389,6 +455,7 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
     h->sp.nnz = prob->nnz;
     h->sp.npos = (int)sp_pos_r.size();
     h->sp.nnzY = (int64_t)sp_ycol.size();
+    h->sp.npairs = (int64_t)sp_pxp.size();
     h->sp.m = m;
     h->sp.con = prob->a_con;
     h->sp.row = prob->a_row;
@@ -499,6 +566,15 @@ extern "C" sdp_status sdp_setup(const sdp_problem* prob, const sdp_options* opt_
     CU(cudaMemcpyAsync(h->sp.yptr, sp_yptr.data(), sp_yptr.size() * b32, cudaMemcpyHostToDevice, h->st));
     CU(cudaMemcpyAsync(h->sp.ycol, sp_ycol.data(), sp_ycol.size() * b32, cudaMemcpyHostToDevice, h->st));
     CU(cudaMemcpyAsync(h->sp.ypidx, sp_ypidx.data(), sp_ypidx.size() * b32, cudaMemcpyHostToDevice, h->st));
+    if (h->sp.npairs > 0) {
+      const size_t np = (size_t)h->sp.npairs;
+      CU(cudaMemcpyAsync(h->sp.pptr, sp_pptr.data(), sp_pptr.size() * b32, cudaMemcpyHostToDevice, h->st));
+      CU(cudaMemcpyAsync(h->sp.pxp, sp_pxp.data(), np * b32, cudaMemcpyHostToDevice, h->st));
+      CU(cudaMemcpyAsync(h->sp.py, sp_py.data(), np * b32, cudaMemcpyHostToDevice, h->st));
+      CU(cudaMemcpyAsync(h->sp.pyp, sp_pyp.data(), np * b32, cudaMemcpyHostToDevice, h->st));
+      CU(cudaMemcpyAsync(h->sp.pcon, sp_pcon.data(), np * b32, cudaMemcpyHostToDevice, h->st));
+      CU(cudaMemcpyAsync(h->sp.pw, sp_pw.data(), np * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    }
   }
   e = cudaMallocHost(&h->ctl_host, sizeof(PcgCtl));
   if (e != cudaSuccess) {
@@ -671,6 +747,16 @@ cudaError_t pack_apply_dense(sdp_handle* h, Space& S, cudaStream_t st, int r, co
 // The dense d-space preconditioner apply runs as one cooperative launch.
 bool pc_coop_on(const sdp_handle* h) {
   return h->space == 1 && !h->lin && h->kind == SDP_A_DENSE_SVEC && h->coop_pc && !h->no_coop;
+}
+
+// The SPARSE kind's d-space complement in its Gram form (no explicit B) where that is cheaper:
+// r^2 column pairs, each a sparse product over the term pairs and one n^3 product, against the
+// m d^2 / 2 of B^T B.
+bool gram_on(const sdp_handle* h) {
+  if (h->kind != SDP_A_SPARSE_COO || h->space != 1 || h->mixed || h->opt.krylov == 1 || h->sp.npairs == 0)
+    return false;
+  const double n = h->n, r = h->r, d = h->d, m = h->m;
+  return r * r * ((double)h->sp.npairs * n + n * n * n) < 0.5 * m * d * d;
 }
 
 // Small DIAG problems in the m-space form run their whole FP64 PCG solve as one cluster launch
@@ -1261,7 +1347,7 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
       }
     }
   } else if (h->kind == SDP_A_SPARSE_COO) {
-    sparse_B(st, h->sp, n, m, r, S.Vs, S.B, d, S.Bt, m, L);
+    if (!gram_on(h)) sparse_B(st, h->sp, n, m, r, S.Vs, S.B, d, S.Bt, m, L);   // else C needs no B
   } else {
     launch_hadamard_sq(st, (int64_t)n * n, S.E, S.EE, L);
     if (h->space == 1) {
@@ -1286,7 +1372,20 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
   } else if (h->space == 1) {
     // C = beta^{-1} B^T B + tau^2 Sigma  (B row-major m x d == column-major d x m); with a linear
     // block, C = B^T Lam^{-1} B + tau^2 Sigma
-    if (h->lin) {
+    if (gram_on(h)) {
+      // Gram form: C = sum_i s_i pack(H_i) pack(H_i)^T with H_i = Vs^T A_i Q, by column pairs
+      // (j1, j2) of the H_i: G = Vs^T W_{j1 j2} Vs over the sparse W of the constraints' term
+      // pairs, scattered into C through the h-coordinate map
+      CU(cudaMemsetAsync(S.Pinv, 0, (size_t)d * d * sizeof(double), st));
+      const double ib = 1.0 / h->ctl_host->beta_pc;
+      for (int j1 = 0; j1 < r; ++j1)
+        for (int j2 = 0; j2 < r; ++j2) {
+          // (S.F and S.Z as scratch: S.Y must stay zero off the pattern for the sparse A^T(.))
+          sparse_gram_spmm(st, h->sp, n, j1, j2, S.Vs, ib, h->lin ? h->lin_lam : nullptr, S.F, L);
+          CU(gemm_big(h, st, true, false, n, n, n, 1.0, S.Vs, n, S.F, n, 0.0, S.Z, n, S.ws, ws, L));
+          sparse_gram_scatter(st, n, r, j1, j2, S.Z, S.Pinv, d, L);
+        }
+    } else if (h->lin) {
       launch_lin_scale_rows(st, m, d, S.B, h->lin_lam, h->lin_Bw, L);
       CU(gemm_big(h, st, false, true, d, d, m, 1.0, h->lin_Bw, d, h->lin_Bw, d, 0.0, S.Pinv, d, S.ws, ws, L,
                   GEMM_LOWER));

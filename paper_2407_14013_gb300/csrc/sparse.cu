@@ -17,6 +17,8 @@
 //   Y Bm        one thread per (row, column of Bm) sums its row's pattern entries (SpMM)
 //   (E Y E)_ab  only at the pattern positions: <E[:, a], (Y E)[:, b]>, one warp each
 // which replaces the two dense n^3 products E Y and (E Y) E by O(nnz(Y) n + npos n) work.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -48,7 +50,8 @@ enum : int {
   kEyPtr, kEyPidx, kEyCol,                              // sparse_EY_kernel
   kDotPtr, kDotRow,                                     // pos_dots_col_kernel
   kApPtr, kApPos, kApRC,                                // sparse_apply_pos_kernel
-  kSelfTest                                             // oob_selftest_kernel
+  kSelfTest,                                            // oob_selftest_kernel
+  kGramPtr, kGramIdx                                    // gram_spmm_kernel, gram_coef_kernel
 };
 
 // Y[r, c] = Y[c, r] = sum over the entries e at position (r, c) of y[con_e] val_e (times scale)
@@ -285,6 +288,64 @@ __global__ void sparse_sumsq_kernel(int64_t nnz, const int32_t* __restrict__ row
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
+// Gram form of the d-space complement, one column pair (j1, j2) of the H_i = Vs^T A_i Q:
+// cf_p = s_{con_p} w_p Q[y_p, j1] Q[y'_p, j2] for every term pair p (Q = Vs[:, :r]) ...
+__global__ void gram_coef_kernel(int64_t np, int n, int j1, int j2, const int32_t* __restrict__ py,
+                                 const int32_t* __restrict__ pyp, const int32_t* __restrict__ pcon,
+                                 const double* __restrict__ pw, const double* __restrict__ Vs, double inv_beta,
+                                 const double* __restrict__ lam, int m, double* __restrict__ cf) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
+    const int y = py[p], yp = pyp[p], i = pcon[p];
+    double v = 0.0;
+    if (WC_IN(kGramIdx, y, n) && WC_IN(kGramIdx, yp, n) && WC_IN(kGramIdx, i, m))
+      v = pw[p] * Vs[y + (int64_t)j1 * n] * Vs[yp + (int64_t)j2 * n] * (lam ? 1.0 / lam[i] : inv_beta);
+    cf[p] = v;
+  }
+}
+
+// ... then Y = W Vs: Y[x, k] = sum over the pairs p of row x of cf_p Vs[x'_p, k]; grid (rows, columns)
+__global__ void gram_spmm_kernel(int n, int64_t np, const int32_t* __restrict__ pptr, const int32_t* __restrict__ pxp,
+                                 const double* __restrict__ cf, const double* __restrict__ Vs, double* __restrict__ Y) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n) return;
+  const int k = blockIdx.y;
+  const double* vk = Vs + (int64_t)k * n;
+  double s = 0.0;
+  for (int p = pptr[x]; p < pptr[x + 1]; ++p) {
+    if (!WC_IN(kGramPtr, p, np)) break;
+    const int xp = pxp[p];
+    if (!WC_IN(kGramIdx, xp, n)) continue;
+    s = fma(cf[p], vk[xp], s);
+  }
+  Y[x + (int64_t)k * n] = s;
+}
+
+// h-coordinate of entry (a, j) of an n x r matrix and its weight in pack(.):  a < r: the svec
+// position of (max, min) with 1 on the diagonal and sqrt2 / 2 off it; a >= r: r(r+1)/2 + (a - r) +
+// j (n - r) with sqrt2
+__device__ __forceinline__ int64_t hcoord(int n, int r, int a, int j, double& c) {
+  if (a < r) {
+    const int i = a > j ? a : j, jj = a > j ? j : a;
+    c = (i == jj) ? 1.0 : 0.5 * WC_SQRT2;
+    return svec_index(r, i, jj);
+  }
+  c = WC_SQRT2;
+  return (int64_t)r * (r + 1) / 2 + (a - r) + (int64_t)j * (n - r);
+}
+
+// C[h(a1, j1), h(a2, j2)] += c(a1, j1) c(a2, j2) G[a1, a2]: within one (j1, j2) every (a1, a2) lands
+// on its own entry of C, so no atomics; the column pairs run one after another (a fixed order)
+__global__ void gram_scatter_kernel(int n, int r, int j1, int j2, const double* __restrict__ G, double* __restrict__ C,
+                                    int64_t ldc) {
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nn; q += (int64_t)gridDim.x * blockDim.x) {
+    const int a1 = (int)(q % n), a2 = (int)(q / n);
+    double c1, c2;
+    const int64_t h1 = hcoord(n, r, a1, j1, c1), h2 = hcoord(n, r, a2, j2, c2);
+    C[h1 + h2 * ldc] += c1 * c2 * G[q];
+  }
+}
+
 // One check of index i against bound and nothing else (no memory is addressed): lets a test see
 // a violation recorded and reported without an out-of-range index ever reaching an access.
 __global__ void oob_selftest_kernel(int64_t i, int64_t bound) { (void)WC_IN(kSelfTest, i, bound); }
@@ -362,6 +423,24 @@ void sparse_apply_pos(cudaStream_t st, const SparseA& S, int n, int m, int r, co
                       const double* Q, double* out, const int32_t* done, int64_t* launches) {
   sparse_apply_pos_kernel<<<nb(m), ST, 0, st>>>(n, m, r, S.con_ptr, S.row, S.col, S.val, S.epos, zpos, U, Q, out,
                                                 lens(S), done);
+  if (launches) ++*launches;
+}
+
+void sparse_gram_spmm(cudaStream_t st, const SparseA& S, int n, int j1, int j2, const double* Vs, double inv_beta,
+                      const double* lam, double* Y, int64_t* launches) {
+  double* cf = S.pcf;   // the pairs' coefficients for this (j1, j2)
+  const int64_t cb = std::min<int64_t>((S.npairs + ST - 1) / ST, 16 * (int64_t)g_num_sms);
+  gram_coef_kernel<<<(unsigned)std::max<int64_t>(cb, 1), ST, 0, st>>>(S.npairs, n, j1, j2, S.py, S.pyp, S.pcon, S.pw,
+                                                                      Vs, inv_beta, lam, S.m, cf);
+  gram_spmm_kernel<<<dim3(nb(n), (unsigned)n), ST, 0, st>>>(n, S.npairs, S.pptr, S.pxp, cf, Vs, Y);
+  if (launches) *launches += 2;
+}
+
+void sparse_gram_scatter(cudaStream_t st, int n, int r, int j1, int j2, const double* G, double* C, int64_t ldc,
+                         int64_t* launches) {
+  const int64_t nn = (int64_t)n * n;
+  const int64_t blocks = std::min<int64_t>((nn + ST - 1) / ST, 16 * (int64_t)g_num_sms);
+  gram_scatter_kernel<<<(unsigned)blocks, ST, 0, st>>>(n, r, j1, j2, G, C, ldc);
   if (launches) ++*launches;
 }
 
