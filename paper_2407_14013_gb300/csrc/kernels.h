@@ -260,11 +260,12 @@ cudaError_t sparse_bounds_selftest(cudaStream_t st, int64_t index, int64_t bound
 //   Y = W Vs with W = sum over term pairs p of s_{con_p} w_p Q[y_p, j1] Q[y'_p, j2] e_{x_p} e_{x'_p}^T
 // (sparse_gram_spmm), G = Vs^T Y = sum_i s_i H_i[:, j1] H_i[:, j2]^T (a dense product by the caller),
 // then C[h(a1, j1), h(a2, j2)] += c(a1, j1) c(a2, j2) G[a1, a2] through the h-coordinate map
-// (sparse_gram_scatter; C d x d column-major, zeroed by the caller before the first block).
+// (sparse_gram_scatter; C d x d column-major, zeroed by the caller before the first block; with
+// mirror also at the transposed entries, the (j2, j1) pair's share, so j1 <= j2 suffices).
 void sparse_gram_spmm(cudaStream_t st, const SparseA& S, int n, int j1, int j2, const double* Vs, double inv_beta,
                       const double* lam, double* Y, int64_t* launches);
-void sparse_gram_scatter(cudaStream_t st, int n, int r, int j1, int j2, const double* G, double* C, int64_t ldc,
-                         int64_t* launches);
+void sparse_gram_scatter(cudaStream_t st, int n, int r, int j1, int j2, bool mirror, const double* G, double* C,
+                         int64_t ldc, int64_t* launches);
 // Position values of Y = A^T(y): ypos[p] = sum over the entries e at position p of y[con_e] val_e.
 void sparse_posval(cudaStream_t st, const SparseA& S, const double* y, double* ypos, const int32_t* done,
                    int64_t* launches);

@@ -750,13 +750,13 @@ bool pc_coop_on(const sdp_handle* h) {
 }
 
 // The SPARSE kind's d-space complement in its Gram form (no explicit B) where that is cheaper:
-// r^2 column pairs, each a sparse product over the term pairs and one n^3 product, against the
-// m d^2 / 2 of B^T B.
+// r (r + 1) / 2 column pairs, each a sparse product over the term pairs and one n^3 product,
+// against the m d^2 / 2 of B^T B.
 bool gram_on(const sdp_handle* h) {
   if (h->kind != SDP_A_SPARSE_COO || h->space != 1 || h->mixed || h->opt.krylov == 1 || h->sp.npairs == 0)
     return false;
   const double n = h->n, r = h->r, d = h->d, m = h->m;
-  return r * r * ((double)h->sp.npairs * n + n * n * n) < 0.5 * m * d * d;
+  return 0.5 * r * (r + 1) * ((double)h->sp.npairs * n + n * n * n) < 0.5 * m * d * d;
 }
 
 // Small DIAG problems in the m-space form run their whole FP64 PCG solve as one cluster launch
@@ -1379,11 +1379,11 @@ sdp_status newton_solve_impl(sdp_handle* h, const double* V, const double* lam, 
       CU(cudaMemsetAsync(S.Pinv, 0, (size_t)d * d * sizeof(double), st));
       const double ib = 1.0 / h->ctl_host->beta_pc;
       for (int j1 = 0; j1 < r; ++j1)
-        for (int j2 = 0; j2 < r; ++j2) {
+        for (int j2 = j1; j2 < r; ++j2) {   // G_{j2 j1} = G_{j1 j2}^T: the scatter mirrors it
           // (S.F and S.Z as scratch: S.Y must stay zero off the pattern for the sparse A^T(.))
           sparse_gram_spmm(st, h->sp, n, j1, j2, S.Vs, ib, h->lin ? h->lin_lam : nullptr, S.F, L);
           CU(gemm_big(h, st, true, false, n, n, n, 1.0, S.Vs, n, S.F, n, 0.0, S.Z, n, S.ws, ws, L));
-          sparse_gram_scatter(st, n, r, j1, j2, S.Z, S.Pinv, d, L);
+          sparse_gram_scatter(st, n, r, j1, j2, j2 != j1, S.Z, S.Pinv, d, L);
         }
     } else if (h->lin) {
       launch_lin_scale_rows(st, m, d, S.B, h->lin_lam, h->lin_Bw, L);

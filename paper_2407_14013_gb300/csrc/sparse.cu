@@ -334,15 +334,20 @@ __device__ __forceinline__ int64_t hcoord(int n, int r, int a, int j, double& c)
 }
 
 // C[h(a1, j1), h(a2, j2)] += c(a1, j1) c(a2, j2) G[a1, a2]: within one (j1, j2) every (a1, a2) lands
-// on its own entry of C, so no atomics; the column pairs run one after another (a fixed order)
-__global__ void gram_scatter_kernel(int n, int r, int j1, int j2, const double* __restrict__ G, double* __restrict__ C,
-                                    int64_t ldc) {
+// on its own entry of C, so no atomics; the column pairs run one after another (a fixed order).
+// mirror (j1 != j2): the same value also at the transposed entry, which is the (j2, j1) pair's
+// contribution (G_{j2 j1} = G_{j1 j2}^T): one product serves both pairs.  The two writes of one thread coincide only when h1 = h2 (then both add, as the two
+// pairs do); two threads never write one entry.
+__global__ void gram_scatter_kernel(int n, int r, int j1, int j2, int mirror, const double* __restrict__ G,
+                                    double* __restrict__ C, int64_t ldc) {
   const int64_t nn = (int64_t)n * n;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nn; q += (int64_t)gridDim.x * blockDim.x) {
     const int a1 = (int)(q % n), a2 = (int)(q / n);
     double c1, c2;
     const int64_t h1 = hcoord(n, r, a1, j1, c1), h2 = hcoord(n, r, a2, j2, c2);
-    C[h1 + h2 * ldc] += c1 * c2 * G[q];
+    const double v = c1 * c2 * G[q];
+    C[h1 + h2 * ldc] += v;
+    if (mirror) C[h2 + h1 * ldc] += v;
   }
 }
 
@@ -436,11 +441,11 @@ void sparse_gram_spmm(cudaStream_t st, const SparseA& S, int n, int j1, int j2, 
   if (launches) *launches += 2;
 }
 
-void sparse_gram_scatter(cudaStream_t st, int n, int r, int j1, int j2, const double* G, double* C, int64_t ldc,
-                         int64_t* launches) {
+void sparse_gram_scatter(cudaStream_t st, int n, int r, int j1, int j2, bool mirror, const double* G, double* C,
+                         int64_t ldc, int64_t* launches) {
   const int64_t nn = (int64_t)n * n;
   const int64_t blocks = std::min<int64_t>((nn + ST - 1) / ST, 16 * (int64_t)g_num_sms);
-  gram_scatter_kernel<<<(unsigned)blocks, ST, 0, st>>>(n, r, j1, j2, G, C, ldc);
+  gram_scatter_kernel<<<(unsigned)blocks, ST, 0, st>>>(n, r, j1, j2, mirror ? 1 : 0, G, C, ldc);
   if (launches) ++*launches;
 }
 
