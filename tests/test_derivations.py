@@ -9,6 +9,11 @@ step, checked against the oracle's definitions on CPU.
   2 (Q (Lam - tau I) Q^T)_il (Qp Lamp Qp^T)_il, with Qp Lamp Qp^T = tau (E - Q Q^T).
 - DIAG kind, products with B without B: B t = rowdot(Vs unpack(t), Q) and
   B^T u = pack(Vs^T diag(u) Q).
+- SPARSE kind, d-space core in its Gram form: with A_i = sum_t w_t e_{x_t} e_{y_t}^T over its terms
+  (an off-diagonal entry gives (r, c) and (c, r)), H_i = Vs^T A_i Q has vec(H_i) =
+  sum_t w_t Q[y_t, :] (x) Vs[x_t, :], so block (j1, j2) of sum_i vec(H_i) vec(H_i)^T is
+  Vs^T W_{j1 j2} Vs, W_{j1 j2} = sum_i sum_{t, t'} w_t w_t' Q[y_t, j1] Q[y_t', j2] e_{x_t} e_{x_t'}^T;
+  B^T B follows through the h-coordinate map of pack(.), one product per unordered (j1, j2).
 """
 import numpy as np
 import pytest
@@ -51,3 +56,53 @@ def test_diag_B_products_without_B(n, r):
     H = Vs.T @ (u[:, None] * s.Q)
     packed = np.concatenate([reform.svec(0.5 * (H[:r] + H[:r].T)), np.sqrt(2) * H[r:].reshape(-1, order="F")])
     assert np.allclose(packed, B.T @ u, rtol=0, atol=1e-13 * np.abs(B.T @ u).max())
+
+
+def _gram_btb(prob, s):
+    """B^T B assembled as the CUDA path does (Gram blocks over the term pairs), in numpy."""
+    n, m, r, d = prob.n, prob.m, s.r, s.d
+    Vs = np.hstack([s.Q, s.Qp])
+    pairs = []
+    for i in range(m):
+        terms = []
+        for e in np.where(prob.a_con == i)[0]:
+            x, y, w = int(prob.a_row[e]), int(prob.a_col[e]), float(prob.a_val[e])
+            terms.append((x, y, w))
+            if x != y:
+                terms.append((y, x, w))
+        pairs += [(t[0], u[0], t[1], u[1], t[2] * u[2]) for t in terms for u in terms]
+    nb = r * (r + 1) // 2
+
+    def hc(a, j):
+        if a < r:
+            i, jj = max(a, j), min(a, j)
+            return jj * r - jj * (jj - 1) // 2 + (i - jj), (1.0 if i == jj else 0.5 * np.sqrt(2.0))
+        return nb + (a - r) + j * (n - r), np.sqrt(2.0)
+
+    C = np.zeros((d, d))
+    for j1 in range(r):
+        for j2 in range(j1, r):
+            Wm = np.zeros((n, n))
+            for x, xp, y, yp, w in pairs:
+                Wm[x, xp] += w * s.Q[y, j1] * s.Q[yp, j2]
+            G = Vs.T @ Wm @ Vs
+            for a1 in range(n):
+                h1, c1 = hc(a1, j1)
+                for a2 in range(n):
+                    h2, c2 = hc(a2, j2)
+                    C[h1, h2] += c1 * c2 * G[a1, a2]
+                    if j1 != j2:
+                        C[h2, h1] += c1 * c2 * G[a1, a2]
+    return C
+
+
+@pytest.mark.parametrize("mk", [lambda: W.completion(8, 7, 2, 0.4, 31), lambda: W.random_sparse(11, 25, 3, 32)],
+                         ids=["completion", "random_sparse"])
+def test_sparse_gram_form_equals_btb(mk):
+    prob = mk()
+    sp = W.scaling_point(prob.n, 3, 1e-3, 33)
+    s = reform.split(sp.V, sp.lam, r_hat=4, s_A=oops.row_norm_scale(prob))
+    B = reform.AQ_matrix(prob, s)
+    ref = B.T @ B
+    got = _gram_btb(prob, s)
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
