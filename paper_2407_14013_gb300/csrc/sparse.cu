@@ -17,6 +17,11 @@
 //   Y Bm        one thread per (row, column of Bm) sums its row's pattern entries (SpMM)
 //   (E Y E)_ab  only at the pattern positions: <E[:, a], (Y E)[:, b]>, one warp each
 // which replaces the two dense n^3 products E Y and (E Y) E by O(nnz(Y) n + npos n) work.
+//
+// The d-space complement C = tau^2 Sigma + sum_i s_i b_i b_i^T (b_i = row i of B = A Q) is formed
+// without B where that is cheaper: for each column pair (j1 <= j2) of the H_i = Vs^T A_i Q, the
+// block sum_i s_i H_i[:, j1] H_i[:, j2]^T equals Vs^T W Vs with W sparse over the constraints'
+// term pairs (gram_*), and its entries go to C through the h-coordinate map of pack(.).
 #include <algorithm>
 
 #include "common.cuh"
