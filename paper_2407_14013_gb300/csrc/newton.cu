@@ -1,8 +1,9 @@
 // C ABI and orchestration of one Newton solve on the well-conditioned reformulation
 // (Section 3 eq. augsys / eq. recover, Section 6 preconditioner, Cor. pcg).
 //
-// Per call (all on the handle's stream; one host read after the split for r, then one
-// read every `check_every` PCG iterations for the stop flag):
+// Per call (all on the handle's stream; one host read after the split for r; the PCG loop is
+// one graph launch with a WHILE node conditioned on the device stop flag, or, where that
+// graph is refused, replays of `check_every` iterations with a host read of the flag between):
 //   a1  split (eq. EQSigdef): sort eig(W), choose r, tau, E = Vs diag(e) Vs^T, Sigma, beta
 //   a2  B = A Q (m x d) and the inverse of the preconditioner's Schur complement
 //       (d-space C = tau^2 Sigma + beta^{-1} B^T B, or m-space K = beta I + B D^{-1} B^T)
@@ -1040,9 +1041,10 @@ sdp_status pcg_start(sdp_handle* h, Space& S, bool mixed, const double* gsub, do
   return SDP_OK;
 }
 
-// PCG iterations until the device stop flag is set.  `check_every` iterations run as one
-// replay of a captured CUDA graph (every kernel returns at once after the stop), with one
-// host read of the control block between replays.
+// PCG iterations until the device stop flag is set: one launch of a graph whose WHILE node
+// repeats one iteration while the flag is clear or, where that graph is refused, replays of a
+// captured graph of `check_every` iterations (every kernel returns at once after the stop),
+// with one host read of the control block between replays.
 sdp_status krylov_loop(sdp_handle* h, Space& S, bool mixed, bool minres) {
   const int every = h->opt.check_every;
   const int nt = h->m + h->d;
