@@ -17,12 +17,14 @@ torchrun; value = iterations of all ranks / max-over-ranks time.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import math
 import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -103,51 +105,112 @@ def read_traffic(name="fx_rows_gemvT_sensing200.txt"):
 
 
 class ClockSampler:
-    FIELDS = ["clocks.sm", "clocks.max.sm", "clocks_event_reasons.active", "clocks_event_reasons.hw_slowdown",
-              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
-              "clocks_event_reasons.sw_power_cap"]
+    """SM clocks and throttle reasons from nvidia-smi, sampled every `interval_ms` while the
+    timed region runs.  Each sample carries nvidia-smi's own timestamp, so `summary(window)` can
+    keep the samples taken inside the timed region (wall-clock seconds, one interval of slack on
+    each side) whatever the pipe's buffering.  `__enter__` gives the sampler up to `first_wait_s`
+    to print its first line before the region starts; if it exits at once (an interval it
+    refuses), it is restarted at 200 ms."""
+    FIELDS = ["timestamp", "clocks.sm", "clocks.max.sm", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    def __init__(self, index: int):
-        self.index = index
+    def __init__(self, index: int, interval_ms: int = 50, first_wait_s: float = 1.0, cmd: str = "nvidia-smi"):
+        self.index, self.interval_ms, self.first_wait_s, self.cmd = index, interval_ms, first_wait_s, cmd
         self.proc = None
+        self.thread = None
+        self.lines = []
+        self.out = ""
+        self.used_ms = None
 
-    def __enter__(self):
+    def _read(self, proc):
+        for line in proc.stdout:
+            self.lines.append(line.rstrip("\n"))
+
+    def _start(self, ms: int) -> bool:
+        """Start the sampler; False if it could not be started or exited before printing."""
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+            proc = subprocess.Popen(
+                [self.cmd, "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", str(ms)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
-            self.proc = None
+            return False
+        self.proc, self.used_ms = proc, ms
+        self.thread = threading.Thread(target=self._read, args=(proc,), daemon=True)
+        self.thread.start()
+        t_end = time.perf_counter() + self.first_wait_s
+        while time.perf_counter() < t_end and not self.lines:
+            if proc.poll() is not None:
+                self.thread.join(timeout=5)
+                if self.lines:
+                    return True
+                self.proc = self.thread = None
+                return False
+            time.sleep(0.01)
+        return True
+
+    def _stop(self):
+        if self.proc is not None:
+            if self.proc.poll() is None:
+                self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+        self.proc = self.thread = None
+
+    def __enter__(self):
+        self.lines = []
+        if not self._start(self.interval_ms) and self.interval_ms != 200:
+            self.lines = []
+            self._start(200)
         return self
 
     def __exit__(self, *a):
-        self.out = ""
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                self.out, _ = self.proc.communicate(timeout=5)
-            except Exception:
-                self.proc.kill()
+        self._stop()
+        self.out = "\n".join(self.lines)
 
-    def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    @staticmethod
+    def _stamp(text: str):
+        try:
+            return datetime.datetime.strptime(text, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    def summary(self, window=None):
+        """Median SM clock, the maximum clock and the throttle reasons seen active.  With
+        window = (t0, t1) (time.time() at the start and the end of the timed steps) only the
+        samples taken inside it count; if none is, all samples of the sampler's span do, and
+        "window" says so."""
+        rows = []
         for line in (self.out or "").strip().splitlines():
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 7:
+            if len(parts) < len(self.FIELDS):
                 continue
             try:
-                sm.append(float(parts[0]))
-                mx = float(parts[1])
+                sm, mx = float(parts[1]), float(parts[2])
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[3:7]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
+            active = {nm for nm, v in zip(self.REASONS, parts[4:8]) if v.lower().startswith("active")}
+            rows.append((self._stamp(parts[0]), sm, mx, active))
+        scope = "sampler span"
+        if window is not None and rows:
+            slack = (self.used_ms or self.interval_ms) / 1e3
+            inside = [r for r in rows if r[0] is not None and window[0] - slack <= r[0] <= window[1] + slack]
+            if inside:
+                rows, scope = inside, "timed steps"
+            else:
+                scope = "sampler span (no sample inside the timed steps)"
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        reasons = set().union(*(r[3] for r in rows))
+        return {"sm_mhz": statistics.median(r[1] for r in rows), "sm_max_mhz": rows[-1][2],
+                "reasons": sorted(reasons), "samples": len(rows), "interval_ms": self.used_ms,
+                "window": scope}
 
 
 def other_configs(dev, reps: int = 2, only=None, tc_n: int = 5000):
@@ -636,6 +699,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
         wall0 = time.perf_counter()
+        acc["t0"] = time.time()
         for k in range(steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -657,6 +721,7 @@ def run_ours(args):
                 acc[key] += val
         torch.cuda.synchronize(dev)
         acc["wall"] = time.perf_counter() - wall0
+        acc["t1"] = time.time()
         if world > 1:
             dist.barrier()
         return acc
@@ -815,7 +880,7 @@ def run_ours(args):
                               "recover": res["rec"] / args.steps},
         "roofline": roofline,
         "operator_only": op_only,
-        "clocks": clk.summary(),
+        "clocks": clk.summary(window=(res["t0"], res["t1"])),
         "gpu_launches": launches,
         "e2e": {"value": e2e_iters / e2e_s if e2e_steps else None, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
@@ -835,7 +900,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
