@@ -13,7 +13,7 @@ def pytest_configure(config):
 
 
 def pytest_collection_modifyitems(config, items):
-    # GPU tests are skipped, not failed, where no GPU exists; -m gpu selects them on a GPU machine
+    # GPU tests are skipped, not failed, where no GPU exists; -m gpu selects them on a machine with a GPU
     try:
         import torch
         has_gpu = torch.cuda.is_available()

@@ -1,6 +1,6 @@
 """GPU parity of the Newton solve (C ABI) against the CPU oracle.
 
-Tolerance: the spec bar for the FP64 form is relative 1e-8.  Both sides solve the
+Tolerance: the FP64 form must agree to relative 1e-8.  Both sides solve the
 same well-conditioned augmented system (eq. augsys) to ||r|| <= 1e-12 ||g||; their
 difference is bounded by cond(augsys) * 1e-12 plus rounding, so 1e-8 holds for the
 moderate spectra used here.  Against the plain Schur-complement definition the FP64
