@@ -551,6 +551,11 @@ int64_t sdp_last_launch_count(const sdp_handle* h);
 /* Message for the most recent failure on this handle (or of sdp_setup when h is NULL). */
 const char* sdp_last_error(const sdp_handle* h);
 
+/* Release the handle: waits for the work on its stream, then frees its device workspace, its
+ * pinned control block, the outer loop's buffers, its captured graphs, events and side streams
+ * (the stream passed to sdp_setup stays the caller's).  NULL is ignored;
+ * the handle must not be used afterwards.  Device pointers the caller passed in stay the
+ * caller's. */
 void sdp_destroy(sdp_handle* h);
 
 #ifdef __cplusplus
